@@ -1,0 +1,403 @@
+"""FP64 CPU oracle for the SOR stress-majorization layout method.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package.  It shares no code with the CUDA library in ``paper_1711_01228_gb300``
+and imports nothing from it; the only common inputs are arrays made by the
+seeded generators in ``paper_1711_01228_gb300.synth``, which hold none of the
+method's arithmetic.
+
+Paper: Wang & Wang, "A Fast Successive Over-Relaxation Algorithm for
+Force-Directed Network Graph Drawing", Sci. China Inf. Sci. 55:677 (2012).
+
+What each function follows, and what pins it (the tests under ``tests/`` named
+``test_oracle_*`` hold the pins):
+
+=====================  ====================================  ===============================================
+function               paper passage                          pin
+=====================  ====================================  ===============================================
+apsp / bfs_row         d_ij "predefined ideal distance",       scipy.sparse.csgraph.shortest_path; Manhattan
+                       Sec. 2 Eq. (1); shortest paths as in    distance on grids; Floyd-Warshall brute force
+                       Gansner et al. (Sec. 2, Prop. 2.3)
+stress                 Eq. (1), w_ij = d_ij^-2 (Sec. 5.1)     closed forms on 2-4 vertex graphs; trace form
+                                                              g(X,X) of Prop. 2.1; invariances
+rhs  (L^X X)           Prop. 2.1, Eq. (2-5)                   finite-difference gradient of sum w d r
+lw_matvec (L^W P)      Prop. 2.1                              finite-difference gradient of sum w r^2; L^W 1=0
+forces                 -1/2 grad of Eq. (1)                   finite differences of stress
+PinnedSolver (H)       Eq. (4), Eq. (2-5), pinning x_1 = 0    residual of Eq. (2-5); majorization chain of
+                       (Sec. 2 after Prop. 2.3)               Prop. 2.2; H minimises g(., X); K2 one-step
+sor_run                Algorithm 1 (omega = 0), Algorithm 2,  monotone stress (Prop. 2.2); omega=0 equals
+                       Eq. (10); strategies of Sec. 5.2       Algorithm 1; analytic optima (C4, K1,3);
+                                                              observed rate = 1 - lambda_min (Thm 3.2)
+omega_draw             probabilistic strategy, Sec. 5.2.3     splitmix64 published test vector; prior
+                                                              frequencies
+=====================  ====================================  ===============================================
+
+The termination rule is not defined by the paper ("until some termination
+conditions were satisfied", Algorithms 1 and 2); the two rules here are the
+library's documented readings (relative displacement of centred layouts, or
+relative stress decrease).  They are pinned only by their definitions.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fd_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+
+ERR_DISCONNECTED = 3
+
+STOP_REL_DISP = 0
+STOP_REL_STRESS = 1
+OMEGA_FIXED = 0
+OMEGA_PROB = 1
+OMEGA_ENUM = 2
+
+_lib_handle = None
+
+
+def build() -> str:
+    """Compile fd_oracle.c with gcc into oracle/_build/liboracle.so."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not os.path.exists(_SO)) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _lib():
+    global _lib_handle
+    if _lib_handle is None:
+        lib = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        i32 = ctypes.c_int
+        lib.orc_bfs.argtypes = [i32, P, P, i32, P, P]
+        lib.orc_apsp.argtypes = [i32, P, P, P, i32, P]
+        lib.orc_apsp.restype = i32
+        lib.orc_stress.argtypes = [i32, i32, P, P]
+        lib.orc_stress.restype = ctypes.c_double
+        for name in ("orc_rhs", "orc_lw_matvec", "orc_forces"):
+            getattr(lib, name).argtypes = [i32, i32, P, P, P]
+        lib.orc_force_row.argtypes = [i32, i32, P, i32, P, P]
+        lib.orc_rhs_row.argtypes = [i32, i32, P, i32, P, P]
+        lib.orc_stress_stream.argtypes = [i32, i32, P, P, P, ctypes.c_double, ctypes.POINTER(i32)]
+        lib.orc_stress_stream.restype = ctypes.c_double
+        _lib_handle = lib
+    return _lib_handle
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(X) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(X, dtype=np.float64))
+
+
+def _i32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+
+
+# --------------------------------------------------------------------------
+# Ideal distances
+# --------------------------------------------------------------------------
+
+def apsp(row_ptr, col_idx, edge_len=None, policy: int = 0):
+    """Dense [n, n] FP64 matrix of ideal distances d_ij (shortest paths).
+
+    Returns (status, D); status 3 means a disconnected graph under policy 0.
+    Policy 1 gives unreachable pairs d = (largest finite d) + 1.
+    """
+    rp, ci = _i32(row_ptr), _i32(col_idx)
+    n = rp.shape[0] - 1
+    D = np.zeros((n, n), dtype=np.float64)
+    ln = None if edge_len is None else _f64(edge_len)
+    st = _lib().orc_apsp(n, _p(rp), _p(ci), None if ln is None else _p(ln), int(policy), _p(D))
+    return int(st), D
+
+
+def bfs_row(row_ptr, col_idx, src: int) -> np.ndarray:
+    """Hop distances from one source (int32, -1 if unreachable)."""
+    rp, ci = _i32(row_ptr), _i32(col_idx)
+    n = rp.shape[0] - 1
+    dist = np.empty(n, dtype=np.int32)
+    q = np.empty(n, dtype=np.int32)
+    _lib().orc_bfs(n, _p(rp), _p(ci), int(src), _p(dist), _p(q))
+    return dist
+
+
+# --------------------------------------------------------------------------
+# Pair functions (Eq. (1), Prop. 2.1)
+# --------------------------------------------------------------------------
+
+def stress(X, D) -> float:
+    """f(X) of Eq. (1) with w = d^-2."""
+    X, D = _f64(X), _f64(D)
+    n, dim = X.shape
+    return float(_lib().orc_stress(n, dim, _p(X), _p(D)))
+
+
+def _pairfn(name, X, D):
+    X, D = _f64(X), _f64(D)
+    n, dim = X.shape
+    out = np.zeros_like(X)
+    getattr(_lib(), name)(n, dim, _p(X), _p(D), _p(out))
+    return out
+
+
+def rhs(X, D) -> np.ndarray:
+    """b = L^X X, the right-hand side of Eq. (2-5)."""
+    return _pairfn("orc_rhs", X, D)
+
+
+def lw_matvec(P, D) -> np.ndarray:
+    """L^W P."""
+    return _pairfn("orc_lw_matvec", P, D)
+
+
+def forces(X, D) -> np.ndarray:
+    """F = (L^X - L^W) X = -1/2 grad f(X)."""
+    return _pairfn("orc_forces", X, D)
+
+
+def force_row(X, i: int, drow) -> np.ndarray:
+    X, dr = _f64(X), _f64(drow)
+    n, dim = X.shape
+    out = np.zeros(dim)
+    _lib().orc_force_row(n, dim, _p(X), int(i), _p(dr), _p(out))
+    return out
+
+
+def rhs_row(X, i: int, drow) -> np.ndarray:
+    X, dr = _f64(X), _f64(drow)
+    n, dim = X.shape
+    out = np.zeros(dim)
+    _lib().orc_rhs_row(n, dim, _p(X), int(i), _p(dr), _p(out))
+    return out
+
+
+def stress_stream(X, row_ptr, col_idx, dfill: float = -1.0) -> float:
+    """Eq. (1) for unit-edge graphs, one BFS per row instead of a stored D."""
+    X = _f64(X)
+    rp, ci = _i32(row_ptr), _i32(col_idx)
+    n, dim = X.shape
+    st = ctypes.c_int(0)
+    f = _lib().orc_stress_stream(n, dim, _p(X), _p(rp), _p(ci), float(dfill), ctypes.byref(st))
+    if st.value != 0:
+        raise ValueError(f"stress_stream status {st.value}")
+    return float(f)
+
+
+# --------------------------------------------------------------------------
+# Matrices of Prop. 2.1 (explicit, for small n) and the majorant g
+# --------------------------------------------------------------------------
+
+def weights(D) -> np.ndarray:
+    """w_ij = d_ij^-2 off the diagonal, 0 on it (Sec. 5.1)."""
+    D = _f64(D)
+    W = np.zeros_like(D)
+    off = ~np.eye(D.shape[0], dtype=bool)
+    W[off] = 1.0 / (D[off] ** 2)
+    return W
+
+
+def lw_dense(D) -> np.ndarray:
+    """L^W of Prop. 2.1 as a dense matrix."""
+    W = weights(D)
+    L = -W
+    np.fill_diagonal(L, W.sum(axis=1))
+    return L
+
+
+def ly_dense(Y, D) -> np.ndarray:
+    """L^Y of Prop. 2.1 as a dense matrix (entries 0 where y_i = y_j)."""
+    Y, D = _f64(Y), _f64(D)
+    n = Y.shape[0]
+    L = np.zeros((n, n))
+    for i in range(n):
+        for j in range(n):
+            if i == j:
+                continue
+            r = float(np.sqrt(np.sum((Y[i] - Y[j]) ** 2)))
+            if r != 0.0:
+                L[i, j] = -(1.0 / D[i, j] ** 2) * D[i, j] / r
+    np.fill_diagonal(L, -L.sum(axis=1))
+    return L
+
+
+def majorant(X, Y, D) -> float:
+    """g(X, Y) = tr(X^T L^W X) - 2 tr(X^T L^Y Y) + C of Eq. (2)."""
+    X, Y, D = _f64(X), _f64(Y), _f64(D)
+    iu = np.triu_indices(D.shape[0], 1)
+    C = float(np.sum((1.0 / D[iu] ** 2) * D[iu] ** 2))
+    return float(np.trace(X.T @ lw_dense(D) @ X) - 2.0 * np.trace(X.T @ ly_dense(Y, D) @ Y) + C)
+
+
+# --------------------------------------------------------------------------
+# The majorization step H (Eq. (4), Eq. (2-5)) with the pinning x_1 = 0
+# --------------------------------------------------------------------------
+
+class PinnedSolver:
+    """Solves L^W Z = b with the first vertex pinned at the origin.
+
+    The paper removes the first row and column of L^W and the first row of
+    the right-hand side; the reduced matrix is strictly diagonally dominant
+    and positive definite, and is factored here once by dense Cholesky
+    (one of the solvers the paper names after Prop. 2.3).
+    """
+
+    def __init__(self, D):
+        D = _f64(D)
+        self.n = D.shape[0]
+        if self.n > 1:
+            A = lw_dense(D)[1:, 1:]
+            self.L = np.linalg.cholesky(A)
+        else:
+            self.L = None
+
+    def solve(self, b) -> np.ndarray:
+        b = _f64(b)
+        Z = np.zeros_like(b)
+        if self.n <= 1:
+            return Z
+        import scipy.linalg as sla
+        y = sla.solve_triangular(self.L, b[1:], lower=True)
+        Z[1:] = sla.solve_triangular(self.L.T, y, lower=False)
+        return Z
+
+
+def H(X, D, solver: PinnedSolver | None = None) -> np.ndarray:
+    """X^{k+1} = H(X^k): argmin_X g(X, X^k), Eq. (4)."""
+    solver = solver or PinnedSolver(D)
+    return solver.solve(rhs(X, D))
+
+
+# --------------------------------------------------------------------------
+# Relaxation factors (Sec. 5.2)
+# --------------------------------------------------------------------------
+
+_MASK64 = (1 << 64) - 1
+_GAMMA = 0x9E3779B97F4A7C15
+
+
+def splitmix64(seed: int, k: int) -> int:
+    """k-th output (k = 0, 1, ...) of SplitMix64 seeded with `seed`
+    (Steele, Lea & Flood, OOPSLA 2014; constants of Vigna's splitmix64.c)."""
+    z = (seed + (k + 1) * _GAMMA) & _MASK64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _MASK64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _MASK64
+    return z ^ (z >> 31)
+
+
+PROB_OMEGAS = (0.5, 1.0, 1.5, 2.0)
+PROB_CUMULATIVE = (0.3, 0.6, 0.8, 1.0)
+
+
+def omega_draw(seed: int, k: int) -> float:
+    """Probabilistic strategy (Sec. 5.2.3): one roulette draw per iteration
+    from the prior P(0.5)=P(1.0)=0.3, P(1.5)=P(2.0)=0.2."""
+    u = (splitmix64(seed, k) >> 11) * (1.0 / 9007199254740992.0)
+    for om, c in zip(PROB_OMEGAS, PROB_CUMULATIVE):
+        if u < c:
+            return om
+    return PROB_OMEGAS[-1]
+
+
+ENUM_OMEGAS = tuple(0.5 * i for i in range(19))  # {0, 0.5, ..., 9}, Sec. 5.2.2
+
+
+# --------------------------------------------------------------------------
+# Algorithm 2 (Algorithm 1 is omega = 0)
+# --------------------------------------------------------------------------
+
+def _centred(X):
+    return X - X.mean(axis=0, keepdims=True)
+
+
+def criterion(stop: int, X_old, X_new, f_old: float, f_new: float) -> float:
+    """Termination criterion after one iteration.
+
+    STOP_REL_DISP:   ||c(X_new) - c(X_old)||_F / ||c(X_new)||_F, c = centring.
+    STOP_REL_STRESS: (f_old - f_new) / f_old.
+    A zero denominator gives 0 (nothing left to move or reduce).
+    """
+    if stop == STOP_REL_DISP:
+        a, b = _centred(X_new), _centred(X_old)
+        den = float(np.sqrt(np.sum(a * a)))
+        return 0.0 if den == 0.0 else float(np.sqrt(np.sum((a - b) ** 2))) / den
+    if stop == STOP_REL_STRESS:
+        return 0.0 if f_old == 0.0 else (f_old - f_new) / f_old
+    raise ValueError("unknown stop rule")
+
+
+@dataclass
+class RunResult:
+    X: np.ndarray
+    iterations: int
+    stress: float
+    trace_f: list = field(default_factory=list)       # f(X^0), f(X^1), ...
+    trace_accept: list = field(default_factory=list)  # line 6 outcome per iteration
+    trace_omega: list = field(default_factory=list)   # omega used per iteration
+    trace_crit: list = field(default_factory=list)    # termination criterion per iteration
+    trace_fH: list = field(default_factory=list)      # f(H(X^k)) per iteration
+    converged: bool = False
+
+
+def sor_step(X, D, omega_k: float, strategy: int = OMEGA_FIXED, solver=None):
+    """One pass of Algorithm 2's loop body: lines 4-8.
+
+    Returns (X_next, f(X_next), accepted, omega_used, f(H(X))).
+    """
+    X = _f64(X)
+    solver = solver or PinnedSolver(D)
+    Z = solver.solve(rhs(X, D))                      # line 4, Eq. (2-5)
+    fZ = stress(Z, D)
+    if strategy == OMEGA_ENUM:                        # Sec. 5.2.2
+        best_f, best_om, best_X = None, None, None
+        for om in ENUM_OMEGAS:
+            Xt = (1.0 + om) * Z - om * X
+            ft = stress(Xt, D)
+            if best_f is None or ft < best_f:
+                best_f, best_om, best_X = ft, om, Xt
+        return best_X, best_f, best_om > 0.0, best_om, fZ
+    Xt = (1.0 + omega_k) * Z - omega_k * X            # line 5, Eq. (10)
+    ft = stress(Xt, D)
+    if ft <= fZ:                                      # line 6
+        return Xt, ft, True, omega_k, fZ              # line 7
+    return Z, fZ, False, omega_k, fZ
+
+
+def sor_run(D, X0, omega: float = 0.0, strategy: int = OMEGA_FIXED, seed: int = 0,
+            stop: int = STOP_REL_DISP, tol: float = 1e-4, max_iter: int = 1000,
+            solver: PinnedSolver | None = None) -> RunResult:
+    """Algorithm 2 from X^0 until the criterion drops below tol or max_iter
+    iterations ran.  omega = 0 with the fixed strategy is Algorithm 1."""
+    D = _f64(D)
+    X = _f64(X0).copy()
+    solver = solver or PinnedSolver(D)
+    f = stress(X, D)
+    res = RunResult(X=X, iterations=0, stress=f, trace_f=[f])
+    for k in range(max_iter):
+        om = omega_draw(seed, k) if strategy == OMEGA_PROB else omega
+        Xn, fn, acc, om_used, fZ = sor_step(X, D, om, strategy, solver)
+        crit = criterion(stop, X, Xn, f, fn)
+        res.trace_f.append(fn)
+        res.trace_accept.append(bool(acc))
+        res.trace_omega.append(float(om_used))
+        res.trace_crit.append(float(crit))
+        res.trace_fH.append(float(fZ))
+        X, f = Xn, fn
+        res.iterations = k + 1
+        if crit < tol:
+            res.converged = True
+            break
+    res.X, res.stress = X, f
+    return res
