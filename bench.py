@@ -1,0 +1,315 @@
+#!/usr/bin/env python3
+"""Benchmark of the SOR stress-majorization layout path on GB300.
+
+Workload (graph-drawing benchmark stand-ins, 2-D, X^0 uniform in [0,1]^2):
+Erdos-Renyi n=10,000 mean degree 6, Delaunay mesh of 20,000 uniform points,
+random binary tree n=16,383.  One step lays out every graph of the workload:
+ideal distances from the CSR (multi-source BFS), then Algorithm 2 to
+convergence (relative displacement 1e-4, at most 1000 iterations) at each
+omega of the step's sweep.  The default sweep is the classical factor 1.5
+(the paper's omega = 0.5); ``--sweep`` runs the classical factors 1.0 .. 1.9.
+
+Metric: unordered pair interactions per second over the whole step (every
+all-pairs pass counts n(n-1)/2 pairs: each CG matvec, and each stress/RHS
+evaluation of a candidate layout); SOR iterations per second beside it.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1711_01228_gb300 import synth  # noqa: E402
+
+WORKLOAD = ("er10k", "delaunay20k", "tree16k")
+FLOP_K2 = {1: 13, 2: 19, 3: 25}   # stress + L^X X per unordered pair per candidate
+FLOP_MV = {1: 4, 2: 8, 3: 12}     # L^W p per unordered pair
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(
+        os.environ.get("LOCAL_RANK", "0"))
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[4:8]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_inputs(names, seed=0):
+    out = []
+    for nm in names:
+        rp, ci = synth.workload(nm, seed)
+        n = len(rp) - 1
+        out.append((nm, rp, ci, synth.initial_layout(n, 2, seed)))
+    return out
+
+
+def omegas(sweep: bool):
+    # classical SOR factor omega_c = 1 + omega (paper's omega)
+    return [round(0.1 * k, 1) for k in range(10)] if sweep else [0.5]
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_1711_01228_gb300 import api, build
+
+    build.build()
+    api.lib()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    inputs = make_inputs(args.workload.split(","))
+    oms = omegas(args.sweep)
+    dev_inputs = [(nm, torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev), torch.from_numpy(x0).to(dev))
+                  for nm, rp, ci, x0 in inputs]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
+    opts = dict(tol=1e-4, max_iter=1000, stop=api.STOP_REL_DISP)
+
+    def one_step(acc, host=False):
+        for (nm, rp, ci, x0), (_, rpd, cid, x0d) in zip(inputs, dev_inputs):
+            if host:
+                L = api.Layout(rp, ci, dim=2, disconnected_policy=1)
+            else:
+                L = api.Layout(rpd, cid, dim=2, disconnected_policy=1, stream=stream.cuda_stream)
+            info = L.info()
+            acc["apsp_ms"] += info["apsp_ms"]
+            acc["h2d"] += rp.nbytes + ci.nbytes
+            for om in oms:
+                if host:
+                    X = x0.copy()
+                    acc["h2d"] += X.nbytes
+                else:
+                    X = x0d.clone()
+                r = L.run(X, omega=om, **opts)
+                if host:
+                    acc["d2h"] += X.nbytes + 8
+                st = r.stats
+                acc["pairs"] += st["pair_passes"] * st["pairs"]
+                acc["iters"] += st["iterations"]
+                acc["kernel_ms"] += st["kernel_ms"]
+                acc["launches"] += 1
+                acc["flops"] += st["pairs"] * (st["matvec_passes"] * FLOP_MV[2] + st["stress_passes"] * FLOP_K2[2])
+                acc["cg"] += st["cg_steps"]
+                acc["runs"].append((nm, om, st["iterations"], st["cg_steps"], st["final_stress"]))
+            acc["n_launch_total"] += 4 + len(oms)  # BFS, fill, row sums, + one layout kernel per run
+            L.close()
+
+    def zero():
+        return dict(pairs=0.0, iters=0, kernel_ms=0.0, apsp_ms=0.0, flops=0.0, cg=0, launches=0, h2d=0, d2h=0,
+                    runs=[], n_launch_total=0)
+
+    for _ in range(args.warmup):
+        one_step(zero())
+    torch.cuda.synchronize()
+    # ----- device-resident timed region
+    sampler = ClockSampler(local_rank)
+    acc = zero()
+    times = []
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    for _ in range(args.steps):
+        flush.fill_(1.0)  # evict L2 between steps (outside the timed interval)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        one_step(acc)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    total_ms = sum(times)
+    # ----- end to end through the public API with host buffers
+    acc_e = zero()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one_step(acc_e, host=True)
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3
+    if world > 1:
+        t = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms, e2e_ms = float(t[0]), float(t[1])
+    value = acc["pairs"] * world / (total_ms / 1e3)
+    e2e_value = acc_e["pairs"] * world / (e2e_ms / 1e3)
+    peaks, src = _peaks()
+    clk = peaks.get("sm_max_mhz", 2070.0)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = sms * 128 * 2 * clk * 1e6 / 1e12  # TFLOP/s at the maximum SM clock
+    achieved = acc["flops"] / (acc["kernel_ms"] / 1e3) / 1e12
+    line = {
+        "metric": "pair-interactions/s",
+        "value": value,
+        "unit": "pairs/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "+".join(args.workload.split(",")) + " 2-D, X0 U[0,1]^2 seed 0, omega_c "
+                   + ("1.0-1.9 sweep" if args.sweep else "1.5") + ", rel-disp tol 1e-4, max 1000 iters",
+                   "graphs": {nm: {"n": len(rp) - 1, "m": int(rp[-1]) // 2} for nm, rp, _, _ in inputs},
+                   "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
+        "sor_iterations_per_s": acc["iters"] * world / (total_ms / 1e3),
+        "cg_steps_per_sor_iteration": acc["cg"] / max(acc["iters"], 1),
+        "gpu_launches": acc["n_launch_total"],
+        "roofline": {"bound": "alu", "kernel": "fd_main_kernel", "achieved": achieved, "peak": fp32_peak,
+                     "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                     "peak_note": f"FP32 CUDA cores {sms} SMs x 128 x 2 flop at {clk:.0f} MHz ({src} max clock)"},
+        "apsp": {"kernel": "bfs_batch_kernel", "ms_per_step": acc["apsp_ms"] / args.steps},
+        "layout_kernel_ms_per_step": acc["kernel_ms"] / args.steps,
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": acc_e["h2d"] // args.steps,
+                "d2h_bytes_per_step": acc_e["d2h"] // args.steps},
+        "runs": acc["runs"][: len(inputs) * len(oms)],
+    }
+    return line
+
+
+def cpu_sample(budget_s: float):
+    """The oracle, as it is, on a bounded sample of the workload: one pass each
+    of stress, L^X X and L^W p over all pairs of the Erdos-Renyi graph
+    (distances from the oracle's BFS, not timed), repeated to ~budget_s."""
+    import oracle
+
+    rp, ci = synth.workload("er10k")
+    n = len(rp) - 1
+    X = synth.initial_layout(n, 2, 0).astype(np.float64)
+    st, D = oracle.apsp(rp, ci, policy=1)
+    pairs = n * (n - 1) / 2
+    done, t0 = 0, time.perf_counter()
+    while True:
+        oracle.stress(X, D)
+        oracle.rhs(X, D)
+        oracle.lw_matvec(X, D)
+        done += 3
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    return {"value": done * pairs / el, "unit": "pairs/s", "cores": 1, "kind": "oracle",
+            "sample": f"oracle stress + L^X X + L^W p, {done} single-thread FP64 passes over the {int(pairs)} "
+                      f"pairs of ER n=10,000 ({el:.1f} s)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    for _ in range(args.warmup):
+        cpu_sample(1.0)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_sample(3.0))
+    el = time.perf_counter() - t0
+    v = statistics.mean(x["value"] for x in vals)
+    return {"impl": "reference", "metric": "pair-interactions/s", "value": v, "unit": "pairs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "er10k oracle sample (see cpu_baseline.sample)"},
+            "cpu_baseline": {**vals[-1], "value": v},
+            "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=",".join(WORKLOAD))
+    ap.add_argument("--sweep", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local_rank = _env_rank()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+    else:
+        line = run_ours(args, rank, world, local_rank)
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_sample(10.0)
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,209 @@
+/*
+ * fd_layout.h -- C ABI of the GB300 (sm_103a) stress-majorization layout
+ * engine with successive over-relaxation.
+ *
+ * Method: Wang & Wang, "A Fast Successive Over-Relaxation Algorithm for
+ * Force-Directed Network Graph Drawing", Sci. China Inf. Sci. 55:677 (2012).
+ *
+ *   stress   f(X) = sum_{i<j} w_ij (||x_i - x_j|| - d_ij)^2           Sec. 2, Eq. (1)
+ *   weights  w_ij = d_ij^{-2}                                         Sec. 5.1
+ *   d_ij     shortest-path length in the graph (hop count, or the sum
+ *            of edge lengths when lengths are given)                  Sec. 2, Sec. 5.4
+ *   step H   solve L^W X^{k+1} = L^{X^k} X^k, first vertex pinned      Prop. 2.3, Eq. (2-5)
+ *   SOR      X~ = (1 + omega) X^{k+1} - omega X^k, kept iff
+ *            f(X~) <= f(X^{k+1})                                       Algorithm 2, Eq. (10)
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Pointers may be host or device (CUDA) memory; the library detects which
+ *    with cudaPointerGetAttributes and copies host data in and out on its
+ *    stream.  Ownership never transfers: the library never frees a caller
+ *    pointer and keeps none after the call returns.
+ *  - Vertices are 0-based.  Positions are float32, row-major [n][dim],
+ *    dim in {1, 2, 3}.
+ *  - Graphs are int32 CSR: row_ptr[n+1] (row_ptr[0] = 0, non-decreasing),
+ *    col_idx[row_ptr[n]] with 0 <= col_idx < n.  The graph must be
+ *    undirected: every (u, v) entry needs a (v, u) entry (with the same
+ *    length when lengths are given).  Self loops and repeated entries are
+ *    allowed and ignored.
+ *  - All GPU work runs on the CUDA stream given at creation (NULL = the
+ *    legacy default stream) on the device that was current at creation.
+ *    Every call returns only after its results are on the host (the stream
+ *    is synchronised), so host scalars are valid on return.
+ *  - Errors are returned as fd_status; the handle also keeps the last
+ *    error.  The library never aborts the process and never traps on the
+ *    GPU: device-side failures (non-finite values, a wait that timed out)
+ *    come back as status codes.
+ *  - A handle is not thread-safe: one host thread at a time per handle.
+ */
+#ifndef FD_LAYOUT_H
+#define FD_LAYOUT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fd_layout fd_layout; /* opaque; owns the distance tiles and all scratch */
+
+typedef enum {
+  FD_OK = 0,
+  FD_ERR_ARG = 1,           /* bad argument (null pointer, dim out of range, n < 1, ...) */
+  FD_ERR_CSR = 2,           /* malformed or non-symmetric CSR, bad edge length */
+  FD_ERR_DISCONNECTED = 3,  /* graph not connected and disconnected_policy == 0 */
+  FD_ERR_NONFINITE = 4,     /* NaN/Inf in the positions or in a computed stress */
+  FD_ERR_CG_BREAKDOWN = 5,  /* p^T L^W p <= 0 inside the linear solve */
+  FD_ERR_CG_MAXITER = 6,    /* reserved (a solve that hits cg_max is counted, not fatal) */
+  FD_ERR_TIMEOUT = 7,       /* a device-side grid barrier wait exceeded its time limit */
+  FD_ERR_OOM = 8,           /* device or host allocation failed */
+  FD_ERR_CUDA = 9,          /* other CUDA runtime error */
+  FD_ERR_UNIMPLEMENTED = 10 /* option not supported by this build */
+} fd_status;
+
+/* How omega is chosen each iteration (Sec. 5.2). */
+typedef enum {
+  FD_OMEGA_FIXED = 0, /* omega constant over the run (Sec. 5.2.1); omega = 0 is Algorithm 1 */
+  FD_OMEGA_PROB = 1,  /* roulette over P(0.5)=P(1)=0.3, P(1.5)=P(2)=0.2 (Sec. 5.2.3) */
+  FD_OMEGA_ENUM = 2   /* argmin of f over omega in {0, 0.5, ..., 9} (Sec. 5.2.2) */
+} fd_omega_strategy;
+
+/* Termination rule.  The paper leaves it open ("until some termination
+ * conditions were satisfied", Algorithms 1 and 2); these are the library's
+ * two readings, each tested after every iteration. */
+typedef enum {
+  FD_STOP_REL_DISP = 0,  /* ||c(X^{k+1}) - c(X^k)||_F / ||c(X^{k+1})||_F < tol, c = centring */
+  FD_STOP_REL_STRESS = 1 /* (f(X^k) - f(X^{k+1})) / f(X^k) < tol */
+} fd_stop_rule;
+
+typedef struct {
+  double omega;      /* the paper's omega >= 0 (Eq. (10)); classical SOR factor is 1 + omega */
+  int32_t strategy;  /* fd_omega_strategy */
+  int32_t stop;      /* fd_stop_rule */
+  uint64_t seed;     /* FD_OMEGA_PROB: draw k uses SplitMix64(seed), k-th output */
+  double tol;        /* termination threshold (see fd_stop_rule) */
+  int32_t max_iter;  /* maximum outer iterations (each one H step) */
+  int32_t cg_max;    /* maximum conjugate-gradient steps per H step */
+  double cg_tol;     /* CG stops when ||r_c|| <= cg_tol * ||b_c|| for every column c */
+} fd_options;
+
+/* Statistics of the last fd_run / fd_sor_step / fd_energy / fd_forces call. */
+typedef struct {
+  int32_t iterations;      /* outer iterations performed */
+  int32_t cg_steps;        /* total CG steps over all H solves */
+  int32_t cg_maxed;        /* H solves that stopped at cg_max before reaching cg_tol */
+  int32_t accepted;        /* iterations whose extrapolation was kept (line 6 true) */
+  double pair_passes;      /* all-pairs passes evaluated (matvec = 1, stress/RHS per candidate = 1) */
+  double pairs;            /* unordered vertex pairs per pass: n (n - 1) / 2 */
+  double final_stress;     /* f at the returned layout */
+  double final_crit;       /* last termination criterion value */
+  double matvec_passes;    /* passes of y = L^W p (inside the H solves) */
+  double stress_passes;    /* passes of stress (+ L^X X or force) per candidate layout */
+  double kernel_ms;        /* device time of the call's layout kernel (CUDA events on the handle's stream) */
+} fd_stats;
+
+/* Library facts about a handle. */
+typedef struct {
+  int32_t n, dim;
+  int32_t diameter;        /* largest finite d_ij (hop count; rounded up when weighted) */
+  int32_t code_bytes;      /* bytes per stored pair: 1 (uint8 hop counts) or 4 (float32) */
+  int32_t tile;            /* vertices per tile side */
+  int32_t num_tiles;       /* stored tiles (unordered tile pairs) */
+  int64_t distance_bytes;  /* device bytes of the stored distance tiles */
+  int32_t disconnected;    /* 1 if some pairs were unreachable and filled by policy 1 */
+  int32_t sm_count;        /* SMs of the device */
+  int32_t grid;            /* CTAs of the cooperative layout kernel */
+  int32_t tasks;           /* work items (runs of tiles) per all-pairs pass */
+  double apsp_ms;          /* device time of the shortest-path kernel at creation (CUDA events) */
+} fd_info;
+
+/* Fills *opt with the defaults: omega 0.5, FIXED, REL_DISP, seed 0,
+ * tol 1e-4, max_iter 1000, cg_max 200, cg_tol 1e-6. */
+void fd_options_default(fd_options* opt);
+
+/* Builds a handle for graph G = (V, E) with n vertices laid out in dim
+ * dimensions: validates the CSR, computes every ideal distance d_ij as a
+ * shortest-path length (multi-source BFS on the GPU; label-correcting
+ * relaxation when edge_len is given) and the row sums s_i = sum_j w_ij of
+ * L^W (Prop. 2.1).  Sec. 2, Eq. (1); w = d^-2 per Sec. 5.1.
+ *   out        receives the handle (NULL on failure)
+ *   n          number of vertices (>= 1)
+ *   dim        layout dimension, 1..3
+ *   row_ptr    int32[n+1], host or device
+ *   col_idx    int32[row_ptr[n]], host or device
+ *   edge_len   float32[row_ptr[n]] positive finite lengths, or NULL for unit edges
+ *   disconnected_policy  0: FD_ERR_DISCONNECTED if some pair is unreachable;
+ *                        1: unreachable pairs get d = (largest finite d) + 1
+ *   cuda_stream cudaStream_t to run on, or NULL
+ * Errors: FD_ERR_ARG, FD_ERR_CSR, FD_ERR_DISCONNECTED, FD_ERR_OOM, FD_ERR_CUDA. */
+fd_status fd_layout_create(fd_layout** out, int32_t n, int32_t dim, const int32_t* row_ptr,
+                           const int32_t* col_idx, const float* edge_len,
+                           int32_t disconnected_policy, void* cuda_stream);
+
+/* Releases every device and host resource of the handle (NULL is a no-op). */
+void fd_layout_destroy(fd_layout* h);
+
+/* Stress f(X) of Eq. (1) at X (float32 [n][dim], host or device), written
+ * to *f_out (host).  Errors: FD_ERR_ARG, FD_ERR_NONFINITE, FD_ERR_CUDA. */
+fd_status fd_energy(fd_layout* h, const float* X, double* f_out);
+
+/* Force F = (L^X - L^W) X = -(1/2) grad f(X) (Prop. 2.1 and Eq. (1)):
+ * F_i = sum_{j != i} w_ij (d_ij / ||x_i - x_j|| - 1)(x_i - x_j); coincident
+ * pairs contribute zero.  X and F_out are float32 [n][dim], host or device;
+ * F_out is written.  Errors: FD_ERR_ARG, FD_ERR_NONFINITE, FD_ERR_CUDA. */
+fd_status fd_forces(fd_layout* h, const float* X, float* F_out);
+
+/* One iteration of Algorithm 2 (lines 4-8): H step by CG on Eq. (2-5) with
+ * the first vertex pinned at the origin, extrapolation Eq. (10) with the
+ * omega the strategy gives for iteration index k (k >= 0), acceptance test
+ * of line 6 (ties accept).  X (float32 [n][dim], host or device) holds X^k
+ * on entry and the accepted X^{k+1} on return.
+ *   f_out      f(X^{k+1}) (host; may be NULL)
+ *   accepted   1 if the extrapolated layout was kept (host; may be NULL)
+ *   crit_out   termination criterion of opt->stop (host; may be NULL)
+ * Errors: FD_ERR_ARG, FD_ERR_NONFINITE, FD_ERR_CG_BREAKDOWN, FD_ERR_TIMEOUT,
+ * FD_ERR_CUDA, FD_ERR_UNIMPLEMENTED. */
+fd_status fd_sor_step(fd_layout* h, float* X, const fd_options* opt, int32_t k, double* f_out,
+                      int32_t* accepted, double* crit_out);
+
+/* Algorithm 2 from X^0 (omega = 0 with FD_OMEGA_FIXED is Algorithm 1) until
+ * the termination rule holds or opt->max_iter iterations ran.  The whole
+ * loop runs on the GPU in one cooperative launch; nothing returns to the
+ * host between iterations.  X (float32 [n][dim], host or device) holds X^0
+ * on entry and the final layout on return.
+ *   iters_out  iterations performed (host; may be NULL)
+ *   f_out      final stress (host; may be NULL)
+ *   trace_f    NULL or host double[max_iter + 1]: f(X^0), f(X^1), ...
+ * Errors: as fd_sor_step. */
+fd_status fd_run(fd_layout* h, float* X, const fd_options* opt, int32_t* iters_out,
+                 double* f_out, double* trace_f);
+
+/* Per-iteration trace of the last fd_run, copied to host arrays of length
+ * >= iterations (any pointer may be NULL): accepted flags, omega used,
+ * CG steps and termination criterion of each iteration. */
+fd_status fd_run_trace(fd_layout* h, int32_t* accepted, double* omega, int32_t* cg_steps,
+                       double* crit);
+
+/* Ideal distances of rows row0 .. row0 + nrows - 1 (all n columns, d_ii = 0)
+ * as stored by the handle, written as float64 to the host array
+ * out[nrows][n].  Unit-edge graphs give exact integers.  Errors: FD_ERR_ARG,
+ * FD_ERR_CUDA. */
+fd_status fd_distance_rows(fd_layout* h, int32_t row0, int32_t nrows, double* out);
+
+/* Facts about the handle (host struct). */
+fd_status fd_layout_info(const fd_layout* h, fd_info* info);
+
+/* Statistics of the last call on the handle (host struct). */
+fd_status fd_last_stats(const fd_layout* h, fd_stats* stats);
+
+/* Status of the last failing call on the handle (FD_OK if none). */
+fd_status fd_last_error(const fd_layout* h);
+
+/* Static, human-readable name of a status code. */
+const char* fd_status_string(fd_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FD_LAYOUT_H */

@@ -1,0 +1,263 @@
+"""Python binding of the C ABI in include/fd_layout.h (argument marshalling only).
+
+Every computation runs in ``libfdlayout.so`` (CUDA kernels for sm_103a); this
+module only converts arrays to pointers and status codes to exceptions.  There
+is no CPU fallback: if the library is missing, :func:`lib` raises.
+
+Arrays may be numpy arrays (host memory) or torch tensors (host or CUDA);
+positions are float32 ``[n, dim]``, graphs int32 CSR.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import build as _build
+
+FD_OK = 0
+STATUS_NAMES = {
+    0: "FD_OK", 1: "FD_ERR_ARG", 2: "FD_ERR_CSR", 3: "FD_ERR_DISCONNECTED", 4: "FD_ERR_NONFINITE",
+    5: "FD_ERR_CG_BREAKDOWN", 6: "FD_ERR_CG_MAXITER", 7: "FD_ERR_TIMEOUT", 8: "FD_ERR_OOM",
+    9: "FD_ERR_CUDA", 10: "FD_ERR_UNIMPLEMENTED",
+}
+OMEGA_FIXED, OMEGA_PROB, OMEGA_ENUM = 0, 1, 2
+STOP_REL_DISP, STOP_REL_STRESS = 0, 1
+
+
+class FdError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = int(status)
+        super().__init__(f"{where}: {STATUS_NAMES.get(self.status, self.status)}")
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("omega", ctypes.c_double), ("strategy", ctypes.c_int32), ("stop", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
+                ("cg_max", ctypes.c_int32), ("cg_tol", ctypes.c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("cg_steps", ctypes.c_int32), ("cg_maxed", ctypes.c_int32),
+                ("accepted", ctypes.c_int32), ("pair_passes", ctypes.c_double), ("pairs", ctypes.c_double),
+                ("final_stress", ctypes.c_double), ("final_crit", ctypes.c_double),
+                ("matvec_passes", ctypes.c_double), ("stress_passes", ctypes.c_double),
+                ("kernel_ms", ctypes.c_double)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("dim", ctypes.c_int32), ("diameter", ctypes.c_int32),
+                ("code_bytes", ctypes.c_int32), ("tile", ctypes.c_int32), ("num_tiles", ctypes.c_int32),
+                ("distance_bytes", ctypes.c_int64), ("disconnected", ctypes.c_int32),
+                ("sm_count", ctypes.c_int32), ("grid", ctypes.c_int32), ("tasks", ctypes.c_int32),
+                ("apsp_ms", ctypes.c_double)]
+
+
+EXPORTED = ["fd_options_default", "fd_layout_create", "fd_layout_destroy", "fd_energy", "fd_forces",
+            "fd_sor_step", "fd_run", "fd_run_trace", "fd_distance_rows", "fd_layout_info",
+            "fd_last_stats", "fd_last_error", "fd_status_string"]
+
+_LIB = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """The loaded libfdlayout.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_1711_01228_gb300.build.build() "
+                           "(nvcc, sm_103a); there is no CPU fallback")
+    L = ctypes.CDLL(path)
+    P, i32, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double
+    L.fd_options_default.argtypes = [ctypes.POINTER(Options)]
+    L.fd_options_default.restype = None
+    L.fd_layout_create.argtypes = [ctypes.POINTER(P), i32, i32, P, P, P, i32, P]
+    L.fd_layout_create.restype = i32
+    L.fd_layout_destroy.argtypes = [P]
+    L.fd_layout_destroy.restype = None
+    L.fd_energy.argtypes = [P, P, ctypes.POINTER(f64)]
+    L.fd_energy.restype = i32
+    L.fd_forces.argtypes = [P, P, P]
+    L.fd_forces.restype = i32
+    L.fd_sor_step.argtypes = [P, P, ctypes.POINTER(Options), i32, ctypes.POINTER(f64), ctypes.POINTER(i32),
+                              ctypes.POINTER(f64)]
+    L.fd_sor_step.restype = i32
+    L.fd_run.argtypes = [P, P, ctypes.POINTER(Options), ctypes.POINTER(i32), ctypes.POINTER(f64), P]
+    L.fd_run.restype = i32
+    L.fd_run_trace.argtypes = [P, P, P, P, P]
+    L.fd_run_trace.restype = i32
+    L.fd_distance_rows.argtypes = [P, i32, i32, P]
+    L.fd_distance_rows.restype = i32
+    L.fd_layout_info.argtypes = [P, ctypes.POINTER(Info)]
+    L.fd_layout_info.restype = i32
+    L.fd_last_stats.argtypes = [P, ctypes.POINTER(Stats)]
+    L.fd_last_stats.restype = i32
+    L.fd_last_error.argtypes = [P]
+    L.fd_last_error.restype = i32
+    L.fd_status_string.argtypes = [i32]
+    L.fd_status_string.restype = ctypes.c_char_p
+    _LIB = L
+    return L
+
+
+def _check(status: int, where: str):
+    if status != FD_OK:
+        raise FdError(status, where)
+
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a, dtype) -> int:
+    """Pointer of a contiguous numpy array or torch tensor of the given dtype."""
+    if a is None:
+        return None
+    if _is_torch(a):
+        import torch
+        want = {np.float32: torch.float32, np.int32: torch.int32}[dtype]
+        if a.dtype != want or not a.is_contiguous():
+            raise TypeError(f"expected a contiguous {want} tensor")
+        return a.data_ptr()
+    if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError(f"expected a C-contiguous numpy {np.dtype(dtype).name} array")
+    return a.ctypes.data
+
+
+def options(**kw) -> Options:
+    o = Options()
+    lib().fd_options_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+@dataclass
+class RunResult:
+    iterations: int
+    stress: float
+    trace_f: np.ndarray = field(default=None)
+    accepted: np.ndarray = field(default=None)
+    omega: np.ndarray = field(default=None)
+    cg_steps: np.ndarray = field(default=None)
+    crit: np.ndarray = field(default=None)
+    stats: dict = field(default_factory=dict)
+
+
+class Layout:
+    """A graph prepared for layout: ideal distances on the GPU plus scratch.
+
+    ``row_ptr``/``col_idx`` int32 CSR (numpy, or torch host/CUDA tensors),
+    ``edge_len`` optional float32 lengths, ``dim`` in {1, 2, 3}.
+    """
+
+    def __init__(self, row_ptr, col_idx, dim: int = 2, edge_len=None, disconnected_policy: int = 0,
+                 stream=None):
+        L = lib()
+        n = int(row_ptr.shape[0]) - 1
+        h = ctypes.c_void_p()
+        st = None if stream is None else ctypes.c_void_p(int(stream))
+        status = L.fd_layout_create(ctypes.byref(h), n, int(dim), _ptr(row_ptr, np.int32),
+                                    _ptr(col_idx, np.int32) if col_idx is not None and len(col_idx) else None,
+                                    _ptr(edge_len, np.float32), int(disconnected_policy), st)
+        _check(status, "fd_layout_create")
+        self._h = h
+        self.n, self.dim = n, int(dim)
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fd_layout_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- queries
+    def info(self) -> dict:
+        i = Info()
+        _check(lib().fd_layout_info(self._h, ctypes.byref(i)), "fd_layout_info")
+        return {k: getattr(i, k) for k, _ in Info._fields_}
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(lib().fd_last_stats(self._h, ctypes.byref(s)), "fd_last_stats")
+        return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+    def distance_rows(self, row0: int, nrows: int) -> np.ndarray:
+        out = np.empty((nrows, self.n), dtype=np.float64)
+        _check(lib().fd_distance_rows(self._h, int(row0), int(nrows), out.ctypes.data), "fd_distance_rows")
+        return out
+
+    # -- the method
+    def _xcheck(self, X):
+        if tuple(X.shape) != (self.n, self.dim):
+            raise ValueError(f"X must have shape ({self.n}, {self.dim})")
+
+    def energy(self, X) -> float:
+        """Stress f(X), Eq. (1)."""
+        self._xcheck(X)
+        f = ctypes.c_double()
+        _check(lib().fd_energy(self._h, _ptr(X, np.float32), ctypes.byref(f)), "fd_energy")
+        return f.value
+
+    def forces(self, X, out=None):
+        """F = (L^X - L^W) X; returns an array of X's kind unless ``out`` is given."""
+        self._xcheck(X)
+        if out is None:
+            if _is_torch(X):
+                import torch
+                out = torch.empty_like(X)
+            else:
+                out = np.empty_like(X)
+        _check(lib().fd_forces(self._h, _ptr(X, np.float32), _ptr(out, np.float32)), "fd_forces")
+        return out
+
+    def sor_step(self, X, k: int = 0, **opts):
+        """One iteration of Algorithm 2 in place on X; returns (f, accepted, crit)."""
+        self._xcheck(X)
+        o = options(**opts)
+        f, acc, crit = ctypes.c_double(), ctypes.c_int32(), ctypes.c_double()
+        _check(lib().fd_sor_step(self._h, _ptr(X, np.float32), ctypes.byref(o), int(k), ctypes.byref(f),
+                                 ctypes.byref(acc), ctypes.byref(crit)), "fd_sor_step")
+        return f.value, bool(acc.value), crit.value
+
+    def run(self, X, trace: bool = False, **opts) -> RunResult:
+        """Algorithm 2 to convergence in place on X."""
+        self._xcheck(X)
+        o = options(**opts)
+        iters, f = ctypes.c_int32(), ctypes.c_double()
+        tf = np.zeros(o.max_iter + 1, dtype=np.float64) if trace else None
+        _check(lib().fd_run(self._h, _ptr(X, np.float32), ctypes.byref(o), ctypes.byref(iters), ctypes.byref(f),
+                            tf.ctypes.data if trace else None), "fd_run")
+        res = RunResult(iterations=iters.value, stress=f.value, stats=self.stats())
+        if trace:
+            k = iters.value
+            res.trace_f = tf[:k + 1].copy()
+            acc = np.zeros(max(k, 1), dtype=np.int32)
+            om = np.zeros(max(k, 1), dtype=np.float64)
+            cg = np.zeros(max(k, 1), dtype=np.int32)
+            cr = np.zeros(max(k, 1), dtype=np.float64)
+            _check(lib().fd_run_trace(self._h, acc.ctypes.data, om.ctypes.data, cg.ctypes.data, cr.ctypes.data),
+                   "fd_run_trace")
+            res.accepted, res.omega, res.cg_steps, res.crit = acc[:k], om[:k], cg[:k], cr[:k]
+        return res

@@ -1,0 +1,318 @@
+// fd_apsp.cu -- ideal distances d_ij on the GPU and the row sums of W.
+//
+// The paper's d_ij is the "predefined ideal distance" of Eq. (1), the
+// graph-theoretic shortest-path length as in Gansner et al. (Sec. 2); edges
+// of weighted graphs carry lengths (Sec. 5.4).  The CSR edge list is read
+// here and nowhere else.
+//
+// Unit edges: bit-parallel multi-source BFS.  One CTA runs the BFS of 64
+// consecutive sources at once; a 64-bit word per vertex holds "reached from
+// source b" bits.  Each level pulls the frontier words of a vertex's
+// neighbours (one pass over the CSR segment of the vertex), so one pass over
+// the edge list advances 64 searches.  Each unordered pair is written once,
+// by the source that owns it in the tile layout (fd_internal.cuh).
+//
+// Weighted edges: one CTA per source runs label-correcting relaxation sweeps
+// (dist[v] = min(dist[v], dist[u] + len(u,v))) until no label changes.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fd_internal.cuh"
+
+namespace fdl {
+
+template <int CODE>
+__device__ __forceinline__ void put_code(void* D, int tile, int off, float value, int* overflow) {
+  if constexpr (CODE == CODE_U8) {
+    unsigned char* p = reinterpret_cast<unsigned char*>(D) + (size_t)tile * TILE * TILE + off;
+    if (value > 255.f) {
+      *p = 255;
+      if (overflow) atomicExch(overflow, 1);
+    } else {
+      *p = (unsigned char)value;
+    }
+  } else {
+    float* p = reinterpret_cast<float*>(D) + (size_t)tile * TILE * TILE + off;
+    *p = value;
+  }
+}
+
+template <int CODE>
+__device__ __forceinline__ float get_code(const void* D, int tile, int off) {
+  if constexpr (CODE == CODE_U8) {
+    return (float)(reinterpret_cast<const unsigned char*>(D)[(size_t)tile * TILE * TILE + off]);
+  } else {
+    return reinterpret_cast<const float*>(D)[(size_t)tile * TILE * TILE + off];
+  }
+}
+
+// Bits of a 64-source batch (sources s0 .. s0+63 of block row I) whose pair
+// with vertex v is stored by the batch: all bits if v's block is in row I's
+// half ring, none if the pair belongs to v's row, and in the diagonal block
+// only the sources s < v.
+__device__ __forceinline__ unsigned long long owned_bits(int v, int s0, int I, int nb, int LI,
+                                                         unsigned long long full, int* k_out) {
+  const int J = v / TILE;
+  int k = J - I;
+  if (k < 0) k += nb;
+  *k_out = k;
+  if (k == 0) {
+    const int dlt = v - s0;
+    if (dlt >= 64) return full;
+    if (dlt <= 0) return 0ull;
+    return ((1ull << dlt) - 1ull) & full;
+  }
+  return (k < LI) ? full : 0ull;
+}
+
+template <int CODE>
+__global__ void __launch_bounds__(1024) bfs_batch_kernel(int n, int nb, const int* __restrict__ row_ptr,
+                                                         const int* __restrict__ col_idx,
+                                                         const int* __restrict__ tile_base,
+                                                         const int* __restrict__ strip_len, void* D,
+                                                         unsigned long long* scratch, size_t stride,
+                                                         int nbatches, int* maxlevel, int* overflow) {
+  unsigned long long* vis = scratch + (size_t)blockIdx.x * stride;
+  for (int batch = blockIdx.x; batch < nbatches; batch += gridDim.x) {
+    unsigned long long* fr = vis + n;
+    unsigned long long* nx = fr + n;
+    const int s0 = batch * 64;
+    const int nsrc = min(64, n - s0);
+    const unsigned long long full = (nsrc == 64) ? ~0ull : ((1ull << nsrc) - 1ull);
+    const int I = s0 / TILE, il0 = s0 % TILE;
+    const int LI = strip_len[I], tb = tile_base[I];
+    for (int v = threadIdx.x; v < n; v += blockDim.x) {
+      const unsigned long long b = (v >= s0 && v < s0 + nsrc) ? (1ull << (v - s0)) : 0ull;
+      vis[v] = b;
+      fr[v] = b;
+    }
+    __syncthreads();
+    int level = 0;
+    while (true) {
+      ++level;
+      int any = 0;
+      for (int v = threadIdx.x; v < n; v += blockDim.x) {
+        const unsigned long long vs = vis[v];
+        unsigned long long nw = 0ull;
+        if (vs != full) {
+          unsigned long long acc = 0ull;
+          const int e1 = row_ptr[v + 1];
+          for (int e = row_ptr[v]; e < e1; ++e) acc |= fr[col_idx[e]];
+          nw = acc & ~vs & full;
+          if (nw) {
+            vis[v] = vs | nw;
+            any = 1;
+            int k;
+            unsigned long long m = nw & owned_bits(v, s0, I, nb, LI, full, &k);
+            const int jl = v % TILE;
+            while (m) {
+              const int b = __ffsll((long long)m) - 1;
+              m &= m - 1ull;
+              put_code<CODE>(D, tb + k, jl * TILE + il0 + b, (float)level, overflow);
+            }
+          }
+        }
+        nx[v] = nw;
+      }
+      any = __syncthreads_or(any);
+      if (!any) break;
+      unsigned long long* t = fr;
+      fr = nx;
+      nx = t;
+    }
+    if (threadIdx.x == 0) atomicMax(maxlevel, level - 1);
+    __syncthreads();
+  }
+}
+
+// Weighted shortest paths: one source per CTA iteration.
+__global__ void __launch_bounds__(1024) sssp_relax_kernel(int n, int nb, const int* __restrict__ row_ptr,
+                                                          const int* __restrict__ col_idx,
+                                                          const float* __restrict__ len,
+                                                          const int* __restrict__ tile_base,
+                                                          const int* __restrict__ strip_len, float* D,
+                                                          float* scratch, int* maxbits) {
+  float* dist = scratch + (size_t)blockIdx.x * n;
+  for (int src = blockIdx.x; src < n; src += gridDim.x) {
+    for (int v = threadIdx.x; v < n; v += blockDim.x) dist[v] = (v == src) ? 0.f : INFINITY;
+    __syncthreads();
+    for (int sweep = 0; sweep < n; ++sweep) {
+      int changed = 0;
+      for (int v = threadIdx.x; v < n; v += blockDim.x) {
+        float best = dist[v];
+        const int e1 = row_ptr[v + 1];
+        for (int e = row_ptr[v]; e < e1; ++e) {
+          const float c = ((volatile float*)dist)[col_idx[e]] + len[e];
+          best = fminf(best, c);
+        }
+        if (best < dist[v]) {
+          dist[v] = best;
+          changed = 1;
+        }
+      }
+      if (!__syncthreads_or(changed)) break;
+    }
+    const int I = src / TILE, il = src % TILE;
+    const int LI = strip_len[I], tb = tile_base[I];
+    int localmax = 0;
+    for (int v = threadIdx.x; v < n; v += blockDim.x) {
+      const float dv = dist[v];
+      if (v == src || !(dv < INFINITY)) continue;
+      const int J = v / TILE;
+      int k = J - I;
+      if (k < 0) k += nb;
+      const bool own = (k == 0) ? (v > src) : (k < LI);
+      if (own) D[(size_t)(tb + k) * TILE * TILE + (v % TILE) * TILE + il] = dv;
+      localmax = max(localmax, __float_as_int(dv));
+    }
+    atomicMax(maxbits, localmax);
+    __syncthreads();
+  }
+}
+
+// Pairs still holding code 0 after the searches were not reached.  Count
+// them and, under policy 1, give them the fill distance.
+template <int CODE>
+__global__ void fill_unreached_kernel(int n, int nb, int ntiles, const int2* __restrict__ tile_ik, void* D,
+                                      float fill, int write, unsigned long long* count) {
+  unsigned long long local = 0;
+  const size_t total = (size_t)ntiles * TILE * TILE;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int tile = (int)(idx / (TILE * TILE));
+    const int off = (int)(idx % (TILE * TILE));
+    const int jl = off / TILE, il = off % TILE;
+    const int2 ik = tile_ik[tile];
+    const int J = (ik.x + ik.y) % nb;
+    const int i = ik.x * TILE + il, j = J * TILE + jl;
+    const bool real = (i < n) && (j < n) && (ik.y > 0 || il < jl);
+    if (real && get_code<CODE>(D, tile, off) == 0.f) {
+      ++local;
+      if (write) put_code<CODE>(D, tile, off, fill, nullptr);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) local += __shfl_down_sync(0xffffffffu, local, o);
+  if ((threadIdx.x & 31) == 0 && local) atomicAdd(count, local);
+}
+
+// s_i = sum_{j != i} w_ij (diagonal of L^W, Prop. 2.1), FP64 accumulation.
+template <int CODE>
+__global__ void __launch_bounds__(TILE) rowsum_kernel(int n, int nb, const int* __restrict__ tile_base,
+                                                      const int* __restrict__ strip_len, const void* D,
+                                                      float* s, float* inv_s) {
+  const int R = blockIdx.x, t = threadIdx.x;
+  __shared__ double wl[LUT_N];
+  if constexpr (CODE == CODE_U8) {
+    for (int c = t; c < LUT_N; c += TILE) wl[c] = (c == 0) ? 0.0 : 1.0 / ((double)c * (double)c);
+    __syncthreads();
+  }
+  auto wgt = [&](int tile, int off) -> double {
+    if constexpr (CODE == CODE_U8) {
+      return wl[reinterpret_cast<const unsigned char*>(D)[(size_t)tile * TILE * TILE + off]];
+    } else {
+      const double d = reinterpret_cast<const float*>(D)[(size_t)tile * TILE * TILE + off];
+      return d > 0.0 ? 1.0 / (d * d) : 0.0;
+    }
+  };
+  double acc = 0.0;
+  // row R as the i side: its own strip, including the diagonal tile (pairs t < jl)
+  for (int k = 0; k < strip_len[R]; ++k) {
+    const int tile = tile_base[R] + k;
+    for (int jl = 0; jl < TILE; ++jl) acc += wgt(tile, jl * TILE + t);
+  }
+  // row R as the j side: the diagonal tile (pairs il < t) and other strips' tiles
+  for (int I = 0; I < nb; ++I) {
+    int k = R - I;
+    if (k < 0) k += nb;
+    if (k >= strip_len[I]) continue;
+    const int tile = tile_base[I] + k;
+    for (int il = 0; il < TILE; ++il) acc += wgt(tile, t * TILE + il);
+  }
+  const int i = R * TILE + t;
+  s[i] = (float)acc;
+  inv_s[i] = (acc > 0.0) ? (float)(1.0 / acc) : 0.f;
+}
+
+template <int CODE>
+__global__ void distance_rows_kernel(int n, int nb, const int* __restrict__ tile_base,
+                                     const int* __restrict__ strip_len, const void* D, int row0, int nrows,
+                                     double* out) {
+  const size_t total = (size_t)nrows * n;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = row0 + (int)(idx / n), j = (int)(idx % n);
+    double v = 0.0;
+    if (i != j) {
+      const int I = i / TILE, J = j / TILE, il = i % TILE, jl = j % TILE;
+      if (I == J) {
+        const int a = min(il, jl), b = max(il, jl);
+        v = get_code<CODE>(D, tile_base[I], b * TILE + a);
+      } else {
+        int k = J - I;
+        if (k < 0) k += nb;
+        if (k < strip_len[I]) {
+          v = get_code<CODE>(D, tile_base[I] + k, jl * TILE + il);
+        } else {
+          int k2 = I - J;
+          if (k2 < 0) k2 += nb;
+          v = get_code<CODE>(D, tile_base[J] + k2, il * TILE + jl);
+        }
+      }
+    }
+    out[idx] = v;
+  }
+}
+
+// ---------------------------------------------------------------- launchers
+
+cudaError_t launch_bfs(int code, int n, int nb, const int* rp, const int* ci, const int* tile_base,
+                       const int* strip_len, void* D, unsigned long long* scratch, size_t stride, int grid,
+                       int* maxlevel, int* overflow, cudaStream_t st) {
+  const int nbatches = (n + 63) / 64;
+  if (code == CODE_U8)
+    bfs_batch_kernel<CODE_U8><<<grid, 1024, 0, st>>>(n, nb, rp, ci, tile_base, strip_len, D, scratch, stride,
+                                                     nbatches, maxlevel, overflow);
+  else
+    bfs_batch_kernel<CODE_F32><<<grid, 1024, 0, st>>>(n, nb, rp, ci, tile_base, strip_len, D, scratch, stride,
+                                                      nbatches, maxlevel, overflow);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sssp(int n, int nb, const int* rp, const int* ci, const float* len, const int* tile_base,
+                        const int* strip_len, float* D, float* scratch, int grid, int* maxbits, cudaStream_t st) {
+  sssp_relax_kernel<<<grid, 1024, 0, st>>>(n, nb, rp, ci, len, tile_base, strip_len, D, scratch, maxbits);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill(int code, int n, int nb, int ntiles, const int2* tile_ik, void* D, float fill, int write,
+                        unsigned long long* count, int grid, cudaStream_t st) {
+  if (code == CODE_U8)
+    fill_unreached_kernel<CODE_U8><<<grid, 256, 0, st>>>(n, nb, ntiles, tile_ik, D, fill, write, count);
+  else
+    fill_unreached_kernel<CODE_F32><<<grid, 256, 0, st>>>(n, nb, ntiles, tile_ik, D, fill, write, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rowsum(int code, int n, int nb, const int* tile_base, const int* strip_len, const void* D,
+                          float* s, float* inv_s, cudaStream_t st) {
+  if (code == CODE_U8)
+    rowsum_kernel<CODE_U8><<<nb, TILE, 0, st>>>(n, nb, tile_base, strip_len, D, s, inv_s);
+  else
+    rowsum_kernel<CODE_F32><<<nb, TILE, 0, st>>>(n, nb, tile_base, strip_len, D, s, inv_s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_distance_rows(int code, int n, int nb, const int* tile_base, const int* strip_len,
+                                 const void* D, int row0, int nrows, double* out, cudaStream_t st) {
+  const size_t total = (size_t)nrows * n;
+  int grid = (int)((total + 255) / 256);
+  if (grid > 4096) grid = 4096;
+  if (grid < 1) grid = 1;
+  if (code == CODE_U8)
+    distance_rows_kernel<CODE_U8><<<grid, 256, 0, st>>>(n, nb, tile_base, strip_len, D, row0, nrows, out);
+  else
+    distance_rows_kernel<CODE_F32><<<grid, 256, 0, st>>>(n, nb, tile_base, strip_len, D, row0, nrows, out);
+  return cudaGetLastError();
+}
+
+}  // namespace fdl

@@ -1,0 +1,851 @@
+// fd_capi.cu -- the C ABI of include/fd_layout.h: handle set-up, CSR
+// validation, distance construction, and the launches of the cooperative
+// layout kernel.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "fd_internal.cuh"
+#include "fd_layout.h"
+
+namespace fdl {
+cudaError_t launch_bfs(int code, int n, int nb, const int* rp, const int* ci, const int* tile_base,
+                       const int* strip_len, void* D, unsigned long long* scratch, size_t stride, int grid,
+                       int* maxlevel, int* overflow, cudaStream_t st);
+cudaError_t launch_sssp(int n, int nb, const int* rp, const int* ci, const float* len, const int* tile_base,
+                        const int* strip_len, float* D, float* scratch, int grid, int* maxbits, cudaStream_t st);
+cudaError_t launch_fill(int code, int n, int nb, int ntiles, const int2* tile_ik, void* D, float fill, int write,
+                        unsigned long long* count, int grid, cudaStream_t st);
+cudaError_t launch_rowsum(int code, int n, int nb, const int* tile_base, const int* strip_len, const void* D,
+                          float* s, float* inv_s, cudaStream_t st);
+cudaError_t launch_distance_rows(int code, int n, int nb, const int* tile_base, const int* strip_len,
+                                 const void* D, int row0, int nrows, double* out, cudaStream_t st);
+cudaError_t main_config_d1(int code, int* blocks_per_sm, size_t* smem);
+cudaError_t main_config_d2(int code, int* blocks_per_sm, size_t* smem);
+cudaError_t main_config_d3(int code, int* blocks_per_sm, size_t* smem);
+cudaError_t launch_main_d1(int code, const KParams& p, int grid, size_t smem, cudaStream_t st);
+cudaError_t launch_main_d2(int code, const KParams& p, int grid, size_t smem, cudaStream_t st);
+cudaError_t launch_main_d3(int code, const KParams& p, int grid, size_t smem, cudaStream_t st);
+}  // namespace fdl
+
+using namespace fdl;
+
+struct fd_layout {
+  int n = 0, dim = 0, dimp = 0, n_pad = 0, nb = 0, ntiles = 0, ntasks = 0, chunk = 1;
+  int code = CODE_U8, diameter = 0, disconnected = 0;
+  int device = 0, sm_count = 0, grid = 0;
+  size_t smem = 0;
+  cudaStream_t stream = nullptr;
+  // device memory
+  void* D = nullptr;
+  size_t D_bytes = 0;
+  int* d_tile_base = nullptr;
+  int* d_strip_len = nullptr;
+  TaskDesc* d_tasks = nullptr;
+  int* d_strip_task_base = nullptr;
+  float4* d_lut = nullptr;
+  float* d_s = nullptr;
+  float* d_inv_s = nullptr;
+  float* d_vec = nullptr;  // pool of the per-vertex vectors
+  float* d_part_j = nullptr;
+  float* d_part_i = nullptr;
+  double* d_sc_task = nullptr;
+  double* d_sc = nullptr;  // sc_a and sc_b
+  Ctrl* d_ctrl = nullptr;
+  float* d_stage_in = nullptr;
+  float* d_stage_out = nullptr;
+  double* d_omega = nullptr;
+  double* d_trace_f = nullptr;
+  double* d_trace_om = nullptr;
+  double* d_trace_crit = nullptr;
+  int* d_trace_acc = nullptr;
+  int* d_trace_cg = nullptr;
+  int trace_cap = 0;
+  int last_iters = 0;
+  // host
+  std::vector<int> tile_base, strip_len, strip_task_base;
+  std::vector<TaskDesc> tasks;
+  fd_status last_error = FD_OK;
+  fd_stats stats;
+  long long timeout_ns = 30000000000LL;
+  double apsp_ms = 0.0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace {
+
+fd_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return FD_OK;
+  if (e == cudaErrorMemoryAllocation) return FD_ERR_OOM;
+  return FD_ERR_CUDA;
+}
+
+#define FD_CK(expr)                          \
+  do {                                       \
+    cudaError_t e_ = (expr);                 \
+    if (e_ != cudaSuccess) {                 \
+      cudaGetLastError();                    \
+      return cuda_status(e_);                \
+    }                                        \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  if (p == nullptr) return false;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <class T>
+fd_status dev_alloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return cuda_status(e);
+  }
+  return FD_OK;
+}
+
+template <class T>
+void dev_free(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+// Copies count elements of a caller array (host or device) to a host vector.
+template <class T>
+fd_status fetch_host(std::vector<T>& out, const T* src, size_t count) {
+  out.resize(count);
+  if (count == 0) return FD_OK;
+  if (is_device_ptr(src)) {
+    FD_CK(cudaMemcpy(out.data(), src, count * sizeof(T), cudaMemcpyDeviceToHost));
+  } else {
+    std::memcpy(out.data(), src, count * sizeof(T));
+  }
+  return FD_OK;
+}
+
+// CSR checks: shape, ranges, symmetry (with equal lengths when given).
+fd_status validate_csr(int n, const std::vector<int>& rp, const std::vector<int>& ci, const std::vector<float>* len) {
+  if ((int)rp.size() != n + 1 || rp[0] != 0) return FD_ERR_CSR;
+  for (int v = 0; v < n; ++v)
+    if (rp[v + 1] < rp[v]) return FD_ERR_CSR;
+  const size_t nnz = (size_t)rp[n];
+  if (ci.size() != nnz) return FD_ERR_CSR;
+  for (size_t e = 0; e < nnz; ++e)
+    if (ci[e] < 0 || ci[e] >= n) return FD_ERR_CSR;
+  if (len) {
+    for (size_t e = 0; e < nnz; ++e)
+      if (!(std::isfinite((*len)[e]) && (*len)[e] > 0.f)) return FD_ERR_CSR;
+  }
+  // per-row sorted (neighbour, shortest length) lists
+  std::vector<std::pair<int, float>> adj(nnz);
+  for (int v = 0; v < n; ++v) {
+    for (int e = rp[v]; e < rp[v + 1]; ++e) adj[e] = {ci[e], len ? (*len)[e] : 1.f};
+    std::sort(adj.begin() + rp[v], adj.begin() + rp[v + 1]);
+  }
+  for (int u = 0; u < n; ++u) {
+    for (int e = rp[u]; e < rp[u + 1]; ++e) {
+      const int v = adj[e].first;
+      if (e > rp[u] && adj[e - 1].first == v) continue;  // first (shortest) entry of a repeated edge
+      if (v == u) continue;
+      auto b = adj.begin() + rp[v], en = adj.begin() + rp[v + 1];
+      auto it = std::lower_bound(b, en, std::make_pair(u, -INFINITY));
+      if (it == en || it->first != u) return FD_ERR_CSR;
+      if (len && it->second != adj[e].second) return FD_ERR_CSR;
+    }
+  }
+  return FD_OK;
+}
+
+// Hop eccentricity of vertex 0 within its component (host BFS).
+int host_ecc0(int n, const std::vector<int>& rp, const std::vector<int>& ci) {
+  std::vector<int> dist(n, -1), q;
+  q.reserve(n);
+  dist[0] = 0;
+  q.push_back(0);
+  int ecc = 0;
+  for (size_t h = 0; h < q.size(); ++h) {
+    const int u = q[h];
+    for (int e = rp[u]; e < rp[u + 1]; ++e) {
+      const int v = ci[e];
+      if (dist[v] < 0) {
+        dist[v] = dist[u] + 1;
+        ecc = std::max(ecc, dist[v]);
+        q.push_back(v);
+      }
+    }
+  }
+  return ecc;
+}
+
+uint64_t splitmix64(uint64_t seed, uint64_t k) {
+  uint64_t z = seed + (k + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Probabilistic strategy of Sec. 5.2.3 (prior 0.3, 0.3, 0.2, 0.2 over 0.5, 1, 1.5, 2).
+double omega_prob(uint64_t seed, uint64_t k) {
+  const double u = (double)(splitmix64(seed, k) >> 11) * (1.0 / 9007199254740992.0);
+  if (u < 0.3) return 0.5;
+  if (u < 0.6) return 1.0;
+  if (u < 0.8) return 1.5;
+  return 2.0;
+}
+
+void build_geometry(fd_layout* h) {
+  h->n_pad = ((h->n + TILE - 1) / TILE) * TILE;
+  h->nb = h->n_pad / TILE;
+  const int nb = h->nb;
+  h->strip_len.assign(nb, 0);
+  h->tile_base.assign(nb + 1, 0);
+  for (int I = 0; I < nb; ++I) {
+    int L;
+    if (nb % 2 == 1) L = (nb + 1) / 2;
+    else L = (I < nb / 2) ? nb / 2 + 1 : nb / 2;
+    h->strip_len[I] = L;
+    h->tile_base[I + 1] = h->tile_base[I] + L;
+  }
+  h->ntiles = h->tile_base[nb];
+}
+
+void build_tasks(fd_layout* h) {
+  // enough tasks to keep every CTA busy, few enough that row partials stay small
+  const long long want = std::max<long long>(1, (long long)h->grid * 6);
+  int chunk = (int)std::max<long long>(1, h->ntiles / want);
+  chunk = std::min(chunk, 16);
+  h->chunk = chunk;
+  h->tasks.clear();
+  h->strip_task_base.assign(h->nb + 1, 0);
+  for (int I = 0; I < h->nb; ++I) {
+    for (int k0 = 0; k0 < h->strip_len[I]; k0 += chunk) {
+      TaskDesc t;
+      t.I = I;
+      t.k0 = k0;
+      t.k1 = std::min(k0 + chunk, h->strip_len[I]);
+      t.tile0 = h->tile_base[I] + k0;
+      h->tasks.push_back(t);
+    }
+    h->strip_task_base[I + 1] = (int)h->tasks.size();
+  }
+  h->ntasks = (int)h->tasks.size();
+}
+
+cudaError_t main_config(int dim, int code, int* bps, size_t* smem) {
+  if (dim == 1) return main_config_d1(code, bps, smem);
+  if (dim == 2) return main_config_d2(code, bps, smem);
+  return main_config_d3(code, bps, smem);
+}
+
+cudaError_t launch_main(int dim, int code, const KParams& p, int grid, size_t smem, cudaStream_t st) {
+  if (dim == 1) return launch_main_d1(code, p, grid, smem, st);
+  if (dim == 2) return launch_main_d2(code, p, grid, smem, st);
+  return launch_main_d3(code, p, grid, smem, st);
+}
+
+void release(fd_layout* h) {
+  dev_free(h->D);
+  dev_free(h->d_tile_base);
+  dev_free(h->d_strip_len);
+  dev_free(h->d_tasks);
+  dev_free(h->d_strip_task_base);
+  dev_free(h->d_lut);
+  dev_free(h->d_s);
+  dev_free(h->d_inv_s);
+  dev_free(h->d_vec);
+  dev_free(h->d_part_j);
+  dev_free(h->d_part_i);
+  dev_free(h->d_sc_task);
+  dev_free(h->d_sc);
+  dev_free(h->d_ctrl);
+  dev_free(h->d_stage_in);
+  dev_free(h->d_stage_out);
+  dev_free(h->d_omega);
+  dev_free(h->d_trace_f);
+  dev_free(h->d_trace_om);
+  dev_free(h->d_trace_crit);
+  dev_free(h->d_trace_acc);
+  dev_free(h->d_trace_cg);
+  if (h->ev0) cudaEventDestroy(h->ev0);
+  if (h->ev1) cudaEventDestroy(h->ev1);
+  h->ev0 = h->ev1 = nullptr;
+}
+
+fd_status fail(fd_layout* h, fd_status s) {
+  if (h) h->last_error = s;
+  return s;
+}
+
+// Distances for unit edges (BFS) or lengths (relaxation); returns the code
+// kind actually used (u8 may fall back to f32 on a large diameter).
+fd_status build_distances(fd_layout* h, const std::vector<int>& rp, const std::vector<int>& ci,
+                          const std::vector<float>* len, int policy) {
+  const int n = h->n, nb = h->nb;
+  cudaStream_t st = h->stream;
+  int *d_rp = nullptr, *d_ci = nullptr, *d_flags = nullptr;
+  float* d_len = nullptr;
+  int2* d_tile_ik = nullptr;
+  unsigned long long* d_count = nullptr;
+  void* scratch = nullptr;
+  fd_status s = FD_OK;
+  const size_t nnz = rp[n];
+  auto cleanup = [&]() {
+    dev_free(d_rp);
+    dev_free(d_ci);
+    dev_free(d_len);
+    dev_free(d_flags);
+    dev_free(d_tile_ik);
+    dev_free(d_count);
+    if (scratch) cudaFree(scratch);
+    scratch = nullptr;
+  };
+#define FD_TRY(expr)            \
+  do {                          \
+    s = (expr);                 \
+    if (s != FD_OK) {           \
+      cleanup();                \
+      return s;                 \
+    }                           \
+  } while (0)
+#define FD_TRYC(expr) FD_TRY(cuda_status(expr))
+
+  FD_TRY(dev_alloc(&d_rp, n + 1));
+  FD_TRY(dev_alloc(&d_ci, nnz));
+  FD_TRY(dev_alloc(&d_flags, 4));
+  FD_TRY(dev_alloc(&d_count, 1));
+  FD_TRYC(cudaMemcpyAsync(d_rp, rp.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
+  if (nnz) FD_TRYC(cudaMemcpyAsync(d_ci, ci.data(), nnz * sizeof(int), cudaMemcpyHostToDevice, st));
+  std::vector<int2> tile_ik(h->ntiles);
+  for (int I = 0; I < nb; ++I)
+    for (int k = 0; k < h->strip_len[I]; ++k) tile_ik[h->tile_base[I] + k] = make_int2(I, k);
+  FD_TRY(dev_alloc(&d_tile_ik, h->ntiles));
+  FD_TRYC(cudaMemcpyAsync(d_tile_ik, tile_ik.data(), h->ntiles * sizeof(int2), cudaMemcpyHostToDevice, st));
+
+  int code = len ? CODE_F32 : CODE_U8;
+  if (code == CODE_U8 && host_ecc0(n, rp, ci) >= 254) code = CODE_F32;
+  float fill = 0.f;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    h->code = code;
+    const size_t cb = (code == CODE_U8) ? 1 : 4;
+    h->D_bytes = (size_t)h->ntiles * TILE * TILE * cb;
+    dev_free(h->D);
+    FD_TRY(dev_alloc((unsigned char**)&h->D, h->D_bytes));
+    FD_TRYC(cudaMemsetAsync(h->D, 0, h->D_bytes, st));
+    FD_TRYC(cudaMemsetAsync(d_flags, 0, 4 * sizeof(int), st));
+    int diameter = 0;
+    if (!len) {
+      const int nbatches = (n + 63) / 64;
+      const int grid = std::max(1, std::min(nbatches, 2 * h->sm_count));
+      const size_t stride = (size_t)3 * n;
+      if (scratch) cudaFree(scratch);
+      scratch = nullptr;
+      FD_TRYC(cudaMalloc(&scratch, (size_t)grid * stride * sizeof(unsigned long long)));
+      FD_TRYC(cudaEventRecord(h->ev0, st));
+      FD_TRYC(launch_bfs(code, n, nb, d_rp, d_ci, h->d_tile_base, h->d_strip_len, h->D,
+                         (unsigned long long*)scratch, stride, grid, d_flags, d_flags + 1, st));
+      FD_TRYC(cudaEventRecord(h->ev1, st));
+      int flags[2];
+      FD_TRYC(cudaMemcpyAsync(flags, d_flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+      FD_TRYC(cudaStreamSynchronize(st));
+      float ms = 0.f;
+      FD_TRYC(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+      h->apsp_ms = ms;
+      diameter = flags[0];
+      if (flags[1] && code == CODE_U8) {  // a level above 255: store float codes
+        code = CODE_F32;
+        continue;
+      }
+      fill = (float)(diameter + 1);
+    } else {
+      FD_TRY(dev_alloc(&d_len, nnz));
+      FD_TRYC(cudaMemcpyAsync(d_len, len->data(), nnz * sizeof(float), cudaMemcpyHostToDevice, st));
+      const int grid = std::max(1, std::min(n, 2 * h->sm_count));
+      if (scratch) cudaFree(scratch);
+      scratch = nullptr;
+      FD_TRYC(cudaMalloc(&scratch, (size_t)grid * n * sizeof(float)));
+      FD_TRYC(cudaEventRecord(h->ev0, st));
+      FD_TRYC(launch_sssp(n, nb, d_rp, d_ci, d_len, h->d_tile_base, h->d_strip_len, (float*)h->D, (float*)scratch,
+                          grid, d_flags + 2, st));
+      FD_TRYC(cudaEventRecord(h->ev1, st));
+      int bits;
+      FD_TRYC(cudaMemcpyAsync(&bits, d_flags + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
+      FD_TRYC(cudaStreamSynchronize(st));
+      float ms = 0.f;
+      FD_TRYC(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+      h->apsp_ms = ms;
+      float dmax;
+      std::memcpy(&dmax, &bits, sizeof(float));
+      diameter = (int)std::ceil(dmax);
+      fill = dmax + 1.f;
+    }
+    // unreachable pairs
+    unsigned long long count = 0;
+    FD_TRYC(cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), st));
+    const int fgrid = 4 * h->sm_count;
+    if (code == CODE_U8 && policy == 1 && fill > 255.f) {
+      code = CODE_F32;  // fill value does not fit a byte
+      continue;
+    }
+    FD_TRYC(launch_fill(code, n, nb, h->ntiles, d_tile_ik, h->D, fill, policy == 1 ? 1 : 0, d_count, fgrid, st));
+    FD_TRYC(cudaMemcpyAsync(&count, d_count, sizeof(count), cudaMemcpyDeviceToHost, st));
+    FD_TRYC(cudaStreamSynchronize(st));
+    if (count > 0 && policy != 1) {
+      cleanup();
+      return FD_ERR_DISCONNECTED;
+    }
+    h->disconnected = count > 0 ? 1 : 0;
+    h->diameter = diameter;
+    break;
+  }
+  cleanup();
+  return FD_OK;
+#undef FD_TRY
+#undef FD_TRYC
+}
+
+fd_status ensure_traces(fd_layout* h, int max_iter) {
+  if (h->trace_cap >= max_iter + 1) return FD_OK;
+  dev_free(h->d_omega);
+  dev_free(h->d_trace_f);
+  dev_free(h->d_trace_om);
+  dev_free(h->d_trace_crit);
+  dev_free(h->d_trace_acc);
+  dev_free(h->d_trace_cg);
+  h->trace_cap = 0;
+  const int cap = max_iter + 1;
+  fd_status s;
+  if ((s = dev_alloc(&h->d_omega, cap)) != FD_OK) return s;
+  if ((s = dev_alloc(&h->d_trace_f, cap)) != FD_OK) return s;
+  if ((s = dev_alloc(&h->d_trace_om, cap)) != FD_OK) return s;
+  if ((s = dev_alloc(&h->d_trace_crit, cap)) != FD_OK) return s;
+  if ((s = dev_alloc(&h->d_trace_acc, cap)) != FD_OK) return s;
+  if ((s = dev_alloc(&h->d_trace_cg, cap)) != FD_OK) return s;
+  h->trace_cap = cap;
+  return FD_OK;
+}
+
+KParams base_params(fd_layout* h, int mode) {
+  KParams p;
+  std::memset(&p, 0, sizeof(p));
+  p.g.n = h->n;
+  p.g.n_pad = h->n_pad;
+  p.g.nb = h->nb;
+  p.g.dim = h->dim;
+  p.g.ntiles = h->ntiles;
+  p.g.ntasks = h->ntasks;
+  p.g.tile_base = h->d_tile_base;
+  p.g.strip_len = h->d_strip_len;
+  p.g.tasks = h->d_tasks;
+  p.g.strip_task_base = h->d_strip_task_base;
+  p.mode = mode;
+  p.D = h->D;
+  p.lut = h->d_lut;
+  p.s = h->d_s;
+  p.inv_s = h->d_inv_s;
+  const size_t vs = (size_t)h->n_pad * h->dimp;
+  float* v = h->d_vec;
+  float** slots[] = {&p.X, &p.Z, &p.Xt, &p.B, &p.Bz, &p.Bt, &p.Zw, &p.R, &p.Zc, &p.Pa, &p.Pb, &p.Q};
+  for (int k = 0; k < 12; ++k) *slots[k] = v + k * vs;
+  p.part_j = h->d_part_j;
+  p.part_i = h->d_part_i;
+  p.sc_task = h->d_sc_task;
+  p.sc_a = h->d_sc;
+  p.sc_b = h->d_sc + (size_t)h->nb * 8;
+  p.ctrl = h->d_ctrl;
+  p.timeout_ns = h->timeout_ns;
+  p.max_iter = 0;
+  return p;
+}
+
+// Runs one cooperative launch; returns the device status and the control block.
+fd_status run_kernel(fd_layout* h, KParams& p, Ctrl* ctrl_out, double* kernel_ms) {
+  cudaStream_t st = h->stream;
+  FD_CK(cudaMemsetAsync(h->d_ctrl, 0, sizeof(Ctrl), st));
+  FD_CK(cudaEventRecord(h->ev0, st));
+  FD_CK(launch_main(h->dim, h->code, p, h->grid, h->smem, st));
+  FD_CK(cudaEventRecord(h->ev1, st));
+  FD_CK(cudaMemcpyAsync(ctrl_out, h->d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+  FD_CK(cudaStreamSynchronize(st));
+  float ms = 0.f;
+  FD_CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+  *kernel_ms = ms;
+  if (ctrl_out->err != 0) return (fd_status)ctrl_out->err;
+  return FD_OK;
+}
+
+void fill_stats(fd_layout* h, const Ctrl& c, double kms) {
+  std::memset(&h->stats, 0, sizeof(h->stats));
+  h->stats.iterations = c.iters;
+  h->stats.cg_steps = c.cg_steps;
+  h->stats.cg_maxed = c.cg_maxed;
+  h->stats.accepted = c.accepted;
+  h->stats.pair_passes = c.pair_passes;
+  h->stats.pairs = 0.5 * (double)h->n * (double)(h->n - 1);
+  h->stats.final_stress = c.f_final;
+  h->stats.final_crit = c.crit_final;
+  h->stats.matvec_passes = c.matvec_passes;
+  h->stats.stress_passes = c.stress_passes;
+  h->stats.kernel_ms = kms;
+}
+
+// Positions in: device pointers are used in place, host arrays are staged.
+fd_status stage_input(fd_layout* h, const float* X, const float** dev_x) {
+  if (is_device_ptr(X)) {
+    *dev_x = X;
+    return FD_OK;
+  }
+  FD_CK(cudaMemcpyAsync(h->d_stage_in, X, (size_t)h->n * h->dim * sizeof(float), cudaMemcpyHostToDevice,
+                        h->stream));
+  *dev_x = h->d_stage_in;
+  return FD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void fd_options_default(fd_options* opt) {
+  if (!opt) return;
+  opt->omega = 0.5;
+  opt->strategy = FD_OMEGA_FIXED;
+  opt->stop = FD_STOP_REL_DISP;
+  opt->seed = 0;
+  opt->tol = 1e-4;
+  opt->max_iter = 1000;
+  opt->cg_max = 200;
+  opt->cg_tol = 1e-6;
+}
+
+const char* fd_status_string(fd_status s) {
+  switch (s) {
+    case FD_OK: return "FD_OK";
+    case FD_ERR_ARG: return "FD_ERR_ARG";
+    case FD_ERR_CSR: return "FD_ERR_CSR";
+    case FD_ERR_DISCONNECTED: return "FD_ERR_DISCONNECTED";
+    case FD_ERR_NONFINITE: return "FD_ERR_NONFINITE";
+    case FD_ERR_CG_BREAKDOWN: return "FD_ERR_CG_BREAKDOWN";
+    case FD_ERR_CG_MAXITER: return "FD_ERR_CG_MAXITER";
+    case FD_ERR_TIMEOUT: return "FD_ERR_TIMEOUT";
+    case FD_ERR_OOM: return "FD_ERR_OOM";
+    case FD_ERR_CUDA: return "FD_ERR_CUDA";
+    case FD_ERR_UNIMPLEMENTED: return "FD_ERR_UNIMPLEMENTED";
+  }
+  return "FD_ERR_UNKNOWN";
+}
+
+fd_status fd_layout_create(fd_layout** out, int32_t n, int32_t dim, const int32_t* row_ptr, const int32_t* col_idx,
+                           const float* edge_len, int32_t disconnected_policy, void* cuda_stream) {
+  if (!out) return FD_ERR_ARG;
+  *out = nullptr;
+  if (n < 1 || dim < 1 || dim > 3 || !row_ptr || (disconnected_policy != 0 && disconnected_policy != 1))
+    return FD_ERR_ARG;
+  std::vector<int> rp, ci;
+  std::vector<float> len;
+  fd_status s = fetch_host(rp, row_ptr, (size_t)n + 1);
+  if (s != FD_OK) return s;
+  if (rp[0] != 0 || rp[n] < 0) return FD_ERR_CSR;
+  if (rp[n] > 0 && !col_idx) return FD_ERR_ARG;
+  if ((s = fetch_host(ci, col_idx, (size_t)rp[n])) != FD_OK) return s;
+  if (edge_len) {
+    if ((s = fetch_host(len, edge_len, (size_t)rp[n])) != FD_OK) return s;
+  }
+  if ((s = validate_csr(n, rp, ci, edge_len ? &len : nullptr)) != FD_OK) return s;
+
+  fd_layout* h = new (std::nothrow) fd_layout();
+  if (!h) return FD_ERR_OOM;
+  std::memset(&h->stats, 0, sizeof(h->stats));
+  h->n = n;
+  h->dim = dim;
+  h->dimp = (dim == 3) ? 4 : dim;
+  h->stream = (cudaStream_t)cuda_stream;
+  auto bail = [&](fd_status e) {
+    release(h);
+    delete h;
+    return e;
+  };
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(FD_ERR_CUDA);
+  }
+  if (cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(FD_ERR_CUDA);
+  }
+  if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(FD_ERR_CUDA);
+  }
+  build_geometry(h);
+  if ((s = dev_alloc(&h->d_tile_base, h->nb + 1)) != FD_OK) return bail(s);
+  if ((s = dev_alloc(&h->d_strip_len, h->nb)) != FD_OK) return bail(s);
+  if (cudaMemcpy(h->d_tile_base, h->tile_base.data(), (h->nb + 1) * sizeof(int), cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
+      cudaMemcpy(h->d_strip_len, h->strip_len.data(), h->nb * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(FD_ERR_CUDA);
+  }
+  if ((s = build_distances(h, rp, ci, edge_len ? &len : nullptr, disconnected_policy)) != FD_OK) return bail(s);
+
+  // launch configuration of the cooperative kernel (depends on the code kind)
+  int bps = 0;
+  if (main_config(dim, h->code, &bps, &h->smem) != cudaSuccess || bps < 1) {
+    cudaGetLastError();
+    return bail(FD_ERR_CUDA);
+  }
+  h->grid = bps * h->sm_count;
+  build_tasks(h);
+
+  // lookup table {1/d, 1/d^2, -1, 0} per uint8 code; code 0 is "no pair"
+  std::vector<float4> lut(LUT_N);
+  lut[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int c = 1; c < LUT_N; ++c)
+    lut[c] = make_float4((float)(1.0 / c), (float)(1.0 / ((double)c * c)), -1.f, 0.f);
+  const size_t vs = (size_t)h->n_pad * h->dimp;
+  if ((s = dev_alloc(&h->d_lut, LUT_N)) != FD_OK) return bail(s);
+  if ((s = dev_alloc(&h->d_s, h->n_pad)) != FD_OK) return bail(s);
+  if ((s = dev_alloc(&h->d_inv_s, h->n_pad)) != FD_OK) return bail(s);
+  if ((s = dev_alloc(&h->d_vec, 12 * vs)) != FD_OK) return bail(s);
+  if ((s = dev_alloc(&h->d_part_j, (size_t)h->ntiles * 2 * TILE * h->dimp)) != FD_OK) return bail(s);
+  if ((s = dev_alloc(&h->d_part_i, (size_t)h->ntasks * 2 * TILE * h->dimp)) != FD_OK) return bail(s);
+  if ((s = dev_alloc(&h->d_sc_task, (size_t)h->ntasks * 2)) != FD_OK) return bail(s);
+  if ((s = dev_alloc(&h->d_sc, (size_t)h->nb * 16)) != FD_OK) return bail(s);
+  if ((s = dev_alloc(&h->d_ctrl, 1)) != FD_OK) return bail(s);
+  if ((s = dev_alloc(&h->d_stage_in, (size_t)n * dim)) != FD_OK) return bail(s);
+  if ((s = dev_alloc(&h->d_stage_out, (size_t)n * dim)) != FD_OK) return bail(s);
+  if ((s = dev_alloc(&h->d_tasks, h->ntasks)) != FD_OK) return bail(s);
+  if ((s = dev_alloc(&h->d_strip_task_base, h->nb + 1)) != FD_OK) return bail(s);
+  cudaStream_t st = h->stream;
+  if (cudaMemcpyAsync(h->d_lut, lut.data(), LUT_N * sizeof(float4), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(h->d_tasks, h->tasks.data(), h->ntasks * sizeof(TaskDesc), cudaMemcpyHostToDevice, st) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(h->d_strip_task_base, h->strip_task_base.data(), (h->nb + 1) * sizeof(int),
+                      cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemsetAsync(h->d_vec, 0, 12 * vs * sizeof(float), st) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(FD_ERR_CUDA);
+  }
+  if (launch_rowsum(h->code, n, h->nb, h->d_tile_base, h->d_strip_len, h->D, h->d_s, h->d_inv_s, st) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(FD_ERR_CUDA);
+  }
+  *out = h;
+  return FD_OK;
+}
+
+void fd_layout_destroy(fd_layout* h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  release(h);
+  delete h;
+}
+
+fd_status fd_energy(fd_layout* h, const float* X, double* f_out) {
+  if (!h) return FD_ERR_ARG;
+  if (!X || !f_out) return fail(h, FD_ERR_ARG);
+  const float* dx = nullptr;
+  fd_status s = stage_input(h, X, &dx);
+  if (s != FD_OK) return fail(h, s);
+  KParams p = base_params(h, KM_ENERGY);
+  p.x_in = dx;
+  Ctrl c;
+  double kms = 0.0;
+  std::memset(&c, 0, sizeof(c));
+  s = run_kernel(h, p, &c, &kms);
+  fill_stats(h, c, kms);
+  if (s != FD_OK) return fail(h, s);
+  *f_out = c.f_final;
+  return FD_OK;
+}
+
+fd_status fd_forces(fd_layout* h, const float* X, float* F_out) {
+  if (!h) return FD_ERR_ARG;
+  if (!X || !F_out) return fail(h, FD_ERR_ARG);
+  const float* dx = nullptr;
+  fd_status s = stage_input(h, X, &dx);
+  if (s != FD_OK) return fail(h, s);
+  KParams p = base_params(h, KM_FORCES);
+  p.x_in = dx;
+  const bool dev_out = is_device_ptr(F_out);
+  p.x_out = dev_out ? F_out : h->d_stage_out;
+  Ctrl c;
+  double kms = 0.0;
+  std::memset(&c, 0, sizeof(c));
+  s = run_kernel(h, p, &c, &kms);
+  fill_stats(h, c, kms);
+  if (s != FD_OK) return fail(h, s);
+  if (!dev_out) {
+    if (cudaMemcpyAsync(F_out, h->d_stage_out, (size_t)h->n * h->dim * sizeof(float), cudaMemcpyDeviceToHost,
+                        h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, FD_ERR_CUDA);
+    }
+  }
+  return FD_OK;
+}
+
+static fd_status run_impl(fd_layout* h, float* X, const fd_options* opt, int k0, int max_iter, Ctrl* c_out) {
+  if (!X || !opt) return FD_ERR_ARG;
+  if (!(opt->omega >= 0.0) || !std::isfinite(opt->omega) || max_iter < 1 || opt->cg_max < 0 ||
+      !(opt->tol >= 0.0) || !(opt->cg_tol >= 0.0) || (opt->stop != FD_STOP_REL_DISP && opt->stop != FD_STOP_REL_STRESS))
+    return FD_ERR_ARG;
+  if (opt->strategy == FD_OMEGA_ENUM) return FD_ERR_UNIMPLEMENTED;
+  if (opt->strategy != FD_OMEGA_FIXED && opt->strategy != FD_OMEGA_PROB) return FD_ERR_ARG;
+  fd_status s = ensure_traces(h, max_iter);
+  if (s != FD_OK) return s;
+  std::vector<double> om(max_iter);
+  for (int k = 0; k < max_iter; ++k)
+    om[k] = (opt->strategy == FD_OMEGA_PROB) ? omega_prob(opt->seed, (uint64_t)(k0 + k)) : opt->omega;
+  FD_CK(cudaMemcpyAsync(h->d_omega, om.data(), max_iter * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  const float* dx = nullptr;
+  if ((s = stage_input(h, X, &dx)) != FD_OK) return s;
+  KParams p = base_params(h, KM_RUN);
+  p.x_in = dx;
+  const bool dev_out = is_device_ptr(X);
+  p.x_out = dev_out ? X : h->d_stage_out;
+  p.omega_seq = h->d_omega;
+  p.trace_f = h->d_trace_f;
+  p.trace_acc = h->d_trace_acc;
+  p.trace_om = h->d_trace_om;
+  p.trace_cg = h->d_trace_cg;
+  p.trace_crit = h->d_trace_crit;
+  p.max_iter = max_iter;
+  p.stop = opt->stop;
+  p.cg_max = opt->cg_max;
+  p.tol = opt->tol;
+  p.cg_tol = opt->cg_tol;
+  double kms = 0.0;
+  std::memset(c_out, 0, sizeof(*c_out));
+  s = run_kernel(h, p, c_out, &kms);
+  fill_stats(h, *c_out, kms);
+  h->last_iters = c_out->iters;
+  if (s != FD_OK) return s;
+  if (!dev_out) {
+    FD_CK(cudaMemcpyAsync(X, h->d_stage_out, (size_t)h->n * h->dim * sizeof(float), cudaMemcpyDeviceToHost,
+                          h->stream));
+    FD_CK(cudaStreamSynchronize(h->stream));
+  }
+  return FD_OK;
+}
+
+fd_status fd_sor_step(fd_layout* h, float* X, const fd_options* opt, int32_t k, double* f_out, int32_t* accepted,
+                      double* crit_out) {
+  if (!h) return FD_ERR_ARG;
+  if (k < 0) return fail(h, FD_ERR_ARG);
+  Ctrl c;
+  fd_status s = run_impl(h, X, opt, k, 1, &c);
+  if (s != FD_OK) return fail(h, s);
+  int acc = 0;
+  if (cudaMemcpy(&acc, h->d_trace_acc, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, FD_ERR_CUDA);
+  }
+  if (f_out) *f_out = c.f_final;
+  if (accepted) *accepted = acc;
+  if (crit_out) *crit_out = c.crit_final;
+  return FD_OK;
+}
+
+fd_status fd_run(fd_layout* h, float* X, const fd_options* opt, int32_t* iters_out, double* f_out, double* trace_f) {
+  if (!h) return FD_ERR_ARG;
+  if (!opt) return fail(h, FD_ERR_ARG);
+  Ctrl c;
+  fd_status s = run_impl(h, X, opt, 0, opt->max_iter, &c);
+  if (s != FD_OK) return fail(h, s);
+  if (iters_out) *iters_out = c.iters;
+  if (f_out) *f_out = c.f_final;
+  if (trace_f) {
+    if (cudaMemcpy(trace_f, h->d_trace_f, (size_t)(c.iters + 1) * sizeof(double), cudaMemcpyDeviceToHost) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, FD_ERR_CUDA);
+    }
+  }
+  return FD_OK;
+}
+
+fd_status fd_run_trace(fd_layout* h, int32_t* accepted, double* omega, int32_t* cg_steps, double* crit) {
+  if (!h) return FD_ERR_ARG;
+  const int k = h->last_iters;
+  if (k <= 0) return FD_OK;
+  struct {
+    void* dst;
+    const void* src;
+    size_t bytes;
+  } cp[] = {{accepted, h->d_trace_acc, k * sizeof(int)},
+            {omega, h->d_trace_om, k * sizeof(double)},
+            {cg_steps, h->d_trace_cg, k * sizeof(int)},
+            {crit, h->d_trace_crit, k * sizeof(double)}};
+  for (auto& c : cp) {
+    if (!c.dst) continue;
+    if (cudaMemcpy(c.dst, c.src, c.bytes, cudaMemcpyDeviceToHost) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, FD_ERR_CUDA);
+    }
+  }
+  return FD_OK;
+}
+
+fd_status fd_distance_rows(fd_layout* h, int32_t row0, int32_t nrows, double* out) {
+  if (!h) return FD_ERR_ARG;
+  if (!out || row0 < 0 || nrows < 0 || row0 + nrows > h->n) return fail(h, FD_ERR_ARG);
+  if (nrows == 0) return FD_OK;
+  double* d = nullptr;
+  fd_status s = dev_alloc(&d, (size_t)nrows * h->n);
+  if (s != FD_OK) return fail(h, s);
+  cudaError_t e = launch_distance_rows(h->code, h->n, h->nb, h->d_tile_base, h->d_strip_len, h->D, row0, nrows, d,
+                                       h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out, d, (size_t)nrows * h->n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  cudaFree(d);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, cuda_status(e));
+  }
+  return FD_OK;
+}
+
+fd_status fd_layout_info(const fd_layout* h, fd_info* info) {
+  if (!h || !info) return FD_ERR_ARG;
+  info->n = h->n;
+  info->dim = h->dim;
+  info->diameter = h->diameter;
+  info->code_bytes = (h->code == CODE_U8) ? 1 : 4;
+  info->tile = TILE;
+  info->num_tiles = h->ntiles;
+  info->distance_bytes = (int64_t)h->D_bytes;
+  info->disconnected = h->disconnected;
+  info->sm_count = h->sm_count;
+  info->grid = h->grid;
+  info->tasks = h->ntasks;
+  info->apsp_ms = h->apsp_ms;
+  return FD_OK;
+}
+
+fd_status fd_last_stats(const fd_layout* h, fd_stats* stats) {
+  if (!h || !stats) return FD_ERR_ARG;
+  *stats = h->stats;
+  return FD_OK;
+}
+
+fd_status fd_last_error(const fd_layout* h) { return h ? h->last_error : FD_ERR_ARG; }
+
+}  // extern "C"

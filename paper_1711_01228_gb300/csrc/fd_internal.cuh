@@ -1,0 +1,214 @@
+// fd_internal.cuh -- shared definitions of the CUDA layout engine.
+//
+// Geometry.  Vertices are padded to n_pad = nb * TILE.  The unordered pairs
+// of tile blocks are covered by a "half ring": block row I owns the tiles
+// (I, J) with J = (I + k) mod nb for k = 0 .. L_I - 1, where
+//   L_I = (nb + 1) / 2                    if nb is odd,
+//   L_I = nb / 2 + 1 (I < nb/2), nb / 2   if nb is even.
+// Every unordered block pair appears exactly once and every block row owns
+// about nb/2 tiles, so the rows are balanced.  Tile k = 0 is the diagonal
+// block, which holds only the pairs i < j.
+//
+// A tile stores one code per (i, j) pair, column-major over i: byte
+// [jl * TILE + il] for i = I*TILE + il, j = J*TILE + jl.  Code 0 means "no
+// pair" (padding, i >= j inside a diagonal tile); a real pair stores its
+// ideal distance d_ij (hop count as uint8, or float32).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fdl {
+
+constexpr int TILE = 128;          // vertices per tile side
+constexpr int CTA = 128;           // threads per CTA of the pair kernels (4 warps)
+constexpr int ROWS_PER_LANE = 4;   // i rows held by each lane (32 lanes x 4 = TILE)
+constexpr int LUT_N = 256;         // uint8 codes
+
+enum CodeKind { CODE_U8 = 0, CODE_F32 = 1 };
+
+// Modes of the cooperative kernel.
+enum KernelMode { KM_ENERGY = 0, KM_FORCES = 1, KM_RUN = 2 };
+
+// Error codes shared with fd_status (include/fd_layout.h).
+enum {
+  E_OK = 0,
+  E_NONFINITE = 4,
+  E_CG_BREAKDOWN = 5,
+  E_TIMEOUT = 7,
+};
+
+struct TaskDesc {
+  int I;      // block row
+  int k0;     // first tile offset in the strip
+  int k1;     // one past the last tile offset
+  int tile0;  // global index of tile (I, k0)
+};
+
+// Device control block of one cooperative launch.
+struct Ctrl {
+  unsigned long long ticket;   // dynamic tile scheduler
+  unsigned int bar_count;      // grid barrier arrivals
+  unsigned int bar_gen;        // grid barrier generation
+  int err;                     // first error (0 = none)
+  int iters;                   // outer iterations done
+  int cg_steps;                // CG steps over the launch
+  int cg_maxed;                // H solves stopped by cg_max
+  int accepted;                // extrapolations kept
+  int pad_;
+  double f_final;              // stress of the output layout
+  double crit_final;           // last termination criterion
+  double pair_passes;          // all-pairs passes evaluated
+  double matvec_passes;        // y = L^W p passes
+  double stress_passes;        // stress (+ RHS or force) passes, per candidate
+  int timeout_where;           // barrier index that timed out (diagnostic)
+  int pad2_;
+};
+
+struct Geometry {
+  int n, n_pad, nb, dim;
+  int ntiles, ntasks;
+  const int* tile_base;        // [nb + 1] first tile index of each strip
+  const int* strip_len;        // [nb] L_I
+  const TaskDesc* tasks;       // [ntasks]
+  const int* strip_task_base;  // [nb + 1]
+};
+
+// Parameters of the cooperative kernel (passed by value).
+struct KParams {
+  Geometry g;
+  int mode;
+  const void* D;               // distance tiles
+  const float4* lut;           // [LUT_N] {1/d, 1/d^2, -1, 0}; entry 0 = {0, 0, 0, 0}
+  const float* s;              // [n_pad] row sums of W (diagonal of L^W)
+  const float* inv_s;          // [n_pad] 1/s (0 for padding)
+  const float* x_in;           // [n][dim] input layout (device staging)
+  float* x_out;                // [n][dim] output (layout or forces)
+  // internal vectors, [n_pad][DIMP] with DIMP = 1, 2, 4 for dim = 1, 2, 3
+  float *X, *Z, *Xt, *B, *Bz, *Bt, *Zw, *R, *Zc, *Pa, *Pb, *Q;
+  float* part_j;               // [ntiles][2][TILE][DIMP]
+  float* part_i;               // [ntasks][2][TILE][DIMP]
+  double* sc_task;             // [ntasks][2] stress per candidate
+  double* sc_a;                // [nb][8] row-block scalars (set A)
+  double* sc_b;                // [nb][8] row-block scalars (set B)
+  Ctrl* ctrl;
+  const double* omega_seq;     // [max_iter] omega of each iteration
+  double* trace_f;             // [max_iter + 1]
+  int* trace_acc;              // [max_iter]
+  double* trace_om;            // [max_iter]
+  int* trace_cg;               // [max_iter]
+  double* trace_crit;          // [max_iter]
+  int max_iter, stop, cg_max;
+  double tol, cg_tol;
+  long long timeout_ns;        // limit of every grid-barrier / mbarrier wait
+};
+
+// ------------------------------------------------------------------------
+// small device helpers
+// ------------------------------------------------------------------------
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier for a cooperative launch (all CTAs co-resident).
+// Every wait is bounded: after timeout_ns the CTA records E_TIMEOUT and
+// leaves.  Returns false if an error is pending (the caller must return).
+__device__ __forceinline__ bool grid_sync(Ctrl* c, long long timeout_ns, int where) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* gen = &c->bar_gen;
+    volatile int* err = &c->err;
+    unsigned int g = *gen;
+    __threadfence();
+    unsigned int arrived = atomicAdd(&c->bar_count, 1u);
+    if (arrived == gridDim.x - 1) {
+      atomicExch(&c->bar_count, 0u);
+      __threadfence();
+      atomicAdd(&c->bar_gen, 1u);
+    } else {
+      unsigned long long t0 = globaltimer_ns();
+      unsigned int ns = 32;
+      while (*gen == g) {
+        if (*err != 0) break;
+        __nanosleep(ns);
+        if (ns < 256) ns <<= 1;
+        if ((long long)(globaltimer_ns() - t0) > timeout_ns) {
+          atomicCAS(&c->err, 0, (int)E_TIMEOUT);
+          atomicExch(&c->timeout_where, where);
+          break;
+        }
+      }
+    }
+    __threadfence();
+    s_ok = (*err == 0);
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__device__ __forceinline__ void set_error(Ctrl* c, int code) { atomicCAS(&c->err, 0, code); }
+
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Kahan-compensated accumulation.
+__device__ __forceinline__ void kahan_add(float& sum, float& comp, float v) {
+  float y = v - comp;
+  float t = sum + y;
+  comp = (t - sum) - y;
+  sum = t;
+}
+
+// shared-memory mbarrier + 1-D bulk copy (TMA) helpers
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count));
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  unsigned b = (unsigned)__cvta_generic_to_shared(bar);
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(d),
+      "l"(src), "r"(bytes), "r"(b)
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait on an mbarrier phase; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, long long timeout_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  unsigned long long t0 = globaltimer_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if ((long long)(globaltimer_ns() - t0) > timeout_ns) return false;
+  }
+  return true;
+}
+
+}  // namespace fdl

@@ -1,0 +1,27 @@
+// fd_solver_d3.cu -- instantiation of the cooperative layout kernel for
+// dim = 3 (one translation unit per dimension so that they build in parallel).
+#include "fd_solver.cuh"
+
+namespace fdl {
+
+template <int CODE>
+static cudaError_t config_one(int* blocks_per_sm, size_t* smem) {
+  using L = SmemLayout<3, CODE>;
+  *smem = L::BYTES;
+  cudaError_t e = cudaFuncSetAttribute(fd_main_kernel<3, CODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)L::BYTES);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fd_main_kernel<3, CODE>, CTA, L::BYTES);
+}
+
+cudaError_t main_config_d3(int code, int* blocks_per_sm, size_t* smem) {
+  return code == CODE_U8 ? config_one<CODE_U8>(blocks_per_sm, smem) : config_one<CODE_F32>(blocks_per_sm, smem);
+}
+
+cudaError_t launch_main_d3(int code, const KParams& p, int grid, size_t smem, cudaStream_t st) {
+  void* args[] = {const_cast<KParams*>(&p)};
+  const void* fn = (code == CODE_U8) ? (const void*)fd_main_kernel<3, CODE_U8> : (const void*)fd_main_kernel<3, CODE_F32>;
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(CTA), args, smem, st);
+}
+
+}  // namespace fdl

@@ -1,0 +1,180 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (derived in DESIGN.md, "Precision and tolerances"):
+  distances       bit-exact (integer hop counts); 1e-5 relative for float lengths
+  stress          1e-5 relative (FP32 pair terms, FP32 sums of <= 128 terms, FP64 above)
+  forces          1e-5 relative, Frobenius norm over all vertices (spec bound)
+  one SOR step    1e-4 relative on the layout (CG stops at relative residual 1e-6)
+  converged run   1e-4 relative on final stress, iterations within 2 % (at least 1)
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1711_01228_gb300 import api, build, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    api.lib()
+
+
+def _dense(rp, ci, policy=1, edge_len=None):
+    st, D = oracle.apsp(rp, ci, edge_len=edge_len, policy=policy)
+    return D
+
+
+GRAPHS = {
+    "path2": lambda: synth.path(2),
+    "k3": lambda: synth.complete(3),
+    "grid20": lambda: synth.grid(20, 20),
+    "er300": lambda: synth.erdos_renyi(300, 4.0, seed=1),
+    "tree383": lambda: synth.random_binary_tree(383, seed=2),
+    "delaunay1000": lambda: synth.delaunay(1000, seed=3),
+    "ba1500": lambda: synth.barabasi_albert(1500, 3, seed=4),
+    "rgg2049": lambda: synth.random_geometric(2049, 2, 6.0, seed=5)[:2],
+}
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+def test_distances_bit_exact(name):
+    rp, ci = GRAPHS[name]()
+    D = _dense(rp, ci)
+    n = len(rp) - 1
+    with api.Layout(rp, ci, dim=2, disconnected_policy=1) as L:
+        got = L.distance_rows(0, n)
+        info = L.info()
+    assert np.array_equal(got, D)
+    assert info["diameter"] == int(D.max()) or info["disconnected"] == 1
+
+
+def test_distances_weighted():
+    rp, ci = synth.delaunay(300, seed=7)
+    rng = np.random.default_rng(0)
+    n = len(rp) - 1
+    lens = {}
+    w = np.empty(len(ci), dtype=np.float32)
+    for u in range(n):
+        for e in range(rp[u], rp[u + 1]):
+            key = (min(u, ci[e]), max(u, ci[e]))
+            lens.setdefault(key, np.float32(rng.uniform(0.5, 2.0)))
+            w[e] = lens[key]
+    D = _dense(rp, ci, edge_len=w.astype(np.float64))
+    with api.Layout(rp, ci, dim=2, edge_len=w) as L:
+        got = L.distance_rows(0, n)
+        assert L.info()["code_bytes"] == 4
+    assert np.allclose(got, D, rtol=1e-5, atol=0)
+
+
+def test_disconnected_policy():
+    rp, ci = synth.erdos_renyi(200, 1.5, seed=3)
+    with pytest.raises(api.FdError) as e:
+        api.Layout(rp, ci, dim=2, disconnected_policy=0)
+    assert e.value.status == 3
+    D = _dense(rp, ci, policy=1)
+    with api.Layout(rp, ci, dim=2, disconnected_policy=1) as L:
+        assert L.info()["disconnected"] == 1
+        assert np.array_equal(L.distance_rows(0, len(rp) - 1), D)
+
+
+CASES = [("path2", 1), ("path2", 2), ("k3", 3), ("grid20", 2), ("er300", 2), ("er300", 3), ("tree383", 1),
+         ("delaunay1000", 2), ("ba1500", 3), ("rgg2049", 2)]
+
+
+@pytest.mark.parametrize("name,dim", CASES)
+def test_energy_and_forces(name, dim):
+    rp, ci = GRAPHS[name]()
+    n = len(rp) - 1
+    D = _dense(rp, ci)
+    X = synth.initial_layout(n, dim, seed=11) * 3.0
+    f_ref = oracle.stress(X, D)
+    F_ref = oracle.forces(X, D)
+    with api.Layout(rp, ci, dim=dim, disconnected_policy=1) as L:
+        f = L.energy(X)
+        F = L.forces(X)
+    assert f == pytest.approx(f_ref, rel=1e-5)
+    err = np.linalg.norm(F.astype(np.float64) - F_ref)
+    assert err <= 1e-5 * np.linalg.norm(F_ref) + 1e-12
+
+
+def test_torch_device_pointers():
+    import torch
+
+    rp, ci = synth.delaunay(700, seed=2)
+    n = len(rp) - 1
+    D = _dense(rp, ci)
+    X = synth.initial_layout(n, 2, seed=1)
+    Xt = torch.from_numpy(X).cuda()
+    with api.Layout(torch.from_numpy(rp).cuda(), torch.from_numpy(ci).cuda(), dim=2) as L:
+        f = L.energy(Xt)
+        F = L.forces(Xt)
+        assert F.is_cuda
+    assert f == pytest.approx(oracle.stress(X, D), rel=1e-5)
+    F_ref = oracle.forces(X, D)
+    assert np.linalg.norm(F.cpu().numpy() - F_ref) <= 1e-5 * np.linalg.norm(F_ref)
+
+
+def test_coincident_and_nonfinite():
+    rp, ci = synth.path(3)
+    D = _dense(rp, ci)
+    X = np.array([[0.0, 0.0], [0.0, 0.0], [1.0, 0.0]], dtype=np.float32)
+    with api.Layout(rp, ci, dim=2) as L:
+        assert L.energy(X) == pytest.approx(oracle.stress(X, D), rel=1e-6)
+        F = L.forces(X)
+        assert np.allclose(F, oracle.forces(X, D), atol=1e-6)
+        Xb = X.copy()
+        Xb[1, 0] = np.nan
+        with pytest.raises(api.FdError) as e:
+            L.energy(Xb)
+        assert e.value.status == 4
+
+
+@pytest.mark.parametrize("name,dim,omega", [("grid20", 2, 0.5), ("delaunay1000", 2, 1.0), ("er300", 3, 0.5),
+                                            ("tree383", 1, 0.0)])
+def test_one_sor_step(name, dim, omega):
+    rp, ci = GRAPHS[name]()
+    n = len(rp) - 1
+    D = _dense(rp, ci)
+    X0 = synth.initial_layout(n, dim, seed=5)
+    Xn, fn, acc, om, fZ = oracle.sor_step(X0.astype(np.float64), D, omega)
+    X = X0.copy()
+    with api.Layout(rp, ci, dim=dim, disconnected_policy=1) as L:
+        f, accepted, crit = L.sor_step(X, k=0, omega=omega, cg_tol=1e-6, cg_max=500)
+    assert accepted == acc
+    assert np.linalg.norm(X - Xn) <= 1e-4 * np.linalg.norm(Xn)
+    assert f == pytest.approx(fn, rel=1e-4)
+    crit_ref = oracle.criterion(oracle.STOP_REL_DISP, X0.astype(np.float64), Xn, 0, 0)
+    assert crit == pytest.approx(crit_ref, rel=1e-3)
+
+
+@pytest.mark.parametrize("omega", [0.0, 0.5])
+def test_converged_run_grid20(omega):
+    # 20x20 grid, X^0 uniform in [0,1]^2 from seed 0, relative displacement 1e-4, max 1000 iterations
+    rp, ci = synth.grid(20, 20)
+    D = _dense(rp, ci)
+    X0 = synth.initial_layout(400, 2, seed=0)
+    ref = oracle.sor_run(D, X0.astype(np.float64), omega=omega, tol=1e-4, max_iter=1000)
+    X = X0.copy()
+    with api.Layout(rp, ci, dim=2) as L:
+        r = L.run(X, trace=True, omega=omega, tol=1e-4, max_iter=1000)
+    assert r.stress == pytest.approx(ref.stress, rel=1e-4)
+    assert abs(r.iterations - ref.iterations) <= max(1, math.ceil(0.02 * ref.iterations))
+    assert np.all(np.diff(r.trace_f) <= 1e-6 * r.trace_f[:-1])  # Prop. 2.2 / line 6
+    assert r.trace_f[0] == pytest.approx(ref.trace_f[0], rel=1e-5)
+
+
+def test_probabilistic_strategy_matches_oracle_sequence():
+    rp, ci = synth.grid(10, 10)
+    D = _dense(rp, ci)
+    X0 = synth.initial_layout(100, 2, seed=3)
+    ref = oracle.sor_run(D, X0.astype(np.float64), strategy=oracle.OMEGA_PROB, seed=42, tol=1e-4, max_iter=30)
+    X = X0.copy()
+    with api.Layout(rp, ci, dim=2) as L:
+        r = L.run(X, trace=True, strategy=api.OMEGA_PROB, seed=42, tol=1e-4, max_iter=30)
+    k = min(r.iterations, ref.iterations)
+    assert np.array_equal(r.omega[:k], np.array(ref.trace_omega[:k]))
