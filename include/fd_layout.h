@@ -147,6 +147,37 @@ void fd_layout_destroy(fd_layout* h);
  * to *f_out (host).  Errors: FD_ERR_ARG, FD_ERR_NONFINITE, FD_ERR_CUDA. */
 fd_status fd_energy(fd_layout* h, const float* X, double* f_out);
 
+/* Largest n accepted by fd_energy_noalloc (its scratch holds one partial sum
+ * per 128 vertices: 4096 doubles plus one, 32 KB per device). */
+#define FD_NOALLOC_MAX_N 524288
+
+/* Stress f(X) like fd_energy, for callers that cannot allocate GPU memory.
+ * The paper has no counterpart to this entry point; it is a library
+ * convenience.  Some callers cannot call cudaMalloc: code inside a process
+ * whose device memory is owned by another allocator (a framework's caching
+ * allocator, a fixed-size arena), where one more allocation may fail or
+ * synchronise the whole device, and latency-critical loops that cannot
+ * afford one.  This call allocates nothing and needs no handle: its only
+ * scratch is a fixed 32 KB array in the library's device image, which every
+ * GPU that loads the library keeps until the process exits.
+ *   X       float32 [n][dim], device memory
+ *   D       float32 [n][n], device memory, row-major; only the strictly lower
+ *           triangle is read: d_ij (i < j) at D[j * n + i], each > 0
+ *   n       1 .. FD_NOALLOC_MAX_N; larger n returns FD_ERR_ARG
+ *   dim     1..3
+ *   f_out   host or device double; written with f(X)
+ *   cuda_stream  stream to run on (NULL = legacy default); the call
+ *           synchronises it before returning
+ * All calls on a device share the scratch array: calls whose work overlaps on
+ * the GPU (two streams, or two host threads at once) race and give wrong
+ * results.  The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Errors: FD_ERR_ARG (null or host X/D, sizes out
+ * of range), FD_ERR_NONFINITE (non-finite result written to a host f_out),
+ * FD_ERR_CUDA. */
+fd_status fd_energy_noalloc(const float* X, const float* D, int32_t n, int32_t dim, double* f_out,
+                            void* cuda_stream);
+
 /* Force F = (L^X - L^W) X = -(1/2) grad f(X) (Prop. 2.1 and Eq. (1)):
  * F_i = sum_{j != i} w_ij (d_ij / ||x_i - x_j|| - 1)(x_i - x_j); coincident
  * pairs contribute zero.  X and F_out are float32 [n][dim], host or device;

@@ -57,7 +57,8 @@ class Info(ctypes.Structure):
 
 EXPORTED = ["fd_options_default", "fd_layout_create", "fd_layout_destroy", "fd_energy", "fd_forces",
             "fd_sor_step", "fd_run", "fd_run_trace", "fd_distance_rows", "fd_layout_info",
-            "fd_last_stats", "fd_last_error", "fd_status_string"]
+            "fd_last_stats", "fd_last_error", "fd_status_string", "fd_energy_noalloc"]
+NOALLOC_MAX_N = 524288
 
 _LIB = None
 
@@ -104,6 +105,8 @@ def lib():
     L.fd_last_error.restype = i32
     L.fd_status_string.argtypes = [i32]
     L.fd_status_string.restype = ctypes.c_char_p
+    L.fd_energy_noalloc.argtypes = [P, P, i32, i32, P, P]
+    L.fd_energy_noalloc.restype = i32
     _LIB = L
     return L
 
@@ -261,3 +264,18 @@ class Layout:
                    "fd_run_trace")
             res.accepted, res.omega, res.cg_steps, res.crit = acc[:k], om[:k], cg[:k], cr[:k]
         return res
+
+
+def energy_noalloc(X, D, stream=None) -> float:
+    """Stress f(X) from a dense device distance matrix without any device
+    allocation by the library (for callers whose GPU memory is owned by
+    another allocator).  X: float32 CUDA tensor [n, dim]; D: float32 CUDA
+    tensor [n, n] whose strictly lower triangle holds d_ij."""
+    n, dim = int(X.shape[0]), int(X.shape[1])
+    if tuple(D.shape) != (n, n):
+        raise ValueError("D must be [n, n]")
+    f = ctypes.c_double()
+    st = None if stream is None else ctypes.c_void_p(int(stream))
+    _check(lib().fd_energy_noalloc(_ptr(X, np.float32), _ptr(D, np.float32), n, dim, ctypes.addressof(f), st),
+           "fd_energy_noalloc")
+    return f.value
