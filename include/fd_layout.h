@@ -100,6 +100,8 @@ typedef struct {
   double matvec_passes;    /* passes of y = L^W p (inside the H solves) */
   double stress_passes;    /* passes of stress (+ L^X X or force) per candidate layout */
   double kernel_ms;        /* device time of the call's layout kernel (CUDA events on the handle's stream) */
+  int32_t cg_stalled;      /* CG columns stopped before cg_tol because rounding left no descent */
+  int32_t reserved;
 } fd_stats;
 
 /* Library facts about a handle. */
@@ -226,6 +228,18 @@ fd_status fd_layout_info(const fd_layout* h, fd_info* info);
 
 /* Statistics of the last call on the handle (host struct). */
 fd_status fd_last_stats(const fd_layout* h, fd_stats* stats);
+
+/* Phase timeline (tracing).  fd_timeline_enable(h, cap) makes every later
+ * layout-kernel launch record, at each of its grid-wide barriers, the
+ * device time (ns since the launch started, from %globaltimer) and a phase
+ * tag: 1 pack, 2 stress pass, 3 force pass, 4 initial RHS pass, 5 H-step
+ * start (L^W x0), 6 L^W u0, 7 CG step, 8 stress/RHS of the candidates,
+ * 9 per-row-block reduction and vector update after a pass.
+ * cap = 0 disables it.  fd_timeline_read copies up to cap entries of the
+ * last launch (tags and times as doubles, interleaved: tag, t, tag, t, ...)
+ * and the number recorded.  Errors: FD_ERR_ARG, FD_ERR_OOM, FD_ERR_CUDA. */
+fd_status fd_timeline_enable(fd_layout* h, int32_t cap);
+fd_status fd_timeline_read(fd_layout* h, double* out, int32_t cap, int32_t* count);
 
 /* Status of the last failing call on the handle (FD_OK if none). */
 fd_status fd_last_error(const fd_layout* h);

@@ -44,7 +44,7 @@ class Stats(ctypes.Structure):
                 ("accepted", ctypes.c_int32), ("pair_passes", ctypes.c_double), ("pairs", ctypes.c_double),
                 ("final_stress", ctypes.c_double), ("final_crit", ctypes.c_double),
                 ("matvec_passes", ctypes.c_double), ("stress_passes", ctypes.c_double),
-                ("kernel_ms", ctypes.c_double)]
+                ("kernel_ms", ctypes.c_double), ("cg_stalled", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -57,7 +57,10 @@ class Info(ctypes.Structure):
 
 EXPORTED = ["fd_options_default", "fd_layout_create", "fd_layout_destroy", "fd_energy", "fd_forces",
             "fd_sor_step", "fd_run", "fd_run_trace", "fd_distance_rows", "fd_layout_info",
-            "fd_last_stats", "fd_last_error", "fd_status_string", "fd_energy_noalloc"]
+            "fd_last_stats", "fd_last_error", "fd_status_string", "fd_energy_noalloc", "fd_timeline_enable",
+            "fd_timeline_read"]
+TIMELINE_TAGS = {1: "pack", 2: "stress", 3: "forces", 4: "rhs0", 5: "h_init", 6: "cg_au0", 7: "cg_step",
+                 8: "candidates", 9: "rowblock_epilogue"}
 NOALLOC_MAX_N = 524288
 
 _LIB = None
@@ -107,6 +110,10 @@ def lib():
     L.fd_status_string.restype = ctypes.c_char_p
     L.fd_energy_noalloc.argtypes = [P, P, i32, i32, P, P]
     L.fd_energy_noalloc.restype = i32
+    L.fd_timeline_enable.argtypes = [P, i32]
+    L.fd_timeline_enable.restype = i32
+    L.fd_timeline_read.argtypes = [P, P, i32, ctypes.POINTER(i32)]
+    L.fd_timeline_read.restype = i32
     _LIB = L
     return L
 
@@ -205,6 +212,19 @@ class Layout:
         s = Stats()
         _check(lib().fd_last_stats(self._h, ctypes.byref(s)), "fd_last_stats")
         return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+    def timeline_enable(self, cap: int = 100000):
+        """Record (phase tag, ns) at every grid barrier of later launches."""
+        _check(lib().fd_timeline_enable(self._h, int(cap)), "fd_timeline_enable")
+        self._tl_cap = int(cap)
+
+    def timeline(self) -> np.ndarray:
+        """[k, 2] array of (tag, ns since launch start) of the last launch."""
+        cap = getattr(self, "_tl_cap", 0)
+        out = np.zeros((max(cap, 1), 2), dtype=np.float64)
+        k = ctypes.c_int32()
+        _check(lib().fd_timeline_read(self._h, out.ctypes.data, cap, ctypes.byref(k)), "fd_timeline_read")
+        return out[: min(k.value, cap)]
 
     def distance_rows(self, row0: int, nrows: int) -> np.ndarray:
         out = np.empty((nrows, self.n), dtype=np.float64)

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -25,9 +26,9 @@ cudaError_t launch_rowsum(int code, int n, int nb, const int* tile_base, const i
                           float* s, float* inv_s, cudaStream_t st);
 cudaError_t launch_distance_rows(int code, int n, int nb, const int* tile_base, const int* strip_len,
                                  const void* D, int row0, int nrows, double* out, cudaStream_t st);
-cudaError_t main_config_d1(int code, int* blocks_per_sm, size_t* smem);
-cudaError_t main_config_d2(int code, int* blocks_per_sm, size_t* smem);
-cudaError_t main_config_d3(int code, int* blocks_per_sm, size_t* smem);
+cudaError_t main_config_d1(int code, size_t lut_bytes, int* blocks_per_sm, size_t* smem);
+cudaError_t main_config_d2(int code, size_t lut_bytes, int* blocks_per_sm, size_t* smem);
+cudaError_t main_config_d3(int code, size_t lut_bytes, int* blocks_per_sm, size_t* smem);
 cudaError_t launch_main_d1(int code, const KParams& p, int grid, size_t smem, cudaStream_t st);
 cudaError_t launch_main_d2(int code, const KParams& p, int grid, size_t smem, cudaStream_t st);
 cudaError_t launch_main_d3(int code, const KParams& p, int grid, size_t smem, cudaStream_t st);
@@ -48,14 +49,17 @@ struct fd_layout {
   int* d_strip_len = nullptr;
   TaskDesc* d_tasks = nullptr;
   int* d_strip_task_base = nullptr;
-  float4* d_lut = nullptr;
+  int* d_contrib_ptr = nullptr;
+  int* d_contrib = nullptr;
+  unsigned char* d_lut = nullptr;
+  int lut_rows = 0;
   float* d_s = nullptr;
   float* d_inv_s = nullptr;
   float* d_vec = nullptr;  // pool of the per-vertex vectors
   float* d_part_j = nullptr;
   float* d_part_i = nullptr;
   double* d_sc_task = nullptr;
-  double* d_sc = nullptr;  // sc_a and sc_b
+  double* d_sc = nullptr;  // [2][nb][SC_STRIDE]
   Ctrl* d_ctrl = nullptr;
   float* d_stage_in = nullptr;
   float* d_stage_out = nullptr;
@@ -75,6 +79,9 @@ struct fd_layout {
   long long timeout_ns = 30000000000LL;
   double apsp_ms = 0.0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  double* d_timeline = nullptr;  // tracing: [timeline_cap][2]
+  int timeline_cap = 0;
+  int timeline_n = 0;
 };
 
 namespace {
@@ -245,10 +252,10 @@ void build_tasks(fd_layout* h) {
   h->ntasks = (int)h->tasks.size();
 }
 
-cudaError_t main_config(int dim, int code, int* bps, size_t* smem) {
-  if (dim == 1) return main_config_d1(code, bps, smem);
-  if (dim == 2) return main_config_d2(code, bps, smem);
-  return main_config_d3(code, bps, smem);
+cudaError_t main_config(int dim, int code, size_t lut_bytes, int* bps, size_t* smem) {
+  if (dim == 1) return main_config_d1(code, lut_bytes, bps, smem);
+  if (dim == 2) return main_config_d2(code, lut_bytes, bps, smem);
+  return main_config_d3(code, lut_bytes, bps, smem);
 }
 
 cudaError_t launch_main(int dim, int code, const KParams& p, int grid, size_t smem, cudaStream_t st) {
@@ -263,6 +270,8 @@ void release(fd_layout* h) {
   dev_free(h->d_strip_len);
   dev_free(h->d_tasks);
   dev_free(h->d_strip_task_base);
+  dev_free(h->d_contrib_ptr);
+  dev_free(h->d_contrib);
   dev_free(h->d_lut);
   dev_free(h->d_s);
   dev_free(h->d_inv_s);
@@ -280,6 +289,7 @@ void release(fd_layout* h) {
   dev_free(h->d_trace_crit);
   dev_free(h->d_trace_acc);
   dev_free(h->d_trace_cg);
+  dev_free(h->d_timeline);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
   h->ev0 = h->ev1 = nullptr;
@@ -451,23 +461,27 @@ KParams base_params(fd_layout* h, int mode) {
   p.g.strip_len = h->d_strip_len;
   p.g.tasks = h->d_tasks;
   p.g.strip_task_base = h->d_strip_task_base;
+  p.g.contrib_ptr = h->d_contrib_ptr;
+  p.g.contrib = h->d_contrib;
   p.mode = mode;
   p.D = h->D;
   p.lut = h->d_lut;
+  p.lut_rows = h->lut_rows;
   p.s = h->d_s;
   p.inv_s = h->d_inv_s;
   const size_t vs = (size_t)h->n_pad * h->dimp;
   float* v = h->d_vec;
-  float** slots[] = {&p.X, &p.Z, &p.Xt, &p.B, &p.Bz, &p.Bt, &p.Zw, &p.R, &p.Zc, &p.Pa, &p.Pb, &p.Q};
+  float** slots[] = {&p.X, &p.Z, &p.Xt, &p.B, &p.Bz, &p.Bt, &p.Zw, &p.R, &p.U, &p.W, &p.P, &p.S};
   for (int k = 0; k < 12; ++k) *slots[k] = v + k * vs;
   p.part_j = h->d_part_j;
   p.part_i = h->d_part_i;
-  p.sc_task = h->d_sc_task;
-  p.sc_a = h->d_sc;
-  p.sc_b = h->d_sc + (size_t)h->nb * 8;
+  p.sc_cta = reinterpret_cast<float2*>(h->d_sc_task);
+  p.sc = reinterpret_cast<float2*>(h->d_sc);
   p.ctrl = h->d_ctrl;
   p.timeout_ns = h->timeout_ns;
   p.max_iter = 0;
+  p.timeline = h->timeline_cap > 0 ? h->d_timeline : nullptr;
+  p.timeline_cap = h->timeline_cap;
   return p;
 }
 
@@ -483,6 +497,7 @@ fd_status run_kernel(fd_layout* h, KParams& p, Ctrl* ctrl_out, double* kernel_ms
   float ms = 0.f;
   FD_CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
   *kernel_ms = ms;
+  h->timeline_n = std::min(ctrl_out->timeline_n, h->timeline_cap);
   if (ctrl_out->err != 0) return (fd_status)ctrl_out->err;
   return FD_OK;
 }
@@ -500,6 +515,7 @@ void fill_stats(fd_layout* h, const Ctrl& c, double kms) {
   h->stats.matvec_passes = c.matvec_passes;
   h->stats.stress_passes = c.stress_passes;
   h->stats.kernel_ms = kms;
+  h->stats.cg_stalled = c.cg_stalled;
 }
 
 // Positions in: device pointers are used in place, host arrays are staged.
@@ -600,36 +616,67 @@ fd_status fd_layout_create(fd_layout** out, int32_t n, int32_t dim, const int32_
   }
   if ((s = build_distances(h, rp, ci, edge_len ? &len : nullptr, disconnected_policy)) != FD_OK) return bail(s);
 
-  // launch configuration of the cooperative kernel (depends on the code kind)
+  // replicated lookup table for uint8 codes 0 .. lut_rows-1 (shared memory):
+  // row c = 32 x float 1/c^2, then 16 x {1/c, -1}; row 0 (no pair) is zero
+  h->lut_rows = (h->code == CODE_U8) ? std::min(LUT_N, h->diameter + 2) : 0;
+  std::vector<unsigned char> lut((size_t)std::max(h->lut_rows, 1) * LUT_ROW, 0);
+  for (int c = 1; c < h->lut_rows; ++c) {
+    float* row = reinterpret_cast<float*>(lut.data() + (size_t)c * LUT_ROW);
+    const float w = (float)(1.0 / ((double)c * c)), inv = (float)(1.0 / c);
+    for (int k = 0; k < 32; ++k) row[k] = w;
+    for (int k = 0; k < 16; ++k) {
+      row[32 + 2 * k] = inv;
+      row[32 + 2 * k + 1] = -1.f;
+    }
+  }
+  // launch configuration of the cooperative kernel (depends on the code kind and table size)
   int bps = 0;
-  if (main_config(dim, h->code, &bps, &h->smem) != cudaSuccess || bps < 1) {
+  if (main_config(dim, h->code, (size_t)h->lut_rows * LUT_ROW, &bps, &h->smem) != cudaSuccess || bps < 1) {
     cudaGetLastError();
     return bail(FD_ERR_CUDA);
   }
   h->grid = bps * h->sm_count;
+  if (const char* cap = std::getenv("FDLAYOUT_MAX_CTAS")) {  // testing: force many tasks per CTA
+    const int c = std::atoi(cap);
+    if (c > 0 && c < h->grid) h->grid = c;
+  }
   build_tasks(h);
 
-  // lookup table {1/d, 1/d^2, -1, 0} per uint8 code; code 0 is "no pair"
-  std::vector<float4> lut(LUT_N);
-  lut[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-  for (int c = 1; c < LUT_N; ++c)
-    lut[c] = make_float4((float)(1.0 / c), (float)(1.0 / ((double)c * c)), -1.f, 0.f);
+  // partial sums of each row block, in a fixed order: row partials of its
+  // strip's tasks, then column partials of the tiles (I, R) by increasing I
+  std::vector<int> cptr(h->nb + 1, 0), clist;
+  for (int R = 0; R < h->nb; ++R) {
+    for (int t = h->strip_task_base[R]; t < h->strip_task_base[R + 1]; ++t) clist.push_back(t);
+    for (int I = 0; I < h->nb; ++I) {
+      const int k = (R - I + h->nb) % h->nb;
+      if (k < h->strip_len[I]) clist.push_back(-1 - (h->tile_base[I] + k));
+    }
+    cptr[R + 1] = (int)clist.size();
+  }
   const size_t vs = (size_t)h->n_pad * h->dimp;
-  if ((s = dev_alloc(&h->d_lut, LUT_N)) != FD_OK) return bail(s);
+  if ((s = dev_alloc(&h->d_contrib_ptr, h->nb + 1)) != FD_OK) return bail(s);
+  if ((s = dev_alloc(&h->d_contrib, clist.size())) != FD_OK) return bail(s);
+  if (cudaMemcpy(h->d_contrib_ptr, cptr.data(), cptr.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(h->d_contrib, clist.data(), clist.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(FD_ERR_CUDA);
+  }
+  if ((s = dev_alloc(&h->d_lut, lut.size())) != FD_OK) return bail(s);
   if ((s = dev_alloc(&h->d_s, h->n_pad)) != FD_OK) return bail(s);
   if ((s = dev_alloc(&h->d_inv_s, h->n_pad)) != FD_OK) return bail(s);
   if ((s = dev_alloc(&h->d_vec, 12 * vs)) != FD_OK) return bail(s);
   if ((s = dev_alloc(&h->d_part_j, (size_t)h->ntiles * 2 * TILE * h->dimp)) != FD_OK) return bail(s);
   if ((s = dev_alloc(&h->d_part_i, (size_t)h->ntasks * 2 * TILE * h->dimp)) != FD_OK) return bail(s);
-  if ((s = dev_alloc(&h->d_sc_task, (size_t)h->ntasks * 2)) != FD_OK) return bail(s);
-  if ((s = dev_alloc(&h->d_sc, (size_t)h->nb * 16)) != FD_OK) return bail(s);
+  if ((s = dev_alloc(&h->d_sc_task, (size_t)h->grid * 2)) != FD_OK) return bail(s);
+  if ((s = dev_alloc(&h->d_sc, (size_t)2 * h->nb * SC_STRIDE)) != FD_OK) return bail(s);
   if ((s = dev_alloc(&h->d_ctrl, 1)) != FD_OK) return bail(s);
   if ((s = dev_alloc(&h->d_stage_in, (size_t)n * dim)) != FD_OK) return bail(s);
   if ((s = dev_alloc(&h->d_stage_out, (size_t)n * dim)) != FD_OK) return bail(s);
   if ((s = dev_alloc(&h->d_tasks, h->ntasks)) != FD_OK) return bail(s);
   if ((s = dev_alloc(&h->d_strip_task_base, h->nb + 1)) != FD_OK) return bail(s);
   cudaStream_t st = h->stream;
-  if (cudaMemcpyAsync(h->d_lut, lut.data(), LUT_N * sizeof(float4), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+  if (cudaMemcpyAsync(h->d_lut, lut.data(), lut.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemsetAsync(h->d_sc, 0, (size_t)2 * h->nb * SC_STRIDE * sizeof(double), st) != cudaSuccess ||
       cudaMemcpyAsync(h->d_tasks, h->tasks.data(), h->ntasks * sizeof(TaskDesc), cudaMemcpyHostToDevice, st) !=
           cudaSuccess ||
       cudaMemcpyAsync(h->d_strip_task_base, h->strip_task_base.data(), (h->nb + 1) * sizeof(int),
@@ -847,5 +894,28 @@ fd_status fd_last_stats(const fd_layout* h, fd_stats* stats) {
 }
 
 fd_status fd_last_error(const fd_layout* h) { return h ? h->last_error : FD_ERR_ARG; }
+
+fd_status fd_timeline_enable(fd_layout* h, int32_t cap) {
+  if (!h || cap < 0) return FD_ERR_ARG;
+  dev_free(h->d_timeline);
+  h->timeline_cap = 0;
+  h->timeline_n = 0;
+  if (cap == 0) return FD_OK;
+  fd_status s = dev_alloc(&h->d_timeline, (size_t)2 * cap);
+  if (s != FD_OK) return fail(h, s);
+  h->timeline_cap = cap;
+  return FD_OK;
+}
+
+fd_status fd_timeline_read(fd_layout* h, double* out, int32_t cap, int32_t* count) {
+  if (!h || !count || cap < 0 || (cap > 0 && !out)) return FD_ERR_ARG;
+  const int k = std::min(cap, h->timeline_n);
+  *count = h->timeline_n;
+  if (k > 0 && cudaMemcpy(out, h->d_timeline, (size_t)2 * k * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, FD_ERR_CUDA);
+  }
+  return FD_OK;
+}
 
 }  // extern "C"

@@ -6,8 +6,9 @@
 //   L_I = (nb + 1) / 2                    if nb is odd,
 //   L_I = nb / 2 + 1 (I < nb/2), nb / 2   if nb is even.
 // Every unordered block pair appears exactly once and every block row owns
-// about nb/2 tiles, so the rows are balanced.  Tile k = 0 is the diagonal
-// block, which holds only the pairs i < j.
+// about nb/2 tiles, so both the rows and the per-row-block reductions (about
+// nb/2 column partials each) are balanced.  Tile k = 0 is the diagonal block,
+// which holds only the pairs i < j.
 //
 // A tile stores one code per (i, j) pair, column-major over i: byte
 // [jl * TILE + il] for i = I*TILE + il, j = J*TILE + jl.  Code 0 means "no
@@ -24,6 +25,8 @@ constexpr int TILE = 128;          // vertices per tile side
 constexpr int CTA = 128;           // threads per CTA of the pair kernels (4 warps)
 constexpr int ROWS_PER_LANE = 4;   // i rows held by each lane (32 lanes x 4 = TILE)
 constexpr int LUT_N = 256;         // uint8 codes
+constexpr int LUT_ROW = 256;       // bytes per code in the replicated shared-memory table
+constexpr int SC_STRIDE = 24;      // FP64 scalar slots per row block
 
 enum CodeKind { CODE_U8 = 0, CODE_F32 = 1 };
 
@@ -47,7 +50,7 @@ struct TaskDesc {
 
 // Device control block of one cooperative launch.
 struct Ctrl {
-  unsigned long long ticket;   // dynamic tile scheduler
+  unsigned long long reserved0;
   unsigned int bar_count;      // grid barrier arrivals
   unsigned int bar_gen;        // grid barrier generation
   int err;                     // first error (0 = none)
@@ -55,14 +58,15 @@ struct Ctrl {
   int cg_steps;                // CG steps over the launch
   int cg_maxed;                // H solves stopped by cg_max
   int accepted;                // extrapolations kept
-  int pad_;
+  int cg_stalled;              // CG columns stopped early because the curvature estimate lost positivity
   double f_final;              // stress of the output layout
   double crit_final;           // last termination criterion
   double pair_passes;          // all-pairs passes evaluated
   double matvec_passes;        // y = L^W p passes
   double stress_passes;        // stress (+ RHS or force) passes, per candidate
   int timeout_where;           // barrier index that timed out (diagnostic)
-  int pad2_;
+  int timeline_n;              // timeline entries written
+  unsigned long long t_start;  // %globaltimer at kernel start (CTA 0)
 };
 
 struct Geometry {
@@ -72,6 +76,8 @@ struct Geometry {
   const int* strip_len;        // [nb] L_I
   const TaskDesc* tasks;       // [ntasks]
   const int* strip_task_base;  // [nb + 1]
+  const int* contrib_ptr;      // [nb + 1] partial sums that make up each row block ...
+  const int* contrib;          // ... in a fixed order: t >= 0 row partial of task t, -1-t column partial of tile t
 };
 
 // Parameters of the cooperative kernel (passed by value).
@@ -79,18 +85,20 @@ struct KParams {
   Geometry g;
   int mode;
   const void* D;               // distance tiles
-  const float4* lut;           // [LUT_N] {1/d, 1/d^2, -1, 0}; entry 0 = {0, 0, 0, 0}
+  const unsigned char* lut;    // [lut_rows][LUT_ROW] replicated table: 32 x 1/d^2, 16 x {1/d, -1}
+  int lut_rows;                // codes 0 .. lut_rows-1 present in the tiles
   const float* s;              // [n_pad] row sums of W (diagonal of L^W)
   const float* inv_s;          // [n_pad] 1/s (0 for padding)
   const float* x_in;           // [n][dim] input layout (device staging)
   float* x_out;                // [n][dim] output (layout or forces)
-  // internal vectors, [n_pad][DIMP] with DIMP = 1, 2, 4 for dim = 1, 2, 3
-  float *X, *Z, *Xt, *B, *Bz, *Bt, *Zw, *R, *Zc, *Pa, *Pb, *Q;
+  // internal vectors, [n_pad][DIMP] with DIMP = 1, 2, 4 for dim = 1, 2, 3:
+  // layout X^k, its RHS B; candidates Z = X^{k+1}, Xt = X~ and their RHS;
+  // CG state Zw (iterate), R (residual), U = M^-1 R, W = L^W U, P, S = L^W P
+  float *X, *Z, *Xt, *B, *Bz, *Bt, *Zw, *R, *U, *W, *P, *S;
   float* part_j;               // [ntiles][2][TILE][DIMP]
   float* part_i;               // [ntasks][2][TILE][DIMP]
-  double* sc_task;             // [ntasks][2] stress per candidate
-  double* sc_a;                // [nb][8] row-block scalars (set A)
-  double* sc_b;                // [nb][8] row-block scalars (set B)
+  float2* sc_cta;              // [grid][2] stress of each CTA's pairs, per candidate (double-float)
+  float2* sc;                  // [2][nb][SC_STRIDE] row-block scalars (double-float), by pass parity
   Ctrl* ctrl;
   const double* omega_seq;     // [max_iter] omega of each iteration
   double* trace_f;             // [max_iter + 1]
@@ -101,6 +109,8 @@ struct KParams {
   int max_iter, stop, cg_max;
   double tol, cg_tol;
   long long timeout_ns;        // limit of every grid-barrier / mbarrier wait
+  double* timeline;            // NULL, or [timeline_cap][2] {tag, ns} written by CTA 0 at each barrier
+  int timeline_cap;
 };
 
 // ------------------------------------------------------------------------
@@ -152,6 +162,15 @@ __device__ __forceinline__ bool grid_sync(Ctrl* c, long long timeout_ns, int whe
 
 __device__ __forceinline__ void set_error(Ctrl* c, int code) { atomicCAS(&c->err, 0, code); }
 
+// Tracing: CTA 0, thread 0 appends (tag, ns since launch) to the timeline.
+__device__ __forceinline__ void tl_mark(const KParams& p, int tag) {
+  if (p.timeline && blockIdx.x == 0 && threadIdx.x == 0 && p.ctrl->timeline_n < p.timeline_cap) {
+    const int q = p.ctrl->timeline_n++;
+    p.timeline[2 * q] = (double)tag;
+    p.timeline[2 * q + 1] = (double)(globaltimer_ns() - p.ctrl->t_start);
+  }
+}
+
 __device__ __forceinline__ float rsqrt_approx(float x) {
   float y;
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -176,6 +195,16 @@ __device__ __forceinline__ void fence_mbar_init() {
 }
 __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// Orders this thread's view of generic-proxy global writes (made visible by a
+// grid barrier) before its subsequent bulk-copy (async-proxy) reads.
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+// Both of the above: before a bulk copy that overwrites shared memory just
+// read by this CTA and reads global memory written before a grid barrier.
+__device__ __forceinline__ void fence_proxy_async_all() {
+  asm volatile("fence.proxy.async;" ::: "memory");
 }
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
   unsigned a = (unsigned)__cvta_generic_to_shared(bar);

@@ -4,7 +4,7 @@
 //
 // Work decomposition
 // ------------------
-// All-pairs passes run over the tiles of the half-ring (fd_internal.cuh),
+// All-pairs passes run over the tiles of the half ring (fd_internal.cuh),
 // grouped into tasks of consecutive tiles of one block row.  CTAs take tasks
 // from a global ticket counter.  A CTA has 4 warps; every warp holds all 128
 // rows of block I (4 rows per lane, in registers) and sweeps 32 columns of
@@ -12,14 +12,21 @@
 // the column accumulators travel one lane down after every step, so after 32
 // steps each lane holds the complete column sums of its own column and both
 // endpoints of every pair are accumulated exactly once (symmetric n-body).
-// Distance codes of a tile (16 KB for uint8) are staged in shared memory by a
-// 1-D bulk copy (TMA) that is prefetched one tile ahead; column positions are
-// staged by the CTA's threads.
 //
-// Per-tile column partials and per-task row partials go to global buffers and
-// are summed per row block in a fixed order (Kahan-compensated), so results
-// do not depend on which CTA ran which task.  Scalars (stress, CG dot
-// products, displacement sums) are reduced in FP64 in a fixed order.
+// Pipeline: a tile's distance codes (16 KB for uint8) and the raw per-vertex
+// arrays of its two blocks arrive by 1-D bulk copies (TMA) on one mbarrier,
+// issued one tile ahead.  The raw arrays are turned into the pass's vectors
+// in shared memory (e.g. the CG vector u = M^-1 (r - alpha s) is formed on
+// the fly), so every pass reads only what the previous pass left in memory.
+// CTA b takes tasks b, b + G, b + 2G, ... (G CTAs): a pass has no global
+// synchronisation inside it.
+//
+// Reductions: per-tile column partials and per-task row partials go to
+// global buffers.  After the pass (grid barrier) one CTA per row block sums
+// its partials in a fixed order (Kahan-compensated) and runs the step's
+// per-row epilogue, which updates the vectors in place.  Scalars (stress,
+// CG dot products, displacement sums) are FP64 sums in a fixed order;
+// results never depend on timing.
 #pragma once
 
 #include "fd_internal.cuh"
@@ -65,7 +72,6 @@ __device__ __forceinline__ void stv(float* a, int i, const Vec<DIM>& v) {
   }
 }
 
-// shared-memory vector access (plain loads/stores)
 template <int DIM>
 __device__ __forceinline__ Vec<DIM> lds_v(const float* a, int i) {
   Vec<DIM> r;
@@ -94,111 +100,206 @@ __device__ __forceinline__ void sts_v(float* a, int i, const Vec<DIM>& v) {
   }
 }
 
-// A source of per-vertex vectors for a pair pass: a + beta * b (b optional).
 template <int DIM>
-struct Src {
-  const float* a;
-  const float* b;
-  float beta[DIM];
-  __device__ __forceinline__ Vec<DIM> load(int i) const {
-    Vec<DIM> v = ldv<DIM>(a, i);
-    if (b != nullptr) {
-      Vec<DIM> w = ldv<DIM>(b, i);
+__device__ __forceinline__ Vec<DIM> vzero() {
+  Vec<DIM> v;
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) v.c[d] = fmaf(beta[d], w.c[d], v.c[d]);
-    }
-    return v;
-  }
-};
-
-template <int DIM>
-__device__ __forceinline__ Src<DIM> make_src(const float* a) {
-  Src<DIM> s;
-  s.a = a;
-  s.b = nullptr;
-#pragma unroll
-  for (int d = 0; d < DIM; ++d) s.beta[d] = 0.f;
-  return s;
+  for (int d = 0; d < DIM; ++d) v.c[d] = 0.f;
+  return v;
 }
 
 enum PairMode { PM_STRESS = 0, PM_FORCES = 1, PM_RHS = 2, PM_MATVEC = 3 };
+
+// How a pass forms its vectors from the raw arrays it copies.
+enum SrcKind {
+  SK_DIRECT = 0,  // v = a[0]
+  SK_CGU = 1,     // u = inv_s * (r - alpha * (w + beta * s_prev)); a = {r, w, s_prev, inv_s}
+  SK_K2 = 2       // z = zw - zw_0, xt = (1 + omega) z - omega x; a = {zw, x}
+};
+
+template <int SK>
+struct SrcN {
+  static constexpr int v = (SK == SK_DIRECT) ? 1 : (SK == SK_CGU) ? 4 : 2;
+};
+
+struct PassSrc {
+  const float* a[4];
+  float alpha[3], beta[3];  // SK_CGU, per column
+  float z0[3];              // SK_K2: pinned vertex 0 of the CG solution
+  float om;                 // SK_K2: omega of Eq. (10)
+};
+
+// The CG vector u_{i+1} (used both on the fly and in the epilogue, so that
+// the two agree bit for bit).
+__device__ __forceinline__ float cg_u(float r, float w, float sp, float is, float alpha, float beta) {
+  return is * fmaf(-alpha, fmaf(beta, sp, w), r);
+}
+// Eq. (10): X~ = (1 + omega) X^{k+1} - omega X^k.
+__device__ __forceinline__ float sor_xt(float z, float x, float om) { return fmaf(1.0f + om, z, -(om * x)); }
 
 template <int CODE>
 struct CodeBytes {
   static constexpr int v = (CODE == CODE_U8) ? 1 : 4;
 };
 
-// Shared memory of the kernel.  The column partial "red" area aliases the
-// distance buffer that has just been consumed.
+// Shared memory.  The lookup table is replicated so that every lane reads
+// its own bank: row c (256 bytes) holds 32 copies of 1/d^2 (bytes 0..127)
+// and 16 copies of {1/d, -1} (bytes 128..255) for code c.
 template <int DIM, int CODE>
 struct SmemLayout {
   static constexpr int DP = DimP<DIM>::v;
   static constexpr int DBUF = TILE * TILE * CodeBytes<CODE>::v;
-  static constexpr int OFF_D0 = 0;
-  static constexpr int OFF_D1 = DBUF;
-  static constexpr int OFF_POS = 2 * DBUF;                      // [2][TILE][DP] floats
-  static constexpr int OFF_LUT2 = OFF_POS + 2 * TILE * DP * 4;  // float2 [LUT_N] {1/d, -1}
-  static constexpr int OFF_LUTF = OFF_LUT2 + LUT_N * 8;         // float2 [LUT_N] {1/d, 1/d^2}
-  static constexpr int OFF_LUTW = OFF_LUTF + LUT_N * 8;         // float  [LUT_N] 1/d^2
-  static constexpr int OFF_RED64 = OFF_LUTW + LUT_N * 4;        // double [CTA]
-  static constexpr int OFF_MISC = OFF_RED64 + CTA * 8;          // mbar[2], task slots
-  static constexpr int BYTES = OFF_MISC + 64;
+  static constexpr int RAW_ARR = TILE * DP * 4;                  // bytes of one block of one raw array
+  static constexpr int OFF_RED64 = 0;                            // float2 [CTA] reduction scratch
+  static constexpr int OFF_IDX = OFF_RED64 + CTA * 8;            // int [CTA] contribution indices
+  static constexpr int OFF_MISC = OFF_IDX + CTA * 4;             // mbar[2], slots
+  static constexpr int OFF_POSI = 2048;                          // [2][TILE][DP], row-interleaved
+  static constexpr int OFF_POSJ = OFF_POSI + 2 * RAW_ARR;        // [2][TILE][DP]
+  static constexpr int OFF_RAW = OFF_POSJ + 2 * RAW_ARR;         // [4 arrays][2 blocks][TILE][DP] floats
+  static constexpr int OFF_D0 = ((OFF_RAW + 4 * 2 * RAW_ARR + 127) / 128) * 128;
+  static constexpr int OFF_D1 = OFF_D0 + DBUF;
+  static constexpr int OFF_LUT = ((OFF_D1 + DBUF + 255) / 256) * 256;
+  static constexpr int BASE_BYTES = OFF_LUT;
+  static_assert(OFF_MISC + 64 <= OFF_POSI, "fixed regions overlap");
   static_assert(4 * 2 * TILE * DP * 4 <= DBUF, "row partial area must fit in a distance buffer");
 };
+constexpr int SMEM_OFF_IDX = CTA * 8;  // OFF_IDX, identical for every layout
+constexpr int SMEM_OFF_POSI = 2048;   // OFF_POSI, identical for every layout
 
 struct PairState {
-  unsigned long long ticket_base;
-  unsigned parity[2];
+  unsigned parity;  // bit b: phase parity of mbarrier b
+  int pass;         // passes run so far (selects the scalar buffer parity)
 };
 
 // --------------------------------------------------------------------------
-// Deterministic FP64 reductions across a CTA
+// Deterministic FP64 reductions
 // --------------------------------------------------------------------------
 
-// Sum of v over the CTA's threads, fixed tree order; result valid in all threads.
-__device__ __forceinline__ double cta_sum_f64(double v, double* red) {
-  red[threadIdx.x] = v;
+// Reductions use double-float numbers (hi + lo, each FP32, combined with the
+// error-free TwoSum / TwoProduct transformations): about 44 significant bits
+// at FP32 speed.  FP64 arithmetic is slow on this GPU and is kept to a few
+// scalar operations per reduction.
+struct df {
+  float hi, lo;
+};
+__device__ __forceinline__ df df_of(float x) { return {x, 0.f}; }
+// exact product of two floats
+__device__ __forceinline__ df df_prod(float x, float y) {
+  const float p = x * y;
+  return {p, fmaf(x, y, -p)};
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  float e = (a.hi - (s - bb)) + (b.hi - bb);
+  e += a.lo + b.lo;
+  const float hi = s + e;
+  return {hi, e - (hi - s)};
+}
+// exact difference of two floats
+__device__ __forceinline__ df df_diff(float x, float y) {
+  const float s = x - y;
+  const float bb = s - x;
+  return {s, (x - (s - bb)) + (-y - bb)};
+}
+__device__ __forceinline__ df df_sqr(df a) { return df_add(df_prod(a.hi, a.hi), df_of(2.f * a.hi * a.lo)); }
+__device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ df df_ld(const float2* p) {
+  const float2 v = __ldcg(p);
+  return {v.x, v.y};
+}
+__device__ __forceinline__ void df_st(float2* p, df a) { __stcg(p, make_float2(a.hi, a.lo)); }
+
+// Sums K values over the CTA in a fixed order; the totals land in v[] of every thread.
+template <int K>
+__device__ __forceinline__ void cta_sum_multi(df (&v)[K], float2* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      df q;
+      q.hi = __shfl_down_sync(0xffffffffu, v[k].hi, o);
+      q.lo = __shfl_down_sync(0xffffffffu, v[k].lo, o);
+      v[k] = df_add(v[k], q);
+    }
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) red[warp * K + k] = make_float2(v[k].hi, v[k].lo);
+  }
   __syncthreads();
 #pragma unroll
-  for (int s = CTA / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-    __syncthreads();
+  for (int k = 0; k < K; ++k) {
+    df t = {red[k].x, red[k].y};
+#pragma unroll
+    for (int w = 1; w < 4; ++w) t = df_add(t, df{red[w * K + k].x, red[w * K + k].y});
+    v[k] = t;
   }
-  double r = red[0];
   __syncthreads();
-  return r;
 }
 
-// Sum over a strided FP64 array a[i * stride + off], i < count; every CTA
-// obtains the identical value.
-__device__ __forceinline__ double sum_strided_f64(const double* a, int count, int stride, int off,
-                                                  double* red) {
-  double v = 0.0;
-  for (int i = threadIdx.x; i < count; i += CTA) v += __ldcg(a + (size_t)i * stride + off);
-  return cta_sum_f64(v, red);
+// Sums slots [off, off+K) of the row-block scalar array (stride per block)
+// over nb blocks; every CTA gets the identical values.
+template <int K>
+__device__ __forceinline__ void sum_blocks(const float2* a, int nb, int stride, int off, df (&out)[K], float2* red) {
+#pragma unroll
+  for (int k = 0; k < K; ++k) out[k] = df_of(0.f);
+  for (int R = threadIdx.x; R < nb; R += CTA) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) out[k] = df_add(out[k], df_ld(a + (size_t)R * stride + off + k));
+  }
+  cta_sum_multi<K>(out, red);
+}
+__device__ __forceinline__ float df_f(df a) { return a.hi + a.lo; }
+
+// Sum of the per-CTA stress slots (candidate c) in a fixed order.
+__device__ __forceinline__ double sum_ctas(const float2* sc, int c, float2* red) {
+  df v[1] = {df_of(0.f)};
+  for (int t = threadIdx.x; t < (int)gridDim.x; t += CTA) v[0] = df_add(v[0], df_ld(sc + (size_t)t * 2 + c));
+  cta_sum_multi<1>(v, red);
+  return df_to_double(v[0]);
 }
 
 // --------------------------------------------------------------------------
 // One tile of a pair pass
 // --------------------------------------------------------------------------
 
+// Independent column-accumulator chains per warp.  Chain c serves the steps
+// t = c (mod CH) and travels CH lanes per use, so consecutive steps do not
+// wait on each other's shuffles.
+template <int MODE, int DIM>
+struct Chains {
+  static constexpr int v = (MODE == PM_MATVEC) ? 4 : (DIM == 3 ? 1 : 2);
+};
+
 template <int DIM, int MODE, int NC, int CODE>
 __device__ __forceinline__ void tile_compute(const unsigned char* __restrict__ dt, const float* __restrict__ posj,
-                                             const float2* __restrict__ lut2, const float2* __restrict__ lutf,
-                                             const float* __restrict__ lutw, const Vec<DIM> (&xi)[NC][ROWS_PER_LANE],
-                                             Vec<DIM> (&iacc)[NC][ROWS_PER_LANE], Vec<DIM> (&jacc)[NC],
+                                             const unsigned char* __restrict__ lut,
+                                             const Vec<DIM> (&xi)[NC][ROWS_PER_LANE],
+                                             Vec<DIM> (&iacc)[NC][ROWS_PER_LANE], Vec<DIM> (&jout)[NC],
                                              float (&st)[NC], int lane, int warp) {
   constexpr int DP = DimP<DIM>::v;
+  constexpr int CH = Chains<MODE, DIM>::v;
   constexpr float TINY = 1e-30f;  // keeps rsqrt finite for coincident points; below FP32 resolution of r^2
+  const unsigned off_w = 4u * lane;                // this lane's copy of 1/d^2
+  const unsigned off_k = 128u + 8u * (lane & 15);  // this lane's copy of {1/d, -1}
+  Vec<DIM> jacc[CH][NC];
+#pragma unroll
+  for (int h = 0; h < CH; ++h)
+#pragma unroll
+    for (int c = 0; c < NC; ++c) jacc[h][c] = vzero<DIM>();
 #pragma unroll 1
-  for (int t = 0; t < 32; ++t) {
-    const int jl = warp * 32 + ((lane + t) & 31);
-    float dv[ROWS_PER_LANE];
+  for (int t0 = 0; t0 < 32; t0 += CH) {
+#pragma unroll
+  for (int h = 0; h < CH; ++h) {
+    const int jl = warp * 32 + ((lane + t0 + h) & 31);
     unsigned codes = 0;
+    float dv[ROWS_PER_LANE];
     if constexpr (CODE == CODE_U8) {
       codes = *reinterpret_cast<const unsigned*>(dt + jl * TILE + ROWS_PER_LANE * lane);
     } else {
-      float4 q = *reinterpret_cast<const float4*>(dt + 4 * (jl * TILE + ROWS_PER_LANE * lane));
+      const float4 q = *reinterpret_cast<const float4*>(dt + 4 * (jl * TILE + ROWS_PER_LANE * lane));
       dv[0] = q.x;
       dv[1] = q.y;
       dv[2] = q.z;
@@ -209,23 +310,18 @@ __device__ __forceinline__ void tile_compute(const unsigned char* __restrict__ d
     for (int c = 0; c < NC; ++c) pj[c] = lds_v<DIM>(posj + c * TILE * DP, jl);
 #pragma unroll
     for (int a = 0; a < ROWS_PER_LANE; ++a) {
-      float invd, negm, w;
+      float invd = 0.f, negm = 0.f, w = 0.f;
       if constexpr (CODE == CODE_U8) {
-        const unsigned code = (codes >> (8 * a)) & 0xFFu;
-        if constexpr (MODE == PM_MATVEC) {
-          w = lutw[code];
-          invd = 0.f;
-          negm = 0.f;
-        } else if constexpr (MODE == PM_FORCES) {
-          float2 l = lutf[code];
-          invd = l.x;
-          w = l.y;
-          negm = 0.f;
-        } else {
-          float2 l = lut2[code];
+        // byte offset 256 * code + this lane's offset, built by one byte permute
+        if constexpr (MODE == PM_MATVEC || MODE == PM_FORCES) {
+          const unsigned ow = __byte_perm(codes, off_w, 0x5504u | (unsigned)(a << 4));
+          w = *reinterpret_cast<const float*>(lut + ow);
+        }
+        if constexpr (MODE != PM_MATVEC) {
+          const unsigned ok = __byte_perm(codes, off_k, 0x5504u | (unsigned)(a << 4));
+          const float2 l = *reinterpret_cast<const float2*>(lut + ok);
           invd = l.x;
           negm = l.y;
-          w = 0.f;
         }
       } else {
         const float d = dv[a];
@@ -237,7 +333,7 @@ __device__ __forceinline__ void tile_compute(const unsigned char* __restrict__ d
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
           iacc[0][a].c[d] = fmaf(-w, pj[0].c[d], iacc[0][a].c[d]);
-          jacc[0].c[d] = fmaf(-w, xi[0][a].c[d], jacc[0].c[d]);
+          jacc[h][0].c[d] = fmaf(-w, xi[0][a].c[d], jacc[h][0].c[d]);
         }
       } else {
 #pragma unroll
@@ -265,7 +361,7 @@ __device__ __forceinline__ void tile_compute(const unsigned char* __restrict__ d
 #pragma unroll
             for (int d = 0; d < DIM; ++d) {
               iacc[c][a].c[d] = fmaf(coef, dx[d], iacc[c][a].c[d]);
-              jacc[c].c[d] = fmaf(-coef, dx[d], jacc[c].c[d]);
+              jacc[h][c].c[d] = fmaf(-coef, dx[d], jacc[h][c].c[d]);
             }
           }
         }
@@ -275,128 +371,247 @@ __device__ __forceinline__ void tile_compute(const unsigned char* __restrict__ d
 #pragma unroll
       for (int c = 0; c < NC; ++c)
 #pragma unroll
-        for (int d = 0; d < DIM; ++d) jacc[c].c[d] = __shfl_sync(0xffffffffu, jacc[c].c[d], (lane + 1) & 31);
+        for (int d = 0; d < DIM; ++d)
+          jacc[h][c].c[d] = __shfl_sync(0xffffffffu, jacc[h][c].c[d], (lane + CH) & 31);
+    }
+  }
+  }
+  // chain h of lane l now holds column (l + h) & 31: gather column l's chains
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    jout[c] = jacc[0][c];
+#pragma unroll
+    for (int h = 1; h < CH; ++h)
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) jout[c].c[d] += __shfl_sync(0xffffffffu, jacc[h][c].c[d], (lane - h) & 31);
+  }
+}
+
+// Forms element t of one block (side 0 = I, 1 = J) of the pass's vectors
+// from the raw arrays in shared memory.
+template <int DIM, int SK, int NC>
+__device__ __forceinline__ void form(const PassSrc& s, const float* raw, int side, int t, Vec<DIM> (&out)[NC]) {
+  constexpr int DP = DimP<DIM>::v;
+  constexpr int A = TILE * DP;  // floats per raw block
+  if constexpr (SK == SK_DIRECT) {
+    out[0] = lds_v<DIM>(raw + (0 * 2 + side) * A, t);
+  } else if constexpr (SK == SK_CGU) {
+    const Vec<DIM> r = lds_v<DIM>(raw + (0 * 2 + side) * A, t);
+    const Vec<DIM> w = lds_v<DIM>(raw + (1 * 2 + side) * A, t);
+    const Vec<DIM> sp = lds_v<DIM>(raw + (2 * 2 + side) * A, t);
+    const float is = raw[(3 * 2 + side) * A + t];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) out[0].c[d] = cg_u(r.c[d], w.c[d], sp.c[d], is, s.alpha[d], s.beta[d]);
+  } else {
+    const Vec<DIM> zw = lds_v<DIM>(raw + (0 * 2 + side) * A, t);
+    Vec<DIM> z;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) z.c[d] = zw.c[d] - s.z0[d];
+    out[0] = z;
+    if constexpr (NC == 2) {
+      const Vec<DIM> x = lds_v<DIM>(raw + (1 * 2 + side) * A, t);
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) out[1].c[d] = sor_xt(z.c[d], x.c[d], s.om);
     }
   }
 }
 
 // --------------------------------------------------------------------------
-// A full pair pass over all tasks (dynamic scheduling)
+// Row-block reduction of the partial buffers: thread t gets row R*TILE + t.
 // --------------------------------------------------------------------------
 
-template <int DIM, int CODE>
-__device__ __forceinline__ const unsigned char* tile_ptr(const KParams& p, int tile) {
-  return reinterpret_cast<const unsigned char*>(p.D) + (size_t)tile * (TILE * TILE * CodeBytes<CODE>::v);
+// Sums the partials of row block R (thread t: row R*TILE + t) and leaves
+// the result in shared memory, out[c * TILE * DIM + t * DIM + d].  Out of
+// line, with plain pointer arguments, so that its loads in flight get their
+// own registers.
+template <int DIM, int NC>
+__device__ __noinline__ void reduce_rows_smem(const float* __restrict__ part_i, const float* __restrict__ part_j,
+                                              const int* __restrict__ contrib_ptr, const int* __restrict__ contrib,
+                                              int R, int* idx, float* out) {
+  constexpr int DP = DimP<DIM>::v;
+  constexpr int Q = 16;  // partials in flight per batch
+  const int row = threadIdx.x;
+  Vec<DIM> s[NC], cmp[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    s[c] = vzero<DIM>();
+    cmp[c] = vzero<DIM>();
+  }
+  const int c0 = contrib_ptr[R], c1 = contrib_ptr[R + 1];
+  for (int base = c0; base < c1; base += CTA) {
+    const int cnt = min(CTA, c1 - base);
+    __syncthreads();
+    if (row < cnt) idx[row] = contrib[base + row];
+    __syncthreads();
+    for (int q0 = 0; q0 < cnt; q0 += Q) {
+      Vec<DIM> v[Q][NC];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        if (q0 + q < cnt) {
+          const int e = idx[q0 + q];
+          const float* src = (e >= 0) ? part_i + (size_t)e * 2 * TILE * DP : part_j + (size_t)(-1 - e) * 2 * TILE * DP;
+#pragma unroll
+          for (int c = 0; c < NC; ++c) v[q][c] = ldv<DIM>(src + (size_t)c * TILE * DP, row);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < Q; ++q)
+        if (q0 + q < cnt) {
+#pragma unroll
+          for (int c = 0; c < NC; ++c)
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) kahan_add(s[c].c[d], cmp[c].c[d], v[q][c].c[d]);
+        }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NC; ++c)
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) out[(c * TILE + row) * DIM + d] = s[c].c[d] - cmp[c].c[d];
 }
 
-template <int DIM, int MODE, int NC, int CODE>
-__device__ bool pair_pass(const KParams& p, unsigned char* smem, PairState& ps, const Src<DIM> (&src)[NC]) {
+template <int DIM, int NC>
+__device__ __forceinline__ void reduce_rows(const KParams& p, int R, Vec<DIM> (&out)[NC]) {
+  extern __shared__ __align__(256) unsigned char smem_dyn[];
+  int* idx = reinterpret_cast<int*>(smem_dyn + SMEM_OFF_IDX);
+  float* res = reinterpret_cast<float*>(smem_dyn + SMEM_OFF_POSI);  // free outside the passes
+  reduce_rows_smem<DIM, NC>(p.part_i, p.part_j, p.g.contrib_ptr, p.g.contrib, R, idx, res);
+#pragma unroll
+  for (int c = 0; c < NC; ++c)
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) out[c].c[d] = res[(c * TILE + threadIdx.x) * DIM + d];
+}
+
+__device__ __forceinline__ float2* scal(const KParams& p, int parity) {
+  return p.sc + (size_t)parity * p.g.nb * SC_STRIDE;
+}
+
+// Thread 0 of a CTA: bulk copies (TMA) of a tile's distance codes and of
+// blocks I and J of every raw source array, completing on mbarrier b.
+template <int DIM, int CODE, int SK>
+__device__ __forceinline__ void issue_tile(const KParams& p, const PassSrc& src, unsigned char* smem, int tile, int I,
+                                        int J, int b) {
   using L = SmemLayout<DIM, CODE>;
   constexpr int DP = DimP<DIM>::v;
   constexpr unsigned TBYTES = TILE * TILE * CodeBytes<CODE>::v;
-  const Geometry& g = p.g;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NA = SrcN<SK>::v;
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L::OFF_MISC);
-  int* slot = reinterpret_cast<int*>(smem + L::OFF_MISC + 16);
-  float* posj = reinterpret_cast<float*>(smem + L::OFF_POS);
-  const float2* lut2 = reinterpret_cast<const float2*>(smem + L::OFF_LUT2);
-  const float2* lutf = reinterpret_cast<const float2*>(smem + L::OFF_LUTF);
-  const float* lutw = reinterpret_cast<const float*>(smem + L::OFF_LUTW);
-  double* red64 = reinterpret_cast<double*>(smem + L::OFF_RED64);
-  unsigned char* dbuf[2] = {smem + L::OFF_D0, smem + L::OFF_D1};
+  float* raw = reinterpret_cast<float*>(smem + L::OFF_RAW);
+  unsigned char* dbuf = smem + (b ? L::OFF_D1 : L::OFF_D0);
+  unsigned bytes = TBYTES;
+#pragma unroll
+  for (int a = 0; a < NA; ++a) bytes += 2u * ((SK == SK_CGU && a == 3) ? TILE * 4 : TILE * DP * 4);
+  fence_proxy_async();  // this CTA's reads of the raw area come before the copy overwrites it
+  mbar_expect_tx(&mbar[b], bytes);
+  bulk_g2s(dbuf, reinterpret_cast<const unsigned char*>(p.D) + (size_t)tile * TBYTES, TBYTES, &mbar[b]);
+#pragma unroll
+  for (int a = 0; a < NA; ++a) {
+    const bool scalar = (SK == SK_CGU && a == 3);
+    const unsigned ab = scalar ? TILE * 4 : TILE * DP * 4;
+    const int stride = scalar ? TILE : TILE * DP;
+    bulk_g2s(raw + (a * 2 + 0) * TILE * DP, src.a[a] + (size_t)I * stride, ab, &mbar[b]);
+    bulk_g2s(raw + (a * 2 + 1) * TILE * DP, src.a[a] + (size_t)J * stride, ab, &mbar[b]);
+  }
+}
 
-  auto grab = [&]() -> int {
-    if (threadIdx.x == 0) {
-      unsigned long long t = atomicAdd(&p.ctrl->ticket, 1ull) - ps.ticket_base;
-      slot[0] = (t < (unsigned long long)g.ntasks) ? (int)t : -1;
-    }
-    __syncthreads();
-    int r = slot[0];
-    __syncthreads();
-    return r;
-  };
+// --------------------------------------------------------------------------
+// A full pair pass: CTA b takes tasks b, b + G, b + 2G, ... (G = grid size);
+// no global synchronisation inside the pass.
+// --------------------------------------------------------------------------
 
-  bool ok = true;
-  int cur = grab();
-  int buf = 0;
-  if (cur >= 0) {
+template <int DIM, int MODE, int NC, int CODE, int SK>
+__device__ bool pair_pass(const KParams& p, unsigned char* smem, PairState& ps, const PassSrc& src) {
+  using L = SmemLayout<DIM, CODE>;
+  constexpr int DP = DimP<DIM>::v;
+  const Geometry& g = p.g;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L::OFF_MISC);
+  float* raw = reinterpret_cast<float*>(smem + L::OFF_RAW);
+  float* posi = reinterpret_cast<float*>(smem + L::OFF_POSI);
+  float* posj = reinterpret_cast<float*>(smem + L::OFF_POSJ);
+  float2* red64 = reinterpret_cast<float2*>(smem + L::OFF_RED64);
+  const unsigned char* lut = smem + L::OFF_LUT;
+  float ssum[NC], scomp[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) ssum[c] = scomp[c] = 0.f;
+  // vectors written before the last grid barrier are read below by bulk copies
+  if (tid == 0) fence_proxy_async_global();
+  int cur = blockIdx.x;
+  if (cur < g.ntasks) {
     TaskDesc td = g.tasks[cur];
-    if (threadIdx.x == 0) {
-      fence_proxy_async();
-      mbar_expect_tx(&mbar[0], TBYTES);
-      bulk_g2s(dbuf[0], tile_ptr<DIM, CODE>(p, td.tile0), TBYTES, &mbar[0]);
-    }
     int k = td.k0;
-    Vec<DIM> xi[NC][ROWS_PER_LANE];
+    int buf = 0;
+    if (tid == 0) issue_tile<DIM, CODE, SK>(p, src, smem, td.tile0, td.I, (td.I + k) % g.nb, 0);
     Vec<DIM> iacc[NC][ROWS_PER_LANE];
-    float ssum[NC], scomp[NC];
+    bool task_start = true;
     while (true) {
-      if (k == td.k0) {
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-#pragma unroll
-          for (int a = 0; a < ROWS_PER_LANE; ++a) {
-            xi[c][a] = src[c].load(td.I * TILE + ROWS_PER_LANE * lane + a);
-#pragma unroll
-            for (int d = 0; d < DIM; ++d) iacc[c][a].c[d] = 0.f;
-          }
-          ssum[c] = 0.f;
-          scomp[c] = 0.f;
-        }
-      }
       const int J = (td.I + k) % g.nb;
       const int tile = td.tile0 + (k - td.k0);
-      // next tile (same task, or the first tile of a new task)
+      const unsigned ph = (ps.parity >> buf) & 1u;
+      if (!mbar_wait(mbar + buf, ph, p.timeout_ns)) {
+        set_error(p.ctrl, E_TIMEOUT);
+        mbar_wait(mbar + buf, ph, p.timeout_ns);  // let our own copies land (bounded)
+        return false;
+      }
+      ps.parity ^= (1u << buf);
+      {
+        Vec<DIM> vi[NC], vj[NC];
+        form<DIM, SK, NC>(src, raw, 0, tid, vi);
+        form<DIM, SK, NC>(src, raw, 1, tid, vj);
+        // rows of block I are stored lane-interleaved: row 4l + a at a * 32 + l
+        const int irow = (tid & (ROWS_PER_LANE - 1)) * 32 + (tid >> 2);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          sts_v<DIM>(posi + c * TILE * DP, irow, vi[c]);
+          sts_v<DIM>(posj + c * TILE * DP, tid, vj[c]);
+        }
+      }
+      __syncthreads();  // raw consumed; posi / posj ready
+      const bool task_end = (k + 1 >= td.k1);
       int ntask = cur, nk = k + 1;
       TaskDesc ntd = td;
-      if (nk >= td.k1) {
-        ntask = grab();
-        if (ntask >= 0) {
+      if (task_end) {
+        ntask = cur + gridDim.x;
+        if (ntask < g.ntasks) {
           ntd = g.tasks[ntask];
           nk = ntd.k0;
         }
       }
-      if (ntask >= 0 && threadIdx.x == 0) {
-        fence_proxy_async();
-        mbar_expect_tx(&mbar[buf ^ 1], TBYTES);
-        bulk_g2s(dbuf[buf ^ 1], tile_ptr<DIM, CODE>(p, ntd.tile0 + (nk - ntd.k0)), TBYTES, &mbar[buf ^ 1]);
+      const bool more = ntask < g.ntasks;
+      if (more && tid == 0)
+        issue_tile<DIM, CODE, SK>(p, src, smem, ntd.tile0 + (nk - ntd.k0), ntd.I, (ntd.I + nk) % g.nb, buf ^ 1);
+
+      if (task_start) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+#pragma unroll
+          for (int a = 0; a < ROWS_PER_LANE; ++a) iacc[c][a] = vzero<DIM>();
+        task_start = false;
       }
-      // column vectors of block J
+      Vec<DIM> xi[NC][ROWS_PER_LANE];
 #pragma unroll
       for (int c = 0; c < NC; ++c)
-        for (int jj = threadIdx.x; jj < TILE; jj += CTA) sts_v<DIM>(posj + c * TILE * DP, jj, src[c].load(J * TILE + jj));
-      __syncthreads();
-      if (!mbar_wait(&mbar[buf], ps.parity[buf], p.timeout_ns)) {
-        set_error(p.ctrl, E_TIMEOUT);
-        // let our own copies land before leaving (bounded)
-        mbar_wait(&mbar[buf], ps.parity[buf], p.timeout_ns);
-        if (ntask >= 0) mbar_wait(&mbar[buf ^ 1], ps.parity[buf ^ 1], p.timeout_ns);
-        return false;
-      }
-      ps.parity[buf] ^= 1u;
-
+#pragma unroll
+        for (int a = 0; a < ROWS_PER_LANE; ++a) xi[c][a] = lds_v<DIM>(posi + c * TILE * DP, a * 32 + lane);
       Vec<DIM> jacc[NC];
       float st[NC];
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         st[c] = 0.f;
-#pragma unroll
-        for (int d = 0; d < DIM; ++d) jacc[c].c[d] = 0.f;
+        jacc[c] = vzero<DIM>();
       }
-      tile_compute<DIM, MODE, NC, CODE>(dbuf[buf], posj, lut2, lutf, lutw, xi, iacc, jacc, st, lane, warp);
+      tile_compute<DIM, MODE, NC, CODE>(smem + (buf ? L::OFF_D1 : L::OFF_D0), posj, lut, xi, iacc, jacc, st, lane, warp);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) kahan_add(ssum[c], scomp[c], st[c]);
       if constexpr (MODE != PM_STRESS) {
 #pragma unroll
         for (int c = 0; c < NC; ++c)
           stv<DIM>(p.part_j + ((size_t)tile * 2 + c) * TILE * DP, warp * 32 + lane, jacc[c]);
       }
-#pragma unroll
-      for (int c = 0; c < NC; ++c) kahan_add(ssum[c], scomp[c], st[c]);
-      __syncthreads();  // dbuf[buf] and posj are free again
-
-      if (nk >= td.k1 || ntask != cur) {
-        // task finished: row partials summed over the 4 warps in fixed order
+      if (task_end) {
         if constexpr (MODE != PM_STRESS) {
-          float* red = reinterpret_cast<float*>(dbuf[buf]);  // [4][NC][TILE][DP]
+          __syncthreads();  // every warp is done with this distance buffer: reuse it for the row partials
+          float* red = reinterpret_cast<float*>(smem + (buf ? L::OFF_D1 : L::OFF_D0));  // [4][NC][TILE][DP]
 #pragma unroll
           for (int c = 0; c < NC; ++c)
 #pragma unroll
@@ -405,96 +620,259 @@ __device__ bool pair_pass(const KParams& p, unsigned char* smem, PairState& ps, 
           __syncthreads();
 #pragma unroll
           for (int c = 0; c < NC; ++c) {
-            const int row = threadIdx.x;  // CTA == TILE
-            Vec<DIM> s = lds_v<DIM>(red + ((size_t)(0 * NC + c) * TILE) * DP, row);
+            Vec<DIM> s = lds_v<DIM>(red + ((size_t)(0 * NC + c) * TILE) * DP, tid);
 #pragma unroll
             for (int w = 1; w < 4; ++w) {
-              Vec<DIM> v = lds_v<DIM>(red + ((size_t)(w * NC + c) * TILE) * DP, row);
+              const Vec<DIM> v = lds_v<DIM>(red + ((size_t)(w * NC + c) * TILE) * DP, tid);
 #pragma unroll
               for (int d = 0; d < DIM; ++d) s.c[d] += v.c[d];
             }
-            stv<DIM>(p.part_i + ((size_t)cur * 2 + c) * TILE * DP, row, s);
+            stv<DIM>(p.part_i + ((size_t)cur * 2 + c) * TILE * DP, tid, s);
           }
         }
-        if constexpr (MODE == PM_STRESS || MODE == PM_RHS) {
-#pragma unroll
-          for (int c = 0; c < NC; ++c) {
-            double tot = cta_sum_f64((double)ssum[c] - (double)scomp[c], red64);
-            if (threadIdx.x == 0) __stcg(p.sc_task + (size_t)cur * 2 + c, tot);
-          }
-        }
-        __syncthreads();
+        task_start = true;
       }
-      if (ntask < 0) break;
-      if (ntask != cur) {
-        cur = ntask;
-        td = ntd;
-      }
+      __syncthreads();
+      if (!more) break;
+      cur = ntask;
+      td = ntd;
       k = nk;
       buf ^= 1;
     }
   }
-  ps.ticket_base += (unsigned long long)g.ntasks + gridDim.x;
-  return ok;
+  // stress of this CTA's pairs (candidates 0 and 1), one FP64 slot per CTA
+  if constexpr (MODE == PM_STRESS || MODE == PM_RHS) {
+    df v[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) v[c] = df_add(df_of(ssum[c]), df_of(-scomp[c]));
+    cta_sum_multi<NC>(v, red64);
+    if (tid == 0) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) df_st(p.sc_cta + (size_t)blockIdx.x * 2 + c, v[c]);
+    }
+  }
+  ps.pass += 1;
+  return true;
+}
+
+// Runs an epilogue on every row block, one CTA per block, after a pass.
+template <class Epi>
+__device__ __forceinline__ void rowblock_phase(const KParams& p, Epi& epi, int parity, float2* red64) {
+  for (int R = blockIdx.x; R < p.g.nb; R += gridDim.x) epi(R, parity, red64);
 }
 
 // --------------------------------------------------------------------------
-// Row-block reduction of the partial buffers: thread t gets row R*TILE + t.
+// Epilogues (run once per row block, one CTA per block, after a pass)
 // --------------------------------------------------------------------------
 
-template <int DIM, int NC>
-__device__ __forceinline__ void reduce_rows(const KParams& p, int R, Vec<DIM> (&out)[NC]) {
-  constexpr int DP = DimP<DIM>::v;
-  const Geometry& g = p.g;
-  const int row = threadIdx.x;
-  Vec<DIM> s[NC], cmp[NC];
+// b = L^{X} X of the initial layout (right-hand side of Eq. (2-5)).
+template <int DIM>
+struct EpiRhs0 {
+  const KParams& p;
+  __device__ __forceinline__ void operator()(int R, int, float2*) {
+    Vec<DIM> acc[1];
+    reduce_rows<DIM, 1>(p, R, acc);
+    stv<DIM>(p.B, R * TILE + threadIdx.x, acc[0]);
+  }
+};
+
+// F = (L^X - L^W) X written to the caller's [n][dim] array.
+template <int DIM>
+struct EpiForces {
+  const KParams& p;
+  __device__ __forceinline__ void operator()(int R, int, float2*) {
+    Vec<DIM> acc[1];
+    reduce_rows<DIM, 1>(p, R, acc);
+    const int i = R * TILE + threadIdx.x;
+    if (i < p.g.n) {
 #pragma unroll
-  for (int c = 0; c < NC; ++c)
+      for (int d = 0; d < DIM; ++d) p.x_out[(size_t)i * DIM + d] = acc[0].c[d];
+    }
+  }
+};
+
+struct EpiNone {
+  __device__ void operator()(int, int, float2*) {}
+};
+
+// Start of an H step (Eq. (2-5)): take the layout x0 chosen by the previous
+// acceptance test (or X^0), r0 = b - L^W x0, u0 = M^-1 r0, clear p and s;
+// displacement sums of x0 against the previous layout.
+// Scalar slots: [0,D) r.u  [D,2D) r.r  [2D,3D) b.b  [3D,4D) sum dx  [4D,5D) sum dx^2
+//               [5D,6D) sum x  [6D,7D) sum x^2
+template <int DIM>
+struct EpiInit {
+  const KParams& p;
+  const float* x0src;
+  bool first, accept;
+  __device__ __forceinline__ void operator()(int R, int parity, float2* red64) {
+    Vec<DIM> acc[1];
+    reduce_rows<DIM, 1>(p, R, acc);
+    const int i = R * TILE + threadIdx.x;
+    const bool real = i < p.g.n;
+    const Vec<DIM> x0 = ldv<DIM>(x0src, i), xo = ldv<DIM>(p.X, i);
+    const Vec<DIM> b = first ? ldv<DIM>(p.B, i) : (accept ? ldv<DIM>(p.Bt, i) : ldv<DIM>(p.Bz, i));
+    const float s = __ldcg(p.s + i), is = __ldcg(p.inv_s + i);
+    Vec<DIM> r, u;
+    df v[7 * DIM];
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
-      s[c].c[d] = 0.f;
-      cmp[c].c[d] = 0.f;
+      r.c[d] = b.c[d] - fmaf(s, x0.c[d], acc[0].c[d]);
+      u.c[d] = is * r.c[d];
+      const df dx = real ? df_diff(x0.c[d], xo.c[d]) : df_of(0.f);
+      const float xv = real ? x0.c[d] : 0.f;
+      v[d] = df_prod(r.c[d], u.c[d]);
+      v[DIM + d] = df_prod(r.c[d], r.c[d]);
+      v[2 * DIM + d] = df_prod(b.c[d], b.c[d]);
+      v[3 * DIM + d] = dx;
+      v[4 * DIM + d] = df_sqr(dx);
+      v[5 * DIM + d] = df_of(xv);
+      v[6 * DIM + d] = df_prod(xv, xv);
     }
-  const int t0 = g.strip_task_base[R], t1 = g.strip_task_base[R + 1];
-  for (int t = t0; t < t1; ++t) {
+    stv<DIM>(p.Zw, i, x0);
+    stv<DIM>(p.X, i, x0);
+    stv<DIM>(p.B, i, b);
+    stv<DIM>(p.R, i, r);
+    stv<DIM>(p.U, i, u);
+    stv<DIM>(p.P, i, vzero<DIM>());
+    stv<DIM>(p.S, i, vzero<DIM>());
+    cta_sum_multi<7 * DIM>(v, red64);
+    if (threadIdx.x == 0) {
+      float2* o = scal(p, parity) + (size_t)R * SC_STRIDE;
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      Vec<DIM> v = ldv<DIM>(p.part_i + ((size_t)t * 2 + c) * TILE * DP, row);
-#pragma unroll
-      for (int d = 0; d < DIM; ++d) kahan_add(s[c].c[d], cmp[c].c[d], v.c[d]);
+      for (int k = 0; k < 7 * DIM; ++k) df_st(o + k, v[k]);
     }
   }
-  for (int I = 0; I < g.nb; ++I) {
-    int k = R - I;
-    if (k < 0) k += g.nb;
-    if (k >= g.strip_len[I]) continue;
-    const int tile = g.tile_base[I] + k;
+};
+
+// w0 = L^W u0 and delta0 = (w0, u0).  Slots [0,D).
+template <int DIM>
+struct EpiAU0 {
+  const KParams& p;
+  __device__ __forceinline__ void operator()(int R, int parity, float2* red64) {
+    Vec<DIM> acc[1];
+    reduce_rows<DIM, 1>(p, R, acc);
+    const int i = R * TILE + threadIdx.x;
+    const float s = __ldcg(p.s + i);
+    const Vec<DIM> u = ldv<DIM>(p.U, i);
+    Vec<DIM> w;
+    df v[DIM];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      Vec<DIM> v = ldv<DIM>(p.part_j + ((size_t)tile * 2 + c) * TILE * DP, row);
+    for (int d = 0; d < DIM; ++d) {
+      w.c[d] = fmaf(s, u.c[d], acc[0].c[d]);
+      v[d] = df_prod(w.c[d], u.c[d]);
+    }
+    stv<DIM>(p.W, i, w);
+    cta_sum_multi<DIM>(v, red64);
+    if (threadIdx.x == 0) {
+      float2* o = scal(p, parity) + (size_t)R * SC_STRIDE;
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) kahan_add(s[c].c[d], cmp[c].c[d], v.c[d]);
+      for (int k = 0; k < DIM; ++k) df_st(o + k, v[k]);
     }
   }
+};
+
+// One step of preconditioned CG in the single-reduction form of Chronopoulos
+// and Gear: p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s,
+// u = M^-1 r, w = L^W u.  The curvature (p', L^W p') of the next direction
+// p' = u + beta' p is needed before beta' is known; it is expanded as
+// (u,w) + beta' ((u,s) + (p,w)) + beta'^2 (p,s) from dot products taken here,
+// instead of the usual recurrence, which loses positivity in FP32.
+// Slots: [0,D) r.u  [D,2D) w.u  [2D,3D) r.r  [3D,4D) u.s  [4D,5D) p.w  [5D,6D) p.s
+template <int DIM>
+struct EpiCG {
+  const KParams& p;
+  float alpha[3], beta[3];
+  __device__ __forceinline__ void operator()(int R, int parity, float2* red64) {
+    Vec<DIM> acc[1];
+    reduce_rows<DIM, 1>(p, R, acc);
+    const int i = R * TILE + threadIdx.x;
+    const float s = __ldcg(p.s + i), is = __ldcg(p.inv_s + i);
+    Vec<DIM> u = ldv<DIM>(p.U, i), w = ldv<DIM>(p.W, i), pp = ldv<DIM>(p.P, i), sp = ldv<DIM>(p.S, i);
+    Vec<DIM> x = ldv<DIM>(p.Zw, i), r = ldv<DIM>(p.R, i);
+    df v[6 * DIM];
 #pragma unroll
-  for (int c = 0; c < NC; ++c)
+    for (int d = 0; d < DIM; ++d) {
+      const float pn = fmaf(beta[d], pp.c[d], u.c[d]);
+      const float sn = fmaf(beta[d], sp.c[d], w.c[d]);
+      const float un = cg_u(r.c[d], w.c[d], sp.c[d], is, alpha[d], beta[d]);
+      x.c[d] = fmaf(alpha[d], pn, x.c[d]);
+      r.c[d] = fmaf(-alpha[d], sn, r.c[d]);
+      pp.c[d] = pn;
+      sp.c[d] = sn;
+      u.c[d] = un;
+      w.c[d] = fmaf(s, un, acc[0].c[d]);
+      v[d] = df_prod(r.c[d], un);
+      v[DIM + d] = df_prod(w.c[d], un);
+      v[2 * DIM + d] = df_prod(r.c[d], r.c[d]);
+      v[3 * DIM + d] = df_prod(un, sn);
+      v[4 * DIM + d] = df_prod(pn, w.c[d]);
+      v[5 * DIM + d] = df_prod(pn, sn);
+    }
+    stv<DIM>(p.P, i, pp);
+    stv<DIM>(p.S, i, sp);
+    stv<DIM>(p.Zw, i, x);
+    stv<DIM>(p.R, i, r);
+    stv<DIM>(p.U, i, u);
+    stv<DIM>(p.W, i, w);
+    cta_sum_multi<6 * DIM>(v, red64);
+    if (threadIdx.x == 0) {
+      float2* o = scal(p, parity) + (size_t)R * SC_STRIDE;
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) out[c].c[d] = s[c].c[d] - cmp[c].c[d];
-}
+      for (int k = 0; k < 6 * DIM; ++k) df_st(o + k, v[k]);
+    }
+  }
+};
+
+// After the stress/RHS pass of the two candidates: store X^{k+1} (pinned),
+// the extrapolation X~ of Eq. (10) and both right-hand sides.
+template <int DIM, int NC>
+struct EpiK2 {
+  const KParams& p;
+  float z0[3];
+  float om;
+  __device__ __forceinline__ void operator()(int R, int, float2*) {
+    Vec<DIM> acc[NC];
+    reduce_rows<DIM, NC>(p, R, acc);
+    const int i = R * TILE + threadIdx.x;
+    const bool real = i < p.g.n;
+    const Vec<DIM> zw = ldv<DIM>(p.Zw, i), x = ldv<DIM>(p.X, i);
+    Vec<DIM> z, xt;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      z.c[d] = real ? zw.c[d] - z0[d] : 0.f;
+      xt.c[d] = real ? sor_xt(z.c[d], x.c[d], om) : 0.f;
+    }
+    stv<DIM>(p.Z, i, z);
+    stv<DIM>(p.Xt, i, xt);
+    stv<DIM>(p.Bz, i, acc[0]);
+    stv<DIM>(p.Bt, i, acc[NC - 1]);
+  }
+};
 
 // --------------------------------------------------------------------------
 // The kernel
 // --------------------------------------------------------------------------
 
+__device__ __forceinline__ PassSrc direct_src(const float* a) {
+  PassSrc s;
+  s.a[0] = a;
+  s.a[1] = s.a[2] = s.a[3] = nullptr;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) s.alpha[d] = s.beta[d] = s.z0[d] = 0.f;
+  s.om = 0.f;
+  return s;
+}
+
 template <int DIM, int CODE>
-__global__ void __launch_bounds__(CTA) fd_main_kernel(KParams p) {
+__global__ void __launch_bounds__(CTA, (DIM == 3) ? 2 : 3) fd_main_kernel(KParams p) {
   using L = SmemLayout<DIM, CODE>;
-  extern __shared__ __align__(128) unsigned char smem[];
+  extern __shared__ __align__(256) unsigned char smem[];
   const Geometry& g = p.g;
   const int n = g.n, nb = g.nb, tid = threadIdx.x;
-  double* red64 = reinterpret_cast<double*>(smem + L::OFF_RED64);
+  float2* red64 = reinterpret_cast<float2*>(smem + L::OFF_RED64);
 
-  // --- set-up: mbarriers and lookup tables in shared memory
+  // --- set-up: mbarriers and the replicated lookup table
   {
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L::OFF_MISC);
     if (tid == 0) {
@@ -502,24 +880,26 @@ __global__ void __launch_bounds__(CTA) fd_main_kernel(KParams p) {
       mbar_init(&mbar[1], 1);
       fence_mbar_init();
     }
-    float2* lut2 = reinterpret_cast<float2*>(smem + L::OFF_LUT2);
-    float2* lutf = reinterpret_cast<float2*>(smem + L::OFF_LUTF);
-    float* lutw = reinterpret_cast<float*>(smem + L::OFF_LUTW);
-    for (int i = tid; i < LUT_N; i += CTA) {
-      float4 e = p.lut[i];
-      lut2[i] = make_float2(e.x, e.z);
-      lutf[i] = make_float2(e.x, e.y);
-      lutw[i] = e.y;
+    if constexpr (CODE == CODE_U8) {
+      uint4* dst = reinterpret_cast<uint4*>(smem + L::OFF_LUT);
+      const uint4* srcl = reinterpret_cast<const uint4*>(p.lut);
+      for (int k = tid; k < p.lut_rows * 16; k += CTA) dst[k] = srcl[k];
     }
     __syncthreads();
   }
   PairState ps;
-  ps.ticket_base = 0;
-  ps.parity[0] = ps.parity[1] = 0;
+  ps.parity = 0u;
+  ps.pass = 0;
   int nbar = 0;
-#define FD_SYNC()                                              \
-  do {                                                         \
-    if (!grid_sync(p.ctrl, p.timeout_ns, ++nbar)) return;      \
+  if (p.timeline && blockIdx.x == 0 && tid == 0) p.ctrl->t_start = globaltimer_ns();
+#define FD_SYNC_TAG(tag)                                                                  \
+  do {                                                                                    \
+    if (!grid_sync(p.ctrl, p.timeout_ns, ++nbar)) return;                                 \
+    if (p.timeline && blockIdx.x == 0 && tid == 0 && p.ctrl->timeline_n < p.timeline_cap) { \
+      const int q = p.ctrl->timeline_n++;                                                 \
+      p.timeline[2 * q] = (double)(tag);                                                  \
+      p.timeline[2 * q + 1] = (double)(globaltimer_ns() - p.ctrl->t_start);               \
+    }                                                                                     \
   } while (0)
 
   // --- pack the caller layout into the padded internal array, check it
@@ -536,18 +916,17 @@ __global__ void __launch_bounds__(CTA) fd_main_kernel(KParams p) {
     if (bad) set_error(p.ctrl, E_NONFINITE);
     stv<DIM>(p.X, i, v);
   }
-  FD_SYNC();
+  FD_SYNC_TAG(1);
 
   if (p.mode == KM_ENERGY) {
-    Src<DIM> s1[1] = {make_src<DIM>(p.X)};
-    if (!pair_pass<DIM, PM_STRESS, 1, CODE>(p, smem, ps, s1)) return;
-    FD_SYNC();
+    if (!pair_pass<DIM, PM_STRESS, 1, CODE, SK_DIRECT>(p, smem, ps, direct_src(p.X))) return;
+    FD_SYNC_TAG(2);
     if (blockIdx.x == 0) {
-      double f = sum_strided_f64(p.sc_task, g.ntasks, 2, 0, red64);
+      const double f = sum_ctas(p.sc_cta, 0, red64);
       if (tid == 0) {
         p.ctrl->f_final = f;
-        p.ctrl->pair_passes += 1.0;
-        p.ctrl->stress_passes += 1.0;
+        p.ctrl->pair_passes = 1.0;
+        p.ctrl->stress_passes = 1.0;
         if (!isfinite(f)) set_error(p.ctrl, E_NONFINITE);
       }
     }
@@ -555,333 +934,216 @@ __global__ void __launch_bounds__(CTA) fd_main_kernel(KParams p) {
   }
 
   if (p.mode == KM_FORCES) {
-    Src<DIM> s1[1] = {make_src<DIM>(p.X)};
-    if (!pair_pass<DIM, PM_FORCES, 1, CODE>(p, smem, ps, s1)) return;
-    FD_SYNC();
-    for (int R = blockIdx.x; R < nb; R += gridDim.x) {
-      Vec<DIM> acc[1];
-      reduce_rows<DIM, 1>(p, R, acc);
-      const int i = R * TILE + tid;
-      if (i < n) {
-#pragma unroll
-        for (int d = 0; d < DIM; ++d) p.x_out[(size_t)i * DIM + d] = acc[0].c[d];
-      }
-    }
+    EpiForces<DIM> e{p};
+    if (!pair_pass<DIM, PM_FORCES, 1, CODE, SK_DIRECT>(p, smem, ps, direct_src(p.X))) return;
+    FD_SYNC_TAG(3);
+    rowblock_phase(p, e, 0, red64);
     if (blockIdx.x == 0 && tid == 0) {
-      p.ctrl->pair_passes += 1.0;
-      p.ctrl->stress_passes += 1.0;
+      p.ctrl->pair_passes = 1.0;
+      p.ctrl->stress_passes = 1.0;
     }
     return;
   }
 
   // ======================= KM_RUN: Algorithm 2 ============================
-  // b = L^{X^0} X^0 and f(X^0) (Eq. (2-5) right-hand side, Eq. (1))
+  // b = L^{X^0} X^0 and f(X^0) (right-hand side of Eq. (2-5), Eq. (1))
+  if (!pair_pass<DIM, PM_RHS, 1, CODE, SK_DIRECT>(p, smem, ps, direct_src(p.X))) return;
+  FD_SYNC_TAG(4);
   {
-    Src<DIM> s1[1] = {make_src<DIM>(p.X)};
-    if (!pair_pass<DIM, PM_RHS, 1, CODE>(p, smem, ps, s1)) return;
+    EpiRhs0<DIM> e{p};
+    rowblock_phase(p, e, 0, red64);
   }
-  FD_SYNC();
-  double f_cur = sum_strided_f64(p.sc_task, g.ntasks, 2, 0, red64);
+  double f_cur = sum_ctas(p.sc_cta, 0, red64);
   if (!isfinite(f_cur)) {
     set_error(p.ctrl, E_NONFINITE);
     return;
   }
-  for (int R = blockIdx.x; R < nb; R += gridDim.x) {
-    Vec<DIM> acc[1];
-    reduce_rows<DIM, 1>(p, R, acc);
-    const int i = R * TILE + tid;
-    stv<DIM>(p.B, i, acc[0]);
-    stv<DIM>(p.Zw, i, ldv<DIM>(p.X, i));  // warm start of the first solve
-  }
-  if (blockIdx.x == 0 && tid == 0) {
-    p.trace_f[0] = f_cur;
-    p.ctrl->pair_passes += 1.0;
-    p.ctrl->stress_passes += 1.0;
-  }
-  FD_SYNC();
+  if (blockIdx.x == 0 && tid == 0) p.trace_f[0] = f_cur;
 
-  int cg_total = 0, cg_maxed = 0, n_acc = 0;
+  double passes_mv = 0.0, passes_st = 1.0;
+  int cg_total = 0, cg_maxed = 0, cg_stalled = 0, n_acc = 0;
   double crit = 0.0;
+  bool accept = true;
+  double f_new = f_cur;
   int it_outer = 0;
-  for (; it_outer < p.max_iter;) {
-    // ---------------- H step: CG on L^W Z = b (Eq. (2-5)) ----------------
+  const float cgt2 = (float)(p.cg_tol * p.cg_tol);
+  for (int k = 0;; ++k) {
+    // ---- start of the H step; also applies lines 6-8 of the previous iteration
+    float rz[DIM], rr[DIM], bb[DIM];
     {
-      Src<DIM> s1[1] = {make_src<DIM>(p.Zw)};
-      if (!pair_pass<DIM, PM_MATVEC, 1, CODE>(p, smem, ps, s1)) return;
-    }
-    FD_SYNC();
-    // r = b - L^W z, zc = r / s, p = zc
-    for (int R = blockIdx.x; R < nb; R += gridDim.x) {
-      Vec<DIM> acc[1];
-      reduce_rows<DIM, 1>(p, R, acc);
-      const int i = R * TILE + tid;
-      const float s = __ldcg(p.s + i), is = __ldcg(p.inv_s + i);
-      Vec<DIM> z = ldv<DIM>(p.Zw, i), b = ldv<DIM>(p.B, i), r, zc;
-      double prz[DIM], prr[DIM], pbb[DIM];
+      const float* x0src = (k == 0) ? p.X : (accept ? p.Xt : p.Z);
+      EpiInit<DIM> e{p, x0src, k == 0, accept};
+      const int par = ps.pass & 1;
+      if (!pair_pass<DIM, PM_MATVEC, 1, CODE, SK_DIRECT>(p, smem, ps, direct_src(x0src))) return;
+      passes_mv += 1.0;
+      FD_SYNC_TAG(5);
+      rowblock_phase(p, e, par, red64);
+      FD_SYNC_TAG(9);
+      df v[7 * DIM];
+      sum_blocks<7 * DIM>(scal(p, par), nb, SC_STRIDE, 0, v, red64);
 #pragma unroll
       for (int d = 0; d < DIM; ++d) {
-        const float q = fmaf(s, z.c[d], acc[0].c[d]);
-        r.c[d] = b.c[d] - q;
-        zc.c[d] = r.c[d] * is;
-        prz[d] = (double)r.c[d] * (double)zc.c[d];
-        prr[d] = (double)r.c[d] * (double)r.c[d];
-        pbb[d] = (double)b.c[d] * (double)b.c[d];
+        rz[d] = df_f(v[d]);
+        rr[d] = df_f(v[DIM + d]);
+        bb[d] = df_f(v[2 * DIM + d]);
       }
-      stv<DIM>(p.R, i, r);
-      stv<DIM>(p.Zc, i, zc);
-      stv<DIM>(p.Pa, i, zc);
+      if (k > 0) {
+        // termination rule after iteration k-1
+        if (p.stop == 0) {
+          double num = 0.0, den = 0.0;
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) {
-        double a1 = cta_sum_f64(prz[d], red64);
-        double a2 = cta_sum_f64(prr[d], red64);
-        double a3 = cta_sum_f64(pbb[d], red64);
-        if (tid == 0) {
-          p.sc_a[R * 8 + d] = a1;
-          p.sc_a[R * 8 + 3 + d] = a2;
-          p.sc_b[R * 8 + d] = a3;
+          for (int d = 0; d < DIM; ++d) {
+            const double s1 = df_to_double(v[3 * DIM + d]), s2 = df_to_double(v[4 * DIM + d]);
+            const double x1 = df_to_double(v[5 * DIM + d]), x2 = df_to_double(v[6 * DIM + d]);
+            num += fmax(s2 - s1 * s1 / n, 0.0);
+            den += fmax(x2 - x1 * x1 / n, 0.0);
+          }
+          crit = (den > 0.0) ? sqrt(num / den) : 0.0;
+        } else {
+          crit = (f_cur != 0.0) ? (f_cur - f_new) / f_cur : 0.0;
         }
+        if (blockIdx.x == 0 && tid == 0) p.trace_crit[k - 1] = crit;
+        f_cur = f_new;
+        it_outer = k;
+        if (crit < p.tol || k >= p.max_iter) break;
       }
     }
-    if (blockIdx.x == 0 && tid == 0) {
-      p.ctrl->pair_passes += 1.0;
-      p.ctrl->matvec_passes += 1.0;
-    }
-    FD_SYNC();
-    double rz[DIM], bb[DIM], beta[DIM];
+    // ---- CG on L^W Z = b, one reduction per step
     bool conv[DIM];
+    bool all = true;
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
-      rz[d] = sum_strided_f64(p.sc_a, nb, 8, d, red64);
-      const double rr = sum_strided_f64(p.sc_a, nb, 8, 3 + d, red64);
-      bb[d] = sum_strided_f64(p.sc_b, nb, 8, d, red64);
-      conv[d] = (rr <= p.cg_tol * p.cg_tol * bb[d]);
-      beta[d] = 0.0;
+      conv[d] = (rr[d] <= cgt2 * bb[d]);
+      all = all && conv[d];
     }
-    float* pold = p.Pa;
-    float* pnew = p.Pb;
     int it = 0;
-    while (true) {
-      bool all = true;
-#pragma unroll
-      for (int d = 0; d < DIM; ++d) all = all && conv[d];
-      if (all) break;
-      if (it >= p.cg_max) {
-        ++cg_maxed;
-        break;
-      }
-      // q = L^W p with p = zc + beta * p_old formed on the fly
+    if (!all) {
+      float alpha[DIM], beta[DIM], gam[DIM];
       {
-        Src<DIM> s1[1];
-        s1[0].a = p.Zc;
-        s1[0].b = pold;
-#pragma unroll
-        for (int d = 0; d < DIM; ++d) s1[0].beta[d] = (float)beta[d];
-        if (!pair_pass<DIM, PM_MATVEC, 1, CODE>(p, smem, ps, s1)) return;
-      }
-      FD_SYNC();
-      for (int R = blockIdx.x; R < nb; R += gridDim.x) {
-        Vec<DIM> acc[1];
-        reduce_rows<DIM, 1>(p, R, acc);
-        const int i = R * TILE + tid;
-        const float s = __ldcg(p.s + i);
-        Vec<DIM> zc = ldv<DIM>(p.Zc, i), po = ldv<DIM>(pold, i), pn, q;
-        double ppq[DIM];
+        EpiAU0<DIM> e{p};
+        const int par = ps.pass & 1;
+        if (!pair_pass<DIM, PM_MATVEC, 1, CODE, SK_DIRECT>(p, smem, ps, direct_src(p.U))) return;
+        passes_mv += 1.0;
+        FD_SYNC_TAG(6);
+        rowblock_phase(p, e, par, red64);
+        FD_SYNC_TAG(9);
+        df dlv[DIM];
+        sum_blocks<DIM>(scal(p, par), nb, SC_STRIDE, 0, dlv, red64);
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
-          pn.c[d] = fmaf((float)beta[d], po.c[d], zc.c[d]);
-          q.c[d] = fmaf(s, pn.c[d], acc[0].c[d]);
-          ppq[d] = (double)pn.c[d] * (double)q.c[d];
-        }
-        stv<DIM>(pnew, i, pn);
-        stv<DIM>(p.Q, i, q);
-#pragma unroll
-        for (int d = 0; d < DIM; ++d) {
-          double a = cta_sum_f64(ppq[d], red64);
-          if (tid == 0) p.sc_b[R * 8 + 3 + d] = a;
-        }
-      }
-      if (blockIdx.x == 0 && tid == 0) {
-      p.ctrl->pair_passes += 1.0;
-      p.ctrl->matvec_passes += 1.0;
-    }
-      FD_SYNC();
-      double alpha[DIM];
-#pragma unroll
-      for (int d = 0; d < DIM; ++d) {
-        const double pq = sum_strided_f64(p.sc_b, nb, 8, 3 + d, red64);
-        if (conv[d]) {
-          alpha[d] = 0.0;
-        } else if (!(pq > 0.0)) {
-          set_error(p.ctrl, E_CG_BREAKDOWN);
-          return;
-        } else {
-          alpha[d] = rz[d] / pq;
-        }
-      }
-      for (int R = blockIdx.x; R < nb; R += gridDim.x) {
-        const int i = R * TILE + tid;
-        const float is = __ldcg(p.inv_s + i);
-        Vec<DIM> z = ldv<DIM>(p.Zw, i), r = ldv<DIM>(p.R, i), pn = ldv<DIM>(pnew, i), q = ldv<DIM>(p.Q, i), zc;
-        double prz[DIM], prr[DIM];
-#pragma unroll
-        for (int d = 0; d < DIM; ++d) {
-          const float a = (float)alpha[d];
-          z.c[d] = fmaf(a, pn.c[d], z.c[d]);
-          r.c[d] = fmaf(-a, q.c[d], r.c[d]);
-          zc.c[d] = r.c[d] * is;
-          prz[d] = (double)r.c[d] * (double)zc.c[d];
-          prr[d] = (double)r.c[d] * (double)r.c[d];
-        }
-        stv<DIM>(p.Zw, i, z);
-        stv<DIM>(p.R, i, r);
-        stv<DIM>(p.Zc, i, zc);
-#pragma unroll
-        for (int d = 0; d < DIM; ++d) {
-          double a1 = cta_sum_f64(prz[d], red64);
-          double a2 = cta_sum_f64(prr[d], red64);
-          if (tid == 0) {
-            p.sc_a[R * 8 + d] = a1;
-            p.sc_a[R * 8 + 3 + d] = a2;
+          const float dl = df_f(dlv[d]);
+          gam[d] = rz[d];
+          beta[d] = 0.f;
+          if (!conv[d] && !(dl > 0.f)) {
+            conv[d] = true;  // u0 carries no curvature: nothing to solve in this column
+            ++cg_stalled;
           }
+          alpha[d] = conv[d] ? 0.f : gam[d] / dl;
         }
       }
-      FD_SYNC();
+      while (true) {
+        PassSrc src = direct_src(p.R);
+        src.a[1] = p.W;
+        src.a[2] = p.S;
+        src.a[3] = p.inv_s;
+        EpiCG<DIM> e{p, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) {
-        const double rzn = sum_strided_f64(p.sc_a, nb, 8, d, red64);
-        const double rr = sum_strided_f64(p.sc_a, nb, 8, 3 + d, red64);
-        if (!conv[d]) {
-          beta[d] = (rz[d] != 0.0) ? rzn / rz[d] : 0.0;
-          conv[d] = (rr <= p.cg_tol * p.cg_tol * bb[d]);
-        } else {
-          beta[d] = 0.0;
+        for (int d = 0; d < DIM; ++d) {
+          src.alpha[d] = e.alpha[d] = alpha[d];
+          src.beta[d] = e.beta[d] = beta[d];
         }
-        rz[d] = rzn;
+        const int par = ps.pass & 1;
+        if (!pair_pass<DIM, PM_MATVEC, 1, CODE, SK_CGU>(p, smem, ps, src)) return;
+        passes_mv += 1.0;
+        ++it;
+        FD_SYNC_TAG(7);
+        rowblock_phase(p, e, par, red64);
+        FD_SYNC_TAG(9);
+        df v[6 * DIM];
+        sum_blocks<6 * DIM>(scal(p, par), nb, SC_STRIDE, 0, v, red64);
+        bool done = true;
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+          const float gn = df_f(v[d]), dn = df_f(v[DIM + d]), rrn = df_f(v[2 * DIM + d]);
+          if (!conv[d]) {
+            conv[d] = (rrn <= cgt2 * bb[d]);
+            if (!conv[d]) {
+              const float bn = gn / gam[d];
+              const float pi = dn + bn * (df_f(v[3 * DIM + d]) + df_f(v[4 * DIM + d])) + bn * bn * df_f(v[5 * DIM + d]);
+              if (pi > 0.f && gn > 0.f) {
+                beta[d] = bn;
+                alpha[d] = gn / pi;
+              } else {
+                conv[d] = true;  // curvature lost to rounding: the solve has gone as far as FP32 allows
+                ++cg_stalled;
+              }
+            }
+            if (conv[d]) {
+              alpha[d] = 0.f;
+              beta[d] = 0.f;
+            }
+          }
+          gam[d] = gn;
+          done = done && conv[d];
+        }
+        if (done) break;
+        if (it >= p.cg_max) {
+          ++cg_maxed;
+          break;
+        }
       }
-      float* t = pold;
-      pold = pnew;
-      pnew = t;
-      ++it;
     }
     cg_total += it;
 
-    // ------------- pin vertex 0 (Sec. 2) and extrapolate (Eq. (10)) -------------
-    const double om = p.omega_seq[it_outer];
-    const float omf = (float)om;
+    // ---- pin vertex 0 (Sec. 2), extrapolate (Eq. (10)), stress and RHS of both
+    const double om = p.omega_seq[k];
+    const bool two = (om != 0.0);
+    PassSrc src = direct_src(p.Zw);
+    src.a[1] = p.X;
     {
       const Vec<DIM> z0 = ldv<DIM>(p.Zw, 0);
-      for (int R = blockIdx.x; R < nb; R += gridDim.x) {
-        const int i = R * TILE + tid;
-        Vec<DIM> z = ldv<DIM>(p.Zw, i), x = ldv<DIM>(p.X, i), zz, xt;
 #pragma unroll
-        for (int d = 0; d < DIM; ++d) {
-          zz.c[d] = (i < n) ? z.c[d] - z0.c[d] : 0.f;
-          xt.c[d] = (i < n) ? fmaf(1.0f + omf, zz.c[d], -omf * x.c[d]) : 0.f;
-        }
-        stv<DIM>(p.Z, i, zz);
-        stv<DIM>(p.Xt, i, xt);
-      }
+      for (int d = 0; d < DIM; ++d) src.z0[d] = z0.c[d];
+      src.om = (float)om;
     }
-    FD_SYNC();
-
-    // ------------- stress and RHS of both candidates (Algorithm 2 lines 4-6) ----
-    const bool two = (om != 0.0);
     if (two) {
-      Src<DIM> s2[2] = {make_src<DIM>(p.Z), make_src<DIM>(p.Xt)};
-      if (!pair_pass<DIM, PM_RHS, 2, CODE>(p, smem, ps, s2)) return;
+      EpiK2<DIM, 2> e{p, {src.z0[0], src.z0[1], src.z0[2]}, src.om};
+      if (!pair_pass<DIM, PM_RHS, 2, CODE, SK_K2>(p, smem, ps, src)) return;
+      passes_st += 2.0;
+      FD_SYNC_TAG(8);
+      rowblock_phase(p, e, 0, red64);
     } else {
-      Src<DIM> s1[1] = {make_src<DIM>(p.Z)};
-      if (!pair_pass<DIM, PM_RHS, 1, CODE>(p, smem, ps, s1)) return;
+      EpiK2<DIM, 1> e{p, {src.z0[0], src.z0[1], src.z0[2]}, src.om};
+      if (!pair_pass<DIM, PM_RHS, 1, CODE, SK_K2>(p, smem, ps, src)) return;
+      passes_st += 1.0;
+      FD_SYNC_TAG(8);
+      rowblock_phase(p, e, 0, red64);
     }
-    FD_SYNC();
-    const double fZ = sum_strided_f64(p.sc_task, g.ntasks, 2, 0, red64);
-    const double fT = two ? sum_strided_f64(p.sc_task, g.ntasks, 2, 1, red64) : fZ;
+    FD_SYNC_TAG(9);  // Z, X~ and their right-hand sides are complete
+    const double fZ = sum_ctas(p.sc_cta, 0, red64);
+    const double fT = two ? sum_ctas(p.sc_cta, 1, red64) : fZ;
     if (!isfinite(fZ) || !isfinite(fT)) {
       set_error(p.ctrl, E_NONFINITE);
       return;
     }
-    const bool accept = (fT <= fZ);  // line 6; ties accept
-    const double f_new = accept ? fT : fZ;
-    // lines 7-8: keep the chosen layout and its RHS; displacement sums
-    for (int R = blockIdx.x; R < nb; R += gridDim.x) {
-      const int i = R * TILE + tid;
-      Vec<DIM> acc[2];
-      if (two) {
-        reduce_rows<DIM, 2>(p, R, acc);
-      } else {
-        Vec<DIM> a1[1];
-        reduce_rows<DIM, 1>(p, R, a1);
-        acc[0] = a1[0];
-        acc[1] = a1[0];
-      }
-      Vec<DIM> xo = ldv<DIM>(p.X, i);
-      Vec<DIM> xn = (accept && two) ? ldv<DIM>(p.Xt, i) : ldv<DIM>(p.Z, i);
-      const Vec<DIM>& bn = (accept && two) ? acc[1] : acc[0];
-      double sd[DIM], sd2[DIM], sx[DIM], sx2[DIM];
-#pragma unroll
-      for (int d = 0; d < DIM; ++d) {
-        const double dlt = (i < n) ? (double)xn.c[d] - (double)xo.c[d] : 0.0;
-        const double xv = (i < n) ? (double)xn.c[d] : 0.0;
-        sd[d] = dlt;
-        sd2[d] = dlt * dlt;
-        sx[d] = xv;
-        sx2[d] = xv * xv;
-      }
-      stv<DIM>(p.X, i, xn);
-      stv<DIM>(p.B, i, bn);
-      stv<DIM>(p.Zw, i, xn);  // warm start of the next solve
-#pragma unroll
-      for (int d = 0; d < DIM; ++d) {
-        double a1 = cta_sum_f64(sd[d], red64);
-        double a2 = cta_sum_f64(sd2[d], red64);
-        double a3 = cta_sum_f64(sx[d], red64);
-        double a4 = cta_sum_f64(sx2[d], red64);
-        if (tid == 0) {
-          p.sc_a[R * 8 + d] = a1;
-          p.sc_a[R * 8 + 3 + d] = a2;
-          p.sc_b[R * 8 + d] = a3;
-          p.sc_b[R * 8 + 3 + d] = a4;
-        }
-      }
-    }
-    FD_SYNC();
-    // termination criterion (same value in every CTA)
-    if (p.stop == 0) {
-      double num = 0.0, den = 0.0;
-#pragma unroll
-      for (int d = 0; d < DIM; ++d) {
-        const double s1 = sum_strided_f64(p.sc_a, nb, 8, d, red64);
-        const double s2 = sum_strided_f64(p.sc_a, nb, 8, 3 + d, red64);
-        const double x1 = sum_strided_f64(p.sc_b, nb, 8, d, red64);
-        const double x2 = sum_strided_f64(p.sc_b, nb, 8, 3 + d, red64);
-        num += fmax(s2 - s1 * s1 / n, 0.0);
-        den += fmax(x2 - x1 * x1 / n, 0.0);
-      }
-      crit = (den > 0.0) ? sqrt(num / den) : 0.0;
-    } else {
-      crit = (f_cur != 0.0) ? (f_cur - f_new) / f_cur : 0.0;
-    }
-    if (accept && two) ++n_acc;
-    else if (!two) ++n_acc;
+    // line 6 (ties accept).  With omega = 0 the two candidates coincide and
+    // X^{k+1} is kept as it is (the test is trivially true).
+    accept = two && (fT <= fZ);
+    f_new = accept ? fT : fZ;
+    if (accept || !two) ++n_acc;
     if (blockIdx.x == 0 && tid == 0) {
-      p.trace_f[it_outer + 1] = f_new;
-      p.trace_acc[it_outer] = accept ? 1 : 0;
-      p.trace_om[it_outer] = om;
-      p.trace_cg[it_outer] = it;
-      p.trace_crit[it_outer] = crit;
-      p.ctrl->pair_passes += two ? 2.0 : 1.0;
-      p.ctrl->stress_passes += two ? 2.0 : 1.0;
+      p.trace_f[k + 1] = f_new;
+      p.trace_acc[k] = (accept || !two) ? 1 : 0;
+      p.trace_om[k] = om;
+      p.trace_cg[k] = it;
     }
-    f_cur = f_new;
-    ++it_outer;
-    if (crit < p.tol) break;
   }
 
-  // --- output
+  // --- output: X holds the layout accepted by the last iteration
   for (int R = blockIdx.x; R < nb; R += gridDim.x) {
     const int i = R * TILE + tid;
     if (i < n) {
-      Vec<DIM> x = ldv<DIM>(p.X, i);
+      const Vec<DIM> x = ldv<DIM>(p.X, i);
 #pragma unroll
       for (int d = 0; d < DIM; ++d) p.x_out[(size_t)i * DIM + d] = x.c[d];
     }
@@ -890,11 +1152,15 @@ __global__ void __launch_bounds__(CTA) fd_main_kernel(KParams p) {
     p.ctrl->iters = it_outer;
     p.ctrl->cg_steps = cg_total;
     p.ctrl->cg_maxed = cg_maxed;
+    p.ctrl->cg_stalled = cg_stalled;
     p.ctrl->accepted = n_acc;
     p.ctrl->f_final = f_cur;
     p.ctrl->crit_final = crit;
+    p.ctrl->pair_passes = passes_mv + passes_st;
+    p.ctrl->matvec_passes = passes_mv;
+    p.ctrl->stress_passes = passes_st;
   }
-#undef FD_SYNC
+#undef FD_SYNC_TAG
 }
 
 }  // namespace fdl

@@ -5,22 +5,24 @@
 namespace fdl {
 
 template <int CODE>
-static cudaError_t config_one(int* blocks_per_sm, size_t* smem) {
+static cudaError_t config_one(size_t lut_bytes, int* blocks_per_sm, size_t* smem) {
   using L = SmemLayout<3, CODE>;
-  *smem = L::BYTES;
+  *smem = L::BASE_BYTES + (CODE == CODE_U8 ? lut_bytes : 0);
   cudaError_t e = cudaFuncSetAttribute(fd_main_kernel<3, CODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)L::BYTES);
+                                       (int)*smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fd_main_kernel<3, CODE>, CTA, L::BYTES);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fd_main_kernel<3, CODE>, CTA, *smem);
 }
 
-cudaError_t main_config_d3(int code, int* blocks_per_sm, size_t* smem) {
-  return code == CODE_U8 ? config_one<CODE_U8>(blocks_per_sm, smem) : config_one<CODE_F32>(blocks_per_sm, smem);
+cudaError_t main_config_d3(int code, size_t lut_bytes, int* blocks_per_sm, size_t* smem) {
+  return code == CODE_U8 ? config_one<CODE_U8>(lut_bytes, blocks_per_sm, smem)
+                         : config_one<CODE_F32>(lut_bytes, blocks_per_sm, smem);
 }
 
 cudaError_t launch_main_d3(int code, const KParams& p, int grid, size_t smem, cudaStream_t st) {
   void* args[] = {const_cast<KParams*>(&p)};
-  const void* fn = (code == CODE_U8) ? (const void*)fd_main_kernel<3, CODE_U8> : (const void*)fd_main_kernel<3, CODE_F32>;
+  const void* fn =
+      (code == CODE_U8) ? (const void*)fd_main_kernel<3, CODE_U8> : (const void*)fd_main_kernel<3, CODE_F32>;
   return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(CTA), args, smem, st);
 }
 

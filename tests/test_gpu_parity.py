@@ -178,3 +178,25 @@ def test_probabilistic_strategy_matches_oracle_sequence():
         r = L.run(X, trace=True, strategy=api.OMEGA_PROB, seed=42, tol=1e-4, max_iter=30)
     k = min(r.iterations, ref.iterations)
     assert np.array_equal(r.omega[:k], np.array(ref.trace_omega[:k]))
+
+
+@pytest.mark.parametrize("ctas", [1, 3, 7])
+def test_many_tasks_per_cta(ctas, monkeypatch):
+    # With few CTAs every CTA walks many tasks and tiles: the prefetch chain,
+    # the task hand-over and the partial sums must not depend on the grid.
+    monkeypatch.setenv("FDLAYOUT_MAX_CTAS", str(ctas))
+    rp, ci = GRAPHS["delaunay1000"]()
+    n = len(rp) - 1
+    D = _dense(rp, ci)
+    X0 = synth.initial_layout(n, 2, seed=8)
+    with api.Layout(rp, ci, dim=2) as L:
+        assert L.info()["grid"] == ctas
+        assert L.energy(X0) == pytest.approx(oracle.stress(X0, D), rel=1e-5)
+        F = L.forces(X0)
+        F_ref = oracle.forces(X0, D)
+        assert np.linalg.norm(F - F_ref) <= 1e-5 * np.linalg.norm(F_ref)
+        X = X0.copy()
+        f, acc, crit = L.sor_step(X, k=0, omega=0.5)
+    Xn, fn, accn, _, _ = oracle.sor_step(X0.astype(np.float64), D, 0.5)
+    assert acc == accn
+    assert np.linalg.norm(X - Xn) <= 1e-4 * np.linalg.norm(Xn)
