@@ -668,7 +668,7 @@ fd_status fd_layout_create(fd_layout** out, int32_t n, int32_t dim, const int32_
   if ((s = dev_alloc(&h->d_part_j, (size_t)h->ntiles * 2 * TILE * h->dimp)) != FD_OK) return bail(s);
   if ((s = dev_alloc(&h->d_part_i, (size_t)h->ntasks * 2 * TILE * h->dimp)) != FD_OK) return bail(s);
   if ((s = dev_alloc(&h->d_sc_task, (size_t)h->grid * 2)) != FD_OK) return bail(s);
-  if ((s = dev_alloc(&h->d_sc, (size_t)2 * h->nb * SC_STRIDE)) != FD_OK) return bail(s);
+  if ((s = dev_alloc(&h->d_sc, (size_t)2 * 4 * h->nb * SC_STRIDE)) != FD_OK) return bail(s);
   if ((s = dev_alloc(&h->d_ctrl, 1)) != FD_OK) return bail(s);
   if ((s = dev_alloc(&h->d_stage_in, (size_t)n * dim)) != FD_OK) return bail(s);
   if ((s = dev_alloc(&h->d_stage_out, (size_t)n * dim)) != FD_OK) return bail(s);
@@ -676,7 +676,7 @@ fd_status fd_layout_create(fd_layout** out, int32_t n, int32_t dim, const int32_
   if ((s = dev_alloc(&h->d_strip_task_base, h->nb + 1)) != FD_OK) return bail(s);
   cudaStream_t st = h->stream;
   if (cudaMemcpyAsync(h->d_lut, lut.data(), lut.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemsetAsync(h->d_sc, 0, (size_t)2 * h->nb * SC_STRIDE * sizeof(double), st) != cudaSuccess ||
+      cudaMemsetAsync(h->d_sc, 0, (size_t)2 * 4 * h->nb * SC_STRIDE * sizeof(double), st) != cudaSuccess ||
       cudaMemcpyAsync(h->d_tasks, h->tasks.data(), h->ntasks * sizeof(TaskDesc), cudaMemcpyHostToDevice, st) !=
           cudaSuccess ||
       cudaMemcpyAsync(h->d_strip_task_base, h->strip_task_base.data(), (h->nb + 1) * sizeof(int),

@@ -67,6 +67,8 @@ struct Ctrl {
   int timeout_where;           // barrier index that timed out (diagnostic)
   int timeline_n;              // timeline entries written
   unsigned long long t_start;  // %globaltimer at kernel start (CTA 0)
+  float2 red[32];              // result of the reduction run by the last CTA at a grid barrier
+  double red_d[4];             // FP64 scalars computed by that CTA (termination criterion)
 };
 
 struct Geometry {
@@ -98,7 +100,7 @@ struct KParams {
   float* part_j;               // [ntiles][2][TILE][DIMP]
   float* part_i;               // [ntasks][2][TILE][DIMP]
   float2* sc_cta;              // [grid][2] stress of each CTA's pairs, per candidate (double-float)
-  float2* sc;                  // [2][nb][SC_STRIDE] row-block scalars (double-float), by pass parity
+  float2* sc;                  // [2][4 nb][SC_STRIDE] scalars per quarter row block (double-float), by pass parity
   Ctrl* ctrl;
   const double* omega_seq;     // [max_iter] omega of each iteration
   double* trace_f;             // [max_iter + 1]

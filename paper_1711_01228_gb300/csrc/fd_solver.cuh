@@ -261,6 +261,83 @@ __device__ __forceinline__ double sum_ctas(const float2* sc, int c, float2* red)
   return df_to_double(v[0]);
 }
 
+// Grid barrier whose last arriving CTA runs `on_last` (all its threads)
+// before it releases the others: reductions over all CTAs' partial sums run
+// once, in a fixed order, instead of in every CTA.  Waits are bounded.
+template <class F>
+__device__ __forceinline__ bool grid_sync_reduce(Ctrl* c, long long timeout_ns, int where, F&& on_last) {
+  __shared__ int s_last, s_ok;
+  __syncthreads();
+  unsigned int g = 0;
+  if (threadIdx.x == 0) {
+    g = *(volatile unsigned int*)&c->bar_gen;
+    __threadfence();
+    const unsigned int arrived = atomicAdd(&c->bar_count, 1u);
+    s_last = (arrived == gridDim.x - 1);
+    if (s_last) __threadfence();
+  }
+  __syncthreads();
+  if (s_last) {
+    on_last();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicExch(&c->bar_count, 0u);
+      __threadfence();
+      atomicAdd(&c->bar_gen, 1u);
+    }
+  } else if (threadIdx.x == 0) {
+    volatile unsigned int* gen = &c->bar_gen;
+    volatile int* err = &c->err;
+    unsigned long long t0 = globaltimer_ns();
+    unsigned int ns = 32;
+    while (*gen == g) {
+      if (*err != 0) break;
+      __nanosleep(ns);
+      if (ns < 256) ns <<= 1;
+      if ((long long)(globaltimer_ns() - t0) > timeout_ns) {
+        atomicCAS(&c->err, 0, (int)E_TIMEOUT);
+        atomicExch(&c->timeout_where, where);
+        break;
+      }
+    }
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_ok = (*(volatile int*)&c->err == 0);
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Run by the last CTA: K consecutive slots of `count` records (stride float2
+// apart) summed in a fixed order into ctrl->red[0..K).
+template <int K>
+__device__ __forceinline__ void reduce_slots_to_ctrl(Ctrl* c, const float2* a, int count, int stride, float2* red) {
+  df t[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) t[k] = df_of(0.f);
+  for (int r = threadIdx.x; r < count; r += CTA) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) t[k] = df_add(t[k], df_ld(a + (size_t)r * stride + k));
+  }
+  cta_sum_multi<K>(t, red);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) __stcg(&c->red[k], make_float2(t[k].hi, t[k].lo));
+  }
+}
+
+// After the barrier: the K reduced values, in every thread.
+template <int K>
+__device__ __forceinline__ void load_red(const Ctrl* c, df (&out)[K]) {
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const float2 v = __ldcg(&c->red[k]);
+    out[k] = {v.x, v.y};
+  }
+}
+
 // --------------------------------------------------------------------------
 // One tile of a pair pass
 // --------------------------------------------------------------------------
@@ -420,17 +497,25 @@ __device__ __forceinline__ void form(const PassSrc& s, const float* raw, int sid
 // Row-block reduction of the partial buffers: thread t gets row R*TILE + t.
 // --------------------------------------------------------------------------
 
-// Sums the partials of row block R (thread t: row R*TILE + t) and leaves
-// the result in shared memory, out[c * TILE * DIM + t * DIM + d].  Out of
-// line, with plain pointer arguments, so that its loads in flight get their
-// own registers.
+// Row-block phase work unit: a quarter (32 rows) of row block R.  The four
+// warps of the CTA take every fourth partial sum of the block's fixed list,
+// for all 32 rows (lane = row), and the four part sums are added in warp
+// order; warp 0 then holds the totals and runs the per-row epilogue.
+constexpr int QROWS = 32;
+
+// Sums the partials of rows R*TILE + 32*qr + lane and leaves the totals in
+// shared memory, out[(c * QROWS + lane) * DIM + d] (valid for warp 0's use).
+// Out of line with plain pointer arguments, so that its loads in flight get
+// their own registers.
 template <int DIM, int NC>
-__device__ __noinline__ void reduce_rows_smem(const float* __restrict__ part_i, const float* __restrict__ part_j,
-                                              const int* __restrict__ contrib_ptr, const int* __restrict__ contrib,
-                                              int R, int* idx, float* out) {
+__device__ __noinline__ void reduce_quarter_smem(const float* __restrict__ part_i, const float* __restrict__ part_j,
+                                                 const int* __restrict__ contrib_ptr,
+                                                 const int* __restrict__ contrib, int R, int qr, int* idx,
+                                                 float* scratch, float* out) {
   constexpr int DP = DimP<DIM>::v;
-  constexpr int Q = 16;  // partials in flight per batch
-  const int row = threadIdx.x;
+  constexpr int Q = 8;  // partials in flight per thread
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int row = QROWS * qr + lane;  // row inside the tile block
   Vec<DIM> s[NC], cmp[NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
@@ -441,14 +526,15 @@ __device__ __noinline__ void reduce_rows_smem(const float* __restrict__ part_i, 
   for (int base = c0; base < c1; base += CTA) {
     const int cnt = min(CTA, c1 - base);
     __syncthreads();
-    if (row < cnt) idx[row] = contrib[base + row];
+    if ((int)threadIdx.x < cnt) idx[threadIdx.x] = contrib[base + threadIdx.x];
     __syncthreads();
-    for (int q0 = 0; q0 < cnt; q0 += Q) {
+    for (int q0 = w; q0 < cnt; q0 += 4 * Q) {
       Vec<DIM> v[Q][NC];
 #pragma unroll
       for (int q = 0; q < Q; ++q) {
-        if (q0 + q < cnt) {
-          const int e = idx[q0 + q];
+        const int k = q0 + 4 * q;
+        if (k < cnt) {
+          const int e = idx[k];
           const float* src = (e >= 0) ? part_i + (size_t)e * 2 * TILE * DP : part_j + (size_t)(-1 - e) * 2 * TILE * DP;
 #pragma unroll
           for (int c = 0; c < NC; ++c) v[q][c] = ldv<DIM>(src + (size_t)c * TILE * DP, row);
@@ -456,7 +542,7 @@ __device__ __noinline__ void reduce_rows_smem(const float* __restrict__ part_i, 
       }
 #pragma unroll
       for (int q = 0; q < Q; ++q)
-        if (q0 + q < cnt) {
+        if (q0 + 4 * q < cnt) {
 #pragma unroll
           for (int c = 0; c < NC; ++c)
 #pragma unroll
@@ -464,26 +550,57 @@ __device__ __noinline__ void reduce_rows_smem(const float* __restrict__ part_i, 
         }
     }
   }
+  // part sums of the four warps, added in warp order
 #pragma unroll
   for (int c = 0; c < NC; ++c)
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) out[(c * TILE + row) * DIM + d] = s[c].c[d] - cmp[c].c[d];
+    for (int d = 0; d < DIM; ++d) scratch[((w * NC + c) * QROWS + lane) * DIM + d] = s[c].c[d] - cmp[c].c[d];
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) {
+        float t = scratch[((0 * NC + c) * QROWS + lane) * DIM + d];
+#pragma unroll
+        for (int ww = 1; ww < 4; ++ww) t += scratch[((ww * NC + c) * QROWS + lane) * DIM + d];
+        out[(c * QROWS + lane) * DIM + d] = t;
+      }
+  }
+  __syncthreads();
 }
 
 template <int DIM, int NC>
-__device__ __forceinline__ void reduce_rows(const KParams& p, int R, Vec<DIM> (&out)[NC]) {
+__device__ __forceinline__ void reduce_rows(const KParams& p, int R, int qr, Vec<DIM> (&out)[NC]) {
   extern __shared__ __align__(256) unsigned char smem_dyn[];
   int* idx = reinterpret_cast<int*>(smem_dyn + SMEM_OFF_IDX);
-  float* res = reinterpret_cast<float*>(smem_dyn + SMEM_OFF_POSI);  // free outside the passes
-  reduce_rows_smem<DIM, NC>(p.part_i, p.part_j, p.g.contrib_ptr, p.g.contrib, R, idx, res);
+  float* scratch = reinterpret_cast<float*>(smem_dyn + SMEM_OFF_POSI);      // free outside the passes
+  float* res = scratch + 4 * 2 * QROWS * 3;
+  reduce_quarter_smem<DIM, NC>(p.part_i, p.part_j, p.g.contrib_ptr, p.g.contrib, R, qr, idx, scratch, res);
+  const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int c = 0; c < NC; ++c)
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) out[c].c[d] = res[(c * TILE + threadIdx.x) * DIM + d];
+    for (int d = 0; d < DIM; ++d) out[c].c[d] = res[(c * QROWS + lane) * DIM + d];
+}
+
+// Warp-level double-float sum (fixed order); the totals land in lane 0.
+template <int K>
+__device__ __forceinline__ void warp_sum_df(df (&v)[K]) {
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      df q;
+      q.hi = __shfl_down_sync(0xffffffffu, v[k].hi, o);
+      q.lo = __shfl_down_sync(0xffffffffu, v[k].lo, o);
+      v[k] = df_add(v[k], q);
+    }
+  }
 }
 
 __device__ __forceinline__ float2* scal(const KParams& p, int parity) {
-  return p.sc + (size_t)parity * p.g.nb * SC_STRIDE;
+  return p.sc + (size_t)parity * 4 * p.g.nb * SC_STRIDE;
 }
 
 // Thread 0 of a CTA: bulk copies (TMA) of a tile's distance codes and of
@@ -655,24 +772,28 @@ __device__ bool pair_pass(const KParams& p, unsigned char* smem, PairState& ps, 
   return true;
 }
 
-// Runs an epilogue on every row block, one CTA per block, after a pass.
+// Runs an epilogue on every quarter row block (32 rows), one CTA per unit, after a pass.
 template <class Epi>
 __device__ __forceinline__ void rowblock_phase(const KParams& p, Epi& epi, int parity, float2* red64) {
-  for (int R = blockIdx.x; R < p.g.nb; R += gridDim.x) epi(R, parity, red64);
+  for (int u = blockIdx.x; u < 4 * p.g.nb; u += gridDim.x) epi(u >> 2, u & 3, parity, red64);
 }
 
 // --------------------------------------------------------------------------
 // Epilogues (run once per row block, one CTA per block, after a pass)
 // --------------------------------------------------------------------------
 
+// Every epilogue below works on the 32 rows R*TILE + 32*qr + lane: the
+// reduction uses the whole CTA, the per-row work runs in warp 0, and scalar
+// partials go to slot (4*R + qr) of the row-block scalar array.
+
 // b = L^{X} X of the initial layout (right-hand side of Eq. (2-5)).
 template <int DIM>
 struct EpiRhs0 {
   const KParams& p;
-  __device__ __forceinline__ void operator()(int R, int, float2*) {
+  __device__ __forceinline__ void operator()(int R, int qr, int, float2*) {
     Vec<DIM> acc[1];
-    reduce_rows<DIM, 1>(p, R, acc);
-    stv<DIM>(p.B, R * TILE + threadIdx.x, acc[0]);
+    reduce_rows<DIM, 1>(p, R, qr, acc);
+    if (threadIdx.x < 32) stv<DIM>(p.B, R * TILE + QROWS * qr + threadIdx.x, acc[0]);
   }
 };
 
@@ -680,20 +801,20 @@ struct EpiRhs0 {
 template <int DIM>
 struct EpiForces {
   const KParams& p;
-  __device__ __forceinline__ void operator()(int R, int, float2*) {
+  __device__ __forceinline__ void operator()(int R, int qr, int, float2*) {
     Vec<DIM> acc[1];
-    reduce_rows<DIM, 1>(p, R, acc);
-    const int i = R * TILE + threadIdx.x;
-    if (i < p.g.n) {
+    reduce_rows<DIM, 1>(p, R, qr, acc);
+    const int i = R * TILE + QROWS * qr + threadIdx.x;
+    if (threadIdx.x < 32 && i < p.g.n) {
 #pragma unroll
       for (int d = 0; d < DIM; ++d) p.x_out[(size_t)i * DIM + d] = acc[0].c[d];
     }
   }
 };
 
-struct EpiNone {
-  __device__ void operator()(int, int, float2*) {}
-};
+__device__ __forceinline__ float2* scal_slot(const KParams& p, int parity, int R, int qr) {
+  return scal(p, parity) + (size_t)(4 * R + qr) * SC_STRIDE;
+}
 
 // Start of an H step (Eq. (2-5)): take the layout x0 chosen by the previous
 // acceptance test (or X^0), r0 = b - L^W x0, u0 = M^-1 r0, clear p and s;
@@ -705,10 +826,11 @@ struct EpiInit {
   const KParams& p;
   const float* x0src;
   bool first, accept;
-  __device__ __forceinline__ void operator()(int R, int parity, float2* red64) {
+  __device__ __forceinline__ void operator()(int R, int qr, int parity, float2*) {
     Vec<DIM> acc[1];
-    reduce_rows<DIM, 1>(p, R, acc);
-    const int i = R * TILE + threadIdx.x;
+    reduce_rows<DIM, 1>(p, R, qr, acc);
+    if (threadIdx.x >= 32) return;
+    const int i = R * TILE + QROWS * qr + threadIdx.x;
     const bool real = i < p.g.n;
     const Vec<DIM> x0 = ldv<DIM>(x0src, i), xo = ldv<DIM>(p.X, i);
     const Vec<DIM> b = first ? ldv<DIM>(p.B, i) : (accept ? ldv<DIM>(p.Bt, i) : ldv<DIM>(p.Bz, i));
@@ -736,9 +858,9 @@ struct EpiInit {
     stv<DIM>(p.U, i, u);
     stv<DIM>(p.P, i, vzero<DIM>());
     stv<DIM>(p.S, i, vzero<DIM>());
-    cta_sum_multi<7 * DIM>(v, red64);
+    warp_sum_df<7 * DIM>(v);
     if (threadIdx.x == 0) {
-      float2* o = scal(p, parity) + (size_t)R * SC_STRIDE;
+      float2* o = scal_slot(p, parity, R, qr);
 #pragma unroll
       for (int k = 0; k < 7 * DIM; ++k) df_st(o + k, v[k]);
     }
@@ -749,10 +871,11 @@ struct EpiInit {
 template <int DIM>
 struct EpiAU0 {
   const KParams& p;
-  __device__ __forceinline__ void operator()(int R, int parity, float2* red64) {
+  __device__ __forceinline__ void operator()(int R, int qr, int parity, float2*) {
     Vec<DIM> acc[1];
-    reduce_rows<DIM, 1>(p, R, acc);
-    const int i = R * TILE + threadIdx.x;
+    reduce_rows<DIM, 1>(p, R, qr, acc);
+    if (threadIdx.x >= 32) return;
+    const int i = R * TILE + QROWS * qr + threadIdx.x;
     const float s = __ldcg(p.s + i);
     const Vec<DIM> u = ldv<DIM>(p.U, i);
     Vec<DIM> w;
@@ -763,9 +886,9 @@ struct EpiAU0 {
       v[d] = df_prod(w.c[d], u.c[d]);
     }
     stv<DIM>(p.W, i, w);
-    cta_sum_multi<DIM>(v, red64);
+    warp_sum_df<DIM>(v);
     if (threadIdx.x == 0) {
-      float2* o = scal(p, parity) + (size_t)R * SC_STRIDE;
+      float2* o = scal_slot(p, parity, R, qr);
 #pragma unroll
       for (int k = 0; k < DIM; ++k) df_st(o + k, v[k]);
     }
@@ -783,10 +906,11 @@ template <int DIM>
 struct EpiCG {
   const KParams& p;
   float alpha[3], beta[3];
-  __device__ __forceinline__ void operator()(int R, int parity, float2* red64) {
+  __device__ __forceinline__ void operator()(int R, int qr, int parity, float2*) {
     Vec<DIM> acc[1];
-    reduce_rows<DIM, 1>(p, R, acc);
-    const int i = R * TILE + threadIdx.x;
+    reduce_rows<DIM, 1>(p, R, qr, acc);
+    if (threadIdx.x >= 32) return;
+    const int i = R * TILE + QROWS * qr + threadIdx.x;
     const float s = __ldcg(p.s + i), is = __ldcg(p.inv_s + i);
     Vec<DIM> u = ldv<DIM>(p.U, i), w = ldv<DIM>(p.W, i), pp = ldv<DIM>(p.P, i), sp = ldv<DIM>(p.S, i);
     Vec<DIM> x = ldv<DIM>(p.Zw, i), r = ldv<DIM>(p.R, i);
@@ -815,9 +939,9 @@ struct EpiCG {
     stv<DIM>(p.R, i, r);
     stv<DIM>(p.U, i, u);
     stv<DIM>(p.W, i, w);
-    cta_sum_multi<6 * DIM>(v, red64);
+    warp_sum_df<6 * DIM>(v);
     if (threadIdx.x == 0) {
-      float2* o = scal(p, parity) + (size_t)R * SC_STRIDE;
+      float2* o = scal_slot(p, parity, R, qr);
 #pragma unroll
       for (int k = 0; k < 6 * DIM; ++k) df_st(o + k, v[k]);
     }
@@ -831,10 +955,11 @@ struct EpiK2 {
   const KParams& p;
   float z0[3];
   float om;
-  __device__ __forceinline__ void operator()(int R, int, float2*) {
+  __device__ __forceinline__ void operator()(int R, int qr, int, float2*) {
     Vec<DIM> acc[NC];
-    reduce_rows<DIM, NC>(p, R, acc);
-    const int i = R * TILE + threadIdx.x;
+    reduce_rows<DIM, NC>(p, R, qr, acc);
+    if (threadIdx.x >= 32) return;
+    const int i = R * TILE + QROWS * qr + threadIdx.x;
     const bool real = i < p.g.n;
     const Vec<DIM> zw = ldv<DIM>(p.Zw, i), x = ldv<DIM>(p.X, i);
     Vec<DIM> z, xt;
@@ -871,6 +996,7 @@ __global__ void __launch_bounds__(CTA, (DIM == 3) ? 2 : 3) fd_main_kernel(KParam
   const Geometry& g = p.g;
   const int n = g.n, nb = g.nb, tid = threadIdx.x;
   float2* red64 = reinterpret_cast<float2*>(smem + L::OFF_RED64);
+  Ctrl* ctrl = p.ctrl;
 
   // --- set-up: mbarriers and the replicated lookup table
   {
@@ -891,16 +1017,29 @@ __global__ void __launch_bounds__(CTA, (DIM == 3) ? 2 : 3) fd_main_kernel(KParam
   ps.parity = 0u;
   ps.pass = 0;
   int nbar = 0;
-  if (p.timeline && blockIdx.x == 0 && tid == 0) p.ctrl->t_start = globaltimer_ns();
-#define FD_SYNC_TAG(tag)                                                                  \
-  do {                                                                                    \
-    if (!grid_sync(p.ctrl, p.timeout_ns, ++nbar)) return;                                 \
-    if (p.timeline && blockIdx.x == 0 && tid == 0 && p.ctrl->timeline_n < p.timeline_cap) { \
-      const int q = p.ctrl->timeline_n++;                                                 \
-      p.timeline[2 * q] = (double)(tag);                                                  \
-      p.timeline[2 * q + 1] = (double)(globaltimer_ns() - p.ctrl->t_start);               \
-    }                                                                                     \
+  if (p.timeline && blockIdx.x == 0 && tid == 0) ctrl->t_start = globaltimer_ns();
+  auto mark = [&](int tag) {
+    if (p.timeline && blockIdx.x == 0 && tid == 0 && ctrl->timeline_n < p.timeline_cap) {
+      const int q = ctrl->timeline_n++;
+      p.timeline[2 * q] = (double)tag;
+      p.timeline[2 * q + 1] = (double)(globaltimer_ns() - ctrl->t_start);
+    }
+  };
+  auto no_reduction = [] {};
+  // grid barrier; the last CTA to arrive runs `red` first (a fixed-order reduction)
+#define FD_SYNC_RED(tag, red)                                                   \
+  do {                                                                          \
+    if (!grid_sync_reduce(ctrl, p.timeout_ns, ++nbar, red)) return;             \
+    mark(tag);                                                                  \
   } while (0)
+#define FD_SYNC(tag) FD_SYNC_RED(tag, no_reduction)
+  // reductions run by the last CTA
+  auto red_stress = [&](int nc) {
+    return [&, nc] {
+      if (nc == 2) reduce_slots_to_ctrl<2>(ctrl, p.sc_cta, gridDim.x, 2, red64);
+      else reduce_slots_to_ctrl<1>(ctrl, p.sc_cta, gridDim.x, 2, red64);
+    };
+  };
 
   // --- pack the caller layout into the padded internal array, check it
   for (int R = blockIdx.x; R < nb; R += gridDim.x) {
@@ -913,22 +1052,22 @@ __global__ void __launch_bounds__(CTA, (DIM == 3) ? 2 : 3) fd_main_kernel(KParam
       if (!isfinite(x)) bad = true;
       v.c[d] = x;
     }
-    if (bad) set_error(p.ctrl, E_NONFINITE);
+    if (bad) set_error(ctrl, E_NONFINITE);
     stv<DIM>(p.X, i, v);
   }
-  FD_SYNC_TAG(1);
+  FD_SYNC(1);
 
   if (p.mode == KM_ENERGY) {
     if (!pair_pass<DIM, PM_STRESS, 1, CODE, SK_DIRECT>(p, smem, ps, direct_src(p.X))) return;
-    FD_SYNC_TAG(2);
-    if (blockIdx.x == 0) {
-      const double f = sum_ctas(p.sc_cta, 0, red64);
-      if (tid == 0) {
-        p.ctrl->f_final = f;
-        p.ctrl->pair_passes = 1.0;
-        p.ctrl->stress_passes = 1.0;
-        if (!isfinite(f)) set_error(p.ctrl, E_NONFINITE);
-      }
+    FD_SYNC_RED(2, red_stress(1));
+    if (blockIdx.x == 0 && tid == 0) {
+      df f[1];
+      load_red<1>(ctrl, f);
+      const double fd = df_to_double(f[0]);
+      ctrl->f_final = fd;
+      ctrl->pair_passes = 1.0;
+      ctrl->stress_passes = 1.0;
+      if (!isfinite(fd)) set_error(ctrl, E_NONFINITE);
     }
     return;
   }
@@ -936,11 +1075,11 @@ __global__ void __launch_bounds__(CTA, (DIM == 3) ? 2 : 3) fd_main_kernel(KParam
   if (p.mode == KM_FORCES) {
     EpiForces<DIM> e{p};
     if (!pair_pass<DIM, PM_FORCES, 1, CODE, SK_DIRECT>(p, smem, ps, direct_src(p.X))) return;
-    FD_SYNC_TAG(3);
+    FD_SYNC(3);
     rowblock_phase(p, e, 0, red64);
     if (blockIdx.x == 0 && tid == 0) {
-      p.ctrl->pair_passes = 1.0;
-      p.ctrl->stress_passes = 1.0;
+      ctrl->pair_passes = 1.0;
+      ctrl->stress_passes = 1.0;
     }
     return;
   }
@@ -948,14 +1087,19 @@ __global__ void __launch_bounds__(CTA, (DIM == 3) ? 2 : 3) fd_main_kernel(KParam
   // ======================= KM_RUN: Algorithm 2 ============================
   // b = L^{X^0} X^0 and f(X^0) (right-hand side of Eq. (2-5), Eq. (1))
   if (!pair_pass<DIM, PM_RHS, 1, CODE, SK_DIRECT>(p, smem, ps, direct_src(p.X))) return;
-  FD_SYNC_TAG(4);
+  FD_SYNC_RED(4, red_stress(1));
   {
     EpiRhs0<DIM> e{p};
     rowblock_phase(p, e, 0, red64);
   }
-  double f_cur = sum_ctas(p.sc_cta, 0, red64);
+  double f_cur;
+  {
+    df f[1];
+    load_red<1>(ctrl, f);
+    f_cur = df_to_double(f[0]);
+  }
   if (!isfinite(f_cur)) {
-    set_error(p.ctrl, E_NONFINITE);
+    set_error(ctrl, E_NONFINITE);
     return;
   }
   if (blockIdx.x == 0 && tid == 0) p.trace_f[0] = f_cur;
@@ -967,6 +1111,7 @@ __global__ void __launch_bounds__(CTA, (DIM == 3) ? 2 : 3) fd_main_kernel(KParam
   double f_new = f_cur;
   int it_outer = 0;
   const float cgt2 = (float)(p.cg_tol * p.cg_tol);
+  const int nunits = 4 * nb;
   for (int k = 0;; ++k) {
     // ---- start of the H step; also applies lines 6-8 of the previous iteration
     float rz[DIM], rr[DIM], bb[DIM];
@@ -976,11 +1121,34 @@ __global__ void __launch_bounds__(CTA, (DIM == 3) ? 2 : 3) fd_main_kernel(KParam
       const int par = ps.pass & 1;
       if (!pair_pass<DIM, PM_MATVEC, 1, CODE, SK_DIRECT>(p, smem, ps, direct_src(x0src))) return;
       passes_mv += 1.0;
-      FD_SYNC_TAG(5);
+      FD_SYNC(5);
       rowblock_phase(p, e, par, red64);
-      FD_SYNC_TAG(9);
-      df v[7 * DIM];
-      sum_blocks<7 * DIM>(scal(p, par), nb, SC_STRIDE, 0, v, red64);
+      // reduce the 7*DIM sums; the last CTA also evaluates the termination rule
+      const double fcur_k = f_cur, fnew_k = f_new;
+      auto red_init = [&] {
+        reduce_slots_to_ctrl<7 * DIM>(ctrl, scal(p, par), nunits, SC_STRIDE, red64);
+        if (threadIdx.x == 0) {
+          double c = 0.0;
+          if (p.stop == 0) {
+            double num = 0.0, den = 0.0;
+            for (int d = 0; d < DIM; ++d) {
+              const float2 a1 = ctrl->red[3 * DIM + d], a2 = ctrl->red[4 * DIM + d];
+              const float2 a3 = ctrl->red[5 * DIM + d], a4 = ctrl->red[6 * DIM + d];
+              const double s1 = (double)a1.x + a1.y, s2 = (double)a2.x + a2.y;
+              const double x1 = (double)a3.x + a3.y, x2 = (double)a4.x + a4.y;
+              num += fmax(s2 - s1 * s1 / n, 0.0);
+              den += fmax(x2 - x1 * x1 / n, 0.0);
+            }
+            c = (den > 0.0) ? sqrt(num / den) : 0.0;
+          } else {
+            c = (fcur_k != 0.0) ? (fcur_k - fnew_k) / fcur_k : 0.0;
+          }
+          ctrl->red_d[0] = c;
+        }
+      };
+      FD_SYNC_RED(9, red_init);
+      df v[3 * DIM];
+      load_red<3 * DIM>(ctrl, v);
 #pragma unroll
       for (int d = 0; d < DIM; ++d) {
         rz[d] = df_f(v[d]);
@@ -988,20 +1156,7 @@ __global__ void __launch_bounds__(CTA, (DIM == 3) ? 2 : 3) fd_main_kernel(KParam
         bb[d] = df_f(v[2 * DIM + d]);
       }
       if (k > 0) {
-        // termination rule after iteration k-1
-        if (p.stop == 0) {
-          double num = 0.0, den = 0.0;
-#pragma unroll
-          for (int d = 0; d < DIM; ++d) {
-            const double s1 = df_to_double(v[3 * DIM + d]), s2 = df_to_double(v[4 * DIM + d]);
-            const double x1 = df_to_double(v[5 * DIM + d]), x2 = df_to_double(v[6 * DIM + d]);
-            num += fmax(s2 - s1 * s1 / n, 0.0);
-            den += fmax(x2 - x1 * x1 / n, 0.0);
-          }
-          crit = (den > 0.0) ? sqrt(num / den) : 0.0;
-        } else {
-          crit = (f_cur != 0.0) ? (f_cur - f_new) / f_cur : 0.0;
-        }
+        crit = __ldcg(&ctrl->red_d[0]);
         if (blockIdx.x == 0 && tid == 0) p.trace_crit[k - 1] = crit;
         f_cur = f_new;
         it_outer = k;
@@ -1024,11 +1179,12 @@ __global__ void __launch_bounds__(CTA, (DIM == 3) ? 2 : 3) fd_main_kernel(KParam
         const int par = ps.pass & 1;
         if (!pair_pass<DIM, PM_MATVEC, 1, CODE, SK_DIRECT>(p, smem, ps, direct_src(p.U))) return;
         passes_mv += 1.0;
-        FD_SYNC_TAG(6);
+        FD_SYNC(6);
         rowblock_phase(p, e, par, red64);
-        FD_SYNC_TAG(9);
+        auto red_au0 = [&] { reduce_slots_to_ctrl<DIM>(ctrl, scal(p, par), nunits, SC_STRIDE, red64); };
+        FD_SYNC_RED(9, red_au0);
         df dlv[DIM];
-        sum_blocks<DIM>(scal(p, par), nb, SC_STRIDE, 0, dlv, red64);
+        load_red<DIM>(ctrl, dlv);
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
           const float dl = df_f(dlv[d]);
@@ -1056,11 +1212,12 @@ __global__ void __launch_bounds__(CTA, (DIM == 3) ? 2 : 3) fd_main_kernel(KParam
         if (!pair_pass<DIM, PM_MATVEC, 1, CODE, SK_CGU>(p, smem, ps, src)) return;
         passes_mv += 1.0;
         ++it;
-        FD_SYNC_TAG(7);
+        FD_SYNC(7);
         rowblock_phase(p, e, par, red64);
-        FD_SYNC_TAG(9);
+        auto red_cg = [&] { reduce_slots_to_ctrl<6 * DIM>(ctrl, scal(p, par), nunits, SC_STRIDE, red64); };
+        FD_SYNC_RED(9, red_cg);
         df v[6 * DIM];
-        sum_blocks<6 * DIM>(scal(p, par), nb, SC_STRIDE, 0, v, red64);
+        load_red<6 * DIM>(ctrl, v);
         bool done = true;
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
@@ -1110,20 +1267,22 @@ __global__ void __launch_bounds__(CTA, (DIM == 3) ? 2 : 3) fd_main_kernel(KParam
       EpiK2<DIM, 2> e{p, {src.z0[0], src.z0[1], src.z0[2]}, src.om};
       if (!pair_pass<DIM, PM_RHS, 2, CODE, SK_K2>(p, smem, ps, src)) return;
       passes_st += 2.0;
-      FD_SYNC_TAG(8);
+      FD_SYNC_RED(8, red_stress(2));
       rowblock_phase(p, e, 0, red64);
     } else {
       EpiK2<DIM, 1> e{p, {src.z0[0], src.z0[1], src.z0[2]}, src.om};
       if (!pair_pass<DIM, PM_RHS, 1, CODE, SK_K2>(p, smem, ps, src)) return;
       passes_st += 1.0;
-      FD_SYNC_TAG(8);
+      FD_SYNC_RED(8, red_stress(1));
       rowblock_phase(p, e, 0, red64);
     }
-    FD_SYNC_TAG(9);  // Z, X~ and their right-hand sides are complete
-    const double fZ = sum_ctas(p.sc_cta, 0, red64);
-    const double fT = two ? sum_ctas(p.sc_cta, 1, red64) : fZ;
+    df fz[2];
+    load_red<2>(ctrl, fz);
+    FD_SYNC(9);  // Z, X~ and their right-hand sides are complete
+    const double fZ = df_to_double(fz[0]);
+    const double fT = two ? df_to_double(fz[1]) : fZ;
     if (!isfinite(fZ) || !isfinite(fT)) {
-      set_error(p.ctrl, E_NONFINITE);
+      set_error(ctrl, E_NONFINITE);
       return;
     }
     // line 6 (ties accept).  With omega = 0 the two candidates coincide and
@@ -1149,18 +1308,19 @@ __global__ void __launch_bounds__(CTA, (DIM == 3) ? 2 : 3) fd_main_kernel(KParam
     }
   }
   if (blockIdx.x == 0 && tid == 0) {
-    p.ctrl->iters = it_outer;
-    p.ctrl->cg_steps = cg_total;
-    p.ctrl->cg_maxed = cg_maxed;
-    p.ctrl->cg_stalled = cg_stalled;
-    p.ctrl->accepted = n_acc;
-    p.ctrl->f_final = f_cur;
-    p.ctrl->crit_final = crit;
-    p.ctrl->pair_passes = passes_mv + passes_st;
-    p.ctrl->matvec_passes = passes_mv;
-    p.ctrl->stress_passes = passes_st;
+    ctrl->iters = it_outer;
+    ctrl->cg_steps = cg_total;
+    ctrl->cg_maxed = cg_maxed;
+    ctrl->cg_stalled = cg_stalled;
+    ctrl->accepted = n_acc;
+    ctrl->f_final = f_cur;
+    ctrl->crit_final = crit;
+    ctrl->pair_passes = passes_mv + passes_st;
+    ctrl->matvec_passes = passes_mv;
+    ctrl->stress_passes = passes_st;
   }
-#undef FD_SYNC_TAG
+#undef FD_SYNC
+#undef FD_SYNC_RED
 }
 
 }  // namespace fdl
