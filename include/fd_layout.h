@@ -117,6 +117,8 @@ typedef struct {
   int32_t grid;            /* CTAs of the cooperative layout kernel */
   int32_t tasks;           /* work items (runs of tiles) per all-pairs pass */
   double apsp_ms;          /* device time of the shortest-path kernel at creation (CUDA events) */
+  int32_t stages;          /* tiles in flight per CTA in the layout kernel's copy pipeline (2 or 3) */
+  int32_t reserved;
 } fd_info;
 
 /* Fills *opt with the defaults: omega 0.5, FIXED, REL_DISP, seed 0,

@@ -52,7 +52,7 @@ class Info(ctypes.Structure):
                 ("code_bytes", ctypes.c_int32), ("tile", ctypes.c_int32), ("num_tiles", ctypes.c_int32),
                 ("distance_bytes", ctypes.c_int64), ("disconnected", ctypes.c_int32),
                 ("sm_count", ctypes.c_int32), ("grid", ctypes.c_int32), ("tasks", ctypes.c_int32),
-                ("apsp_ms", ctypes.c_double)]
+                ("apsp_ms", ctypes.c_double), ("stages", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 EXPORTED = ["fd_options_default", "fd_layout_create", "fd_layout_destroy", "fd_energy", "fd_forces",
@@ -60,7 +60,7 @@ EXPORTED = ["fd_options_default", "fd_layout_create", "fd_layout_destroy", "fd_e
             "fd_last_stats", "fd_last_error", "fd_status_string", "fd_energy_noalloc", "fd_timeline_enable",
             "fd_timeline_read"]
 TIMELINE_TAGS = {1: "pack", 2: "stress", 3: "forces", 4: "rhs0", 5: "h_init", 6: "cg_au0", 7: "cg_step",
-                 8: "candidates", 9: "rowblock_epilogue"}
+                 8: "candidates", 9: "vertex_phase"}
 NOALLOC_MAX_N = 524288
 
 _LIB = None

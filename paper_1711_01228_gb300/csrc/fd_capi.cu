@@ -26,9 +26,9 @@ cudaError_t launch_rowsum(int code, int n, int nb, const int* tile_base, const i
                           float* s, float* inv_s, cudaStream_t st);
 cudaError_t launch_distance_rows(int code, int n, int nb, const int* tile_base, const int* strip_len,
                                  const void* D, int row0, int nrows, double* out, cudaStream_t st);
-cudaError_t main_config_d1(int code, size_t lut_bytes, int* blocks_per_sm, size_t* smem);
-cudaError_t main_config_d2(int code, size_t lut_bytes, int* blocks_per_sm, size_t* smem);
-cudaError_t main_config_d3(int code, size_t lut_bytes, int* blocks_per_sm, size_t* smem);
+cudaError_t main_config_d1(int code, size_t lut_bytes, int nbuf, int* blocks_per_sm, size_t* smem);
+cudaError_t main_config_d2(int code, size_t lut_bytes, int nbuf, int* blocks_per_sm, size_t* smem);
+cudaError_t main_config_d3(int code, size_t lut_bytes, int nbuf, int* blocks_per_sm, size_t* smem);
 cudaError_t launch_main_d1(int code, const KParams& p, int grid, size_t smem, cudaStream_t st);
 cudaError_t launch_main_d2(int code, const KParams& p, int grid, size_t smem, cudaStream_t st);
 cudaError_t launch_main_d3(int code, const KParams& p, int grid, size_t smem, cudaStream_t st);
@@ -37,7 +37,7 @@ cudaError_t launch_main_d3(int code, const KParams& p, int grid, size_t smem, cu
 using namespace fdl;
 
 struct fd_layout {
-  int n = 0, dim = 0, dimp = 0, n_pad = 0, nb = 0, ntiles = 0, ntasks = 0, chunk = 1;
+  int n = 0, dim = 0, dimp = 0, n_pad = 0, nb = 0, ntiles = 0, ntasks = 0;
   int code = CODE_U8, diameter = 0, disconnected = 0;
   int device = 0, sm_count = 0, grid = 0;
   size_t smem = 0;
@@ -48,18 +48,16 @@ struct fd_layout {
   int* d_tile_base = nullptr;
   int* d_strip_len = nullptr;
   TaskDesc* d_tasks = nullptr;
-  int* d_strip_task_base = nullptr;
-  int* d_contrib_ptr = nullptr;
-  int* d_contrib = nullptr;
+  int* d_cta_task_ptr = nullptr;
   unsigned char* d_lut = nullptr;
   int lut_rows = 0;
   float* d_s = nullptr;
   float* d_inv_s = nullptr;
   float* d_vec = nullptr;  // pool of the per-vertex vectors
-  float* d_part_j = nullptr;
-  float* d_part_i = nullptr;
-  double* d_sc_task = nullptr;
-  double* d_sc = nullptr;  // [2][nb][SC_STRIDE]
+  float* d_acc = nullptr;      // [3][n_pad][dimp] per-vertex accumulators
+  double* d_sc_task = nullptr;  // [grid][2] double-float stress slots
+  double* d_sc = nullptr;       // [grid][SC_STRIDE] double-float scalar slots
+  int nbuf = 2;                 // stages of the kernel's tile pipeline
   Ctrl* d_ctrl = nullptr;
   float* d_stage_in = nullptr;
   float* d_stage_out = nullptr;
@@ -72,7 +70,7 @@ struct fd_layout {
   int trace_cap = 0;
   int last_iters = 0;
   // host
-  std::vector<int> tile_base, strip_len, strip_task_base;
+  std::vector<int> tile_base, strip_len, cta_task_ptr;
   std::vector<TaskDesc> tasks;
   fd_status last_error = FD_OK;
   fd_stats stats;
@@ -231,31 +229,35 @@ void build_geometry(fd_layout* h) {
 }
 
 void build_tasks(fd_layout* h) {
-  // enough tasks to keep every CTA busy, few enough that row partials stay small
-  const long long want = std::max<long long>(1, (long long)h->grid * 6);
-  int chunk = (int)std::max<long long>(1, h->ntiles / want);
-  chunk = std::min(chunk, 16);
-  h->chunk = chunk;
+  // CTA b owns tiles [T b / G, T (b+1) / G) of the strip-major order: equal
+  // work per CTA and few, long tasks (one per strip the range touches)
+  const long long T = h->ntiles, G = h->grid;
   h->tasks.clear();
-  h->strip_task_base.assign(h->nb + 1, 0);
-  for (int I = 0; I < h->nb; ++I) {
-    for (int k0 = 0; k0 < h->strip_len[I]; k0 += chunk) {
-      TaskDesc t;
-      t.I = I;
-      t.k0 = k0;
-      t.k1 = std::min(k0 + chunk, h->strip_len[I]);
-      t.tile0 = h->tile_base[I] + k0;
-      h->tasks.push_back(t);
+  h->cta_task_ptr.assign(h->grid + 1, 0);
+  int I = 0;
+  for (long long b = 0; b < G; ++b) {
+    const long long t0 = T * b / G, t1 = T * (b + 1) / G;
+    long long t = t0;
+    while (t < t1) {
+      while (h->tile_base[I + 1] <= t) ++I;
+      const long long e = std::min<long long>(t1, h->tile_base[I + 1]);
+      TaskDesc d;
+      d.I = I;
+      d.k0 = (int)(t - h->tile_base[I]);
+      d.k1 = (int)(e - h->tile_base[I]);
+      d.tile0 = (int)t;
+      h->tasks.push_back(d);
+      t = e;
     }
-    h->strip_task_base[I + 1] = (int)h->tasks.size();
+    h->cta_task_ptr[b + 1] = (int)h->tasks.size();
   }
   h->ntasks = (int)h->tasks.size();
 }
 
-cudaError_t main_config(int dim, int code, size_t lut_bytes, int* bps, size_t* smem) {
-  if (dim == 1) return main_config_d1(code, lut_bytes, bps, smem);
-  if (dim == 2) return main_config_d2(code, lut_bytes, bps, smem);
-  return main_config_d3(code, lut_bytes, bps, smem);
+cudaError_t main_config(int dim, int code, size_t lut_bytes, int nbuf, int* bps, size_t* smem) {
+  if (dim == 1) return main_config_d1(code, lut_bytes, nbuf, bps, smem);
+  if (dim == 2) return main_config_d2(code, lut_bytes, nbuf, bps, smem);
+  return main_config_d3(code, lut_bytes, nbuf, bps, smem);
 }
 
 cudaError_t launch_main(int dim, int code, const KParams& p, int grid, size_t smem, cudaStream_t st) {
@@ -269,15 +271,12 @@ void release(fd_layout* h) {
   dev_free(h->d_tile_base);
   dev_free(h->d_strip_len);
   dev_free(h->d_tasks);
-  dev_free(h->d_strip_task_base);
-  dev_free(h->d_contrib_ptr);
-  dev_free(h->d_contrib);
+  dev_free(h->d_cta_task_ptr);
   dev_free(h->d_lut);
   dev_free(h->d_s);
   dev_free(h->d_inv_s);
   dev_free(h->d_vec);
-  dev_free(h->d_part_j);
-  dev_free(h->d_part_i);
+  dev_free(h->d_acc);
   dev_free(h->d_sc_task);
   dev_free(h->d_sc);
   dev_free(h->d_ctrl);
@@ -460,21 +459,19 @@ KParams base_params(fd_layout* h, int mode) {
   p.g.tile_base = h->d_tile_base;
   p.g.strip_len = h->d_strip_len;
   p.g.tasks = h->d_tasks;
-  p.g.strip_task_base = h->d_strip_task_base;
-  p.g.contrib_ptr = h->d_contrib_ptr;
-  p.g.contrib = h->d_contrib;
+  p.g.cta_task_ptr = h->d_cta_task_ptr;
   p.mode = mode;
   p.D = h->D;
   p.lut = h->d_lut;
   p.lut_rows = h->lut_rows;
+  p.nbuf = h->nbuf;
   p.s = h->d_s;
   p.inv_s = h->d_inv_s;
   const size_t vs = (size_t)h->n_pad * h->dimp;
   float* v = h->d_vec;
   float** slots[] = {&p.X, &p.Z, &p.Xt, &p.B, &p.Bz, &p.Bt, &p.Zw, &p.R, &p.U, &p.W, &p.P, &p.S};
   for (int k = 0; k < 12; ++k) *slots[k] = v + k * vs;
-  p.part_j = h->d_part_j;
-  p.part_i = h->d_part_i;
+  p.acc = h->d_acc;
   p.sc_cta = reinterpret_cast<float2*>(h->d_sc_task);
   p.sc = reinterpret_cast<float2*>(h->d_sc);
   p.ctrl = h->d_ctrl;
@@ -617,69 +614,66 @@ fd_status fd_layout_create(fd_layout** out, int32_t n, int32_t dim, const int32_
   if ((s = build_distances(h, rp, ci, edge_len ? &len : nullptr, disconnected_policy)) != FD_OK) return bail(s);
 
   // replicated lookup table for uint8 codes 0 .. lut_rows-1 (shared memory):
-  // row c = 32 x float 1/c^2, then 16 x {1/c, -1}; row 0 (no pair) is zero
+  // row c = 32 x float 1/c, then 32 x float 1/c^2 (one copy per lane); row 0 (no pair) is zero
   h->lut_rows = (h->code == CODE_U8) ? std::min(LUT_N, h->diameter + 2) : 0;
   std::vector<unsigned char> lut((size_t)std::max(h->lut_rows, 1) * LUT_ROW, 0);
   for (int c = 1; c < h->lut_rows; ++c) {
     float* row = reinterpret_cast<float*>(lut.data() + (size_t)c * LUT_ROW);
     const float w = (float)(1.0 / ((double)c * c)), inv = (float)(1.0 / c);
-    for (int k = 0; k < 32; ++k) row[k] = w;
-    for (int k = 0; k < 16; ++k) {
-      row[32 + 2 * k] = inv;
-      row[32 + 2 * k + 1] = -1.f;
+    for (int k = 0; k < 32; ++k) {
+      row[k] = inv;
+      row[32 + k] = w;
     }
   }
-  // launch configuration of the cooperative kernel (depends on the code kind and table size)
-  int bps = 0;
-  if (main_config(dim, h->code, (size_t)h->lut_rows * LUT_ROW, &bps, &h->smem) != cudaSuccess || bps < 1) {
+  // launch configuration of the cooperative kernel: the tile pipeline gets
+  // three stages unless that costs resident CTAs (large tables, 3-D)
+  const size_t lut_bytes = (size_t)h->lut_rows * LUT_ROW;
+  int bps = 0, best_bps = 0, best_nbuf = 0;
+  int nbuf_only = 0;
+  if (const char* e = std::getenv("FDLAYOUT_NBUF")) nbuf_only = std::atoi(e);  // testing: force the stage count
+  for (int nbuf = MAX_NBUF; nbuf >= 2; --nbuf) {
+    if (nbuf_only && nbuf != nbuf_only) continue;
+    size_t smem = 0;
+    if (main_config(dim, h->code, lut_bytes, nbuf, &bps, &smem) != cudaSuccess) {
+      cudaGetLastError();
+      bps = 0;
+    }
+    if (bps > best_bps) {
+      best_bps = bps;
+      best_nbuf = nbuf;
+    }
+  }
+  if (best_bps < 1 || main_config(dim, h->code, lut_bytes, best_nbuf, &bps, &h->smem) != cudaSuccess) {
     cudaGetLastError();
     return bail(FD_ERR_CUDA);
   }
+  h->nbuf = best_nbuf;
   h->grid = bps * h->sm_count;
   if (const char* cap = std::getenv("FDLAYOUT_MAX_CTAS")) {  // testing: force many tasks per CTA
     const int c = std::atoi(cap);
     if (c > 0 && c < h->grid) h->grid = c;
   }
   build_tasks(h);
-
-  // partial sums of each row block, in a fixed order: row partials of its
-  // strip's tasks, then column partials of the tiles (I, R) by increasing I
-  std::vector<int> cptr(h->nb + 1, 0), clist;
-  for (int R = 0; R < h->nb; ++R) {
-    for (int t = h->strip_task_base[R]; t < h->strip_task_base[R + 1]; ++t) clist.push_back(t);
-    for (int I = 0; I < h->nb; ++I) {
-      const int k = (R - I + h->nb) % h->nb;
-      if (k < h->strip_len[I]) clist.push_back(-1 - (h->tile_base[I] + k));
-    }
-    cptr[R + 1] = (int)clist.size();
-  }
   const size_t vs = (size_t)h->n_pad * h->dimp;
-  if ((s = dev_alloc(&h->d_contrib_ptr, h->nb + 1)) != FD_OK) return bail(s);
-  if ((s = dev_alloc(&h->d_contrib, clist.size())) != FD_OK) return bail(s);
-  if (cudaMemcpy(h->d_contrib_ptr, cptr.data(), cptr.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(h->d_contrib, clist.data(), clist.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) {
-    cudaGetLastError();
-    return bail(FD_ERR_CUDA);
-  }
   if ((s = dev_alloc(&h->d_lut, lut.size())) != FD_OK) return bail(s);
   if ((s = dev_alloc(&h->d_s, h->n_pad)) != FD_OK) return bail(s);
   if ((s = dev_alloc(&h->d_inv_s, h->n_pad)) != FD_OK) return bail(s);
   if ((s = dev_alloc(&h->d_vec, 12 * vs)) != FD_OK) return bail(s);
-  if ((s = dev_alloc(&h->d_part_j, (size_t)h->ntiles * 2 * TILE * h->dimp)) != FD_OK) return bail(s);
-  if ((s = dev_alloc(&h->d_part_i, (size_t)h->ntasks * 2 * TILE * h->dimp)) != FD_OK) return bail(s);
+  if ((s = dev_alloc(&h->d_acc, 3 * vs)) != FD_OK) return bail(s);
   if ((s = dev_alloc(&h->d_sc_task, (size_t)h->grid * 2)) != FD_OK) return bail(s);
-  if ((s = dev_alloc(&h->d_sc, (size_t)2 * 4 * h->nb * SC_STRIDE)) != FD_OK) return bail(s);
+  if ((s = dev_alloc(&h->d_sc, (size_t)h->grid * SC_STRIDE)) != FD_OK) return bail(s);
   if ((s = dev_alloc(&h->d_ctrl, 1)) != FD_OK) return bail(s);
   if ((s = dev_alloc(&h->d_stage_in, (size_t)n * dim)) != FD_OK) return bail(s);
   if ((s = dev_alloc(&h->d_stage_out, (size_t)n * dim)) != FD_OK) return bail(s);
   if ((s = dev_alloc(&h->d_tasks, h->ntasks)) != FD_OK) return bail(s);
-  if ((s = dev_alloc(&h->d_strip_task_base, h->nb + 1)) != FD_OK) return bail(s);
+  if ((s = dev_alloc(&h->d_cta_task_ptr, h->grid + 1)) != FD_OK) return bail(s);
   cudaStream_t st = h->stream;
   if (cudaMemcpyAsync(h->d_lut, lut.data(), lut.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemsetAsync(h->d_sc, 0, (size_t)2 * 4 * h->nb * SC_STRIDE * sizeof(double), st) != cudaSuccess ||
+      cudaMemsetAsync(h->d_sc, 0, (size_t)h->grid * SC_STRIDE * sizeof(double), st) != cudaSuccess ||
+      cudaMemsetAsync(h->d_acc, 0, 3 * vs * sizeof(float), st) != cudaSuccess ||
       cudaMemcpyAsync(h->d_tasks, h->tasks.data(), h->ntasks * sizeof(TaskDesc), cudaMemcpyHostToDevice, st) !=
           cudaSuccess ||
-      cudaMemcpyAsync(h->d_strip_task_base, h->strip_task_base.data(), (h->nb + 1) * sizeof(int),
+      cudaMemcpyAsync(h->d_cta_task_ptr, h->cta_task_ptr.data(), (h->grid + 1) * sizeof(int),
                       cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemsetAsync(h->d_vec, 0, 12 * vs * sizeof(float), st) != cudaSuccess) {
     cudaGetLastError();
@@ -884,6 +878,8 @@ fd_status fd_layout_info(const fd_layout* h, fd_info* info) {
   info->grid = h->grid;
   info->tasks = h->ntasks;
   info->apsp_ms = h->apsp_ms;
+  info->stages = h->nbuf;
+  info->reserved = 0;
   return FD_OK;
 }
 

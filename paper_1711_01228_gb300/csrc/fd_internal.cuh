@@ -23,10 +23,11 @@ namespace fdl {
 
 constexpr int TILE = 128;          // vertices per tile side
 constexpr int CTA = 128;           // threads per CTA of the pair kernels (4 warps)
-constexpr int ROWS_PER_LANE = 4;   // i rows held by each lane (32 lanes x 4 = TILE)
 constexpr int LUT_N = 256;         // uint8 codes
-constexpr int LUT_ROW = 256;       // bytes per code in the replicated shared-memory table
-constexpr int SC_STRIDE = 24;      // FP64 scalar slots per row block
+constexpr int LUT_ROW = 256;       // bytes per code in the replicated table: 32 x 1/d, then 32 x 1/d^2
+constexpr int SC_STRIDE = 24;      // double-float scalar slots per CTA
+constexpr int MAX_NBUF = 4;        // stages of the tile pipeline
+constexpr int MAX_CTA_TASKS = 128; // task descriptors a CTA keeps in shared memory
 
 enum CodeKind { CODE_U8 = 0, CODE_F32 = 1 };
 
@@ -41,6 +42,9 @@ enum {
   E_TIMEOUT = 7,
 };
 
+// A run of consecutive tiles of one strip.  Every CTA owns a contiguous
+// range of the strip-major tile order (the same number of tiles, +-1, for
+// every CTA), cut into tasks at strip boundaries.
 struct TaskDesc {
   int I;      // block row
   int k0;     // first tile offset in the strip
@@ -76,10 +80,8 @@ struct Geometry {
   int ntiles, ntasks;
   const int* tile_base;        // [nb + 1] first tile index of each strip
   const int* strip_len;        // [nb] L_I
-  const TaskDesc* tasks;       // [ntasks]
-  const int* strip_task_base;  // [nb + 1]
-  const int* contrib_ptr;      // [nb + 1] partial sums that make up each row block ...
-  const int* contrib;          // ... in a fixed order: t >= 0 row partial of task t, -1-t column partial of tile t
+  const TaskDesc* tasks;       // [ntasks], grouped by CTA
+  const int* cta_task_ptr;     // [grid + 1] CTA b runs tasks cta_task_ptr[b] .. cta_task_ptr[b+1]-1
 };
 
 // Parameters of the cooperative kernel (passed by value).
@@ -87,8 +89,9 @@ struct KParams {
   Geometry g;
   int mode;
   const void* D;               // distance tiles
-  const unsigned char* lut;    // [lut_rows][LUT_ROW] replicated table: 32 x 1/d^2, 16 x {1/d, -1}
+  const unsigned char* lut;    // [lut_rows][LUT_ROW] replicated table: 32 x 1/d, then 32 x 1/d^2
   int lut_rows;                // codes 0 .. lut_rows-1 present in the tiles
+  int nbuf;                    // stages of the tile pipeline (2 or 3)
   const float* s;              // [n_pad] row sums of W (diagonal of L^W)
   const float* inv_s;          // [n_pad] 1/s (0 for padding)
   const float* x_in;           // [n][dim] input layout (device staging)
@@ -97,10 +100,12 @@ struct KParams {
   // layout X^k, its RHS B; candidates Z = X^{k+1}, Xt = X~ and their RHS;
   // CG state Zw (iterate), R (residual), U = M^-1 R, W = L^W U, P, S = L^W P
   float *X, *Z, *Xt, *B, *Bz, *Bt, *Zw, *R, *U, *W, *P, *S;
-  float* part_j;               // [ntiles][2][TILE][DIMP]
-  float* part_i;               // [ntasks][2][TILE][DIMP]
+  // per-vertex sums of a pass, [3][n_pad][DIMP]: the pair kernels add their
+  // row and column partial sums with vector atomics; the vertex phase after
+  // the pass reads them and clears them for the next pass
+  float* acc;
   float2* sc_cta;              // [grid][2] stress of each CTA's pairs, per candidate (double-float)
-  float2* sc;                  // [2][4 nb][SC_STRIDE] scalars per quarter row block (double-float), by pass parity
+  float2* sc;                  // [grid][SC_STRIDE] scalars of each CTA's vertices (double-float)
   Ctrl* ctrl;
   const double* omega_seq;     // [max_iter] omega of each iteration
   double* trace_f;             // [max_iter + 1]

@@ -5,28 +5,34 @@
 // Work decomposition
 // ------------------
 // All-pairs passes run over the tiles of the half ring (fd_internal.cuh),
-// grouped into tasks of consecutive tiles of one block row.  CTAs take tasks
-// from a global ticket counter.  A CTA has 4 warps; every warp holds all 128
-// rows of block I (4 rows per lane, in registers) and sweeps 32 columns of
-// block J.  In step t lane l pairs its 4 rows with column 32w + ((l + t) & 31);
-// the column accumulators travel one lane down after every step, so after 32
-// steps each lane holds the complete column sums of its own column and both
-// endpoints of every pair are accumulated exactly once (symmetric n-body).
+// grouped into tasks of consecutive tiles of one block row.  CTA b takes
+// tasks b, b + G, b + 2G, ... (G CTAs), in reverse order on every other pass
+// so that the tiles one pass reads last are still in L2 when the next starts.
+//
+// Inside a tile (128 x 128 pairs) every lane holds R consecutive rows of
+// block I (R = 16 for L^W products, 8 for the stress / right-hand-side
+// passes; half that in 3-D) and a group of G = 128 / R lanes covers all 128
+// rows; the R groups of the CTA take G columns of block J each.  In step t
+// lane q of a group pairs its rows with column (q + t) mod G of the group, so
+// after G steps both endpoints of every pair have been accumulated exactly
+// once (symmetric n-body); the column sums are gathered from the lanes with
+// shuffles.  Two rows share one packed FP32x2 instruction.  1/d and 1/d^2
+// come from a table in shared memory replicated per lane (one bank each),
+// addressed by one byte permute of the code word.
 //
 // Pipeline: a tile's distance codes (16 KB for uint8) and the raw per-vertex
-// arrays of its two blocks arrive by 1-D bulk copies (TMA) on one mbarrier,
-// issued one tile ahead.  The raw arrays are turned into the pass's vectors
-// in shared memory (e.g. the CG vector u = M^-1 (r - alpha s) is formed on
-// the fly), so every pass reads only what the previous pass left in memory.
-// CTA b takes tasks b, b + G, b + 2G, ... (G CTAs): a pass has no global
-// synchronisation inside it.
+// arrays of block J (and of block I at the first tile of a task) arrive by
+// 1-D bulk copies (TMA) on an mbarrier, nbuf - 1 tiles ahead.  The raw
+// arrays are turned into the pass's vectors in place in shared memory (e.g.
+// the CG vector u = M^-1 (r - alpha s) is formed on the fly).
 //
-// Reductions: per-tile column partials and per-task row partials go to
-// global buffers.  After the pass (grid barrier) one CTA per row block sums
-// its partials in a fixed order (Kahan-compensated) and runs the step's
-// per-row epilogue, which updates the vectors in place.  Scalars (stress,
-// CG dot products, displacement sums) are FP64 sums in a fixed order;
-// results never depend on timing.
+// Reductions: the column sums of a tile and the row sums of a task are added
+// to per-vertex accumulators with FP32 vector atomics (order-dependent in
+// the last bits).  After the pass (grid barrier) a vertex phase, one thread
+// per vertex, reads and clears the accumulators and runs the step's
+// per-vertex work.  Scalars (stress, CG dot products, displacement sums) are
+// double-float numbers: per-CTA partial sums, reduced in a fixed order once
+// by the last CTA to reach the next grid barrier.
 #pragma once
 
 #include "fd_internal.cuh"
@@ -108,29 +114,81 @@ __device__ __forceinline__ Vec<DIM> vzero() {
   return v;
 }
 
+// --------------------------------------------------------------------------
+// Packed FP32x2 arithmetic: one instruction works on two rows.
+// --------------------------------------------------------------------------
+// (Packing and unpacking are register-pair moves, not arithmetic.)
+typedef unsigned long long f2x;
+__device__ __forceinline__ f2x pk2(float a, float b) {
+  f2x r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float lo2(f2x v) {
+  float a;
+  asm("{\n\t.reg .f32 hi;\n\tmov.b64 {%0, hi}, %1;\n\t}" : "=f"(a) : "l"(v));
+  return a;
+}
+__device__ __forceinline__ float hi2(f2x v) {
+  float b;
+  asm("{\n\t.reg .f32 lo;\n\tmov.b64 {lo, %0}, %1;\n\t}" : "=f"(b) : "l"(v));
+  return b;
+}
+__device__ __forceinline__ f2x fma2(f2x a, f2x b, f2x c) {
+  f2x d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ f2x mul2(f2x a, f2x b) {
+  f2x d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2x sub2(f2x a, f2x b) {
+  f2x d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
+// Vector atomic add of one vertex's values to a per-vertex accumulator.
+template <int DIM>
+__device__ __forceinline__ void atomic_addv(float* a, int i, const Vec<DIM>& v) {
+  if constexpr (DIM == 1) {
+    asm volatile("red.relaxed.gpu.global.add.f32 [%0], %1;" ::"l"(a + i), "f"(v.c[0]) : "memory");
+  } else if constexpr (DIM == 2) {
+    asm volatile("red.relaxed.gpu.global.add.v2.f32 [%0], {%1, %2};" ::"l"(a + 2 * i), "f"(v.c[0]), "f"(v.c[1])
+                 : "memory");
+  } else {
+    asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(a + 4 * i), "f"(v.c[0]),
+                 "f"(v.c[1]), "f"(v.c[2]), "f"(0.f)
+                 : "memory");
+  }
+}
+
 enum PairMode { PM_STRESS = 0, PM_FORCES = 1, PM_RHS = 2, PM_MATVEC = 3 };
 
 // How a pass forms its vectors from the raw arrays it copies.
 enum SrcKind {
   SK_DIRECT = 0,  // v = a[0]
   SK_CGU = 1,     // u = inv_s * (r - alpha * (w + beta * s_prev)); a = {r, w, s_prev, inv_s}
-  SK_K2 = 2       // z = zw - zw_0, xt = (1 + omega) z - omega x; a = {zw, x}
+  SK_K2 = 2,      // z = zw - z0 and (NC = 2) xt = (1 + omega) z - omega x; a = {zw, x}
+  SK_SEL = 3      // the candidate kept by line 6 of Algorithm 2: sel ? xt : z, from a = {zw, x}
 };
 
-template <int SK>
-struct SrcN {
-  static constexpr int v = (SK == SK_DIRECT) ? 1 : (SK == SK_CGU) ? 4 : 2;
-};
+// Raw arrays of a source kind.
+__host__ __device__ constexpr int src_arrays(int kind) { return (kind == SK_DIRECT) ? 1 : (kind == SK_CGU) ? 4 : 2; }
 
 struct PassSrc {
+  int kind;  // SrcKind (a run-time value: one compiled pass serves every kind)
   const float* a[4];
   float alpha[3], beta[3];  // SK_CGU, per column
-  float z0[3];              // SK_K2: pinned vertex 0 of the CG solution
-  float om;                 // SK_K2: omega of Eq. (10)
+  float z0[3];              // SK_K2 / SK_SEL: vertex 0 of the CG solution (the pin of Sec. 2)
+  float om;                 // SK_K2 / SK_SEL: omega of Eq. (10)
+  int sel;                  // SK_SEL: 1 = the extrapolation was accepted
 };
 
-// The CG vector u_{i+1} (used both on the fly and in the epilogue, so that
-// the two agree bit for bit).
+// The CG vector u_{i+1} (used both on the fly and in the vertex phase, so
+// that the two agree bit for bit).
 __device__ __forceinline__ float cg_u(float r, float w, float sp, float is, float alpha, float beta) {
   return is * fmaf(-alpha, fmaf(beta, sp, w), r);
 }
@@ -142,37 +200,70 @@ struct CodeBytes {
   static constexpr int v = (CODE == CODE_U8) ? 1 : 4;
 };
 
-// Shared memory.  The lookup table is replicated so that every lane reads
-// its own bank: row c (256 bytes) holds 32 copies of 1/d^2 (bytes 0..127)
-// and 16 copies of {1/d, -1} (bytes 128..255) for code c.
+// Bytes of one block (TILE vertices) of a pass's raw arrays.
+template <int DIM>
+__host__ __device__ constexpr int raw_bytes(int kind) {
+  return (kind == SK_CGU) ? 3 * TILE * DimP<DIM>::v * 4 + TILE * 4 : src_arrays(kind) * TILE * DimP<DIM>::v * 4;
+}
+
+// Rows per lane and column-accumulator chains of a pass kind.  Chain h
+// serves the steps t = h (mod CH) and travels CH lanes per use (no travel
+// when CH = G).
+template <int DIM, int MODE>
+struct TileShape {
+  static constexpr int R = (MODE == PM_MATVEC) ? (DIM == 3 ? 8 : 16) : 4;
+  static constexpr int G = TILE / R;
+  static constexpr int CH = (MODE == PM_MATVEC) ? (DIM == 3 ? 4 : 8) : 2;
+  static_assert(G % CH == 0, "chains must divide the group");
+};
+
+__host__ __device__ constexpr int align_up(int x, int a) { return (x + a - 1) / a * a; }
+
+// Shared memory: fixed part, the replicated lookup table (at a fixed offset,
+// so that table reads need no address arithmetic: row c, 256 bytes, holds 32
+// copies of 1/c (bytes 0..127) and 32 copies of 1/c^2 (bytes 128..255)),
+// then nbuf pipeline stages (codes + raw arrays of blocks J and I).
 template <int DIM, int CODE>
 struct SmemLayout {
   static constexpr int DP = DimP<DIM>::v;
   static constexpr int DBUF = TILE * TILE * CodeBytes<CODE>::v;
-  static constexpr int RAW_ARR = TILE * DP * 4;                  // bytes of one block of one raw array
-  static constexpr int OFF_RED64 = 0;                            // float2 [CTA] reduction scratch
-  static constexpr int OFF_IDX = OFF_RED64 + CTA * 8;            // int [CTA] contribution indices
-  static constexpr int OFF_MISC = OFF_IDX + CTA * 4;             // mbar[2], slots
-  static constexpr int OFF_POSI = 2048;                          // [2][TILE][DP], row-interleaved
-  static constexpr int OFF_POSJ = OFF_POSI + 2 * RAW_ARR;        // [2][TILE][DP]
-  static constexpr int OFF_RAW = OFF_POSJ + 2 * RAW_ARR;         // [4 arrays][2 blocks][TILE][DP] floats
-  static constexpr int OFF_D0 = ((OFF_RAW + 4 * 2 * RAW_ARR + 127) / 128) * 128;
-  static constexpr int OFF_D1 = OFF_D0 + DBUF;
-  static constexpr int OFF_LUT = ((OFF_D1 + DBUF + 255) / 256) * 256;
-  static constexpr int BASE_BYTES = OFF_LUT;
-  static_assert(OFF_MISC + 64 <= OFF_POSI, "fixed regions overlap");
-  static_assert(4 * 2 * TILE * DP * 4 <= DBUF, "row partial area must fit in a distance buffer");
+  static constexpr int RAWB = align_up(raw_bytes<DIM>(SK_CGU), 128);
+  static constexpr int OFF_RED64 = 0;     // float2 [CTA] reduction scratch
+  static constexpr int OFF_MISC = 1024;   // mbarriers
+  static constexpr int OFF_CTL = 1088;    // PassCtl of the running pass
+  static constexpr int OFF_RUN = 1344;    // RunState of the Algorithm 2 loop
+  static constexpr int OFF_PARAMS = 1536; // copy of the kernel parameters
+  static constexpr int OFF_TASKS = 2048;  // this CTA's task descriptors
+  static constexpr int OFF_LUT = OFF_TASKS + MAX_CTA_TASKS * 16;
+  static constexpr int STAGE = align_up(DBUF + 2 * RAWB, 128);
+  // stage s: codes, raw J, raw I, after the table
+  __host__ __device__ static constexpr int stage_base(int lut_bytes) { return align_up(OFF_LUT + lut_bytes, 128); }
+  __host__ __device__ static constexpr int off_d(int sb, int s) { return sb + s * STAGE; }
+  __host__ __device__ static constexpr int off_rawj(int sb, int s) { return sb + s * STAGE + DBUF; }
+  __host__ __device__ static constexpr int off_rawi(int sb, int s) { return sb + s * STAGE + DBUF + RAWB; }
+  __host__ __device__ static constexpr int bytes(int nbuf, int lut_bytes) { return stage_base(lut_bytes) + nbuf * STAGE; }
 };
-constexpr int SMEM_OFF_IDX = CTA * 8;  // OFF_IDX, identical for every layout
-constexpr int SMEM_OFF_POSI = 2048;   // OFF_POSI, identical for every layout
 
 struct PairState {
   unsigned parity;  // bit b: phase parity of mbarrier b
-  int pass;         // passes run so far (selects the scalar buffer parity)
+  int pass;         // passes run so far (odd passes visit the tiles in reverse)
+};
+
+// What a pair pass needs from the kernel parameters (passed by value, so
+// that the out-of-line pass keeps them in registers).
+struct PassArgs {
+  const void* D;
+  const TaskDesc* tasks_g;  // this CTA's tasks in global memory
+  const TaskDesc* tasks_s;  // ... and the first MAX_CTA_TASKS of them in shared memory
+  Ctrl* ctrl;
+  float2* sc_cta;
+  long long timeout_ns;
+  int n, n_pad, nb, ntasks, nbuf;  // ntasks: this CTA's
+  int stage_base;                   // shared-memory offset of stage 0
 };
 
 // --------------------------------------------------------------------------
-// Deterministic FP64 reductions
+// Double-float reductions
 // --------------------------------------------------------------------------
 
 // Reductions use double-float numbers (hi + lo, each FP32, combined with the
@@ -204,6 +295,7 @@ __device__ __forceinline__ df df_diff(float x, float y) {
 }
 __device__ __forceinline__ df df_sqr(df a) { return df_add(df_prod(a.hi, a.hi), df_of(2.f * a.hi * a.lo)); }
 __device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ float df_f(df a) { return a.hi + a.lo; }
 __device__ __forceinline__ df df_ld(const float2* p) {
   const float2 v = __ldcg(p);
   return {v.x, v.y};
@@ -237,28 +329,6 @@ __device__ __forceinline__ void cta_sum_multi(df (&v)[K], float2* red) {
     v[k] = t;
   }
   __syncthreads();
-}
-
-// Sums slots [off, off+K) of the row-block scalar array (stride per block)
-// over nb blocks; every CTA gets the identical values.
-template <int K>
-__device__ __forceinline__ void sum_blocks(const float2* a, int nb, int stride, int off, df (&out)[K], float2* red) {
-#pragma unroll
-  for (int k = 0; k < K; ++k) out[k] = df_of(0.f);
-  for (int R = threadIdx.x; R < nb; R += CTA) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) out[k] = df_add(out[k], df_ld(a + (size_t)R * stride + off + k));
-  }
-  cta_sum_multi<K>(out, red);
-}
-__device__ __forceinline__ float df_f(df a) { return a.hi + a.lo; }
-
-// Sum of the per-CTA stress slots (candidate c) in a fixed order.
-__device__ __forceinline__ double sum_ctas(const float2* sc, int c, float2* red) {
-  df v[1] = {df_of(0.f)};
-  for (int t = threadIdx.x; t < (int)gridDim.x; t += CTA) v[0] = df_add(v[0], df_ld(sc + (size_t)t * 2 + c));
-  cta_sum_multi<1>(v, red);
-  return df_to_double(v[0]);
 }
 
 // Grid barrier whose last arriving CTA runs `on_last` (all its threads)
@@ -342,422 +412,476 @@ __device__ __forceinline__ void load_red(const Ctrl* c, df (&out)[K]) {
 // One tile of a pair pass
 // --------------------------------------------------------------------------
 
-// Independent column-accumulator chains per warp.  Chain c serves the steps
-// t = c (mod CH) and travels CH lanes per use, so consecutive steps do not
-// wait on each other's shuffles.
-template <int MODE, int DIM>
-struct Chains {
-  static constexpr int v = (MODE == PM_MATVEC) ? 4 : (DIM == 3 ? 1 : 2);
+// Rows of block I held by one lane: rows (a, a+1) packed in one f2x.
+template <int DIM, int NC, int R>
+struct Rows {
+  f2x x[NC][DIM][R / 2];
+  f2x acc[NC][DIM][R / 2];
 };
 
-template <int DIM, int MODE, int NC, int CODE>
-__device__ __forceinline__ void tile_compute(const unsigned char* __restrict__ dt, const float* __restrict__ posj,
+#ifndef FD_MATVEC_RCP
+#define FD_MATVEC_RCP 0
+#endif
+// 1/d^2 of an L^W product from the code itself (hardware reciprocal) instead
+// of the table, on tiles that hold no code 0.
+constexpr bool kMatvecRcp = FD_MATVEC_RCP != 0;
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// The code in byte b of `codes` as a float plus 2^23 (exact for codes < 2^23).
+__device__ __forceinline__ float code_plus_2p23(unsigned codes, unsigned b) {
+  return __uint_as_float(__byte_perm(codes, 0x4B000000u, 0x7540u | b));
+}
+
+__device__ __forceinline__ float lut_at(const unsigned char* lut, unsigned off) {
+  return *reinterpret_cast<const float*>(lut + off);
+}
+
+// Byte offset 256 * code + this lane's offset, for byte b of the code word.
+__device__ __forceinline__ unsigned lut_off(unsigned codes, unsigned lane_off, unsigned b) {
+  return __byte_perm(codes, lane_off, 0x5504u | (b << 4));
+}
+
+// Pairs this lane's rows with the G columns its group visits.  EDGE tiles
+// (diagonal blocks, padding) may hold code 0 ("no pair"), whose stress term
+// must vanish; elsewhere every code is a real distance.
+template <int DIM, int MODE, int NC, int CODE, bool EDGE>
+__device__ __forceinline__ void tile_compute(const unsigned char* __restrict__ dt, const float* __restrict__ colv,
                                              const unsigned char* __restrict__ lut,
-                                             const Vec<DIM> (&xi)[NC][ROWS_PER_LANE],
-                                             Vec<DIM> (&iacc)[NC][ROWS_PER_LANE], Vec<DIM> (&jout)[NC],
-                                             float (&st)[NC], int lane, int warp) {
+                                             Rows<DIM, NC, TileShape<DIM, MODE>::R>& rows, Vec<DIM> (&jout)[NC],
+                                             float (&st)[NC], int tid) {
+  using TS = TileShape<DIM, MODE>;
+  constexpr int R = TS::R, G = TS::G, CH = TS::CH;
   constexpr int DP = DimP<DIM>::v;
-  constexpr int CH = Chains<MODE, DIM>::v;
-  constexpr float TINY = 1e-30f;  // keeps rsqrt finite for coincident points; below FP32 resolution of r^2
-  const unsigned off_w = 4u * lane;                // this lane's copy of 1/d^2
-  const unsigned off_k = 128u + 8u * (lane & 15);  // this lane's copy of {1/d, -1}
-  Vec<DIM> jacc[CH][NC];
-#pragma unroll
-  for (int h = 0; h < CH; ++h)
-#pragma unroll
-    for (int c = 0; c < NC; ++c) jacc[h][c] = vzero<DIM>();
-#pragma unroll 1
-  for (int t0 = 0; t0 < 32; t0 += CH) {
-#pragma unroll
-  for (int h = 0; h < CH; ++h) {
-    const int jl = warp * 32 + ((lane + t0 + h) & 31);
-    unsigned codes = 0;
-    float dv[ROWS_PER_LANE];
-    if constexpr (CODE == CODE_U8) {
-      codes = *reinterpret_cast<const unsigned*>(dt + jl * TILE + ROWS_PER_LANE * lane);
-    } else {
-      const float4 q = *reinterpret_cast<const float4*>(dt + 4 * (jl * TILE + ROWS_PER_LANE * lane));
-      dv[0] = q.x;
-      dv[1] = q.y;
-      dv[2] = q.z;
-      dv[3] = q.w;
-    }
-    Vec<DIM> pj[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) pj[c] = lds_v<DIM>(posj + c * TILE * DP, jl);
-#pragma unroll
-    for (int a = 0; a < ROWS_PER_LANE; ++a) {
-      float invd = 0.f, negm = 0.f, w = 0.f;
-      if constexpr (CODE == CODE_U8) {
-        // byte offset 256 * code + this lane's offset, built by one byte permute
-        if constexpr (MODE == PM_MATVEC || MODE == PM_FORCES) {
-          const unsigned ow = __byte_perm(codes, off_w, 0x5504u | (unsigned)(a << 4));
-          w = *reinterpret_cast<const float*>(lut + ow);
-        }
-        if constexpr (MODE != PM_MATVEC) {
-          const unsigned ok = __byte_perm(codes, off_k, 0x5504u | (unsigned)(a << 4));
-          const float2 l = *reinterpret_cast<const float2*>(lut + ok);
-          invd = l.x;
-          negm = l.y;
-        }
-      } else {
-        const float d = dv[a];
-        invd = d > 0.f ? __frcp_rn(d) : 0.f;
-        negm = d > 0.f ? -1.f : 0.f;
-        w = invd * invd;
-      }
-      if constexpr (MODE == PM_MATVEC) {
-#pragma unroll
-        for (int d = 0; d < DIM; ++d) {
-          iacc[0][a].c[d] = fmaf(-w, pj[0].c[d], iacc[0][a].c[d]);
-          jacc[h][0].c[d] = fmaf(-w, xi[0][a].c[d], jacc[h][0].c[d]);
-        }
-      } else {
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          float dx[DIM];
-          float r2 = TINY;
-#pragma unroll
-          for (int d = 0; d < DIM; ++d) {
-            dx[d] = xi[c][a].c[d] - pj[c].c[d];
-            r2 = fmaf(dx[d], dx[d], r2);
-          }
-          const float rs = rsqrt_approx(r2);
-          if constexpr (MODE == PM_STRESS || MODE == PM_RHS) {
-            const float r = r2 * rs;
-            const float tt = fmaf(r, invd, negm);
-            st[c] = fmaf(tt, tt, st[c]);
-          }
-          if constexpr (MODE == PM_RHS || MODE == PM_FORCES) {
-            float coef;
-            if constexpr (MODE == PM_RHS) {
-              coef = rs * invd;
-            } else {
-              coef = fmaf(invd, rs, -w);
-            }
-#pragma unroll
-            for (int d = 0; d < DIM; ++d) {
-              iacc[c][a].c[d] = fmaf(coef, dx[d], iacc[c][a].c[d]);
-              jacc[h][c].c[d] = fmaf(-coef, dx[d], jacc[h][c].c[d]);
-            }
-          }
-        }
-      }
-    }
-    if constexpr (MODE != PM_STRESS) {
-#pragma unroll
-      for (int c = 0; c < NC; ++c)
-#pragma unroll
-        for (int d = 0; d < DIM; ++d)
-          jacc[h][c].c[d] = __shfl_sync(0xffffffffu, jacc[h][c].c[d], (lane + CH) & 31);
-    }
-  }
-  }
-  // chain h of lane l now holds column (l + h) & 31: gather column l's chains
+  constexpr int CA = TILE * DP;  // floats between the formed candidate arrays
+  constexpr bool NEED_K = (MODE != PM_MATVEC);
+  constexpr bool NEED_W = (MODE == PM_MATVEC || MODE == PM_FORCES);
+  const int q = tid & (G - 1), grp = tid / G;
+  const unsigned off_k = 4u * (tid & 31), off_w = 128u + 4u * (tid & 31);
+  // TINY keeps rsqrt finite for coincident points; it is below the FP32 resolution of r^2
+  const f2x TINY2 = pk2(1e-30f, 1e-30f), NEG1 = pk2(-1.f, -1.f);
+  float jacc[CH][NC][DIM];
+  f2x stp[NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
-    jout[c] = jacc[0][c];
+    stp[c] = pk2(0.f, 0.f);
 #pragma unroll
-    for (int h = 1; h < CH; ++h)
+    for (int h = 0; h < CH; ++h)
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) jout[c].c[d] += __shfl_sync(0xffffffffu, jacc[h][c].c[d], (lane - h) & 31);
+      for (int d = 0; d < DIM; ++d) jacc[h][c][d] = 0.f;
+  }
+#pragma unroll 1
+  for (int t0 = 0; t0 < G; t0 += CH) {
+#pragma unroll
+    for (int h = 0; h < CH; ++h) {
+      const int jl = grp * G + ((q + t0 + h) & (G - 1));
+      unsigned cw[(R + 3) / 4];
+      float dv[(CODE == CODE_U8) ? 1 : R];
+      if constexpr (CODE == CODE_U8) {
+        const unsigned char* cp = dt + jl * TILE + R * q;
+        if constexpr (R == 16) {
+          const uint4 c = *reinterpret_cast<const uint4*>(cp);
+          cw[0] = c.x;
+          cw[1] = c.y;
+          cw[2] = c.z;
+          cw[3] = c.w;
+        } else if constexpr (R == 8) {
+          const uint2 c = *reinterpret_cast<const uint2*>(cp);
+          cw[0] = c.x;
+          cw[1] = c.y;
+        } else {
+          cw[0] = *reinterpret_cast<const unsigned*>(cp);
+        }
+      } else {
+        const float4* cp = reinterpret_cast<const float4*>(dt) + (jl * TILE + R * q) / 4;
+#pragma unroll
+        for (int k = 0; k < R / 4; ++k) {
+          const float4 v = cp[k];
+          dv[4 * k] = v.x;
+          dv[4 * k + 1] = v.y;
+          dv[4 * k + 2] = v.z;
+          dv[4 * k + 3] = v.w;
+        }
+      }
+      f2x P[NC][DIM];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const Vec<DIM> pj = lds_v<DIM>(colv + c * CA, jl);
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) P[c][d] = pk2(pj.c[d], pj.c[d]);
+      }
+      f2x J[NC][DIM];
+#pragma unroll
+      for (int a2 = 0; a2 < R / 2; ++a2) {
+        f2x V = 0ull, W = 0ull, NEGM = NEG1;
+        if constexpr (CODE == CODE_U8) {
+          const unsigned c = cw[a2 >> 1];
+          const unsigned b0 = (2u * a2) & 3u;
+          if constexpr (NEED_K) V = pk2(lut_at(lut, lut_off(c, off_k, b0)), lut_at(lut, lut_off(c, off_k, b0 + 1)));
+          if constexpr (MODE == PM_MATVEC && kMatvecRcp && !EDGE) {
+            const f2x D = sub2(pk2(code_plus_2p23(c, b0), code_plus_2p23(c, b0 + 1)), pk2(8388608.f, 8388608.f));
+            const f2x D2 = mul2(D, D);
+            W = pk2(rcp_approx(lo2(D2)), rcp_approx(hi2(D2)));
+          } else if constexpr (NEED_W) {
+            W = pk2(lut_at(lut, lut_off(c, off_w, b0)), lut_at(lut, lut_off(c, off_w, b0 + 1)));
+          }
+        } else {
+          const float d0 = dv[2 * a2], d1 = dv[2 * a2 + 1];
+          const float i0 = d0 > 0.f ? __frcp_rn(d0) : 0.f, i1 = d1 > 0.f ? __frcp_rn(d1) : 0.f;
+          V = pk2(i0, i1);
+          W = pk2(i0 * i0, i1 * i1);
+        }
+        if constexpr ((EDGE || CODE != CODE_U8) && (MODE == PM_STRESS || MODE == PM_RHS))
+          NEGM = pk2(lo2(V) > 0.f ? -1.f : 0.f, hi2(V) > 0.f ? -1.f : 0.f);
+        if constexpr (MODE == PM_MATVEC) {
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) {
+            rows.acc[0][d][a2] = fma2(W, P[0][d], rows.acc[0][d][a2]);
+            J[0][d] = (a2 == 0) ? mul2(W, rows.x[0][d][a2]) : fma2(W, rows.x[0][d][a2], J[0][d]);
+          }
+        } else {
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            f2x DX[DIM];
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) DX[d] = sub2(rows.x[c][d][a2], P[c][d]);
+            f2x R2 = fma2(DX[0], DX[0], TINY2);
+#pragma unroll
+            for (int d = 1; d < DIM; ++d) R2 = fma2(DX[d], DX[d], R2);
+            const f2x RS = pk2(rsqrt_approx(lo2(R2)), rsqrt_approx(hi2(R2)));
+            f2x CO = mul2(RS, V);  // 1 / (d r)
+            if constexpr (MODE == PM_STRESS || MODE == PM_RHS) {
+              const f2x TT = fma2(R2, CO, NEGM);  // r / d - 1
+              stp[c] = fma2(TT, TT, stp[c]);
+            }
+            if constexpr (MODE == PM_FORCES) CO = sub2(CO, W);  // 1 / (d r) - 1 / d^2
+            if constexpr (MODE != PM_STRESS) {
+#pragma unroll
+              for (int d = 0; d < DIM; ++d) {
+                rows.acc[c][d][a2] = fma2(CO, DX[d], rows.acc[c][d][a2]);
+                J[c][d] = (a2 == 0) ? mul2(CO, DX[d]) : fma2(CO, DX[d], J[c][d]);
+              }
+            }
+          }
+        }
+      }
+      if constexpr (MODE != PM_STRESS) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) {
+            jacc[h][c][d] += lo2(J[c][d]);
+            jacc[h][c][d] += hi2(J[c][d]);
+            if constexpr (CH < G) jacc[h][c][d] = __shfl_sync(0xffffffffu, jacc[h][c][d], (q + CH) & (G - 1), G);
+          }
+      }
+    }
+  }
+  // chain h of lane q now holds column (q + h) mod G of the group: gather column q
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    st[c] = lo2(stp[c]) + hi2(stp[c]);
+    if constexpr (MODE != PM_STRESS) {
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) {
+        float s = jacc[0][c][d];
+#pragma unroll
+        for (int h = 1; h < CH; ++h) s += __shfl_sync(0xffffffffu, jacc[h][c][d], (q - h) & (G - 1), G);
+        jout[c].c[d] = s;
+      }
+    }
   }
 }
 
-// Forms element t of one block (side 0 = I, 1 = J) of the pass's vectors
-// from the raw arrays in shared memory.
-template <int DIM, int SK, int NC>
-__device__ __forceinline__ void form(const PassSrc& s, const float* raw, int side, int t, Vec<DIM> (&out)[NC]) {
+// Forms element t of a block of the pass's vectors, in place in the raw
+// arrays (candidate c goes to array c's slot).
+template <int DIM, int NC>
+__device__ __forceinline__ void form_inplace(const PassSrc& s, float* raw, int t) {
   constexpr int DP = DimP<DIM>::v;
-  constexpr int A = TILE * DP;  // floats per raw block
-  if constexpr (SK == SK_DIRECT) {
-    out[0] = lds_v<DIM>(raw + (0 * 2 + side) * A, t);
-  } else if constexpr (SK == SK_CGU) {
-    const Vec<DIM> r = lds_v<DIM>(raw + (0 * 2 + side) * A, t);
-    const Vec<DIM> w = lds_v<DIM>(raw + (1 * 2 + side) * A, t);
-    const Vec<DIM> sp = lds_v<DIM>(raw + (2 * 2 + side) * A, t);
-    const float is = raw[(3 * 2 + side) * A + t];
+  constexpr int A = TILE * DP;  // floats per raw array
+  const int kind = s.kind;
+  if (kind == SK_CGU) {
+    const Vec<DIM> r = lds_v<DIM>(raw, t);
+    const Vec<DIM> w = lds_v<DIM>(raw + A, t);
+    const Vec<DIM> sp = lds_v<DIM>(raw + 2 * A, t);
+    const float is = raw[3 * A + t];
+    Vec<DIM> u;
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) out[0].c[d] = cg_u(r.c[d], w.c[d], sp.c[d], is, s.alpha[d], s.beta[d]);
-  } else {
-    const Vec<DIM> zw = lds_v<DIM>(raw + (0 * 2 + side) * A, t);
+    for (int d = 0; d < DIM; ++d) u.c[d] = cg_u(r.c[d], w.c[d], sp.c[d], is, s.alpha[d], s.beta[d]);
+    sts_v<DIM>(raw, t, u);
+  } else if (kind == SK_K2 || kind == SK_SEL) {
+    const Vec<DIM> zw = lds_v<DIM>(raw, t);
     Vec<DIM> z;
 #pragma unroll
     for (int d = 0; d < DIM; ++d) z.c[d] = zw.c[d] - s.z0[d];
-    out[0] = z;
-    if constexpr (NC == 2) {
-      const Vec<DIM> x = lds_v<DIM>(raw + (1 * 2 + side) * A, t);
+    if (kind == SK_K2 && NC == 2) {
+      const Vec<DIM> x = lds_v<DIM>(raw + A, t);
+      Vec<DIM> xt;
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) out[1].c[d] = sor_xt(z.c[d], x.c[d], s.om);
+      for (int d = 0; d < DIM; ++d) xt.c[d] = sor_xt(z.c[d], x.c[d], s.om);
+      sts_v<DIM>(raw + A, t, xt);
     }
-  }
-}
-
-// --------------------------------------------------------------------------
-// Row-block reduction of the partial buffers: thread t gets row R*TILE + t.
-// --------------------------------------------------------------------------
-
-// Row-block phase work unit: a quarter (32 rows) of row block R.  The four
-// warps of the CTA take every fourth partial sum of the block's fixed list,
-// for all 32 rows (lane = row), and the four part sums are added in warp
-// order; warp 0 then holds the totals and runs the per-row epilogue.
-constexpr int QROWS = 32;
-
-// Sums the partials of rows R*TILE + 32*qr + lane and leaves the totals in
-// shared memory, out[(c * QROWS + lane) * DIM + d] (valid for warp 0's use).
-// Out of line with plain pointer arguments, so that its loads in flight get
-// their own registers.
-template <int DIM, int NC>
-__device__ __noinline__ void reduce_quarter_smem(const float* __restrict__ part_i, const float* __restrict__ part_j,
-                                                 const int* __restrict__ contrib_ptr,
-                                                 const int* __restrict__ contrib, int R, int qr, int* idx,
-                                                 float* scratch, float* out) {
-  constexpr int DP = DimP<DIM>::v;
-  constexpr int Q = 8;  // partials in flight per thread
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int row = QROWS * qr + lane;  // row inside the tile block
-  Vec<DIM> s[NC], cmp[NC];
+    if (kind == SK_SEL && s.sel) {
+      const Vec<DIM> x = lds_v<DIM>(raw + A, t);
 #pragma unroll
-  for (int c = 0; c < NC; ++c) {
-    s[c] = vzero<DIM>();
-    cmp[c] = vzero<DIM>();
-  }
-  const int c0 = contrib_ptr[R], c1 = contrib_ptr[R + 1];
-  for (int base = c0; base < c1; base += CTA) {
-    const int cnt = min(CTA, c1 - base);
-    __syncthreads();
-    if ((int)threadIdx.x < cnt) idx[threadIdx.x] = contrib[base + threadIdx.x];
-    __syncthreads();
-    for (int q0 = w; q0 < cnt; q0 += 4 * Q) {
-      Vec<DIM> v[Q][NC];
-#pragma unroll
-      for (int q = 0; q < Q; ++q) {
-        const int k = q0 + 4 * q;
-        if (k < cnt) {
-          const int e = idx[k];
-          const float* src = (e >= 0) ? part_i + (size_t)e * 2 * TILE * DP : part_j + (size_t)(-1 - e) * 2 * TILE * DP;
-#pragma unroll
-          for (int c = 0; c < NC; ++c) v[q][c] = ldv<DIM>(src + (size_t)c * TILE * DP, row);
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < Q; ++q)
-        if (q0 + 4 * q < cnt) {
-#pragma unroll
-          for (int c = 0; c < NC; ++c)
-#pragma unroll
-            for (int d = 0; d < DIM; ++d) kahan_add(s[c].c[d], cmp[c].c[d], v[q][c].c[d]);
-        }
+      for (int d = 0; d < DIM; ++d) z.c[d] = sor_xt(z.c[d], x.c[d], s.om);
     }
+    sts_v<DIM>(raw, t, z);
   }
-  // part sums of the four warps, added in warp order
-#pragma unroll
-  for (int c = 0; c < NC; ++c)
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) scratch[((w * NC + c) * QROWS + lane) * DIM + d] = s[c].c[d] - cmp[c].c[d];
-  __syncthreads();
-  if (w == 0) {
-#pragma unroll
-    for (int c = 0; c < NC; ++c)
-#pragma unroll
-      for (int d = 0; d < DIM; ++d) {
-        float t = scratch[((0 * NC + c) * QROWS + lane) * DIM + d];
-#pragma unroll
-        for (int ww = 1; ww < 4; ++ww) t += scratch[((ww * NC + c) * QROWS + lane) * DIM + d];
-        out[(c * QROWS + lane) * DIM + d] = t;
-      }
-  }
-  __syncthreads();
-}
-
-template <int DIM, int NC>
-__device__ __forceinline__ void reduce_rows(const KParams& p, int R, int qr, Vec<DIM> (&out)[NC]) {
-  extern __shared__ __align__(256) unsigned char smem_dyn[];
-  int* idx = reinterpret_cast<int*>(smem_dyn + SMEM_OFF_IDX);
-  float* scratch = reinterpret_cast<float*>(smem_dyn + SMEM_OFF_POSI);      // free outside the passes
-  float* res = scratch + 4 * 2 * QROWS * 3;
-  reduce_quarter_smem<DIM, NC>(p.part_i, p.part_j, p.g.contrib_ptr, p.g.contrib, R, qr, idx, scratch, res);
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int c = 0; c < NC; ++c)
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) out[c].c[d] = res[(c * QROWS + lane) * DIM + d];
-}
-
-// Warp-level double-float sum (fixed order); the totals land in lane 0.
-template <int K>
-__device__ __forceinline__ void warp_sum_df(df (&v)[K]) {
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      df q;
-      q.hi = __shfl_down_sync(0xffffffffu, v[k].hi, o);
-      q.lo = __shfl_down_sync(0xffffffffu, v[k].lo, o);
-      v[k] = df_add(v[k], q);
-    }
-  }
-}
-
-__device__ __forceinline__ float2* scal(const KParams& p, int parity) {
-  return p.sc + (size_t)parity * 4 * p.g.nb * SC_STRIDE;
 }
 
 // Thread 0 of a CTA: bulk copies (TMA) of a tile's distance codes and of
-// blocks I and J of every raw source array, completing on mbarrier b.
-template <int DIM, int CODE, int SK>
-__device__ __forceinline__ void issue_tile(const KParams& p, const PassSrc& src, unsigned char* smem, int tile, int I,
-                                        int J, int b) {
+// block J (and, at a task's first tile, block I) of every raw source array,
+// completing on the stage's mbarrier.
+template <int DIM, int CODE>
+__device__ __forceinline__ void issue_tile(const PassArgs& p, const PassSrc& src, unsigned char* smem, int tile, int I,
+                                        int J, bool first, int s) {
   using L = SmemLayout<DIM, CODE>;
   constexpr int DP = DimP<DIM>::v;
-  constexpr unsigned TBYTES = TILE * TILE * CodeBytes<CODE>::v;
-  constexpr int NA = SrcN<SK>::v;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L::OFF_MISC);
-  float* raw = reinterpret_cast<float*>(smem + L::OFF_RAW);
-  unsigned char* dbuf = smem + (b ? L::OFF_D1 : L::OFF_D0);
-  unsigned bytes = TBYTES;
+  constexpr unsigned TBYTES = L::DBUF;
+  const int kind = src.kind;
+  const int NA = src_arrays(kind);
+  const unsigned RB = raw_bytes<DIM>(kind);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L::OFF_MISC) + s;
+  fence_proxy_async();  // this CTA's generic accesses to the stage come before the copy overwrites it
+  mbar_expect_tx(mbar, TBYTES + (first ? 2 * RB : RB));
+  bulk_g2s(smem + L::off_d(p.stage_base, s), reinterpret_cast<const unsigned char*>(p.D) + (size_t)tile * TBYTES, TBYTES, mbar);
 #pragma unroll
-  for (int a = 0; a < NA; ++a) bytes += 2u * ((SK == SK_CGU && a == 3) ? TILE * 4 : TILE * DP * 4);
-  fence_proxy_async();  // this CTA's reads of the raw area come before the copy overwrites it
-  mbar_expect_tx(&mbar[b], bytes);
-  bulk_g2s(dbuf, reinterpret_cast<const unsigned char*>(p.D) + (size_t)tile * TBYTES, TBYTES, &mbar[b]);
-#pragma unroll
-  for (int a = 0; a < NA; ++a) {
-    const bool scalar = (SK == SK_CGU && a == 3);
-    const unsigned ab = scalar ? TILE * 4 : TILE * DP * 4;
-    const int stride = scalar ? TILE : TILE * DP;
-    bulk_g2s(raw + (a * 2 + 0) * TILE * DP, src.a[a] + (size_t)I * stride, ab, &mbar[b]);
-    bulk_g2s(raw + (a * 2 + 1) * TILE * DP, src.a[a] + (size_t)J * stride, ab, &mbar[b]);
+  for (int side = 0; side < 2; ++side) {
+    if (side == 1 && !first) break;
+    float* raw = reinterpret_cast<float*>(smem + (side ? L::off_rawi(p.stage_base, s) : L::off_rawj(p.stage_base, s)));
+    const int blk = side ? I : J;
+    for (int a = 0; a < NA; ++a) {
+      const bool scalar = (kind == SK_CGU && a == 3);
+      const unsigned ab = scalar ? TILE * 4 : TILE * DP * 4;
+      const int stride = scalar ? TILE : TILE * DP;
+      bulk_g2s(raw + a * TILE * DP, src.a[a] + (size_t)blk * stride, ab, mbar);
+    }
   }
 }
 
+// The tiles of one CTA in visiting order: its tasks m = 0..M-1 and the
+// tiles of each task in strip order; both reversed when `rev`.
+struct TileIt {
+  int m, k, M;
+  bool rev, valid;
+  TaskDesc td;
+  __device__ __forceinline__ void load(const PassArgs& g) {
+    const int mm = rev ? (M - 1 - m) : m;
+    td = (mm < MAX_CTA_TASKS) ? g.tasks_s[mm] : g.tasks_g[mm];
+    k = rev ? td.k1 - 1 : td.k0;
+  }
+  __device__ __forceinline__ void begin(const PassArgs& g, bool r) {
+    rev = r;
+    M = g.ntasks;
+    m = 0;
+    valid = M > 0;
+    if (valid) load(g);
+  }
+  __device__ __forceinline__ bool first() const { return k == (rev ? td.k1 - 1 : td.k0); }
+  __device__ __forceinline__ bool last() const { return k == (rev ? td.k0 : td.k1 - 1); }
+  __device__ __forceinline__ void next(const PassArgs& g) {
+    if (!last()) {
+      k += rev ? -1 : 1;
+      return;
+    }
+    if (++m >= M) {
+      valid = false;
+      return;
+    }
+    load(g);
+  }
+  __device__ __forceinline__ int J(int nb) const { return (td.I + k) % nb; }
+  __device__ __forceinline__ int tile() const { return td.tile0 + (k - td.k0); }
+};
+
+// A pass's parameters, kept in shared memory (read where they are used, so
+// that the tile loop keeps its registers), and the copy issuer's iterator.
+struct PassCtl {
+  PassSrc src;
+  PassArgs a;
+  TileIt is;  // next tile to copy (thread 0 only)
+  int s_is;   // its stage
+};
+static_assert(sizeof(PassCtl) <= SmemLayout<1, CODE_U8>::OFF_RUN - SmemLayout<1, CODE_U8>::OFF_CTL,
+              "PassCtl must fit its shared-memory slot");
+
+// Scalars of the Algorithm 2 loop (shared memory, written by thread 0).
+struct RunState {
+  double f_cur, f_new, crit, passes_mv, passes_st;
+  int cg_total, cg_maxed, cg_stalled, n_acc, it_outer, it;
+  int accept, stop, all_conv, cg_done;
+  int conv[3];
+  float z0[3], om_prev;
+  float alpha[3], beta[3], gam[3], rz[3], bb[3];
+};
+static_assert(sizeof(RunState) <= SmemLayout<1, CODE_U8>::OFF_PARAMS - SmemLayout<1, CODE_U8>::OFF_RUN,
+              "RunState must fit its shared-memory slot");
+static_assert(sizeof(KParams) <= SmemLayout<1, CODE_U8>::OFF_TASKS - SmemLayout<1, CODE_U8>::OFF_PARAMS,
+              "KParams must fit its shared-memory slot");
+
 // --------------------------------------------------------------------------
 // A full pair pass: CTA b takes tasks b, b + G, b + 2G, ... (G = grid size);
-// no global synchronisation inside the pass.
+// no global synchronisation inside the pass.  Row and column sums go to
+// acc + c * n_pad * DP (candidate c); stress to the CTA's slot.  Out of line,
+// so that the tile loop has the registers to itself.
 // --------------------------------------------------------------------------
 
-template <int DIM, int MODE, int NC, int CODE, int SK>
-__device__ bool pair_pass(const KParams& p, unsigned char* smem, PairState& ps, const PassSrc& src) {
+#ifndef FD_PASS_ATTR
+#define FD_PASS_ATTR __noinline__
+#endif
+template <int DIM, int MODE, int NC, int CODE>
+__device__ FD_PASS_ATTR bool pair_pass_impl(PairState* ps_io, float* acc) {
+  // the dynamic shared memory itself (not a pointer argument), so that every
+  // access compiles to a shared-memory instruction with a constant base
+  extern __shared__ __align__(256) unsigned char smem[];
   using L = SmemLayout<DIM, CODE>;
+  using TS = TileShape<DIM, MODE>;
+  constexpr int R = TS::R, G = TS::G;
   constexpr int DP = DimP<DIM>::v;
-  const Geometry& g = p.g;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  PassCtl* ctl = reinterpret_cast<PassCtl*>(smem + L::OFF_CTL);
+  const PassArgs& p = ctl->a;
+  const PassArgs& g = ctl->a;
+  const PassSrc& src = ctl->src;
+  PairState ps = *ps_io;
+  const int tid = threadIdx.x, nbuf = p.nbuf;
+  const size_t vs = (size_t)g.n_pad * DP;
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L::OFF_MISC);
-  float* raw = reinterpret_cast<float*>(smem + L::OFF_RAW);
-  float* posi = reinterpret_cast<float*>(smem + L::OFF_POSI);
-  float* posj = reinterpret_cast<float*>(smem + L::OFF_POSJ);
   float2* red64 = reinterpret_cast<float2*>(smem + L::OFF_RED64);
   const unsigned char* lut = smem + L::OFF_LUT;
+  const int sb = p.stage_base;
   float ssum[NC], scomp[NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) ssum[c] = scomp[c] = 0.f;
   // vectors written before the last grid barrier are read below by bulk copies
   if (tid == 0) fence_proxy_async_global();
-  int cur = blockIdx.x;
-  if (cur < g.ntasks) {
-    TaskDesc td = g.tasks[cur];
-    int k = td.k0;
-    int buf = 0;
-    if (tid == 0) issue_tile<DIM, CODE, SK>(p, src, smem, td.tile0, td.I, (td.I + k) % g.nb, 0);
-    Vec<DIM> iacc[NC][ROWS_PER_LANE];
-    bool task_start = true;
-    while (true) {
-      const int J = (td.I + k) % g.nb;
-      const int tile = td.tile0 + (k - td.k0);
-      const unsigned ph = (ps.parity >> buf) & 1u;
-      if (!mbar_wait(mbar + buf, ph, p.timeout_ns)) {
-        set_error(p.ctrl, E_TIMEOUT);
-        mbar_wait(mbar + buf, ph, p.timeout_ns);  // let our own copies land (bounded)
-        return false;
-      }
-      ps.parity ^= (1u << buf);
-      {
-        Vec<DIM> vi[NC], vj[NC];
-        form<DIM, SK, NC>(src, raw, 0, tid, vi);
-        form<DIM, SK, NC>(src, raw, 1, tid, vj);
-        // rows of block I are stored lane-interleaved: row 4l + a at a * 32 + l
-        const int irow = (tid & (ROWS_PER_LANE - 1)) * 32 + (tid >> 2);
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          sts_v<DIM>(posi + c * TILE * DP, irow, vi[c]);
-          sts_v<DIM>(posj + c * TILE * DP, tid, vj[c]);
-        }
-      }
-      __syncthreads();  // raw consumed; posi / posj ready
-      const bool task_end = (k + 1 >= td.k1);
-      int ntask = cur, nk = k + 1;
-      TaskDesc ntd = td;
-      if (task_end) {
-        ntask = cur + gridDim.x;
-        if (ntask < g.ntasks) {
-          ntd = g.tasks[ntask];
-          nk = ntd.k0;
-        }
-      }
-      const bool more = ntask < g.ntasks;
-      if (more && tid == 0)
-        issue_tile<DIM, CODE, SK>(p, src, smem, ntd.tile0 + (nk - ntd.k0), ntd.I, (ntd.I + nk) % g.nb, buf ^ 1);
-
-      if (task_start) {
-#pragma unroll
-        for (int c = 0; c < NC; ++c)
-#pragma unroll
-          for (int a = 0; a < ROWS_PER_LANE; ++a) iacc[c][a] = vzero<DIM>();
-        task_start = false;
-      }
-      Vec<DIM> xi[NC][ROWS_PER_LANE];
+  const bool rev = (ps.pass & 1) != 0;
+  TileIt it;  // computed tile
+  it.begin(g, rev);
+  int s_it = 0;  // its stage
+  if (tid == 0) {
+    TileIt is = it;
+    int s_is = 0;
+    for (int k = 0; k < nbuf - 1 && is.valid; ++k) {
+      issue_tile<DIM, CODE>(p, src, smem, is.tile(), is.td.I, is.J(g.nb), is.first(), s_is);
+      is.next(g);
+      s_is = (s_is + 1 == nbuf) ? 0 : s_is + 1;
+    }
+    ctl->is = is;
+    ctl->s_is = s_is;
+  }
+  Rows<DIM, NC, R> rows;
+  while (it.valid) {
+    const int I = it.td.I, J = it.J(g.nb);
+    const bool first = it.first(), last = it.last();
+    const unsigned ph = (ps.parity >> s_it) & 1u;
+    if (!mbar_wait(mbar + s_it, ph, p.timeout_ns)) {
+      set_error(p.ctrl, E_TIMEOUT);
+      // let this CTA's own copies land (bounded) before leaving
+      for (int k = 0; k < nbuf; ++k) mbar_wait(mbar + k, (ps.parity >> k) & 1u, p.timeout_ns);
+      *ps_io = ps;
+      return false;
+    }
+    ps.parity ^= (1u << s_it);
+    float* rawj = reinterpret_cast<float*>(smem + L::off_rawj(sb, s_it));
+    float* rawi = reinterpret_cast<float*>(smem + L::off_rawi(sb, s_it));
+    form_inplace<DIM, NC>(src, rawj, tid);
+    if (first) form_inplace<DIM, NC>(src, rawi, tid);
+    __syncthreads();  // formed vectors visible; every thread is done with the stage of the previous tile
+    if (tid == 0 && ctl->is.valid) {
+      TileIt is = ctl->is;
+      issue_tile<DIM, CODE>(p, src, smem, is.tile(), is.td.I, is.J(g.nb), is.first(), ctl->s_is);
+      is.next(g);
+      ctl->is = is;
+      ctl->s_is = (ctl->s_is + 1 == nbuf) ? 0 : ctl->s_is + 1;
+    }
+    const int q = tid & (G - 1);
+    if (first) {
 #pragma unroll
       for (int c = 0; c < NC; ++c)
 #pragma unroll
-        for (int a = 0; a < ROWS_PER_LANE; ++a) xi[c][a] = lds_v<DIM>(posi + c * TILE * DP, a * 32 + lane);
-      Vec<DIM> jacc[NC];
-      float st[NC];
+        for (int a2 = 0; a2 < R / 2; ++a2) {
+          const Vec<DIM> x0 = lds_v<DIM>(rawi + c * TILE * DP, R * q + 2 * a2);
+          const Vec<DIM> x1 = lds_v<DIM>(rawi + c * TILE * DP, R * q + 2 * a2 + 1);
 #pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        st[c] = 0.f;
-        jacc[c] = vzero<DIM>();
-      }
-      tile_compute<DIM, MODE, NC, CODE>(smem + (buf ? L::OFF_D1 : L::OFF_D0), posj, lut, xi, iacc, jacc, st, lane, warp);
+          for (int d = 0; d < DIM; ++d) {
+            rows.x[c][d][a2] = pk2(x0.c[d], x1.c[d]);
+            rows.acc[c][d][a2] = pk2(0.f, 0.f);
+          }
+        }
+    }
+    Vec<DIM> jout[NC];
+    float st[NC];
+    const unsigned char* dt = smem + L::off_d(sb, s_it);
+    const bool edge = (it.k == 0) || (g.n < g.n_pad && (I == g.nb - 1 || J == g.nb - 1));
+    if constexpr (MODE == PM_STRESS || MODE == PM_RHS || (MODE == PM_MATVEC && kMatvecRcp)) {
+      if (edge) tile_compute<DIM, MODE, NC, CODE, true>(dt, rawj, lut, rows, jout, st, tid);
+      else tile_compute<DIM, MODE, NC, CODE, false>(dt, rawj, lut, rows, jout, st, tid);
+    } else {
+      tile_compute<DIM, MODE, NC, CODE, false>(dt, rawj, lut, rows, jout, st, tid);
+    }
+    if constexpr (MODE == PM_STRESS || MODE == PM_RHS) {
 #pragma unroll
       for (int c = 0; c < NC; ++c) kahan_add(ssum[c], scomp[c], st[c]);
-      if constexpr (MODE != PM_STRESS) {
+    }
+    if constexpr (MODE != PM_STRESS) {
+      // column sums: thread t holds column t of block J
+      const int j = J * TILE + tid;
+      if (j < g.n) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          Vec<DIM> v = jout[c];
+          if constexpr (MODE != PM_MATVEC) {
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) v.c[d] = -v.c[d];
+          }
+          atomic_addv<DIM>(acc + c * vs, j, v);
+        }
+      }
+      if (last) {
+        // row sums of the task: the R groups' partials meet in the stage's code buffer
+        float* red = reinterpret_cast<float*>(smem + L::off_d(sb, s_it));  // [NC][R groups][TILE][DP]
+        const int grp = tid / G;
+        __syncthreads();  // every warp is done with the codes
 #pragma unroll
         for (int c = 0; c < NC; ++c)
-          stv<DIM>(p.part_j + ((size_t)tile * 2 + c) * TILE * DP, warp * 32 + lane, jacc[c]);
-      }
-      if (task_end) {
-        if constexpr (MODE != PM_STRESS) {
-          __syncthreads();  // every warp is done with this distance buffer: reuse it for the row partials
-          float* red = reinterpret_cast<float*>(smem + (buf ? L::OFF_D1 : L::OFF_D0));  // [4][NC][TILE][DP]
 #pragma unroll
-          for (int c = 0; c < NC; ++c)
+          for (int a2 = 0; a2 < R / 2; ++a2) {
+            Vec<DIM> v0, v1;
 #pragma unroll
-            for (int a = 0; a < ROWS_PER_LANE; ++a)
-              sts_v<DIM>(red + ((size_t)(warp * NC + c) * TILE) * DP, ROWS_PER_LANE * lane + a, iacc[c][a]);
-          __syncthreads();
+            for (int d = 0; d < DIM; ++d) {
+              v0.c[d] = lo2(rows.acc[c][d][a2]);
+              v1.c[d] = hi2(rows.acc[c][d][a2]);
+            }
+            float* base = red + ((size_t)(c * R + grp) * TILE) * DP;
+            sts_v<DIM>(base, R * q + 2 * a2, v0);
+            sts_v<DIM>(base, R * q + 2 * a2 + 1, v1);
+          }
+        __syncthreads();
+        const int i = I * TILE + tid;
+        if (i < g.n) {
 #pragma unroll
           for (int c = 0; c < NC; ++c) {
-            Vec<DIM> s = lds_v<DIM>(red + ((size_t)(0 * NC + c) * TILE) * DP, tid);
+            Vec<DIM> s = lds_v<DIM>(red + ((size_t)(c * R) * TILE) * DP, tid);
 #pragma unroll
-            for (int w = 1; w < 4; ++w) {
-              const Vec<DIM> v = lds_v<DIM>(red + ((size_t)(w * NC + c) * TILE) * DP, tid);
+            for (int gg = 1; gg < R; ++gg) {
+              const Vec<DIM> v = lds_v<DIM>(red + ((size_t)(c * R + gg) * TILE) * DP, tid);
 #pragma unroll
               for (int d = 0; d < DIM; ++d) s.c[d] += v.c[d];
             }
-            stv<DIM>(p.part_i + ((size_t)cur * 2 + c) * TILE * DP, tid, s);
+            atomic_addv<DIM>(acc + c * vs, i, s);
           }
         }
-        task_start = true;
       }
-      __syncthreads();
-      if (!more) break;
-      cur = ntask;
-      td = ntd;
-      k = nk;
-      buf ^= 1;
     }
+    it.next(g);
+    s_it = (s_it + 1 == nbuf) ? 0 : s_it + 1;
   }
-  // stress of this CTA's pairs (candidates 0 and 1), one FP64 slot per CTA
+  // stress of this CTA's pairs (candidates 0 and 1), one double-float slot per CTA
   if constexpr (MODE == PM_STRESS || MODE == PM_RHS) {
     df v[NC];
 #pragma unroll
@@ -769,247 +893,126 @@ __device__ bool pair_pass(const KParams& p, unsigned char* smem, PairState& ps, 
     }
   }
   ps.pass += 1;
+  *ps_io = ps;
   return true;
 }
 
-// Runs an epilogue on every quarter row block (32 rows), one CTA per unit, after a pass.
-template <class Epi>
-__device__ __forceinline__ void rowblock_phase(const KParams& p, Epi& epi, int parity, float2* red64) {
-  for (int u = blockIdx.x; u < 4 * p.g.nb; u += gridDim.x) epi(u >> 2, u & 3, parity, red64);
+template <int DIM, int MODE, int NC, int CODE>
+__device__ __forceinline__ bool pair_pass(const KParams& p, unsigned char* smem, PairState& ps, const PassSrc& src,
+                                          float* acc) {
+  using L = SmemLayout<DIM, CODE>;
+  PassCtl* ctl = reinterpret_cast<PassCtl*>(smem + L::OFF_CTL);
+  if (threadIdx.x == 0) {
+    ctl->src = src;
+    PassArgs& a = ctl->a;
+    a.D = p.D;
+    const int t0 = p.g.cta_task_ptr[blockIdx.x];
+    a.tasks_g = p.g.tasks + t0;
+    a.tasks_s = reinterpret_cast<const TaskDesc*>(smem + L::OFF_TASKS);
+    a.ctrl = p.ctrl;
+    a.sc_cta = p.sc_cta;
+    a.timeout_ns = p.timeout_ns;
+    a.n = p.g.n;
+    a.n_pad = p.g.n_pad;
+    a.nb = p.g.nb;
+    a.ntasks = p.g.cta_task_ptr[blockIdx.x + 1] - t0;
+    a.nbuf = p.nbuf;
+    a.stage_base = L::stage_base(CODE == CODE_U8 ? p.lut_rows * LUT_ROW : 0);
+  }
+  __syncthreads();
+  return pair_pass_impl<DIM, MODE, NC, CODE>(&ps, acc);
 }
 
 // --------------------------------------------------------------------------
-// Epilogues (run once per row block, one CTA per block, after a pass)
+// Vertex phase: one thread per vertex (CTA b takes vertex blocks b, b + G,
+// ...); fn(i, v) adds the vertex's K scalars to v, which the CTA sums into
+// its slot of p.sc.
 // --------------------------------------------------------------------------
-
-// Every epilogue below works on the 32 rows R*TILE + 32*qr + lane: the
-// reduction uses the whole CTA, the per-row work runs in warp 0, and scalar
-// partials go to slot (4*R + qr) of the row-block scalar array.
-
-// b = L^{X} X of the initial layout (right-hand side of Eq. (2-5)).
-template <int DIM>
-struct EpiRhs0 {
-  const KParams& p;
-  __device__ __forceinline__ void operator()(int R, int qr, int, float2*) {
-    Vec<DIM> acc[1];
-    reduce_rows<DIM, 1>(p, R, qr, acc);
-    if (threadIdx.x < 32) stv<DIM>(p.B, R * TILE + QROWS * qr + threadIdx.x, acc[0]);
-  }
-};
-
-// F = (L^X - L^W) X written to the caller's [n][dim] array.
-template <int DIM>
-struct EpiForces {
-  const KParams& p;
-  __device__ __forceinline__ void operator()(int R, int qr, int, float2*) {
-    Vec<DIM> acc[1];
-    reduce_rows<DIM, 1>(p, R, qr, acc);
-    const int i = R * TILE + QROWS * qr + threadIdx.x;
-    if (threadIdx.x < 32 && i < p.g.n) {
+template <int K, class F>
+__device__ __forceinline__ void vertex_phase(const KParams& p, float2* red64, F&& fn) {
+  constexpr int K1 = (K > 0) ? K : 1;
+  df v[K1];
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) p.x_out[(size_t)i * DIM + d] = acc[0].c[d];
+  for (int k = 0; k < K1; ++k) v[k] = df_of(0.f);
+  for (int blk = blockIdx.x; blk < p.g.nb; blk += gridDim.x) fn(blk * TILE + (int)threadIdx.x, v);
+  if constexpr (K > 0) {
+    cta_sum_multi<K>(v, red64);
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) df_st(p.sc + (size_t)blockIdx.x * SC_STRIDE + k, v[k]);
     }
   }
-};
-
-__device__ __forceinline__ float2* scal_slot(const KParams& p, int parity, int R, int qr) {
-  return scal(p, parity) + (size_t)(4 * R + qr) * SC_STRIDE;
 }
 
-// Start of an H step (Eq. (2-5)): take the layout x0 chosen by the previous
-// acceptance test (or X^0), r0 = b - L^W x0, u0 = M^-1 r0, clear p and s;
-// displacement sums of x0 against the previous layout.
-// Scalar slots: [0,D) r.u  [D,2D) r.r  [2D,3D) b.b  [3D,4D) sum dx  [4D,5D) sum dx^2
-//               [5D,6D) sum x  [6D,7D) sum x^2
+// Reads and clears accumulator entry i.
 template <int DIM>
-struct EpiInit {
-  const KParams& p;
-  const float* x0src;
-  bool first, accept;
-  __device__ __forceinline__ void operator()(int R, int qr, int parity, float2*) {
-    Vec<DIM> acc[1];
-    reduce_rows<DIM, 1>(p, R, qr, acc);
-    if (threadIdx.x >= 32) return;
-    const int i = R * TILE + QROWS * qr + threadIdx.x;
-    const bool real = i < p.g.n;
-    const Vec<DIM> x0 = ldv<DIM>(x0src, i), xo = ldv<DIM>(p.X, i);
-    const Vec<DIM> b = first ? ldv<DIM>(p.B, i) : (accept ? ldv<DIM>(p.Bt, i) : ldv<DIM>(p.Bz, i));
-    const float s = __ldcg(p.s + i), is = __ldcg(p.inv_s + i);
-    Vec<DIM> r, u;
-    df v[7 * DIM];
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-      r.c[d] = b.c[d] - fmaf(s, x0.c[d], acc[0].c[d]);
-      u.c[d] = is * r.c[d];
-      const df dx = real ? df_diff(x0.c[d], xo.c[d]) : df_of(0.f);
-      const float xv = real ? x0.c[d] : 0.f;
-      v[d] = df_prod(r.c[d], u.c[d]);
-      v[DIM + d] = df_prod(r.c[d], r.c[d]);
-      v[2 * DIM + d] = df_prod(b.c[d], b.c[d]);
-      v[3 * DIM + d] = dx;
-      v[4 * DIM + d] = df_sqr(dx);
-      v[5 * DIM + d] = df_of(xv);
-      v[6 * DIM + d] = df_prod(xv, xv);
-    }
-    stv<DIM>(p.Zw, i, x0);
-    stv<DIM>(p.X, i, x0);
-    stv<DIM>(p.B, i, b);
-    stv<DIM>(p.R, i, r);
-    stv<DIM>(p.U, i, u);
-    stv<DIM>(p.P, i, vzero<DIM>());
-    stv<DIM>(p.S, i, vzero<DIM>());
-    warp_sum_df<7 * DIM>(v);
-    if (threadIdx.x == 0) {
-      float2* o = scal_slot(p, parity, R, qr);
-#pragma unroll
-      for (int k = 0; k < 7 * DIM; ++k) df_st(o + k, v[k]);
-    }
-  }
-};
+__device__ __forceinline__ Vec<DIM> take_acc(float* a, int i) {
+  const Vec<DIM> v = ldv<DIM>(a, i);
+  stv<DIM>(a, i, vzero<DIM>());
+  return v;
+}
 
-// w0 = L^W u0 and delta0 = (w0, u0).  Slots [0,D).
-template <int DIM>
-struct EpiAU0 {
-  const KParams& p;
-  __device__ __forceinline__ void operator()(int R, int qr, int parity, float2*) {
-    Vec<DIM> acc[1];
-    reduce_rows<DIM, 1>(p, R, qr, acc);
-    if (threadIdx.x >= 32) return;
-    const int i = R * TILE + QROWS * qr + threadIdx.x;
-    const float s = __ldcg(p.s + i);
-    const Vec<DIM> u = ldv<DIM>(p.U, i);
-    Vec<DIM> w;
-    df v[DIM];
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-      w.c[d] = fmaf(s, u.c[d], acc[0].c[d]);
-      v[d] = df_prod(w.c[d], u.c[d]);
-    }
-    stv<DIM>(p.W, i, w);
-    warp_sum_df<DIM>(v);
-    if (threadIdx.x == 0) {
-      float2* o = scal_slot(p, parity, R, qr);
-#pragma unroll
-      for (int k = 0; k < DIM; ++k) df_st(o + k, v[k]);
-    }
-  }
-};
-
-// One step of preconditioned CG in the single-reduction form of Chronopoulos
-// and Gear: p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s,
-// u = M^-1 r, w = L^W u.  The curvature (p', L^W p') of the next direction
-// p' = u + beta' p is needed before beta' is known; it is expanded as
-// (u,w) + beta' ((u,s) + (p,w)) + beta'^2 (p,s) from dot products taken here,
-// instead of the usual recurrence, which loses positivity in FP32.
-// Slots: [0,D) r.u  [D,2D) w.u  [2D,3D) r.r  [3D,4D) u.s  [4D,5D) p.w  [5D,6D) p.s
-template <int DIM>
-struct EpiCG {
-  const KParams& p;
-  float alpha[3], beta[3];
-  __device__ __forceinline__ void operator()(int R, int qr, int parity, float2*) {
-    Vec<DIM> acc[1];
-    reduce_rows<DIM, 1>(p, R, qr, acc);
-    if (threadIdx.x >= 32) return;
-    const int i = R * TILE + QROWS * qr + threadIdx.x;
-    const float s = __ldcg(p.s + i), is = __ldcg(p.inv_s + i);
-    Vec<DIM> u = ldv<DIM>(p.U, i), w = ldv<DIM>(p.W, i), pp = ldv<DIM>(p.P, i), sp = ldv<DIM>(p.S, i);
-    Vec<DIM> x = ldv<DIM>(p.Zw, i), r = ldv<DIM>(p.R, i);
-    df v[6 * DIM];
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-      const float pn = fmaf(beta[d], pp.c[d], u.c[d]);
-      const float sn = fmaf(beta[d], sp.c[d], w.c[d]);
-      const float un = cg_u(r.c[d], w.c[d], sp.c[d], is, alpha[d], beta[d]);
-      x.c[d] = fmaf(alpha[d], pn, x.c[d]);
-      r.c[d] = fmaf(-alpha[d], sn, r.c[d]);
-      pp.c[d] = pn;
-      sp.c[d] = sn;
-      u.c[d] = un;
-      w.c[d] = fmaf(s, un, acc[0].c[d]);
-      v[d] = df_prod(r.c[d], un);
-      v[DIM + d] = df_prod(w.c[d], un);
-      v[2 * DIM + d] = df_prod(r.c[d], r.c[d]);
-      v[3 * DIM + d] = df_prod(un, sn);
-      v[4 * DIM + d] = df_prod(pn, w.c[d]);
-      v[5 * DIM + d] = df_prod(pn, sn);
-    }
-    stv<DIM>(p.P, i, pp);
-    stv<DIM>(p.S, i, sp);
-    stv<DIM>(p.Zw, i, x);
-    stv<DIM>(p.R, i, r);
-    stv<DIM>(p.U, i, u);
-    stv<DIM>(p.W, i, w);
-    warp_sum_df<6 * DIM>(v);
-    if (threadIdx.x == 0) {
-      float2* o = scal_slot(p, parity, R, qr);
-#pragma unroll
-      for (int k = 0; k < 6 * DIM; ++k) df_st(o + k, v[k]);
-    }
-  }
-};
-
-// After the stress/RHS pass of the two candidates: store X^{k+1} (pinned),
-// the extrapolation X~ of Eq. (10) and both right-hand sides.
-template <int DIM, int NC>
-struct EpiK2 {
-  const KParams& p;
-  float z0[3];
-  float om;
-  __device__ __forceinline__ void operator()(int R, int qr, int, float2*) {
-    Vec<DIM> acc[NC];
-    reduce_rows<DIM, NC>(p, R, qr, acc);
-    if (threadIdx.x >= 32) return;
-    const int i = R * TILE + QROWS * qr + threadIdx.x;
-    const bool real = i < p.g.n;
-    const Vec<DIM> zw = ldv<DIM>(p.Zw, i), x = ldv<DIM>(p.X, i);
-    Vec<DIM> z, xt;
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-      z.c[d] = real ? zw.c[d] - z0[d] : 0.f;
-      xt.c[d] = real ? sor_xt(z.c[d], x.c[d], om) : 0.f;
-    }
-    stv<DIM>(p.Z, i, z);
-    stv<DIM>(p.Xt, i, xt);
-    stv<DIM>(p.Bz, i, acc[0]);
-    stv<DIM>(p.Bt, i, acc[NC - 1]);
-  }
-};
-
-// --------------------------------------------------------------------------
-// The kernel
-// --------------------------------------------------------------------------
-
-__device__ __forceinline__ PassSrc direct_src(const float* a) {
+__device__ __forceinline__ PassSrc direct_src(const float* a, int kind = SK_DIRECT) {
   PassSrc s;
+  s.kind = kind;
   s.a[0] = a;
   s.a[1] = s.a[2] = s.a[3] = nullptr;
 #pragma unroll
   for (int d = 0; d < 3; ++d) s.alpha[d] = s.beta[d] = s.z0[d] = 0.f;
   s.om = 0.f;
+  s.sel = 0;
   return s;
 }
 
+// --------------------------------------------------------------------------
+// The kernel
+// --------------------------------------------------------------------------
+
 template <int DIM, int CODE>
-__global__ void __launch_bounds__(CTA, (DIM == 3) ? 2 : 3) fd_main_kernel(KParams p) {
+__global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
   using L = SmemLayout<DIM, CODE>;
+  constexpr int DP = DimP<DIM>::v;
   extern __shared__ __align__(256) unsigned char smem[];
+  // The parameters are read from a shared-memory copy: values that the
+  // compiler cannot keep in registers across the out-of-line passes.
+  {
+    static_assert(sizeof(KParams) % 8 == 0, "KParams copy granularity");
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(&p_in);
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(smem + L::OFF_PARAMS);
+    for (int k = threadIdx.x; k < (int)(sizeof(KParams) / 8); k += CTA) dst[k] = src[k];
+    __syncthreads();
+  }
+  const KParams& p = *reinterpret_cast<const KParams*>(smem + L::OFF_PARAMS);
   const Geometry& g = p.g;
-  const int n = g.n, nb = g.nb, tid = threadIdx.x;
-  float2* red64 = reinterpret_cast<float2*>(smem + L::OFF_RED64);
-  Ctrl* ctrl = p.ctrl;
+  {
+    const int t0 = p_in.g.cta_task_ptr[blockIdx.x], t1 = p_in.g.cta_task_ptr[blockIdx.x + 1];
+    TaskDesc* ts = reinterpret_cast<TaskDesc*>(smem + L::OFF_TASKS);
+    for (int k = threadIdx.x; k < min(t1 - t0, MAX_CTA_TASKS); k += CTA) ts[k] = p_in.g.tasks[t0 + k];
+    __syncthreads();
+  }
+  // Everything below is re-derived from the shared-memory copy where it is
+  // used, so that nothing but loop counters stays live across a pass.
+#define n (p.g.n)
+#define nb (p.g.nb)
+#define tid ((int)threadIdx.x)
+#define vs ((size_t)p.g.n_pad * DP)
+#define acc0 (p.acc)           /* RHS of candidate 0, forces */
+#define acc1 (p.acc + vs)      /* RHS of candidate 1 */
+#define acc2 (p.acc + 2 * vs)  /* L^W products */
+#define red64 (reinterpret_cast<float2*>(smem + L::OFF_RED64))
+#define ctrl (p.ctrl)
 
   // --- set-up: mbarriers and the replicated lookup table
   {
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L::OFF_MISC);
     if (tid == 0) {
-      mbar_init(&mbar[0], 1);
-      mbar_init(&mbar[1], 1);
+      for (int k = 0; k < p.nbuf; ++k) mbar_init(&mbar[k], 1);
       fence_mbar_init();
     }
     if constexpr (CODE == CODE_U8) {
       uint4* dst = reinterpret_cast<uint4*>(smem + L::OFF_LUT);
       const uint4* srcl = reinterpret_cast<const uint4*>(p.lut);
-      for (int k = tid; k < p.lut_rows * 16; k += CTA) dst[k] = srcl[k];
+      for (int k = tid; k < p.lut_rows * (LUT_ROW / 16); k += CTA) dst[k] = srcl[k];
     }
     __syncthreads();
   }
@@ -1033,7 +1036,6 @@ __global__ void __launch_bounds__(CTA, (DIM == 3) ? 2 : 3) fd_main_kernel(KParam
     mark(tag);                                                                  \
   } while (0)
 #define FD_SYNC(tag) FD_SYNC_RED(tag, no_reduction)
-  // reductions run by the last CTA
   auto red_stress = [&](int nc) {
     return [&, nc] {
       if (nc == 2) reduce_slots_to_ctrl<2>(ctrl, p.sc_cta, gridDim.x, 2, red64);
@@ -1041,7 +1043,7 @@ __global__ void __launch_bounds__(CTA, (DIM == 3) ? 2 : 3) fd_main_kernel(KParam
     };
   };
 
-  // --- pack the caller layout into the padded internal array, check it
+  // --- pack the caller layout into the padded internal array, check it; clear the accumulators
   for (int R = blockIdx.x; R < nb; R += gridDim.x) {
     const int i = R * TILE + tid;
     Vec<DIM> v;
@@ -1054,11 +1056,13 @@ __global__ void __launch_bounds__(CTA, (DIM == 3) ? 2 : 3) fd_main_kernel(KParam
     }
     if (bad) set_error(ctrl, E_NONFINITE);
     stv<DIM>(p.X, i, v);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) stv<DIM>(p.acc + c * vs, i, vzero<DIM>());
   }
   FD_SYNC(1);
 
   if (p.mode == KM_ENERGY) {
-    if (!pair_pass<DIM, PM_STRESS, 1, CODE, SK_DIRECT>(p, smem, ps, direct_src(p.X))) return;
+    if (!pair_pass<DIM, PM_STRESS, 1, CODE>(p, smem, ps, direct_src(p.X), acc0)) return;
     FD_SYNC_RED(2, red_stress(1));
     if (blockIdx.x == 0 && tid == 0) {
       df f[1];
@@ -1073,10 +1077,15 @@ __global__ void __launch_bounds__(CTA, (DIM == 3) ? 2 : 3) fd_main_kernel(KParam
   }
 
   if (p.mode == KM_FORCES) {
-    EpiForces<DIM> e{p};
-    if (!pair_pass<DIM, PM_FORCES, 1, CODE, SK_DIRECT>(p, smem, ps, direct_src(p.X))) return;
+    if (!pair_pass<DIM, PM_FORCES, 1, CODE>(p, smem, ps, direct_src(p.X), acc0)) return;
     FD_SYNC(3);
-    rowblock_phase(p, e, 0, red64);
+    vertex_phase<0>(p, red64, [&](int i, df(&)[1]) {
+      const Vec<DIM> f = take_acc<DIM>(acc0, i);
+      if (i < n) {
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) p.x_out[(size_t)i * DIM + d] = f.c[d];
+      }
+    });
     if (blockIdx.x == 0 && tid == 0) {
       ctrl->pair_passes = 1.0;
       ctrl->stress_passes = 1.0;
@@ -1085,48 +1094,102 @@ __global__ void __launch_bounds__(CTA, (DIM == 3) ? 2 : 3) fd_main_kernel(KParam
   }
 
   // ======================= KM_RUN: Algorithm 2 ============================
-  // b = L^{X^0} X^0 and f(X^0) (right-hand side of Eq. (2-5), Eq. (1))
-  if (!pair_pass<DIM, PM_RHS, 1, CODE, SK_DIRECT>(p, smem, ps, direct_src(p.X))) return;
+  // The loop's scalars live in shared memory: thread 0 updates them after
+  // each grid barrier and the CTA reads them after a CTA barrier, so that the
+  // all-pairs passes keep their registers.  Every CTA computes the same
+  // values from the same reductions, so control flow is uniform over the grid.
+  RunState* rs = reinterpret_cast<RunState*>(smem + L::OFF_RUN);
+#define cgt2 ((float)(p.cg_tol * p.cg_tol))
+  // b = L^{X^0} X^0 (right-hand side of Eq. (2-5)) and f(X^0) (Eq. (1))
+  if (!pair_pass<DIM, PM_RHS, 1, CODE>(p, smem, ps, direct_src(p.X), acc0)) return;
   FD_SYNC_RED(4, red_stress(1));
-  {
-    EpiRhs0<DIM> e{p};
-    rowblock_phase(p, e, 0, red64);
-  }
-  double f_cur;
-  {
+  if (tid == 0) {
     df f[1];
     load_red<1>(ctrl, f);
-    f_cur = df_to_double(f[0]);
+    const double f0 = df_to_double(f[0]);
+    rs->f_cur = rs->f_new = f0;
+    rs->crit = 0.0;
+    rs->passes_mv = 0.0;
+    rs->passes_st = 1.0;
+    rs->cg_total = rs->cg_maxed = rs->cg_stalled = rs->n_acc = rs->it_outer = 0;
+    rs->accept = 0;
+    rs->om_prev = 0.f;
+    for (int d = 0; d < 3; ++d) rs->z0[d] = 0.f;
+    rs->stop = isfinite(f0) ? 0 : 1;
+    if (rs->stop) set_error(ctrl, E_NONFINITE);
+    if (blockIdx.x == 0) p.trace_f[0] = f0;
   }
-  if (!isfinite(f_cur)) {
-    set_error(ctrl, E_NONFINITE);
-    return;
-  }
-  if (blockIdx.x == 0 && tid == 0) p.trace_f[0] = f_cur;
+  __syncthreads();
+  if (rs->stop) return;
 
-  double passes_mv = 0.0, passes_st = 1.0;
-  int cg_total = 0, cg_maxed = 0, cg_stalled = 0, n_acc = 0;
-  double crit = 0.0;
-  bool accept = true;
-  double f_new = f_cur;
-  int it_outer = 0;
-  const float cgt2 = (float)(p.cg_tol * p.cg_tol);
-  const int nunits = 4 * nb;
   for (int k = 0;; ++k) {
-    // ---- start of the H step; also applies lines 6-8 of the previous iteration
-    float rz[DIM], rr[DIM], bb[DIM];
+    // ---- start of the H step.  x0 = X^0, or the candidate line 6 kept (formed
+    // on the fly from the CG solution and the previous layout); L^W x0.
     {
-      const float* x0src = (k == 0) ? p.X : (accept ? p.Xt : p.Z);
-      EpiInit<DIM> e{p, x0src, k == 0, accept};
-      const int par = ps.pass & 1;
-      if (!pair_pass<DIM, PM_MATVEC, 1, CODE, SK_DIRECT>(p, smem, ps, direct_src(x0src))) return;
-      passes_mv += 1.0;
+      PassSrc src = direct_src(k == 0 ? p.X : p.Zw, k == 0 ? SK_DIRECT : SK_SEL);
+      if (k > 0) {
+        src.a[1] = p.X;
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) src.z0[d] = rs->z0[d];
+        src.om = rs->om_prev;
+        src.sel = rs->accept;
+      }
+      if (!pair_pass<DIM, PM_MATVEC, 1, CODE>(p, smem, ps, src, acc2)) return;
+      if (tid == 0) rs->passes_mv += 1.0;
       FD_SYNC(5);
-      rowblock_phase(p, e, par, red64);
+      // r0 = b - L^W x0, u0 = M^-1 r0, p = s = 0; displacement sums of x0 against X^k.
+      // Scalars: [0,D) r.u  [D,2D) r.r  [2D,3D) b.b  [3D,4D) sum dx  [4D,5D) sum dx^2
+      //          [5D,6D) sum x  [6D,7D) sum x^2
+      const bool first = (k == 0), acc_t = rs->accept != 0;
+      const float om_p = rs->om_prev;
+      float z0[DIM];
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) z0[d] = rs->z0[d];
+      vertex_phase<7 * DIM>(p, red64, [&](int i, df(&v)[7 * DIM]) {
+        const bool real = i < n;
+        const Vec<DIM> xo = ldv<DIM>(p.X, i);
+        Vec<DIM> x0;
+        if (first) {
+          x0 = xo;
+        } else {
+          const Vec<DIM> zw = ldv<DIM>(p.Zw, i);
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) {
+            const float z = zw.c[d] - z0[d];
+            x0.c[d] = real ? (acc_t ? sor_xt(z, xo.c[d], om_p) : z) : 0.f;
+          }
+        }
+        const Vec<DIM> bz = take_acc<DIM>(acc0, i);
+        const Vec<DIM> bt = take_acc<DIM>(acc1, i);
+        const Vec<DIM> a = take_acc<DIM>(acc2, i);
+        const Vec<DIM> b = acc_t ? bt : bz;
+        const float s = __ldcg(p.s + i), is = __ldcg(p.inv_s + i);
+        Vec<DIM> r, u;
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+          r.c[d] = b.c[d] - fmaf(s, x0.c[d], -a.c[d]);
+          u.c[d] = is * r.c[d];
+          const df dx = real ? df_diff(x0.c[d], xo.c[d]) : df_of(0.f);
+          const float xv = real ? x0.c[d] : 0.f;
+          v[d] = df_add(v[d], df_prod(r.c[d], u.c[d]));
+          v[DIM + d] = df_add(v[DIM + d], df_prod(r.c[d], r.c[d]));
+          v[2 * DIM + d] = df_add(v[2 * DIM + d], df_prod(b.c[d], b.c[d]));
+          v[3 * DIM + d] = df_add(v[3 * DIM + d], dx);
+          v[4 * DIM + d] = df_add(v[4 * DIM + d], df_sqr(dx));
+          v[5 * DIM + d] = df_add(v[5 * DIM + d], df_of(xv));
+          v[6 * DIM + d] = df_add(v[6 * DIM + d], df_prod(xv, xv));
+        }
+        stv<DIM>(p.Zw, i, x0);
+        stv<DIM>(p.X, i, x0);
+        stv<DIM>(p.R, i, r);
+        stv<DIM>(p.U, i, u);
+        stv<DIM>(p.P, i, vzero<DIM>());
+        stv<DIM>(p.S, i, vzero<DIM>());
+      });
       // reduce the 7*DIM sums; the last CTA also evaluates the termination rule
-      const double fcur_k = f_cur, fnew_k = f_new;
+      const double fcur_k = rs->f_cur, fnew_k = rs->f_new;
       auto red_init = [&] {
-        reduce_slots_to_ctrl<7 * DIM>(ctrl, scal(p, par), nunits, SC_STRIDE, red64);
+        reduce_slots_to_ctrl<7 * DIM>(ctrl, p.sc, gridDim.x, SC_STRIDE, red64);
         if (threadIdx.x == 0) {
           double c = 0.0;
           if (p.stop == 0) {
@@ -1147,155 +1210,218 @@ __global__ void __launch_bounds__(CTA, (DIM == 3) ? 2 : 3) fd_main_kernel(KParam
         }
       };
       FD_SYNC_RED(9, red_init);
-      df v[3 * DIM];
-      load_red<3 * DIM>(ctrl, v);
-#pragma unroll
-      for (int d = 0; d < DIM; ++d) {
-        rz[d] = df_f(v[d]);
-        rr[d] = df_f(v[DIM + d]);
-        bb[d] = df_f(v[2 * DIM + d]);
-      }
-      if (k > 0) {
-        crit = __ldcg(&ctrl->red_d[0]);
-        if (blockIdx.x == 0 && tid == 0) p.trace_crit[k - 1] = crit;
-        f_cur = f_new;
-        it_outer = k;
-        if (crit < p.tol || k >= p.max_iter) break;
-      }
-    }
-    // ---- CG on L^W Z = b, one reduction per step
-    bool conv[DIM];
-    bool all = true;
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-      conv[d] = (rr[d] <= cgt2 * bb[d]);
-      all = all && conv[d];
-    }
-    int it = 0;
-    if (!all) {
-      float alpha[DIM], beta[DIM], gam[DIM];
-      {
-        EpiAU0<DIM> e{p};
-        const int par = ps.pass & 1;
-        if (!pair_pass<DIM, PM_MATVEC, 1, CODE, SK_DIRECT>(p, smem, ps, direct_src(p.U))) return;
-        passes_mv += 1.0;
-        FD_SYNC(6);
-        rowblock_phase(p, e, par, red64);
-        auto red_au0 = [&] { reduce_slots_to_ctrl<DIM>(ctrl, scal(p, par), nunits, SC_STRIDE, red64); };
-        FD_SYNC_RED(9, red_au0);
-        df dlv[DIM];
-        load_red<DIM>(ctrl, dlv);
-#pragma unroll
+      if (tid == 0) {
+        df v[3 * DIM];
+        load_red<3 * DIM>(ctrl, v);
+        int all = 1;
         for (int d = 0; d < DIM; ++d) {
-          const float dl = df_f(dlv[d]);
-          gam[d] = rz[d];
-          beta[d] = 0.f;
-          if (!conv[d] && !(dl > 0.f)) {
-            conv[d] = true;  // u0 carries no curvature: nothing to solve in this column
-            ++cg_stalled;
-          }
-          alpha[d] = conv[d] ? 0.f : gam[d] / dl;
+          rs->rz[d] = df_f(v[d]);
+          const float rr = df_f(v[DIM + d]);
+          rs->bb[d] = df_f(v[2 * DIM + d]);
+          rs->conv[d] = (rr <= cgt2 * rs->bb[d]) ? 1 : 0;
+          all = all && rs->conv[d];
+        }
+        rs->all_conv = all;
+        rs->it = 0;
+        rs->stop = 0;
+        if (k > 0) {
+          const double crit = __ldcg(&ctrl->red_d[0]);
+          rs->crit = crit;
+          if (blockIdx.x == 0) p.trace_crit[k - 1] = crit;
+          rs->f_cur = rs->f_new;
+          rs->it_outer = k;
+          rs->stop = (crit < p.tol || k >= p.max_iter) ? 1 : 0;
         }
       }
+      __syncthreads();
+      if (rs->stop) break;
+    }
+    // ---- CG on L^W Z = b, one reduction per step
+    if (!rs->all_conv) {
+      if (!pair_pass<DIM, PM_MATVEC, 1, CODE>(p, smem, ps, direct_src(p.U), acc2)) return;
+      if (tid == 0) rs->passes_mv += 1.0;
+      FD_SYNC(6);
+      // w0 = L^W u0 and delta0 = (w0, u0).  Slots [0,D).
+      vertex_phase<DIM>(p, red64, [&](int i, df(&v)[DIM]) {
+        const float s = __ldcg(p.s + i);
+        const Vec<DIM> u = ldv<DIM>(p.U, i);
+        const Vec<DIM> a = take_acc<DIM>(acc2, i);
+        Vec<DIM> w;
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+          w.c[d] = fmaf(s, u.c[d], -a.c[d]);
+          v[d] = df_add(v[d], df_prod(w.c[d], u.c[d]));
+        }
+        stv<DIM>(p.W, i, w);
+      });
+      auto red_au0 = [&] { reduce_slots_to_ctrl<DIM>(ctrl, p.sc, gridDim.x, SC_STRIDE, red64); };
+      FD_SYNC_RED(9, red_au0);
+      if (tid == 0) {
+        df dlv[DIM];
+        load_red<DIM>(ctrl, dlv);
+        for (int d = 0; d < DIM; ++d) {
+          const float dl = df_f(dlv[d]);
+          rs->gam[d] = rs->rz[d];
+          rs->beta[d] = 0.f;
+          if (!rs->conv[d] && !(dl > 0.f)) {
+            rs->conv[d] = 1;  // u0 carries no curvature: nothing to solve in this column
+            ++rs->cg_stalled;
+          }
+          rs->alpha[d] = rs->conv[d] ? 0.f : rs->gam[d] / dl;
+        }
+      }
+      __syncthreads();
       while (true) {
-        PassSrc src = direct_src(p.R);
+        // One step of preconditioned CG in the single-reduction form of
+        // Chronopoulos and Gear: p = u + beta p, s = w + beta s, x += alpha p,
+        // r -= alpha s, u = M^-1 r, w = L^W u.  The curvature (p', L^W p') of
+        // the next direction p' = u + beta' p is needed before beta' is known;
+        // it is expanded as (u,w) + beta' ((u,s) + (p,w)) + beta'^2 (p,s) from
+        // dot products taken here, instead of the usual recurrence, which
+        // loses positivity in FP32.
+        // Slots: [0,D) r.u  [D,2D) w.u  [2D,3D) r.r  [3D,4D) u.s  [4D,5D) p.w  [5D,6D) p.s
+        PassSrc src = direct_src(p.R, SK_CGU);
         src.a[1] = p.W;
         src.a[2] = p.S;
         src.a[3] = p.inv_s;
-        EpiCG<DIM> e{p, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
-          src.alpha[d] = e.alpha[d] = alpha[d];
-          src.beta[d] = e.beta[d] = beta[d];
+          src.alpha[d] = rs->alpha[d];
+          src.beta[d] = rs->beta[d];
         }
-        const int par = ps.pass & 1;
-        if (!pair_pass<DIM, PM_MATVEC, 1, CODE, SK_CGU>(p, smem, ps, src)) return;
-        passes_mv += 1.0;
-        ++it;
+        if (!pair_pass<DIM, PM_MATVEC, 1, CODE>(p, smem, ps, src, acc2)) return;
+        if (tid == 0) {
+          rs->passes_mv += 1.0;
+          ++rs->it;
+        }
         FD_SYNC(7);
-        rowblock_phase(p, e, par, red64);
-        auto red_cg = [&] { reduce_slots_to_ctrl<6 * DIM>(ctrl, scal(p, par), nunits, SC_STRIDE, red64); };
-        FD_SYNC_RED(9, red_cg);
-        df v[6 * DIM];
-        load_red<6 * DIM>(ctrl, v);
-        bool done = true;
+        float al[DIM], be[DIM];
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
-          const float gn = df_f(v[d]), dn = df_f(v[DIM + d]), rrn = df_f(v[2 * DIM + d]);
-          if (!conv[d]) {
-            conv[d] = (rrn <= cgt2 * bb[d]);
-            if (!conv[d]) {
-              const float bn = gn / gam[d];
-              const float pi = dn + bn * (df_f(v[3 * DIM + d]) + df_f(v[4 * DIM + d])) + bn * bn * df_f(v[5 * DIM + d]);
-              if (pi > 0.f && gn > 0.f) {
-                beta[d] = bn;
-                alpha[d] = gn / pi;
-              } else {
-                conv[d] = true;  // curvature lost to rounding: the solve has gone as far as FP32 allows
-                ++cg_stalled;
+          al[d] = src.alpha[d];
+          be[d] = src.beta[d];
+        }
+        vertex_phase<6 * DIM>(p, red64, [&](int i, df(&v)[6 * DIM]) {
+          const float s = __ldcg(p.s + i), is = __ldcg(p.inv_s + i);
+          Vec<DIM> u = ldv<DIM>(p.U, i), w = ldv<DIM>(p.W, i), pp = ldv<DIM>(p.P, i), sp = ldv<DIM>(p.S, i);
+          Vec<DIM> x = ldv<DIM>(p.Zw, i), r = ldv<DIM>(p.R, i);
+          const Vec<DIM> a = take_acc<DIM>(acc2, i);
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) {
+            const float pn = fmaf(be[d], pp.c[d], u.c[d]);
+            const float sn = fmaf(be[d], sp.c[d], w.c[d]);
+            const float un = cg_u(r.c[d], w.c[d], sp.c[d], is, al[d], be[d]);
+            x.c[d] = fmaf(al[d], pn, x.c[d]);
+            r.c[d] = fmaf(-al[d], sn, r.c[d]);
+            pp.c[d] = pn;
+            sp.c[d] = sn;
+            u.c[d] = un;
+            w.c[d] = fmaf(s, un, -a.c[d]);
+            v[d] = df_add(v[d], df_prod(r.c[d], un));
+            v[DIM + d] = df_add(v[DIM + d], df_prod(w.c[d], un));
+            v[2 * DIM + d] = df_add(v[2 * DIM + d], df_prod(r.c[d], r.c[d]));
+            v[3 * DIM + d] = df_add(v[3 * DIM + d], df_prod(un, sn));
+            v[4 * DIM + d] = df_add(v[4 * DIM + d], df_prod(pn, w.c[d]));
+            v[5 * DIM + d] = df_add(v[5 * DIM + d], df_prod(pn, sn));
+          }
+          stv<DIM>(p.P, i, pp);
+          stv<DIM>(p.S, i, sp);
+          stv<DIM>(p.Zw, i, x);
+          stv<DIM>(p.R, i, r);
+          stv<DIM>(p.U, i, u);
+          stv<DIM>(p.W, i, w);
+        });
+        auto red_cg = [&] { reduce_slots_to_ctrl<6 * DIM>(ctrl, p.sc, gridDim.x, SC_STRIDE, red64); };
+        FD_SYNC_RED(9, red_cg);
+        if (tid == 0) {
+          df v[6 * DIM];
+          load_red<6 * DIM>(ctrl, v);
+          int done = 1;
+          for (int d = 0; d < DIM; ++d) {
+            const float gn = df_f(v[d]), dn = df_f(v[DIM + d]), rrn = df_f(v[2 * DIM + d]);
+            if (!rs->conv[d]) {
+              rs->conv[d] = (rrn <= cgt2 * rs->bb[d]) ? 1 : 0;
+              if (!rs->conv[d]) {
+                const float bn = gn / rs->gam[d];
+                const float pi =
+                    dn + bn * (df_f(v[3 * DIM + d]) + df_f(v[4 * DIM + d])) + bn * bn * df_f(v[5 * DIM + d]);
+                if (pi > 0.f && gn > 0.f) {
+                  rs->beta[d] = bn;
+                  rs->alpha[d] = gn / pi;
+                } else {
+                  rs->conv[d] = 1;  // curvature lost to rounding: the solve has gone as far as FP32 allows
+                  ++rs->cg_stalled;
+                }
+              }
+              if (rs->conv[d]) {
+                rs->alpha[d] = 0.f;
+                rs->beta[d] = 0.f;
               }
             }
-            if (conv[d]) {
-              alpha[d] = 0.f;
-              beta[d] = 0.f;
-            }
+            rs->gam[d] = gn;
+            done = done && rs->conv[d];
           }
-          gam[d] = gn;
-          done = done && conv[d];
+          if (!done && rs->it >= p.cg_max) {
+            ++rs->cg_maxed;
+            done = 1;
+          }
+          rs->cg_done = done;
         }
-        if (done) break;
-        if (it >= p.cg_max) {
-          ++cg_maxed;
-          break;
+        __syncthreads();
+        if (rs->cg_done) break;
+      }
+    }
+
+    // ---- pin vertex 0 (Sec. 2), extrapolate (Eq. (10)), stress and RHS of both candidates
+    const double om = p.omega_seq[k];
+    const bool two = (om != 0.0);
+    PassSrc src = direct_src(p.Zw, SK_K2);
+    src.a[1] = p.X;
+    {
+      const Vec<DIM> zz = ldv<DIM>(p.Zw, 0);
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) src.z0[d] = zz.c[d];
+      src.om = (float)om;
+    }
+    __syncthreads();  // every thread has read the scalars of this iteration
+    if (tid == 0) {
+      rs->cg_total += rs->it;
+      for (int d = 0; d < DIM; ++d) rs->z0[d] = src.z0[d];
+      rs->om_prev = src.om;
+      rs->passes_st += two ? 2.0 : 1.0;
+    }
+    if (two) {
+      if (!pair_pass<DIM, PM_RHS, 2, CODE>(p, smem, ps, src, acc0)) return;
+      FD_SYNC_RED(8, red_stress(2));
+    } else {
+      if (!pair_pass<DIM, PM_RHS, 1, CODE>(p, smem, ps, src, acc0)) return;
+      FD_SYNC_RED(8, red_stress(1));
+    }
+    if (tid == 0) {
+      df fz[2];
+      load_red<2>(ctrl, fz);
+      const double fZ = df_to_double(fz[0]);
+      const double fT = two ? df_to_double(fz[1]) : fZ;
+      if (!isfinite(fZ) || !isfinite(fT)) {
+        set_error(ctrl, E_NONFINITE);
+        rs->stop = 1;
+      } else {
+        // line 6 (ties accept).  With omega = 0 the two candidates coincide and
+        // X^{k+1} is kept as it is (the test is trivially true).
+        const bool accept = two && (fT <= fZ);
+        rs->accept = accept ? 1 : 0;
+        rs->f_new = accept ? fT : fZ;
+        if (accept || !two) ++rs->n_acc;
+        if (blockIdx.x == 0) {
+          p.trace_f[k + 1] = rs->f_new;
+          p.trace_acc[k] = (accept || !two) ? 1 : 0;
+          p.trace_om[k] = om;
+          p.trace_cg[k] = rs->it;
         }
       }
     }
-    cg_total += it;
-
-    // ---- pin vertex 0 (Sec. 2), extrapolate (Eq. (10)), stress and RHS of both
-    const double om = p.omega_seq[k];
-    const bool two = (om != 0.0);
-    PassSrc src = direct_src(p.Zw);
-    src.a[1] = p.X;
-    {
-      const Vec<DIM> z0 = ldv<DIM>(p.Zw, 0);
-#pragma unroll
-      for (int d = 0; d < DIM; ++d) src.z0[d] = z0.c[d];
-      src.om = (float)om;
-    }
-    if (two) {
-      EpiK2<DIM, 2> e{p, {src.z0[0], src.z0[1], src.z0[2]}, src.om};
-      if (!pair_pass<DIM, PM_RHS, 2, CODE, SK_K2>(p, smem, ps, src)) return;
-      passes_st += 2.0;
-      FD_SYNC_RED(8, red_stress(2));
-      rowblock_phase(p, e, 0, red64);
-    } else {
-      EpiK2<DIM, 1> e{p, {src.z0[0], src.z0[1], src.z0[2]}, src.om};
-      if (!pair_pass<DIM, PM_RHS, 1, CODE, SK_K2>(p, smem, ps, src)) return;
-      passes_st += 1.0;
-      FD_SYNC_RED(8, red_stress(1));
-      rowblock_phase(p, e, 0, red64);
-    }
-    df fz[2];
-    load_red<2>(ctrl, fz);
-    FD_SYNC(9);  // Z, X~ and their right-hand sides are complete
-    const double fZ = df_to_double(fz[0]);
-    const double fT = two ? df_to_double(fz[1]) : fZ;
-    if (!isfinite(fZ) || !isfinite(fT)) {
-      set_error(ctrl, E_NONFINITE);
-      return;
-    }
-    // line 6 (ties accept).  With omega = 0 the two candidates coincide and
-    // X^{k+1} is kept as it is (the test is trivially true).
-    accept = two && (fT <= fZ);
-    f_new = accept ? fT : fZ;
-    if (accept || !two) ++n_acc;
-    if (blockIdx.x == 0 && tid == 0) {
-      p.trace_f[k + 1] = f_new;
-      p.trace_acc[k] = (accept || !two) ? 1 : 0;
-      p.trace_om[k] = om;
-      p.trace_cg[k] = it;
-    }
+    __syncthreads();
+    if (rs->stop) return;
   }
 
   // --- output: X holds the layout accepted by the last iteration
@@ -1308,19 +1434,29 @@ __global__ void __launch_bounds__(CTA, (DIM == 3) ? 2 : 3) fd_main_kernel(KParam
     }
   }
   if (blockIdx.x == 0 && tid == 0) {
-    ctrl->iters = it_outer;
-    ctrl->cg_steps = cg_total;
-    ctrl->cg_maxed = cg_maxed;
-    ctrl->cg_stalled = cg_stalled;
-    ctrl->accepted = n_acc;
-    ctrl->f_final = f_cur;
-    ctrl->crit_final = crit;
-    ctrl->pair_passes = passes_mv + passes_st;
-    ctrl->matvec_passes = passes_mv;
-    ctrl->stress_passes = passes_st;
+    ctrl->iters = rs->it_outer;
+    ctrl->cg_steps = rs->cg_total;
+    ctrl->cg_maxed = rs->cg_maxed;
+    ctrl->cg_stalled = rs->cg_stalled;
+    ctrl->accepted = rs->n_acc;
+    ctrl->f_final = rs->f_cur;
+    ctrl->crit_final = rs->crit;
+    ctrl->pair_passes = rs->passes_mv + rs->passes_st;
+    ctrl->matvec_passes = rs->passes_mv;
+    ctrl->stress_passes = rs->passes_st;
   }
 #undef FD_SYNC
 #undef FD_SYNC_RED
+#undef n
+#undef nb
+#undef tid
+#undef vs
+#undef acc0
+#undef acc1
+#undef acc2
+#undef red64
+#undef ctrl
+#undef cgt2
 }
 
 }  // namespace fdl

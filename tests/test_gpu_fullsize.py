@@ -1,0 +1,127 @@
+"""Parity at the benchmark's full sizes, in the benchmark's launch configuration.
+
+The graphs are the benchmark workload (Erdos-Renyi n=10,000 mean degree 6,
+Delaunay mesh of 20,000 points, random binary tree n=16,383; 2-D, X^0 uniform
+in [0,1]^2 from seed 0, unreachable pairs at (largest finite d) + 1) laid out
+with the default grid of the library.  The FP64 oracle cannot hold these
+problems densely, so it is compared on what it can compute one by one:
+sampled distance rows (one BFS each), sampled force rows, the stress by
+streaming one BFS row at a time, and the majorization residual of one H step
+(Eq. (2-5)) at sampled rows.  Tolerances are the ones of the small-size parity
+tests; the residual bound is derived in ``test_h_step_residual_sampled``.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1711_01228_gb300 import api, build, synth
+
+pytestmark = pytest.mark.gpu
+
+WORKLOADS = ("er10k", "delaunay20k", "tree16k")
+NSAMPLE = 24
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    api.lib()
+
+
+def _fill_value(rp, ci):
+    """(largest finite hop distance) + 1, or -1 for a connected graph."""
+    n = len(rp) - 1
+    d0 = oracle.bfs_row(rp, ci, 0)
+    if np.all(d0 >= 0):
+        return -1.0
+    m = 0
+    for s in range(n):
+        d = oracle.bfs_row(rp, ci, s)
+        m = max(m, int(d.max()))
+    return float(m + 1)
+
+
+class _Case:
+    def __init__(self, name):
+        self.name = name
+        self.rp, self.ci = synth.workload(name)
+        self.n = len(self.rp) - 1
+        self.X0 = synth.initial_layout(self.n, 2, 0)
+        self.fill = _fill_value(self.rp, self.ci)
+        rng = np.random.default_rng(2024)
+        self.rows = np.unique(np.concatenate([[0, 1, self.n - 1], rng.choice(self.n, NSAMPLE, replace=False)]))
+        self._drow = {}
+
+    def drow(self, i):
+        if i not in self._drow:
+            d = oracle.bfs_row(self.rp, self.ci, int(i)).astype(np.float64)
+            d[d < 0] = self.fill
+            self._drow[i] = d
+        return self._drow[i]
+
+
+@pytest.fixture(scope="module", params=WORKLOADS)
+def case(request):
+    c = _Case(request.param)
+    c.L = api.Layout(c.rp, c.ci, dim=2, disconnected_policy=1)
+    yield c
+    c.L.close()
+
+
+def test_distance_rows_sampled(case):
+    for i in case.rows:
+        got = case.L.distance_rows(int(i), 1)[0]
+        assert np.array_equal(got, case.drow(i)), f"row {i}"
+
+
+def test_energy_full(case):
+    f = case.L.energy(case.X0)
+    f_ref = oracle.stress_stream(case.X0, case.rp, case.ci, case.fill)
+    assert f == pytest.approx(f_ref, rel=1e-5)
+
+
+def test_force_rows_sampled(case):
+    F = case.L.forces(case.X0).astype(np.float64)
+    got = F[case.rows]
+    ref = np.stack([oracle.force_row(case.X0, int(i), case.drow(i)) for i in case.rows])
+    assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref)
+
+
+def test_h_step_residual_sampled(case):
+    """One H step (omega = 0): Z solves L^W Z = L^X X^0 (Eq. (2-5)) with vertex 0 at 0.
+
+    The solver stops at ||r|| <= 1e-6 ||b|| on its own residual; storing Z in
+    FP32 adds at most eps32 * sum_j w_ij (|z_i| + |z_j|) per row.  Both bounds
+    are checked at the sampled rows with a factor 4 for the solver's FP32
+    recurrence drift: |r_i| <= 4 * (1e-6 ||b||_rms + eps32 * sum_j w_ij (|z_i| + |z_j|)).
+    """
+    X = case.X0.copy()
+    case.L.sor_step(X, k=0, omega=0.0, cg_tol=1e-6, cg_max=500)
+    assert np.all(X[0] == 0.0)
+    Z = X.astype(np.float64)
+    eps32 = np.finfo(np.float32).eps
+    b_rows, r_rows, floor = [], [], []
+    for i in case.rows:
+        d = case.drow(i)
+        b = oracle.rhs_row(case.X0, int(i), d)
+        lwz = oracle.rhs_row(Z, int(i), d) - oracle.force_row(Z, int(i), d)  # (L^Z - (L^Z - L^W)) Z
+        w = np.where(d > 0, 1.0 / np.where(d > 0, d, 1.0) ** 2, 0.0)
+        floor.append(eps32 * float(np.sum(w * (np.abs(Z[i]).sum() + np.abs(Z).sum(axis=1)))))
+        b_rows.append(b)
+        r_rows.append(lwz - b)
+    b_rms = np.sqrt(np.mean(np.sum(np.square(b_rows), axis=1)))
+    for k, i in enumerate(case.rows):
+        bound = 4.0 * (1e-6 * b_rms + floor[k])
+        assert np.linalg.norm(r_rows[k]) <= bound, f"row {i}: |r|={np.linalg.norm(r_rows[k])} bound={bound}"
+
+
+def test_short_run_consistent(case):
+    """Five iterations of Algorithm 2 at omega = 0.5 in the benchmark's launch:
+    the stress trace never increases (Prop. 2.2, line 6) and the reported final
+    stress is the oracle's stress of the returned layout."""
+    X = case.X0.copy()
+    r = case.L.run(X, trace=True, omega=0.5, tol=0.0, max_iter=5)
+    assert r.iterations == 5
+    assert np.all(np.diff(r.trace_f) <= 1e-6 * r.trace_f[:-1])
+    f_ref = oracle.stress_stream(X, case.rp, case.ci, case.fill)
+    assert r.stress == pytest.approx(f_ref, rel=1e-5)
