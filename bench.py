@@ -41,6 +41,37 @@ def _env_rank():
         os.environ.get("LOCAL_RANK", "0"))
 
 
+KERNEL_SOURCES = ("fd_internal.cuh", "fd_solver.cuh", "fd_solver_d2.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fd_main_kernel_bench_traffic.txt")
+
+
+def kernel_hash() -> str:
+    """Hash of the layout kernel's sources: DRAM counters taken from another
+    version of the kernel do not describe this one."""
+    import hashlib
+    h = hashlib.sha1()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1711_01228_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload: str):
+    """DRAM bytes (read + write) per layout-kernel launch of this workload, from
+    the committed ncu capture, or None when the kernel has changed since."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    kv = {}
+    with open(TRAFFIC_FILE) as f:
+        for line in f:
+            if "=" in line and not line.startswith("#"):
+                k, v = line.split("=", 1)
+                kv[k.strip()] = v.strip()
+    if kv.get("kernel_hash") != kernel_hash() or kv.get("workload") != workload:
+        return None
+    return float(kv["dram_bytes_per_launch"])
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -226,7 +257,9 @@ def run_ours(args, rank, world, local_rank):
         "cg_steps_per_sor_iteration": acc["cg"] / max(acc["iters"], 1),
         "gpu_launches": acc["n_launch_total"],
         "roofline": {"bound": "alu", "kernel": "fd_main_kernel", "achieved": achieved, "peak": fp32_peak,
-                     "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                     "traffic": measured_traffic(",".join(args.workload.split(","))),
+                     "traffic_unit": "DRAM bytes per launch (ncu, read + write)",
                      "peak_note": f"FP32 CUDA cores {sms} SMs x 128 x 2 flop at {clk:.0f} MHz ({src} max clock)"},
         "apsp": {"kernel": "bfs_batch_kernel", "ms_per_step": acc["apsp_ms"] / args.steps},
         "layout_kernel_ms_per_step": acc["kernel_ms"] / args.steps,

@@ -65,7 +65,8 @@ typedef enum {
 typedef enum {
   FD_OMEGA_FIXED = 0, /* omega constant over the run (Sec. 5.2.1); omega = 0 is Algorithm 1 */
   FD_OMEGA_PROB = 1,  /* roulette over P(0.5)=P(1)=0.3, P(1.5)=P(2)=0.2 (Sec. 5.2.3) */
-  FD_OMEGA_ENUM = 2   /* argmin of f over omega in {0, 0.5, ..., 9} (Sec. 5.2.2) */
+  FD_OMEGA_ENUM = 2   /* argmin of f over omega in {0, 0.5, ..., 9} (Sec. 5.2.2), ties to the smaller omega;
+                         X^{k+1} is the argmin ("accepted" when it is not omega = 0) */
 } fd_omega_strategy;
 
 /* Termination rule.  The paper leaves it open ("until some termination
@@ -197,7 +198,7 @@ fd_status fd_forces(fd_layout* h, const float* X, float* F_out);
  *   accepted   1 if the extrapolated layout was kept (host; may be NULL)
  *   crit_out   termination criterion of opt->stop (host; may be NULL)
  * Errors: FD_ERR_ARG, FD_ERR_NONFINITE, FD_ERR_CG_BREAKDOWN, FD_ERR_TIMEOUT,
- * FD_ERR_CUDA, FD_ERR_UNIMPLEMENTED. */
+ * FD_ERR_CUDA. */
 fd_status fd_sor_step(fd_layout* h, float* X, const fd_options* opt, int32_t k, double* f_out,
                       int32_t* accepted, double* crit_out);
 

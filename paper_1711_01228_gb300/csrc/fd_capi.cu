@@ -747,13 +747,15 @@ static fd_status run_impl(fd_layout* h, float* X, const fd_options* opt, int k0,
   if (!(opt->omega >= 0.0) || !std::isfinite(opt->omega) || max_iter < 1 || opt->cg_max < 0 ||
       !(opt->tol >= 0.0) || !(opt->cg_tol >= 0.0) || (opt->stop != FD_STOP_REL_DISP && opt->stop != FD_STOP_REL_STRESS))
     return FD_ERR_ARG;
-  if (opt->strategy == FD_OMEGA_ENUM) return FD_ERR_UNIMPLEMENTED;
-  if (opt->strategy != FD_OMEGA_FIXED && opt->strategy != FD_OMEGA_PROB) return FD_ERR_ARG;
+  if (opt->strategy != FD_OMEGA_FIXED && opt->strategy != FD_OMEGA_PROB && opt->strategy != FD_OMEGA_ENUM)
+    return FD_ERR_ARG;
   fd_status s = ensure_traces(h, max_iter);
   if (s != FD_OK) return s;
   std::vector<double> om(max_iter);
   for (int k = 0; k < max_iter; ++k)
-    om[k] = (opt->strategy == FD_OMEGA_PROB) ? omega_prob(opt->seed, (uint64_t)(k0 + k)) : opt->omega;
+    om[k] = (opt->strategy == FD_OMEGA_PROB)   ? omega_prob(opt->seed, (uint64_t)(k0 + k))
+            : (opt->strategy == FD_OMEGA_ENUM) ? 0.0
+                                               : opt->omega;
   FD_CK(cudaMemcpyAsync(h->d_omega, om.data(), max_iter * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   const float* dx = nullptr;
   if ((s = stage_input(h, X, &dx)) != FD_OK) return s;
@@ -768,6 +770,7 @@ static fd_status run_impl(fd_layout* h, float* X, const fd_options* opt, int k0,
   p.trace_cg = h->d_trace_cg;
   p.trace_crit = h->d_trace_crit;
   p.max_iter = max_iter;
+  p.enum_omega = (opt->strategy == FD_OMEGA_ENUM) ? 1 : 0;
   p.stop = opt->stop;
   p.cg_max = opt->cg_max;
   p.tol = opt->tol;

@@ -114,6 +114,7 @@ struct KParams {
   int* trace_cg;               // [max_iter]
   double* trace_crit;          // [max_iter]
   int max_iter, stop, cg_max;
+  int enum_omega;              // 1: omega is the argmin of f over {0, 0.5, ..., 9} each iteration (Sec. 5.2.2)
   double tol, cg_tol;
   long long timeout_ns;        // limit of every grid-barrier / mbarrier wait
   double* timeline;            // NULL, or [timeline_cap][2] {tag, ns} written by CTA 0 at each barrier

@@ -165,14 +165,25 @@ __device__ __forceinline__ void atomic_addv(float* a, int i, const Vec<DIM>& v) 
   }
 }
 
-enum PairMode { PM_STRESS = 0, PM_FORCES = 1, PM_RHS = 2, PM_MATVEC = 3 };
+// PM_ENUM: stress of the NENUM extrapolations (1 + omega) z - omega x,
+// omega = 0, 0.5, ..., 9, of one CG solution z (Sec. 5.2.2).
+enum PairMode { PM_STRESS = 0, PM_FORCES = 1, PM_RHS = 2, PM_MATVEC = 3, PM_ENUM = 4 };
+constexpr int NENUM = 19;
+constexpr float ENUM_STEP = 0.5f;
+
+// Stress sums of a pass: one per candidate, NENUM for PM_ENUM.
+template <int MODE, int NC>
+struct NStress {
+  static constexpr int v = (MODE == PM_ENUM) ? NENUM : NC;
+};
 
 // How a pass forms its vectors from the raw arrays it copies.
 enum SrcKind {
   SK_DIRECT = 0,  // v = a[0]
   SK_CGU = 1,     // u = inv_s * (r - alpha * (w + beta * s_prev)); a = {r, w, s_prev, inv_s}
   SK_K2 = 2,      // z = zw - z0 and (NC = 2) xt = (1 + omega) z - omega x; a = {zw, x}
-  SK_SEL = 3      // the candidate kept by line 6 of Algorithm 2: sel ? xt : z, from a = {zw, x}
+  SK_SEL = 3,     // the candidate kept by line 6 of Algorithm 2: sel ? xt : z, from a = {zw, x}
+  SK_ZX = 4       // z = zw - z0 and the previous layout x, from a = {zw, x}
 };
 
 // Raw arrays of a source kind.
@@ -257,6 +268,7 @@ struct PassArgs {
   const TaskDesc* tasks_s;  // ... and the first MAX_CTA_TASKS of them in shared memory
   Ctrl* ctrl;
   float2* sc_cta;
+  float2* sc;  // PM_ENUM: the per-CTA stress of each candidate
   long long timeout_ns;
   int n, n_pad, nb, ntasks, nbuf;  // ntasks: this CTA's
   int stage_base;                   // shared-memory offset of stage 0
@@ -453,7 +465,7 @@ template <int DIM, int MODE, int NC, int CODE, bool EDGE>
 __device__ __forceinline__ void tile_compute(const unsigned char* __restrict__ dt, const float* __restrict__ colv,
                                              const unsigned char* __restrict__ lut,
                                              Rows<DIM, NC, TileShape<DIM, MODE>::R>& rows, Vec<DIM> (&jout)[NC],
-                                             float (&st)[NC], int tid) {
+                                             float (&st)[NStress<MODE, NC>::v], int tid) {
   using TS = TileShape<DIM, MODE>;
   constexpr int R = TS::R, G = TS::G, CH = TS::CH;
   constexpr int DP = DimP<DIM>::v;
@@ -464,11 +476,13 @@ __device__ __forceinline__ void tile_compute(const unsigned char* __restrict__ d
   const unsigned off_k = 4u * (tid & 31), off_w = 128u + 4u * (tid & 31);
   // TINY keeps rsqrt finite for coincident points; it is below the FP32 resolution of r^2
   const f2x TINY2 = pk2(1e-30f, 1e-30f), NEG1 = pk2(-1.f, -1.f);
+  constexpr int NS = NStress<MODE, NC>::v;
   float jacc[CH][NC][DIM];
-  f2x stp[NC];
+  f2x stp[NS];
+#pragma unroll
+  for (int e = 0; e < NS; ++e) stp[e] = pk2(0.f, 0.f);
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
-    stp[c] = pk2(0.f, 0.f);
 #pragma unroll
     for (int h = 0; h < CH; ++h)
 #pragma unroll
@@ -535,13 +549,34 @@ __device__ __forceinline__ void tile_compute(const unsigned char* __restrict__ d
           V = pk2(i0, i1);
           W = pk2(i0 * i0, i1 * i1);
         }
-        if constexpr ((EDGE || CODE != CODE_U8) && (MODE == PM_STRESS || MODE == PM_RHS))
+        if constexpr ((EDGE || CODE != CODE_U8) && (MODE == PM_STRESS || MODE == PM_RHS || MODE == PM_ENUM))
           NEGM = pk2(lo2(V) > 0.f ? -1.f : 0.f, hi2(V) > 0.f ? -1.f : 0.f);
         if constexpr (MODE == PM_MATVEC) {
 #pragma unroll
           for (int d = 0; d < DIM; ++d) {
             rows.acc[0][d][a2] = fma2(W, P[0][d], rows.acc[0][d][a2]);
             J[0][d] = (a2 == 0) ? mul2(W, rows.x[0][d][a2]) : fma2(W, rows.x[0][d][a2], J[0][d]);
+          }
+        } else if constexpr (MODE == PM_ENUM) {
+          // candidate e: Delta = Delta_z + omega_e (Delta_z - Delta_x), omega_e = e / 2
+          f2x DZ[DIM], DD[DIM];
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) {
+            DZ[d] = sub2(rows.x[0][d][a2], P[0][d]);
+            DD[d] = sub2(DZ[d], sub2(rows.x[1][d][a2], P[1][d]));
+          }
+#pragma unroll
+          for (int e = 0; e < NENUM; ++e) {
+            const f2x OM = pk2(ENUM_STEP * e, ENUM_STEP * e);
+            f2x R2 = TINY2;
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) {
+              const f2x DE = fma2(OM, DD[d], DZ[d]);
+              R2 = fma2(DE, DE, R2);
+            }
+            const f2x RS = pk2(rsqrt_approx(lo2(R2)), rsqrt_approx(hi2(R2)));
+            const f2x TT = fma2(R2, mul2(RS, V), NEGM);  // r / d - 1
+            stp[e] = fma2(TT, TT, stp[e]);
           }
         } else {
 #pragma unroll
@@ -569,7 +604,7 @@ __device__ __forceinline__ void tile_compute(const unsigned char* __restrict__ d
           }
         }
       }
-      if constexpr (MODE != PM_STRESS) {
+      if constexpr (MODE != PM_STRESS && MODE != PM_ENUM) {
 #pragma unroll
         for (int c = 0; c < NC; ++c)
 #pragma unroll
@@ -583,9 +618,10 @@ __device__ __forceinline__ void tile_compute(const unsigned char* __restrict__ d
   }
   // chain h of lane q now holds column (q + h) mod G of the group: gather column q
 #pragma unroll
+  for (int e = 0; e < NS; ++e) st[e] = lo2(stp[e]) + hi2(stp[e]);
+#pragma unroll
   for (int c = 0; c < NC; ++c) {
-    st[c] = lo2(stp[c]) + hi2(stp[c]);
-    if constexpr (MODE != PM_STRESS) {
+    if constexpr (MODE != PM_STRESS && MODE != PM_ENUM) {
 #pragma unroll
       for (int d = 0; d < DIM; ++d) {
         float s = jacc[0][c][d];
@@ -613,7 +649,7 @@ __device__ __forceinline__ void form_inplace(const PassSrc& s, float* raw, int t
 #pragma unroll
     for (int d = 0; d < DIM; ++d) u.c[d] = cg_u(r.c[d], w.c[d], sp.c[d], is, s.alpha[d], s.beta[d]);
     sts_v<DIM>(raw, t, u);
-  } else if (kind == SK_K2 || kind == SK_SEL) {
+  } else if (kind == SK_K2 || kind == SK_SEL || kind == SK_ZX) {
     const Vec<DIM> zw = lds_v<DIM>(raw, t);
     Vec<DIM> z;
 #pragma unroll
@@ -714,7 +750,7 @@ static_assert(sizeof(PassCtl) <= SmemLayout<1, CODE_U8>::OFF_RUN - SmemLayout<1,
 struct RunState {
   double f_cur, f_new, crit, passes_mv, passes_st;
   int cg_total, cg_maxed, cg_stalled, n_acc, it_outer, it;
-  int accept, stop, all_conv, cg_done;
+  int accept, bsel, stop, all_conv, cg_done;
   int conv[3];
   float z0[3], om_prev;
   float alpha[3], beta[3], gam[3], rz[3], bb[3];
@@ -754,9 +790,10 @@ __device__ FD_PASS_ATTR bool pair_pass_impl(PairState* ps_io, float* acc) {
   float2* red64 = reinterpret_cast<float2*>(smem + L::OFF_RED64);
   const unsigned char* lut = smem + L::OFF_LUT;
   const int sb = p.stage_base;
-  float ssum[NC], scomp[NC];
+  constexpr int NS = NStress<MODE, NC>::v;
+  float ssum[NS], scomp[NS];
 #pragma unroll
-  for (int c = 0; c < NC; ++c) ssum[c] = scomp[c] = 0.f;
+  for (int c = 0; c < NS; ++c) ssum[c] = scomp[c] = 0.f;
   // vectors written before the last grid barrier are read below by bulk copies
   if (tid == 0) fence_proxy_async_global();
   const bool rev = (ps.pass & 1) != 0;
@@ -815,20 +852,20 @@ __device__ FD_PASS_ATTR bool pair_pass_impl(PairState* ps_io, float* acc) {
         }
     }
     Vec<DIM> jout[NC];
-    float st[NC];
+    float st[NS];
     const unsigned char* dt = smem + L::off_d(sb, s_it);
     const bool edge = (it.k == 0) || (g.n < g.n_pad && (I == g.nb - 1 || J == g.nb - 1));
-    if constexpr (MODE == PM_STRESS || MODE == PM_RHS || (MODE == PM_MATVEC && kMatvecRcp)) {
+    if constexpr (MODE == PM_STRESS || MODE == PM_RHS || MODE == PM_ENUM || (MODE == PM_MATVEC && kMatvecRcp)) {
       if (edge) tile_compute<DIM, MODE, NC, CODE, true>(dt, rawj, lut, rows, jout, st, tid);
       else tile_compute<DIM, MODE, NC, CODE, false>(dt, rawj, lut, rows, jout, st, tid);
     } else {
       tile_compute<DIM, MODE, NC, CODE, false>(dt, rawj, lut, rows, jout, st, tid);
     }
-    if constexpr (MODE == PM_STRESS || MODE == PM_RHS) {
+    if constexpr (MODE == PM_STRESS || MODE == PM_RHS || MODE == PM_ENUM) {
 #pragma unroll
-      for (int c = 0; c < NC; ++c) kahan_add(ssum[c], scomp[c], st[c]);
+      for (int c = 0; c < NS; ++c) kahan_add(ssum[c], scomp[c], st[c]);
     }
-    if constexpr (MODE != PM_STRESS) {
+    if constexpr (MODE != PM_STRESS && MODE != PM_ENUM) {
       // column sums: thread t holds column t of block J
       const int j = J * TILE + tid;
       if (j < g.n) {
@@ -881,15 +918,18 @@ __device__ FD_PASS_ATTR bool pair_pass_impl(PairState* ps_io, float* acc) {
     it.next(g);
     s_it = (s_it + 1 == nbuf) ? 0 : s_it + 1;
   }
-  // stress of this CTA's pairs (candidates 0 and 1), one double-float slot per CTA
-  if constexpr (MODE == PM_STRESS || MODE == PM_RHS) {
-    df v[NC];
+  // stress of this CTA's pairs (per candidate), double-float slots per CTA
+  if constexpr (MODE == PM_STRESS || MODE == PM_RHS || MODE == PM_ENUM) {
+    df v[NS];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) v[c] = df_add(df_of(ssum[c]), df_of(-scomp[c]));
-    cta_sum_multi<NC>(v, red64);
+    for (int c = 0; c < NS; ++c) v[c] = df_add(df_of(ssum[c]), df_of(-scomp[c]));
+    cta_sum_multi<NS>(v, red64);
     if (tid == 0) {
 #pragma unroll
-      for (int c = 0; c < NC; ++c) df_st(p.sc_cta + (size_t)blockIdx.x * 2 + c, v[c]);
+      for (int c = 0; c < NS; ++c) {
+        if constexpr (MODE == PM_ENUM) df_st(p.sc + (size_t)blockIdx.x * SC_STRIDE + c, v[c]);
+        else df_st(p.sc_cta + (size_t)blockIdx.x * 2 + c, v[c]);
+      }
     }
   }
   ps.pass += 1;
@@ -911,6 +951,7 @@ __device__ __forceinline__ bool pair_pass(const KParams& p, unsigned char* smem,
     a.tasks_s = reinterpret_cast<const TaskDesc*>(smem + L::OFF_TASKS);
     a.ctrl = p.ctrl;
     a.sc_cta = p.sc_cta;
+    a.sc = p.sc;
     a.timeout_ns = p.timeout_ns;
     a.n = p.g.n;
     a.n_pad = p.g.n_pad;
@@ -968,7 +1009,9 @@ __device__ __forceinline__ PassSrc direct_src(const float* a, int kind = SK_DIRE
 // The kernel
 // --------------------------------------------------------------------------
 
-template <int DIM, int CODE>
+// WITH_ENUM: the variant that also runs the enumerating strategy (its pass is
+// kept out of the other variant, whose passes then keep their registers).
+template <int DIM, int CODE, bool WITH_ENUM>
 __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
   using L = SmemLayout<DIM, CODE>;
   constexpr int DP = DimP<DIM>::v;
@@ -1113,6 +1156,7 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
     rs->passes_st = 1.0;
     rs->cg_total = rs->cg_maxed = rs->cg_stalled = rs->n_acc = rs->it_outer = 0;
     rs->accept = 0;
+    rs->bsel = 0;
     rs->om_prev = 0.f;
     for (int d = 0; d < 3; ++d) rs->z0[d] = 0.f;
     rs->stop = isfinite(f0) ? 0 : 1;
@@ -1140,7 +1184,7 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
       // r0 = b - L^W x0, u0 = M^-1 r0, p = s = 0; displacement sums of x0 against X^k.
       // Scalars: [0,D) r.u  [D,2D) r.r  [2D,3D) b.b  [3D,4D) sum dx  [4D,5D) sum dx^2
       //          [5D,6D) sum x  [6D,7D) sum x^2
-      const bool first = (k == 0), acc_t = rs->accept != 0;
+      const bool first = (k == 0), acc_t = rs->accept != 0, bsel = rs->bsel != 0;
       const float om_p = rs->om_prev;
       float z0[DIM];
 #pragma unroll
@@ -1162,7 +1206,7 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
         const Vec<DIM> bz = take_acc<DIM>(acc0, i);
         const Vec<DIM> bt = take_acc<DIM>(acc1, i);
         const Vec<DIM> a = take_acc<DIM>(acc2, i);
-        const Vec<DIM> b = acc_t ? bt : bz;
+        const Vec<DIM> b = bsel ? bt : bz;
         const float s = __ldcg(p.s + i), is = __ldcg(p.inv_s + i);
         Vec<DIM> r, u;
 #pragma unroll
@@ -1372,6 +1416,74 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
       }
     }
 
+    if (WITH_ENUM && p.enum_omega) {
+      // ---- enumerating strategy (Sec. 5.2.2): the stress of every
+      // (1 + omega) z - omega x, omega in {0, 0.5, ..., 9}, from one pass; the
+      // argmin (ties to the smaller omega) becomes X^{k+1}, and a second pass
+      // gives its right-hand side and stress.
+      PassSrc src = direct_src(p.Zw, SK_ZX);
+      src.a[1] = p.X;
+      const Vec<DIM> zz = ldv<DIM>(p.Zw, 0);
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) src.z0[d] = zz.c[d];
+      __syncthreads();  // every thread has read the scalars of this iteration
+      if (tid == 0) {
+        rs->cg_total += rs->it;
+        for (int d = 0; d < DIM; ++d) rs->z0[d] = src.z0[d];
+        rs->passes_st += (double)NENUM + 1.0;
+      }
+      if constexpr (WITH_ENUM) {
+        if (!pair_pass<DIM, PM_ENUM, 2, CODE>(p, smem, ps, src, acc0)) return;
+      }
+      auto red_enum = [&] { reduce_slots_to_ctrl<NENUM>(ctrl, p.sc, gridDim.x, SC_STRIDE, red64); };
+      FD_SYNC_RED(8, red_enum);
+      if (tid == 0) {
+        df fv[NENUM];
+        load_red<NENUM>(ctrl, fv);
+        int best = 0;
+        double fbest = df_to_double(fv[0]);
+        for (int e = 1; e < NENUM; ++e) {
+          const double fe = df_to_double(fv[e]);
+          if (fe < fbest) {
+            fbest = fe;
+            best = e;
+          }
+        }
+        rs->om_prev = ENUM_STEP * best;
+        rs->accept = (best > 0) ? 1 : 0;
+        rs->bsel = 0;
+      }
+      __syncthreads();
+      PassSrc sel = direct_src(p.Zw, SK_SEL);
+      sel.a[1] = p.X;
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) sel.z0[d] = src.z0[d];
+      sel.om = rs->om_prev;
+      sel.sel = rs->accept;
+      if (!pair_pass<DIM, PM_RHS, 1, CODE>(p, smem, ps, sel, acc0)) return;
+      FD_SYNC_RED(8, red_stress(1));
+      if (tid == 0) {
+        df fz[1];
+        load_red<1>(ctrl, fz);
+        const double fX = df_to_double(fz[0]);
+        if (!isfinite(fX)) {
+          set_error(ctrl, E_NONFINITE);
+          rs->stop = 1;
+        } else {
+          rs->f_new = fX;
+          if (rs->accept) ++rs->n_acc;
+          if (blockIdx.x == 0) {
+            p.trace_f[k + 1] = fX;
+            p.trace_acc[k] = rs->accept;
+            p.trace_om[k] = (double)rs->om_prev;
+            p.trace_cg[k] = rs->it;
+          }
+        }
+      }
+      __syncthreads();
+      if (rs->stop) return;
+      continue;
+    }
     // ---- pin vertex 0 (Sec. 2), extrapolate (Eq. (10)), stress and RHS of both candidates
     const double om = p.omega_seq[k];
     const bool two = (om != 0.0);
@@ -1410,6 +1522,7 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
         // X^{k+1} is kept as it is (the test is trivially true).
         const bool accept = two && (fT <= fZ);
         rs->accept = accept ? 1 : 0;
+        rs->bsel = rs->accept;
         rs->f_new = accept ? fT : fZ;
         if (accept || !two) ++rs->n_acc;
         if (blockIdx.x == 0) {

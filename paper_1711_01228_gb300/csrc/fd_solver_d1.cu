@@ -8,10 +8,17 @@ template <int CODE>
 static cudaError_t config_one(size_t lut_bytes, int nbuf, int* blocks_per_sm, size_t* smem) {
   using L = SmemLayout<1, CODE>;
   *smem = (size_t)L::bytes(nbuf, CODE == CODE_U8 ? (int)lut_bytes : 0);
-  cudaError_t e = cudaFuncSetAttribute(fd_main_kernel<1, CODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(fd_main_kernel<1, CODE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)*smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fd_main_kernel<1, CODE>, CTA, *smem);
+  e = cudaFuncSetAttribute(fd_main_kernel<1, CODE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
+  if (e != cudaSuccess) return e;
+  int b0 = 0, b1 = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, fd_main_kernel<1, CODE, false>, CTA, *smem);
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, fd_main_kernel<1, CODE, true>, CTA, *smem);
+  *blocks_per_sm = b0 < b1 ? b0 : b1;
+  return e;
 }
 
 cudaError_t main_config_d1(int code, size_t lut_bytes, int nbuf, int* blocks_per_sm, size_t* smem) {
@@ -21,8 +28,12 @@ cudaError_t main_config_d1(int code, size_t lut_bytes, int nbuf, int* blocks_per
 
 cudaError_t launch_main_d1(int code, const KParams& p, int grid, size_t smem, cudaStream_t st) {
   void* args[] = {const_cast<KParams*>(&p)};
-  const void* fn =
-      (code == CODE_U8) ? (const void*)fd_main_kernel<1, CODE_U8> : (const void*)fd_main_kernel<1, CODE_F32>;
+  const void* fn;
+  if (p.enum_omega)
+    fn = (code == CODE_U8) ? (const void*)fd_main_kernel<1, CODE_U8, true> : (const void*)fd_main_kernel<1, CODE_F32, true>;
+  else
+    fn = (code == CODE_U8) ? (const void*)fd_main_kernel<1, CODE_U8, false>
+                           : (const void*)fd_main_kernel<1, CODE_F32, false>;
   return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(CTA), args, smem, st);
 }
 

@@ -200,3 +200,19 @@ def test_many_tasks_per_cta(ctas, monkeypatch):
     Xn, fn, accn, _, _ = oracle.sor_step(X0.astype(np.float64), D, 0.5)
     assert acc == accn
     assert np.linalg.norm(X - Xn) <= 1e-4 * np.linalg.norm(Xn)
+
+
+def test_enumerating_strategy_matches_oracle():
+    # Sec. 5.2.2: omega = argmin of f over {0, 0.5, ..., 9}, ties to the smaller omega
+    rp, ci = synth.grid(10, 10)
+    D = _dense(rp, ci)
+    X0 = synth.initial_layout(100, 2, seed=4)
+    ref = oracle.sor_run(D, X0.astype(np.float64), strategy=oracle.OMEGA_ENUM, tol=1e-4, max_iter=60)
+    X = X0.copy()
+    with api.Layout(rp, ci, dim=2) as L:
+        r = L.run(X, trace=True, strategy=api.OMEGA_ENUM, tol=1e-4, max_iter=60)
+    k = min(5, r.iterations, ref.iterations)
+    assert np.array_equal(r.omega[:k], np.array(ref.trace_omega[:k]))
+    assert r.stress == pytest.approx(ref.stress, rel=1e-4)
+    assert abs(r.iterations - ref.iterations) <= max(1, math.ceil(0.02 * ref.iterations))
+    assert np.all(np.diff(r.trace_f) <= 1e-6 * r.trace_f[:-1])
