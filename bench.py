@@ -130,12 +130,12 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_inputs(names, seed=0):
+def make_inputs(names, dim=2, seed=0):
     out = []
     for nm in names:
         rp, ci = synth.workload(nm, seed)
         n = len(rp) - 1
-        out.append((nm, rp, ci, synth.initial_layout(n, 2, seed)))
+        out.append((nm, rp, ci, synth.initial_layout(n, dim, seed)))
     return out
 
 
@@ -154,7 +154,7 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
-    inputs = make_inputs(args.workload.split(","))
+    inputs = make_inputs(args.workload.split(","), args.dim)
     oms = omegas(args.sweep)
     dev_inputs = [(nm, torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev), torch.from_numpy(x0).to(dev))
                   for nm, rp, ci, x0 in inputs]
@@ -164,9 +164,9 @@ def run_ours(args, rank, world, local_rank):
     def one_step(acc, host=False):
         for (nm, rp, ci, x0), (_, rpd, cid, x0d) in zip(inputs, dev_inputs):
             if host:
-                L = api.Layout(rp, ci, dim=2, disconnected_policy=1)
+                L = api.Layout(rp, ci, dim=args.dim, disconnected_policy=1)
             else:
-                L = api.Layout(rpd, cid, dim=2, disconnected_policy=1, stream=stream.cuda_stream)
+                L = api.Layout(rpd, cid, dim=args.dim, disconnected_policy=1, stream=stream.cuda_stream)
             info = L.info()
             acc["apsp_ms"] += info["apsp_ms"]
             acc["h2d"] += rp.nbytes + ci.nbytes
@@ -184,7 +184,7 @@ def run_ours(args, rank, world, local_rank):
                 acc["iters"] += st["iterations"]
                 acc["kernel_ms"] += st["kernel_ms"]
                 acc["launches"] += 1
-                acc["flops"] += st["pairs"] * (st["matvec_passes"] * FLOP_MV[2] + st["stress_passes"] * FLOP_K2[2])
+                acc["flops"] += st["pairs"] * (st["matvec_passes"] * FLOP_MV[args.dim] + st["stress_passes"] * FLOP_K2[args.dim])
                 acc["cg"] += st["cg_steps"]
                 acc["runs"].append((nm, om, st["iterations"], st["cg_steps"], st["final_stress"]))
             acc["n_launch_total"] += 4 + len(oms)  # BFS, fill, row sums, + one layout kernel per run
@@ -249,7 +249,7 @@ def run_ours(args, rank, world, local_rank):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": "+".join(args.workload.split(",")) + " 2-D, X0 U[0,1]^2 seed 0, omega_c "
+        "config": {"workload": "+".join(args.workload.split(",")) + f" {args.dim}-D, X0 U[0,1]^{args.dim} seed 0, omega_c "
                    + ("1.0-1.9 sweep" if args.sweep else "1.5") + ", rel-disp tol 1e-4, max 1000 iters",
                    "graphs": {nm: {"n": len(rp) - 1, "m": int(rp[-1]) // 2} for nm, rp, _, _ in inputs},
                    "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
@@ -326,6 +326,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass")
     ap.add_argument("--max-iter", type=int, default=1000, help="iteration cap per run (1000 = the workload)")
+    ap.add_argument("--dim", type=int, default=2, choices=[1, 2, 3], help="layout dimension (2 = the workload)")
     args = ap.parse_args()
     rank, world, local_rank = _env_rank()
     if world > 1:
