@@ -244,6 +244,108 @@ fd_status fd_last_stats(const fd_layout* h, fd_stats* stats);
 fd_status fd_timeline_enable(fd_layout* h, int32_t cap);
 fd_status fd_timeline_read(fd_layout* h, double* out, int32_t cap, int32_t* count);
 
+/* ------------------------------------------------------------------------
+ * Batched form: many independent small graphs laid out in one persistent
+ * kernel launch.  Each graph runs the same Algorithm 2 as fd_run (H step by
+ * CG on Eq. (2-5), extrapolation Eq. (10), acceptance test of line 6, the
+ * termination rule of fd_stop_rule) and stops on its own criterion; graphs
+ * share nothing but the launch.
+ * ------------------------------------------------------------------------ */
+
+typedef struct fd_batch fd_batch; /* opaque; owns every graph's distances and state */
+
+/* Largest graph of a batch (vertices). */
+#define FD_BATCH_MAX_N 2048
+
+/* Facts about a batch handle. */
+typedef struct {
+  int32_t num_graphs, dim;
+  int64_t total_vertices;  /* sum of the graphs' n */
+  int64_t num_tiles;       /* stored 128 x 128 tiles over all graphs */
+  int64_t distance_bytes;  /* device bytes of the uint8 distance tiles */
+  int32_t max_n;           /* largest graph */
+  int32_t max_diameter;    /* largest stored d_ij over all graphs (fill included) */
+  int32_t disconnected;    /* graphs with unreachable pairs (filled under policy 1) */
+  int32_t sm_count;
+  int32_t grid;            /* CTAs of the persistent kernel */
+  int32_t groups;          /* 128-thread tile groups per CTA (1 or 2) */
+  int32_t stages;          /* tiles in flight per group (2 or 3) */
+  int32_t graph_captured;  /* 1 once the launch runs from a captured CUDA graph */
+  double apsp_ms;          /* device time of the batched shortest-path kernels at creation */
+} fd_batch_info;
+
+/* Builds a batch of num_graphs undirected graphs in one concatenated CSR:
+ * graph g owns vertices graph_ptr[g] .. graph_ptr[g+1] - 1 (0-based,
+ * graph_ptr[0] = 0) and every edge of the CSR joins two vertices of the
+ * same graph.  Each graph has 1 .. FD_BATCH_MAX_N vertices.  Computes every
+ * graph's hop distances (bit-parallel BFS, one 64-source batch per CTA) and
+ * the row sums of its L^W; unit edge lengths only, hop diameter (fill
+ * included) at most 253.
+ *   graph_ptr  int32[num_graphs + 1], host or device
+ *   row_ptr    int32[N + 1] with N = graph_ptr[num_graphs], host or device
+ *   col_idx    int32[row_ptr[N]] global vertex ids, host or device
+ *   disconnected_policy, cuda_stream: as in fd_layout_create
+ * Errors: FD_ERR_ARG (sizes, a graph above FD_BATCH_MAX_N), FD_ERR_CSR
+ * (malformed, non-symmetric, or an edge between graphs), FD_ERR_DISCONNECTED,
+ * FD_ERR_UNIMPLEMENTED (a diameter above 253), FD_ERR_OOM, FD_ERR_CUDA. */
+fd_status fd_batch_create(fd_batch** out, int32_t num_graphs, int32_t dim, const int32_t* graph_ptr,
+                          const int32_t* row_ptr, const int32_t* col_idx, int32_t disconnected_policy,
+                          void* cuda_stream);
+
+/* Releases every resource of the batch (NULL is a no-op). */
+void fd_batch_destroy(fd_batch* b);
+
+/* Algorithm 2 on every graph of the batch, in one persistent launch (replayed
+ * from a captured CUDA graph after the first call with the same launch
+ * configuration).  X (float32 [N][dim], host or device; graph g's rows are
+ * graph_ptr[g] ..) holds every X^0 on entry and the final layouts on return.
+ *   opt        strategy FD_OMEGA_FIXED or FD_OMEGA_PROB (the same omega
+ *              sequence for every graph); FD_OMEGA_ENUM returns
+ *              FD_ERR_UNIMPLEMENTED.  tol, stop, max_iter, cg_tol, cg_max
+ *              apply to every graph.
+ *   omega      NULL (every graph uses opt->omega) or double[num_graphs]
+ *              (host or device): graph g's fixed omega (FD_OMEGA_FIXED)
+ *   iters      NULL or host int32[num_graphs]: iterations per graph
+ *   f_out      NULL or host double[num_graphs]: final stress per graph
+ * Per-graph failures (non-finite input or stress) are reported by
+ * fd_batch_results and make the call return FD_ERR_NONFINITE after every
+ * other graph has finished.  Errors: FD_ERR_ARG, FD_ERR_UNIMPLEMENTED,
+ * FD_ERR_NONFINITE, FD_ERR_TIMEOUT, FD_ERR_CUDA. */
+fd_status fd_batch_run(fd_batch* b, float* X, const fd_options* opt, const double* omega, int32_t* iters,
+                       double* f_out);
+
+/* Per-graph details of the last fd_batch_run, to host arrays of length
+ * num_graphs (any pointer may be NULL): fd_status of the graph, CG steps,
+ * accepted extrapolations, last termination criterion, L^W passes, stress
+ * passes (per candidate), and the device time (ms, %globaltimer) the CTA
+ * that ran the graph spent on it. */
+fd_status fd_batch_results(const fd_batch* b, int32_t* status, int32_t* cg_steps, int32_t* accepted, double* crit,
+                           double* matvec_passes, double* stress_passes, double* graph_ms);
+
+/* Chooses the launch shape of the persistent kernel (128-thread tile groups
+ * per CTA in {1, 2} x tiles in flight per group in {2, 3}) by timing each
+ * feasible shape on this batch: `probe_iter` iterations of fd_batch_run from
+ * X (host or device, left unchanged), best of `repeats` runs each.  The
+ * winner is kept for later runs; *groups and *stages receive it (may be
+ * NULL).  Errors: as fd_batch_run. */
+fd_status fd_batch_tune(fd_batch* b, const float* X, const fd_options* opt, int32_t probe_iter, int32_t repeats,
+                        int32_t* groups, int32_t* stages);
+
+/* Sets the launch shape directly (groups 1 or 2, stages 2 or 3).
+ * Errors: FD_ERR_ARG (infeasible shape). */
+fd_status fd_batch_set_shape(fd_batch* b, int32_t groups, int32_t stages);
+
+/* The hop distances of graph g as stored, float64 [n_g][n_g] host array
+ * (d_ii = 0).  Errors: FD_ERR_ARG, FD_ERR_OOM, FD_ERR_CUDA. */
+fd_status fd_batch_distances(fd_batch* b, int32_t g, double* out);
+
+/* Facts about the batch; statistics of its last run (sums over graphs:
+ * iterations, cg_steps, accepted, pair_passes weighted by each graph's
+ * pairs in `pairs` = sum over graphs of pair_passes_g * n_g (n_g - 1) / 2,
+ * kernel_ms of the one launch). */
+fd_status fd_batch_get_info(const fd_batch* b, fd_batch_info* info);
+fd_status fd_batch_last_stats(const fd_batch* b, fd_stats* stats);
+
 /* Status of the last failing call on the handle (FD_OK if none). */
 fd_status fd_last_error(const fd_layout* h);
 

@@ -55,10 +55,21 @@ class Info(ctypes.Structure):
                 ("apsp_ms", ctypes.c_double), ("stages", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("num_graphs", ctypes.c_int32), ("dim", ctypes.c_int32), ("total_vertices", ctypes.c_int64),
+                ("num_tiles", ctypes.c_int64), ("distance_bytes", ctypes.c_int64), ("max_n", ctypes.c_int32),
+                ("max_diameter", ctypes.c_int32), ("disconnected", ctypes.c_int32), ("sm_count", ctypes.c_int32),
+                ("grid", ctypes.c_int32), ("groups", ctypes.c_int32), ("stages", ctypes.c_int32),
+                ("graph_captured", ctypes.c_int32), ("apsp_ms", ctypes.c_double)]
+
+
 EXPORTED = ["fd_options_default", "fd_layout_create", "fd_layout_destroy", "fd_energy", "fd_forces",
             "fd_sor_step", "fd_run", "fd_run_trace", "fd_distance_rows", "fd_layout_info",
             "fd_last_stats", "fd_last_error", "fd_status_string", "fd_energy_noalloc", "fd_timeline_enable",
-            "fd_timeline_read"]
+            "fd_timeline_read", "fd_batch_create", "fd_batch_destroy", "fd_batch_run", "fd_batch_results",
+            "fd_batch_tune", "fd_batch_set_shape", "fd_batch_distances", "fd_batch_get_info",
+            "fd_batch_last_stats"]
+BATCH_MAX_N = 2048
 TIMELINE_TAGS = {1: "pack", 2: "stress", 3: "forces", 4: "rhs0", 5: "h_init", 6: "cg_au0", 7: "cg_step",
                  8: "candidates", 9: "vertex_phase"}
 NOALLOC_MAX_N = 524288
@@ -114,6 +125,24 @@ def lib():
     L.fd_timeline_enable.restype = i32
     L.fd_timeline_read.argtypes = [P, P, i32, ctypes.POINTER(i32)]
     L.fd_timeline_read.restype = i32
+    L.fd_batch_create.argtypes = [ctypes.POINTER(P), i32, i32, P, P, P, i32, P]
+    L.fd_batch_create.restype = i32
+    L.fd_batch_destroy.argtypes = [P]
+    L.fd_batch_destroy.restype = None
+    L.fd_batch_run.argtypes = [P, P, ctypes.POINTER(Options), P, P, P]
+    L.fd_batch_run.restype = i32
+    L.fd_batch_results.argtypes = [P, P, P, P, P, P, P, P]
+    L.fd_batch_results.restype = i32
+    L.fd_batch_tune.argtypes = [P, P, ctypes.POINTER(Options), i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    L.fd_batch_tune.restype = i32
+    L.fd_batch_set_shape.argtypes = [P, i32, i32]
+    L.fd_batch_set_shape.restype = i32
+    L.fd_batch_distances.argtypes = [P, i32, P]
+    L.fd_batch_distances.restype = i32
+    L.fd_batch_get_info.argtypes = [P, ctypes.POINTER(BatchInfo)]
+    L.fd_batch_get_info.restype = i32
+    L.fd_batch_last_stats.argtypes = [P, ctypes.POINTER(Stats)]
+    L.fd_batch_last_stats.restype = i32
     _LIB = L
     return L
 
@@ -133,7 +162,7 @@ def _ptr(a, dtype) -> int:
         return None
     if _is_torch(a):
         import torch
-        want = {np.float32: torch.float32, np.int32: torch.int32}[dtype]
+        want = {np.float32: torch.float32, np.int32: torch.int32, np.float64: torch.float64}[dtype]
         if a.dtype != want or not a.is_contiguous():
             raise TypeError(f"expected a contiguous {want} tensor")
         return a.data_ptr()
@@ -299,3 +328,143 @@ def energy_noalloc(X, D, stream=None) -> float:
     _check(lib().fd_energy_noalloc(_ptr(X, np.float32), _ptr(D, np.float32), n, dim, ctypes.addressof(f), st),
            "fd_energy_noalloc")
     return f.value
+
+
+@dataclass
+class BatchResult:
+    iterations: np.ndarray      # [G] iterations per graph
+    stress: np.ndarray          # [G] final stress per graph
+    status: np.ndarray          # [G] fd_status per graph
+    cg_steps: np.ndarray
+    accepted: np.ndarray
+    crit: np.ndarray
+    matvec_passes: np.ndarray
+    stress_passes: np.ndarray
+    graph_ms: np.ndarray        # [G] device time spent on each graph
+    stats: dict = field(default_factory=dict)
+
+
+class Batch:
+    """Many independent graphs (each at most BATCH_MAX_N vertices) laid out in
+    one persistent launch.
+
+    ``graph_ptr`` int32 [G+1] vertex offsets; ``row_ptr``/``col_idx`` the
+    concatenated int32 CSR with global vertex ids (edges stay inside graphs).
+    """
+
+    def __init__(self, graph_ptr, row_ptr, col_idx, dim: int = 2, disconnected_policy: int = 0, stream=None):
+        L = lib()
+        G = int(graph_ptr.shape[0]) - 1
+        h = ctypes.c_void_p()
+        st = None if stream is None else ctypes.c_void_p(int(stream))
+        status = L.fd_batch_create(ctypes.byref(h), G, int(dim), _ptr(graph_ptr, np.int32), _ptr(row_ptr, np.int32),
+                                   _ptr(col_idx, np.int32) if col_idx is not None and len(col_idx) else None,
+                                   int(disconnected_policy), st)
+        _check(status, "fd_batch_create")
+        self._h = h
+        self.G, self.dim = G, int(dim)
+        gp = graph_ptr.cpu().numpy() if _is_torch(graph_ptr) else np.asarray(graph_ptr)
+        self.sizes = np.diff(gp.astype(np.int64))
+        self.graph_ptr = gp.astype(np.int64)
+        self.N = int(gp[-1])
+
+    @classmethod
+    def from_graphs(cls, graphs, dim: int = 2, disconnected_policy: int = 0, stream=None):
+        """Batch from a list of (row_ptr, col_idx) numpy CSR pairs."""
+        gp, rp, ci = concat_graphs(graphs)
+        return cls(gp, rp, ci, dim=dim, disconnected_policy=disconnected_policy, stream=stream)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fd_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def info(self) -> dict:
+        i = BatchInfo()
+        _check(lib().fd_batch_get_info(self._h, ctypes.byref(i)), "fd_batch_get_info")
+        return {k: getattr(i, k) for k, _ in BatchInfo._fields_}
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(lib().fd_batch_last_stats(self._h, ctypes.byref(s)), "fd_batch_last_stats")
+        return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+    def distances(self, g: int) -> np.ndarray:
+        """Stored hop distances of graph g, [n_g, n_g] float64."""
+        n = int(self.sizes[g])
+        out = np.empty((n, n), dtype=np.float64)
+        _check(lib().fd_batch_distances(self._h, int(g), out.ctypes.data), "fd_batch_distances")
+        return out
+
+    def set_shape(self, groups: int, stages: int):
+        _check(lib().fd_batch_set_shape(self._h, int(groups), int(stages)), "fd_batch_set_shape")
+
+    def tune(self, X, probe_iter: int = 5, repeats: int = 2, **opts):
+        """Times every feasible launch shape on X and keeps the fastest."""
+        o = options(**opts)
+        g, s = ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().fd_batch_tune(self._h, _ptr(X, np.float32), ctypes.byref(o), int(probe_iter), int(repeats),
+                                   ctypes.byref(g), ctypes.byref(s)), "fd_batch_tune")
+        return g.value, s.value
+
+    def run(self, X, omega=None, check: bool = True, **opts) -> BatchResult:
+        """Algorithm 2 on every graph, in place on X ([N, dim] float32).
+        ``omega``: None (the default option), one number for every graph, or a
+        float64 array [G] of per-graph omegas."""
+        if tuple(X.shape) != (self.N, self.dim):
+            raise ValueError(f"X must have shape ({self.N}, {self.dim})")
+        G = self.G
+        om = None
+        if omega is not None:
+            if not _is_torch(omega) and np.ndim(omega) == 0:
+                opts["omega"] = float(omega)  # one omega for every graph
+            else:
+                om = omega if _is_torch(omega) else np.ascontiguousarray(omega, dtype=np.float64)
+                if tuple(om.shape) != (G,):
+                    raise ValueError(f"per-graph omega must have shape ({G},)")
+        o = options(**opts)
+        it = np.zeros(G, dtype=np.int32)
+        f = np.zeros(G, dtype=np.float64)
+        status = lib().fd_batch_run(self._h, _ptr(X, np.float32), ctypes.byref(o),
+                                    _ptr(om, np.float64) if om is not None else None, it.ctypes.data, f.ctypes.data)
+        if check:
+            _check(status, "fd_batch_run")
+        st = np.zeros(G, dtype=np.int32)
+        cg = np.zeros(G, dtype=np.int32)
+        acc = np.zeros(G, dtype=np.int32)
+        cr = np.zeros(G, dtype=np.float64)
+        mv = np.zeros(G, dtype=np.float64)
+        sp = np.zeros(G, dtype=np.float64)
+        gm = np.zeros(G, dtype=np.float64)
+        _check(lib().fd_batch_results(self._h, st.ctypes.data, cg.ctypes.data, acc.ctypes.data, cr.ctypes.data,
+                                      mv.ctypes.data, sp.ctypes.data, gm.ctypes.data), "fd_batch_results")
+        return BatchResult(iterations=it, stress=f, status=st, cg_steps=cg, accepted=acc, crit=cr,
+                           matvec_passes=mv, stress_passes=sp, graph_ms=gm, stats=self.stats())
+
+
+def concat_graphs(graphs):
+    """(graph_ptr, row_ptr, col_idx) of the disjoint union of CSR graphs."""
+    sizes = [len(rp) - 1 for rp, _ in graphs]
+    gp = np.zeros(len(graphs) + 1, dtype=np.int32)
+    gp[1:] = np.cumsum(sizes)
+    rps, cis = [np.zeros(1, dtype=np.int64)], []
+    e0 = 0
+    for (rp, ci), v0 in zip(graphs, gp[:-1]):
+        rps.append(np.asarray(rp[1:], dtype=np.int64) + e0)
+        cis.append(np.asarray(ci, dtype=np.int64) + int(v0))
+        e0 += int(rp[-1])
+    rp_all = np.concatenate(rps).astype(np.int32)
+    ci_all = np.concatenate(cis).astype(np.int32) if cis else np.zeros(0, dtype=np.int32)
+    return gp, rp_all, ci_all

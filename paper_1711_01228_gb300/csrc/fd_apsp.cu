@@ -263,6 +263,172 @@ __global__ void distance_rows_kernel(int n, int nb, const int* __restrict__ tile
   }
 }
 
+// ------------------------------------------------------------ batched form
+//
+// Many independent graphs of at most BMAX_N vertices, concatenated: graph g
+// owns vertices v0 .. v0 + n - 1 of the shared CSR (every edge stays inside
+// its graph) and the tiles t0 .. t0 + hr_tiles(nb) - 1 of the uint8 distance
+// pool.  One CTA runs the 64 searches of one work item (graph, first source)
+// with the "reached" words in shared memory.
+
+__global__ void __launch_bounds__(512) bfs_multi_kernel(const BGraph* __restrict__ graphs,
+                                                        const int2* __restrict__ items, int nitems,
+                                                        const int* __restrict__ row_ptr,
+                                                        const int* __restrict__ col_idx, unsigned char* D,
+                                                        int* maxlevel, int* overflow) {
+  extern __shared__ unsigned long long bw[];  // vis[n], fr[n], nx[n]
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int2 item = items[it];
+    const BGraph gr = graphs[item.x];
+    const int n = gr.n, nb = gr.nb, v0 = gr.v0, s0 = item.y;
+    unsigned long long* vis = bw;
+    unsigned long long* fr = bw + n;
+    unsigned long long* nx = fr + n;
+    const int nsrc = min(64, n - s0);
+    const unsigned long long full = (nsrc == 64) ? ~0ull : ((1ull << nsrc) - 1ull);
+    const int I = s0 / TILE, il0 = s0 % TILE;
+    const int LI = hr_len(nb, I), tb = hr_base(nb, I);
+    unsigned char* Dg = D + (size_t)gr.t0 * TILE * TILE;
+    for (int v = threadIdx.x; v < n; v += blockDim.x) {
+      const unsigned long long b = (v >= s0 && v < s0 + nsrc) ? (1ull << (v - s0)) : 0ull;
+      vis[v] = b;
+      fr[v] = b;
+    }
+    __syncthreads();
+    int level = 0;
+    while (true) {
+      ++level;
+      int any = 0;
+      for (int v = threadIdx.x; v < n; v += blockDim.x) {
+        const unsigned long long vs = vis[v];
+        unsigned long long nw = 0ull;
+        if (vs != full) {
+          unsigned long long acc = 0ull;
+          const int e1 = row_ptr[v0 + v + 1];
+          for (int e = row_ptr[v0 + v]; e < e1; ++e) acc |= fr[col_idx[e] - v0];
+          nw = acc & ~vs & full;
+          if (nw) {
+            vis[v] = vs | nw;
+            any = 1;
+            int k;
+            unsigned long long m = nw & owned_bits(v, s0, I, nb, LI, full, &k);
+            const int jl = v % TILE;
+            while (m) {
+              const int b = __ffsll((long long)m) - 1;
+              m &= m - 1ull;
+              put_code<CODE_U8>(Dg, tb + k, jl * TILE + il0 + b, (float)level, overflow);
+            }
+          }
+        }
+        nx[v] = nw;
+      }
+      any = __syncthreads_or(any);
+      if (!any) break;
+      unsigned long long* t = fr;
+      fr = nx;
+      nx = t;
+    }
+    if (threadIdx.x == 0) atomicMax(maxlevel + item.x, level - 1);
+    __syncthreads();
+  }
+}
+
+// Unreached pairs of every graph: counted per graph and, under policy 1,
+// given the graph's fill distance (largest finite d) + 1.  One CTA per tile.
+__global__ void __launch_bounds__(256) fill_multi_kernel(const BGraph* __restrict__ graphs,
+                                                         const int* __restrict__ tile_graph,
+                                                         const int2* __restrict__ tile_ik, long long ntiles,
+                                                         unsigned char* D, const int* __restrict__ maxlevel,
+                                                         int write, int* unreached, int* overflow) {
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int g = tile_graph[t];
+    const int2 ik = tile_ik[t];
+    const BGraph gr = graphs[g];
+    const int nb = gr.nb, n = gr.n;
+    const int J = (ik.x + ik.y) % nb;
+    const float fill = (float)(maxlevel[g] + 1);
+    unsigned char* Dt = D + (size_t)t * TILE * TILE;
+    int local = 0;
+    for (int off = threadIdx.x; off < TILE * TILE; off += blockDim.x) {
+      const int jl = off / TILE, il = off % TILE;
+      const int i = ik.x * TILE + il, j = J * TILE + jl;
+      const bool real = (i < n) && (j < n) && (ik.y > 0 || il < jl);
+      if (real && Dt[off] == 0) {
+        ++local;
+        if (write) {
+          if (fill > 255.f) {
+            Dt[off] = 255;
+            atomicExch(overflow, 1);
+          } else {
+            Dt[off] = (unsigned char)fill;
+          }
+        }
+      }
+    }
+    if (local) atomicAdd(unreached + g, local);
+  }
+}
+
+// s_i = sum_{j != i} w_ij of every graph (FP64 accumulation); work item =
+// (graph, block row R), thread t = vertex R * TILE + t.
+__global__ void __launch_bounds__(TILE) rowsum_multi_kernel(const BGraph* __restrict__ graphs,
+                                                            const int2* __restrict__ items, int nitems,
+                                                            const unsigned char* D, float* s, float* inv_s) {
+  __shared__ double wl[LUT_N];
+  for (int c = threadIdx.x; c < LUT_N; c += TILE) wl[c] = (c == 0) ? 0.0 : 1.0 / ((double)c * (double)c);
+  __syncthreads();
+  const int t = threadIdx.x;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int2 item = items[it];
+    const BGraph gr = graphs[item.x];
+    const int nb = gr.nb, R = item.y;
+    const unsigned char* Dg = D + (size_t)gr.t0 * TILE * TILE;
+    double acc = 0.0;
+    for (int k = 0; k < hr_len(nb, R); ++k) {
+      const size_t tile = (size_t)hr_base(nb, R) + k;
+      for (int jl = 0; jl < TILE; ++jl) acc += wl[Dg[tile * TILE * TILE + jl * TILE + t]];
+    }
+    for (int I = 0; I < nb; ++I) {
+      int k = R - I;
+      if (k < 0) k += nb;
+      if (k >= hr_len(nb, I)) continue;
+      const size_t tile = (size_t)hr_base(nb, I) + k;
+      for (int il = 0; il < TILE; ++il) acc += wl[Dg[tile * TILE * TILE + t * TILE + il]];
+    }
+    const size_t i = (size_t)gr.p0 + R * TILE + t;
+    s[i] = (float)acc;
+    inv_s[i] = (acc > 0.0) ? (float)(1.0 / acc) : 0.f;
+  }
+}
+
+// The full distance matrix of one graph of a batch (float64 [n][n], d_ii = 0).
+__global__ void distance_graph_kernel(const unsigned char* Dg, int n, int nb, double* out) {
+  const size_t total = (size_t)n * n;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / n), j = (int)(idx % n);
+    double v = 0.0;
+    if (i != j) {
+      const int I = i / TILE, J = j / TILE, il = i % TILE, jl = j % TILE;
+      if (I == J) {
+        const int a = min(il, jl), b = max(il, jl);
+        v = Dg[(size_t)hr_base(nb, I) * TILE * TILE + b * TILE + a];
+      } else {
+        int k = J - I;
+        if (k < 0) k += nb;
+        if (k < hr_len(nb, I)) {
+          v = Dg[((size_t)hr_base(nb, I) + k) * TILE * TILE + jl * TILE + il];
+        } else {
+          int k2 = I - J;
+          if (k2 < 0) k2 += nb;
+          v = Dg[((size_t)hr_base(nb, J) + k2) * TILE * TILE + il * TILE + jl];
+        }
+      }
+    }
+    out[idx] = v;
+  }
+}
+
 // ---------------------------------------------------------------- launchers
 
 cudaError_t launch_bfs(int code, int n, int nb, const int* rp, const int* ci, const int* tile_base,
@@ -312,6 +478,38 @@ cudaError_t launch_distance_rows(int code, int n, int nb, const int* tile_base, 
     distance_rows_kernel<CODE_U8><<<grid, 256, 0, st>>>(n, nb, tile_base, strip_len, D, row0, nrows, out);
   else
     distance_rows_kernel<CODE_F32><<<grid, 256, 0, st>>>(n, nb, tile_base, strip_len, D, row0, nrows, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bfs_multi(const BGraph* graphs, const int2* items, int nitems, const int* rp, const int* ci,
+                             unsigned char* D, int n_max, int* maxlevel, int* overflow, int grid, cudaStream_t st) {
+  const size_t smem = (size_t)3 * n_max * sizeof(unsigned long long);
+  cudaError_t e = cudaFuncSetAttribute(bfs_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  bfs_multi_kernel<<<grid, 512, smem, st>>>(graphs, items, nitems, rp, ci, D, maxlevel, overflow);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_multi(const BGraph* graphs, const int* tile_graph, const int2* tile_ik, long long ntiles,
+                              unsigned char* D, const int* maxlevel, int write, int* unreached, int* overflow, int grid,
+                              cudaStream_t st) {
+  fill_multi_kernel<<<grid, 256, 0, st>>>(graphs, tile_graph, tile_ik, ntiles, D, maxlevel, write, unreached,
+                                          overflow);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rowsum_multi(const BGraph* graphs, const int2* items, int nitems, const unsigned char* D, float* s,
+                                float* inv_s, int grid, cudaStream_t st) {
+  rowsum_multi_kernel<<<grid, TILE, 0, st>>>(graphs, items, nitems, D, s, inv_s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_distance_graph(const unsigned char* Dg, int n, int nb, double* out, cudaStream_t st) {
+  const size_t total = (size_t)n * n;
+  int grid = (int)((total + 255) / 256);
+  if (grid > 4096) grid = 4096;
+  if (grid < 1) grid = 1;
+  distance_graph_kernel<<<grid, 256, 0, st>>>(Dg, n, nb, out);
   return cudaGetLastError();
 }
 

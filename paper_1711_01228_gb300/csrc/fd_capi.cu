@@ -9,6 +9,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <numeric>
 #include <vector>
 
 #include "fd_internal.cuh"
@@ -32,6 +33,20 @@ cudaError_t main_config_d3(int code, size_t lut_bytes, int nbuf, int* blocks_per
 cudaError_t launch_main_d1(int code, const KParams& p, int grid, size_t smem, cudaStream_t st);
 cudaError_t launch_main_d2(int code, const KParams& p, int grid, size_t smem, cudaStream_t st);
 cudaError_t launch_main_d3(int code, const KParams& p, int grid, size_t smem, cudaStream_t st);
+cudaError_t launch_bfs_multi(const BGraph* graphs, const int2* items, int nitems, const int* rp, const int* ci,
+                             unsigned char* D, int n_max, int* maxlevel, int* overflow, int grid, cudaStream_t st);
+cudaError_t launch_fill_multi(const BGraph* graphs, const int* tile_graph, const int2* tile_ik, long long ntiles,
+                              unsigned char* D, const int* maxlevel, int write, int* unreached, int* overflow, int grid,
+                              cudaStream_t st);
+cudaError_t launch_rowsum_multi(const BGraph* graphs, const int2* items, int nitems, const unsigned char* D, float* s,
+                                float* inv_s, int grid, cudaStream_t st);
+cudaError_t launch_distance_graph(const unsigned char* Dg, int n, int nb, double* out, cudaStream_t st);
+cudaError_t batch_config_d1(int W, int lut_bytes, int n_pad_max, int nbuf, int* blocks_per_sm, size_t* smem);
+cudaError_t batch_config_d2(int W, int lut_bytes, int n_pad_max, int nbuf, int* blocks_per_sm, size_t* smem);
+cudaError_t batch_config_d3(int W, int lut_bytes, int n_pad_max, int nbuf, int* blocks_per_sm, size_t* smem);
+cudaError_t launch_batch_d1(int W, const BParams* p, int grid, size_t smem, cudaStream_t st);
+cudaError_t launch_batch_d2(int W, const BParams* p, int grid, size_t smem, cudaStream_t st);
+cudaError_t launch_batch_d3(int W, const BParams* p, int grid, size_t smem, cudaStream_t st);
 }  // namespace fdl
 
 using namespace fdl;
@@ -914,6 +929,624 @@ fd_status fd_timeline_read(fd_layout* h, double* out, int32_t cap, int32_t* coun
     cudaGetLastError();
     return fail(h, FD_ERR_CUDA);
   }
+  return FD_OK;
+}
+
+}  // extern "C"
+
+// ==========================================================================
+// Batched form
+// ==========================================================================
+
+struct fd_batch {
+  int G = 0, dim = 0, dimp = 0, N = 0, P = 0, max_n = 0, n_pad_max = 0;
+  long long ntiles = 0;
+  int device = 0, sm_count = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<BGraph> graphs;
+  std::vector<int> order;
+  BGraph* d_graphs = nullptr;
+  int* d_order = nullptr;
+  unsigned char* D = nullptr;
+  size_t D_bytes = 0;
+  unsigned char* d_lut = nullptr;
+  int lut_rows = 0, max_diam = 0, disconnected = 0;
+  float* d_s = nullptr;
+  float* d_inv_s = nullptr;
+  float* d_pool = nullptr;   // X, Z, R, P, B: [5][P][dimp]
+  float* d_xin = nullptr;    // [N][dim] staging of host layouts
+  double* d_omega = nullptr; // [G]
+  double* d_omega_seq = nullptr;
+  int omega_seq_cap = 0;
+  int* d_queue = nullptr;    // [0] queue position, [1] launch error
+  int* d_iout = nullptr;     // [4][G] iterations, CG steps, accepted, status
+  double* d_dout = nullptr;  // [5][G] final stress, criterion, L^W passes, stress passes, device ms
+  BParams* d_params = nullptr;
+  int W = 2, nbuf = 2, grid = 0;
+  size_t smem = 0;
+  cudaGraphExec_t gexec = nullptr;
+  int g_W = 0, g_nbuf = 0, g_grid = 0;
+  size_t g_smem = 0;
+  int captured = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  double apsp_ms = 0.0;
+  long long timeout_ns = 30000000000LL;
+  std::vector<int> h_iout;
+  std::vector<double> h_dout;
+  fd_stats stats;
+};
+
+namespace {
+
+void batch_release(fd_batch* b) {
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  b->gexec = nullptr;
+  dev_free(b->d_graphs);
+  dev_free(b->d_order);
+  dev_free(b->D);
+  dev_free(b->d_lut);
+  dev_free(b->d_s);
+  dev_free(b->d_inv_s);
+  dev_free(b->d_pool);
+  dev_free(b->d_xin);
+  dev_free(b->d_omega);
+  dev_free(b->d_omega_seq);
+  dev_free(b->d_queue);
+  dev_free(b->d_iout);
+  dev_free(b->d_dout);
+  dev_free(b->d_params);
+  if (b->ev0) cudaEventDestroy(b->ev0);
+  if (b->ev1) cudaEventDestroy(b->ev1);
+  b->ev0 = b->ev1 = nullptr;
+}
+
+cudaError_t batch_config(int dim, int W, int lut_bytes, int n_pad_max, int nbuf, int* bps, size_t* smem) {
+  if (dim == 1) return batch_config_d1(W, lut_bytes, n_pad_max, nbuf, bps, smem);
+  if (dim == 2) return batch_config_d2(W, lut_bytes, n_pad_max, nbuf, bps, smem);
+  return batch_config_d3(W, lut_bytes, n_pad_max, nbuf, bps, smem);
+}
+
+cudaError_t launch_batch(int dim, int W, const BParams* p, int grid, size_t smem, cudaStream_t st) {
+  if (dim == 1) return launch_batch_d1(W, p, grid, smem, st);
+  if (dim == 2) return launch_batch_d2(W, p, grid, smem, st);
+  return launch_batch_d3(W, p, grid, smem, st);
+}
+
+// Sets the launch shape if it is feasible (at least one resident CTA per SM).
+fd_status batch_shape(fd_batch* b, int W, int nbuf) {
+  if ((W != 1 && W != 2) || nbuf < 2 || nbuf > 3) return FD_ERR_ARG;
+  int bps = 0;
+  size_t smem = 0;
+  if (batch_config(b->dim, W, b->lut_rows * LUT_ROW, b->n_pad_max, nbuf, &bps, &smem) != cudaSuccess) {
+    cudaGetLastError();
+    return FD_ERR_ARG;
+  }
+  if (bps < 1) return FD_ERR_ARG;
+  b->W = W;
+  b->nbuf = nbuf;
+  b->smem = smem;
+  b->grid = bps * b->sm_count;
+  return FD_OK;
+}
+
+// One launch of the persistent batched kernel (from a captured CUDA graph
+// when the stream can be captured); returns the launch-level error flag.
+fd_status batch_launch(fd_batch* b, double* kernel_ms) {
+  cudaStream_t st = b->stream;
+  const bool same = b->gexec && b->g_W == b->W && b->g_nbuf == b->nbuf && b->g_grid == b->grid && b->g_smem == b->smem;
+  if (!same && b->gexec) {
+    cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+  }
+  if (!b->gexec && st != nullptr) {
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      cudaError_t e1 = cudaMemsetAsync(b->d_queue, 0, 2 * sizeof(int), st);
+      cudaError_t e2 = launch_batch(b->dim, b->W, b->d_params, b->grid, b->smem, st);
+      cudaError_t e3 = cudaStreamEndCapture(st, &graph);
+      if (e1 == cudaSuccess && e2 == cudaSuccess && e3 == cudaSuccess && graph) {
+        if (cudaGraphInstantiate(&b->gexec, graph, 0) != cudaSuccess) b->gexec = nullptr;
+      }
+      if (graph) cudaGraphDestroy(graph);
+    }
+    cudaGetLastError();
+    if (b->gexec) {
+      b->g_W = b->W;
+      b->g_nbuf = b->nbuf;
+      b->g_grid = b->grid;
+      b->g_smem = b->smem;
+    }
+  }
+  FD_CK(cudaEventRecord(b->ev0, st));
+  if (b->gexec) {
+    FD_CK(cudaGraphLaunch(b->gexec, st));
+    b->captured = 1;
+  } else {
+    FD_CK(cudaMemsetAsync(b->d_queue, 0, 2 * sizeof(int), st));
+    FD_CK(launch_batch(b->dim, b->W, b->d_params, b->grid, b->smem, st));
+    b->captured = 0;
+  }
+  FD_CK(cudaEventRecord(b->ev1, st));
+  int q[2] = {0, 0};
+  b->h_iout.resize((size_t)4 * b->G);
+  b->h_dout.resize((size_t)5 * b->G);
+  FD_CK(cudaMemcpyAsync(q, b->d_queue, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  FD_CK(cudaMemcpyAsync(b->h_iout.data(), b->d_iout, (size_t)4 * b->G * sizeof(int), cudaMemcpyDeviceToHost, st));
+  FD_CK(cudaMemcpyAsync(b->h_dout.data(), b->d_dout, (size_t)5 * b->G * sizeof(double), cudaMemcpyDeviceToHost, st));
+  FD_CK(cudaStreamSynchronize(st));
+  float ms = 0.f;
+  FD_CK(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+  *kernel_ms = ms;
+  if (q[1] != 0) return (fd_status)q[1];
+  return FD_OK;
+}
+
+// Runs Algorithm 2 on every graph from the layouts at x_in, writing x_out.
+fd_status batch_run_dev(fd_batch* b, const float* x_in, float* x_out, const fd_options* opt, const double* omega,
+                        int max_iter, double* kernel_ms) {
+  if (!opt || !(opt->omega >= 0.0) || !std::isfinite(opt->omega) || max_iter < 1 || opt->cg_max < 0 ||
+      !(opt->tol >= 0.0) || !(opt->cg_tol >= 0.0) || (opt->stop != FD_STOP_REL_DISP && opt->stop != FD_STOP_REL_STRESS))
+    return FD_ERR_ARG;
+  if (opt->strategy == FD_OMEGA_ENUM) return FD_ERR_UNIMPLEMENTED;
+  if (opt->strategy != FD_OMEGA_FIXED && opt->strategy != FD_OMEGA_PROB) return FD_ERR_ARG;
+  cudaStream_t st = b->stream;
+  std::vector<double> om((size_t)b->G, opt->omega);
+  if (omega && opt->strategy == FD_OMEGA_FIXED) {
+    fd_status s = fetch_host(om, omega, (size_t)b->G);
+    if (s != FD_OK) return s;
+    for (double v : om)
+      if (!(v >= 0.0) || !std::isfinite(v)) return FD_ERR_ARG;
+  }
+  FD_CK(cudaMemcpyAsync(b->d_omega, om.data(), (size_t)b->G * sizeof(double), cudaMemcpyHostToDevice, st));
+  const double* seq = nullptr;
+  std::vector<double> omk;
+  if (opt->strategy == FD_OMEGA_PROB) {
+    if (b->omega_seq_cap < max_iter) {
+      dev_free(b->d_omega_seq);
+      b->omega_seq_cap = 0;
+      fd_status s = dev_alloc(&b->d_omega_seq, (size_t)max_iter);
+      if (s != FD_OK) return s;
+      b->omega_seq_cap = max_iter;
+    }
+    omk.resize(max_iter);
+    for (int k = 0; k < max_iter; ++k) omk[k] = omega_prob(opt->seed, (uint64_t)k);
+    FD_CK(cudaMemcpyAsync(b->d_omega_seq, omk.data(), max_iter * sizeof(double), cudaMemcpyHostToDevice, st));
+    seq = b->d_omega_seq;
+  }
+  BParams p;
+  std::memset(&p, 0, sizeof(p));
+  p.graphs = b->d_graphs;
+  p.order = b->d_order;
+  p.G = b->G;
+  p.dim = b->dim;
+  p.D = b->D;
+  p.lut = b->d_lut;
+  p.lut_rows = b->lut_rows;
+  p.s = b->d_s;
+  p.inv_s = b->d_inv_s;
+  p.x_in = x_in;
+  p.x_out = x_out;
+  const size_t ps = (size_t)b->P * b->dimp;
+  p.X = b->d_pool;
+  p.Z = b->d_pool + ps;
+  p.R = b->d_pool + 2 * ps;
+  p.Pd = b->d_pool + 3 * ps;
+  p.B = b->d_pool + 4 * ps;
+  p.omega = b->d_omega;
+  p.omega_seq = seq;
+  p.max_iter = max_iter;
+  p.cg_max = opt->cg_max;
+  p.stop = opt->stop;
+  p.tol = opt->tol;
+  p.cg_tol = opt->cg_tol;
+  p.queue = b->d_queue;
+  p.err = b->d_queue + 1;
+  const size_t G = (size_t)b->G;
+  p.iters = b->d_iout;
+  p.cg_steps = b->d_iout + G;
+  p.accepted = b->d_iout + 2 * G;
+  p.status = b->d_iout + 3 * G;
+  p.f_final = b->d_dout;
+  p.crit_final = b->d_dout + G;
+  p.passes_mv = b->d_dout + 2 * G;
+  p.passes_st = b->d_dout + 3 * G;
+  p.graph_ms = b->d_dout + 4 * G;
+  p.nbuf = b->nbuf;
+  p.n_pad_max = b->n_pad_max;
+  p.timeout_ns = b->timeout_ns;
+  FD_CK(cudaMemcpyAsync(b->d_params, &p, sizeof(p), cudaMemcpyHostToDevice, st));
+  FD_CK(cudaMemsetAsync(b->d_iout, 0, 4 * G * sizeof(int), st));
+  fd_status s = batch_launch(b, kernel_ms);
+  // statistics (sums over graphs)
+  fd_stats& S = b->stats;
+  std::memset(&S, 0, sizeof(S));
+  double pairs_w = 0.0, mv = 0.0, sp = 0.0, f = 0.0;
+  for (int g = 0; g < b->G; ++g) {
+    const double pg = 0.5 * (double)b->graphs[g].n * (double)(b->graphs[g].n - 1);
+    S.iterations += b->h_iout[g];
+    S.cg_steps += b->h_iout[G + g];
+    S.accepted += b->h_iout[2 * G + g];
+    const double m = b->h_dout[2 * G + g], t = b->h_dout[3 * G + g];
+    mv += m;
+    sp += t;
+    pairs_w += (m + t) * pg;
+    f += b->h_dout[g];
+  }
+  S.pair_passes = mv + sp;
+  S.pairs = pairs_w;
+  S.matvec_passes = mv;
+  S.stress_passes = sp;
+  S.final_stress = f;
+  S.kernel_ms = *kernel_ms;
+  if (s != FD_OK) return s;
+  for (int g = 0; g < b->G; ++g)
+    if (b->h_iout[3 * G + g] != 0) return (fd_status)b->h_iout[3 * G + g];
+  return FD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fd_status fd_batch_create(fd_batch** out, int32_t num_graphs, int32_t dim, const int32_t* graph_ptr,
+                          const int32_t* row_ptr, const int32_t* col_idx, int32_t disconnected_policy,
+                          void* cuda_stream) {
+  if (!out) return FD_ERR_ARG;
+  *out = nullptr;
+  if (num_graphs < 1 || dim < 1 || dim > 3 || !graph_ptr || !row_ptr ||
+      (disconnected_policy != 0 && disconnected_policy != 1))
+    return FD_ERR_ARG;
+  const int G = num_graphs;
+  std::vector<int> gp, rp, ci;
+  fd_status s = fetch_host(gp, graph_ptr, (size_t)G + 1);
+  if (s != FD_OK) return s;
+  if (gp[0] != 0) return FD_ERR_ARG;
+  for (int g = 0; g < G; ++g)
+    if (gp[g + 1] - gp[g] < 1 || gp[g + 1] - gp[g] > BMAX_N) return FD_ERR_ARG;
+  const int N = gp[G];
+  if ((s = fetch_host(rp, row_ptr, (size_t)N + 1)) != FD_OK) return s;
+  if (rp[0] != 0 || rp[N] < 0) return FD_ERR_CSR;
+  if (rp[N] > 0 && !col_idx) return FD_ERR_ARG;
+  if ((s = fetch_host(ci, col_idx, (size_t)rp[N])) != FD_OK) return s;
+  if ((s = validate_csr(N, rp, ci, nullptr)) != FD_OK) return s;
+  for (int g = 0; g < G; ++g)
+    for (int e = rp[gp[g]]; e < rp[gp[g + 1]]; ++e)
+      if (ci[e] < gp[g] || ci[e] >= gp[g + 1]) return FD_ERR_CSR;  // an edge between two graphs
+
+  fd_batch* b = new (std::nothrow) fd_batch();
+  if (!b) return FD_ERR_OOM;
+  std::memset(&b->stats, 0, sizeof(b->stats));
+  auto bail = [&](fd_status e) {
+    batch_release(b);
+    delete b;
+    return e;
+  };
+  b->G = G;
+  b->dim = dim;
+  b->dimp = (dim == 3) ? 4 : dim;
+  b->N = N;
+  b->stream = (cudaStream_t)cuda_stream;
+  if (cudaGetDevice(&b->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess ||
+      cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(FD_ERR_CUDA);
+  }
+  // geometry: padded vertex pools and tile pool, graph order (largest first)
+  b->graphs.resize(G);
+  long long p0 = 0, t0 = 0;
+  for (int g = 0; g < G; ++g) {
+    BGraph& gr = b->graphs[g];
+    gr.n = gp[g + 1] - gp[g];
+    gr.nb = (gr.n + TILE - 1) / TILE;
+    gr.v0 = gp[g];
+    gr.p0 = (int)p0;
+    gr.t0 = t0;
+    p0 += (long long)gr.nb * TILE;
+    t0 += hr_tiles(gr.nb);
+    b->max_n = std::max(b->max_n, gr.n);
+  }
+  if (p0 > INT32_MAX) return bail(FD_ERR_ARG);
+  b->P = (int)p0;
+  b->ntiles = t0;
+  b->n_pad_max = ((b->max_n + TILE - 1) / TILE) * TILE;
+  b->order.resize(G);
+  std::iota(b->order.begin(), b->order.end(), 0);
+  std::stable_sort(b->order.begin(), b->order.end(),
+                   [&](int a, int c) { return b->graphs[a].n > b->graphs[c].n; });
+  cudaStream_t st = b->stream;
+  b->D_bytes = (size_t)b->ntiles * TILE * TILE;
+  if ((s = dev_alloc(&b->d_graphs, G)) != FD_OK) return bail(s);
+  if ((s = dev_alloc(&b->d_order, G)) != FD_OK) return bail(s);
+  if ((s = dev_alloc(&b->D, b->D_bytes)) != FD_OK) return bail(s);
+  if (cudaMemcpyAsync(b->d_graphs, b->graphs.data(), G * sizeof(BGraph), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(b->d_order, b->order.data(), G * sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemsetAsync(b->D, 0, b->D_bytes, st) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(FD_ERR_CUDA);
+  }
+  // distances: batched BFS, then the unreached pairs
+  {
+    std::vector<int2> items, rows;
+    for (int g = 0; g < G; ++g) {
+      for (int s0 = 0; s0 < b->graphs[g].n; s0 += 64) items.push_back(make_int2(g, s0));
+      for (int R = 0; R < b->graphs[g].nb; ++R) rows.push_back(make_int2(g, R));
+    }
+    std::vector<int> tile_graph((size_t)b->ntiles);
+    std::vector<int2> tile_ik((size_t)b->ntiles);
+    for (int g = 0; g < G; ++g) {
+      const BGraph& gr = b->graphs[g];
+      for (int I = 0; I < gr.nb; ++I)
+        for (int k = 0; k < hr_len(gr.nb, I); ++k) {
+          const size_t t = (size_t)gr.t0 + hr_base(gr.nb, I) + k;
+          tile_graph[t] = g;
+          tile_ik[t] = make_int2(I, k);
+        }
+    }
+    int *d_rp = nullptr, *d_ci = nullptr, *d_flags = nullptr, *d_tg = nullptr;
+    int2 *d_items = nullptr, *d_rows = nullptr, *d_tik = nullptr;
+    auto cleanup = [&]() {
+      dev_free(d_rp);
+      dev_free(d_ci);
+      dev_free(d_flags);
+      dev_free(d_tg);
+      dev_free(d_items);
+      dev_free(d_rows);
+      dev_free(d_tik);
+    };
+    const size_t nnz = (size_t)rp[N];
+    fd_status e = FD_OK;
+    if ((e = dev_alloc(&d_rp, (size_t)N + 1)) != FD_OK || (e = dev_alloc(&d_ci, nnz)) != FD_OK ||
+        (e = dev_alloc(&d_flags, (size_t)2 * G + 1)) != FD_OK || (e = dev_alloc(&d_tg, (size_t)b->ntiles)) != FD_OK ||
+        (e = dev_alloc(&d_items, items.size())) != FD_OK || (e = dev_alloc(&d_rows, rows.size())) != FD_OK ||
+        (e = dev_alloc(&d_tik, (size_t)b->ntiles)) != FD_OK) {
+      cleanup();
+      return bail(e);
+    }
+    int* d_maxlevel = d_flags;
+    int* d_unreached = d_flags + G;
+    int* d_overflow = d_flags + 2 * G;
+    std::vector<int> flags((size_t)2 * G + 1, 0);
+    float ms = 0.f;
+    cudaError_t ce = cudaMemcpyAsync(d_rp, rp.data(), (N + 1) * sizeof(int), cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess && nnz) ce = cudaMemcpyAsync(d_ci, ci.data(), nnz * sizeof(int), cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(d_flags, 0, (2 * G + 1) * sizeof(int), st);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(d_rows, rows.data(), rows.size() * sizeof(int2), cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(d_tg, tile_graph.data(), tile_graph.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(d_tik, tile_ik.data(), tile_ik.size() * sizeof(int2), cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess) ce = cudaEventRecord(b->ev0, st);
+    if (ce == cudaSuccess) {
+      const int grid = std::max(1, std::min((int)items.size(), 4 * b->sm_count));
+      ce = launch_bfs_multi(b->d_graphs, d_items, (int)items.size(), d_rp, d_ci, b->D, b->max_n, d_maxlevel,
+                            d_overflow, grid, st);
+    }
+    if (ce == cudaSuccess) {
+      const int grid = (int)std::max(1LL, std::min(b->ntiles, 8LL * b->sm_count));
+      ce = launch_fill_multi(b->d_graphs, d_tg, d_tik, b->ntiles, b->D, d_maxlevel, disconnected_policy == 1 ? 1 : 0,
+                             d_unreached, d_overflow, grid, st);
+    }
+    if (ce == cudaSuccess) ce = cudaEventRecord(b->ev1, st);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(flags.data(), d_flags, (2 * G + 1) * sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, b->ev0, b->ev1);
+    if (ce != cudaSuccess) {
+      cudaGetLastError();
+      cleanup();
+      return bail(cuda_status(ce));
+    }
+    b->apsp_ms = ms;
+    bool any_unreached = false;
+    for (int g = 0; g < G; ++g) {
+      const int unr = flags[G + g];
+      b->max_diam = std::max(b->max_diam, flags[g] + (unr ? 1 : 0));
+      if (unr) {
+        any_unreached = true;
+        ++b->disconnected;
+      }
+    }
+    if (any_unreached && disconnected_policy != 1) {
+      cleanup();
+      return bail(FD_ERR_DISCONNECTED);
+    }
+    if (flags[2 * G] != 0 || b->max_diam > 253) {
+      cleanup();
+      return bail(FD_ERR_UNIMPLEMENTED);
+    }
+    // diagonal of every graph's L^W
+    if ((e = dev_alloc(&b->d_s, (size_t)b->P)) != FD_OK || (e = dev_alloc(&b->d_inv_s, (size_t)b->P)) != FD_OK) {
+      cleanup();
+      return bail(e);
+    }
+    const int rgrid = std::max(1, std::min((int)rows.size(), 8 * b->sm_count));
+    ce = launch_rowsum_multi(b->d_graphs, d_rows, (int)rows.size(), b->D, b->d_s, b->d_inv_s, rgrid, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    cleanup();
+    if (ce != cudaSuccess) {
+      cudaGetLastError();
+      return bail(cuda_status(ce));
+    }
+  }
+  // lookup table of 1/d and 1/d^2 (replicated per lane), as for one graph
+  b->lut_rows = std::min(LUT_N, b->max_diam + 2);
+  std::vector<unsigned char> lut((size_t)b->lut_rows * LUT_ROW, 0);
+  for (int c = 1; c < b->lut_rows; ++c) {
+    float* row = reinterpret_cast<float*>(lut.data() + (size_t)c * LUT_ROW);
+    const float w = (float)(1.0 / ((double)c * c)), inv = (float)(1.0 / c);
+    for (int k = 0; k < 32; ++k) {
+      row[k] = inv;
+      row[32 + k] = w;
+    }
+  }
+  const size_t ps = (size_t)b->P * b->dimp;
+  if ((s = dev_alloc(&b->d_lut, lut.size())) != FD_OK) return bail(s);
+  if ((s = dev_alloc(&b->d_pool, 5 * ps)) != FD_OK) return bail(s);
+  if ((s = dev_alloc(&b->d_xin, (size_t)N * dim)) != FD_OK) return bail(s);
+  if ((s = dev_alloc(&b->d_omega, (size_t)G)) != FD_OK) return bail(s);
+  if ((s = dev_alloc(&b->d_queue, 2)) != FD_OK) return bail(s);
+  if ((s = dev_alloc(&b->d_iout, (size_t)4 * G)) != FD_OK) return bail(s);
+  if ((s = dev_alloc(&b->d_dout, (size_t)5 * G)) != FD_OK) return bail(s);
+  if ((s = dev_alloc(&b->d_params, 1)) != FD_OK) return bail(s);
+  if (cudaMemcpyAsync(b->d_lut, lut.data(), lut.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemsetAsync(b->d_pool, 0, 5 * ps * sizeof(float), st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(FD_ERR_CUDA);
+  }
+  // default launch shape: two tile groups, two stages, else the first that fits
+  const int shapes[4][2] = {{2, 2}, {1, 2}, {2, 3}, {1, 3}};
+  s = FD_ERR_ARG;
+  for (auto& sh : shapes)
+    if ((s = batch_shape(b, sh[0], sh[1])) == FD_OK) break;
+  if (s != FD_OK) return bail(FD_ERR_CUDA);
+  *out = b;
+  return FD_OK;
+}
+
+void fd_batch_destroy(fd_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  else cudaDeviceSynchronize();
+  batch_release(b);
+  delete b;
+}
+
+fd_status fd_batch_run(fd_batch* b, float* X, const fd_options* opt, const double* omega, int32_t* iters,
+                       double* f_out) {
+  if (!b || !X || !opt) return FD_ERR_ARG;
+  const bool dev = is_device_ptr(X);
+  const size_t nx = (size_t)b->N * b->dim;
+  if (!dev) {
+    FD_CK(cudaMemcpyAsync(b->d_xin, X, nx * sizeof(float), cudaMemcpyHostToDevice, b->stream));
+  }
+  // a device layout is updated in place: each graph reads its rows before it writes them
+  float* xo = dev ? X : b->d_xin;
+  double kms = 0.0;
+  fd_status s = batch_run_dev(b, dev ? X : b->d_xin, xo, opt, omega, opt->max_iter, &kms);
+  if (s != FD_OK && s != FD_ERR_NONFINITE) return s;
+  if (!dev) {
+    FD_CK(cudaMemcpyAsync(X, b->d_xin, nx * sizeof(float), cudaMemcpyDeviceToHost, b->stream));
+    FD_CK(cudaStreamSynchronize(b->stream));
+  }
+  const size_t G = (size_t)b->G;
+  for (size_t g = 0; g < G; ++g) {
+    if (iters) iters[g] = b->h_iout[g];
+    if (f_out) f_out[g] = b->h_dout[g];
+  }
+  return s;
+}
+
+fd_status fd_batch_results(const fd_batch* b, int32_t* status, int32_t* cg_steps, int32_t* accepted, double* crit,
+                           double* matvec_passes, double* stress_passes, double* graph_ms) {
+  if (!b) return FD_ERR_ARG;
+  const size_t G = (size_t)b->G;
+  if (b->h_iout.size() < 4 * G) return FD_ERR_ARG;  // no run yet
+  for (size_t g = 0; g < G; ++g) {
+    if (status) status[g] = b->h_iout[3 * G + g];
+    if (cg_steps) cg_steps[g] = b->h_iout[G + g];
+    if (accepted) accepted[g] = b->h_iout[2 * G + g];
+    if (crit) crit[g] = b->h_dout[G + g];
+    if (matvec_passes) matvec_passes[g] = b->h_dout[2 * G + g];
+    if (stress_passes) stress_passes[g] = b->h_dout[3 * G + g];
+    if (graph_ms) graph_ms[g] = b->h_dout[4 * G + g];
+  }
+  return FD_OK;
+}
+
+fd_status fd_batch_set_shape(fd_batch* b, int32_t groups, int32_t stages) {
+  if (!b) return FD_ERR_ARG;
+  return batch_shape(b, groups, stages);
+}
+
+fd_status fd_batch_tune(fd_batch* b, const float* X, const fd_options* opt, int32_t probe_iter, int32_t repeats,
+                        int32_t* groups, int32_t* stages) {
+  if (!b || !X || !opt || probe_iter < 1 || repeats < 1) return FD_ERR_ARG;
+  const size_t nx = (size_t)b->N * b->dim;
+  float* d_out = nullptr;
+  fd_status s = dev_alloc(&d_out, nx);
+  if (s != FD_OK) return s;
+  const cudaMemcpyKind kind = is_device_ptr(X) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const int W0 = b->W, nbuf0 = b->nbuf;
+  int bestW = W0, bestN = nbuf0;
+  double best = 1e300;
+  const int shapes[4][2] = {{1, 2}, {1, 3}, {2, 2}, {2, 3}};
+  for (auto& sh : shapes) {
+    if (batch_shape(b, sh[0], sh[1]) != FD_OK) continue;
+    double t_best = 1e300;
+    for (int r = 0; r < repeats && s == FD_OK; ++r) {
+      if (cudaMemcpyAsync(b->d_xin, X, nx * sizeof(float), kind, b->stream) != cudaSuccess) {
+        cudaGetLastError();
+        s = FD_ERR_CUDA;
+        break;
+      }
+      double kms = 0.0;
+      fd_status e = batch_run_dev(b, b->d_xin, d_out, opt, nullptr, probe_iter, &kms);
+      if (e != FD_OK && e != FD_ERR_NONFINITE) s = e;
+      t_best = std::min(t_best, kms);
+    }
+    if (s != FD_OK) break;
+    if (t_best < best) {
+      best = t_best;
+      bestW = sh[0];
+      bestN = sh[1];
+    }
+  }
+  dev_free(d_out);
+  if (s != FD_OK) {
+    batch_shape(b, W0, nbuf0);
+    return s;
+  }
+  batch_shape(b, bestW, bestN);
+  if (groups) *groups = b->W;
+  if (stages) *stages = b->nbuf;
+  return FD_OK;
+}
+
+fd_status fd_batch_distances(fd_batch* b, int32_t g, double* out) {
+  if (!b || !out || g < 0 || g >= b->G) return FD_ERR_ARG;
+  const BGraph& gr = b->graphs[g];
+  const size_t nn = (size_t)gr.n * gr.n;
+  double* d = nullptr;
+  fd_status s = dev_alloc(&d, nn);
+  if (s != FD_OK) return s;
+  cudaError_t e = launch_distance_graph(b->D + (size_t)gr.t0 * TILE * TILE, gr.n, gr.nb, d, b->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, d, nn * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  cudaFree(d);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_status(e);
+  }
+  return FD_OK;
+}
+
+fd_status fd_batch_get_info(const fd_batch* b, fd_batch_info* info) {
+  if (!b || !info) return FD_ERR_ARG;
+  info->num_graphs = b->G;
+  info->dim = b->dim;
+  info->total_vertices = b->N;
+  info->num_tiles = b->ntiles;
+  info->distance_bytes = (int64_t)b->D_bytes;
+  info->max_n = b->max_n;
+  info->max_diameter = b->max_diam;
+  info->disconnected = b->disconnected;
+  info->sm_count = b->sm_count;
+  info->grid = b->grid;
+  info->groups = b->W;
+  info->stages = b->nbuf;
+  info->graph_captured = b->captured;
+  info->apsp_ms = b->apsp_ms;
+  return FD_OK;
+}
+
+fd_status fd_batch_last_stats(const fd_batch* b, fd_stats* stats) {
+  if (!b || !stats) return FD_ERR_ARG;
+  *stats = b->stats;
   return FD_OK;
 }
 

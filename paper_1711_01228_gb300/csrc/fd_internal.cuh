@@ -122,6 +122,67 @@ struct KParams {
 };
 
 // ------------------------------------------------------------------------
+// Batched form: many independent graphs, each with its own half ring
+// ------------------------------------------------------------------------
+
+constexpr int BMAX_N = 2048;  // largest graph of the batched form
+
+// Half-ring geometry of an nb-block graph: strip length and first tile of
+// block row I (the same layout as above, in closed form).
+__host__ __device__ __forceinline__ int hr_len(int nb, int I) {
+  return (nb & 1) ? (nb + 1) / 2 : (I < nb / 2 ? nb / 2 + 1 : nb / 2);
+}
+__host__ __device__ __forceinline__ int hr_base(int nb, int I) {
+  if (nb & 1) return I * ((nb + 1) / 2);
+  const int h = nb / 2;
+  return (I <= h) ? I * (h + 1) : h * (h + 1) + (I - h) * h;
+}
+__host__ __device__ __forceinline__ int hr_tiles(int nb) { return nb * (nb + 1) / 2; }
+
+// One graph of a batch.
+struct BGraph {
+  int n, nb;     // vertices, blocks of TILE vertices
+  int v0;        // first vertex of the graph in the caller's concatenated arrays
+  int p0;        // first padded vertex in the internal pools (a multiple of TILE)
+  long long t0;  // first tile of the graph in the distance pool
+};
+
+// Parameters of one batched launch (device memory, so that a captured CUDA
+// graph keeps one pointer while the host rewrites the block between runs).
+struct BParams {
+  const BGraph* graphs;   // [G]
+  const int* order;       // [G] processing order (largest first)
+  int G, dim;
+  const unsigned char* D; // uint8 distance tiles of every graph
+  const unsigned char* lut;
+  int lut_rows;
+  const float* s;         // [P] row sums of W (diagonal of L^W)
+  const float* inv_s;     // [P] 1 / s (0 for padding)
+  const float* x_in;      // [N][dim] input layouts, concatenated
+  float* x_out;           // [N][dim] output layouts
+  float *X, *Z, *R, *Pd, *B;  // [P][DP] layout, CG iterate, residual, direction, right-hand side
+  const double* omega;    // [G] omega of each graph (FD_OMEGA_FIXED)
+  const double* omega_seq;// [max_iter] omega of iteration k (FD_OMEGA_PROB), or NULL
+  int max_iter, cg_max, stop;
+  double tol, cg_tol;
+  int* queue;             // next position in `order`
+  int* err;               // first launch-level error
+  // per-graph results
+  int* iters;
+  int* cg_steps;
+  int* accepted;
+  int* status;
+  double* f_final;
+  double* crit_final;
+  double* passes_mv;      // [G] L^W passes
+  double* passes_st;      // [G] stress passes (per candidate)
+  double* graph_ms;       // [G] device time the CTA spent on the graph
+  int nbuf;
+  int n_pad_max;
+  long long timeout_ns;
+};
+
+// ------------------------------------------------------------------------
 // small device helpers
 // ------------------------------------------------------------------------
 

@@ -202,6 +202,36 @@ def initial_layout(n: int, dim: int = 2, seed: int = 0) -> np.ndarray:
     return np.random.default_rng(seed).random((n, dim)).astype(np.float32)
 
 
+def batch_sizes(num_graphs: int, n_min: int = 16, n_max: int = 2048, seed: int = 0) -> np.ndarray:
+    """Graph sizes log-uniform in [n_min, n_max]: floor(exp(U[ln n_min, ln n_max]))."""
+    rng = np.random.default_rng(seed)
+    u = rng.uniform(math.log(n_min), math.log(n_max), size=num_graphs)
+    return np.clip(np.floor(np.exp(u)).astype(np.int64), n_min, n_max)
+
+
+def batch_graphs(num_graphs: int = 4096, n_min: int = 16, n_max: int = 2048, seed: int = 0):
+    """The batched workload: sizes log-uniform in [n_min, n_max]; graphs with
+    an even index are Erdos-Renyi with mean degree 4, odd ones random geometric
+    graphs in the unit square with the radius bisected to mean degree 6 (+-0.5).
+    Graph g draws from seed 1000003 * seed + g.  Returns a list of CSR pairs."""
+    sizes = batch_sizes(num_graphs, n_min, n_max, seed)
+    out = []
+    for g, n in enumerate(sizes.tolist()):
+        sg = 1000003 * seed + g
+        if g % 2 == 0:
+            out.append(erdos_renyi(n, 4.0, sg))
+        else:
+            rp, ci, _ = random_geometric(n, 2, 6.0, sg)
+            out.append((rp, ci))
+    return out
+
+
+def batch_initial_layout(sizes, dim: int = 2, seed: int = 0) -> np.ndarray:
+    """X^0 of every graph of a batch, concatenated: graph g's rows are
+    initial_layout(n_g, dim, 1000003 * seed + g)."""
+    return np.concatenate([initial_layout(int(n), dim, 1000003 * seed + g) for g, n in enumerate(sizes)])
+
+
 # Named workloads (sizes of the graph-drawing benchmark stand-ins).
 def workload(name: str, seed: int = 0):
     """CSR of a named synthetic workload."""
