@@ -169,6 +169,10 @@ def run_ours(args, rank, world, local_rank):
                 L = api.Layout(rpd, cid, dim=args.dim, disconnected_policy=1, stream=stream.cuda_stream)
             info = L.info()
             acc["apsp_ms"] += info["apsp_ms"]
+            n_g, m2 = len(rp) - 1, int(rp[-1])
+            # edge pass: per pass over the edge list 20 B per vertex (row_ptr, reached word, next word)
+            # and 12 B per edge end (col_idx, the neighbour's frontier word); 1 B per pair written once
+            acc["apsp_bytes"] += info["bfs_sweeps"] * (20.0 * n_g + 12.0 * m2) + 0.5 * n_g * (n_g - 1)
             acc["h2d"] += rp.nbytes + ci.nbytes
             for om in oms:
                 if host:
@@ -191,8 +195,8 @@ def run_ours(args, rank, world, local_rank):
             L.close()
 
     def zero():
-        return dict(pairs=0.0, iters=0, kernel_ms=0.0, apsp_ms=0.0, flops=0.0, cg=0, launches=0, h2d=0, d2h=0,
-                    runs=[], n_launch_total=0)
+        return dict(pairs=0.0, iters=0, kernel_ms=0.0, apsp_ms=0.0, apsp_bytes=0.0, flops=0.0, cg=0, launches=0,
+                    h2d=0, d2h=0, runs=[], n_launch_total=0)
 
     for _ in range(args.warmup):
         one_step(zero())
@@ -237,6 +241,7 @@ def run_ours(args, rank, world, local_rank):
     fp32_peak = sms * 128 * 2 * clk * 1e6 / 1e12  # TFLOP/s at the maximum SM clock
     achieved = acc["flops"] / (acc["kernel_ms"] / 1e3) / 1e12
     batched = run_batched(args, local_rank, fp32_peak) if (args.batch and rank == 0) else None
+    differentiable = run_differentiable(args, local_rank) if (args.grad and rank == 0) else None
     line = {
         "metric": "pair-interactions/s",
         "value": value,
@@ -262,7 +267,14 @@ def run_ours(args, rank, world, local_rank):
                      "traffic": measured_traffic(",".join(args.workload.split(","))),
                      "traffic_unit": "DRAM bytes per launch (ncu, read + write)",
                      "peak_note": f"FP32 CUDA cores {sms} SMs x 128 x 2 flop at {clk:.0f} MHz ({src} max clock)"},
-        "apsp": {"kernel": "bfs_batch_kernel", "ms_per_step": acc["apsp_ms"] / args.steps},
+        "apsp": {"kernel": "bfs_batch_kernel", "ms_per_step": acc["apsp_ms"] / args.steps,
+                 "algorithmic_bytes_per_step": acc["apsp_bytes"] / args.steps,
+                 "achieved_gbs": acc["apsp_bytes"] / (acc["apsp_ms"] / 1e3) / 1e9,
+                 "peak_gbs": peaks.get("hbm_gbs", 6800.0),
+                 "frac": acc["apsp_bytes"] / (acc["apsp_ms"] / 1e3) / 1e9 / peaks.get("hbm_gbs", 6800.0),
+                 "note": "bytes a pass over the edge list must move per 64-source search (row_ptr, reached and "
+                         "next words, col_idx, neighbour frontier words) times the passes run, plus 1 B per "
+                         "pair written; the per-search words are L2-resident, so this is not DRAM traffic"},
         "layout_kernel_ms_per_step": acc["kernel_ms"] / args.steps,
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": acc_e["h2d"] // args.steps,
@@ -271,6 +283,8 @@ def run_ours(args, rank, world, local_rank):
     }
     if batched is not None:
         line["batched"] = batched
+    if differentiable is not None:
+        line["differentiable"] = differentiable
     return line
 
 
@@ -355,6 +369,84 @@ def run_batched(args, local_rank, peak_tflops):
     }
 
 
+def run_differentiable(args, local_rank):
+    """The differentiable form: stress of a weighted random geometric graph in
+    3-D with its two gradients (positions: the force kernel; edge lengths:
+    shortest-path back-propagation), timed beside the plain stress pass."""
+    import torch
+
+    from paper_1711_01228_gb300 import api, autograd
+
+    dev = torch.device("cuda", local_rank)
+    n = args.grad_n
+    for s in range(100):
+        rp, ci, pts = synth.random_geometric(n, 3, 6.0, seed=s)
+        if _connected(rp, ci):
+            break
+    rng = np.random.default_rng(s)
+    w = np.empty(len(ci), dtype=np.float32)
+    seen = {}
+    for u in range(n):
+        for e in range(rp[u], rp[u + 1]):
+            key = (min(u, int(ci[e])), max(u, int(ci[e])))
+            seen.setdefault(key, np.float32(rng.uniform(0.5, 2.0)))
+            w[e] = seen[key]
+    X = torch.from_numpy((pts * 10.0).astype(np.float32)).to(dev)
+    wt = torch.from_numpy(w).to(dev).requires_grad_(True)
+    rpt, cit = torch.from_numpy(rp), torch.from_numpy(ci)
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    L = api.Layout(rp, ci, dim=3, edge_len=w, disconnected_policy=0)
+    F = torch.empty_like(X)
+    G = torch.empty(len(ci), dtype=torch.float32, device=dev)
+    ms_energy = timed(lambda: L.energy(X))
+    ms_forces = timed(lambda: L.forces(X, out=F))
+    ms_lgrad = timed(lambda: L.length_grad(X, out=G))
+    create_ms = L.info()["apsp_ms"]
+    L.close()
+
+    def step():
+        wt.grad = None
+        f = autograd.stress_lengths(X, wt, rpt, cit)
+        f.backward()
+
+    ms_step = timed(step)
+    pairs = 0.5 * n * (n - 1)
+    return {"workload": f"random geometric graph n={n} in the unit cube x 10, mean degree 6, connected seed {s}; "
+                        "edge lengths seeded in [0.5, 2]; 3-D",
+            "stress_pass_ms": ms_energy, "position_grad_ms": ms_forces, "length_grad_ms": ms_lgrad,
+            "weighted_apsp_ms": create_ms, "autograd_step_ms": ms_step,
+            "stress_pairs_per_s": pairs / (ms_energy / 1e3), "position_grad_pairs_per_s": pairs / (ms_forces / 1e3),
+            "note": "autograd step = fd_layout_create (weighted shortest paths) + stress + forces + length "
+                    "gradient, through torch.autograd; every value from the CUDA library"}
+
+
+def _connected(rp, ci):
+    n = len(rp) - 1
+    seen = np.zeros(n, dtype=bool)
+    stack = [0]
+    seen[0] = True
+    while stack:
+        u = stack.pop()
+        for v in ci[rp[u]:rp[u + 1]]:
+            if not seen[v]:
+                seen[v] = True
+                stack.append(int(v))
+    return bool(seen.all())
+
+
 def cpu_sample(budget_s: float):
     """The oracle, as it is, on a bounded sample of the workload: one pass each
     of stress, L^X X and L^W p over all pairs of the Erdos-Renyi graph
@@ -415,6 +507,8 @@ def main():
     ap.add_argument("--batch-graphs", type=int, default=4096)
     ap.add_argument("--batch-steps", type=int, default=2)
     ap.add_argument("--batch-sample", type=int, default=64, help="graphs timed through the single-graph path")
+    ap.add_argument("--no-grad", dest="grad", action="store_false", help="skip the differentiable-form section")
+    ap.add_argument("--grad-n", type=int, default=4096, help="vertices of the differentiable workload (<= 4096)")
     args = ap.parse_args()
     rank, world, local_rank = _env_rank()
     if world > 1:

@@ -118,8 +118,8 @@ typedef struct {
   int32_t grid;            /* CTAs of the cooperative layout kernel */
   int32_t tasks;           /* work items (runs of tiles) per all-pairs pass */
   double apsp_ms;          /* device time of the shortest-path kernel at creation (CUDA events) */
-  int32_t stages;          /* tiles in flight per CTA in the layout kernel's copy pipeline (2 or 3) */
-  int32_t reserved;
+  int32_t stages;          /* tiles in flight per CTA in the layout kernel's copy pipeline (2 to 4) */
+  int32_t bfs_sweeps;      /* unit edges: passes over the edge list summed over the 64-source searches */
 } fd_info;
 
 /* Fills *opt with the defaults: omega 0.5, FIXED, REL_DISP, seed 0,
@@ -188,6 +188,27 @@ fd_status fd_energy_noalloc(const float* X, const float* D, int32_t n, int32_t d
  * pairs contribute zero.  X and F_out are float32 [n][dim], host or device;
  * F_out is written.  Errors: FD_ERR_ARG, FD_ERR_NONFINITE, FD_ERR_CUDA. */
 fd_status fd_forces(fd_layout* h, const float* X, float* F_out);
+
+/* Largest graph accepted by fd_energy_length_grad. */
+#define FD_GRAD_MAX_N 4096
+
+/* Derivative of the stress f(X) of Eq. (1) with respect to the edge lengths
+ * of a weighted graph (d_ij = weighted shortest-path length, Sec. 2 and
+ * Sec. 5.4; w_ij = d_ij^-2, Sec. 5.1).  With G_ij = d f / d d_ij =
+ * -2 r_ij (r_ij - d_ij) / d_ij^3, the derivative for edge e is the sum of
+ * G_ij over the pairs whose shortest path uses e; where two paths tie, the
+ * path through the lower-index predecessor is used (ties have measure zero
+ * for real-valued lengths).  The handle must come from fd_layout_create with
+ * edge_len, on a connected simple graph (no self loops or repeated entries)
+ * of at most FD_GRAD_MAX_N vertices.
+ *   X         float32 [n][dim], host or device
+ *   grad_len  float32[row_ptr[n]], host or device: one value per CSR entry,
+ *             equal for the two entries of an undirected edge
+ *   f_out     f(X) (host; may be NULL)
+ * Errors: FD_ERR_ARG (handle without edge lengths, null pointers),
+ * FD_ERR_UNIMPLEMENTED (n above the limit, disconnected or non-simple
+ * graph), FD_ERR_NONFINITE, FD_ERR_OOM, FD_ERR_CUDA. */
+fd_status fd_energy_length_grad(fd_layout* h, const float* X, float* grad_len, double* f_out);
 
 /* One iteration of Algorithm 2 (lines 4-8): H step by CG on Eq. (2-5) with
  * the first vertex pinned at the origin, extrapolation Eq. (10) with the

@@ -401,3 +401,82 @@ def sor_run(D, X0, omega: float = 0.0, strategy: int = OMEGA_FIXED, seed: int = 
             break
     res.X, res.stress = X, f
     return res
+
+
+# --------------------------------------------------------------------------
+# Derivative of the stress with respect to edge lengths
+# --------------------------------------------------------------------------
+
+def stress_length_grad(X, row_ptr, col_idx, edge_len) -> np.ndarray:
+    """d f / d l_e for Eq. (1) when d_ij is the weighted shortest-path length
+    (Sec. 5.4) and w_ij = d_ij^-2 (Sec. 5.1).
+
+    f = sum_{i<j} (r_ij / d_ij - 1)^2, so d f / d d_ij = -2 r_ij (r_ij - d_ij) / d_ij^3,
+    and d d_ij / d l_e = 1 when e lies on the shortest path of (i, j) (0
+    otherwise; ties between paths have measure zero for real-valued lengths
+    and are broken here by the lower predecessor index).  Plain loops: for
+    every source, Dijkstra with predecessors, then every target's path is
+    walked back edge by edge.  Returns one value per CSR entry, equal for
+    the two entries of an undirected edge.  Connected graphs, small n.
+    """
+    import heapq
+
+    X = _f64(X)
+    rp, ci = _i32(row_ptr), _i32(col_idx)
+    ln = _f64(edge_len)
+    n = rp.shape[0] - 1
+    entry = {}
+    for u in range(n):
+        for e in range(rp[u], rp[u + 1]):
+            v = int(ci[e])
+            if v != u:
+                key = (min(u, v), max(u, v))
+                entry.setdefault(key, []).append(e)
+    g_edge = {k: 0.0 for k in entry}
+    for s in range(n):
+        dist = np.full(n, np.inf)
+        pred = np.full(n, -1, dtype=np.int64)
+        dist[s] = 0.0
+        heap = [(0.0, s)]
+        done = np.zeros(n, dtype=bool)
+        while heap:
+            du, u = heapq.heappop(heap)
+            if done[u]:
+                continue
+            done[u] = True
+            for e in range(rp[u], rp[u + 1]):
+                v = int(ci[e])
+                c = du + ln[e]
+                if c < dist[v]:
+                    dist[v] = c
+                    heapq.heappush(heap, (c, v))
+        if not np.all(np.isfinite(dist)):
+            raise ValueError("stress_length_grad needs a connected graph")
+        for v in range(n):  # predecessor: the lowest-index tight neighbour
+            if v == s:
+                continue
+            best = None
+            for e in range(rp[v], rp[v + 1]):
+                u = int(ci[e])
+                if u != v and dist[u] + ln[e] == dist[v] and (best is None or u < best):
+                    best = u
+            if best is None:  # rounding: take the neighbour closest to tight
+                best = min((abs(dist[int(ci[e])] + ln[e] - dist[v]), int(ci[e])) for e in range(rp[v], rp[v + 1]))[1]
+            pred[v] = best
+        for t in range(n):
+            if t == s:
+                continue
+            r = float(np.linalg.norm(X[s] - X[t]))
+            d = dist[t]
+            G = -2.0 * r * (r - d) / d ** 3
+            v = t
+            while v != s:
+                u = int(pred[v])
+                g_edge[(min(u, v), max(u, v))] += 0.5 * G  # every pair is met from both ends
+                v = u
+    out = np.zeros(len(ci), dtype=np.float64)
+    for k, es in entry.items():
+        for e in es:
+            out[e] = g_edge[k]
+    return out
+

@@ -52,7 +52,7 @@ class Info(ctypes.Structure):
                 ("code_bytes", ctypes.c_int32), ("tile", ctypes.c_int32), ("num_tiles", ctypes.c_int32),
                 ("distance_bytes", ctypes.c_int64), ("disconnected", ctypes.c_int32),
                 ("sm_count", ctypes.c_int32), ("grid", ctypes.c_int32), ("tasks", ctypes.c_int32),
-                ("apsp_ms", ctypes.c_double), ("stages", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("apsp_ms", ctypes.c_double), ("stages", ctypes.c_int32), ("bfs_sweeps", ctypes.c_int32)]
 
 
 class BatchInfo(ctypes.Structure):
@@ -68,7 +68,8 @@ EXPORTED = ["fd_options_default", "fd_layout_create", "fd_layout_destroy", "fd_e
             "fd_last_stats", "fd_last_error", "fd_status_string", "fd_energy_noalloc", "fd_timeline_enable",
             "fd_timeline_read", "fd_batch_create", "fd_batch_destroy", "fd_batch_run", "fd_batch_results",
             "fd_batch_tune", "fd_batch_set_shape", "fd_batch_distances", "fd_batch_get_info",
-            "fd_batch_last_stats"]
+            "fd_batch_last_stats", "fd_energy_length_grad"]
+GRAD_MAX_N = 4096
 BATCH_MAX_N = 2048
 TIMELINE_TAGS = {1: "pack", 2: "stress", 3: "forces", 4: "rhs0", 5: "h_init", 6: "cg_au0", 7: "cg_step",
                  8: "candidates", 9: "vertex_phase"}
@@ -143,6 +144,8 @@ def lib():
     L.fd_batch_get_info.restype = i32
     L.fd_batch_last_stats.argtypes = [P, ctypes.POINTER(Stats)]
     L.fd_batch_last_stats.restype = i32
+    L.fd_energy_length_grad.argtypes = [P, P, P, ctypes.POINTER(f64)]
+    L.fd_energy_length_grad.restype = i32
     _LIB = L
     return L
 
@@ -212,6 +215,7 @@ class Layout:
         _check(status, "fd_layout_create")
         self._h = h
         self.n, self.dim = n, int(dim)
+        self._nnz = int(row_ptr[-1])
 
     # -- lifetime
     def close(self):
@@ -283,6 +287,23 @@ class Layout:
                 out = np.empty_like(X)
         _check(lib().fd_forces(self._h, _ptr(X, np.float32), _ptr(out, np.float32)), "fd_forces")
         return out
+
+    def length_grad(self, X, out=None):
+        """d f / d l_e for every CSR entry of a weighted graph (equal for the
+        two entries of an edge); returns (f, grad) with grad of X's kind
+        unless ``out`` is given."""
+        self._xcheck(X)
+        if out is None:
+            nnz = self._nnz
+            if _is_torch(X):
+                import torch
+                out = torch.empty(nnz, dtype=torch.float32, device=X.device)
+            else:
+                out = np.empty(nnz, dtype=np.float32)
+        f = ctypes.c_double()
+        _check(lib().fd_energy_length_grad(self._h, _ptr(X, np.float32), _ptr(out, np.float32), ctypes.byref(f)),
+               "fd_energy_length_grad")
+        return f.value, out
 
     def sor_step(self, X, k: int = 0, **opts):
         """One iteration of Algorithm 2 in place on X; returns (f, accepted, crit)."""

@@ -71,7 +71,8 @@ __global__ void __launch_bounds__(1024) bfs_batch_kernel(int n, int nb, const in
                                                          const int* __restrict__ tile_base,
                                                          const int* __restrict__ strip_len, void* D,
                                                          unsigned long long* scratch, size_t stride,
-                                                         int nbatches, int* maxlevel, int* overflow) {
+                                                         int nbatches, int* maxlevel, int* overflow,
+                                                         int* sweeps) {
   unsigned long long* vis = scratch + (size_t)blockIdx.x * stride;
   for (int batch = blockIdx.x; batch < nbatches; batch += gridDim.x) {
     unsigned long long* fr = vis + n;
@@ -120,7 +121,10 @@ __global__ void __launch_bounds__(1024) bfs_batch_kernel(int n, int nb, const in
       fr = nx;
       nx = t;
     }
-    if (threadIdx.x == 0) atomicMax(maxlevel, level - 1);
+    if (threadIdx.x == 0) {
+      atomicMax(maxlevel, level - 1);
+      atomicAdd(sweeps, level);  // passes over the edge list, the last (empty) one included
+    }
     __syncthreads();
   }
 }
@@ -433,14 +437,14 @@ __global__ void distance_graph_kernel(const unsigned char* Dg, int n, int nb, do
 
 cudaError_t launch_bfs(int code, int n, int nb, const int* rp, const int* ci, const int* tile_base,
                        const int* strip_len, void* D, unsigned long long* scratch, size_t stride, int grid,
-                       int* maxlevel, int* overflow, cudaStream_t st) {
+                       int* maxlevel, int* overflow, int* sweeps, cudaStream_t st) {
   const int nbatches = (n + 63) / 64;
   if (code == CODE_U8)
     bfs_batch_kernel<CODE_U8><<<grid, 1024, 0, st>>>(n, nb, rp, ci, tile_base, strip_len, D, scratch, stride,
-                                                     nbatches, maxlevel, overflow);
+                                                     nbatches, maxlevel, overflow, sweeps);
   else
     bfs_batch_kernel<CODE_F32><<<grid, 1024, 0, st>>>(n, nb, rp, ci, tile_base, strip_len, D, scratch, stride,
-                                                      nbatches, maxlevel, overflow);
+                                                      nbatches, maxlevel, overflow, sweeps);
   return cudaGetLastError();
 }
 

@@ -18,7 +18,7 @@
 namespace fdl {
 cudaError_t launch_bfs(int code, int n, int nb, const int* rp, const int* ci, const int* tile_base,
                        const int* strip_len, void* D, unsigned long long* scratch, size_t stride, int grid,
-                       int* maxlevel, int* overflow, cudaStream_t st);
+                       int* maxlevel, int* overflow, int* sweeps, cudaStream_t st);
 cudaError_t launch_sssp(int n, int nb, const int* rp, const int* ci, const float* len, const int* tile_base,
                         const int* strip_len, float* D, float* scratch, int grid, int* maxbits, cudaStream_t st);
 cudaError_t launch_fill(int code, int n, int nb, int ntiles, const int2* tile_ik, void* D, float fill, int write,
@@ -41,6 +41,9 @@ cudaError_t launch_fill_multi(const BGraph* graphs, const int* tile_graph, const
 cudaError_t launch_rowsum_multi(const BGraph* graphs, const int2* items, int nitems, const unsigned char* D, float* s,
                                 float* inv_s, int grid, cudaStream_t st);
 cudaError_t launch_distance_graph(const unsigned char* Dg, int n, int nb, double* out, cudaStream_t st);
+cudaError_t launch_length_grad(int n, int nb, int dim, const int2* tile_ik, int ntiles, const float* D,
+                               const float* X, float* Gt, const int* rp, const int* ci, const float* len,
+                               const int* rev, int nnz, float* gacc, float* out, int sm_count, cudaStream_t st);
 cudaError_t batch_config_d1(int W, int lut_bytes, int n_pad_max, int nbuf, int* blocks_per_sm, size_t* smem);
 cudaError_t batch_config_d2(int W, int lut_bytes, int n_pad_max, int nbuf, int* blocks_per_sm, size_t* smem);
 cudaError_t batch_config_d3(int W, int lut_bytes, int n_pad_max, int nbuf, int* blocks_per_sm, size_t* smem);
@@ -95,6 +98,14 @@ struct fd_layout {
   double* d_timeline = nullptr;  // tracing: [timeline_cap][2]
   int timeline_cap = 0;
   int timeline_n = 0;
+  // weighted graphs: the CSR kept for the derivative in the edge lengths
+  int* d_wrp = nullptr;
+  int* d_wci = nullptr;
+  float* d_wlen = nullptr;
+  int* d_wrev = nullptr;  // index of the reverse entry of every CSR entry
+  int wnnz = 0;
+  int wsimple = 0;        // no self loops, no repeated entries
+  int bfs_sweeps = 0;     // passes over the edge list of all 64-source searches
 };
 
 namespace {
@@ -304,6 +315,10 @@ void release(fd_layout* h) {
   dev_free(h->d_trace_acc);
   dev_free(h->d_trace_cg);
   dev_free(h->d_timeline);
+  dev_free(h->d_wrp);
+  dev_free(h->d_wci);
+  dev_free(h->d_wlen);
+  dev_free(h->d_wrev);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
   h->ev0 = h->ev1 = nullptr;
@@ -380,14 +395,15 @@ fd_status build_distances(fd_layout* h, const std::vector<int>& rp, const std::v
       FD_TRYC(cudaMalloc(&scratch, (size_t)grid * stride * sizeof(unsigned long long)));
       FD_TRYC(cudaEventRecord(h->ev0, st));
       FD_TRYC(launch_bfs(code, n, nb, d_rp, d_ci, h->d_tile_base, h->d_strip_len, h->D,
-                         (unsigned long long*)scratch, stride, grid, d_flags, d_flags + 1, st));
+                         (unsigned long long*)scratch, stride, grid, d_flags, d_flags + 1, d_flags + 3, st));
       FD_TRYC(cudaEventRecord(h->ev1, st));
-      int flags[2];
-      FD_TRYC(cudaMemcpyAsync(flags, d_flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+      int flags[4];
+      FD_TRYC(cudaMemcpyAsync(flags, d_flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
       FD_TRYC(cudaStreamSynchronize(st));
       float ms = 0.f;
       FD_TRYC(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
       h->apsp_ms = ms;
+      h->bfs_sweeps = flags[3];
       diameter = flags[0];
       if (flags[1] && code == CODE_U8) {  // a level above 255: store float codes
         code = CODE_F32;
@@ -627,6 +643,40 @@ fd_status fd_layout_create(fd_layout** out, int32_t n, int32_t dim, const int32_
     return bail(FD_ERR_CUDA);
   }
   if ((s = build_distances(h, rp, ci, edge_len ? &len : nullptr, disconnected_policy)) != FD_OK) return bail(s);
+  if (edge_len) {
+    // keep the CSR on the device for fd_energy_length_grad, with the reverse of every entry
+    const int nnz = rp[n];
+    std::vector<int> rev(nnz, -1);
+    bool simple = true;
+    for (int u = 0; u < n && simple; ++u) {
+      for (int e = rp[u]; e < rp[u + 1]; ++e) {
+        const int v = ci[e];
+        if (v == u || (e > rp[u] && std::find(ci.begin() + rp[u], ci.begin() + e, v) != ci.begin() + e)) {
+          simple = false;
+          break;
+        }
+        for (int f = rp[v]; f < rp[v + 1]; ++f)
+          if (ci[f] == u) {
+            rev[e] = f;
+            break;
+          }
+      }
+    }
+    h->wsimple = simple ? 1 : 0;
+    h->wnnz = nnz;
+    if (simple && nnz > 0) {
+      if ((s = dev_alloc(&h->d_wrp, (size_t)n + 1)) != FD_OK || (s = dev_alloc(&h->d_wci, (size_t)nnz)) != FD_OK ||
+          (s = dev_alloc(&h->d_wlen, (size_t)nnz)) != FD_OK || (s = dev_alloc(&h->d_wrev, (size_t)nnz)) != FD_OK)
+        return bail(s);
+      if (cudaMemcpy(h->d_wrp, rp.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+          cudaMemcpy(h->d_wci, ci.data(), nnz * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+          cudaMemcpy(h->d_wlen, len.data(), nnz * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+          cudaMemcpy(h->d_wrev, rev.data(), nnz * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(FD_ERR_CUDA);
+      }
+    }
+  }
 
   // replicated lookup table for uint8 codes 0 .. lut_rows-1 (shared memory):
   // row c = 32 x float 1/c, then 32 x float 1/c^2 (one copy per lane); row 0 (no pair) is zero
@@ -754,6 +804,57 @@ fd_status fd_forces(fd_layout* h, const float* X, float* F_out) {
       return fail(h, FD_ERR_CUDA);
     }
   }
+  return FD_OK;
+}
+
+fd_status fd_energy_length_grad(fd_layout* h, const float* X, float* grad_len, double* f_out) {
+  if (!h) return FD_ERR_ARG;
+  if (!X || !grad_len) return fail(h, FD_ERR_ARG);
+  if (h->code != CODE_F32 || !h->d_wrp || h->wnnz == 0) return fail(h, FD_ERR_ARG);  // not a weighted graph
+  if (h->n > FD_GRAD_MAX_N || h->disconnected || !h->wsimple) return fail(h, FD_ERR_UNIMPLEMENTED);
+  const float* dx = nullptr;
+  fd_status s = stage_input(h, X, &dx);
+  if (s != FD_OK) return fail(h, s);
+  // the stress itself (one stress pass of the layout kernel)
+  KParams p = base_params(h, KM_ENERGY);
+  p.x_in = dx;
+  Ctrl c;
+  double kms = 0.0;
+  std::memset(&c, 0, sizeof(c));
+  s = run_kernel(h, p, &c, &kms);
+  fill_stats(h, c, kms);
+  if (s != FD_OK) return fail(h, s);
+  std::vector<int2> tile_ik(h->ntiles);
+  for (int I = 0; I < h->nb; ++I)
+    for (int k = 0; k < h->strip_len[I]; ++k) tile_ik[h->tile_base[I] + k] = make_int2(I, k);
+  int2* d_tik = nullptr;
+  float *d_G = nullptr, *d_acc = nullptr, *d_out = nullptr;
+  const bool dev_out = is_device_ptr(grad_len);
+  auto cleanup = [&]() {
+    dev_free(d_tik);
+    dev_free(d_G);
+    dev_free(d_acc);
+    dev_free(d_out);
+  };
+  if ((s = dev_alloc(&d_tik, (size_t)h->ntiles)) != FD_OK || (s = dev_alloc(&d_G, (size_t)h->ntiles * TILE * TILE)) != FD_OK ||
+      (s = dev_alloc(&d_acc, (size_t)h->wnnz)) != FD_OK || (!dev_out && (s = dev_alloc(&d_out, (size_t)h->wnnz)) != FD_OK)) {
+    cleanup();
+    return fail(h, s);
+  }
+  cudaStream_t st = h->stream;
+  cudaError_t e = cudaMemcpyAsync(d_tik, tile_ik.data(), h->ntiles * sizeof(int2), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = launch_length_grad(h->n, h->nb, h->dim, d_tik, h->ntiles, (const float*)h->D, dx, d_G, h->d_wrp, h->d_wci,
+                           h->d_wlen, h->d_wrev, h->wnnz, d_acc, dev_out ? grad_len : d_out, h->sm_count, st);
+  if (e == cudaSuccess && !dev_out)
+    e = cudaMemcpyAsync(grad_len, d_out, (size_t)h->wnnz * sizeof(float), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cleanup();
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, cuda_status(e));
+  }
+  if (f_out) *f_out = c.f_final;
   return FD_OK;
 }
 
@@ -897,7 +998,7 @@ fd_status fd_layout_info(const fd_layout* h, fd_info* info) {
   info->tasks = h->ntasks;
   info->apsp_ms = h->apsp_ms;
   info->stages = h->nbuf;
-  info->reserved = 0;
+  info->bfs_sweeps = h->bfs_sweeps;
   return FD_OK;
 }
 

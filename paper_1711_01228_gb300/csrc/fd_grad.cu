@@ -1,0 +1,184 @@
+// fd_grad.cu -- derivative of the stress (Eq. (1)) with respect to the edge
+// lengths of a weighted graph.
+//
+// With w_ij = d_ij^-2 (Sec. 5.1) the pair term is (r_ij / d_ij - 1)^2, so
+//     d f / d d_ij = -2 r_ij (r_ij - d_ij) / d_ij^3 =: G_ij,
+// and d_ij, the weighted shortest-path length (Sec. 2, Sec. 5.4), moves with
+// the length of every edge on the shortest path of (i, j) (ties between
+// paths have measure zero for real-valued lengths).  So
+//     d f / d l_e = sum over pairs whose shortest path uses e of G_ij.
+//
+// pair_dgrad_kernel writes G_ij into a float array laid out like the
+// distance tiles.  sp_backprop_kernel then takes one source s per CTA
+// iteration: label-correcting distances from s in shared memory, the
+// shortest-path tree (parent = lowest-index neighbour u with
+// dist[u] + l(u, v) == dist[v], an exact FP32 equality at the fixed point),
+// a bitonic sort of the vertices by distance, and one sweep from the
+// farthest vertex inwards that adds each subtree's sum of G_sv to the
+// subtree's parent edge.  Every unordered pair is met from both ends, so the
+// per-edge sums are halved when the two directions are combined.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fd_internal.cuh"
+
+namespace fdl {
+
+__global__ void __launch_bounds__(TILE) pair_dgrad_kernel(int n, int nb, int dim, const int2* __restrict__ tile_ik,
+                                                          int ntiles, const float* __restrict__ D,
+                                                          const float* __restrict__ X, float* Gt) {
+  __shared__ float xi[TILE][3], xj[TILE][3];
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int2 ik = tile_ik[t];
+    const int I = ik.x, J = (ik.x + ik.y) % nb;
+    const int i = I * TILE + threadIdx.x, j = J * TILE + threadIdx.x;
+    for (int d = 0; d < 3; ++d) {
+      xi[threadIdx.x][d] = (i < n && d < dim) ? X[(size_t)i * dim + d] : 0.f;
+      xj[threadIdx.x][d] = (j < n && d < dim) ? X[(size_t)j * dim + d] : 0.f;
+    }
+    __syncthreads();
+    const int il = threadIdx.x;
+    for (int jl = 0; jl < TILE; ++jl) {
+      const size_t off = (size_t)t * TILE * TILE + (size_t)jl * TILE + il;
+      const float dd = D[off];
+      float g = 0.f;
+      if (dd > 0.f) {
+        float r2 = 0.f;
+        for (int d = 0; d < dim; ++d) {
+          const float a = xi[il][d] - xj[jl][d];
+          r2 = fmaf(a, a, r2);
+        }
+        const float r = sqrtf(r2);
+        g = -2.f * r * (r - dd) / (dd * dd * dd);
+      }
+      Gt[off] = g;
+    }
+    __syncthreads();
+  }
+}
+
+// Value of pair (i, j) in an array laid out like the distance tiles.
+__device__ __forceinline__ float pair_value(const float* T, int nb, int i, int j) {
+  const int I = i / TILE, J = j / TILE, il = i % TILE, jl = j % TILE;
+  constexpr size_t TT = (size_t)TILE * TILE;
+  if (I == J) {
+    const int a = min(il, jl), b = max(il, jl);
+    return T[(size_t)hr_base(nb, I) * TT + b * TILE + a];
+  }
+  int k = J - I;
+  if (k < 0) k += nb;
+  if (k < hr_len(nb, I)) return T[((size_t)hr_base(nb, I) + k) * TT + jl * TILE + il];
+  int k2 = I - J;
+  if (k2 < 0) k2 += nb;
+  return T[((size_t)hr_base(nb, J) + k2) * TT + il * TILE + jl];
+}
+
+__global__ void __launch_bounds__(256) sp_backprop_kernel(int n, int nb, int npow2, const int* __restrict__ rp,
+                                                          const int* __restrict__ ci, const float* __restrict__ len,
+                                                          const float* __restrict__ Gt, float* gacc) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  unsigned long long* key = reinterpret_cast<unsigned long long*>(sm);  // [npow2]
+  float* dist = reinterpret_cast<float*>(key + npow2);                 // [n]
+  float* acc = dist + n;                                               // [n]
+  int* par_e = reinterpret_cast<int*>(acc + n);                        // [n]
+  const int tid = threadIdx.x, bd = blockDim.x;
+  for (int s = blockIdx.x; s < n; s += gridDim.x) {
+    for (int v = tid; v < n; v += bd) dist[v] = (v == s) ? 0.f : INFINITY;
+    __syncthreads();
+    for (int sweep = 0; sweep < n; ++sweep) {
+      int changed = 0;
+      for (int v = tid; v < n; v += bd) {
+        float best = dist[v];
+        for (int e = rp[v]; e < rp[v + 1]; ++e) best = fminf(best, ((volatile float*)dist)[ci[e]] + len[e]);
+        if (best < dist[v]) {
+          dist[v] = best;
+          changed = 1;
+        }
+      }
+      if (!__syncthreads_or(changed)) break;
+    }
+    // shortest-path tree: the lowest-index tight neighbour is the parent
+    for (int v = tid; v < n; v += bd) {
+      int be = -1, bu = 0x7fffffff;
+      if (v != s && dist[v] < INFINITY) {
+        for (int e = rp[v]; e < rp[v + 1]; ++e) {
+          const int u = ci[e];
+          if (u != v && dist[u] + len[e] == dist[v] && u < bu) {
+            bu = u;
+            be = e;
+          }
+        }
+      }
+      par_e[v] = be;
+      acc[v] = (v != s) ? pair_value(Gt, nb, s, v) : 0.f;
+    }
+    for (int v = tid; v < npow2; v += bd)
+      key[v] = (v < n && dist[v] < INFINITY) ? (((unsigned long long)__float_as_uint(dist[v]) << 32) | (unsigned)v)
+                                              : ~0ull;
+    __syncthreads();
+    // bitonic sort, ascending distance (non-negative floats order as their bit patterns)
+    for (int k = 2; k <= npow2; k <<= 1) {
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int i = tid; i < npow2; i += bd) {
+          const int ixj = i ^ j;
+          if (ixj > i) {
+            const unsigned long long a = key[i], b = key[ixj];
+            const bool up = (i & k) == 0;
+            if ((a > b) == up) {
+              key[i] = b;
+              key[ixj] = a;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    // farthest first: each subtree's sum reaches its parent edge
+    if (tid == 0) {
+      for (int k = npow2 - 1; k >= 0; --k) {
+        const unsigned long long kk = key[k];
+        if (kk == ~0ull) continue;
+        const int v = (int)(kk & 0xffffffffull);
+        const int e = par_e[v];
+        if (v == s || e < 0) continue;
+        const float a = acc[v];
+        acc[ci[e]] += a;
+        atomicAdd(gacc + e, a);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// The undirected edge's derivative from its two CSR entries (each pair was
+// met from both ends, hence the half).
+__global__ void combine_directions_kernel(int nnz, const int* __restrict__ rev, const float* __restrict__ gacc,
+                                          float* out) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += gridDim.x * blockDim.x)
+    out[e] = 0.5f * (gacc[e] + gacc[rev[e]]);
+}
+
+cudaError_t launch_length_grad(int n, int nb, int dim, const int2* tile_ik, int ntiles, const float* D,
+                               const float* X, float* Gt, const int* rp, const int* ci, const float* len,
+                               const int* rev, int nnz, float* gacc, float* out, int sm_count, cudaStream_t st) {
+  const int tgrid = ntiles < 8 * sm_count ? ntiles : 8 * sm_count;
+  pair_dgrad_kernel<<<tgrid > 0 ? tgrid : 1, TILE, 0, st>>>(n, nb, dim, tile_ik, ntiles, D, X, Gt);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  int npow2 = 1;
+  while (npow2 < n) npow2 <<= 1;
+  const size_t smem = (size_t)npow2 * 8 + (size_t)n * 12;
+  e = cudaFuncSetAttribute(sp_backprop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(gacc, 0, (size_t)nnz * sizeof(float), st);
+  if (e != cudaSuccess) return e;
+  const int sgrid = n < 2 * sm_count ? n : 2 * sm_count;
+  sp_backprop_kernel<<<sgrid, 256, smem, st>>>(n, nb, npow2, rp, ci, len, Gt, gacc);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int cgrid = (nnz + 255) / 256;
+  if (nnz > 0) combine_directions_kernel<<<cgrid < 4096 ? cgrid : 4096, 256, 0, st>>>(nnz, rev, gacc, out);
+  return cudaGetLastError();
+}
+
+}  // namespace fdl

@@ -1,0 +1,139 @@
+"""The differentiable form: gradients of the stress through the C ABI,
+checked in FP64 against the oracle and central finite differences.
+
+d f / d X is the force kernel (-2 F); d f / d l (edge lengths) sums the pair
+derivatives along shortest paths.  Graphs: random geometric graphs in 3-D
+with 64 vertices and seeded lengths in [0.5, 2] (the subgraph size of the
+differentiable workload's gradient check).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1711_01228_gb300 import api, build, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    api.lib()
+
+
+def _weighted_rgg(n, dim, seed):
+    for s in range(seed, seed + 50):
+        rp, ci, pts = synth.random_geometric(n, dim, 6.0, seed=s)
+        if oracle.apsp(rp, ci)[0] == 0:
+            break
+    rng = np.random.default_rng(s)
+    lens = {}
+    w = np.empty(len(ci), dtype=np.float32)
+    for u in range(n):
+        for e in range(rp[u], rp[u + 1]):
+            key = (min(u, int(ci[e])), max(u, int(ci[e])))
+            lens.setdefault(key, np.float32(rng.uniform(0.5, 2.0)))
+            w[e] = lens[key]
+    return rp, ci, w, pts
+
+
+@pytest.mark.parametrize("seed", [0, 3])
+def test_position_gradient_is_minus_two_forces(seed):
+    import torch
+
+    from paper_1711_01228_gb300 import autograd
+
+    rp, ci, w, _ = _weighted_rgg(64, 3, seed)
+    D = oracle.apsp(rp, ci, edge_len=w.astype(np.float64))[1]
+    X0 = (np.random.default_rng(seed).random((64, 3)) * 3.0).astype(np.float32)
+    X = torch.from_numpy(X0).cuda().requires_grad_(True)
+    with api.Layout(rp, ci, dim=3, edge_len=w) as L:
+        f = autograd.stress(X, L)
+        f.backward()
+    assert float(f) == pytest.approx(oracle.stress(X0, D), rel=1e-5)
+    Xd = X0.astype(np.float64)
+    fd = np.zeros_like(Xd)
+    h = 1e-6
+    for i in range(64):
+        for d in range(3):
+            Xp, Xm = Xd.copy(), Xd.copy()
+            Xp[i, d] += h
+            Xm[i, d] -= h
+            fd[i, d] = (oracle.stress(Xp, D) - oracle.stress(Xm, D)) / (2 * h)
+    g = X.grad.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(g - fd) <= 1e-5 * np.linalg.norm(fd)
+
+
+@pytest.mark.parametrize("seed", [0, 3])
+def test_length_gradient_matches_oracle_and_finite_differences(seed):
+    rp, ci, w, _ = _weighted_rgg(64, 3, seed)
+    X0 = (np.random.default_rng(seed + 1).random((64, 3)) * 3.0).astype(np.float32)
+    with api.Layout(rp, ci, dim=3, edge_len=w) as L:
+        f, g = L.length_grad(X0)
+    wd = w.astype(np.float64)
+    ref = oracle.stress_length_grad(X0, rp, ci, wd)
+    assert np.linalg.norm(g - ref) <= 1e-4 * np.linalg.norm(ref)
+    # both entries of an edge carry the same value
+    n = len(rp) - 1
+    for u in range(n):
+        for e in range(rp[u], rp[u + 1]):
+            v = int(ci[e])
+            rev = [k for k in range(rp[v], rp[v + 1]) if ci[k] == u][0]
+            assert g[e] == g[rev]
+    # central differences of the FP64 stress over re-run shortest paths, on a few edges
+    h = 1e-6
+    for e in np.random.default_rng(seed).choice(len(ci), 6, replace=False):
+        u = int(np.searchsorted(rp, e, side="right") - 1)
+        v = int(ci[e])
+        idx = [e] + [k for k in range(rp[v], rp[v + 1]) if ci[k] == u]
+        wp, wm = wd.copy(), wd.copy()
+        wp[idx] += h
+        wm[idx] -= h
+        fdv = (oracle.stress(X0, oracle.apsp(rp, ci, edge_len=wp)[1]) -
+               oracle.stress(X0, oracle.apsp(rp, ci, edge_len=wm)[1])) / (2 * h)
+        assert g[e] == pytest.approx(fdv, rel=1e-3, abs=1e-4 * np.abs(ref).max())
+
+
+def test_autograd_lengths_and_fit():
+    import torch
+
+    from paper_1711_01228_gb300 import autograd
+
+    # fit edge lengths (all 1.0 at first) so that the graph distances match a target layout Y
+    rp, ci, _, pts = _weighted_rgg(256, 3, 7)
+    Y = torch.from_numpy((pts * 10.0).astype(np.float32)).cuda()
+    rpt, cit = torch.from_numpy(rp), torch.from_numpy(ci)
+    lens = torch.ones(len(ci), dtype=torch.float32, device="cuda", requires_grad=True)
+    f0 = autograd.stress_lengths(Y, lens, rpt, cit)
+    f0.backward()
+    with api.Layout(rp, ci, dim=3, edge_len=np.ones(len(ci), dtype=np.float32)) as L:
+        _, g_full = L.length_grad(Y.cpu().numpy())
+    # the per-edge sums are added with atomics: equal to FP32 rounding
+    assert torch.allclose(lens.grad.cpu(), 0.5 * torch.from_numpy(g_full), rtol=1e-5, atol=0)
+    opt = torch.optim.Adam([lens], lr=0.05)
+    fs = []
+    for _ in range(40):
+        opt.zero_grad()
+        f = autograd.stress_lengths(Y, lens, rpt, cit)
+        f.backward()
+        opt.step()
+        with torch.no_grad():
+            lens.clamp_(min=0.05)
+        fs.append(float(f))
+    assert fs[-1] < 0.6 * fs[0], fs[::8]
+    assert fs[-1] <= 1.05 * min(fs[:10]), fs[::8]
+
+
+def test_length_gradient_errors():
+    rp, ci = synth.grid(5, 5)
+    X = synth.initial_layout(25, 2, 0)
+    with api.Layout(rp, ci, dim=2) as L:  # no edge lengths
+        with pytest.raises(api.FdError) as e:
+            L.length_grad(X)
+        assert e.value.status == 1
+    rp, ci = synth.grid(65, 65)  # 4225 vertices > FD_GRAD_MAX_N
+    w = np.ones(len(ci), dtype=np.float32)
+    with api.Layout(rp, ci, dim=2, edge_len=w) as L:
+        with pytest.raises(api.FdError) as e:
+            L.length_grad(synth.initial_layout(4225, 2, 0))
+        assert e.value.status == 10
