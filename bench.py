@@ -425,11 +425,40 @@ def run_differentiable(args, local_rank):
         f.backward()
 
     ms_step = timed(step)
+
+    # adjoint through K = 32 unrolled iterations (checkpoint every 8): fit lengths to target distances
+    K, every = 32, 8
+    rng2 = np.random.default_rng(1)
+    Yt = torch.from_numpy((rng2.random((n, 3)) * 10.0).astype(np.float32)).to(dev)
+    pi = torch.from_numpy(rng2.integers(0, n, 4096)).to(dev)
+    pj = torch.from_numpy(rng2.integers(0, n, 4096)).to(dev)
+    keep = pi != pj
+    pi, pj = pi[keep], pj[keep]
+    tgt = (Yt[pi] - Yt[pj]).norm(dim=1)
+    X0 = X.clone()
+
+    def unrolled_step():
+        wt.grad = None
+        XK = autograd.unrolled_layout(X0, wt, rpt, cit, K=K, omega=0.5, every=every)
+        loss = ((XK[pi] - XK[pj]).norm(dim=1) - tgt).pow(2).sum()
+        loss.backward()
+
+    ms_unrolled = timed(unrolled_step, reps=2)
+
+    def unrolled_forward():
+        with torch.no_grad():
+            autograd.unrolled_layout(X0, wt.detach(), rpt, cit, K=K, omega=0.5, every=every)
+
+    ms_unrolled_fwd = timed(unrolled_forward, reps=2)
     pairs = 0.5 * n * (n - 1)
     return {"workload": f"largest component (n={n}) of a random geometric graph of {args.grad_n} points in the "
                         "unit cube x 10, mean degree 6 (seed 0); edge lengths seeded in [0.5, 2]; 3-D",
             "stress_pass_ms": ms_energy, "position_grad_ms": ms_forces, "length_grad_ms": ms_lgrad,
             "weighted_apsp_ms": create_ms, "autograd_step_ms": ms_step,
+            "unrolled": {"iterations": K, "checkpoint_every": every, "omega_c": 1.5,
+                         "forward_ms": ms_unrolled_fwd, "forward_backward_ms": ms_unrolled,
+                         "loss": "squared error of 4096 sampled pair distances of X^K against a seeded "
+                                 "random layout's"},
             "stress_pairs_per_s": pairs / (ms_energy / 1e3), "position_grad_pairs_per_s": pairs / (ms_forces / 1e3),
             "note": "autograd step = fd_layout_create (weighted shortest paths) + stress + forces + length "
                     "gradient, through torch.autograd; every value from the CUDA library"}

@@ -210,6 +210,40 @@ fd_status fd_forces(fd_layout* h, const float* X, float* F_out);
  * graph), FD_ERR_NONFINITE, FD_ERR_OOM, FD_ERR_CUDA. */
 fd_status fd_energy_length_grad(fd_layout* h, const float* X, float* grad_len, double* f_out);
 
+/* Unrolled differentiation of Algorithm 2: the adjoint of one iteration.
+ * The forward iteration (fd_sor_step) is b = L^X X (Prop. 2.1), Y solving
+ * L^W Y = b with vertex 0 pinned (Eq. (2-5), Sec. 2), and X' = (1 + omega) Y -
+ * omega X if line 6 kept the extrapolation (Eq. (10)), else X' = Y.  Given
+ * Xbar_k1 = dL/dX' this writes Xbar_k = dL/dX with the acceptance held fixed:
+ * the pinning's adjoint, one solve L^W lam = Ybar by the layout kernel's CG
+ * (opt->cg_tol, opt->cg_max; NULL = defaults), and the transposed Jacobian
+ * of L^X X applied to lam.  After fd_adjoint_reset, it also adds every pair's
+ * sensitivity dL/dd_ij to an accumulator of the handle (weighted graphs that
+ * fd_energy_length_grad accepts); fd_adjoint_length_grad turns the sum into
+ * dL/dl_e through the shortest paths.
+ *   X_k, X_k1   float32 [n][dim]: the iteration's input and output layouts
+ *   accepted    the outcome of line 6 (fd_sor_step's *accepted)
+ *   omega       the omega the iteration used
+ *   Xbar_k1     float32 [n][dim]: dL/dX_k1;  Xbar_k: float32 [n][dim], written
+ *   cg_steps    CG steps of the adjoint solve (host; may be NULL)
+ * Arrays host or device.  Errors: FD_ERR_ARG, FD_ERR_NONFINITE, FD_ERR_CUDA,
+ * FD_ERR_TIMEOUT. */
+fd_status fd_sor_step_adjoint(fd_layout* h, const float* X_k, const float* X_k1, int32_t accepted, double omega,
+                              const float* Xbar_k1, float* Xbar_k, const fd_options* opt, int32_t* cg_steps);
+
+/* Clears (allocating on first use) the handle's accumulator of pair
+ * sensitivities.  Weighted graphs only, with the limits of
+ * fd_energy_length_grad.  Errors: FD_ERR_ARG (no edge lengths),
+ * FD_ERR_UNIMPLEMENTED, FD_ERR_OOM, FD_ERR_CUDA. */
+fd_status fd_adjoint_reset(fd_layout* h);
+
+/* dL/dl_e from the accumulated pair sensitivities (the sum over the
+ * fd_sor_step_adjoint calls since fd_adjoint_reset), pushed through every
+ * pair's shortest path as in fd_energy_length_grad; float32[row_ptr[n]],
+ * host or device, equal for the two entries of an edge.  Errors: FD_ERR_ARG
+ * (no accumulator), FD_ERR_OOM, FD_ERR_CUDA. */
+fd_status fd_adjoint_length_grad(fd_layout* h, float* grad_len);
+
 /* One iteration of Algorithm 2 (lines 4-8): H step by CG on Eq. (2-5) with
  * the first vertex pinned at the origin, extrapolation Eq. (10) with the
  * omega the strategy gives for iteration index k (k >= 0), acceptance test

@@ -407,35 +407,15 @@ def sor_run(D, X0, omega: float = 0.0, strategy: int = OMEGA_FIXED, seed: int = 
 # Derivative of the stress with respect to edge lengths
 # --------------------------------------------------------------------------
 
-def stress_length_grad(X, row_ptr, col_idx, edge_len) -> np.ndarray:
-    """d f / d l_e for Eq. (1) when d_ij is the weighted shortest-path length
-    (Sec. 5.4) and w_ij = d_ij^-2 (Sec. 5.1).
-
-    f = sum_{i<j} (r_ij / d_ij - 1)^2, so d f / d d_ij = -2 r_ij (r_ij - d_ij) / d_ij^3,
-    and d d_ij / d l_e = 1 when e lies on the shortest path of (i, j) (0
-    otherwise; ties between paths have measure zero for real-valued lengths
-    and are broken here by the lower predecessor index).  Plain loops: for
-    every source, Dijkstra with predecessors, then every target's path is
-    walked back edge by edge.  Returns one value per CSR entry, equal for
-    the two entries of an undirected edge.  Connected graphs, small n.
-    """
+def _shortest_path_trees(rp, ci, ln):
+    """For every source: Dijkstra distances and predecessors (the lowest-index
+    tight neighbour).  Connected graphs only."""
     import heapq
 
-    X = _f64(X)
-    rp, ci = _i32(row_ptr), _i32(col_idx)
-    ln = _f64(edge_len)
     n = rp.shape[0] - 1
-    entry = {}
-    for u in range(n):
-        for e in range(rp[u], rp[u + 1]):
-            v = int(ci[e])
-            if v != u:
-                key = (min(u, v), max(u, v))
-                entry.setdefault(key, []).append(e)
-    g_edge = {k: 0.0 for k in entry}
+    out = []
     for s in range(n):
         dist = np.full(n, np.inf)
-        pred = np.full(n, -1, dtype=np.int64)
         dist[s] = 0.0
         heap = [(0.0, s)]
         done = np.zeros(n, dtype=bool)
@@ -451,8 +431,9 @@ def stress_length_grad(X, row_ptr, col_idx, edge_len) -> np.ndarray:
                     dist[v] = c
                     heapq.heappush(heap, (c, v))
         if not np.all(np.isfinite(dist)):
-            raise ValueError("stress_length_grad needs a connected graph")
-        for v in range(n):  # predecessor: the lowest-index tight neighbour
+            raise ValueError("a connected graph is needed")
+        pred = np.full(n, -1, dtype=np.int64)
+        for v in range(n):
             if v == s:
                 continue
             best = None
@@ -463,16 +444,34 @@ def stress_length_grad(X, row_ptr, col_idx, edge_len) -> np.ndarray:
             if best is None:  # rounding: take the neighbour closest to tight
                 best = min((abs(dist[int(ci[e])] + ln[e] - dist[v]), int(ci[e])) for e in range(rp[v], rp[v + 1]))[1]
             pred[v] = best
+        out.append((dist, pred))
+    return out
+
+
+def pair_to_edge_grad(row_ptr, col_idx, edge_len, G) -> np.ndarray:
+    """d L / d l_e from pair sensitivities G[i, j] = d L / d d_ij (symmetric
+    n x n) when d_ij is the weighted shortest-path length (Sec. 5.4): every
+    pair's path is walked back edge by edge (ties between paths have measure
+    zero; the lower predecessor index is taken).  One value per CSR entry,
+    equal for the two entries of an edge.  Connected graphs, small n."""
+    rp, ci = _i32(row_ptr), _i32(col_idx)
+    ln = _f64(edge_len)
+    n = rp.shape[0] - 1
+    entry = {}
+    for u in range(n):
+        for e in range(rp[u], rp[u + 1]):
+            v = int(ci[e])
+            if v != u:
+                entry.setdefault((min(u, v), max(u, v)), []).append(e)
+    g_edge = {k: 0.0 for k in entry}
+    for s, (dist, pred) in enumerate(_shortest_path_trees(rp, ci, ln)):
         for t in range(n):
             if t == s:
                 continue
-            r = float(np.linalg.norm(X[s] - X[t]))
-            d = dist[t]
-            G = -2.0 * r * (r - d) / d ** 3
             v = t
             while v != s:
                 u = int(pred[v])
-                g_edge[(min(u, v), max(u, v))] += 0.5 * G  # every pair is met from both ends
+                g_edge[(min(u, v), max(u, v))] += 0.5 * G[s, t]  # every pair is met from both ends
                 v = u
     out = np.zeros(len(ci), dtype=np.float64)
     for k, es in entry.items():
@@ -480,3 +479,84 @@ def stress_length_grad(X, row_ptr, col_idx, edge_len) -> np.ndarray:
             out[e] = g_edge[k]
     return out
 
+
+def stress_length_grad(X, row_ptr, col_idx, edge_len) -> np.ndarray:
+    """d f / d l_e for Eq. (1) when d_ij is the weighted shortest-path length
+    (Sec. 5.4) and w_ij = d_ij^-2 (Sec. 5.1).
+
+    f = sum_{i<j} (r_ij / d_ij - 1)^2, so d f / d d_ij = -2 r_ij (r_ij - d_ij) / d_ij^3,
+    and d d_ij / d l_e = 1 when e lies on the shortest path of (i, j) (0
+    otherwise).  Returns one value per CSR entry, equal for the two entries
+    of an undirected edge.  Connected graphs, small n.
+    """
+    X = _f64(X)
+    _, D = apsp(row_ptr, col_idx, edge_len=edge_len)
+    n = X.shape[0]
+    G = np.zeros((n, n))
+    for i in range(n):
+        for j in range(n):
+            if i != j:
+                r = float(np.linalg.norm(X[i] - X[j]))
+                G[i, j] = -2.0 * r * (r - D[i, j]) / D[i, j] ** 3
+    return pair_to_edge_grad(row_ptr, col_idx, edge_len, G)
+
+
+# --------------------------------------------------------------------------
+# Unrolled differentiation of Algorithm 2 (the acceptance of line 6 held fixed)
+# --------------------------------------------------------------------------
+
+def unrolled_run(D, X0, K: int, omega: float):
+    """K iterations of Algorithm 2 with exact solves; returns the layouts
+    X^0..X^K, the H-step outputs Z^1..Z^K and the acceptance of each step."""
+    solver = PinnedSolver(D)
+    Xs, Zs, acc = [_f64(X0).copy()], [], []
+    for _ in range(K):
+        X = Xs[-1]
+        Xn, fn, a, om, fZ = sor_step(X, D, omega, OMEGA_FIXED, solver)
+        Z = solver.solve(rhs(X, D))
+        Xs.append(Xn)
+        Zs.append(Z)
+        acc.append(bool(a))
+    return Xs, Zs, acc
+
+
+def unrolled_adjoint(D, Xs, Zs, acc, omega: float, Xbar_K):
+    """Backward pass of unrolled_run: returns dL/dX^0 and the pair
+    sensitivities dL/dd_ij (symmetric n x n) summed over the steps.
+
+    Per step (Eq. (2-5), pinning, Eq. (10)): Zb = (1+omega) Xb' or Xb', Xb = -omega Xb'
+    or 0; Yb = Zb - e_0 (1^T Zb); L^W lam = Yb; Xb += J_b(X)^T lam with
+    b_i = sum_j (1/d_ij) (x_i - x_j)/r_ij; dL/dd_ij += -(dlam . u)/d^2 + 2 (dlam . dY)/d^3.
+    Plain loops over pairs."""
+    D = _f64(D)
+    n = D.shape[0]
+    solver = PinnedSolver(D)
+    Xb1 = _f64(Xbar_K).copy()
+    Gd = np.zeros((n, n))
+    for k in reversed(range(len(acc))):
+        X, Y = Xs[k], Zs[k]
+        if acc[k]:
+            Zb, Xb = (1.0 + omega) * Xb1, -omega * Xb1
+        else:
+            Zb, Xb = Xb1.copy(), np.zeros_like(Xb1)
+        Yb = Zb.copy()
+        Yb[0] -= Zb.sum(axis=0)
+        lam = solver.solve(Yb)
+        for i in range(n):
+            for j in range(i + 1, n):
+                d = D[i, j]
+                dx = X[i] - X[j]
+                dl = lam[i] - lam[j]
+                g = 2.0 * float(dl @ (Y[i] - Y[j])) / d ** 3
+                r = float(np.linalg.norm(dx))
+                if r > 0.0:
+                    u = dx / r
+                    ul = float(u @ dl)
+                    g -= ul / d ** 2
+                    v = (dl - u * ul) / (d * r)
+                    Xb[i] += v
+                    Xb[j] -= v
+                Gd[i, j] += g
+                Gd[j, i] += g
+        Xb1 = Xb
+    return Xb1, Gd

@@ -68,7 +68,8 @@ EXPORTED = ["fd_options_default", "fd_layout_create", "fd_layout_destroy", "fd_e
             "fd_last_stats", "fd_last_error", "fd_status_string", "fd_energy_noalloc", "fd_timeline_enable",
             "fd_timeline_read", "fd_batch_create", "fd_batch_destroy", "fd_batch_run", "fd_batch_results",
             "fd_batch_tune", "fd_batch_set_shape", "fd_batch_distances", "fd_batch_get_info",
-            "fd_batch_last_stats", "fd_energy_length_grad"]
+            "fd_batch_last_stats", "fd_energy_length_grad", "fd_sor_step_adjoint", "fd_adjoint_reset",
+            "fd_adjoint_length_grad"]
 GRAD_MAX_N = 4096
 BATCH_MAX_N = 2048
 TIMELINE_TAGS = {1: "pack", 2: "stress", 3: "forces", 4: "rhs0", 5: "h_init", 6: "cg_au0", 7: "cg_step",
@@ -146,8 +147,22 @@ def lib():
     L.fd_batch_last_stats.restype = i32
     L.fd_energy_length_grad.argtypes = [P, P, P, ctypes.POINTER(f64)]
     L.fd_energy_length_grad.restype = i32
+    L.fd_sor_step_adjoint.argtypes = [P, P, P, i32, f64, P, P, ctypes.POINTER(Options), ctypes.POINTER(i32)]
+    L.fd_sor_step_adjoint.restype = i32
+    L.fd_adjoint_reset.argtypes = [P]
+    L.fd_adjoint_reset.restype = i32
+    L.fd_adjoint_length_grad.argtypes = [P, P]
+    L.fd_adjoint_length_grad.restype = i32
     _LIB = L
     return L
+
+
+def torch_empty_like(a):
+    """An uninitialised array of a's kind, shape and dtype."""
+    if _is_torch(a):
+        import torch
+        return torch.empty_like(a)
+    return np.empty_like(a)
 
 
 def _check(status: int, where: str):
@@ -304,6 +319,29 @@ class Layout:
         _check(lib().fd_energy_length_grad(self._h, _ptr(X, np.float32), _ptr(out, np.float32), ctypes.byref(f)),
                "fd_energy_length_grad")
         return f.value, out
+
+    def sor_step_adjoint(self, X_k, X_k1, accepted: bool, omega: float, Xbar_k1, out=None, **opts):
+        """dL/dX_k from dL/dX_k1 through one iteration of Algorithm 2 (acceptance
+        held fixed); adds the pair sensitivities to the accumulator after
+        adjoint_reset().  Returns (Xbar_k, CG steps of the adjoint solve)."""
+        if out is None:
+            out = torch_empty_like(X_k)
+        o = options(**opts)
+        cg = ctypes.c_int32()
+        _check(lib().fd_sor_step_adjoint(self._h, _ptr(X_k, np.float32), _ptr(X_k1, np.float32), int(bool(accepted)),
+                                         float(omega), _ptr(Xbar_k1, np.float32), _ptr(out, np.float32),
+                                         ctypes.byref(o), ctypes.byref(cg)), "fd_sor_step_adjoint")
+        return out, cg.value
+
+    def adjoint_reset(self):
+        _check(lib().fd_adjoint_reset(self._h), "fd_adjoint_reset")
+
+    def adjoint_length_grad(self, out=None):
+        """dL/dl_e from the pair sensitivities accumulated since adjoint_reset()."""
+        if out is None:
+            out = np.empty(self._nnz, dtype=np.float32)
+        _check(lib().fd_adjoint_length_grad(self._h, _ptr(out, np.float32)), "fd_adjoint_length_grad")
+        return out
 
     def sor_step(self, X, k: int = 0, **opts):
         """One iteration of Algorithm 2 in place on X; returns (f, accepted, crit)."""

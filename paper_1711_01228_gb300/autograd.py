@@ -13,6 +13,10 @@ so each entry receives half of the edge's derivative (a per-edge parameter
 scattered to both entries gets the whole derivative back).  Each forward
 call rebuilds the distances for the current lengths (``fd_layout_create``).
 
+``unrolled_layout(X0, l, row_ptr, col_idx, K, omega, every)`` is X^K after K
+iterations of Algorithm 2, differentiable in X0 and l through the adjoint of
+each iteration (checkpoints every ``every`` iterations).
+
 Argument marshalling only: every value comes from the CUDA library.
 """
 from __future__ import annotations
@@ -66,3 +70,56 @@ def stress_lengths(X: torch.Tensor, edge_len: torch.Tensor, row_ptr, col_idx) ->
     """f(X; l) for a weighted graph; differentiable in X and in the edge
     lengths l (float32, one per CSR entry, equal for an edge's two entries)."""
     return _StressLengths.apply(X, edge_len, row_ptr, col_idx)
+
+
+class _Unrolled(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, X0, edge_len, row_ptr, col_idx, K, omega, every, cg_tol, cg_max):
+        lens = edge_len.detach().contiguous()
+        L = api.Layout(row_ptr, col_idx, dim=int(X0.shape[1]), edge_len=lens, stream=None)
+        opts = dict(omega=float(omega), strategy=api.OMEGA_FIXED, cg_tol=cg_tol, cg_max=cg_max)
+        X = X0.detach().contiguous().clone()
+        ckpt = {0: X.clone()}
+        for k in range(K):
+            L.sor_step(X, k=k, **opts)
+            if (k + 1) % every == 0 and k + 1 < K:
+                ckpt[k + 1] = X.clone()
+        ctx.L, ctx.ckpt, ctx.K, ctx.every, ctx.opts = L, ckpt, K, every, opts
+        ctx.lens_dtype = edge_len.dtype
+        return X
+
+    @staticmethod
+    def backward(ctx, gXK):
+        L, K, every, opts = ctx.L, ctx.K, ctx.every, ctx.opts
+        L.adjoint_reset()
+        xbar = gXK.detach().contiguous().clone()
+        for s in reversed(range(0, K, every)):
+            # recompute the layouts of this segment from its checkpoint
+            X = ctx.ckpt[s].clone()
+            traj, accs = [X.clone()], []
+            for k in range(s, min(s + every, K)):
+                _, acc, _ = L.sor_step(X, k=k, **opts)
+                traj.append(X.clone())
+                accs.append(acc)
+            for k in reversed(range(len(accs))):
+                xbar, _ = L.sor_step_adjoint(traj[k], traj[k + 1], accs[k], opts["omega"], xbar,
+                                             cg_tol=opts["cg_tol"], cg_max=opts["cg_max"])
+        g_full = torch.empty(L._nnz, dtype=torch.float32, device=gXK.device)
+        L.adjoint_length_grad(out=g_full)
+        L.close()
+        ctx.L = None
+        return xbar, (0.5 * g_full).to(ctx.lens_dtype), None, None, None, None, None, None, None
+
+
+def unrolled_layout(X0: torch.Tensor, edge_len: torch.Tensor, row_ptr, col_idx, K: int = 32, omega: float = 0.5,
+                    every: int = 8, cg_tol: float = 1e-6, cg_max: int = 500) -> torch.Tensor:
+    """X^K after K iterations of Algorithm 2 (fixed omega) from X0 on a
+    weighted graph; differentiable in X0 and in the edge lengths.  The
+    backward pass recomputes the layouts from checkpoints taken every
+    ``every`` iterations and runs the adjoint of each iteration
+    (``fd_sor_step_adjoint``; the acceptance of line 6 held at its forward
+    outcome), then pushes the summed pair sensitivities through the shortest
+    paths (``fd_adjoint_length_grad``).  As in ``stress_lengths``, each CSR
+    entry of an edge receives half of the edge's derivative."""
+    return _Unrolled.apply(X0, edge_len, row_ptr, col_idx, int(K), float(omega), int(every), float(cg_tol),
+                           int(cg_max))

@@ -41,6 +41,13 @@ cudaError_t launch_fill_multi(const BGraph* graphs, const int* tile_graph, const
 cudaError_t launch_rowsum_multi(const BGraph* graphs, const int2* items, int nitems, const unsigned char* D, float* s,
                                 float* inv_s, int grid, cudaStream_t st);
 cudaError_t launch_distance_graph(const unsigned char* Dg, int n, int nb, double* out, cudaStream_t st);
+cudaError_t launch_adjoint_prep(int n, int dim, const float* Xk, const float* Xk1, const float* Xb1, int accepted,
+                                float omega, float* Y, float* Yb, float* Xb, cudaStream_t st);
+cudaError_t launch_pair_adjoint(int code, int n, int nb, int dim, const int2* tile_ik, int ntiles, const void* D,
+                                const float* X, const float* lam, const float* Y, float* Xb, float* Db, int sm_count,
+                                cudaStream_t st);
+cudaError_t launch_sp_backprop(int n, int nb, const float* Gt, const int* rp, const int* ci, const float* len,
+                               const int* rev, int nnz, float* gacc, float* out, int sm_count, cudaStream_t st);
 cudaError_t launch_length_grad(int n, int nb, int dim, const int2* tile_ik, int ntiles, const float* D,
                                const float* X, float* Gt, const int* rp, const int* ci, const float* len,
                                const int* rev, int nnz, float* gacc, float* out, int sm_count, cudaStream_t st);
@@ -106,6 +113,9 @@ struct fd_layout {
   int wnnz = 0;
   int wsimple = 0;        // no self loops, no repeated entries
   int bfs_sweeps = 0;     // passes over the edge list of all 64-source searches
+  // unrolled differentiation: pair sensitivities summed over the adjoint steps (tile layout)
+  float* d_dbar = nullptr;
+  float* d_adj = nullptr;  // [4][n][dim]: Y, Yb, lam, Xb staging
 };
 
 namespace {
@@ -319,6 +329,8 @@ void release(fd_layout* h) {
   dev_free(h->d_wci);
   dev_free(h->d_wlen);
   dev_free(h->d_wrev);
+  dev_free(h->d_dbar);
+  dev_free(h->d_adj);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
   h->ev0 = h->ev1 = nullptr;
@@ -855,6 +867,127 @@ fd_status fd_energy_length_grad(fd_layout* h, const float* X, float* grad_len, d
     return fail(h, cuda_status(e));
   }
   if (f_out) *f_out = c.f_final;
+  return FD_OK;
+}
+
+// Tile coordinates (block row, strip offset) of every stored tile, on the device.
+static fd_status upload_tile_ik(fd_layout* h, int2** out) {
+  std::vector<int2> tile_ik(h->ntiles);
+  for (int I = 0; I < h->nb; ++I)
+    for (int k = 0; k < h->strip_len[I]; ++k) tile_ik[h->tile_base[I] + k] = make_int2(I, k);
+  fd_status s = dev_alloc(out, (size_t)h->ntiles);
+  if (s != FD_OK) return s;
+  FD_CK(cudaMemcpyAsync(*out, tile_ik.data(), h->ntiles * sizeof(int2), cudaMemcpyHostToDevice, h->stream));
+  return FD_OK;
+}
+
+fd_status fd_adjoint_reset(fd_layout* h) {
+  if (!h) return FD_ERR_ARG;
+  if (h->code != CODE_F32 || !h->d_wrp || h->wnnz == 0) return fail(h, FD_ERR_ARG);
+  if (h->n > FD_GRAD_MAX_N || h->disconnected || !h->wsimple) return fail(h, FD_ERR_UNIMPLEMENTED);
+  const size_t cnt = (size_t)h->ntiles * TILE * TILE;
+  if (!h->d_dbar) {
+    fd_status s = dev_alloc(&h->d_dbar, cnt);
+    if (s != FD_OK) return fail(h, s);
+  }
+  if (cudaMemsetAsync(h->d_dbar, 0, cnt * sizeof(float), h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, FD_ERR_CUDA);
+  }
+  return FD_OK;
+}
+
+fd_status fd_sor_step_adjoint(fd_layout* h, const float* X_k, const float* X_k1, int32_t accepted, double omega,
+                              const float* Xbar_k1, float* Xbar_k, const fd_options* opt, int32_t* cg_steps) {
+  if (!h) return FD_ERR_ARG;
+  if (!X_k || !X_k1 || !Xbar_k1 || !Xbar_k || !(omega >= 0.0) || !std::isfinite(omega)) return fail(h, FD_ERR_ARG);
+  fd_options o;
+  fd_options_default(&o);
+  if (opt) o = *opt;
+  if (o.cg_max < 0 || !(o.cg_tol >= 0.0)) return fail(h, FD_ERR_ARG);
+  const size_t nd = (size_t)h->n * h->dim;
+  fd_status s = FD_OK;
+  if (!h->d_adj && (s = dev_alloc(&h->d_adj, 7 * nd)) != FD_OK) return fail(h, s);
+  float* Y = h->d_adj;
+  float* Yb = Y + nd;
+  float* lam = Y + 2 * nd;
+  float* Xb = Y + 3 * nd;
+  float* in0 = Y + 4 * nd;  // staging of host inputs
+  float* in1 = Y + 5 * nd;
+  float* in2 = Y + 6 * nd;
+  cudaStream_t st = h->stream;
+  auto stage = [&](const float* src, float* dst) -> const float* {
+    if (is_device_ptr(src)) return src;
+    if (cudaMemcpyAsync(dst, src, nd * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess) return nullptr;
+    return dst;
+  };
+  const float* xk = stage(X_k, in0);
+  const float* xk1 = stage(X_k1, in1);
+  const float* xb1 = stage(Xbar_k1, in2);
+  if (!xk || !xk1 || !xb1) {
+    cudaGetLastError();
+    return fail(h, FD_ERR_CUDA);
+  }
+  const bool dev_out = is_device_ptr(Xbar_k);
+  float* xb = dev_out ? Xbar_k : Xb;
+  if (launch_adjoint_prep(h->n, h->dim, xk, xk1, xb1, accepted ? 1 : 0, (float)omega, Y, Yb, xb, st) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, FD_ERR_CUDA);
+  }
+  // lam: L^W lam = Yb (one H-step solve of the layout kernel)
+  KParams p = base_params(h, KM_SOLVE);
+  p.x_in = Yb;
+  p.x_out = lam;
+  p.max_iter = 1;
+  p.cg_max = o.cg_max;
+  p.cg_tol = o.cg_tol;
+  p.tol = 0.0;
+  Ctrl c;
+  double kms = 0.0;
+  std::memset(&c, 0, sizeof(c));
+  s = run_kernel(h, p, &c, &kms);
+  fill_stats(h, c, kms);
+  if (s != FD_OK) return fail(h, s);
+  int2* d_tik = nullptr;
+  if ((s = upload_tile_ik(h, &d_tik)) != FD_OK) return fail(h, s);
+  cudaError_t e = launch_pair_adjoint(h->code, h->n, h->nb, h->dim, d_tik, h->ntiles, h->D, xk, lam, Y, xb, h->d_dbar,
+                                      h->sm_count, st);
+  if (e == cudaSuccess && !dev_out)
+    e = cudaMemcpyAsync(Xbar_k, xb, nd * sizeof(float), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  dev_free(d_tik);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, cuda_status(e));
+  }
+  if (cg_steps) *cg_steps = c.cg_steps;
+  return FD_OK;
+}
+
+fd_status fd_adjoint_length_grad(fd_layout* h, float* grad_len) {
+  if (!h || !grad_len) return FD_ERR_ARG;
+  if (!h->d_dbar) return fail(h, FD_ERR_ARG);  // fd_adjoint_reset first
+  float *d_acc = nullptr, *d_out = nullptr;
+  const bool dev_out = is_device_ptr(grad_len);
+  fd_status s = dev_alloc(&d_acc, (size_t)h->wnnz);
+  if (s == FD_OK && !dev_out) s = dev_alloc(&d_out, (size_t)h->wnnz);
+  if (s != FD_OK) {
+    dev_free(d_acc);
+    return fail(h, s);
+  }
+  cudaStream_t st = h->stream;
+  cudaError_t e = launch_sp_backprop(h->n, h->nb, h->d_dbar, h->d_wrp, h->d_wci, h->d_wlen, h->d_wrev, h->wnnz, d_acc,
+                                     dev_out ? grad_len : d_out, h->sm_count, st);
+  if (e == cudaSuccess && !dev_out)
+    e = cudaMemcpyAsync(grad_len, d_out, (size_t)h->wnnz * sizeof(float), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  dev_free(d_acc);
+  dev_free(d_out);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, cuda_status(e));
+  }
   return FD_OK;
 }
 

@@ -158,6 +158,153 @@ __global__ void combine_directions_kernel(int nnz, const int* __restrict__ rev, 
     out[e] = 0.5f * (gacc[e] + gacc[rev[e]]);
 }
 
+// --------------------------------------------------------------------------
+// Adjoint of one iteration of Algorithm 2 (lines 4-8), for unrolled
+// differentiation.  Forward: b = L^X X (Prop. 2.1), Y solves L^W Y = b,
+// Z = Y - 1 y_0^T (pinning), X' = (1 + omega) Z - omega X if line 6 accepted
+// the extrapolation (Eq. (10)), else X' = Z.  The acceptance decision is held
+// fixed.  Backward, from Xb' = dL/dX':
+//   Zb = (1 + omega) Xb' or Xb';  Xb = -omega Xb' or 0
+//   Yb = Zb - e_0 (1^T Zb)                   (adjoint of the pinning)
+//   L^W lam = Yb                             (KM_SOLVE of the layout kernel)
+//   Xb += J_b(X)^T lam,  per pair: (1/(d r)) (dlam - u (u . dlam)) to i, minus that to j
+//   db_ij += -(dlam . u) / d^2 + 2 (dlam . dY) / d^3   (through b and through L^W)
+// with u = (x_i - x_j)/r, dlam = lam_i - lam_j, dY = Y_i - Y_j.
+// --------------------------------------------------------------------------
+
+// One CTA: Z (recovered from X' and X), the right-hand side Yb of the adjoint
+// solve, and the part of Xb that does not pass through the solve.
+__global__ void __launch_bounds__(1024) adjoint_prep_kernel(int n, int dim, const float* __restrict__ Xk,
+                                                            const float* __restrict__ Xk1, const float* __restrict__ Xb1,
+                                                            int accepted, float omega, float* Y, float* Yb, float* Xb) {
+  __shared__ double part[32][3];
+  double s[3] = {0.0, 0.0, 0.0};
+  const float zs = accepted ? 1.f + omega : 1.f;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    for (int d = 0; d < dim; ++d) {
+      const size_t k = (size_t)i * dim + d;
+      const float xb1 = Xb1[k];
+      Y[k] = accepted ? (Xk1[k] + omega * Xk[k]) / (1.f + omega) : Xk1[k];
+      const float zb = zs * xb1;
+      Yb[k] = zb;
+      Xb[k] = accepted ? -omega * xb1 : 0.f;
+      s[d] += (double)zb;
+    }
+  }
+  for (int d = 0; d < 3; ++d)
+    for (int o = 16; o > 0; o >>= 1) s[d] += __shfl_down_sync(0xffffffffu, s[d], o);
+  if ((threadIdx.x & 31) == 0)
+    for (int d = 0; d < 3; ++d) part[threadIdx.x >> 5][d] = s[d];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int d = 0; d < dim; ++d) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w][d];
+      Yb[d] = (float)((double)Yb[d] - t);  // vertex 0 is pinned
+    }
+  }
+}
+
+// One CTA per tile: the vector-Jacobian product of b = L^X X with lam, and
+// the pair sensitivities, added to Xb (atomics) and to the float tile array Db.
+template <int CODE>
+__global__ void __launch_bounds__(TILE) pair_adjoint_kernel(int n, int nb, int dim, const int2* __restrict__ tile_ik,
+                                                            int ntiles, const void* __restrict__ D,
+                                                            const float* __restrict__ X, const float* __restrict__ lam,
+                                                            const float* __restrict__ Y, float* Xb, float* Db) {
+  __shared__ float xi[TILE][3], xj[TILE][3], li[TILE][3], lj[TILE][3], yi[TILE][3], yj[TILE][3];
+  __shared__ float colacc[TILE][3];
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int2 ik = tile_ik[t];
+    const int I = ik.x, J = (ik.x + ik.y) % nb;
+    const int i = I * TILE + threadIdx.x, j = J * TILE + threadIdx.x;
+    for (int d = 0; d < 3; ++d) {
+      const bool ri = (i < n && d < dim), rj = (j < n && d < dim);
+      xi[threadIdx.x][d] = ri ? X[(size_t)i * dim + d] : 0.f;
+      xj[threadIdx.x][d] = rj ? X[(size_t)j * dim + d] : 0.f;
+      li[threadIdx.x][d] = ri ? lam[(size_t)i * dim + d] : 0.f;
+      lj[threadIdx.x][d] = rj ? lam[(size_t)j * dim + d] : 0.f;
+      yi[threadIdx.x][d] = ri ? Y[(size_t)i * dim + d] : 0.f;
+      yj[threadIdx.x][d] = rj ? Y[(size_t)j * dim + d] : 0.f;
+      colacc[threadIdx.x][d] = 0.f;
+    }
+    __syncthreads();
+    const int il = threadIdx.x;
+    float rowacc[3] = {0.f, 0.f, 0.f};
+    for (int jj = 0; jj < TILE; ++jj) {
+      const int jl = (il + jj) & (TILE - 1);  // rotate the columns so that the shared-memory atomics spread
+      const size_t off = (size_t)t * TILE * TILE + (size_t)jl * TILE + il;
+      float dd;
+      if constexpr (CODE == CODE_U8) dd = (float)reinterpret_cast<const unsigned char*>(D)[off];
+      else dd = reinterpret_cast<const float*>(D)[off];
+      if (!(dd > 0.f)) continue;
+      float dx[3], dl[3], r2 = 0.f, ul = 0.f, ly = 0.f;
+      for (int d = 0; d < dim; ++d) {
+        dx[d] = xi[il][d] - xj[jl][d];
+        dl[d] = li[il][d] - lj[jl][d];
+        r2 = fmaf(dx[d], dx[d], r2);
+        ly = fmaf(dl[d], yi[il][d] - yj[jl][d], ly);
+      }
+      const float inv_d = 1.f / dd;
+      float g = 2.f * ly * inv_d * inv_d * inv_d;  // through w = d^-2 in L^W
+      if (r2 > 0.f) {
+        const float r = sqrtf(r2), inv_r = 1.f / r;
+        for (int d = 0; d < dim; ++d) ul = fmaf(dx[d] * inv_r, dl[d], ul);
+        g -= ul * inv_d * inv_d;  // through the coefficient 1/d of b
+        const float c = inv_d * inv_r;
+        for (int d = 0; d < dim; ++d) {
+          const float v = c * (dl[d] - dx[d] * inv_r * ul);
+          rowacc[d] += v;
+          atomicAdd(&colacc[jl][d], -v);
+        }
+      }
+      if (Db) Db[off] += g;
+    }
+    __syncthreads();
+    if (i < n)
+      for (int d = 0; d < dim; ++d) atomicAdd(Xb + (size_t)i * dim + d, rowacc[d]);
+    if (j < n)
+      for (int d = 0; d < dim; ++d) atomicAdd(Xb + (size_t)j * dim + d, colacc[threadIdx.x][d]);
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_adjoint_prep(int n, int dim, const float* Xk, const float* Xk1, const float* Xb1, int accepted,
+                                float omega, float* Y, float* Yb, float* Xb, cudaStream_t st) {
+  adjoint_prep_kernel<<<1, 1024, 0, st>>>(n, dim, Xk, Xk1, Xb1, accepted, omega, Y, Yb, Xb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pair_adjoint(int code, int n, int nb, int dim, const int2* tile_ik, int ntiles, const void* D,
+                                const float* X, const float* lam, const float* Y, float* Xb, float* Db, int sm_count,
+                                cudaStream_t st) {
+  const int grid = ntiles < 8 * sm_count ? ntiles : 8 * sm_count;
+  if (code == CODE_U8)
+    pair_adjoint_kernel<CODE_U8><<<grid > 0 ? grid : 1, TILE, 0, st>>>(n, nb, dim, tile_ik, ntiles, D, X, lam, Y, Xb, Db);
+  else
+    pair_adjoint_kernel<CODE_F32><<<grid > 0 ? grid : 1, TILE, 0, st>>>(n, nb, dim, tile_ik, ntiles, D, X, lam, Y, Xb, Db);
+  return cudaGetLastError();
+}
+
+// Shortest-path back-propagation of an array of pair sensitivities (tile layout) to the edges.
+cudaError_t launch_sp_backprop(int n, int nb, const float* Gt, const int* rp, const int* ci, const float* len,
+                               const int* rev, int nnz, float* gacc, float* out, int sm_count, cudaStream_t st) {
+  int npow2 = 1;
+  while (npow2 < n) npow2 <<= 1;
+  const size_t smem = (size_t)npow2 * 8 + (size_t)n * 12;
+  cudaError_t e = cudaFuncSetAttribute(sp_backprop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(gacc, 0, (size_t)nnz * sizeof(float), st);
+  if (e != cudaSuccess) return e;
+  const int sgrid = n < 2 * sm_count ? n : 2 * sm_count;
+  sp_backprop_kernel<<<sgrid, 256, smem, st>>>(n, nb, npow2, rp, ci, len, Gt, gacc);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int cgrid = (nnz + 255) / 256;
+  if (nnz > 0) combine_directions_kernel<<<cgrid < 4096 ? cgrid : 4096, 256, 0, st>>>(nnz, rev, gacc, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_length_grad(int n, int nb, int dim, const int2* tile_ik, int ntiles, const float* D,
                                const float* X, float* Gt, const int* rp, const int* ci, const float* len,
                                const int* rev, int nnz, float* gacc, float* out, int sm_count, cudaStream_t st) {

@@ -32,7 +32,9 @@ constexpr int MAX_CTA_TASKS = 128; // task descriptors a CTA keeps in shared mem
 enum CodeKind { CODE_U8 = 0, CODE_F32 = 1 };
 
 // Modes of the cooperative kernel.
-enum KernelMode { KM_ENERGY = 0, KM_FORCES = 1, KM_RUN = 2 };
+// KM_SOLVE: one H-step solve of L^W Y = B for a given B (x_in), Y pinned at
+// vertex 0 (the adjoint of Eq. (2-5) needs it with another right-hand side).
+enum KernelMode { KM_ENERGY = 0, KM_FORCES = 1, KM_RUN = 2, KM_SOLVE = 3 };
 
 // Error codes shared with fd_status (include/fd_layout.h).
 enum {

@@ -1098,9 +1098,15 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
       v.c[d] = x;
     }
     if (bad) set_error(ctrl, E_NONFINITE);
-    stv<DIM>(p.X, i, v);
 #pragma unroll
     for (int c = 0; c < 3; ++c) stv<DIM>(p.acc + c * vs, i, vzero<DIM>());
+    if (p.mode == KM_SOLVE) {
+      // the given right-hand side takes the place of L^X X; the CG starts from 0
+      stv<DIM>(p.X, i, vzero<DIM>());
+      stv<DIM>(acc0, i, v);
+    } else {
+      stv<DIM>(p.X, i, v);
+    }
   }
   FD_SYNC(1);
 
@@ -1143,17 +1149,21 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
   // values from the same reductions, so control flow is uniform over the grid.
   RunState* rs = reinterpret_cast<RunState*>(smem + L::OFF_RUN);
 #define cgt2 ((float)(p.cg_tol * p.cg_tol))
-  // b = L^{X^0} X^0 (right-hand side of Eq. (2-5)) and f(X^0) (Eq. (1))
-  if (!pair_pass<DIM, PM_RHS, 1, CODE>(p, smem, ps, direct_src(p.X), acc0)) return;
-  FD_SYNC_RED(4, red_stress(1));
+  // b = L^{X^0} X^0 (right-hand side of Eq. (2-5)) and f(X^0) (Eq. (1));
+  // KM_SOLVE has its right-hand side already
+  if (p.mode != KM_SOLVE) {
+    if (!pair_pass<DIM, PM_RHS, 1, CODE>(p, smem, ps, direct_src(p.X), acc0)) return;
+    FD_SYNC_RED(4, red_stress(1));
+  }
   if (tid == 0) {
     df f[1];
-    load_red<1>(ctrl, f);
+    if (p.mode != KM_SOLVE) load_red<1>(ctrl, f);
+    else f[0] = df_of(0.f);
     const double f0 = df_to_double(f[0]);
     rs->f_cur = rs->f_new = f0;
     rs->crit = 0.0;
     rs->passes_mv = 0.0;
-    rs->passes_st = 1.0;
+    rs->passes_st = (p.mode != KM_SOLVE) ? 1.0 : 0.0;
     rs->cg_total = rs->cg_maxed = rs->cg_stalled = rs->n_acc = rs->it_outer = 0;
     rs->accept = 0;
     rs->bsel = 0;
@@ -1161,7 +1171,7 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
     for (int d = 0; d < 3; ++d) rs->z0[d] = 0.f;
     rs->stop = isfinite(f0) ? 0 : 1;
     if (rs->stop) set_error(ctrl, E_NONFINITE);
-    if (blockIdx.x == 0) p.trace_f[0] = f0;
+    if (blockIdx.x == 0 && p.mode != KM_SOLVE) p.trace_f[0] = f0;
   }
   __syncthreads();
   if (rs->stop) return;
@@ -1416,6 +1426,28 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
       }
     }
 
+    if (p.mode == KM_SOLVE) {
+      // Y = the CG solution with vertex 0 moved to the origin (Sec. 2 after Prop. 2.3)
+      const Vec<DIM> zz = ldv<DIM>(p.Zw, 0);
+      for (int R = blockIdx.x; R < nb; R += gridDim.x) {
+        const int i = R * TILE + tid;
+        if (i < n) {
+          const Vec<DIM> z = ldv<DIM>(p.Zw, i);
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) p.x_out[(size_t)i * DIM + d] = z.c[d] - zz.c[d];
+        }
+      }
+      if (blockIdx.x == 0 && tid == 0) {
+        ctrl->iters = 0;
+        ctrl->cg_steps = rs->it;
+        ctrl->cg_maxed = rs->cg_maxed;
+        ctrl->cg_stalled = rs->cg_stalled;
+        ctrl->pair_passes = rs->passes_mv;
+        ctrl->matvec_passes = rs->passes_mv;
+        ctrl->stress_passes = 0.0;
+      }
+      return;
+    }
     if (WITH_ENUM && p.enum_omega) {
       // ---- enumerating strategy (Sec. 5.2.2): the stress of every
       // (1 + omega) z - omega x, omega in {0, 0.5, ..., 9}, from one pass; the

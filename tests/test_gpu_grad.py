@@ -137,3 +137,51 @@ def test_length_gradient_errors():
         with pytest.raises(api.FdError) as e:
             L.length_grad(synth.initial_layout(4225, 2, 0))
         assert e.value.status == 10
+
+
+@pytest.mark.parametrize("omega", [0.0, 0.5])
+def test_unrolled_adjoint_matches_oracle(omega):
+    """Gradient of a loss on X^K (K = 4 iterations of Algorithm 2, checkpoints
+    every 2) in X^0 and in the edge lengths, against the FP64 oracle's adjoint
+    (itself pinned by finite differences), with the same acceptance decisions."""
+    import torch
+
+    from paper_1711_01228_gb300 import autograd
+
+    rp, ci, w, _ = _weighted_rgg(64, 3, 11)
+    n, K = 64, 4
+    rng = np.random.default_rng(5)
+    X0 = (rng.random((n, 3)) * 3.0).astype(np.float32)
+    pairs = np.array([rng.choice(n, 2, replace=False) for _ in range(40)])
+    targets = rng.uniform(0.5, 4.0, size=len(pairs))
+    Xt = torch.from_numpy(X0).cuda().requires_grad_(True)
+    lt = torch.from_numpy(w).cuda().requires_grad_(True)
+    XK = autograd.unrolled_layout(Xt, lt, torch.from_numpy(rp), torch.from_numpy(ci), K=K, omega=omega, every=2,
+                                  cg_tol=1e-7, cg_max=1000)
+    pi, pj = torch.from_numpy(pairs[:, 0]).cuda(), torch.from_numpy(pairs[:, 1]).cuda()
+    tt = torch.from_numpy(targets).cuda()
+    loss = ((XK[pi] - XK[pj]).double().norm(dim=1) - tt).pow(2).sum()
+    loss.backward()
+    # the GPU's acceptance decisions, from a plain re-run
+    accs = []
+    with api.Layout(rp, ci, dim=3, edge_len=w) as L:
+        X = X0.copy()
+        for k in range(K):
+            _, acc, _ = L.sor_step(X, k=k, omega=omega, cg_tol=1e-7, cg_max=1000)
+            accs.append(bool(acc))
+    D = oracle.apsp(rp, ci, edge_len=w.astype(np.float64))[1]
+    Xs, Zs, acc_ref = oracle.unrolled_run(D, X0.astype(np.float64), K, omega)
+    assert accs == acc_ref
+    XKr = Xs[-1]
+    gK = np.zeros_like(XKr)
+    for (i, j), t in zip(pairs, targets):
+        dx = XKr[i] - XKr[j]
+        r = np.linalg.norm(dx)
+        gK[i] += 2 * (r - t) * dx / r
+        gK[j] -= 2 * (r - t) * dx / r
+    gX0, Gd = oracle.unrolled_adjoint(D, Xs, Zs, acc_ref, omega, gK)
+    gw = 0.5 * oracle.pair_to_edge_grad(rp, ci, w.astype(np.float64), Gd)
+    g_x = Xt.grad.cpu().numpy().astype(np.float64)
+    g_l = lt.grad.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(g_x - gX0) <= 2e-3 * np.linalg.norm(gX0)
+    assert np.linalg.norm(g_l - gw) <= 2e-3 * np.linalg.norm(gw)

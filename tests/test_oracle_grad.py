@@ -71,3 +71,69 @@ def test_length_grad_matches_finite_differences(seed):
             fm = oracle.stress(X, oracle.apsp(rp, ci, edge_len=wm)[1])
             fd = (fp - fm) / (2 * h)
             assert g[e] == pytest.approx(fd, rel=1e-5, abs=1e-7), key
+
+
+def _loss_and_grad(XK, pairs, targets):
+    L = 0.0
+    g = np.zeros_like(XK)
+    for (i, j), t in zip(pairs, targets):
+        dx = XK[i] - XK[j]
+        r = float(np.linalg.norm(dx))
+        L += (r - t) ** 2
+        g[i] += 2.0 * (r - t) * dx / r
+        g[j] -= 2.0 * (r - t) * dx / r
+    return L, g
+
+
+@pytest.mark.parametrize("omega", [0.0, 0.5])
+def test_unrolled_adjoint_matches_finite_differences(omega):
+    # K = 3 iterations of Algorithm 2 on a weighted 16-vertex graph; loss on sampled pair distances
+    rp, ci = synth.grid(4, 4)
+    rng = np.random.default_rng(3)
+    w = _sym_lengths(rp, ci, rng)
+    n, K = 16, 3
+    X0 = rng.random((n, 2)) * 2.0
+    pairs = [tuple(rng.choice(n, 2, replace=False)) for _ in range(12)]
+    targets = rng.uniform(0.5, 3.0, size=len(pairs))
+
+    def run(X0_, w_):
+        D = oracle.apsp(rp, ci, edge_len=w_)[1]
+        Xs, Zs, acc = oracle.unrolled_run(D, X0_, K, omega)
+        return Xs, Zs, acc, D
+
+    Xs, Zs, acc, D = run(X0, w)
+    L0, gK = _loss_and_grad(Xs[-1], pairs, targets)
+    gX0, Gd = oracle.unrolled_adjoint(D, Xs, Zs, acc, omega, gK)
+    gw = oracle.pair_to_edge_grad(rp, ci, w, Gd)
+    h = 1e-6
+    checked = 0
+    for i in range(n):
+        for d in range(2):
+            Xp, Xm = X0.copy(), X0.copy()
+            Xp[i, d] += h
+            Xm[i, d] -= h
+            rp_, rm_ = run(Xp, w), run(Xm, w)
+            if rp_[2] != acc or rm_[2] != acc:
+                continue  # an acceptance decision flipped: not differentiable here
+            fd = (_loss_and_grad(rp_[0][-1], pairs, targets)[0] - _loss_and_grad(rm_[0][-1], pairs, targets)[0]) / (2 * h)
+            assert gX0[i, d] == pytest.approx(fd, rel=1e-4, abs=1e-6 * max(1.0, abs(L0)))
+            checked += 1
+    assert checked >= 24
+    seen = set()
+    for u in range(n):
+        for e in range(rp[u], rp[u + 1]):
+            v = int(ci[e])
+            key = (min(u, v), max(u, v))
+            if key in seen:
+                continue
+            seen.add(key)
+            idx = [k for k in range(rp[key[0]], rp[key[0] + 1]) if ci[k] == key[1]] + \
+                  [k for k in range(rp[key[1]], rp[key[1] + 1]) if ci[k] == key[0]]
+            wp, wm = w.copy(), w.copy()
+            wp[idx] += h
+            wm[idx] -= h
+            rp_, rm_ = run(X0, wp), run(X0, wm)
+            if rp_[2] != acc or rm_[2] != acc:
+                continue
+            fd = (_loss_and_grad(rp_[0][-1], pairs, targets)[0] - _loss_and_grad(rm_[0][-1], pairs, targets)[0]) / (2 * h)
+            assert gw[e] == pytest.approx(fd, rel=1e-4, abs=1e-6 * max(1.0, abs(L0))), key
