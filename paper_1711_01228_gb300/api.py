@@ -374,6 +374,30 @@ class Layout:
         return res
 
 
+def trace_records(result: RunResult) -> list:
+    """Per-iteration records of a run made with ``trace=True``: iteration k
+    (1-based), stress after it, whether line 6 kept the extrapolation, the
+    omega used, CG steps of its H step and the termination criterion."""
+    if result.trace_f is None:
+        raise ValueError("the run was made without trace=True")
+    out = []
+    for k in range(result.iterations):
+        out.append({"k": k + 1, "stress": float(result.trace_f[k + 1]), "accepted": bool(result.accepted[k]),
+                    "omega": float(result.omega[k]), "cg_steps": int(result.cg_steps[k]),
+                    "crit": float(result.crit[k])})
+    return out
+
+
+def write_trace_jsonl(result: RunResult, path: str, **extra) -> None:
+    """One JSON line per iteration (``trace_records``), each with ``extra`` fields added."""
+    import json
+
+    with open(path, "w") as f:
+        for rec in trace_records(result):
+            rec.update(extra)
+            f.write(json.dumps(rec) + "\n")
+
+
 def energy_noalloc(X, D, stream=None) -> float:
     """Stress f(X) from a dense device distance matrix without any device
     allocation by the library (for callers whose GPU memory is owned by

@@ -41,3 +41,17 @@ def test_batch_graph_mix():
             assert v not in nb and len(set(nb.tolist())) == len(nb)
     X = synth.batch_initial_layout([len(rp) - 1 for rp, _ in gs], 2, seed=0)
     assert X.dtype == np.float32 and X.shape[1] == 2 and np.all((X >= 0) & (X < 1))
+
+
+def test_trace_jsonl(tmp_path):
+    import json
+
+    r = api.RunResult(iterations=2, stress=1.5, trace_f=np.array([3.0, 2.0, 1.5]),
+                      accepted=np.array([1, 0], dtype=np.int32), omega=np.array([0.5, 0.5]),
+                      cg_steps=np.array([4, 3], dtype=np.int32), crit=np.array([0.1, 0.01]))
+    p = tmp_path / "t.jsonl"
+    api.write_trace_jsonl(r, str(p), graph="g")
+    recs = [json.loads(line) for line in p.read_text().splitlines()]
+    assert recs == [{"k": 1, "stress": 2.0, "accepted": True, "omega": 0.5, "cg_steps": 4, "crit": 0.1, "graph": "g"},
+                    {"k": 2, "stress": 1.5, "accepted": False, "omega": 0.5, "cg_steps": 3, "crit": 0.01,
+                     "graph": "g"}]
