@@ -479,6 +479,56 @@ def _largest_component(rp, ci):
     return sub.indptr.astype(np.int32), sub.indices.astype(np.int32), keep
 
 
+TABLE1_AVG = {"iters": {"0": 100.0, "0.5": 67.5, "1.0": 50.4, "1.5": 44.9, "auto": 47.2, "enum": 41.8},
+              "time": {"0": 100.0, "0.5": 100.1, "1.0": 74.8, "1.5": 66.7, "auto": 70.2, "enum": 140.9}}
+
+
+def run_table1(args, local_rank):
+    """Iterations and device time of every omega strategy of Sec. 5.2 on
+    synthetic stand-ins at the sizes of Table 1 (band-46 ... net-2305), with
+    the table's relative-error tolerances (stress decrease), averaged over
+    seeded initial layouts; ratios against omega = 0 beside the table's
+    average row."""
+    from paper_1711_01228_gb300 import api
+
+    cases = [("rgg46", 46, 1e-6), ("rgg62", 62, 1e-6), ("rgg86", 86, 1e-6), ("rgg156", 156, 1e-5),
+             ("rgg303", 303, 1e-5), ("rgg516", 516, 1e-5), ("grid33x34", 1122, 1e-4), ("grid34x34", 1156, 1e-4),
+             ("ba2305", 2305, 1e-4)]
+    strategies = [("0", dict(omega=0.0)), ("0.5", dict(omega=0.5)), ("1.0", dict(omega=1.0)),
+                  ("1.5", dict(omega=1.5)), ("auto", dict(strategy=api.OMEGA_PROB)),
+                  ("enum", dict(strategy=api.OMEGA_ENUM))]
+    out = {}
+    for name, n, tol in cases:
+        if name.startswith("rgg"):
+            rp, ci, _ = synth.random_geometric(n, 2, 6.0, seed=1)
+        elif name.startswith("grid"):
+            a, b = (int(v) for v in name[4:].split("x"))
+            rp, ci = synth.grid(a, b)
+        else:
+            rp, ci = synth.barabasi_albert(n, 3, seed=1)
+        n = len(rp) - 1
+        res = {}
+        with api.Layout(rp, ci, dim=2, disconnected_policy=1) as L:
+            for key, kw in strategies:
+                its, ms = [], []
+                for seed in range(args.table1_seeds):
+                    X = synth.initial_layout(n, 2, seed)
+                    r = L.run(X, tol=tol, max_iter=5000, stop=api.STOP_REL_STRESS, seed=seed, **kw)
+                    its.append(r.iterations)
+                    ms.append(r.stats["kernel_ms"])
+                res[key] = {"iterations": float(np.mean(its)), "ms": float(np.mean(ms))}
+        out[name] = {"n": n, "tol": tol, "strategies": res}
+    ratio = {k: float(np.mean([100.0 * v["strategies"][k]["iterations"] / v["strategies"]["0"]["iterations"]
+                               for v in out.values()])) for k, _ in strategies}
+    tratio = {k: float(np.mean([100.0 * v["strategies"][k]["ms"] / v["strategies"]["0"]["ms"]
+                                for v in out.values()])) for k, _ in strategies}
+    return {"table1_synthetic": out, "avg_iterations_pct_of_omega0": ratio, "avg_time_pct_of_omega0": tratio,
+            "paper_table1_average_row": TABLE1_AVG,
+            "note": "omega is the paper's (0 = Algorithm 1); auto = probabilistic strategy, enum = enumerating; "
+                    "stop when the relative stress decrease falls below the tolerance; "
+                    f"{args.table1_seeds} seeded X0 per case; synthetic graphs stand in for the paper's data sets"}
+
+
 def cpu_sample(budget_s: float):
     """The oracle, as it is, on a bounded sample of the workload: one pass each
     of stress, L^X X and L^W p over all pairs of the Erdos-Renyi graph
@@ -540,9 +590,21 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=2)
     ap.add_argument("--batch-sample", type=int, default=64, help="graphs timed through the single-graph path")
     ap.add_argument("--no-grad", dest="grad", action="store_false", help="skip the differentiable-form section")
+    ap.add_argument("--table1", action="store_true", help="omega strategies on stand-ins at Table 1's sizes, then exit")
+    ap.add_argument("--table1-seeds", type=int, default=5)
     ap.add_argument("--grad-n", type=int, default=4096, help="vertices of the differentiable workload (<= 4096)")
     args = ap.parse_args()
     rank, world, local_rank = _env_rank()
+    if args.table1:
+        import torch
+
+        from paper_1711_01228_gb300 import build
+
+        build.build()
+        torch.cuda.set_device(local_rank)
+        if rank == 0:
+            print(json.dumps(run_table1(args, local_rank)), flush=True)
+        return
     if world > 1:
         import torch.distributed as dist
 
