@@ -479,6 +479,57 @@ def _largest_component(rp, ci):
     return sub.indptr.astype(np.int32), sub.indices.astype(np.int32), keep
 
 
+def run_scale(args, local_rank):
+    """The method at scale: Barabasi-Albert n = 200,000 (m = 3), 2-D and 3-D,
+    200 iterations of Algorithm 2 at omega = 0.5 (classical 1.5).  Reports
+    throughput, the L^W passes' streaming rate against HBM (the 20 GB of
+    distance codes do not fit in L2), and the error against the FP64 oracle
+    on sampled vertices (distance rows, force rows at X^0)."""
+    import torch
+
+    import oracle
+    from paper_1711_01228_gb300 import api
+
+    rp, ci = synth.workload("ba200k")
+    n = len(rp) - 1
+    peaks, _ = _peaks()
+    rng = np.random.default_rng(7)
+    rows = np.unique(np.concatenate([[0, n - 1], rng.choice(n, 14, replace=False)]))
+    out = {"workload": f"Barabasi-Albert n={n}, m=3 ({int(rp[-1]) // 2} edges), X0 U[0,1]^d seed 0, "
+                       "200 iterations at omega_c 1.5 (tolerance 0)", "dims": {}}
+    for dim in (2, 3):
+        X0 = synth.initial_layout(n, dim, 0)
+        with api.Layout(rp, ci, dim=dim) as L:
+            info = L.info()
+            F = L.forces(X0).astype(np.float64)[rows]
+            Xd = torch.from_numpy(X0).cuda()
+            r = L.run(Xd, omega=0.5, tol=0.0, max_iter=200)
+            st = r.stats
+        Fr = []
+        for i in rows:
+            d = oracle.bfs_row(rp, ci, int(i)).astype(np.float64)
+            Fr.append(oracle.force_row(X0, int(i), d))
+        Fr = np.stack(Fr)
+        pairs = st["pairs"]
+        code_bytes = info["distance_bytes"]
+        out["dims"][str(dim)] = {
+            "distance_bytes": code_bytes, "apsp_ms": info["apsp_ms"], "iterations": st["iterations"],
+            "cg_steps": st["cg_steps"], "kernel_ms": st["kernel_ms"],
+            "pair_interactions_per_s": st["pair_passes"] * pairs / (st["kernel_ms"] / 1e3),
+            "fp32_tflops": pairs * (st["matvec_passes"] * FLOP_MV[dim] + st["stress_passes"] * FLOP_K2[dim])
+            / (st["kernel_ms"] / 1e3) / 1e12,
+            "code_stream_gbs": (st["matvec_passes"] + st["stress_passes"] / 2.0) * code_bytes / (st["kernel_ms"] / 1e3) / 1e9,
+            "hbm_peak_gbs": peaks.get("hbm_gbs", 6800.0),
+            "final_stress": r.stress,
+            "force_rel_err_sampled": float(np.linalg.norm(F - Fr) / np.linalg.norm(Fr)),
+            "sampled_vertices": int(len(rows)),
+        }
+    out["note"] = ("code_stream_gbs counts one read of the distance codes per pass (two-candidate passes read "
+                   "them once for both candidates); force error is Frobenius over the sampled rows, FP32 vs "
+                   "the FP64 oracle")
+    return out
+
+
 TABLE1_AVG = {"iters": {"0": 100.0, "0.5": 67.5, "1.0": 50.4, "1.5": 44.9, "auto": 47.2, "enum": 41.8},
               "time": {"0": 100.0, "0.5": 100.1, "1.0": 74.8, "1.5": 66.7, "auto": 70.2, "enum": 140.9}}
 
@@ -591,10 +642,21 @@ def main():
     ap.add_argument("--batch-sample", type=int, default=64, help="graphs timed through the single-graph path")
     ap.add_argument("--no-grad", dest="grad", action="store_false", help="skip the differentiable-form section")
     ap.add_argument("--table1", action="store_true", help="omega strategies on stand-ins at Table 1's sizes, then exit")
+    ap.add_argument("--scale", action="store_true", help="Barabasi-Albert n=200,000, 2-D and 3-D, 200 iterations, then exit")
     ap.add_argument("--table1-seeds", type=int, default=5)
     ap.add_argument("--grad-n", type=int, default=4096, help="vertices of the differentiable workload (<= 4096)")
     args = ap.parse_args()
     rank, world, local_rank = _env_rank()
+    if args.scale:
+        import torch
+
+        from paper_1711_01228_gb300 import build
+
+        build.build()
+        torch.cuda.set_device(local_rank)
+        if rank == 0:
+            print(json.dumps(run_scale(args, local_rank)), flush=True)
+        return
     if args.table1:
         import torch
 
