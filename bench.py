@@ -130,6 +130,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(values, device, world):
+    """Each value's maximum over the ranks (the slowest replica sets the job's time)."""
+    if world <= 1:
+        return list(values)
+    import torch
+
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(v) for v in t]
+
+
+def job_rate(units_per_rank, world, ms):
+    """Whole-job throughput: every rank processes units_per_rank in at most ms."""
+    return units_per_rank * world / (ms / 1e3)
+
+
 def make_inputs(names, dim=2, seed=0):
     out = []
     for nm in names:
@@ -229,12 +245,9 @@ def run_ours(args, rank, world, local_rank):
         one_step(acc_e, host=True)
     torch.cuda.synchronize()
     e2e_ms = max((time.perf_counter() - t0) * 1e3, 1e-9)
-    if world > 1:
-        t = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms, e2e_ms = float(t[0]), float(t[1])
-    value = acc["pairs"] * world / (total_ms / 1e3)
-    e2e_value = acc_e["pairs"] * world / (e2e_ms / 1e3)
+    total_ms, e2e_ms = max_over_ranks([total_ms, e2e_ms], dev, world)
+    value = job_rate(acc["pairs"], world, total_ms)
+    e2e_value = job_rate(acc_e["pairs"], world, e2e_ms)
     peaks, src = _peaks()
     clk = peaks.get("sm_max_mhz", 2070.0)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
