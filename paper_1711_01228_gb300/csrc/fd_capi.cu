@@ -99,7 +99,8 @@ struct fd_layout {
   std::vector<TaskDesc> tasks;
   fd_status last_error = FD_OK;
   fd_stats stats;
-  long long timeout_ns = 30000000000LL;
+  long long timeout_ns = 30000000000LL;      // copy (mbarrier) waits
+  long long bar_timeout_ns = 30000000000LL;  // grid-barrier waits
   double apsp_ms = 0.0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   double* d_timeline = nullptr;  // tracing: [timeline_cap][2]
@@ -519,6 +520,7 @@ KParams base_params(fd_layout* h, int mode) {
   p.sc = reinterpret_cast<float2*>(h->d_sc);
   p.ctrl = h->d_ctrl;
   p.timeout_ns = h->timeout_ns;
+  p.bar_timeout_ns = h->bar_timeout_ns;
   p.max_iter = 0;
   p.timeline = h->timeline_cap > 0 ? h->d_timeline : nullptr;
   p.timeline_cap = h->timeline_cap;
@@ -726,6 +728,10 @@ fd_status fd_layout_create(fd_layout** out, int32_t n, int32_t dim, const int32_
   }
   h->nbuf = best_nbuf;
   h->grid = bps * h->sm_count;
+  if (const char* t = std::getenv("FDLAYOUT_BARRIER_TIMEOUT_NS")) {  // testing: make grid-barrier waits run out
+    const long long v = std::atoll(t);
+    if (v > 0) h->bar_timeout_ns = v;
+  }
   if (const char* cap = std::getenv("FDLAYOUT_MAX_CTAS")) {  // testing: force many tasks per CTA
     const int c = std::atoi(cap);
     if (c > 0 && c < h->grid) h->grid = c;

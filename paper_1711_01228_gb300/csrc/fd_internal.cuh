@@ -118,7 +118,8 @@ struct KParams {
   int max_iter, stop, cg_max;
   int enum_omega;              // 1: omega is the argmin of f over {0, 0.5, ..., 9} each iteration (Sec. 5.2.2)
   double tol, cg_tol;
-  long long timeout_ns;        // limit of every grid-barrier / mbarrier wait
+  long long timeout_ns;        // limit of every mbarrier (copy) wait
+  long long bar_timeout_ns;    // limit of every grid-barrier wait
   double* timeline;            // NULL, or [timeline_cap][2] {tag, ns} written by CTA 0 at each barrier
   int timeline_cap;
 };

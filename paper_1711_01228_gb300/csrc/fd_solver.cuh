@@ -1075,7 +1075,7 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
   // grid barrier; the last CTA to arrive runs `red` first (a fixed-order reduction)
 #define FD_SYNC_RED(tag, red)                                                   \
   do {                                                                          \
-    if (!grid_sync_reduce(ctrl, p.timeout_ns, ++nbar, red)) return;             \
+    if (!grid_sync_reduce(ctrl, p.bar_timeout_ns, ++nbar, red)) return;         \
     mark(tag);                                                                  \
   } while (0)
 #define FD_SYNC(tag) FD_SYNC_RED(tag, no_reduction)

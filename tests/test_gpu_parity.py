@@ -216,3 +216,63 @@ def test_enumerating_strategy_matches_oracle():
     assert r.stress == pytest.approx(ref.stress, rel=1e-4)
     assert abs(r.iterations - ref.iterations) <= max(1, math.ceil(0.02 * ref.iterations))
     assert np.all(np.diff(r.trace_f) <= 1e-6 * r.trace_f[:-1])
+
+
+def test_barrier_timeout_reports_status_and_context_survives(monkeypatch):
+    # Failure detection without a GPU fault: the grid-barrier waits get a 1 ns
+    # limit, run out, and the kernel returns FD_ERR_TIMEOUT (the copy waits keep
+    # their own limit, so no CTA leaves with a copy in flight).  The next handle
+    # on the same device still computes correctly.
+    rp, ci = synth.grid(30, 30)
+    n = len(rp) - 1
+    X = synth.initial_layout(n, 2, seed=2)
+    monkeypatch.setenv("FDLAYOUT_BARRIER_TIMEOUT_NS", "1")
+    with api.Layout(rp, ci, dim=2) as L:
+        with pytest.raises(api.FdError) as e:
+            L.energy(X)
+        assert e.value.status == 7
+        with pytest.raises(api.FdError) as e:
+            L.run(X.copy(), omega=0.5, tol=1e-4, max_iter=5)
+        assert e.value.status == 7
+        assert api.lib().fd_last_error(L._h) == 7
+    monkeypatch.delenv("FDLAYOUT_BARRIER_TIMEOUT_NS")
+    D = _dense(rp, ci)
+    with api.Layout(rp, ci, dim=2) as L:
+        assert L.energy(X) == pytest.approx(oracle.stress(X, D), rel=1e-5)
+        Xr = X.copy()
+        r = L.run(Xr, omega=0.5, tol=1e-4, max_iter=20)
+        assert r.iterations > 0
+
+
+@pytest.mark.parametrize("seed", [0, 3])
+def test_fig4_graph_runs_match_oracle(seed):
+    # the paper's Fig. 4 (left) graph, Algorithm 2 at omega = 0.5 to relative stress decrease 1e-6
+    import test_oracle_fig4
+
+    rp, ci, _ = test_oracle_fig4.load_fig4()
+    D = _dense(rp, ci)
+    X0 = synth.initial_layout(179, 2, seed)
+    ref = oracle.sor_run(D, X0.astype(np.float64), omega=0.5, tol=1e-6, stop=oracle.STOP_REL_STRESS, max_iter=5000)
+    X = X0.copy()
+    with api.Layout(rp, ci, dim=2) as L:
+        r = L.run(X, omega=0.5, tol=1e-6, stop=api.STOP_REL_STRESS, max_iter=5000)
+    assert r.stress == pytest.approx(ref.stress, rel=1e-4)
+    assert abs(r.iterations - ref.iterations) <= max(1, math.ceil(0.02 * ref.iterations))
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_invariance_under_rigid_motion(dim):
+    # f depends only on distances (Eq. (1)): translation and rotation leave it unchanged and rotate F
+    rp, ci = GRAPHS["delaunay1000"]()
+    n = len(rp) - 1
+    rng = np.random.default_rng(3)
+    X = synth.initial_layout(n, dim, seed=4).astype(np.float64) * 3.0
+    Q, _ = np.linalg.qr(rng.normal(size=(dim, dim)))
+    t = rng.normal(size=dim) * 5.0
+    Y = X @ Q.T + t
+    with api.Layout(rp, ci, dim=dim, disconnected_policy=1) as L:
+        fX, fY = L.energy(X.astype(np.float32)), L.energy(Y.astype(np.float32))
+        FX = L.forces(X.astype(np.float32)).astype(np.float64)
+        FY = L.forces(Y.astype(np.float32)).astype(np.float64)
+    assert fY == pytest.approx(fX, rel=1e-5)
+    assert np.linalg.norm(FY - FX @ Q.T) <= 1e-4 * np.linalg.norm(FX)
