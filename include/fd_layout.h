@@ -257,6 +257,18 @@ fd_status fd_adjoint_length_grad(fd_layout* h, float* grad_len);
 fd_status fd_sor_step(fd_layout* h, float* X, const fd_options* opt, int32_t k, double* f_out,
                       int32_t* accepted, double* crit_out);
 
+/* Per-vertex relaxation factors (Sec. 6, first item of further work: a
+ * separate stride factor for every vertex, x~_i = x_i^{k+1} + omega_i
+ * (x_i^{k+1} - x_i^k)).  Every later fd_run / fd_sor_step of the handle uses
+ * omega_i = omega m_i, omega being the factor the strategy gives for the
+ * iteration; FD_OMEGA_FIXED with omega = 1 makes m the paper's omega vector.
+ * The acceptance test (line 6 of Algorithm 2) is unchanged.  With
+ * FD_OMEGA_ENUM the candidates are x + omega_e m (x - x_prev).
+ *   m   float32 [n] (host or device), every m_i finite and >= 0; copied.
+ *       NULL restores omega_i = omega.
+ * Errors: FD_ERR_ARG (negative or non-finite factor), FD_ERR_OOM, FD_ERR_CUDA. */
+fd_status fd_set_vertex_omega(fd_layout* h, const float* m);
+
 /* Algorithm 2 from X^0 (omega = 0 with FD_OMEGA_FIXED is Algorithm 1) until
  * the termination rule holds or opt->max_iter iterations ran.  The whole
  * loop runs on the GPU in one cooperative launch; nothing returns to the

@@ -31,6 +31,9 @@ sor_run                Algorithm 1 (omega = 0), Algorithm 2,  monotone stress (P
                                                               observed rate = 1 - lambda_min (Thm 3.2)
 omega_draw             probabilistic strategy, Sec. 5.2.3     splitmix64 published test vector; prior
                                                               frequencies
+extrapolate            line 5 of Algorithm 2, Eq. (10); the   m = 1 and m = c reduce to Eq. (10) with omega
+                       per-vertex omega_i of Sec. 6           and omega c; m = 0 gives Algorithm 1; candidate
+                                                              derived by hand on K2; relabelling equivariance
 =====================  ====================================  ===============================================
 
 The termination rule is not defined by the paper ("until some termination
@@ -351,8 +354,21 @@ class RunResult:
     converged: bool = False
 
 
-def sor_step(X, D, omega_k: float, strategy: int = OMEGA_FIXED, solver=None):
-    """One pass of Algorithm 2's loop body: lines 4-8.
+def extrapolate(Z, X, omega: float, m=None) -> np.ndarray:
+    """Line 5 of Algorithm 2.  Without m: Eq. (10), (1 + omega) Z - omega X.
+    With per-vertex factors m (Sec. 6, first item of further work): vertex i
+    moves by its own stride, x~_i = z_i + omega_i (z_i - x_i), with
+    omega_i = omega * m_i."""
+    Z, X = _f64(Z), _f64(X)
+    if m is None:
+        return (1.0 + omega) * Z - omega * X
+    om_i = omega * np.asarray(m, dtype=np.float64).reshape(-1, 1)
+    return Z + om_i * (Z - X)
+
+
+def sor_step(X, D, omega_k: float, strategy: int = OMEGA_FIXED, solver=None, omega_vertex=None):
+    """One pass of Algorithm 2's loop body: lines 4-8.  omega_vertex: None,
+    or the per-vertex factors m of `extrapolate`.
 
     Returns (X_next, f(X_next), accepted, omega_used, f(H(X))).
     """
@@ -363,12 +379,12 @@ def sor_step(X, D, omega_k: float, strategy: int = OMEGA_FIXED, solver=None):
     if strategy == OMEGA_ENUM:                        # Sec. 5.2.2
         best_f, best_om, best_X = None, None, None
         for om in ENUM_OMEGAS:
-            Xt = (1.0 + om) * Z - om * X
+            Xt = extrapolate(Z, X, om, omega_vertex)
             ft = stress(Xt, D)
             if best_f is None or ft < best_f:
                 best_f, best_om, best_X = ft, om, Xt
         return best_X, best_f, best_om > 0.0, best_om, fZ
-    Xt = (1.0 + omega_k) * Z - omega_k * X            # line 5, Eq. (10)
+    Xt = extrapolate(Z, X, omega_k, omega_vertex)     # line 5, Eq. (10)
     ft = stress(Xt, D)
     if ft <= fZ:                                      # line 6
         return Xt, ft, True, omega_k, fZ              # line 7
@@ -377,9 +393,10 @@ def sor_step(X, D, omega_k: float, strategy: int = OMEGA_FIXED, solver=None):
 
 def sor_run(D, X0, omega: float = 0.0, strategy: int = OMEGA_FIXED, seed: int = 0,
             stop: int = STOP_REL_DISP, tol: float = 1e-4, max_iter: int = 1000,
-            solver: PinnedSolver | None = None) -> RunResult:
+            solver: PinnedSolver | None = None, omega_vertex=None) -> RunResult:
     """Algorithm 2 from X^0 until the criterion drops below tol or max_iter
-    iterations ran.  omega = 0 with the fixed strategy is Algorithm 1."""
+    iterations ran.  omega = 0 with the fixed strategy is Algorithm 1.
+    omega_vertex: per-vertex factors m (omega_i = omega m_i, Sec. 6)."""
     D = _f64(D)
     X = _f64(X0).copy()
     solver = solver or PinnedSolver(D)
@@ -387,7 +404,7 @@ def sor_run(D, X0, omega: float = 0.0, strategy: int = OMEGA_FIXED, seed: int = 
     res = RunResult(X=X, iterations=0, stress=f, trace_f=[f])
     for k in range(max_iter):
         om = omega_draw(seed, k) if strategy == OMEGA_PROB else omega
-        Xn, fn, acc, om_used, fZ = sor_step(X, D, om, strategy, solver)
+        Xn, fn, acc, om_used, fZ = sor_step(X, D, om, strategy, solver, omega_vertex)
         crit = criterion(stop, X, Xn, f, fn)
         res.trace_f.append(fn)
         res.trace_accept.append(bool(acc))

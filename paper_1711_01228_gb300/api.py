@@ -69,7 +69,7 @@ EXPORTED = ["fd_options_default", "fd_layout_create", "fd_layout_destroy", "fd_e
             "fd_timeline_read", "fd_batch_create", "fd_batch_destroy", "fd_batch_run", "fd_batch_results",
             "fd_batch_tune", "fd_batch_set_shape", "fd_batch_distances", "fd_batch_get_info",
             "fd_batch_last_stats", "fd_energy_length_grad", "fd_sor_step_adjoint", "fd_adjoint_reset",
-            "fd_adjoint_length_grad"]
+            "fd_adjoint_length_grad", "fd_set_vertex_omega"]
 GRAD_MAX_N = 4096
 BATCH_MAX_N = 2048
 TIMELINE_TAGS = {1: "pack", 2: "stress", 3: "forces", 4: "rhs0", 5: "h_init", 6: "cg_au0", 7: "cg_step",
@@ -109,6 +109,8 @@ def lib():
     L.fd_sor_step.restype = i32
     L.fd_run.argtypes = [P, P, ctypes.POINTER(Options), ctypes.POINTER(i32), ctypes.POINTER(f64), P]
     L.fd_run.restype = i32
+    L.fd_set_vertex_omega.argtypes = [P, P]
+    L.fd_set_vertex_omega.restype = i32
     L.fd_run_trace.argtypes = [P, P, P, P, P]
     L.fd_run_trace.restype = i32
     L.fd_distance_rows.argtypes = [P, i32, i32, P]
@@ -342,6 +344,22 @@ class Layout:
             out = np.empty(self._nnz, dtype=np.float32)
         _check(lib().fd_adjoint_length_grad(self._h, _ptr(out, np.float32)), "fd_adjoint_length_grad")
         return out
+
+    def set_vertex_omega(self, m=None):
+        """Per-vertex relaxation factors (Sec. 6): later runs use omega_i =
+        omega * m[i] (m: n non-negative floats, host or device); None
+        restores a single omega."""
+        if m is None:
+            _check(lib().fd_set_vertex_omega(self._h, None), "fd_set_vertex_omega")
+            return
+        if _is_torch(m):
+            if m.numel() != self.n:
+                raise ValueError("m must have n entries")
+        else:
+            m = np.ascontiguousarray(m, dtype=np.float32)
+            if m.shape != (self.n,):
+                raise ValueError("m must have n entries")
+        _check(lib().fd_set_vertex_omega(self._h, _ptr(m, np.float32)), "fd_set_vertex_omega")
 
     def sor_step(self, X, k: int = 0, **opts):
         """One iteration of Algorithm 2 in place on X; returns (f, accepted, crit)."""

@@ -117,6 +117,8 @@ struct fd_layout {
   // unrolled differentiation: pair sensitivities summed over the adjoint steps (tile layout)
   float* d_dbar = nullptr;
   float* d_adj = nullptr;  // [4][n][dim]: Y, Yb, lam, Xb staging
+  // per-vertex relaxation factors m_i (omega_i = omega m_i, Sec. 6); NULL: none
+  float* d_om_scale = nullptr;  // [n_pad], padding 0
 };
 
 namespace {
@@ -332,6 +334,7 @@ void release(fd_layout* h) {
   dev_free(h->d_wrev);
   dev_free(h->d_dbar);
   dev_free(h->d_adj);
+  dev_free(h->d_om_scale);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
   h->ev0 = h->ev1 = nullptr;
@@ -1026,6 +1029,7 @@ static fd_status run_impl(fd_layout* h, float* X, const fd_options* opt, int k0,
   p.trace_crit = h->d_trace_crit;
   p.max_iter = max_iter;
   p.enum_omega = (opt->strategy == FD_OMEGA_ENUM) ? 1 : 0;
+  p.om_scale = h->d_om_scale;
   p.stop = opt->stop;
   p.cg_max = opt->cg_max;
   p.tol = opt->tol;
@@ -1040,6 +1044,34 @@ static fd_status run_impl(fd_layout* h, float* X, const fd_options* opt, int k0,
     FD_CK(cudaMemcpyAsync(X, h->d_stage_out, (size_t)h->n * h->dim * sizeof(float), cudaMemcpyDeviceToHost,
                           h->stream));
     FD_CK(cudaStreamSynchronize(h->stream));
+  }
+  return FD_OK;
+}
+
+fd_status fd_set_vertex_omega(fd_layout* h, const float* m) {
+  if (!h) return FD_ERR_ARG;
+  if (!m) {
+    dev_free(h->d_om_scale);
+    return FD_OK;
+  }
+  std::vector<float> hm((size_t)h->n_pad, 0.f);
+  if (is_device_ptr(m)) {
+    if (cudaMemcpy(hm.data(), m, (size_t)h->n * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, FD_ERR_CUDA);
+    }
+  } else {
+    std::memcpy(hm.data(), m, (size_t)h->n * sizeof(float));
+  }
+  for (int i = 0; i < h->n; ++i)
+    if (!std::isfinite(hm[i]) || hm[i] < 0.f) return fail(h, FD_ERR_ARG);
+  if (!h->d_om_scale) {
+    fd_status s = dev_alloc(&h->d_om_scale, (size_t)h->n_pad);
+    if (s != FD_OK) return fail(h, s);
+  }
+  if (cudaMemcpy(h->d_om_scale, hm.data(), (size_t)h->n_pad * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, FD_ERR_CUDA);
   }
   return FD_OK;
 }

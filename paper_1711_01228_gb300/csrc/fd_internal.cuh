@@ -117,6 +117,7 @@ struct KParams {
   double* trace_crit;          // [max_iter]
   int max_iter, stop, cg_max;
   int enum_omega;              // 1: omega is the argmin of f over {0, 0.5, ..., 9} each iteration (Sec. 5.2.2)
+  const float* om_scale;       // NULL, or [n_pad] per-vertex factors m_i: omega_i = omega m_i (Sec. 6), padding 0
   double tol, cg_tol;
   long long timeout_ns;        // limit of every mbarrier (copy) wait
   long long bar_timeout_ns;    // limit of every grid-barrier wait

@@ -196,6 +196,7 @@ struct PassSrc {
   float z0[3];              // SK_K2 / SK_SEL: vertex 0 of the CG solution (the pin of Sec. 2)
   float om;                 // SK_K2 / SK_SEL: omega of Eq. (10)
   int sel;                  // SK_SEL: 1 = the extrapolation was accepted
+  const float* oms;         // SK_K2 / SK_SEL / SK_ZX: per-vertex factors m_i, omega_i = om * m_i (Sec. 6); NULL: all 1
 };
 
 // The CG vector u_{i+1} (used both on the fly and in the vertex phase, so
@@ -633,10 +634,10 @@ __device__ __forceinline__ void tile_compute(const unsigned char* __restrict__ d
   }
 }
 
-// Forms element t of a block of the pass's vectors, in place in the raw
+// Forms element t of block blk of the pass's vectors, in place in the raw
 // arrays (candidate c goes to array c's slot).
 template <int DIM, int NC>
-__device__ __forceinline__ void form_inplace(const PassSrc& s, float* raw, int t) {
+__device__ __forceinline__ void form_inplace(const PassSrc& s, float* raw, int blk, int t) {
   constexpr int DP = DimP<DIM>::v;
   constexpr int A = TILE * DP;  // floats per raw array
   const int kind = s.kind;
@@ -654,17 +655,29 @@ __device__ __forceinline__ void form_inplace(const PassSrc& s, float* raw, int t
     Vec<DIM> z;
 #pragma unroll
     for (int d = 0; d < DIM; ++d) z.c[d] = zw.c[d] - s.z0[d];
+    // omega_i of vertex blk * TILE + t (the padding's factors are 0)
+    const float mi = s.oms ? __ldg(s.oms + (size_t)blk * TILE + t) : 1.f;
+    const float om = s.oms ? s.om * mi : s.om;
     if (kind == SK_K2 && NC == 2) {
       const Vec<DIM> x = lds_v<DIM>(raw + A, t);
       Vec<DIM> xt;
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) xt.c[d] = sor_xt(z.c[d], x.c[d], s.om);
+      for (int d = 0; d < DIM; ++d) xt.c[d] = sor_xt(z.c[d], x.c[d], om);
       sts_v<DIM>(raw + A, t, xt);
+    }
+    if (kind == SK_ZX && s.oms) {
+      // the enumeration pass forms z + omega_e (z - x) pairwise; with
+      // per-vertex factors its second vector is z - m_i (z - x)
+      const Vec<DIM> x = lds_v<DIM>(raw + A, t);
+      Vec<DIM> xm;
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) xm.c[d] = fmaf(-mi, z.c[d] - x.c[d], z.c[d]);
+      sts_v<DIM>(raw + A, t, xm);
     }
     if (kind == SK_SEL && s.sel) {
       const Vec<DIM> x = lds_v<DIM>(raw + A, t);
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) z.c[d] = sor_xt(z.c[d], x.c[d], s.om);
+      for (int d = 0; d < DIM; ++d) z.c[d] = sor_xt(z.c[d], x.c[d], om);
     }
     sts_v<DIM>(raw, t, z);
   }
@@ -826,8 +839,8 @@ __device__ FD_PASS_ATTR bool pair_pass_impl(PairState* ps_io, float* acc) {
     ps.parity ^= (1u << s_it);
     float* rawj = reinterpret_cast<float*>(smem + L::off_rawj(sb, s_it));
     float* rawi = reinterpret_cast<float*>(smem + L::off_rawi(sb, s_it));
-    form_inplace<DIM, NC>(src, rawj, tid);
-    if (first) form_inplace<DIM, NC>(src, rawi, tid);
+    form_inplace<DIM, NC>(src, rawj, J, tid);
+    if (first) form_inplace<DIM, NC>(src, rawi, I, tid);
     __syncthreads();  // formed vectors visible; every thread is done with the stage of the previous tile
     if (tid == 0 && ctl->is.valid) {
       TileIt is = ctl->is;
@@ -1002,6 +1015,7 @@ __device__ __forceinline__ PassSrc direct_src(const float* a, int kind = SK_DIRE
   for (int d = 0; d < 3; ++d) s.alpha[d] = s.beta[d] = s.z0[d] = 0.f;
   s.om = 0.f;
   s.sel = 0;
+  s.oms = nullptr;
   return s;
 }
 
@@ -1187,6 +1201,7 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
         for (int d = 0; d < DIM; ++d) src.z0[d] = rs->z0[d];
         src.om = rs->om_prev;
         src.sel = rs->accept;
+        src.oms = p.om_scale;
       }
       if (!pair_pass<DIM, PM_MATVEC, 1, CODE>(p, smem, ps, src, acc2)) return;
       if (tid == 0) rs->passes_mv += 1.0;
@@ -1196,6 +1211,7 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
       //          [5D,6D) sum x  [6D,7D) sum x^2
       const bool first = (k == 0), acc_t = rs->accept != 0, bsel = rs->bsel != 0;
       const float om_p = rs->om_prev;
+      const float* oms = p.om_scale;
       float z0[DIM];
 #pragma unroll
       for (int d = 0; d < DIM; ++d) z0[d] = rs->z0[d];
@@ -1207,10 +1223,11 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
           x0 = xo;
         } else {
           const Vec<DIM> zw = ldv<DIM>(p.Zw, i);
+          const float om_i = oms ? om_p * __ldg(oms + i) : om_p;  // Sec. 6: omega_i = omega m_i
 #pragma unroll
           for (int d = 0; d < DIM; ++d) {
             const float z = zw.c[d] - z0[d];
-            x0.c[d] = real ? (acc_t ? sor_xt(z, xo.c[d], om_p) : z) : 0.f;
+            x0.c[d] = real ? (acc_t ? sor_xt(z, xo.c[d], om_i) : z) : 0.f;
           }
         }
         const Vec<DIM> bz = take_acc<DIM>(acc0, i);
@@ -1455,6 +1472,7 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
       // gives its right-hand side and stress.
       PassSrc src = direct_src(p.Zw, SK_ZX);
       src.a[1] = p.X;
+      src.oms = p.om_scale;
       const Vec<DIM> zz = ldv<DIM>(p.Zw, 0);
 #pragma unroll
       for (int d = 0; d < DIM; ++d) src.z0[d] = zz.c[d];
@@ -1492,6 +1510,7 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
       for (int d = 0; d < DIM; ++d) sel.z0[d] = src.z0[d];
       sel.om = rs->om_prev;
       sel.sel = rs->accept;
+      sel.oms = p.om_scale;
       if (!pair_pass<DIM, PM_RHS, 1, CODE>(p, smem, ps, sel, acc0)) return;
       FD_SYNC_RED(8, red_stress(1));
       if (tid == 0) {
@@ -1521,6 +1540,7 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
     const bool two = (om != 0.0);
     PassSrc src = direct_src(p.Zw, SK_K2);
     src.a[1] = p.X;
+    src.oms = p.om_scale;
     {
       const Vec<DIM> zz = ldv<DIM>(p.Zw, 0);
 #pragma unroll
