@@ -69,6 +69,13 @@ typedef enum {
                          X^{k+1} is the argmin ("accepted" when it is not omega = 0) */
 } fd_omega_strategy;
 
+/* Solver of Eq. (2-5) (Sec. 2 names Cholesky factorisation, CG and
+ * Gauss-Seidel).  FD_SOLVER_DIRECT needs fd_factor on the handle first. */
+typedef enum {
+  FD_SOLVER_CG = 0,     /* Jacobi-preconditioned CG, warm-started from the previous layout */
+  FD_SOLVER_DIRECT = 1  /* refinement with the inverse made by fd_factor: x += A'^-1 r, r -= L^W (A'^-1 r) */
+} fd_solver;
+
 /* Termination rule.  The paper leaves it open ("until some termination
  * conditions were satisfied", Algorithms 1 and 2); these are the library's
  * two readings, each tested after every iteration. */
@@ -84,8 +91,9 @@ typedef struct {
   uint64_t seed;     /* FD_OMEGA_PROB: draw k uses SplitMix64(seed), k-th output */
   double tol;        /* termination threshold (see fd_stop_rule) */
   int32_t max_iter;  /* maximum outer iterations (each one H step) */
-  int32_t cg_max;    /* maximum conjugate-gradient steps per H step */
-  double cg_tol;     /* CG stops when ||r_c|| <= cg_tol * ||b_c|| for every column c */
+  int32_t cg_max;    /* maximum conjugate-gradient (or refinement) steps per H step */
+  double cg_tol;     /* the H solve stops when ||r_c|| <= cg_tol * ||b_c|| for every column c */
+  int32_t solver;    /* fd_solver: how Eq. (2-5) is solved in every H step */
 } fd_options;
 
 /* Statistics of the last fd_run / fd_sor_step / fd_energy / fd_forces call. */
@@ -120,10 +128,12 @@ typedef struct {
   double apsp_ms;          /* device time of the shortest-path kernel at creation (CUDA events) */
   int32_t stages;          /* tiles in flight per CTA in the layout kernel's copy pipeline (2 to 4) */
   int32_t bfs_sweeps;      /* unit edges: passes over the edge list summed over the 64-source searches */
+  int32_t factored;        /* 1 after fd_factor (FD_SOLVER_DIRECT available) */
+  double factor_ms;        /* device time of the last fd_factor (CUDA events) */
 } fd_info;
 
 /* Fills *opt with the defaults: omega 0.5, FIXED, REL_DISP, seed 0,
- * tol 1e-4, max_iter 1000, cg_max 200, cg_tol 1e-6. */
+ * tol 1e-4, max_iter 1000, cg_max 200, cg_tol 1e-6, FD_SOLVER_CG. */
 void fd_options_default(fd_options* opt);
 
 /* Builds a handle for graph G = (V, E) with n vertices laid out in dim
@@ -216,7 +226,7 @@ fd_status fd_energy_length_grad(fd_layout* h, const float* X, float* grad_len, d
  * omega X if line 6 kept the extrapolation (Eq. (10)), else X' = Y.  Given
  * Xbar_k1 = dL/dX' this writes Xbar_k = dL/dX with the acceptance held fixed:
  * the pinning's adjoint, one solve L^W lam = Ybar by the layout kernel's CG
- * (opt->cg_tol, opt->cg_max; NULL = defaults), and the transposed Jacobian
+ * (opt->cg_tol, opt->cg_max, opt->solver; NULL = defaults), and the transposed Jacobian
  * of L^X X applied to lam.  After fd_adjoint_reset, it also adds every pair's
  * sensitivity dL/dd_ij to an accumulator of the handle (weighted graphs that
  * fd_energy_length_grad accepts); fd_adjoint_length_grad turns the sum into
@@ -256,6 +266,34 @@ fd_status fd_adjoint_length_grad(fd_layout* h, float* grad_len);
  * FD_ERR_CUDA. */
 fd_status fd_sor_step(fd_layout* h, float* X, const fd_options* opt, int32_t k, double* f_out,
                       int32_t* accepted, double* crit_out);
+
+/* Direct solver of Eq. (2-5).  L^W does not change during a run, so its
+ * factorisation is made once (Sec. 2 names Cholesky factorisation for this
+ * system).  fd_factor builds, in device memory, the dense FP32 inverse of
+ *     A' = L^W + (sigma / n) 1 1^T,   sigma = (1/n) sum_i s_i,
+ * (Gauss-Jordan elimination in 128 x 128 blocks, no pivoting: A' is positive
+ * definite).  A' has the eigenvalues of L^W except that the null vector 1
+ * gets sigma, so its condition number is that of L^W, not the n-fold one of
+ * the pinned matrix; for a right-hand side of zero sum A'^-1 b solves
+ * L^W z = b, and pinning vertex 0 is a translation.  With
+ * opt->solver = FD_SOLVER_DIRECT every H step then refines from the warm
+ * start: x += A'^-1 r, r -= L^W (A'^-1 r), until opt->cg_tol or opt->cg_max.
+ * Memory: 4 n_pad^2 bytes (n_pad = n rounded up to 128), kept by the handle
+ * until fd_factor_release or destroy.  Cost: about 2 n_pad^3 FP32 flops.
+ *   n   at most FD_DIRECT_MAX_N
+ * Errors: FD_ERR_ARG (n too large), FD_ERR_OOM, FD_ERR_CG_BREAKDOWN (a pivot
+ * was not positive: the matrix is not numerically positive definite in FP32),
+ * FD_ERR_CUDA. */
+#define FD_DIRECT_MAX_N 32768
+fd_status fd_factor(fd_layout* h);
+
+/* Rows row0 .. row0 + nrows - 1 of A'^-1 (columns 0 .. n - 1), as float64 to
+ * the host array out[nrows][n].  Errors: FD_ERR_ARG (not factored, range),
+ * FD_ERR_CUDA. */
+fd_status fd_factor_rows(fd_layout* h, int32_t row0, int32_t nrows, double* out);
+
+/* Frees the inverse made by fd_factor.  Errors: FD_ERR_ARG. */
+fd_status fd_factor_release(fd_layout* h);
 
 /* Per-vertex relaxation factors (Sec. 6, first item of further work: a
  * separate stride factor for every vertex, x~_i = x_i^{k+1} + omega_i
@@ -303,8 +341,9 @@ fd_status fd_last_stats(const fd_layout* h, fd_stats* stats);
  * layout-kernel launch record, at each of its grid-wide barriers, the
  * device time (ns since the launch started, from %globaltimer) and a phase
  * tag: 1 pack, 2 stress pass, 3 force pass, 4 initial RHS pass, 5 H-step
- * start (L^W x0), 6 L^W u0, 7 CG step, 8 stress/RHS of the candidates,
- * 9 per-row-block reduction and vector update after a pass.
+ * start (L^W x0), 6 L^W u0, 7 CG step (or L^W of a refinement step),
+ * 8 stress/RHS of the candidates, 9 per-row-block reduction and vector
+ * update after a pass, 10 application of the factored inverse.
  * cap = 0 disables it.  fd_timeline_read copies up to cap entries of the
  * last launch (tags and times as doubles, interleaved: tag, t, tag, t, ...)
  * and the number recorded.  Errors: FD_ERR_ARG, FD_ERR_OOM, FD_ERR_CUDA. */

@@ -31,6 +31,9 @@ sor_run                Algorithm 1 (omega = 0), Algorithm 2,  monotone stress (P
                                                               observed rate = 1 - lambda_min (Thm 3.2)
 omega_draw             probabilistic strategy, Sec. 5.2.3     splitmix64 published test vector; prior
                                                               frequencies
+shifted_inverse        solver of Eq. (2-5) with L^W fixed        closed forms on K2 and K5; A'^-1 1 = 1/sigma;
+                       (Sec. 2): inverse of L^W + sigma/n 11^T  A'^-1 b minus the pinned Cholesky solve is a
+                                                              translation (zero-sum b)
 extrapolate            line 5 of Algorithm 2, Eq. (10); the   m = 1 and m = c reduce to Eq. (10) with omega
                        per-vertex omega_i of Sec. 6           and omega c; m = 0 gives Algorithm 1; candidate
                                                               derived by hand on K2; relabelling equivariance
@@ -275,6 +278,24 @@ class PinnedSolver:
         y = sla.solve_triangular(self.L, b[1:], lower=True)
         Z[1:] = sla.solve_triangular(self.L.T, y, lower=False)
         return Z
+
+
+def shifted_inverse(D) -> np.ndarray:
+    """Dense inverse of A' = L^W + (sigma / n) 1 1^T, sigma = mean_i s_i.
+
+    L^W is singular with null vector 1 (Prop. 2.1); the shift gives 1 the
+    eigenvalue sigma and leaves the rest of the spectrum, so A' is positive
+    definite.  For a right-hand side b with zero sum, A'^-1 b solves
+    L^W z = b (the solution of zero sum), which differs from the pinned
+    solution of Eq. (2-5) by a translation.  The direct solver of the
+    library applies this matrix in every H step.
+    """
+    L = lw_dense(D)
+    n = L.shape[0]
+    sigma = float(np.trace(L)) / n if n else 1.0
+    if not sigma > 0.0:
+        sigma = 1.0  # n = 1
+    return np.linalg.inv(L + sigma / n)
 
 
 def H(X, D, solver: PinnedSolver | None = None) -> np.ndarray:

@@ -25,6 +25,8 @@ STATUS_NAMES = {
 }
 OMEGA_FIXED, OMEGA_PROB, OMEGA_ENUM = 0, 1, 2
 STOP_REL_DISP, STOP_REL_STRESS = 0, 1
+SOLVER_CG, SOLVER_DIRECT = 0, 1
+DIRECT_MAX_N = 32768
 
 
 class FdError(RuntimeError):
@@ -36,7 +38,7 @@ class FdError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("omega", ctypes.c_double), ("strategy", ctypes.c_int32), ("stop", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
-                ("cg_max", ctypes.c_int32), ("cg_tol", ctypes.c_double)]
+                ("cg_max", ctypes.c_int32), ("cg_tol", ctypes.c_double), ("solver", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -52,7 +54,8 @@ class Info(ctypes.Structure):
                 ("code_bytes", ctypes.c_int32), ("tile", ctypes.c_int32), ("num_tiles", ctypes.c_int32),
                 ("distance_bytes", ctypes.c_int64), ("disconnected", ctypes.c_int32),
                 ("sm_count", ctypes.c_int32), ("grid", ctypes.c_int32), ("tasks", ctypes.c_int32),
-                ("apsp_ms", ctypes.c_double), ("stages", ctypes.c_int32), ("bfs_sweeps", ctypes.c_int32)]
+                ("apsp_ms", ctypes.c_double), ("stages", ctypes.c_int32), ("bfs_sweeps", ctypes.c_int32),
+                ("factored", ctypes.c_int32), ("factor_ms", ctypes.c_double)]
 
 
 class BatchInfo(ctypes.Structure):
@@ -69,7 +72,7 @@ EXPORTED = ["fd_options_default", "fd_layout_create", "fd_layout_destroy", "fd_e
             "fd_timeline_read", "fd_batch_create", "fd_batch_destroy", "fd_batch_run", "fd_batch_results",
             "fd_batch_tune", "fd_batch_set_shape", "fd_batch_distances", "fd_batch_get_info",
             "fd_batch_last_stats", "fd_energy_length_grad", "fd_sor_step_adjoint", "fd_adjoint_reset",
-            "fd_adjoint_length_grad", "fd_set_vertex_omega"]
+            "fd_adjoint_length_grad", "fd_set_vertex_omega", "fd_factor", "fd_factor_rows", "fd_factor_release"]
 GRAD_MAX_N = 4096
 BATCH_MAX_N = 2048
 TIMELINE_TAGS = {1: "pack", 2: "stress", 3: "forces", 4: "rhs0", 5: "h_init", 6: "cg_au0", 7: "cg_step",
@@ -111,6 +114,12 @@ def lib():
     L.fd_run.restype = i32
     L.fd_set_vertex_omega.argtypes = [P, P]
     L.fd_set_vertex_omega.restype = i32
+    L.fd_factor.argtypes = [P]
+    L.fd_factor.restype = i32
+    L.fd_factor_rows.argtypes = [P, i32, i32, P]
+    L.fd_factor_rows.restype = i32
+    L.fd_factor_release.argtypes = [P]
+    L.fd_factor_release.restype = i32
     L.fd_run_trace.argtypes = [P, P, P, P, P]
     L.fd_run_trace.restype = i32
     L.fd_distance_rows.argtypes = [P, i32, i32, P]
@@ -344,6 +353,21 @@ class Layout:
             out = np.empty(self._nnz, dtype=np.float32)
         _check(lib().fd_adjoint_length_grad(self._h, _ptr(out, np.float32)), "fd_adjoint_length_grad")
         return out
+
+    def factor(self) -> float:
+        """Inverts the shifted L^W once on the device for solver=SOLVER_DIRECT;
+        returns the device time in ms."""
+        _check(lib().fd_factor(self._h), "fd_factor")
+        return self.info()["factor_ms"]
+
+    def factor_rows(self, row0: int, nrows: int) -> np.ndarray:
+        """Rows of the factored inverse (L^W + sigma/n 1 1^T)^-1, float64 [nrows, n]."""
+        out = np.empty((nrows, self.n), dtype=np.float64)
+        _check(lib().fd_factor_rows(self._h, int(row0), int(nrows), out.ctypes.data), "fd_factor_rows")
+        return out
+
+    def factor_release(self):
+        _check(lib().fd_factor_release(self._h), "fd_factor_release")
 
     def set_vertex_omega(self, m=None):
         """Per-vertex relaxation factors (Sec. 6): later runs use omega_i =

@@ -33,6 +33,9 @@ cudaError_t main_config_d3(int code, size_t lut_bytes, int nbuf, int* blocks_per
 cudaError_t launch_main_d1(int code, const KParams& p, int grid, size_t smem, cudaStream_t st);
 cudaError_t launch_main_d2(int code, const KParams& p, int grid, size_t smem, cudaStream_t st);
 cudaError_t launch_main_d3(int code, const KParams& p, int grid, size_t smem, cudaStream_t st);
+cudaError_t launch_direct_factor(int n, int n_pad, int nb, int code, const void* D, const int2* tile_ik, int ntiles,
+                                 const float* s, float shift, float* M, float* P, int* err, int sm_count,
+                                 cudaStream_t st);
 cudaError_t launch_bfs_multi(const BGraph* graphs, const int2* items, int nitems, const int* rp, const int* ci,
                              unsigned char* D, int n_max, int* maxlevel, int* overflow, int grid, cudaStream_t st);
 cudaError_t launch_fill_multi(const BGraph* graphs, const int* tile_graph, const int2* tile_ik, long long ntiles,
@@ -119,6 +122,9 @@ struct fd_layout {
   float* d_adj = nullptr;  // [4][n][dim]: Y, Yb, lam, Xb staging
   // per-vertex relaxation factors m_i (omega_i = omega m_i, Sec. 6); NULL: none
   float* d_om_scale = nullptr;  // [n_pad], padding 0
+  // direct solver: (L^W + sigma/n 1 1^T)^-1, [n_pad][n_pad] (fd_factor)
+  float* d_ainv = nullptr;
+  double factor_ms = 0.0;
 };
 
 namespace {
@@ -335,6 +341,7 @@ void release(fd_layout* h) {
   dev_free(h->d_dbar);
   dev_free(h->d_adj);
   dev_free(h->d_om_scale);
+  dev_free(h->d_ainv);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
   h->ev0 = h->ev1 = nullptr;
@@ -589,6 +596,7 @@ void fd_options_default(fd_options* opt) {
   opt->max_iter = 1000;
   opt->cg_max = 200;
   opt->cg_tol = 1e-6;
+  opt->solver = FD_SOLVER_CG;
 }
 
 const char* fd_status_string(fd_status s) {
@@ -880,6 +888,18 @@ fd_status fd_energy_length_grad(fd_layout* h, const float* X, float* grad_len, d
 }
 
 // Tile coordinates (block row, strip offset) of every stored tile, on the device.
+// The H-step solver of a launch: CG, or refinement with the factored inverse.
+static fd_status set_solver(fd_layout* h, int32_t solver, KParams* p) {
+  if (solver == FD_SOLVER_CG) {
+    p->solver = SOLVER_CG;
+    return FD_OK;
+  }
+  if (solver != FD_SOLVER_DIRECT || !h->d_ainv) return FD_ERR_ARG;
+  p->solver = SOLVER_DIRECT;
+  p->ainv = h->d_ainv;
+  return FD_OK;
+}
+
 static fd_status upload_tile_ik(fd_layout* h, int2** out) {
   std::vector<int2> tile_ik(h->ntiles);
   for (int I = 0; I < h->nb; ++I)
@@ -952,6 +972,7 @@ fd_status fd_sor_step_adjoint(fd_layout* h, const float* X_k, const float* X_k1,
   p.cg_max = o.cg_max;
   p.cg_tol = o.cg_tol;
   p.tol = 0.0;
+  if ((s = set_solver(h, o.solver, &p)) != FD_OK) return fail(h, s);
   Ctrl c;
   double kms = 0.0;
   std::memset(&c, 0, sizeof(c));
@@ -1000,6 +1021,82 @@ fd_status fd_adjoint_length_grad(fd_layout* h, float* grad_len) {
   return FD_OK;
 }
 
+fd_status fd_factor(fd_layout* h) {
+  if (!h) return FD_ERR_ARG;
+  if (h->n > FD_DIRECT_MAX_N) return fail(h, FD_ERR_ARG);
+  cudaStream_t st = h->stream;
+  const size_t np = (size_t)h->n_pad;
+  fd_status s = FD_OK;
+  if (!h->d_ainv && (s = dev_alloc(&h->d_ainv, np * np)) != FD_OK) return fail(h, s);
+  float* P = nullptr;
+  int* err = nullptr;
+  int2* tik = nullptr;
+  auto cleanup = [&] {
+    dev_free(P);
+    dev_free(err);
+    dev_free(tik);
+  };
+  if ((s = dev_alloc(&P, (size_t)TILE * TILE)) != FD_OK || (s = dev_alloc(&err, 1)) != FD_OK ||
+      (s = upload_tile_ik(h, &tik)) != FD_OK) {
+    cleanup();
+    dev_free(h->d_ainv);
+    return fail(h, s);
+  }
+  // shift sigma / n with sigma = mean_i s_i (the eigenvalue the null vector 1 of L^W gets)
+  std::vector<float> hs((size_t)h->n);
+  cudaError_t e = cudaMemcpy(hs.data(), h->d_s, (size_t)h->n * sizeof(float), cudaMemcpyDeviceToHost);
+  double sigma = 0.0;
+  for (float v : hs) sigma += v;
+  sigma /= h->n;
+  if (!(sigma > 0.0)) sigma = 1.0;  // n = 1: L^W = 0
+  int herr = 0;
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev0, st);
+  if (e == cudaSuccess)
+    e = launch_direct_factor(h->n, h->n_pad, h->nb, h->code, h->D, tik, h->ntiles, h->d_s, (float)(sigma / h->n),
+                             h->d_ainv, P, err, h->sm_count, st);
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev1, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+  cleanup();
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    dev_free(h->d_ainv);
+    return fail(h, cuda_status(e));
+  }
+  if (herr) {
+    dev_free(h->d_ainv);
+    return fail(h, FD_ERR_CG_BREAKDOWN);
+  }
+  h->factor_ms = ms;
+  return FD_OK;
+}
+
+fd_status fd_factor_rows(fd_layout* h, int32_t row0, int32_t nrows, double* out) {
+  if (!h) return FD_ERR_ARG;
+  if (!h->d_ainv || !out || row0 < 0 || nrows < 0 || row0 + nrows > h->n) return fail(h, FD_ERR_ARG);
+  if (nrows == 0) return FD_OK;
+  std::vector<float> buf((size_t)nrows * h->n);
+  if (cudaMemcpy2D(buf.data(), (size_t)h->n * sizeof(float), h->d_ainv + (size_t)row0 * h->n_pad,
+                   (size_t)h->n_pad * sizeof(float), (size_t)h->n * sizeof(float), (size_t)nrows,
+                   cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, FD_ERR_CUDA);
+  }
+  for (size_t k = 0; k < buf.size(); ++k) out[k] = buf[k];
+  return FD_OK;
+}
+
+fd_status fd_factor_release(fd_layout* h) {
+  if (!h) return FD_ERR_ARG;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  dev_free(h->d_ainv);
+  h->factor_ms = 0.0;
+  return FD_OK;
+}
+
 static fd_status run_impl(fd_layout* h, float* X, const fd_options* opt, int k0, int max_iter, Ctrl* c_out) {
   if (!X || !opt) return FD_ERR_ARG;
   if (!(opt->omega >= 0.0) || !std::isfinite(opt->omega) || max_iter < 1 || opt->cg_max < 0 ||
@@ -1030,6 +1127,7 @@ static fd_status run_impl(fd_layout* h, float* X, const fd_options* opt, int k0,
   p.max_iter = max_iter;
   p.enum_omega = (opt->strategy == FD_OMEGA_ENUM) ? 1 : 0;
   p.om_scale = h->d_om_scale;
+  if ((s = set_solver(h, opt->solver, &p)) != FD_OK) return s;
   p.stop = opt->stop;
   p.cg_max = opt->cg_max;
   p.tol = opt->tol;
@@ -1170,6 +1268,8 @@ fd_status fd_layout_info(const fd_layout* h, fd_info* info) {
   info->apsp_ms = h->apsp_ms;
   info->stages = h->nbuf;
   info->bfs_sweeps = h->bfs_sweeps;
+  info->factored = h->d_ainv ? 1 : 0;
+  info->factor_ms = h->factor_ms;
   return FD_OK;
 }
 

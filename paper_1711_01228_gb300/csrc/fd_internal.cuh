@@ -87,6 +87,8 @@ struct Geometry {
 };
 
 // Parameters of the cooperative kernel (passed by value).
+enum Solver { SOLVER_CG = 0, SOLVER_DIRECT = 1 };
+
 struct KParams {
   Geometry g;
   int mode;
@@ -118,6 +120,10 @@ struct KParams {
   int max_iter, stop, cg_max;
   int enum_omega;              // 1: omega is the argmin of f over {0, 0.5, ..., 9} each iteration (Sec. 5.2.2)
   const float* om_scale;       // NULL, or [n_pad] per-vertex factors m_i: omega_i = omega m_i (Sec. 6), padding 0
+  // direct solver: the H step refines with A'^-1 = (L^W + sigma/n 1 1^T)^-1
+  // ([n_pad][n_pad], row-major) in place of CG
+  const float* ainv;
+  int solver;                  // SOLVER_CG or SOLVER_DIRECT
   double tol, cg_tol;
   long long timeout_ns;        // limit of every mbarrier (copy) wait
   long long bar_timeout_ns;    // limit of every grid-barrier wait

@@ -998,6 +998,100 @@ __device__ __forceinline__ void vertex_phase(const KParams& p, float2* red64, F&
   }
 }
 
+// --------------------------------------------------------------------------
+// Direct solver: z = A'^-1 r with the dense inverse of the shifted L^W
+// (L^W + sigma/n 1 1^T, inverted once before the launch).  The inverse is
+// streamed once from HBM with 16-byte loads; a CTA takes 8 rows at a time
+// (2 per warp, each lane 4 consecutive columns), r goes through shared memory
+// in chunks of DCH vertices, one coordinate per array (so that a lane's 4
+// vertices are one 16-byte read), double-buffered through registers.  Every
+// row sum has one fixed order: the result does not depend on the grid.
+// --------------------------------------------------------------------------
+constexpr int DCH = 1024;  // vertices per staged chunk of r
+
+template <int DIM>
+__device__ __noinline__ void dense_apply(const KParams& p, float* buf, const float* __restrict__ r,
+                                            float* __restrict__ z) {
+  constexpr int DP = DimP<DIM>::v;
+  constexpr int PT = DCH * DP / 4 / CTA;  // float4 of a chunk per thread
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int np = p.g.n_pad;  // a multiple of TILE
+  const int nch = (np + DCH - 1) / DCH;
+  float4 pre[PT];
+  auto fetch = [&](int ch) {
+    const float4* src = reinterpret_cast<const float4*>(r + (size_t)ch * DCH * DP);
+    const int lim = min(DCH, np - ch * DCH) * DP / 4;
+#pragma unroll
+    for (int q = 0; q < PT; ++q) {
+      const int idx = threadIdx.x + q * CTA;
+      pre[q] = (idx < lim) ? __ldcg(src + idx) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  };
+  auto put = [&](float* b) {
+#pragma unroll
+    for (int q = 0; q < PT; ++q) {
+      const int idx = threadIdx.x + q * CTA;
+      const float4 v = pre[q];
+      if constexpr (DP == 1) {
+        reinterpret_cast<float4*>(b)[idx] = v;
+      } else if constexpr (DP == 2) {
+        reinterpret_cast<float2*>(b)[idx] = make_float2(v.x, v.z);
+        reinterpret_cast<float2*>(b + DCH)[idx] = make_float2(v.y, v.w);
+      } else {
+        b[idx] = v.x;
+        b[DCH + idx] = v.y;
+        b[2 * DCH + idx] = v.z;
+      }
+    }
+  };
+  for (int gi = blockIdx.x; gi < np / 8; gi += gridDim.x) {
+    const int i0 = gi * 8 + warp * 2;
+    const float* a0 = p.ainv + (size_t)i0 * np;
+    const float* a1 = a0 + np;
+    float s0[DIM], s1[DIM];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) s0[d] = s1[d] = 0.f;
+    fetch(0);
+    put(buf);
+    __syncthreads();
+    for (int ch = 0; ch < nch; ++ch) {
+      if (ch + 1 < nch) fetch(ch + 1);
+      const float* rb = buf + (ch & 1) * DIM * DCH;
+      const int c0 = ch * DCH, len = min(DCH, np - c0);
+#pragma unroll 4
+      for (int c = lane * 4; c < len; c += 128) {
+        const float4 u0 = __ldcs(reinterpret_cast<const float4*>(a0 + c0 + c));
+        const float4 u1 = __ldcs(reinterpret_cast<const float4*>(a1 + c0 + c));
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+          const float4 v = *reinterpret_cast<const float4*>(rb + d * DCH + c);
+          s0[d] = fmaf(u0.x, v.x, fmaf(u0.y, v.y, fmaf(u0.z, v.z, fmaf(u0.w, v.w, s0[d]))));
+          s1[d] = fmaf(u1.x, v.x, fmaf(u1.y, v.y, fmaf(u1.z, v.z, fmaf(u1.w, v.w, s1[d]))));
+        }
+      }
+      if (ch + 1 < nch) put(buf + ((ch + 1) & 1) * DIM * DCH);
+      __syncthreads();
+    }
+#pragma unroll
+    for (int d = 0; d < DIM; ++d)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        s0[d] += __shfl_xor_sync(0xffffffffu, s0[d], o);
+        s1[d] += __shfl_xor_sync(0xffffffffu, s1[d], o);
+      }
+    if (lane == 0) {
+      Vec<DIM> v0, v1;
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) {
+        v0.c[d] = s0[d];
+        v1.c[d] = s1[d];
+      }
+      stv<DIM>(z, i0, v0);
+      stv<DIM>(z, i0 + 1, v1);
+    }
+  }
+}
+
 // Reads and clears accumulator entry i.
 template <int DIM>
 __device__ __forceinline__ Vec<DIM> take_acc(float* a, int i) {
@@ -1307,8 +1401,56 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
       __syncthreads();
       if (rs->stop) break;
     }
+    if (p.solver == SOLVER_DIRECT) {
+      // ---- refinement with the factored inverse: delta = A'^-1 r, x += delta,
+      // r -= L^W delta (pair pass), until every column meets cg_tol or cg_max
+      // steps ran.  r sums to zero (b = L^X X does, L^W x does), so A'^-1 r
+      // is the minimum-norm solution of L^W delta = r.
+      float* dbuf = reinterpret_cast<float*>(smem + L::stage_base(CODE == CODE_U8 ? p.lut_rows * LUT_ROW : 0));
+      while (!rs->all_conv) {
+        dense_apply<DIM>(p, dbuf, p.R, p.U);
+        FD_SYNC(10);
+        if (!pair_pass<DIM, PM_MATVEC, 1, CODE>(p, smem, ps, direct_src(p.U), acc2)) return;
+        if (tid == 0) {
+          rs->passes_mv += 1.0;
+          ++rs->it;
+        }
+        FD_SYNC(7);
+        vertex_phase<DIM>(p, red64, [&](int i, df(&v)[DIM]) {
+          const float s = __ldcg(p.s + i);
+          const Vec<DIM> u = ldv<DIM>(p.U, i);
+          const Vec<DIM> a = take_acc<DIM>(acc2, i);
+          Vec<DIM> x = ldv<DIM>(p.Zw, i), r = ldv<DIM>(p.R, i);
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) {
+            x.c[d] += u.c[d];
+            r.c[d] -= fmaf(s, u.c[d], -a.c[d]);
+            v[d] = df_add(v[d], df_prod(r.c[d], r.c[d]));
+          }
+          stv<DIM>(p.Zw, i, x);
+          stv<DIM>(p.R, i, r);
+        });
+        auto red_dir = [&] { reduce_slots_to_ctrl<DIM>(ctrl, p.sc, gridDim.x, SC_STRIDE, red64); };
+        FD_SYNC_RED(9, red_dir);
+        if (tid == 0) {
+          df v[DIM];
+          load_red<DIM>(ctrl, v);
+          int all = 1;
+          for (int d = 0; d < DIM; ++d) {
+            if (!rs->conv[d]) rs->conv[d] = (df_f(v[d]) <= cgt2 * rs->bb[d]) ? 1 : 0;
+            all = all && rs->conv[d];
+          }
+          if (!all && rs->it >= p.cg_max) {
+            ++rs->cg_maxed;
+            all = 1;
+          }
+          rs->all_conv = all;
+        }
+        __syncthreads();
+      }
+    }
     // ---- CG on L^W Z = b, one reduction per step
-    if (!rs->all_conv) {
+    if (p.solver != SOLVER_DIRECT && !rs->all_conv) {
       if (!pair_pass<DIM, PM_MATVEC, 1, CODE>(p, smem, ps, direct_src(p.U), acc2)) return;
       if (tid == 0) rs->passes_mv += 1.0;
       FD_SYNC(6);
