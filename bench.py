@@ -252,9 +252,11 @@ def run_ours(args, rank, world, local_rank):
     clk = peaks.get("sm_max_mhz", 2070.0)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     fp32_peak = sms * 128 * 2 * clk * 1e6 / 1e12  # TFLOP/s at the maximum SM clock
+    fp32_measured = {"fma_f32": api.fp32_peak(False), "fma_f32x2": api.fp32_peak(True)}
     achieved = acc["flops"] / (acc["kernel_ms"] / 1e3) / 1e12
     batched = run_batched(args, local_rank, fp32_peak) if (args.batch and rank == 0) else None
     differentiable = run_differentiable(args, local_rank) if (args.grad and rank == 0) else None
+    direct = run_direct(args, local_rank, peaks, fp32_peak) if (args.direct_sec and rank == 0) else None
     line = {
         "metric": "pair-interactions/s",
         "value": value,
@@ -279,7 +281,10 @@ def run_ours(args, rank, world, local_rank):
                      "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                      "traffic": measured_traffic(",".join(args.workload.split(","))),
                      "traffic_unit": "DRAM bytes per launch (ncu, read + write)",
-                     "peak_note": f"FP32 CUDA cores {sms} SMs x 128 x 2 flop at {clk:.0f} MHz ({src} max clock)"},
+                     "peak_note": f"FP32 CUDA cores {sms} SMs x 128 x 2 flop at {clk:.0f} MHz ({src} max clock)",
+                     "peak_measured_tflops": fp32_measured,
+                     "peak_measured_note": "fd_fp32_peak: 16 independent FMA chains per thread, scalar and "
+                                           "two-wide packed, best of 5 launches"},
         "apsp": {"kernel": "bfs_batch_kernel", "ms_per_step": acc["apsp_ms"] / args.steps,
                  "algorithmic_bytes_per_step": acc["apsp_bytes"] / args.steps,
                  "achieved_gbs": acc["apsp_bytes"] / (acc["apsp_ms"] / 1e3) / 1e9,
@@ -298,6 +303,8 @@ def run_ours(args, rank, world, local_rank):
         line["batched"] = batched
     if differentiable is not None:
         line["differentiable"] = differentiable
+    if direct is not None:
+        line["direct_solver"] = direct
     return line
 
 
@@ -475,6 +482,96 @@ def run_differentiable(args, local_rank):
             "stress_pairs_per_s": pairs / (ms_energy / 1e3), "position_grad_pairs_per_s": pairs / (ms_forces / 1e3),
             "note": "autograd step = fd_layout_create (weighted shortest paths) + stress + forces + length "
                     "gradient, through torch.autograd; every value from the CUDA library"}
+
+
+def run_direct(args, local_rank, peaks, fp32_peak):
+    """The direct solver of Eq. (2-5) beside CG on one graph of the workload:
+    the factorisation (fd_factor: FP32 Gauss-Jordan inverse of the shifted
+    L^W), then Algorithm 2 with each solver, same options as the headline
+    runs.  The dense apply is a phase of the layout kernel; its duration comes
+    from the kernel's %globaltimer marks (fd_timeline), the rest from CUDA
+    events."""
+    import ctypes
+
+    import torch
+
+    from paper_1711_01228_gb300 import api
+
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    if args.direct_n:
+        rp, ci = synth.delaunay(args.direct_n, seed=0)
+        name = f"delaunay{args.direct_n}"
+    else:
+        name = "delaunay20k"
+        rp, ci = synth.workload(name)
+    n = len(rp) - 1
+    x0 = synth.initial_layout(n, 2, seed=0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    opts = dict(omega=0.5, tol=1e-4, max_iter=args.max_iter, stop=api.STOP_REL_DISP)
+    L = api.Layout(torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev), dim=2, disconnected_policy=1,
+                   stream=stream.cuda_stream)
+    X0 = torch.from_numpy(x0).to(dev)
+    n_pad = L.info()["tile"] * ((n + L.info()["tile"] - 1) // L.info()["tile"])
+
+    def runs(solver, reps):
+        out = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            X = X0.clone()
+            r = L.run(X, solver=solver, **opts)
+            out.append(r.stats)
+        return out
+
+    runs(api.SOLVER_CG, 1)
+    cg = runs(api.SOLVER_CG, 2)
+    factor_ms = [L.factor() for _ in range(2)]
+    runs(api.SOLVER_DIRECT, 1)
+    dr = runs(api.SOLVER_DIRECT, 2)
+    # phase durations of one direct run: tag 10 = the dense apply (ns between the barrier before it and its own)
+    cap = 400000
+    api.lib().fd_timeline_enable(L._h, cap)
+    L.run(X0.clone(), solver=api.SOLVER_DIRECT, **opts)
+    buf = np.zeros(2 * cap)
+    cnt = ctypes.c_int32()
+    api.lib().fd_timeline_read(L._h, buf.ctypes.data, cap, ctypes.byref(cnt))
+    api.lib().fd_timeline_enable(L._h, 0)
+    tl = buf[:2 * cnt.value].reshape(-1, 2)
+    apply_ns = [b[1] - a[1] for a, b in zip(tl[:-1], tl[1:]) if int(b[0]) == 10]
+    L.close()
+    ms_cg = statistics.median(st["kernel_ms"] for st in cg)
+    ms_dr = statistics.median(st["kernel_ms"] for st in dr)
+    fac = min(factor_ms)
+    nb = n_pad // 128
+    # Gauss-Jordan: per block step, (nb-1)^2 trailing block products and 2 (nb-1) panel products of
+    # 2 * 128^3 flops each (the pivot blocks are not counted)
+    gj_flops = nb * ((nb - 1) ** 2 + 2 * (nb - 1)) * 2.0 * 128 ** 3
+    apply_bytes = 4.0 * n_pad * n_pad
+    apply_us = float(np.mean(apply_ns)) / 1e3 if apply_ns else float("nan")
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    st_cg, st_dr = cg[0], dr[0]
+    return {"workload": f"{name} (n={n}), 2-D, X0 U[0,1]^2 seed 0, omega_c 1.5, rel-disp tol 1e-4, "
+                        f"max {args.max_iter} iters; L2 flushed before each run",
+            "cg": {"kernel_ms": ms_cg, "iterations": st_cg["iterations"], "solver_steps": st_cg["cg_steps"],
+                   "matvec_passes": st_cg["matvec_passes"], "final_stress": st_cg["final_stress"],
+                   "pairs_per_s": st_cg["pair_passes"] * st_cg["pairs"] / (ms_cg / 1e3)},
+            "direct": {"kernel_ms": ms_dr, "iterations": st_dr["iterations"], "solver_steps": st_dr["cg_steps"],
+                       "matvec_passes": st_dr["matvec_passes"], "dense_applies": st_dr["cg_steps"],
+                       "final_stress": st_dr["final_stress"],
+                       "pairs_per_s": st_dr["pair_passes"] * st_dr["pairs"] / (ms_dr / 1e3)},
+            "factor": {"kernel": "gj_update_kernel (+ gj_pivot/row/col, dense_build)", "ms": fac,
+                       "flops": gj_flops, "achieved_tflops": gj_flops / (fac / 1e3) / 1e12,
+                       "peak_tflops": fp32_peak, "frac": gj_flops / (fac / 1e3) / 1e12 / fp32_peak,
+                       "bound": "alu", "bytes_resident": apply_bytes},
+            "dense_apply": {"bound": "hbm", "bytes": apply_bytes, "us": apply_us,
+                            "achieved_gbs": apply_bytes / (apply_us * 1e-6) / 1e9 if apply_ns else None,
+                            "peak_gbs": hbm,
+                            "frac": apply_bytes / (apply_us * 1e-6) / 1e9 / hbm if apply_ns else None,
+                            "note": "one read of the FP32 inverse (4 n_pad^2 bytes) per application; duration "
+                                    "from the layout kernel's %globaltimer marks, grid barrier included"},
+            "speedup_per_run": ms_cg / ms_dr,
+            "break_even_runs": fac / (ms_cg - ms_dr) if ms_cg > ms_dr else None}
 
 
 def _largest_component(rp, ci):
@@ -658,6 +755,9 @@ def main():
     ap.add_argument("--scale", action="store_true", help="Barabasi-Albert n=200,000, 2-D and 3-D, 200 iterations, then exit")
     ap.add_argument("--table1-seeds", type=int, default=5)
     ap.add_argument("--grad-n", type=int, default=4096, help="vertices of the differentiable workload (<= 4096)")
+    ap.add_argument("--no-direct", dest="direct_sec", action="store_false", help="skip the direct-solver section")
+    ap.add_argument("--direct", action="store_true", help="only the direct-solver section, then exit")
+    ap.add_argument("--direct-n", type=int, default=0, help="Delaunay graph size of --direct (0 = delaunay20k)")
     args = ap.parse_args()
     rank, world, local_rank = _env_rank()
     if args.scale:
@@ -669,6 +769,20 @@ def main():
         torch.cuda.set_device(local_rank)
         if rank == 0:
             print(json.dumps(run_scale(args, local_rank)), flush=True)
+        return
+    if args.direct:
+        import torch
+
+        from paper_1711_01228_gb300 import api, build
+
+        build.build()
+        api.lib()
+        torch.cuda.set_device(local_rank)
+        if rank == 0:
+            peaks, src = _peaks()
+            sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
+            fp32_peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            print(json.dumps(run_direct(args, local_rank, peaks, fp32_peak)), flush=True)
         return
     if args.table1:
         import torch

@@ -337,6 +337,15 @@ fd_status fd_layout_info(const fd_layout* h, fd_info* info);
 /* Statistics of the last call on the handle (host struct). */
 fd_status fd_last_stats(const fd_layout* h, fd_stats* stats);
 
+/* Measured FP32 FMA throughput of the current device (the denominator of
+ * the layout kernel's roofline, beside the nominal SMs x 128 lanes x 2 flop
+ * x clock): every thread runs 16 independent FMA chains, scalar
+ * (packed = 0, fma.rn.f32) or two-wide (packed = 1, fma.rn.f32x2, the
+ * instruction the pair passes use); best of 5 timed launches.
+ *   tflops  TFLOP/s (host)        ms  the best launch's time (host)
+ * Errors: FD_ERR_ARG, FD_ERR_OOM, FD_ERR_CUDA. */
+fd_status fd_fp32_peak(int32_t packed, double* tflops, double* ms);
+
 /* Phase timeline (tracing).  fd_timeline_enable(h, cap) makes every later
  * layout-kernel launch record, at each of its grid-wide barriers, the
  * device time (ns since the launch started, from %globaltimer) and a phase

@@ -72,7 +72,8 @@ EXPORTED = ["fd_options_default", "fd_layout_create", "fd_layout_destroy", "fd_e
             "fd_timeline_read", "fd_batch_create", "fd_batch_destroy", "fd_batch_run", "fd_batch_results",
             "fd_batch_tune", "fd_batch_set_shape", "fd_batch_distances", "fd_batch_get_info",
             "fd_batch_last_stats", "fd_energy_length_grad", "fd_sor_step_adjoint", "fd_adjoint_reset",
-            "fd_adjoint_length_grad", "fd_set_vertex_omega", "fd_factor", "fd_factor_rows", "fd_factor_release"]
+            "fd_adjoint_length_grad", "fd_set_vertex_omega", "fd_factor", "fd_factor_rows", "fd_factor_release",
+            "fd_fp32_peak"]
 GRAD_MAX_N = 4096
 BATCH_MAX_N = 2048
 TIMELINE_TAGS = {1: "pack", 2: "stress", 3: "forces", 4: "rhs0", 5: "h_init", 6: "cg_au0", 7: "cg_step",
@@ -114,6 +115,8 @@ def lib():
     L.fd_run.restype = i32
     L.fd_set_vertex_omega.argtypes = [P, P]
     L.fd_set_vertex_omega.restype = i32
+    L.fd_fp32_peak.argtypes = [i32, ctypes.POINTER(f64), ctypes.POINTER(f64)]
+    L.fd_fp32_peak.restype = i32
     L.fd_factor.argtypes = [P]
     L.fd_factor.restype = i32
     L.fd_factor_rows.argtypes = [P, i32, i32, P]
@@ -414,6 +417,14 @@ class Layout:
                    "fd_run_trace")
             res.accepted, res.omega, res.cg_steps, res.crit = acc[:k], om[:k], cg[:k], cr[:k]
         return res
+
+
+def fp32_peak(packed: bool = True) -> float:
+    """Measured FP32 FMA throughput of the current device in TFLOP/s
+    (two-wide packed FMAs when ``packed``)."""
+    t, ms = ctypes.c_double(), ctypes.c_double()
+    _check(lib().fd_fp32_peak(int(bool(packed)), ctypes.byref(t), ctypes.byref(ms)), "fd_fp32_peak")
+    return t.value
 
 
 def trace_records(result: RunResult) -> list:

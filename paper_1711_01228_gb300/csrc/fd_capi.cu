@@ -33,6 +33,7 @@ cudaError_t main_config_d3(int code, size_t lut_bytes, int nbuf, int* blocks_per
 cudaError_t launch_main_d1(int code, const KParams& p, int grid, size_t smem, cudaStream_t st);
 cudaError_t launch_main_d2(int code, const KParams& p, int grid, size_t smem, cudaStream_t st);
 cudaError_t launch_main_d3(int code, const KParams& p, int grid, size_t smem, cudaStream_t st);
+cudaError_t measure_fp32_peak(int packed, int sm_count, int reps, double* tflops, double* best_ms);
 cudaError_t launch_direct_factor(int n, int n_pad, int nb, int code, const void* D, const int2* tile_ik, int ntiles,
                                  const float* s, float shift, float* M, float* P, int* err, int sm_count,
                                  cudaStream_t st);
@@ -1017,6 +1018,21 @@ fd_status fd_adjoint_length_grad(fd_layout* h, float* grad_len) {
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(h, cuda_status(e));
+  }
+  return FD_OK;
+}
+
+fd_status fd_fp32_peak(int32_t packed, double* tflops, double* ms) {
+  if (!tflops || !ms) return FD_ERR_ARG;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return FD_ERR_CUDA;
+  }
+  cudaError_t e = measure_fp32_peak(packed ? 1 : 0, sms, 5, tflops, ms);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_status(e);
   }
   return FD_OK;
 }
