@@ -544,9 +544,10 @@ def run_direct(args, local_rank, peaks, fp32_peak):
     ms_dr = statistics.median(st["kernel_ms"] for st in dr)
     fac = min(factor_ms)
     nb = n_pad // 128
-    # Gauss-Jordan: per block step, (nb-1)^2 trailing block products and 2 (nb-1) panel products of
-    # 2 * 128^3 flops each (the pivot blocks are not counted)
-    gj_flops = nb * ((nb - 1) ** 2 + 2 * (nb - 1)) * 2.0 * 128 ** 3
+    # symmetric sweep: per block step, m (m + 1) / 2 trailing block products (lower blocks, m = nb - 1)
+    # and m panel products of 2 * 128^3 flops each (the pivot blocks are not counted)
+    m = nb - 1
+    gj_flops = nb * (m * (m + 1) // 2 + m) * 2.0 * 128 ** 3
     apply_bytes = 4.0 * n_pad * n_pad
     apply_us = float(np.mean(apply_ns)) / 1e3 if apply_ns else float("nan")
     hbm = peaks.get("hbm_gbs", 6800.0)
@@ -560,7 +561,7 @@ def run_direct(args, local_rank, peaks, fp32_peak):
                        "matvec_passes": st_dr["matvec_passes"], "dense_applies": st_dr["cg_steps"],
                        "final_stress": st_dr["final_stress"],
                        "pairs_per_s": st_dr["pair_passes"] * st_dr["pairs"] / (ms_dr / 1e3)},
-            "factor": {"kernel": "gj_update_kernel (+ gj_pivot/row/col, dense_build)", "ms": fac,
+            "factor": {"kernel": "sw_update_kernel (+ sw_pivot/panel/finish, dense_build)", "ms": fac,
                        "flops": gj_flops, "achieved_tflops": gj_flops / (fac / 1e3) / 1e12,
                        "peak_tflops": fp32_peak, "frac": gj_flops / (fac / 1e3) / 1e12 / fp32_peak,
                        "bound": "alu", "bytes_resident": apply_bytes},

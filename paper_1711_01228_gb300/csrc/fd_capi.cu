@@ -35,8 +35,8 @@ cudaError_t launch_main_d2(int code, const KParams& p, int grid, size_t smem, cu
 cudaError_t launch_main_d3(int code, const KParams& p, int grid, size_t smem, cudaStream_t st);
 cudaError_t measure_fp32_peak(int packed, int sm_count, int reps, double* tflops, double* best_ms);
 cudaError_t launch_direct_factor(int n, int n_pad, int nb, int code, const void* D, const int2* tile_ik, int ntiles,
-                                 const float* s, float shift, float* M, float* P, int* err, int sm_count,
-                                 cudaStream_t st);
+                                 const float* s, float shift, float* M, float* P, float* QT, float* AT, int* err,
+                                 int sm_count, cudaStream_t st);
 cudaError_t launch_bfs_multi(const BGraph* graphs, const int2* items, int nitems, const int* rp, const int* ci,
                              unsigned char* D, int n_max, int* maxlevel, int* overflow, int grid, cudaStream_t st);
 cudaError_t launch_fill_multi(const BGraph* graphs, const int* tile_graph, const int2* tile_ik, long long ntiles,
@@ -1044,15 +1044,19 @@ fd_status fd_factor(fd_layout* h) {
   const size_t np = (size_t)h->n_pad;
   fd_status s = FD_OK;
   if (!h->d_ainv && (s = dev_alloc(&h->d_ainv, np * np)) != FD_OK) return fail(h, s);
-  float* P = nullptr;
+  float *P = nullptr, *QT = nullptr, *AT = nullptr;
   int* err = nullptr;
   int2* tik = nullptr;
   auto cleanup = [&] {
     dev_free(P);
+    dev_free(QT);
+    dev_free(AT);
     dev_free(err);
     dev_free(tik);
   };
-  if ((s = dev_alloc(&P, (size_t)TILE * TILE)) != FD_OK || (s = dev_alloc(&err, 1)) != FD_OK ||
+  const size_t panel = (size_t)h->nb * TILE * TILE;
+  if ((s = dev_alloc(&P, (size_t)TILE * TILE)) != FD_OK || (s = dev_alloc(&QT, panel)) != FD_OK ||
+      (s = dev_alloc(&AT, panel)) != FD_OK || (s = dev_alloc(&err, 1)) != FD_OK ||
       (s = upload_tile_ik(h, &tik)) != FD_OK) {
     cleanup();
     dev_free(h->d_ainv);
@@ -1071,7 +1075,7 @@ fd_status fd_factor(fd_layout* h) {
   if (e == cudaSuccess) e = cudaEventRecord(h->ev0, st);
   if (e == cudaSuccess)
     e = launch_direct_factor(h->n, h->n_pad, h->nb, h->code, h->D, tik, h->ntiles, h->d_s, (float)(sigma / h->n),
-                             h->d_ainv, P, err, h->sm_count, st);
+                             h->d_ainv, P, QT, AT, err, h->sm_count, st);
   if (e == cudaSuccess) e = cudaEventRecord(h->ev1, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);

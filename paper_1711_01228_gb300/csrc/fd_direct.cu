@@ -12,17 +12,12 @@
 // L^W z = b; pinning vertex 0 is then a translation.
 //
 // A' is stored dense, FP32, n_pad x n_pad (padding rows and columns are the
-// identity), and inverted in place by blocked Gauss-Jordan elimination
-// without pivoting (stable for a positive definite matrix), 128 x 128
-// blocks.  Step k:
-//     P      = (M_kk)^-1                 one CTA, unblocked, in shared memory
-//     M_kj  := P M_kj          (j != k)  row panel
-//     M_ij  -= M_ik M_kj    (i, j != k)  trailing update (old M_ik, new M_kj)
-//     M_ik  := -M_ik P         (i != k)  column panel
-//     M_kk  := P
-// which leaves A'^-1 after the last step.  The three multiplications share
-// one 128 x 128 x 128 FP32 block product from shared memory (8 x 8 outputs
-// per thread).
+// identity), and inverted in place by the symmetric sweep (Gauss-Jordan
+// elimination that keeps the matrix symmetric; no pivoting, which is stable
+// for a positive definite matrix) in 128 x 128 blocks, updating only the
+// lower triangle: n_pad^3 flops, half of plain Gauss-Jordan.  The block
+// products are FP32 on the CUDA cores, 128 x 128 outputs per CTA (8 x 8 per
+// thread) from shared memory.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -34,8 +29,6 @@ namespace {
 
 constexpr int NB = TILE;       // block side of the elimination
 constexpr int LDT = NB + 4;    // shared-memory row stride (floats): 16-byte rows, fewer bank conflicts
-constexpr int MM_THREADS = 256;
-constexpr size_t MM_SMEM = 2 * (size_t)NB * LDT * sizeof(float);
 
 // ---------------------------------------------------------------- build A'
 // One CTA per stored tile (I, J = (I + k) mod nb): its 128 x 128 distances go
@@ -89,8 +82,8 @@ __global__ void __launch_bounds__(256) dense_build_kernel(int n, int n_pad, int 
 }
 
 // ------------------------------------------------------------- block product
-// Loads the 128 x 128 block at g (leading dimension ld) into shared memory,
-// row-major (dst[r][c]) or transposed (dst[c][r]).
+// Loads the 128 x 128 block at g (leading dimension ld) into shared memory
+// (row stride LDT), row-major (dst[r][c]) or transposed (dst[c][r]).
 __device__ __forceinline__ void load_block(float* dst, const float* g, size_t ld, bool transpose) {
   if (!transpose) {
     // a warp reads one row (512 contiguous bytes) and writes it as one row
@@ -117,11 +110,12 @@ __device__ __forceinline__ void load_block(float* dst, const float* g, size_t ld
 // and the same columns with tx.
 __device__ __forceinline__ int own(int base, int q) { return (q < 4) ? 4 * base + q : 64 + 4 * base + (q - 4); }
 
-// acc[q][u] += sum_k A[own(ty,q)][k] * B[k][own(tx,u)], with At = A transposed
-// and Bs = B, both [NB][LDT] in shared memory.
+// acc[q][u] += sum_{k < K} A[own(ty,q)][k] * B[k][own(tx,u)], with At = A
+// transposed and Bs = B, both [K][LDT] in shared memory.
+template <int K, int U>
 __device__ __forceinline__ void block_mma(const float* At, const float* Bs, float (&acc)[8][8], int ty, int tx) {
-#pragma unroll 2
-  for (int k = 0; k < NB; ++k) {
+#pragma unroll U
+  for (int k = 0; k < K; ++k) {
     const float4 a0 = *reinterpret_cast<const float4*>(At + k * LDT + 4 * ty);
     const float4 a1 = *reinterpret_cast<const float4*>(At + k * LDT + 64 + 4 * ty);
     const float4 b0 = *reinterpret_cast<const float4*>(Bs + k * LDT + 4 * tx);
@@ -146,67 +140,168 @@ __device__ __forceinline__ void store_acc(float* g, size_t ld, const float (&acc
   }
 }
 
-// ------------------------------------------------------------ elimination
-// P = (M_kk)^-1 by unblocked Gauss-Jordan in shared memory; M_kk := P.  A
-// pivot that is not positive (impossible for a positive definite matrix in
-// exact arithmetic) sets *err and is replaced by 1 so that the step ends.
-__global__ void __launch_bounds__(512) gj_pivot_kernel(float* __restrict__ M, size_t ld, int k, float* __restrict__ P,
-                                                       int* err) {
-  extern __shared__ __align__(16) float S[];  // [NB][LDT]
+__device__ __forceinline__ void cp_async16(float* smem_dst, const float* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// ------------------------------------------------------------- the sweep
+// The symmetric sweep keeps the matrix symmetric, so only blocks (i, j) with
+// i >= j are kept up to date.  Step k (P = (M_kk)^-1):
+//     M_ij -= (M_ik P) M_kj   (i >= j, i, j != k)   trailing update
+//     M_ik := M_ik P          (i != k)              panel
+//     M_kk := -P
+// After every block has been the pivot, the lower triangle holds -A'^-1.
+
+// P = (M_kk)^-1 by unblocked Gauss-Jordan, the block held in registers:
+// thread t owns rows 8 (t / 32) .. + 7 and columns 4 (t % 32) .. + 3.  Per
+// pivot p the owners of row p and column p publish them in shared memory
+// (two buffers, alternating, so one barrier per pivot).  Writes P to Pbuf
+// and -P to M_kk.  A pivot that is not positive (impossible for a positive
+// definite matrix in exact arithmetic) sets *err and is replaced by 1.
+constexpr int PIV_THREADS = 512;
+__global__ void __launch_bounds__(PIV_THREADS) sw_pivot_kernel(float* __restrict__ M, size_t ld, int k,
+                                                                float* __restrict__ P, int* err) {
+  __shared__ float rowb[2][NB], colb[2][NB];
+  const int t = threadIdx.x, r0 = (t / 32) * 8, c0 = (t % 32) * 4;
   float* g = M + (size_t)k * NB * ld + (size_t)k * NB;
-  load_block(S, g, ld, false);
-  __syncthreads();
-  const int tid = threadIdx.x, nt = blockDim.x;
+  float a[8][4];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const float4 v = *reinterpret_cast<const float4*>(g + (size_t)(r0 + q) * ld + c0);
+    a[q][0] = v.x, a[q][1] = v.y, a[q][2] = v.z, a[q][3] = v.w;
+  }
+  bool bad = false;
   for (int p = 0; p < NB; ++p) {
-    float piv = S[p * LDT + p];
+    const int b = p & 1;
+    if (p >= r0 && p < r0 + 8) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (r0 + q == p)
+#pragma unroll
+          for (int u = 0; u < 4; ++u) rowb[b][c0 + u] = a[q][u];
+    }
+    if (p >= c0 && p < c0 + 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (c0 + u == p)
+#pragma unroll
+          for (int q = 0; q < 8; ++q) colb[b][r0 + q] = a[q][u];
+    }
+    __syncthreads();
+    float piv = rowb[b][p];
     if (!(piv > 0.f) || !isfinite(piv)) {
-      if (tid == 0) atomicExch(err, 1);
+      bad = true;
       piv = 1.f;
     }
     const float inv = 1.f / piv;
-    for (int j = tid; j < NB; j += nt)
-      if (j != p) S[p * LDT + j] *= inv;
-    __syncthreads();
-    for (int e = tid; e < NB * NB; e += nt) {
-      const int i = e / NB, j = e % NB;
-      if (i != p && j != p) S[i * LDT + j] = fmaf(-S[i * LDT + p], S[p * LDT + j], S[i * LDT + j]);
-    }
-    __syncthreads();
-    for (int i = tid; i < NB; i += nt) S[i * LDT + p] = (i == p) ? inv : -S[i * LDT + p] * inv;
-    __syncthreads();
+    float rj[4], ci[8];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) rj[u] = rowb[b][c0 + u];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) ci[q] = colb[b][r0 + q] * inv;
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = r0 + q, j = c0 + u;
+        if (i == p) a[q][u] = (j == p) ? inv : a[q][u] * inv;  // row p scaled, pivot inverted
+        else if (j == p) a[q][u] = -ci[q];                      // column p: -a_ip / piv
+        else a[q][u] = fmaf(-ci[q], rj[u], a[q][u]);            // a_ij - a_ip a_pj / piv
+      }
   }
-  for (int e = tid; e < NB * NB; e += nt) {
-    const int i = e / NB, j = e % NB;
-    P[i * NB + j] = S[i * LDT + j];
-    g[(size_t)i * ld + j] = S[i * LDT + j];
+  if (bad) atomicExch(err, 1);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    *reinterpret_cast<float4*>(P + (r0 + q) * NB + c0) = make_float4(a[q][0], a[q][1], a[q][2], a[q][3]);
+    *reinterpret_cast<float4*>(g + (size_t)(r0 + q) * ld + c0) = make_float4(-a[q][0], -a[q][1], -a[q][2], -a[q][3]);
   }
 }
 
-// Row panel: M_kj := P M_kj for the nb - 1 blocks j != k.
-__global__ void __launch_bounds__(MM_THREADS) gj_row_kernel(float* __restrict__ M, size_t ld, int k,
-                                                            const float* __restrict__ P) {
+// Panel, one CTA per block i != k: Q_i = M_ik P with M_ik read from the
+// lower triangle (block (i, k) if i > k, the transpose of block (k, i) if
+// i < k).  Writes the update's two operands, both [K][row] so that its
+// copies are plain: QT_i = Q_i^T and AT_i = M_ik^T (before scaling); and
+// the new panel M_ik := Q_i into the lower triangle.
+constexpr int MM_THREADS = 256;
+constexpr size_t PANEL_SMEM = 2 * (size_t)NB * LDT * sizeof(float);
+__global__ void __launch_bounds__(MM_THREADS) sw_panel_kernel(float* __restrict__ M, size_t ld, int k,
+                                                              const float* __restrict__ P, float* __restrict__ QT,
+                                                              float* __restrict__ AT) {
   extern __shared__ __align__(16) float sm[];
   float *At = sm, *Bs = sm + NB * LDT;
-  const int j = blockIdx.x + (blockIdx.x >= k ? 1 : 0);
-  float* g = M + (size_t)k * NB * ld + (size_t)j * NB;
-  load_block(At, P, NB, true);
-  load_block(Bs, g, ld, false);
+  const int i = blockIdx.x + (blockIdx.x >= k ? 1 : 0);
+  const bool below = i > k;
+  float* gpan = below ? M + (size_t)i * NB * ld + (size_t)k * NB : M + (size_t)k * NB * ld + (size_t)i * NB;
+  load_block(At, gpan, ld, below);  // At[kk][r] = M_ik[r][kk]
+  load_block(Bs, P, NB, false);
   __syncthreads();
+  float* at = AT + (size_t)i * NB * NB;
+  for (int e = threadIdx.x; e < NB * NB / 4; e += blockDim.x) {
+    const int r = e / (NB / 4), c4 = (e % (NB / 4)) * 4;
+    *reinterpret_cast<float4*>(at + r * NB + c4) = *reinterpret_cast<const float4*>(At + r * LDT + c4);
+  }
   const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
   float acc[8][8] = {};
-  block_mma(At, Bs, acc, ty, tx);
-  store_acc(g, ld, acc, ty, tx, 1.f);
+  block_mma<NB, 2>(At, Bs, acc, ty, tx);
+  __syncthreads();  // At is reused for Q_i
+  constexpr int LQ = NB + 1;
+  float* Cs = sm;  // [NB][LQ]: Cs[r][c] = Q_i[r][c]
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+#pragma unroll
+    for (int u = 0; u < 8; ++u) Cs[own(ty, q) * LQ + own(tx, u)] = acc[q][u];
+  __syncthreads();
+  float* qt = QT + (size_t)i * NB * NB;
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int a = e / NB, b = e % NB;  // QT_i[a][b] = Q_i[b][a]
+    const float v = Cs[b * LQ + a];
+    qt[a * NB + b] = v;
+    if (!below) gpan[(size_t)a * ld + b] = v;  // block (k, i) = Q_i^T
+  }
+  if (below)
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+      const int r = e / NB, c = e % NB;
+      gpan[(size_t)r * ld + c] = Cs[r * LQ + c];  // block (i, k) = Q_i
+    }
 }
 
-// Trailing update: M_ij -= M_ik M_kj for i, j != k.
-__global__ void __launch_bounds__(MM_THREADS) gj_update_kernel(float* __restrict__ M, size_t ld, int k, int nb) {
+// Trailing update of the lower blocks: one CTA per block (i, j), i >= j,
+// i, j != k:  M_ij -= Q_i M_kj = sum_kk QT_i[kk][r] AT_j[kk][c].  The two
+// operands stream through shared memory in chunks of BK rows, two stages,
+// by cp.async; the output block stays in registers.  Two CTAs per SM.
+constexpr int BK = 32;
+constexpr size_t UPD_STAGE = 2 * (size_t)BK * LDT;  // floats per stage (QT chunk + AT chunk)
+constexpr size_t UPD_SMEM = 2 * UPD_STAGE * sizeof(float);
+__global__ void __launch_bounds__(MM_THREADS, 2) sw_update_kernel(float* __restrict__ M, size_t ld, int k, int nb,
+                                                                 const float* __restrict__ QT,
+                                                                 const float* __restrict__ AT) {
   extern __shared__ __align__(16) float sm[];
-  float *At = sm, *Bs = sm + NB * LDT;
-  const int m = nb - 1;
-  const int ii = blockIdx.x / m, jj = blockIdx.x % m;
+  // block b of the lower triangle of an m x m grid, row-major: ii (ii + 1) / 2 <= b
+  const int b = blockIdx.x;
+  int ii = (int)((sqrtf(8.f * b + 1.f) - 1.f) * 0.5f);
+  while ((ii + 1) * (ii + 2) / 2 <= b) ++ii;
+  while (ii * (ii + 1) / 2 > b) --ii;
+  const int jj = b - ii * (ii + 1) / 2;
   const int i = ii + (ii >= k ? 1 : 0), j = jj + (jj >= k ? 1 : 0);
-  load_block(At, M + (size_t)i * NB * ld + (size_t)k * NB, ld, true);
-  load_block(Bs, M + (size_t)k * NB * ld + (size_t)j * NB, ld, false);
+  const float* qa = QT + (size_t)i * NB * NB;
+  const float* ab = AT + (size_t)j * NB * NB;
+  auto issue = [&](int chunk, int stage) {
+    float* As = sm + stage * UPD_STAGE;
+    float* Bs = As + BK * LDT;
+    for (int e = threadIdx.x; e < BK * NB / 4; e += blockDim.x) {
+      const int r = e / (NB / 4), c4 = (e % (NB / 4)) * 4;
+      cp_async16(As + r * LDT + c4, qa + (size_t)(chunk * BK + r) * NB + c4);
+      cp_async16(Bs + r * LDT + c4, ab + (size_t)(chunk * BK + r) * NB + c4);
+    }
+    cp_async_commit();
+  };
+  issue(0, 0);
   const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
   float* g = M + (size_t)i * NB * ld + (size_t)j * NB;
   float acc[8][8];
@@ -215,61 +310,87 @@ __global__ void __launch_bounds__(MM_THREADS) gj_update_kernel(float* __restrict
     const float* row = g + (size_t)own(ty, q) * ld;
     const float4 c0 = *reinterpret_cast<const float4*>(row + 4 * tx);
     const float4 c1 = *reinterpret_cast<const float4*>(row + 64 + 4 * tx);
-    // negated, so that the shared product adds: -(M_ij - M_ik M_kj) = -M_ij + M_ik M_kj
+    // negated, so that the block product adds: -(M_ij - Q_i M_kj) = -M_ij + Q_i M_kj
     acc[q][0] = -c0.x, acc[q][1] = -c0.y, acc[q][2] = -c0.z, acc[q][3] = -c0.w;
     acc[q][4] = -c1.x, acc[q][5] = -c1.y, acc[q][6] = -c1.z, acc[q][7] = -c1.w;
   }
-  __syncthreads();
-  block_mma(At, Bs, acc, ty, tx);
+  constexpr int NCH = NB / BK;
+#pragma unroll 1
+  for (int c = 0; c < NCH; ++c) {
+    if (c + 1 < NCH) {
+      issue(c + 1, (c + 1) & 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();  // chunk c visible to every thread
+    const float* As = sm + (c & 1) * UPD_STAGE;
+    block_mma<BK, 1>(As, As + BK * LDT, acc, ty, tx);  // unrolled further it spills at 2 CTAs per SM
+    __syncthreads();  // every thread is done with the stage before chunk c + 2 overwrites it
+  }
   store_acc(g, ld, acc, ty, tx, -1.f);
 }
 
-// Column panel: M_ik := -M_ik P for the nb - 1 blocks i != k.
-__global__ void __launch_bounds__(MM_THREADS) gj_col_kernel(float* __restrict__ M, size_t ld, int k,
-                                                            const float* __restrict__ P) {
-  extern __shared__ __align__(16) float sm[];
-  float *At = sm, *Bs = sm + NB * LDT;
-  const int i = blockIdx.x + (blockIdx.x >= k ? 1 : 0);
-  float* g = M + (size_t)i * NB * ld + (size_t)k * NB;
-  load_block(At, g, ld, true);
-  load_block(Bs, P, NB, false);
+// Lower triangle holds -A'^-1: negate it and mirror it to the upper
+// triangle.  One CTA per lower block (i, j); the transpose goes through
+// shared memory so that both writes are row by row.
+constexpr size_t FIN_SMEM = (size_t)NB * (NB + 1) * sizeof(float);
+__global__ void __launch_bounds__(256) sw_finish_kernel(float* __restrict__ M, size_t ld) {
+  extern __shared__ __align__(16) float fin[];
+  auto Cs = reinterpret_cast<float(*)[NB + 1]>(fin);
+  const int b = blockIdx.x;
+  int i = (int)((sqrtf(8.f * b + 1.f) - 1.f) * 0.5f);
+  while ((i + 1) * (i + 2) / 2 <= b) ++i;
+  while (i * (i + 1) / 2 > b) --i;
+  const int j = b - i * (i + 1) / 2;
+  float* g = M + (size_t)i * NB * ld + (size_t)j * NB;
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int r = e / NB, c = e % NB;
+    const float v = -g[(size_t)r * ld + c];
+    Cs[r][c] = v;
+    g[(size_t)r * ld + c] = v;
+  }
+  if (i == j) return;
   __syncthreads();
-  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
-  float acc[8][8] = {};
-  block_mma(At, Bs, acc, ty, tx);
-  store_acc(g, ld, acc, ty, tx, -1.f);
+  float* h = M + (size_t)j * NB * ld + (size_t)i * NB;
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int r = e / NB, c = e % NB;
+    h[(size_t)r * ld + c] = Cs[c][r];
+  }
 }
 
 }  // namespace
 
-// Builds A' from the distance tiles and inverts it in place (stream-ordered;
-// *err is set on the device if a pivot was not positive).
+// Builds A' from the distance tiles and inverts it in place by the
+// symmetric sweep (stream-ordered; *err is set on the device if a pivot was
+// not positive).  Scratch: P [NB][NB], QT and AT [nb][NB][NB] each.
 cudaError_t launch_direct_factor(int n, int n_pad, int nb, int code, const void* D, const int2* tile_ik, int ntiles,
-                                 const float* s, float shift, float* M, float* P, int* err, int sm_count,
-                                 cudaStream_t st) {
+                                 const float* s, float shift, float* M, float* P, float* QT, float* AT, int* err,
+                                 int sm_count, cudaStream_t st) {
   const size_t build_smem = (size_t)TILE * (TILE + 1) * sizeof(float);
   cudaError_t e = cudaFuncSetAttribute(dense_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)build_smem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(gj_pivot_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(NB * LDT * 4));
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(gj_row_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MM_SMEM);
+    e = cudaFuncSetAttribute(sw_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PANEL_SMEM);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(gj_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MM_SMEM);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(gj_col_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MM_SMEM);
+    e = cudaFuncSetAttribute(sw_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)UPD_SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(sw_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FIN_SMEM);
   if (e != cudaSuccess) return e;
   const int bgrid = ntiles < 4 * sm_count ? ntiles : 4 * sm_count;
   dense_build_kernel<<<bgrid, 256, build_smem, st>>>(n, n_pad, nb, code, D, tile_ik, ntiles, s, shift, M);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const size_t ld = (size_t)n_pad;
+  const int m = nb - 1;
   for (int k = 0; k < nb; ++k) {
-    gj_pivot_kernel<<<1, 512, NB * LDT * 4, st>>>(M, ld, k, P, err);
-    if (nb > 1) {
-      gj_row_kernel<<<nb - 1, MM_THREADS, MM_SMEM, st>>>(M, ld, k, P);
-      gj_update_kernel<<<(unsigned)((nb - 1) * (nb - 1)), MM_THREADS, MM_SMEM, st>>>(M, ld, k, nb);
-      gj_col_kernel<<<nb - 1, MM_THREADS, MM_SMEM, st>>>(M, ld, k, P);
+    sw_pivot_kernel<<<1, PIV_THREADS, 0, st>>>(M, ld, k, P, err);
+    if (m > 0) {
+      sw_panel_kernel<<<m, MM_THREADS, PANEL_SMEM, st>>>(M, ld, k, P, QT, AT);
+      sw_update_kernel<<<(unsigned)(m * (m + 1) / 2), MM_THREADS, UPD_SMEM, st>>>(M, ld, k, nb, QT, AT);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  return cudaSuccess;
+  sw_finish_kernel<<<(unsigned)(nb * (nb + 1) / 2), 256, FIN_SMEM, st>>>(M, ld);
+  return cudaGetLastError();
 }
 
 }  // namespace fdl
