@@ -125,3 +125,41 @@ def test_short_run_consistent(case):
     assert np.all(np.diff(r.trace_f) <= 1e-6 * r.trace_f[:-1])
     f_ref = oracle.stress_stream(X, case.rp, case.ci, case.fill)
     assert r.stress == pytest.approx(f_ref, rel=1e-5)
+
+
+def test_direct_inverse_sampled(case):
+    """The factored inverse at full size, through the identity it must meet:
+    A' = L^W + (sigma/n) 1 1^T and A'^-1 1 = 1/sigma give, for any rows r, r',
+    (L^W A'^-1)_{r'r} + 1/n = delta_{r'r}; L^W row r' comes from one BFS row.
+    Tolerance: the inverse's forward error is about sqrt(n) kappa eps32
+    (141 * 13 * 6e-8 = 1.1e-4 at n = 20,000); 1e-3 leaves a factor 9."""
+    case.L.factor()
+    try:
+        for r in case.rows[:4]:
+            a = case.L.factor_rows(int(r), 1)[0]
+            for rp_ in case.rows:
+                d = case.drow(rp_)
+                w = np.where(d > 0, 1.0 / np.where(d > 0, d, 1.0) ** 2, 0.0)
+                lw_a = w.sum() * a[rp_] - np.dot(w, a)
+                want = 1.0 if rp_ == r else 0.0
+                assert abs(lw_a + 1.0 / case.n - want) <= 1e-3, f"rows {rp_}, {r}"
+    finally:
+        case.L.factor_release()
+
+
+def test_direct_short_run_matches_cg(case):
+    """Five iterations of Algorithm 2 at omega = 0.5 with the direct solver and
+    with CG, in the benchmark's launch: both solve every H step to relative
+    residual 1e-6, so the stress traces agree to 1e-5 and the layouts to 1e-4."""
+    Xc = case.X0.copy()
+    rc = case.L.run(Xc, trace=True, omega=0.5, tol=0.0, max_iter=5, cg_tol=1e-6, cg_max=500)
+    case.L.factor()
+    try:
+        Xd = case.X0.copy()
+        rd = case.L.run(Xd, trace=True, omega=0.5, tol=0.0, max_iter=5, cg_tol=1e-6, cg_max=50,
+                        solver=api.SOLVER_DIRECT)
+    finally:
+        case.L.factor_release()
+    assert np.allclose(rd.trace_f, rc.trace_f, rtol=1e-5, atol=0)
+    assert np.array_equal(rd.accepted, rc.accepted)
+    assert np.linalg.norm(Xd - Xc) <= 1e-4 * np.linalg.norm(Xc)
