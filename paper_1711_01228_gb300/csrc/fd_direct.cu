@@ -129,6 +129,42 @@ __device__ __forceinline__ void block_mma(const float* At, const float* Bs, floa
   }
 }
 
+// The same product with two-wide FMAs (fma.rn.f32x2: two independent IEEE
+// FMAs, so every output is rounded exactly as by fmaf, in the same order):
+// acc[q][v] holds columns own(tx, 2v) and own(tx, 2v + 1) of row own(ty, q).
+typedef unsigned long long f2x;
+__device__ __forceinline__ f2x pk2(float lo, float hi) {
+  f2x r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void up2(f2x v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2x fma2(f2x a, f2x b, f2x c) {
+  f2x d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+template <int K, int U>
+__device__ __forceinline__ void block_mma2(const float* At, const float* Bs, f2x (&acc)[8][4], int ty, int tx) {
+#pragma unroll U
+  for (int k = 0; k < K; ++k) {
+    const float4 a0 = *reinterpret_cast<const float4*>(At + k * LDT + 4 * ty);
+    const float4 a1 = *reinterpret_cast<const float4*>(At + k * LDT + 64 + 4 * ty);
+    const ulonglong2 b0 = *reinterpret_cast<const ulonglong2*>(Bs + k * LDT + 4 * tx);
+    const ulonglong2 b1 = *reinterpret_cast<const ulonglong2*>(Bs + k * LDT + 64 + 4 * tx);
+    const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    const f2x b[4] = {b0.x, b0.y, b1.x, b1.y};
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const f2x aa = pk2(a[q], a[q]);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[q][v] = fma2(aa, b[v], acc[q][v]);
+    }
+  }
+}
+
 __device__ __forceinline__ void store_acc(float* g, size_t ld, const float (&acc)[8][8], int ty, int tx, float scale) {
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
@@ -304,15 +340,15 @@ __global__ void __launch_bounds__(MM_THREADS, 2) sw_update_kernel(float* __restr
   issue(0, 0);
   const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
   float* g = M + (size_t)i * NB * ld + (size_t)j * NB;
-  float acc[8][8];
+  f2x acc[8][4];
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     const float* row = g + (size_t)own(ty, q) * ld;
     const float4 c0 = *reinterpret_cast<const float4*>(row + 4 * tx);
     const float4 c1 = *reinterpret_cast<const float4*>(row + 64 + 4 * tx);
     // negated, so that the block product adds: -(M_ij - Q_i M_kj) = -M_ij + Q_i M_kj
-    acc[q][0] = -c0.x, acc[q][1] = -c0.y, acc[q][2] = -c0.z, acc[q][3] = -c0.w;
-    acc[q][4] = -c1.x, acc[q][5] = -c1.y, acc[q][6] = -c1.z, acc[q][7] = -c1.w;
+    acc[q][0] = pk2(-c0.x, -c0.y), acc[q][1] = pk2(-c0.z, -c0.w);
+    acc[q][2] = pk2(-c1.x, -c1.y), acc[q][3] = pk2(-c1.z, -c1.w);
   }
   constexpr int NCH = NB / BK;
 #pragma unroll 1
@@ -325,10 +361,18 @@ __global__ void __launch_bounds__(MM_THREADS, 2) sw_update_kernel(float* __restr
     }
     __syncthreads();  // chunk c visible to every thread
     const float* As = sm + (c & 1) * UPD_STAGE;
-    block_mma<BK, 1>(As, As + BK * LDT, acc, ty, tx);  // unrolled further it spills at 2 CTAs per SM
+    block_mma2<BK, 2>(As, As + BK * LDT, acc, ty, tx);
     __syncthreads();  // every thread is done with the stage before chunk c + 2 overwrites it
   }
-  store_acc(g, ld, acc, ty, tx, -1.f);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    float v[8];
+#pragma unroll
+    for (int w = 0; w < 4; ++w) up2(acc[q][w], v[2 * w], v[2 * w + 1]);
+    float* row = g + (size_t)own(ty, q) * ld;
+    *reinterpret_cast<float4*>(row + 4 * tx) = make_float4(-v[0], -v[1], -v[2], -v[3]);
+    *reinterpret_cast<float4*>(row + 64 + 4 * tx) = make_float4(-v[4], -v[5], -v[6], -v[7]);
+  }
 }
 
 // Lower triangle holds -A'^-1: negate it and mirror it to the upper
