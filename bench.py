@@ -257,6 +257,7 @@ def run_ours(args, rank, world, local_rank):
     batched = run_batched(args, local_rank, fp32_peak) if (args.batch and rank == 0) else None
     differentiable = run_differentiable(args, local_rank) if (args.grad and rank == 0) else None
     direct = run_direct(args, local_rank, peaks, fp32_peak) if (args.direct_sec and rank == 0) else None
+    vertex_omega = run_vertex_omega(args, local_rank) if (args.direct_sec and rank == 0) else None
     line = {
         "metric": "pair-interactions/s",
         "value": value,
@@ -305,6 +306,8 @@ def run_ours(args, rank, world, local_rank):
         line["differentiable"] = differentiable
     if direct is not None:
         line["direct_solver"] = direct
+    if vertex_omega is not None:
+        line["vertex_omega"] = vertex_omega
     return line
 
 
@@ -575,6 +578,47 @@ def run_direct(args, local_rank, peaks, fp32_peak):
             "break_even_runs": fac / (ms_cg - ms_dr) if ms_cg > ms_dr else None}
 
 
+def run_vertex_omega(args, local_rank):
+    """Per-vertex relaxation factors (omega_i = omega m_i, Sec. 6) on the
+    Delaunay 20,000 graph with the headline options: no factors, m = 1 (the
+    same trajectory: the cost of forming omega_i per vertex) and seeded
+    m_i uniform in [0, 2] (the paper gives no rule for choosing them)."""
+    import torch
+
+    from paper_1711_01228_gb300 import api
+
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    rp, ci = synth.workload("delaunay20k")
+    n = len(rp) - 1
+    X0 = torch.from_numpy(synth.initial_layout(n, 2, seed=0)).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    L = api.Layout(torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev), dim=2, disconnected_policy=1,
+                   stream=stream.cuda_stream)
+    cases = {"none": None, "ones": np.ones(n, np.float32),
+             "uniform_0_2": np.random.default_rng(0).uniform(0.0, 2.0, n).astype(np.float32)}
+    out = {}
+    for name, m in cases.items():
+        L.set_vertex_omega(m)
+        stats = []
+        for rep in range(3):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            r = L.run(X0.clone(), omega=0.5, tol=1e-4, max_iter=args.max_iter, stop=api.STOP_REL_DISP)
+            if rep > 0:
+                stats.append(r.stats)
+        ms = statistics.median(st["kernel_ms"] for st in stats)
+        st = stats[0]
+        out[name] = {"kernel_ms": ms, "iterations": st["iterations"], "accepted": st["accepted"],
+                     "final_stress": st["final_stress"], "ms_per_iteration": ms / max(st["iterations"], 1),
+                     "pairs_per_s": st["pair_passes"] * st["pairs"] / (ms / 1e3)}
+    L.close()
+    return {"workload": "delaunay20k (n=20000), 2-D, X0 U[0,1]^2 seed 0, omega 0.5 (classical 1.5) times "
+                        "per-vertex factors m, rel-disp tol 1e-4; L2 flushed before each run; median of 2",
+            "cases": out,
+            "overhead_ones_vs_none": out["ones"]["ms_per_iteration"] / out["none"]["ms_per_iteration"] - 1.0}
+
+
 def _largest_component(rp, ci):
     """CSR of the largest connected component (vertices renumbered in order)."""
     import scipy.sparse as sp
@@ -756,7 +800,8 @@ def main():
     ap.add_argument("--scale", action="store_true", help="Barabasi-Albert n=200,000, 2-D and 3-D, 200 iterations, then exit")
     ap.add_argument("--table1-seeds", type=int, default=5)
     ap.add_argument("--grad-n", type=int, default=4096, help="vertices of the differentiable workload (<= 4096)")
-    ap.add_argument("--no-direct", dest="direct_sec", action="store_false", help="skip the direct-solver section")
+    ap.add_argument("--no-direct", dest="direct_sec", action="store_false",
+                    help="skip the direct-solver and per-vertex omega sections")
     ap.add_argument("--direct", action="store_true", help="only the direct-solver section, then exit")
     ap.add_argument("--direct-n", type=int, default=0, help="Delaunay graph size of --direct (0 = delaunay20k)")
     args = ap.parse_args()
@@ -784,6 +829,8 @@ def main():
             sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
             fp32_peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
             print(json.dumps(run_direct(args, local_rank, peaks, fp32_peak)), flush=True)
+            if not args.direct_n:
+                print(json.dumps(run_vertex_omega(args, local_rank)), flush=True)
         return
     if args.table1:
         import torch
