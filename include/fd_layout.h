@@ -233,7 +233,8 @@ fd_status fd_energy_length_grad(fd_layout* h, const float* X, float* grad_len, d
  * dL/dl_e through the shortest paths.
  *   X_k, X_k1   float32 [n][dim]: the iteration's input and output layouts
  *   accepted    the outcome of line 6 (fd_sor_step's *accepted)
- *   omega       the omega the iteration used
+ *   omega       the omega the iteration used (times the per-vertex factors of
+ *               fd_set_vertex_omega, if set, as in the forward iteration)
  *   Xbar_k1     float32 [n][dim]: dL/dX_k1;  Xbar_k: float32 [n][dim], written
  *   cg_steps    CG steps of the adjoint solve (host; may be NULL)
  * Arrays host or device.  Errors: FD_ERR_ARG, FD_ERR_NONFINITE, FD_ERR_CUDA,
@@ -415,9 +416,9 @@ void fd_batch_destroy(fd_batch* b);
  * configuration).  X (float32 [N][dim], host or device; graph g's rows are
  * graph_ptr[g] ..) holds every X^0 on entry and the final layouts on return.
  *   opt        strategy FD_OMEGA_FIXED or FD_OMEGA_PROB (the same omega
- *              sequence for every graph); FD_OMEGA_ENUM returns
- *              FD_ERR_UNIMPLEMENTED.  tol, stop, max_iter, cg_tol, cg_max
- *              apply to every graph.
+ *              sequence for every graph); FD_OMEGA_ENUM and FD_SOLVER_DIRECT
+ *              return FD_ERR_UNIMPLEMENTED (the batched kernel solves by CG).
+ *              tol, stop, max_iter, cg_tol, cg_max apply to every graph.
  *   omega      NULL (every graph uses opt->omega) or double[num_graphs]
  *              (host or device): graph g's fixed omega (FD_OMEGA_FIXED)
  *   iters      NULL or host int32[num_graphs]: iterations per graph

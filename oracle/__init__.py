@@ -543,14 +543,15 @@ def stress_length_grad(X, row_ptr, col_idx, edge_len) -> np.ndarray:
 # Unrolled differentiation of Algorithm 2 (the acceptance of line 6 held fixed)
 # --------------------------------------------------------------------------
 
-def unrolled_run(D, X0, K: int, omega: float):
+def unrolled_run(D, X0, K: int, omega: float, omega_vertex=None):
     """K iterations of Algorithm 2 with exact solves; returns the layouts
-    X^0..X^K, the H-step outputs Z^1..Z^K and the acceptance of each step."""
+    X^0..X^K, the H-step outputs Z^1..Z^K and the acceptance of each step.
+    omega_vertex: per-vertex factors m (omega_i = omega m_i, Sec. 6)."""
     solver = PinnedSolver(D)
     Xs, Zs, acc = [_f64(X0).copy()], [], []
     for _ in range(K):
         X = Xs[-1]
-        Xn, fn, a, om, fZ = sor_step(X, D, omega, OMEGA_FIXED, solver)
+        Xn, fn, a, om, fZ = sor_step(X, D, omega, OMEGA_FIXED, solver, omega_vertex)
         Z = solver.solve(rhs(X, D))
         Xs.append(Xn)
         Zs.append(Z)
@@ -558,23 +559,24 @@ def unrolled_run(D, X0, K: int, omega: float):
     return Xs, Zs, acc
 
 
-def unrolled_adjoint(D, Xs, Zs, acc, omega: float, Xbar_K):
+def unrolled_adjoint(D, Xs, Zs, acc, omega: float, Xbar_K, omega_vertex=None):
     """Backward pass of unrolled_run: returns dL/dX^0 and the pair
     sensitivities dL/dd_ij (symmetric n x n) summed over the steps.
 
     Per step (Eq. (2-5), pinning, Eq. (10)): Zb = (1+omega) Xb' or Xb', Xb = -omega Xb'
-    or 0; Yb = Zb - e_0 (1^T Zb); L^W lam = Yb; Xb += J_b(X)^T lam with
-    b_i = sum_j (1/d_ij) (x_i - x_j)/r_ij; dL/dd_ij += -(dlam . u)/d^2 + 2 (dlam . dY)/d^3.
-    Plain loops over pairs."""
+    or 0 (omega_i = omega m_i per vertex with factors m); Yb = Zb - e_0 (1^T Zb);
+    L^W lam = Yb; Xb += J_b(X)^T lam with b_i = sum_j (1/d_ij) (x_i - x_j)/r_ij;
+    dL/dd_ij += -(dlam . u)/d^2 + 2 (dlam . dY)/d^3.  Plain loops over pairs."""
     D = _f64(D)
     n = D.shape[0]
     solver = PinnedSolver(D)
     Xb1 = _f64(Xbar_K).copy()
     Gd = np.zeros((n, n))
+    om = omega if omega_vertex is None else omega * np.asarray(omega_vertex, dtype=np.float64).reshape(-1, 1)
     for k in reversed(range(len(acc))):
         X, Y = Xs[k], Zs[k]
         if acc[k]:
-            Zb, Xb = (1.0 + omega) * Xb1, -omega * Xb1
+            Zb, Xb = (1.0 + om) * Xb1, -om * Xb1
         else:
             Zb, Xb = Xb1.copy(), np.zeros_like(Xb1)
         Yb = Zb.copy()

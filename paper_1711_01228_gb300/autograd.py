@@ -74,9 +74,11 @@ def stress_lengths(X: torch.Tensor, edge_len: torch.Tensor, row_ptr, col_idx) ->
 
 class _Unrolled(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, X0, edge_len, row_ptr, col_idx, K, omega, every, cg_tol, cg_max):
+    def forward(ctx, X0, edge_len, row_ptr, col_idx, K, omega, every, cg_tol, cg_max, omega_vertex):
         lens = edge_len.detach().contiguous()
         L = api.Layout(row_ptr, col_idx, dim=int(X0.shape[1]), edge_len=lens, stream=None)
+        if omega_vertex is not None:
+            L.set_vertex_omega(omega_vertex)
         opts = dict(omega=float(omega), strategy=api.OMEGA_FIXED, cg_tol=cg_tol, cg_max=cg_max)
         X = X0.detach().contiguous().clone()
         ckpt = {0: X.clone()}
@@ -108,11 +110,11 @@ class _Unrolled(torch.autograd.Function):
         L.adjoint_length_grad(out=g_full)
         L.close()
         ctx.L = None
-        return xbar, (0.5 * g_full).to(ctx.lens_dtype), None, None, None, None, None, None, None
+        return xbar, (0.5 * g_full).to(ctx.lens_dtype), None, None, None, None, None, None, None, None
 
 
 def unrolled_layout(X0: torch.Tensor, edge_len: torch.Tensor, row_ptr, col_idx, K: int = 32, omega: float = 0.5,
-                    every: int = 8, cg_tol: float = 1e-6, cg_max: int = 500) -> torch.Tensor:
+                    every: int = 8, cg_tol: float = 1e-6, cg_max: int = 500, omega_vertex=None) -> torch.Tensor:
     """X^K after K iterations of Algorithm 2 (fixed omega) from X0 on a
     weighted graph; differentiable in X0 and in the edge lengths.  The
     backward pass recomputes the layouts from checkpoints taken every
@@ -120,6 +122,7 @@ def unrolled_layout(X0: torch.Tensor, edge_len: torch.Tensor, row_ptr, col_idx, 
     (``fd_sor_step_adjoint``; the acceptance of line 6 held at its forward
     outcome), then pushes the summed pair sensitivities through the shortest
     paths (``fd_adjoint_length_grad``).  As in ``stress_lengths``, each CSR
-    entry of an edge receives half of the edge's derivative."""
+    entry of an edge receives half of the edge's derivative.  ``omega_vertex``:
+    per-vertex factors m (omega_i = omega m_i, Sec. 6; not differentiated)."""
     return _Unrolled.apply(X0, edge_len, row_ptr, col_idx, int(K), float(omega), int(every), float(cg_tol),
-                           int(cg_max))
+                           int(cg_max), omega_vertex)

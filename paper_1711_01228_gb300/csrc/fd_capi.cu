@@ -46,7 +46,7 @@ cudaError_t launch_rowsum_multi(const BGraph* graphs, const int2* items, int nit
                                 float* inv_s, int grid, cudaStream_t st);
 cudaError_t launch_distance_graph(const unsigned char* Dg, int n, int nb, double* out, cudaStream_t st);
 cudaError_t launch_adjoint_prep(int n, int dim, const float* Xk, const float* Xk1, const float* Xb1, int accepted,
-                                float omega, float* Y, float* Yb, float* Xb, cudaStream_t st);
+                                float omega, const float* oms, float* Y, float* Yb, float* Xb, cudaStream_t st);
 cudaError_t launch_pair_adjoint(int code, int n, int nb, int dim, const int2* tile_ik, int ntiles, const void* D,
                                 const float* X, const float* lam, const float* Y, float* Xb, float* Db, int sm_count,
                                 cudaStream_t st);
@@ -961,7 +961,8 @@ fd_status fd_sor_step_adjoint(fd_layout* h, const float* X_k, const float* X_k1,
   }
   const bool dev_out = is_device_ptr(Xbar_k);
   float* xb = dev_out ? Xbar_k : Xb;
-  if (launch_adjoint_prep(h->n, h->dim, xk, xk1, xb1, accepted ? 1 : 0, (float)omega, Y, Yb, xb, st) != cudaSuccess) {
+  if (launch_adjoint_prep(h->n, h->dim, xk, xk1, xb1, accepted ? 1 : 0, (float)omega, h->d_om_scale, Y, Yb, xb, st) !=
+      cudaSuccess) {
     cudaGetLastError();
     return fail(h, FD_ERR_CUDA);
   }
@@ -1479,8 +1480,9 @@ fd_status batch_run_dev(fd_batch* b, const float* x_in, float* x_out, const fd_o
   if (!opt || !(opt->omega >= 0.0) || !std::isfinite(opt->omega) || max_iter < 1 || opt->cg_max < 0 ||
       !(opt->tol >= 0.0) || !(opt->cg_tol >= 0.0) || (opt->stop != FD_STOP_REL_DISP && opt->stop != FD_STOP_REL_STRESS))
     return FD_ERR_ARG;
-  if (opt->strategy == FD_OMEGA_ENUM) return FD_ERR_UNIMPLEMENTED;
+  if (opt->strategy == FD_OMEGA_ENUM || opt->solver == FD_SOLVER_DIRECT) return FD_ERR_UNIMPLEMENTED;
   if (opt->strategy != FD_OMEGA_FIXED && opt->strategy != FD_OMEGA_PROB) return FD_ERR_ARG;
+  if (opt->solver != FD_SOLVER_CG) return FD_ERR_ARG;
   cudaStream_t st = b->stream;
   std::vector<double> om((size_t)b->G, opt->omega);
   if (omega && opt->strategy == FD_OMEGA_FIXED) {

@@ -176,18 +176,22 @@ __global__ void combine_directions_kernel(int nnz, const int* __restrict__ rev, 
 // solve, and the part of Xb that does not pass through the solve.
 __global__ void __launch_bounds__(1024) adjoint_prep_kernel(int n, int dim, const float* __restrict__ Xk,
                                                             const float* __restrict__ Xk1, const float* __restrict__ Xb1,
-                                                            int accepted, float omega, float* Y, float* Yb, float* Xb) {
+                                                            int accepted, float omega,
+                                                            const float* __restrict__ oms, float* Y, float* Yb,
+                                                            float* Xb) {
   __shared__ double part[32][3];
   double s[3] = {0.0, 0.0, 0.0};
-  const float zs = accepted ? 1.f + omega : 1.f;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    // omega_i = omega m_i with per-vertex factors (Sec. 6), as in the forward step
+    const float om = oms ? omega * oms[i] : omega;
+    const float zs = accepted ? 1.f + om : 1.f;
     for (int d = 0; d < dim; ++d) {
       const size_t k = (size_t)i * dim + d;
       const float xb1 = Xb1[k];
-      Y[k] = accepted ? (Xk1[k] + omega * Xk[k]) / (1.f + omega) : Xk1[k];
+      Y[k] = accepted ? (Xk1[k] + om * Xk[k]) / (1.f + om) : Xk1[k];
       const float zb = zs * xb1;
       Yb[k] = zb;
-      Xb[k] = accepted ? -omega * xb1 : 0.f;
+      Xb[k] = accepted ? -om * xb1 : 0.f;
       s[d] += (double)zb;
     }
   }
@@ -270,8 +274,8 @@ __global__ void __launch_bounds__(TILE) pair_adjoint_kernel(int n, int nb, int d
 }
 
 cudaError_t launch_adjoint_prep(int n, int dim, const float* Xk, const float* Xk1, const float* Xb1, int accepted,
-                                float omega, float* Y, float* Yb, float* Xb, cudaStream_t st) {
-  adjoint_prep_kernel<<<1, 1024, 0, st>>>(n, dim, Xk, Xk1, Xb1, accepted, omega, Y, Yb, Xb);
+                                float omega, const float* oms, float* Y, float* Yb, float* Xb, cudaStream_t st) {
+  adjoint_prep_kernel<<<1, 1024, 0, st>>>(n, dim, Xk, Xk1, Xb1, accepted, omega, oms, Y, Yb, Xb);
   return cudaGetLastError();
 }
 

@@ -190,6 +190,9 @@ def test_batch_errors():
         with pytest.raises(api.FdError) as e:
             B.run(X.copy(), strategy=api.OMEGA_ENUM)
         assert e.value.status == 10
+        with pytest.raises(api.FdError) as e:
+            B.run(X.copy(), solver=api.SOLVER_DIRECT)
+        assert e.value.status == 10
         Xn = X.copy()
         Xn[3, 0] = np.nan  # graph 0 only
         r = B.run(Xn, check=False, omega=0.5)

@@ -139,8 +139,8 @@ def test_length_gradient_errors():
         assert e.value.status == 10
 
 
-@pytest.mark.parametrize("omega", [0.0, 0.5])
-def test_unrolled_adjoint_matches_oracle(omega):
+@pytest.mark.parametrize("omega,vertex", [(0.0, False), (0.5, False), (0.5, True)])
+def test_unrolled_adjoint_matches_oracle(omega, vertex):
     """Gradient of a loss on X^K (K = 4 iterations of Algorithm 2, checkpoints
     every 2) in X^0 and in the edge lengths, against the FP64 oracle's adjoint
     (itself pinned by finite differences), with the same acceptance decisions."""
@@ -156,8 +156,9 @@ def test_unrolled_adjoint_matches_oracle(omega):
     targets = rng.uniform(0.5, 4.0, size=len(pairs))
     Xt = torch.from_numpy(X0).cuda().requires_grad_(True)
     lt = torch.from_numpy(w).cuda().requires_grad_(True)
+    m = np.random.default_rng(9).uniform(0.0, 2.0, n).astype(np.float32) if vertex else None
     XK = autograd.unrolled_layout(Xt, lt, torch.from_numpy(rp), torch.from_numpy(ci), K=K, omega=omega, every=2,
-                                  cg_tol=1e-7, cg_max=1000)
+                                  cg_tol=1e-7, cg_max=1000, omega_vertex=m)
     pi, pj = torch.from_numpy(pairs[:, 0]).cuda(), torch.from_numpy(pairs[:, 1]).cuda()
     tt = torch.from_numpy(targets).cuda()
     loss = ((XK[pi] - XK[pj]).double().norm(dim=1) - tt).pow(2).sum()
@@ -165,12 +166,15 @@ def test_unrolled_adjoint_matches_oracle(omega):
     # the GPU's acceptance decisions, from a plain re-run
     accs = []
     with api.Layout(rp, ci, dim=3, edge_len=w) as L:
+        if vertex:
+            L.set_vertex_omega(m)
         X = X0.copy()
         for k in range(K):
             _, acc, _ = L.sor_step(X, k=k, omega=omega, cg_tol=1e-7, cg_max=1000)
             accs.append(bool(acc))
     D = oracle.apsp(rp, ci, edge_len=w.astype(np.float64))[1]
-    Xs, Zs, acc_ref = oracle.unrolled_run(D, X0.astype(np.float64), K, omega)
+    m64 = m.astype(np.float64) if vertex else None
+    Xs, Zs, acc_ref = oracle.unrolled_run(D, X0.astype(np.float64), K, omega, omega_vertex=m64)
     assert accs == acc_ref
     XKr = Xs[-1]
     gK = np.zeros_like(XKr)
@@ -179,7 +183,7 @@ def test_unrolled_adjoint_matches_oracle(omega):
         r = np.linalg.norm(dx)
         gK[i] += 2 * (r - t) * dx / r
         gK[j] -= 2 * (r - t) * dx / r
-    gX0, Gd = oracle.unrolled_adjoint(D, Xs, Zs, acc_ref, omega, gK)
+    gX0, Gd = oracle.unrolled_adjoint(D, Xs, Zs, acc_ref, omega, gK, omega_vertex=m64)
     gw = 0.5 * oracle.pair_to_edge_grad(rp, ci, w.astype(np.float64), Gd)
     g_x = Xt.grad.cpu().numpy().astype(np.float64)
     g_l = lt.grad.cpu().numpy().astype(np.float64)

@@ -85,9 +85,10 @@ def _loss_and_grad(XK, pairs, targets):
     return L, g
 
 
-@pytest.mark.parametrize("omega", [0.0, 0.5])
-def test_unrolled_adjoint_matches_finite_differences(omega):
-    # K = 3 iterations of Algorithm 2 on a weighted 16-vertex graph; loss on sampled pair distances
+@pytest.mark.parametrize("omega,vertex", [(0.0, False), (0.5, False), (0.5, True)])
+def test_unrolled_adjoint_matches_finite_differences(omega, vertex):
+    # K = 3 iterations of Algorithm 2 on a weighted 16-vertex graph; loss on sampled pair distances;
+    # with vertex=True each vertex has its own factor omega_i = omega m_i (Sec. 6)
     rp, ci = synth.grid(4, 4)
     rng = np.random.default_rng(3)
     w = _sym_lengths(rp, ci, rng)
@@ -95,15 +96,16 @@ def test_unrolled_adjoint_matches_finite_differences(omega):
     X0 = rng.random((n, 2)) * 2.0
     pairs = [tuple(rng.choice(n, 2, replace=False)) for _ in range(12)]
     targets = rng.uniform(0.5, 3.0, size=len(pairs))
+    m = np.random.default_rng(9).uniform(0.0, 2.0, n) if vertex else None
 
     def run(X0_, w_):
         D = oracle.apsp(rp, ci, edge_len=w_)[1]
-        Xs, Zs, acc = oracle.unrolled_run(D, X0_, K, omega)
+        Xs, Zs, acc = oracle.unrolled_run(D, X0_, K, omega, omega_vertex=m)
         return Xs, Zs, acc, D
 
     Xs, Zs, acc, D = run(X0, w)
     L0, gK = _loss_and_grad(Xs[-1], pairs, targets)
-    gX0, Gd = oracle.unrolled_adjoint(D, Xs, Zs, acc, omega, gK)
+    gX0, Gd = oracle.unrolled_adjoint(D, Xs, Zs, acc, omega, gK, omega_vertex=m)
     gw = oracle.pair_to_edge_grad(rp, ci, w, Gd)
     h = 1e-6
     checked = 0
