@@ -241,15 +241,27 @@ __global__ void __launch_bounds__(PIV_THREADS) sw_pivot_kernel(float* __restrict
     for (int u = 0; u < 4; ++u) rj[u] = rowb[b][c0 + u];
 #pragma unroll
     for (int q = 0; q < 8; ++q) ci[q] = colb[b][r0 + q] * inv;
+    // a_ij - a_ip a_pj / piv for every entry; row p and column p are then
+    // overwritten by their owners (warp-uniform for the row, one lane per
+    // warp for the column)
 #pragma unroll
     for (int q = 0; q < 8; ++q)
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int i = r0 + q, j = c0 + u;
-        if (i == p) a[q][u] = (j == p) ? inv : a[q][u] * inv;  // row p scaled, pivot inverted
-        else if (j == p) a[q][u] = -ci[q];                      // column p: -a_ip / piv
-        else a[q][u] = fmaf(-ci[q], rj[u], a[q][u]);            // a_ij - a_ip a_pj / piv
-      }
+      for (int u = 0; u < 4; ++u) a[q][u] = fmaf(-ci[q], rj[u], a[q][u]);
+    if (p >= r0 && p < r0 + 8) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (r0 + q == p)
+#pragma unroll
+          for (int u = 0; u < 4; ++u) a[q][u] = rj[u] * inv;  // row p scaled
+    }
+    if (p >= c0 && p < c0 + 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (c0 + u == p)
+#pragma unroll
+          for (int q = 0; q < 8; ++q) a[q][u] = (r0 + q == p) ? inv : -ci[q];  // column p: -a_ip / piv; pivot 1/piv
+    }
   }
   if (bad) atomicExch(err, 1);
 #pragma unroll
