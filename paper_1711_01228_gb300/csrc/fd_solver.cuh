@@ -1001,11 +1001,12 @@ __device__ __forceinline__ void vertex_phase(const KParams& p, float2* red64, F&
 // --------------------------------------------------------------------------
 // Direct solver: z = A'^-1 r with the dense inverse of the shifted L^W
 // (L^W + sigma/n 1 1^T, inverted once before the launch).  The inverse is
-// streamed once from HBM with 16-byte loads; a CTA takes 8 rows at a time
-// (2 per warp, each lane 4 consecutive columns), r goes through shared memory
-// in chunks of DCH vertices, one coordinate per array (so that a lane's 4
-// vertices are one 16-byte read), double-buffered through registers.  Every
-// row sum has one fixed order: the result does not depend on the grid.
+// streamed once from HBM with 16-byte loads; a CTA takes 8 rows and half of
+// the columns at a time (2 rows per warp, each lane 4 consecutive columns),
+// r goes through shared memory in chunks of DCH vertices, one coordinate per
+// array (so that a lane's 4 vertices are one 16-byte read), double-buffered
+// through registers.  Every partial sum has one fixed order and each row gets
+// two: the result does not depend on the grid.  z must be zero on entry.
 // --------------------------------------------------------------------------
 constexpr int DCH = 1024;  // vertices per staged chunk of r
 
@@ -1044,19 +1045,27 @@ __device__ __noinline__ void dense_apply(const KParams& p, float* buf, const flo
       }
     }
   };
-  for (int gi = blockIdx.x; gi < np / 8; gi += gridDim.x) {
+  // Work items: (row group, column half).  Halving the columns doubles the
+  // items, so that the last round over the grid is nearly full; each row
+  // receives its two partial sums by atomic adds into z, which is zero on
+  // entry (two adds into zero give the same result in either order).
+  const int half = (nch + 1) / 2;
+  for (int it = blockIdx.x; it < np / 4; it += gridDim.x) {
+    const int gi = it >> 1, h = it & 1;
+    const int ch0 = h * half, ch1 = min(nch, ch0 + half);
+    if (ch0 >= ch1) continue;  // one chunk only: the second half is empty (uniform over the CTA)
     const int i0 = gi * 8 + warp * 2;
     const float* a0 = p.ainv + (size_t)i0 * np;
     const float* a1 = a0 + np;
     float s0[DIM], s1[DIM];
 #pragma unroll
     for (int d = 0; d < DIM; ++d) s0[d] = s1[d] = 0.f;
-    fetch(0);
+    fetch(ch0);
     put(buf);
     __syncthreads();
-    for (int ch = 0; ch < nch; ++ch) {
-      if (ch + 1 < nch) fetch(ch + 1);
-      const float* rb = buf + (ch & 1) * DIM * DCH;
+    for (int ch = ch0; ch < ch1; ++ch) {
+      if (ch + 1 < ch1) fetch(ch + 1);
+      const float* rb = buf + ((ch - ch0) & 1) * DIM * DCH;
       const int c0 = ch * DCH, len = min(DCH, np - c0);
 #pragma unroll 4
       for (int c = lane * 4; c < len; c += 128) {
@@ -1069,7 +1078,7 @@ __device__ __noinline__ void dense_apply(const KParams& p, float* buf, const flo
           s1[d] = fmaf(u1.x, v.x, fmaf(u1.y, v.y, fmaf(u1.z, v.z, fmaf(u1.w, v.w, s1[d]))));
         }
       }
-      if (ch + 1 < nch) put(buf + ((ch + 1) & 1) * DIM * DCH);
+      if (ch + 1 < ch1) put(buf + ((ch + 1 - ch0) & 1) * DIM * DCH);
       __syncthreads();
     }
 #pragma unroll
@@ -1086,8 +1095,8 @@ __device__ __noinline__ void dense_apply(const KParams& p, float* buf, const flo
         v0.c[d] = s0[d];
         v1.c[d] = s1[d];
       }
-      stv<DIM>(z, i0, v0);
-      stv<DIM>(z, i0 + 1, v1);
+      atomic_addv<DIM>(z, i0, v0);
+      atomic_addv<DIM>(z, i0 + 1, v1);
     }
   }
 }
@@ -1408,9 +1417,11 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
       // is the minimum-norm solution of L^W delta = r.
       float* dbuf = reinterpret_cast<float*>(smem + L::stage_base(CODE == CODE_U8 ? p.lut_rows * LUT_ROW : 0));
       while (!rs->all_conv) {
-        dense_apply<DIM>(p, dbuf, p.R, p.U);
+        // delta goes to P (unused by this solver; zeroed at the start of the H
+        // step and by every refinement's vertex phase)
+        dense_apply<DIM>(p, dbuf, p.R, p.P);
         FD_SYNC(10);
-        if (!pair_pass<DIM, PM_MATVEC, 1, CODE>(p, smem, ps, direct_src(p.U), acc2)) return;
+        if (!pair_pass<DIM, PM_MATVEC, 1, CODE>(p, smem, ps, direct_src(p.P), acc2)) return;
         if (tid == 0) {
           rs->passes_mv += 1.0;
           ++rs->it;
@@ -1418,7 +1429,7 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
         FD_SYNC(7);
         vertex_phase<DIM>(p, red64, [&](int i, df(&v)[DIM]) {
           const float s = __ldcg(p.s + i);
-          const Vec<DIM> u = ldv<DIM>(p.U, i);
+          const Vec<DIM> u = take_acc<DIM>(p.P, i);
           const Vec<DIM> a = take_acc<DIM>(acc2, i);
           Vec<DIM> x = ldv<DIM>(p.Zw, i), r = ldv<DIM>(p.R, i);
 #pragma unroll
