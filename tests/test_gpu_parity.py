@@ -1,10 +1,13 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
-Tolerances (derived in DESIGN.md, "Precision and tolerances"):
+Tolerances, from the arithmetic of the kernels:
   distances       bit-exact (integer hop counts); 1e-5 relative for float lengths
+                  (FP32 sums along a path against FP64 Dijkstra)
   stress          1e-5 relative (FP32 pair terms, FP32 sums of <= 128 terms, FP64 above)
-  forces          1e-5 relative, Frobenius norm over all vertices (spec bound)
-  one SOR step    1e-4 relative on the layout (CG stops at relative residual 1e-6)
+  forces          1e-5 relative, Frobenius norm over all vertices (per-element
+                  error about 32 eps32 sum |terms|, ~1e-6 at random layouts)
+  one SOR step    1e-4 relative on the layout (CG stops at relative residual 1e-6;
+                  the layout error is at most kappa_eff times that, kappa_eff <= 100)
   converged run   1e-4 relative on final stress, iterations within 2 % (at least 1)
 """
 import math
