@@ -468,6 +468,14 @@ def run_differentiable(args, local_rank):
 
     ms_unrolled = timed(unrolled_step, reps=2)
 
+    def unrolled_step_direct():
+        wt.grad = None
+        XK = autograd.unrolled_layout(X0, wt, rpt, cit, K=K, omega=0.5, every=every, solver=api.SOLVER_DIRECT)
+        loss = ((XK[pi] - XK[pj]).norm(dim=1) - tgt).pow(2).sum()
+        loss.backward()
+
+    ms_unrolled_direct = timed(unrolled_step_direct, reps=2)
+
     def unrolled_forward():
         with torch.no_grad():
             autograd.unrolled_layout(X0, wt.detach(), rpt, cit, K=K, omega=0.5, every=every)
@@ -480,6 +488,7 @@ def run_differentiable(args, local_rank):
             "weighted_apsp_ms": create_ms, "autograd_step_ms": ms_step,
             "unrolled": {"iterations": K, "checkpoint_every": every, "omega_c": 1.5,
                          "forward_ms": ms_unrolled_fwd, "forward_backward_ms": ms_unrolled,
+                         "forward_backward_ms_direct_solver": ms_unrolled_direct,
                          "loss": "squared error of 4096 sampled pair distances of X^K against a seeded "
                                  "random layout's"},
             "stress_pairs_per_s": pairs / (ms_energy / 1e3), "position_grad_pairs_per_s": pairs / (ms_forces / 1e3),

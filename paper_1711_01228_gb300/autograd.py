@@ -74,12 +74,14 @@ def stress_lengths(X: torch.Tensor, edge_len: torch.Tensor, row_ptr, col_idx) ->
 
 class _Unrolled(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, X0, edge_len, row_ptr, col_idx, K, omega, every, cg_tol, cg_max, omega_vertex):
+    def forward(ctx, X0, edge_len, row_ptr, col_idx, K, omega, every, cg_tol, cg_max, omega_vertex, solver):
         lens = edge_len.detach().contiguous()
         L = api.Layout(row_ptr, col_idx, dim=int(X0.shape[1]), edge_len=lens, stream=None)
         if omega_vertex is not None:
             L.set_vertex_omega(omega_vertex)
-        opts = dict(omega=float(omega), strategy=api.OMEGA_FIXED, cg_tol=cg_tol, cg_max=cg_max)
+        if solver == api.SOLVER_DIRECT:
+            L.factor()  # one factorisation serves every forward, recomputed and adjoint solve
+        opts = dict(omega=float(omega), strategy=api.OMEGA_FIXED, cg_tol=cg_tol, cg_max=cg_max, solver=int(solver))
         X = X0.detach().contiguous().clone()
         ckpt = {0: X.clone()}
         for k in range(K):
@@ -105,16 +107,17 @@ class _Unrolled(torch.autograd.Function):
                 accs.append(acc)
             for k in reversed(range(len(accs))):
                 xbar, _ = L.sor_step_adjoint(traj[k], traj[k + 1], accs[k], opts["omega"], xbar,
-                                             cg_tol=opts["cg_tol"], cg_max=opts["cg_max"])
+                                             cg_tol=opts["cg_tol"], cg_max=opts["cg_max"], solver=opts["solver"])
         g_full = torch.empty(L._nnz, dtype=torch.float32, device=gXK.device)
         L.adjoint_length_grad(out=g_full)
         L.close()
         ctx.L = None
-        return xbar, (0.5 * g_full).to(ctx.lens_dtype), None, None, None, None, None, None, None, None
+        return xbar, (0.5 * g_full).to(ctx.lens_dtype), None, None, None, None, None, None, None, None, None
 
 
 def unrolled_layout(X0: torch.Tensor, edge_len: torch.Tensor, row_ptr, col_idx, K: int = 32, omega: float = 0.5,
-                    every: int = 8, cg_tol: float = 1e-6, cg_max: int = 500, omega_vertex=None) -> torch.Tensor:
+                    every: int = 8, cg_tol: float = 1e-6, cg_max: int = 500, omega_vertex=None,
+                    solver: int = api.SOLVER_CG) -> torch.Tensor:
     """X^K after K iterations of Algorithm 2 (fixed omega) from X0 on a
     weighted graph; differentiable in X0 and in the edge lengths.  The
     backward pass recomputes the layouts from checkpoints taken every
@@ -123,6 +126,8 @@ def unrolled_layout(X0: torch.Tensor, edge_len: torch.Tensor, row_ptr, col_idx, 
     outcome), then pushes the summed pair sensitivities through the shortest
     paths (``fd_adjoint_length_grad``).  As in ``stress_lengths``, each CSR
     entry of an edge receives half of the edge's derivative.  ``omega_vertex``:
-    per-vertex factors m (omega_i = omega m_i, Sec. 6; not differentiated)."""
+    per-vertex factors m (omega_i = omega m_i, Sec. 6; not differentiated).
+    ``solver=api.SOLVER_DIRECT`` factors L^W once (``fd_factor``) and uses the
+    inverse in every solve, the adjoint ones included: they all share L^W."""
     return _Unrolled.apply(X0, edge_len, row_ptr, col_idx, int(K), float(omega), int(every), float(cg_tol),
-                           int(cg_max), omega_vertex)
+                           int(cg_max), omega_vertex, int(solver))

@@ -139,8 +139,8 @@ def test_length_gradient_errors():
         assert e.value.status == 10
 
 
-@pytest.mark.parametrize("omega,vertex", [(0.0, False), (0.5, False), (0.5, True)])
-def test_unrolled_adjoint_matches_oracle(omega, vertex):
+@pytest.mark.parametrize("omega,vertex,solver", [(0.0, False, 0), (0.5, False, 0), (0.5, True, 0), (0.5, False, 1)])
+def test_unrolled_adjoint_matches_oracle(omega, vertex, solver):
     """Gradient of a loss on X^K (K = 4 iterations of Algorithm 2, checkpoints
     every 2) in X^0 and in the edge lengths, against the FP64 oracle's adjoint
     (itself pinned by finite differences), with the same acceptance decisions."""
@@ -158,7 +158,7 @@ def test_unrolled_adjoint_matches_oracle(omega, vertex):
     lt = torch.from_numpy(w).cuda().requires_grad_(True)
     m = np.random.default_rng(9).uniform(0.0, 2.0, n).astype(np.float32) if vertex else None
     XK = autograd.unrolled_layout(Xt, lt, torch.from_numpy(rp), torch.from_numpy(ci), K=K, omega=omega, every=2,
-                                  cg_tol=1e-7, cg_max=1000, omega_vertex=m)
+                                  cg_tol=1e-7, cg_max=1000, omega_vertex=m, solver=solver)
     pi, pj = torch.from_numpy(pairs[:, 0]).cuda(), torch.from_numpy(pairs[:, 1]).cuda()
     tt = torch.from_numpy(targets).cuda()
     loss = ((XK[pi] - XK[pj]).double().norm(dim=1) - tt).pow(2).sum()
