@@ -698,6 +698,30 @@ TABLE1_AVG = {"iters": {"0": 100.0, "0.5": 67.5, "1.0": 50.4, "1.5": 44.9, "auto
               "time": {"0": 100.0, "0.5": 100.1, "1.0": 74.8, "1.5": 66.7, "auto": 70.2, "enum": 140.9}}
 
 
+def best_omega_stats(traces):
+    """The two observations of Sec. 5.2.2 on the enumerated best omega of
+    every iteration: the share of iterations whose best omega lies in
+    [0.5, 2], and the zigzag: among the moves of the best omega, the share
+    of turning points (the move reverses the previous one; an independent
+    sequence gives 2/3), and the lag-1 autocorrelation of the moves
+    (negative for a zigzag; -1/2 for an independent sequence's increments)."""
+    inside, turns, moves, ac = [], 0, 0, []
+    for om in traces:
+        if len(om) == 0:
+            continue
+        inside.append(float(np.mean((om >= 0.5) & (om <= 2.0))))
+        d = np.diff(om)
+        d = d[d != 0.0]
+        if len(d) >= 2:
+            turns += int(np.sum(np.sign(d[1:]) != np.sign(d[:-1])))
+            moves += len(d) - 1
+            if np.std(d[1:]) > 0 and np.std(d[:-1]) > 0:
+                ac.append(float(np.corrcoef(d[:-1], d[1:])[0, 1]))
+    return {"in_0.5_2": float(np.mean(inside)) if inside else float("nan"),
+            "turning_points": turns / moves if moves else float("nan"),
+            "lag1_autocorr": float(np.mean(ac)) if ac else float("nan")}
+
+
 def run_table1(args, local_rank):
     """Iterations and device time of every omega strategy of Sec. 5.2 on
     synthetic stand-ins at the sizes of Table 1 (band-46 ... net-2305), with
@@ -723,21 +747,28 @@ def run_table1(args, local_rank):
             rp, ci = synth.barabasi_albert(n, 3, seed=1)
         n = len(rp) - 1
         res = {}
+        traces = []
         with api.Layout(rp, ci, dim=2, disconnected_policy=1) as L:
             for key, kw in strategies:
                 its, ms = [], []
                 for seed in range(args.table1_seeds):
                     X = synth.initial_layout(n, 2, seed)
-                    r = L.run(X, tol=tol, max_iter=5000, stop=api.STOP_REL_STRESS, seed=seed, **kw)
+                    r = L.run(X, tol=tol, max_iter=5000, stop=api.STOP_REL_STRESS, seed=seed, trace=(key == "enum"),
+                              **kw)
                     its.append(r.iterations)
                     ms.append(r.stats["kernel_ms"])
+                    if key == "enum":
+                        traces.append(np.asarray(r.omega, dtype=np.float64))
                 res[key] = {"iterations": float(np.mean(its)), "ms": float(np.mean(ms))}
-        out[name] = {"n": n, "tol": tol, "strategies": res}
+        out[name] = {"n": n, "tol": tol, "strategies": res, "enum_best_omega": best_omega_stats(traces)}
     ratio = {k: float(np.mean([100.0 * v["strategies"][k]["iterations"] / v["strategies"]["0"]["iterations"]
                                for v in out.values()])) for k, _ in strategies}
     tratio = {k: float(np.mean([100.0 * v["strategies"][k]["ms"] / v["strategies"]["0"]["ms"]
                                 for v in out.values()])) for k, _ in strategies}
+    zig = {k: float(np.mean([v["enum_best_omega"][k] for v in out.values()]))
+           for k in ("in_0.5_2", "turning_points", "lag1_autocorr")}
     return {"table1_synthetic": out, "avg_iterations_pct_of_omega0": ratio, "avg_time_pct_of_omega0": tratio,
+            "enum_best_omega_mean_over_cases": zig,
             "paper_table1_average_row": TABLE1_AVG,
             "note": "omega is the paper's (0 = Algorithm 1); auto = probabilistic strategy, enum = enumerating; "
                     "stop when the relative stress decrease falls below the tolerance; "
