@@ -84,10 +84,12 @@ class _Unrolled(torch.autograd.Function):
         opts = dict(omega=float(omega), strategy=api.OMEGA_FIXED, cg_tol=cg_tol, cg_max=cg_max, solver=int(solver))
         X = X0.detach().contiguous().clone()
         ckpt = {0: X.clone()}
-        for k in range(K):
-            L.sor_step(X, k=k, **opts)
-            if (k + 1) % every == 0 and k + 1 < K:
-                ckpt[k + 1] = X.clone()
+        # one launch per checkpoint segment: tol = 0 runs exactly the
+        # segment's iterations (the backward pass recomputes them one by one)
+        for s0 in range(0, K, every):
+            L.run(X, max_iter=min(every, K - s0), tol=0.0, **opts)
+            if s0 + every < K:
+                ckpt[s0 + every] = X.clone()
         ctx.L, ctx.ckpt, ctx.K, ctx.every, ctx.opts = L, ckpt, K, every, opts
         ctx.lens_dtype = edge_len.dtype
         return X
