@@ -94,6 +94,9 @@ typedef struct {
   int32_t cg_max;    /* maximum conjugate-gradient (or refinement) steps per H step */
   double cg_tol;     /* the H solve stops when ||r_c|| <= cg_tol * ||b_c|| for every column c */
   int32_t solver;    /* fd_solver: how Eq. (2-5) is solved in every H step */
+  int32_t first_iter; /* fd_run: index k of its first iteration (FD_OMEGA_PROB draws the k-th
+                         output), so that a run checkpointed after k iterations (its X) resumes
+                         with the same omega sequence; 0 for a fresh run */
 } fd_options;
 
 /* Statistics of the last fd_run / fd_sor_step / fd_energy / fd_forces call. */
@@ -133,7 +136,7 @@ typedef struct {
 } fd_info;
 
 /* Fills *opt with the defaults: omega 0.5, FIXED, REL_DISP, seed 0,
- * tol 1e-4, max_iter 1000, cg_max 200, cg_tol 1e-6, FD_SOLVER_CG. */
+ * tol 1e-4, max_iter 1000, cg_max 200, cg_tol 1e-6, FD_SOLVER_CG, first_iter 0. */
 void fd_options_default(fd_options* opt);
 
 /* Builds a handle for graph G = (V, E) with n vertices laid out in dim

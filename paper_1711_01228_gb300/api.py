@@ -38,7 +38,8 @@ class FdError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("omega", ctypes.c_double), ("strategy", ctypes.c_int32), ("stop", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
-                ("cg_max", ctypes.c_int32), ("cg_tol", ctypes.c_double), ("solver", ctypes.c_int32)]
+                ("cg_max", ctypes.c_int32), ("cg_tol", ctypes.c_double), ("solver", ctypes.c_int32),
+                ("first_iter", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):

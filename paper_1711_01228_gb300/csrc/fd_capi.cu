@@ -598,6 +598,7 @@ void fd_options_default(fd_options* opt) {
   opt->cg_max = 200;
   opt->cg_tol = 1e-6;
   opt->solver = FD_SOLVER_CG;
+  opt->first_iter = 0;
 }
 
 const char* fd_status_string(fd_status s) {
@@ -1216,8 +1217,9 @@ fd_status fd_sor_step(fd_layout* h, float* X, const fd_options* opt, int32_t k, 
 fd_status fd_run(fd_layout* h, float* X, const fd_options* opt, int32_t* iters_out, double* f_out, double* trace_f) {
   if (!h) return FD_ERR_ARG;
   if (!opt) return fail(h, FD_ERR_ARG);
+  if (opt->first_iter < 0) return fail(h, FD_ERR_ARG);
   Ctrl c;
-  fd_status s = run_impl(h, X, opt, 0, opt->max_iter, &c);
+  fd_status s = run_impl(h, X, opt, opt->first_iter, opt->max_iter, &c);
   if (s != FD_OK) return fail(h, s);
   if (iters_out) *iters_out = c.iters;
   if (f_out) *f_out = c.f_final;
@@ -1481,6 +1483,7 @@ fd_status batch_run_dev(fd_batch* b, const float* x_in, float* x_out, const fd_o
       !(opt->tol >= 0.0) || !(opt->cg_tol >= 0.0) || (opt->stop != FD_STOP_REL_DISP && opt->stop != FD_STOP_REL_STRESS))
     return FD_ERR_ARG;
   if (opt->strategy == FD_OMEGA_ENUM || opt->solver == FD_SOLVER_DIRECT) return FD_ERR_UNIMPLEMENTED;
+  if (opt->first_iter < 0) return FD_ERR_ARG;
   if (opt->strategy != FD_OMEGA_FIXED && opt->strategy != FD_OMEGA_PROB) return FD_ERR_ARG;
   if (opt->solver != FD_SOLVER_CG) return FD_ERR_ARG;
   cudaStream_t st = b->stream;
@@ -1503,7 +1506,7 @@ fd_status batch_run_dev(fd_batch* b, const float* x_in, float* x_out, const fd_o
       b->omega_seq_cap = max_iter;
     }
     omk.resize(max_iter);
-    for (int k = 0; k < max_iter; ++k) omk[k] = omega_prob(opt->seed, (uint64_t)k);
+    for (int k = 0; k < max_iter; ++k) omk[k] = omega_prob(opt->seed, (uint64_t)(opt->first_iter + k));
     FD_CK(cudaMemcpyAsync(b->d_omega_seq, omk.data(), max_iter * sizeof(double), cudaMemcpyHostToDevice, st));
     seq = b->d_omega_seq;
   }
