@@ -329,6 +329,13 @@ fd_status fd_run(fd_layout* h, float* X, const fd_options* opt, int32_t* iters_o
 fd_status fd_run_trace(fd_layout* h, int32_t* accepted, double* omega, int32_t* cg_steps,
                        double* crit);
 
+/* More of the last fd_run / fd_sor_step's per-iteration trace, to host
+ * arrays of length >= iterations (any pointer may be NULL): f(H(X^k)) (the
+ * omega = 0 candidate of line 4), f of the extrapolated candidate of line 5
+ * (under FD_OMEGA_ENUM the argmin), and the device time in ms from the
+ * start of the launch to the end of each iteration (%globaltimer). */
+fd_status fd_run_trace_ext(fd_layout* h, double* f_h, double* f_extrapolated, double* t_ms);
+
 /* Ideal distances of rows row0 .. row0 + nrows - 1 (all n columns, d_ii = 0)
  * as stored by the handle, written as float64 to the host array
  * out[nrows][n].  Unit-edge graphs give exact integers.  Errors: FD_ERR_ARG,

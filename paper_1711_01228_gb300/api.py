@@ -74,7 +74,7 @@ EXPORTED = ["fd_options_default", "fd_layout_create", "fd_layout_destroy", "fd_e
             "fd_batch_tune", "fd_batch_set_shape", "fd_batch_distances", "fd_batch_get_info",
             "fd_batch_last_stats", "fd_energy_length_grad", "fd_sor_step_adjoint", "fd_adjoint_reset",
             "fd_adjoint_length_grad", "fd_set_vertex_omega", "fd_factor", "fd_factor_rows", "fd_factor_release",
-            "fd_fp32_peak"]
+            "fd_fp32_peak", "fd_run_trace_ext"]
 GRAD_MAX_N = 4096
 BATCH_MAX_N = 2048
 TIMELINE_TAGS = {1: "pack", 2: "stress", 3: "forces", 4: "rhs0", 5: "h_init", 6: "cg_au0", 7: "cg_step",
@@ -126,6 +126,8 @@ def lib():
     L.fd_factor_release.restype = i32
     L.fd_run_trace.argtypes = [P, P, P, P, P]
     L.fd_run_trace.restype = i32
+    L.fd_run_trace_ext.argtypes = [P, P, P, P]
+    L.fd_run_trace_ext.restype = i32
     L.fd_distance_rows.argtypes = [P, i32, i32, P]
     L.fd_distance_rows.restype = i32
     L.fd_layout_info.argtypes = [P, ctypes.POINTER(Info)]
@@ -223,6 +225,9 @@ class RunResult:
     omega: np.ndarray = field(default=None)
     cg_steps: np.ndarray = field(default=None)
     crit: np.ndarray = field(default=None)
+    f_h: np.ndarray = field(default=None)             # f(H(X^k)) per iteration
+    f_extrapolated: np.ndarray = field(default=None)  # f of line 5's candidate per iteration
+    t_ms: np.ndarray = field(default=None)            # device ms from the launch to the end of iteration k
     stats: dict = field(default_factory=dict)
 
 
@@ -417,6 +422,11 @@ class Layout:
             _check(lib().fd_run_trace(self._h, acc.ctypes.data, om.ctypes.data, cg.ctypes.data, cr.ctypes.data),
                    "fd_run_trace")
             res.accepted, res.omega, res.cg_steps, res.crit = acc[:k], om[:k], cg[:k], cr[:k]
+            fh = np.zeros(max(k, 1), dtype=np.float64)
+            ft = np.zeros(max(k, 1), dtype=np.float64)
+            tm = np.zeros(max(k, 1), dtype=np.float64)
+            _check(lib().fd_run_trace_ext(self._h, fh.ctypes.data, ft.ctypes.data, tm.ctypes.data), "fd_run_trace_ext")
+            res.f_h, res.f_extrapolated, res.t_ms = fh[:k], ft[:k], tm[:k]
         return res
 
 
@@ -430,15 +440,18 @@ def fp32_peak(packed: bool = True) -> float:
 
 def trace_records(result: RunResult) -> list:
     """Per-iteration records of a run made with ``trace=True``: iteration k
-    (1-based), stress after it, whether line 6 kept the extrapolation, the
-    omega used, CG steps of its H step and the termination criterion."""
+    (1-based), stress after it, f(H(X^k)) and f of the extrapolated
+    candidate, whether line 6 kept the extrapolation, the omega used, CG
+    steps of its H step, the termination criterion and the device time since
+    the launch began."""
     if result.trace_f is None:
         raise ValueError("the run was made without trace=True")
     out = []
     for k in range(result.iterations):
-        out.append({"k": k + 1, "stress": float(result.trace_f[k + 1]), "accepted": bool(result.accepted[k]),
+        out.append({"k": k + 1, "stress": float(result.trace_f[k + 1]), "stress_h": float(result.f_h[k]),
+                    "stress_extrapolated": float(result.f_extrapolated[k]), "accepted": bool(result.accepted[k]),
                     "omega": float(result.omega[k]), "cg_steps": int(result.cg_steps[k]),
-                    "crit": float(result.crit[k])})
+                    "crit": float(result.crit[k]), "t_ms": float(result.t_ms[k])})
     return out
 
 

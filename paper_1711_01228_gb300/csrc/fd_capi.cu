@@ -94,6 +94,9 @@ struct fd_layout {
   double* d_trace_f = nullptr;
   double* d_trace_om = nullptr;
   double* d_trace_crit = nullptr;
+  double* d_trace_fh = nullptr;
+  double* d_trace_ft = nullptr;
+  double* d_trace_t = nullptr;
   int* d_trace_acc = nullptr;
   int* d_trace_cg = nullptr;
   int trace_cap = 0;
@@ -332,6 +335,9 @@ void release(fd_layout* h) {
   dev_free(h->d_trace_f);
   dev_free(h->d_trace_om);
   dev_free(h->d_trace_crit);
+  dev_free(h->d_trace_fh);
+  dev_free(h->d_trace_ft);
+  dev_free(h->d_trace_t);
   dev_free(h->d_trace_acc);
   dev_free(h->d_trace_cg);
   dev_free(h->d_timeline);
@@ -487,6 +493,9 @@ fd_status ensure_traces(fd_layout* h, int max_iter) {
   dev_free(h->d_trace_f);
   dev_free(h->d_trace_om);
   dev_free(h->d_trace_crit);
+  dev_free(h->d_trace_fh);
+  dev_free(h->d_trace_ft);
+  dev_free(h->d_trace_t);
   dev_free(h->d_trace_acc);
   dev_free(h->d_trace_cg);
   h->trace_cap = 0;
@@ -496,6 +505,9 @@ fd_status ensure_traces(fd_layout* h, int max_iter) {
   if ((s = dev_alloc(&h->d_trace_f, cap)) != FD_OK) return s;
   if ((s = dev_alloc(&h->d_trace_om, cap)) != FD_OK) return s;
   if ((s = dev_alloc(&h->d_trace_crit, cap)) != FD_OK) return s;
+  if ((s = dev_alloc(&h->d_trace_fh, cap)) != FD_OK) return s;
+  if ((s = dev_alloc(&h->d_trace_ft, cap)) != FD_OK) return s;
+  if ((s = dev_alloc(&h->d_trace_t, cap)) != FD_OK) return s;
   if ((s = dev_alloc(&h->d_trace_acc, cap)) != FD_OK) return s;
   if ((s = dev_alloc(&h->d_trace_cg, cap)) != FD_OK) return s;
   h->trace_cap = cap;
@@ -1146,6 +1158,9 @@ static fd_status run_impl(fd_layout* h, float* X, const fd_options* opt, int k0,
   p.trace_om = h->d_trace_om;
   p.trace_cg = h->d_trace_cg;
   p.trace_crit = h->d_trace_crit;
+  p.trace_fh = h->d_trace_fh;
+  p.trace_ft = h->d_trace_ft;
+  p.trace_t = h->d_trace_t;
   p.max_iter = max_iter;
   p.enum_omega = (opt->strategy == FD_OMEGA_ENUM) ? 1 : 0;
   p.om_scale = h->d_om_scale;
@@ -1248,6 +1263,24 @@ fd_status fd_run_trace(fd_layout* h, int32_t* accepted, double* omega, int32_t* 
   for (auto& c : cp) {
     if (!c.dst) continue;
     if (cudaMemcpy(c.dst, c.src, c.bytes, cudaMemcpyDeviceToHost) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, FD_ERR_CUDA);
+    }
+  }
+  return FD_OK;
+}
+
+fd_status fd_run_trace_ext(fd_layout* h, double* f_h, double* f_extrapolated, double* t_ms) {
+  if (!h) return FD_ERR_ARG;
+  const int k = h->last_iters;
+  if (k <= 0) return FD_OK;
+  struct {
+    void* dst;
+    const void* src;
+  } cp[] = {{f_h, h->d_trace_fh}, {f_extrapolated, h->d_trace_ft}, {t_ms, h->d_trace_t}};
+  for (auto& c : cp) {
+    if (!c.dst) continue;
+    if (cudaMemcpy(c.dst, c.src, k * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) {
       cudaGetLastError();
       return fail(h, FD_ERR_CUDA);
     }

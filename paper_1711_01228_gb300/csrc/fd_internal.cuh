@@ -117,6 +117,9 @@ struct KParams {
   double* trace_om;            // [max_iter]
   int* trace_cg;               // [max_iter]
   double* trace_crit;          // [max_iter]
+  double* trace_fh;            // [max_iter] f(H(X^k)) (the omega = 0 candidate)
+  double* trace_ft;            // [max_iter] f of the extrapolated candidate (the argmin under enumeration)
+  double* trace_t;             // [max_iter] ms since the launch began, at the end of iteration k
   int max_iter, stop, cg_max;
   int enum_omega;              // 1: omega is the argmin of f over {0, 0.5, ..., 9} each iteration (Sec. 5.2.2)
   const float* om_scale;       // NULL, or [n_pad] per-vertex factors m_i: omega_i = omega m_i (Sec. 6), padding 0

@@ -761,7 +761,7 @@ static_assert(sizeof(PassCtl) <= SmemLayout<1, CODE_U8>::OFF_RUN - SmemLayout<1,
 
 // Scalars of the Algorithm 2 loop (shared memory, written by thread 0).
 struct RunState {
-  double f_cur, f_new, crit, passes_mv, passes_st;
+  double f_cur, f_new, crit, passes_mv, passes_st, f_enum0;
   int cg_total, cg_maxed, cg_stalled, n_acc, it_outer, it;
   int accept, bsel, stop, all_conv, cg_done;
   int conv[3];
@@ -1180,6 +1180,8 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
   ps.parity = 0u;
   ps.pass = 0;
   int nbar = 0;
+  // start of the launch for the per-iteration times (read by CTA 0, thread 0 only)
+  const unsigned long long t_launch = (blockIdx.x == 0 && tid == 0) ? globaltimer_ns() : 0ull;
   if (p.timeline && blockIdx.x == 0 && tid == 0) ctrl->t_start = globaltimer_ns();
   auto mark = [&](int tag) {
     if (p.timeline && blockIdx.x == 0 && tid == 0 && ctrl->timeline_n < p.timeline_cap) {
@@ -1655,6 +1657,7 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
         rs->om_prev = ENUM_STEP * best;
         rs->accept = (best > 0) ? 1 : 0;
         rs->bsel = 0;
+        rs->f_enum0 = df_to_double(fv[0]);
       }
       __syncthreads();
       PassSrc sel = direct_src(p.Zw, SK_SEL);
@@ -1681,6 +1684,9 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
             p.trace_acc[k] = rs->accept;
             p.trace_om[k] = (double)rs->om_prev;
             p.trace_cg[k] = rs->it;
+            p.trace_fh[k] = rs->f_enum0;
+            p.trace_ft[k] = fX;
+            p.trace_t[k] = 1e-6 * (double)(globaltimer_ns() - t_launch);
           }
         }
       }
@@ -1735,6 +1741,9 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
           p.trace_acc[k] = (accept || !two) ? 1 : 0;
           p.trace_om[k] = om;
           p.trace_cg[k] = rs->it;
+          p.trace_fh[k] = fZ;
+          p.trace_ft[k] = fT;
+          p.trace_t[k] = 1e-6 * (double)(globaltimer_ns() - t_launch);
         }
       }
     }

@@ -48,10 +48,12 @@ def test_trace_jsonl(tmp_path):
 
     r = api.RunResult(iterations=2, stress=1.5, trace_f=np.array([3.0, 2.0, 1.5]),
                       accepted=np.array([1, 0], dtype=np.int32), omega=np.array([0.5, 0.5]),
-                      cg_steps=np.array([4, 3], dtype=np.int32), crit=np.array([0.1, 0.01]))
+                      cg_steps=np.array([4, 3], dtype=np.int32), crit=np.array([0.1, 0.01]),
+                      f_h=np.array([2.2, 1.5]), f_extrapolated=np.array([2.0, 1.7]), t_ms=np.array([0.25, 0.5]))
     p = tmp_path / "t.jsonl"
     api.write_trace_jsonl(r, str(p), graph="g")
     recs = [json.loads(line) for line in p.read_text().splitlines()]
-    assert recs == [{"k": 1, "stress": 2.0, "accepted": True, "omega": 0.5, "cg_steps": 4, "crit": 0.1, "graph": "g"},
-                    {"k": 2, "stress": 1.5, "accepted": False, "omega": 0.5, "cg_steps": 3, "crit": 0.01,
-                     "graph": "g"}]
+    assert recs == [{"k": 1, "stress": 2.0, "stress_h": 2.2, "stress_extrapolated": 2.0, "accepted": True,
+                     "omega": 0.5, "cg_steps": 4, "crit": 0.1, "t_ms": 0.25, "graph": "g"},
+                    {"k": 2, "stress": 1.5, "stress_h": 1.5, "stress_extrapolated": 1.7, "accepted": False,
+                     "omega": 0.5, "cg_steps": 3, "crit": 0.01, "t_ms": 0.5, "graph": "g"}]

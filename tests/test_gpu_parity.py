@@ -171,6 +171,27 @@ def test_converged_run_grid20(omega):
     assert r.trace_f[0] == pytest.approx(ref.trace_f[0], rel=1e-5)
 
 
+def test_extended_trace_matches_oracle():
+    # f(H(X^k)) and f of the extrapolated candidate per iteration (lines 4-6 of
+    # Algorithm 2), against the oracle's trace_fH; the times increase
+    rp, ci = synth.grid(12, 12)
+    D = _dense(rp, ci)
+    X0 = synth.initial_layout(144, 2, seed=6)
+    ref = oracle.sor_run(D, X0.astype(np.float64), omega=1.0, tol=1e-5, max_iter=60)
+    X = X0.copy()
+    with api.Layout(rp, ci, dim=2) as L:
+        r = L.run(X, trace=True, omega=1.0, tol=1e-5, max_iter=60)
+    k = min(10, r.iterations, ref.iterations)
+    assert np.allclose(r.f_h[:k], np.array(ref.trace_fH[:k]), rtol=1e-4, atol=0)
+    for i in range(r.iterations):
+        # line 6: the kept stress is the extrapolated one if accepted, else f(H(X^k))
+        kept = r.f_extrapolated[i] if r.accepted[i] else r.f_h[i]
+        assert r.trace_f[i + 1] == kept
+        assert r.accepted[i] == (r.f_extrapolated[i] <= r.f_h[i])
+    assert np.all(np.diff(r.t_ms) > 0) and r.t_ms[0] > 0
+    assert r.t_ms[-1] <= r.stats["kernel_ms"] * 1.01 + 0.05
+
+
 def test_probabilistic_strategy_matches_oracle_sequence():
     rp, ci = synth.grid(10, 10)
     D = _dense(rp, ci)
