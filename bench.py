@@ -271,10 +271,7 @@ def run_ours(args, rank, world, local_rank):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": "+".join(args.workload.split(",")) + f" {args.dim}-D, X0 U[0,1]^{args.dim} seed 0, omega_c "
-                   + ("1.0-1.9 sweep" if args.sweep else "1.5") + ", rel-disp tol 1e-4, max 1000 iters",
-                   "graphs": {nm: {"n": len(rp) - 1, "m": int(rp[-1]) // 2} for nm, rp, _, _ in inputs},
-                   "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
+        "config": workload_config(args, inputs, world),
         "sor_iterations_per_s": acc["iters"] * world / (total_ms / 1e3),
         "cg_steps_per_sor_iteration": acc["cg"] / max(acc["iters"], 1),
         "gpu_launches": acc["n_launch_total"],
@@ -800,7 +797,17 @@ def cpu_sample(budget_s: float):
                       f"pairs of ER n=10,000 ({el:.1f} s)"}
 
 
+def workload_config(args, inputs, world):
+    """The bench line's config: the workload both arms are quoted on."""
+    return {"workload": "+".join(args.workload.split(",")) + f" {args.dim}-D, X0 U[0,1]^{args.dim} seed 0, omega_c "
+            + ("1.0-1.9 sweep" if args.sweep else "1.5") + ", rel-disp tol 1e-4, max 1000 iters",
+            "graphs": {nm: {"n": len(rp) - 1, "m": int(rp[-1]) // 2} for nm, rp, _, _ in inputs},
+            "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args, rank, world):
+    """The oracle, as it is, on the host cores: each step a bounded sample of
+    the workload (see cpu_sample), on the GPU arm's config and metric."""
     if rank != 0:
         return None
     for _ in range(args.warmup):
@@ -814,7 +821,7 @@ def run_reference(args, rank, world):
     return {"impl": "reference", "metric": "pair-interactions/s", "value": v, "unit": "pairs/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "er10k oracle sample (see cpu_baseline.sample)"},
+            "config": workload_config(args, make_inputs(args.workload.split(","), args.dim), world),
             "cpu_baseline": {**vals[-1], "value": v},
             "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 

@@ -182,3 +182,38 @@ def test_direct_solver_needs_a_factor():
             L.run(X.copy(), solver=api.SOLVER_DIRECT)
         with pytest.raises(api.FdError):
             L.factor_rows(0, 1)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3])
+def test_tiny_graphs(n):
+    # one vertex: L^W = 0 and the shift alone is inverted; two and three vertices: K2, P3
+    rp, ci = synth.path(n)
+    X0 = synth.initial_layout(n, 2, seed=1)
+    with api.Layout(rp, ci, dim=2) as L:
+        L.factor()
+        Ai = L.factor_rows(0, n)
+        X = X0.copy()
+        r = L.run(X, omega=0.5, tol=1e-6, max_iter=50, solver=api.SOLVER_DIRECT)
+    if n == 1:
+        assert Ai[0, 0] == pytest.approx(1.0)  # A' = [sigma / n] with sigma = 1 when L^W = 0
+        assert r.stress == 0.0
+        return
+    D = _D(rp, ci)
+    assert np.allclose(Ai, oracle.shifted_inverse(D), rtol=1e-5, atol=1e-7)
+    ref = oracle.sor_run(D, X0.astype(np.float64), omega=0.5, tol=1e-6, max_iter=50)
+    assert r.stress == pytest.approx(ref.stress, abs=1e-6 * max(1.0, ref.stress))
+
+
+def test_weighted_graph_run_matches_oracle():
+    rp, ci = synth.grid(10, 10)
+    ln = _lengths(rp, ci, 5)
+    n = len(rp) - 1
+    D = _D(rp, ci, edge_len=ln.astype(np.float64))
+    X0 = synth.initial_layout(n, 2, seed=2) * 10.0
+    ref = oracle.sor_run(D, X0.astype(np.float64), omega=0.5, tol=1e-5, stop=oracle.STOP_REL_STRESS, max_iter=500)
+    X = X0.copy()
+    with api.Layout(rp, ci, dim=2, edge_len=ln) as L:
+        L.factor()
+        r = L.run(X, omega=0.5, tol=1e-5, stop=api.STOP_REL_STRESS, max_iter=500, solver=api.SOLVER_DIRECT)
+    assert r.stress == pytest.approx(ref.stress, rel=1e-4)
+    assert abs(r.iterations - ref.iterations) <= max(1, math.ceil(0.02 * ref.iterations))
