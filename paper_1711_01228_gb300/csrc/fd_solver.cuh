@@ -347,34 +347,56 @@ __device__ __forceinline__ void cta_sum_multi(df (&v)[K], float2* red) {
 // Grid barrier whose last arriving CTA runs `on_last` (all its threads)
 // before it releases the others: reductions over all CTAs' partial sums run
 // once, in a fixed order, instead of in every CTA.  Waits are bounded.
+// Ordering: every CTA arrives with an acquire-release add on the counter
+// (releasing its writes, which its threads ordered before thread 0 with the
+// CTA barrier); the last arrival's add acquires all of them (the adds form
+// one release sequence), and its release of the generation publishes them,
+// with the reduction, to every CTA that acquires the new generation.
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* a) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned int ld_relaxed_u32(const unsigned int* a) {
+  unsigned int v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned int atom_add_acq_rel_u32(unsigned int* a, unsigned int x) {
+  unsigned int v;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(v) : "l"(a), "r"(x) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_u32(unsigned int* a, unsigned int x) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(a), "r"(x) : "memory");
+}
+__device__ __forceinline__ void red_release_add_u32(unsigned int* a, unsigned int x) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(a), "r"(x) : "memory");
+}
+
 template <class F>
 __device__ __forceinline__ bool grid_sync_reduce(Ctrl* c, long long timeout_ns, int where, F&& on_last) {
   __shared__ int s_last, s_ok;
   __syncthreads();
   unsigned int g = 0;
   if (threadIdx.x == 0) {
-    g = *(volatile unsigned int*)&c->bar_gen;
-    __threadfence();
-    const unsigned int arrived = atomicAdd(&c->bar_count, 1u);
+    g = ld_relaxed_u32(&c->bar_gen);
+    const unsigned int arrived = atom_add_acq_rel_u32(&c->bar_count, 1u);
     s_last = (arrived == gridDim.x - 1);
-    if (s_last) __threadfence();
   }
   __syncthreads();
   if (s_last) {
     on_last();
     __syncthreads();
     if (threadIdx.x == 0) {
-      __threadfence();
-      atomicExch(&c->bar_count, 0u);
-      __threadfence();
-      atomicAdd(&c->bar_gen, 1u);
+      st_relaxed_u32(&c->bar_count, 0u);
+      red_release_add_u32(&c->bar_gen, 1u);
     }
   } else if (threadIdx.x == 0) {
-    volatile unsigned int* gen = &c->bar_gen;
     volatile int* err = &c->err;
     unsigned long long t0 = globaltimer_ns();
     unsigned int ns = 32;
-    while (*gen == g) {
+    while (ld_acquire_u32(&c->bar_gen) == g) {
       if (*err != 0) break;
       __nanosleep(ns);
       if (ns < 256) ns <<= 1;
@@ -385,10 +407,7 @@ __device__ __forceinline__ bool grid_sync_reduce(Ctrl* c, long long timeout_ns, 
       }
     }
   }
-  if (threadIdx.x == 0) {
-    __threadfence();
-    s_ok = (*(volatile int*)&c->err == 0);
-  }
+  if (threadIdx.x == 0) s_ok = (*(volatile int*)&c->err == 0);
   __syncthreads();
   return s_ok != 0;
 }
