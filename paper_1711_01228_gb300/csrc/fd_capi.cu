@@ -84,8 +84,6 @@ struct fd_layout {
   float* d_inv_s = nullptr;
   float* d_vec = nullptr;  // pool of the per-vertex vectors
   float* d_acc = nullptr;      // [3][n_pad][dimp] per-vertex accumulators
-  double* d_sc_task = nullptr;  // [grid][2] double-float stress slots
-  double* d_sc = nullptr;       // [grid][SC_STRIDE] double-float scalar slots
   int nbuf = 2;                 // stages of the kernel's tile pipeline
   Ctrl* d_ctrl = nullptr;
   float* d_stage_in = nullptr;
@@ -326,8 +324,6 @@ void release(fd_layout* h) {
   dev_free(h->d_inv_s);
   dev_free(h->d_vec);
   dev_free(h->d_acc);
-  dev_free(h->d_sc_task);
-  dev_free(h->d_sc);
   dev_free(h->d_ctrl);
   dev_free(h->d_stage_in);
   dev_free(h->d_stage_out);
@@ -539,8 +535,6 @@ KParams base_params(fd_layout* h, int mode) {
   float** slots[] = {&p.X, &p.Z, &p.Xt, &p.B, &p.Bz, &p.Bt, &p.Zw, &p.R, &p.U, &p.W, &p.P, &p.S};
   for (int k = 0; k < 12; ++k) *slots[k] = v + k * vs;
   p.acc = h->d_acc;
-  p.sc_cta = reinterpret_cast<float2*>(h->d_sc_task);
-  p.sc = reinterpret_cast<float2*>(h->d_sc);
   p.ctrl = h->d_ctrl;
   p.timeout_ns = h->timeout_ns;
   p.bar_timeout_ns = h->bar_timeout_ns;
@@ -768,8 +762,6 @@ fd_status fd_layout_create(fd_layout** out, int32_t n, int32_t dim, const int32_
   if ((s = dev_alloc(&h->d_inv_s, h->n_pad)) != FD_OK) return bail(s);
   if ((s = dev_alloc(&h->d_vec, 12 * vs)) != FD_OK) return bail(s);
   if ((s = dev_alloc(&h->d_acc, 3 * vs)) != FD_OK) return bail(s);
-  if ((s = dev_alloc(&h->d_sc_task, (size_t)h->grid * 2)) != FD_OK) return bail(s);
-  if ((s = dev_alloc(&h->d_sc, (size_t)h->grid * SC_STRIDE)) != FD_OK) return bail(s);
   if ((s = dev_alloc(&h->d_ctrl, 1)) != FD_OK) return bail(s);
   if ((s = dev_alloc(&h->d_stage_in, (size_t)n * dim)) != FD_OK) return bail(s);
   if ((s = dev_alloc(&h->d_stage_out, (size_t)n * dim)) != FD_OK) return bail(s);
@@ -777,7 +769,6 @@ fd_status fd_layout_create(fd_layout** out, int32_t n, int32_t dim, const int32_
   if ((s = dev_alloc(&h->d_cta_task_ptr, h->grid + 1)) != FD_OK) return bail(s);
   cudaStream_t st = h->stream;
   if (cudaMemcpyAsync(h->d_lut, lut.data(), lut.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemsetAsync(h->d_sc, 0, (size_t)h->grid * SC_STRIDE * sizeof(double), st) != cudaSuccess ||
       cudaMemsetAsync(h->d_acc, 0, 3 * vs * sizeof(float), st) != cudaSuccess ||
       cudaMemcpyAsync(h->d_tasks, h->tasks.data(), h->ntasks * sizeof(TaskDesc), cudaMemcpyHostToDevice, st) !=
           cudaSuccess ||

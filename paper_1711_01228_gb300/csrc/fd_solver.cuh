@@ -268,8 +268,7 @@ struct PassArgs {
   const TaskDesc* tasks_g;  // this CTA's tasks in global memory
   const TaskDesc* tasks_s;  // ... and the first MAX_CTA_TASKS of them in shared memory
   Ctrl* ctrl;
-  float2* sc_cta;
-  float2* sc;  // PM_ENUM: the per-CTA stress of each candidate
+  double* rsum;  // stress passes: the grid-wide sums (one per candidate) this CTA adds to
   long long timeout_ns;
   int n, n_pad, nb, ntasks, nbuf;  // ntasks: this CTA's
   int stage_base;                   // shared-memory offset of stage 0
@@ -344,9 +343,9 @@ __device__ __forceinline__ void cta_sum_multi(df (&v)[K], float2* red) {
   __syncthreads();
 }
 
-// Grid barrier whose last arriving CTA runs `on_last` (all its threads)
-// before it releases the others: reductions over all CTAs' partial sums run
-// once, in a fixed order, instead of in every CTA.  Waits are bounded.
+// Grid barrier whose last arriving CTA runs `on_last(sums)` (all its
+// threads) before it releases the others, with the grid-wide sums that the
+// CTAs added before arriving.  Waits are bounded.
 // Ordering: every CTA arrives with an acquire-release add on the counter
 // (releasing its writes, which its threads ordered before thread 0 with the
 // CTA barrier); the last arrival's add acquires all of them (the adds form
@@ -386,7 +385,10 @@ __device__ __forceinline__ bool grid_sync_reduce(Ctrl* c, long long timeout_ns, 
   }
   __syncthreads();
   if (s_last) {
-    on_last();
+    // the sums of the next reduction go to the other set: clear it (every
+    // CTA read it before arriving here)
+    if (threadIdx.x < SC_STRIDE) c->acc_d[(where + 1) & 1][threadIdx.x] = 0.0;
+    on_last(c->acc_d[where & 1]);
     __syncthreads();
     if (threadIdx.x == 0) {
       st_relaxed_u32(&c->bar_count, 0u);
@@ -412,22 +414,16 @@ __device__ __forceinline__ bool grid_sync_reduce(Ctrl* c, long long timeout_ns, 
   return s_ok != 0;
 }
 
-// Run by the last CTA: K consecutive slots of `count` records (stride float2
-// apart) summed in a fixed order into ctrl->red[0..K).
+// Run by the last CTA: the K grid-wide sums into ctrl->red[0..K) as
+// double-float values (read by every CTA after the barrier).
 template <int K>
-__device__ __forceinline__ void reduce_slots_to_ctrl(Ctrl* c, const float2* a, int count, int stride, float2* red) {
-  df t[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) t[k] = df_of(0.f);
-  for (int r = threadIdx.x; r < count; r += CTA) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) t[k] = df_add(t[k], df_ld(a + (size_t)r * stride + k));
+__device__ __forceinline__ void take_sums(Ctrl* c, const double* sums) {
+  if (threadIdx.x < K) {
+    const double d = __ldcg(sums + threadIdx.x);
+    const float hi = (float)d;
+    c->red[threadIdx.x] = make_float2(hi, (float)(d - (double)hi));
   }
-  cta_sum_multi<K>(t, red);
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) __stcg(&c->red[k], make_float2(t[k].hi, t[k].lo));
-  }
+  __syncthreads();
 }
 
 // After the barrier: the K reduced values, in every thread.
@@ -958,10 +954,7 @@ __device__ FD_PASS_ATTR bool pair_pass_impl(PairState* ps_io, float* acc) {
     cta_sum_multi<NS>(v, red64);
     if (tid == 0) {
 #pragma unroll
-      for (int c = 0; c < NS; ++c) {
-        if constexpr (MODE == PM_ENUM) df_st(p.sc + (size_t)blockIdx.x * SC_STRIDE + c, v[c]);
-        else df_st(p.sc_cta + (size_t)blockIdx.x * 2 + c, v[c]);
-      }
+      for (int c = 0; c < NS; ++c) atomicAdd(p.rsum + c, df_to_double(v[c]));
     }
   }
   ps.pass += 1;
@@ -971,7 +964,7 @@ __device__ FD_PASS_ATTR bool pair_pass_impl(PairState* ps_io, float* acc) {
 
 template <int DIM, int MODE, int NC, int CODE>
 __device__ __forceinline__ bool pair_pass(const KParams& p, unsigned char* smem, PairState& ps, const PassSrc& src,
-                                          float* acc) {
+                                          float* acc, double* rsum = nullptr) {
   using L = SmemLayout<DIM, CODE>;
   PassCtl* ctl = reinterpret_cast<PassCtl*>(smem + L::OFF_CTL);
   if (threadIdx.x == 0) {
@@ -982,8 +975,7 @@ __device__ __forceinline__ bool pair_pass(const KParams& p, unsigned char* smem,
     a.tasks_g = p.g.tasks + t0;
     a.tasks_s = reinterpret_cast<const TaskDesc*>(smem + L::OFF_TASKS);
     a.ctrl = p.ctrl;
-    a.sc_cta = p.sc_cta;
-    a.sc = p.sc;
+    a.rsum = rsum;
     a.timeout_ns = p.timeout_ns;
     a.n = p.g.n;
     a.n_pad = p.g.n_pad;
@@ -998,11 +990,11 @@ __device__ __forceinline__ bool pair_pass(const KParams& p, unsigned char* smem,
 
 // --------------------------------------------------------------------------
 // Vertex phase: one thread per vertex (CTA b takes vertex blocks b, b + G,
-// ...); fn(i, v) adds the vertex's K scalars to v, which the CTA sums into
-// its slot of p.sc.
+// ...); fn(i, v) adds the vertex's K scalars to v, which the CTA sums and
+// adds to the grid-wide sums rsum (FP64 atomics).
 // --------------------------------------------------------------------------
 template <int K, class F>
-__device__ __forceinline__ void vertex_phase(const KParams& p, float2* red64, F&& fn) {
+__device__ __forceinline__ void vertex_phase(const KParams& p, float2* red64, double* rsum, F&& fn) {
   constexpr int K1 = (K > 0) ? K : 1;
   df v[K1];
 #pragma unroll
@@ -1012,7 +1004,7 @@ __device__ __forceinline__ void vertex_phase(const KParams& p, float2* red64, F&
     cta_sum_multi<K>(v, red64);
     if (threadIdx.x == 0) {
 #pragma unroll
-      for (int k = 0; k < K; ++k) df_st(p.sc + (size_t)blockIdx.x * SC_STRIDE + k, v[k]);
+      for (int k = 0; k < K; ++k) atomicAdd(rsum + k, df_to_double(v[k]));
     }
   }
 }
@@ -1209,18 +1201,20 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
       p.timeline[2 * q + 1] = (double)(globaltimer_ns() - ctrl->t_start);
     }
   };
-  auto no_reduction = [] {};
-  // grid barrier; the last CTA to arrive runs `red` first (a fixed-order reduction)
+  auto no_reduction = [](const double*) {};
+  // grid barrier; the last CTA to arrive runs `red` on the grid-wide sums first
 #define FD_SYNC_RED(tag, red)                                                   \
   do {                                                                          \
     if (!grid_sync_reduce(ctrl, p.bar_timeout_ns, ++nbar, red)) return;         \
     mark(tag);                                                                  \
   } while (0)
 #define FD_SYNC(tag) FD_SYNC_RED(tag, no_reduction)
+  // the grid-wide sums the next reduction barrier (index nbar + 1) collects
+#define RSUM (ctrl->acc_d[(nbar + 1) & 1])
   auto red_stress = [&](int nc) {
-    return [&, nc] {
-      if (nc == 2) reduce_slots_to_ctrl<2>(ctrl, p.sc_cta, gridDim.x, 2, red64);
-      else reduce_slots_to_ctrl<1>(ctrl, p.sc_cta, gridDim.x, 2, red64);
+    return [&, nc](const double* sums) {
+      if (nc == 2) take_sums<2>(ctrl, sums);
+      else take_sums<1>(ctrl, sums);
     };
   };
 
@@ -1249,7 +1243,7 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
   FD_SYNC(1);
 
   if (p.mode == KM_ENERGY) {
-    if (!pair_pass<DIM, PM_STRESS, 1, CODE>(p, smem, ps, direct_src(p.X), acc0)) return;
+    if (!pair_pass<DIM, PM_STRESS, 1, CODE>(p, smem, ps, direct_src(p.X), acc0, RSUM)) return;
     FD_SYNC_RED(2, red_stress(1));
     if (blockIdx.x == 0 && tid == 0) {
       df f[1];
@@ -1266,7 +1260,7 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
   if (p.mode == KM_FORCES) {
     if (!pair_pass<DIM, PM_FORCES, 1, CODE>(p, smem, ps, direct_src(p.X), acc0)) return;
     FD_SYNC(3);
-    vertex_phase<0>(p, red64, [&](int i, df(&)[1]) {
+    vertex_phase<0>(p, red64, nullptr, [&](int i, df(&)[1]) {
       const Vec<DIM> f = take_acc<DIM>(acc0, i);
       if (i < n) {
 #pragma unroll
@@ -1290,7 +1284,7 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
   // b = L^{X^0} X^0 (right-hand side of Eq. (2-5)) and f(X^0) (Eq. (1));
   // KM_SOLVE has its right-hand side already
   if (p.mode != KM_SOLVE) {
-    if (!pair_pass<DIM, PM_RHS, 1, CODE>(p, smem, ps, direct_src(p.X), acc0)) return;
+    if (!pair_pass<DIM, PM_RHS, 1, CODE>(p, smem, ps, direct_src(p.X), acc0, RSUM)) return;
     FD_SYNC_RED(4, red_stress(1));
   }
   if (tid == 0) {
@@ -1339,7 +1333,7 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
       float z0[DIM];
 #pragma unroll
       for (int d = 0; d < DIM; ++d) z0[d] = rs->z0[d];
-      vertex_phase<7 * DIM>(p, red64, [&](int i, df(&v)[7 * DIM]) {
+      vertex_phase<7 * DIM>(p, red64, RSUM, [&](int i, df(&v)[7 * DIM]) {
         const bool real = i < n;
         const Vec<DIM> xo = ldv<DIM>(p.X, i);
         Vec<DIM> x0;
@@ -1383,8 +1377,8 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
       });
       // reduce the 7*DIM sums; the last CTA also evaluates the termination rule
       const double fcur_k = rs->f_cur, fnew_k = rs->f_new;
-      auto red_init = [&] {
-        reduce_slots_to_ctrl<7 * DIM>(ctrl, p.sc, gridDim.x, SC_STRIDE, red64);
+      auto red_init = [&](const double* sums) {
+        take_sums<7 * DIM>(ctrl, sums);
         if (threadIdx.x == 0) {
           double c = 0.0;
           if (p.stop == 0) {
@@ -1448,7 +1442,7 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
           ++rs->it;
         }
         FD_SYNC(7);
-        vertex_phase<DIM>(p, red64, [&](int i, df(&v)[DIM]) {
+        vertex_phase<DIM>(p, red64, RSUM, [&](int i, df(&v)[DIM]) {
           const float s = __ldcg(p.s + i);
           const Vec<DIM> u = take_acc<DIM>(p.P, i);
           const Vec<DIM> a = take_acc<DIM>(acc2, i);
@@ -1462,7 +1456,7 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
           stv<DIM>(p.Zw, i, x);
           stv<DIM>(p.R, i, r);
         });
-        auto red_dir = [&] { reduce_slots_to_ctrl<DIM>(ctrl, p.sc, gridDim.x, SC_STRIDE, red64); };
+        auto red_dir = [&](const double* sums) { take_sums<DIM>(ctrl, sums); };
         FD_SYNC_RED(9, red_dir);
         if (tid == 0) {
           df v[DIM];
@@ -1487,7 +1481,7 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
       if (tid == 0) rs->passes_mv += 1.0;
       FD_SYNC(6);
       // w0 = L^W u0 and delta0 = (w0, u0).  Slots [0,D).
-      vertex_phase<DIM>(p, red64, [&](int i, df(&v)[DIM]) {
+      vertex_phase<DIM>(p, red64, RSUM, [&](int i, df(&v)[DIM]) {
         const float s = __ldcg(p.s + i);
         const Vec<DIM> u = ldv<DIM>(p.U, i);
         const Vec<DIM> a = take_acc<DIM>(acc2, i);
@@ -1499,7 +1493,7 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
         }
         stv<DIM>(p.W, i, w);
       });
-      auto red_au0 = [&] { reduce_slots_to_ctrl<DIM>(ctrl, p.sc, gridDim.x, SC_STRIDE, red64); };
+      auto red_au0 = [&](const double* sums) { take_sums<DIM>(ctrl, sums); };
       FD_SYNC_RED(9, red_au0);
       if (tid == 0) {
         df dlv[DIM];
@@ -1546,7 +1540,7 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
           al[d] = src.alpha[d];
           be[d] = src.beta[d];
         }
-        vertex_phase<6 * DIM>(p, red64, [&](int i, df(&v)[6 * DIM]) {
+        vertex_phase<6 * DIM>(p, red64, RSUM, [&](int i, df(&v)[6 * DIM]) {
           const float s = __ldcg(p.s + i), is = __ldcg(p.inv_s + i);
           Vec<DIM> u = ldv<DIM>(p.U, i), w = ldv<DIM>(p.W, i), pp = ldv<DIM>(p.P, i), sp = ldv<DIM>(p.S, i);
           Vec<DIM> x = ldv<DIM>(p.Zw, i), r = ldv<DIM>(p.R, i);
@@ -1576,7 +1570,7 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
           stv<DIM>(p.U, i, u);
           stv<DIM>(p.W, i, w);
         });
-        auto red_cg = [&] { reduce_slots_to_ctrl<6 * DIM>(ctrl, p.sc, gridDim.x, SC_STRIDE, red64); };
+        auto red_cg = [&](const double* sums) { take_sums<6 * DIM>(ctrl, sums); };
         FD_SYNC_RED(9, red_cg);
         if (tid == 0) {
           df v[6 * DIM];
@@ -1657,9 +1651,9 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
         rs->passes_st += (double)NENUM + 1.0;
       }
       if constexpr (WITH_ENUM) {
-        if (!pair_pass<DIM, PM_ENUM, 2, CODE>(p, smem, ps, src, acc0)) return;
+        if (!pair_pass<DIM, PM_ENUM, 2, CODE>(p, smem, ps, src, acc0, RSUM)) return;
       }
-      auto red_enum = [&] { reduce_slots_to_ctrl<NENUM>(ctrl, p.sc, gridDim.x, SC_STRIDE, red64); };
+      auto red_enum = [&](const double* sums) { take_sums<NENUM>(ctrl, sums); };
       FD_SYNC_RED(8, red_enum);
       if (tid == 0) {
         df fv[NENUM];
@@ -1686,7 +1680,7 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
       sel.om = rs->om_prev;
       sel.sel = rs->accept;
       sel.oms = p.om_scale;
-      if (!pair_pass<DIM, PM_RHS, 1, CODE>(p, smem, ps, sel, acc0)) return;
+      if (!pair_pass<DIM, PM_RHS, 1, CODE>(p, smem, ps, sel, acc0, RSUM)) return;
       FD_SYNC_RED(8, red_stress(1));
       if (tid == 0) {
         df fz[1];
@@ -1733,10 +1727,10 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
       rs->passes_st += two ? 2.0 : 1.0;
     }
     if (two) {
-      if (!pair_pass<DIM, PM_RHS, 2, CODE>(p, smem, ps, src, acc0)) return;
+      if (!pair_pass<DIM, PM_RHS, 2, CODE>(p, smem, ps, src, acc0, RSUM)) return;
       FD_SYNC_RED(8, red_stress(2));
     } else {
-      if (!pair_pass<DIM, PM_RHS, 1, CODE>(p, smem, ps, src, acc0)) return;
+      if (!pair_pass<DIM, PM_RHS, 1, CODE>(p, smem, ps, src, acc0, RSUM)) return;
       FD_SYNC_RED(8, red_stress(1));
     }
     if (tid == 0) {
@@ -1793,6 +1787,7 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
   }
 #undef FD_SYNC
 #undef FD_SYNC_RED
+#undef RSUM
 #undef n
 #undef nb
 #undef tid
