@@ -86,7 +86,6 @@ struct fd_layout {
   float* d_acc = nullptr;      // [3][n_pad][dimp] per-vertex accumulators
   int nbuf = 2;                 // stages of the kernel's tile pipeline
   Ctrl* d_ctrl = nullptr;
-  RSums* d_rsums = nullptr;  // grid-wide sums of the layout kernel's reductions
   float* d_stage_in = nullptr;
   float* d_stage_out = nullptr;
   double* d_omega = nullptr;
@@ -326,7 +325,6 @@ void release(fd_layout* h) {
   dev_free(h->d_vec);
   dev_free(h->d_acc);
   dev_free(h->d_ctrl);
-  dev_free(h->d_rsums);
   dev_free(h->d_stage_in);
   dev_free(h->d_stage_out);
   dev_free(h->d_omega);
@@ -538,7 +536,6 @@ KParams base_params(fd_layout* h, int mode) {
   for (int k = 0; k < 12; ++k) *slots[k] = v + k * vs;
   p.acc = h->d_acc;
   p.ctrl = h->d_ctrl;
-  p.rsums = h->d_rsums;
   p.timeout_ns = h->timeout_ns;
   p.bar_timeout_ns = h->bar_timeout_ns;
   p.max_iter = 0;
@@ -551,7 +548,6 @@ KParams base_params(fd_layout* h, int mode) {
 fd_status run_kernel(fd_layout* h, KParams& p, Ctrl* ctrl_out, double* kernel_ms) {
   cudaStream_t st = h->stream;
   FD_CK(cudaMemsetAsync(h->d_ctrl, 0, sizeof(Ctrl), st));
-  FD_CK(cudaMemsetAsync(h->d_rsums, 0, sizeof(RSums), st));
   FD_CK(cudaEventRecord(h->ev0, st));
   FD_CK(launch_main(h->dim, h->code, p, h->grid, h->smem, st));
   FD_CK(cudaEventRecord(h->ev1, st));
@@ -767,7 +763,6 @@ fd_status fd_layout_create(fd_layout** out, int32_t n, int32_t dim, const int32_
   if ((s = dev_alloc(&h->d_vec, 12 * vs)) != FD_OK) return bail(s);
   if ((s = dev_alloc(&h->d_acc, 3 * vs)) != FD_OK) return bail(s);
   if ((s = dev_alloc(&h->d_ctrl, 1)) != FD_OK) return bail(s);
-  if ((s = dev_alloc(&h->d_rsums, 1)) != FD_OK) return bail(s);
   if ((s = dev_alloc(&h->d_stage_in, (size_t)n * dim)) != FD_OK) return bail(s);
   if ((s = dev_alloc(&h->d_stage_out, (size_t)n * dim)) != FD_OK) return bail(s);
   if ((s = dev_alloc(&h->d_tasks, h->ntasks)) != FD_OK) return bail(s);

@@ -26,8 +26,6 @@ constexpr int CTA = 128;           // threads per CTA of the pair kernels (4 war
 constexpr int LUT_N = 256;         // uint8 codes
 constexpr int LUT_ROW = 256;       // bytes per code in the replicated table: 32 x 1/d, then 32 x 1/d^2
 constexpr int SC_STRIDE = 24;      // scalars of one grid-wide reduction, at most
-constexpr int RSUM_GROUPS = 16;    // slots per grid-wide sum (spread the atomics)
-constexpr int RSUM_LINE = 16;      // doubles per slot: one 128-byte line
 constexpr int MAX_NBUF = 4;        // stages of the tile pipeline
 constexpr int MAX_CTA_TASKS = 128; // task descriptors a CTA keeps in shared memory
 
@@ -77,16 +75,10 @@ struct Ctrl {
   unsigned long long t_start;  // %globaltimer at kernel start (CTA 0)
   float2 red[32];              // grid-wide sums of a reduction barrier (double-float), written by its last CTA
   double red_d[4];             // FP64 scalars computed by that CTA (termination criterion)
-};
-
-// Grid-wide sums of the reductions: every CTA adds its partial sums (FP64
-// atomics) to set (b & 1) before it arrives at reduction barrier b; the last
-// CTA at barrier b clears set (b + 1) & 1, read after barrier b - 1, for the
-// next reduction.  Value k of a set has RSUM_GROUPS slots (CTA c adds to slot
-// c mod RSUM_GROUPS), each on its own 128-byte line, so that the grid's
-// atomics spread over lines instead of queueing on one.  Zero at launch.
-struct RSums {
-  double v[2][SC_STRIDE][RSUM_GROUPS][RSUM_LINE];
+  // every CTA adds its partial sums (FP64 atomics) to set (b & 1) before it
+  // arrives at reduction barrier b; the last CTA at barrier b clears set
+  // (b + 1) & 1, read after barrier b - 1, for the next reduction
+  double acc_d[2][SC_STRIDE];
 };
 
 struct Geometry {
@@ -121,7 +113,6 @@ struct KParams {
   // the pass reads them and clears them for the next pass
   float* acc;
   Ctrl* ctrl;
-  RSums* rsums;                // grid-wide sums (zeroed before every launch)
   const double* omega_seq;     // [max_iter] omega of each iteration
   double* trace_f;             // [max_iter + 1]
   int* trace_acc;              // [max_iter]

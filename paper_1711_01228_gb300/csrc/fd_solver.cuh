@@ -374,8 +374,7 @@ __device__ __forceinline__ void red_release_add_u32(unsigned int* a, unsigned in
 }
 
 template <class F>
-__device__ __forceinline__ bool grid_sync_reduce(Ctrl* c, RSums* rs_all, long long timeout_ns, int where,
-                                                 F&& on_last) {
+__device__ __forceinline__ bool grid_sync_reduce(Ctrl* c, long long timeout_ns, int where, F&& on_last) {
   __shared__ int s_last, s_ok;
   __syncthreads();
   unsigned int g = 0;
@@ -388,9 +387,8 @@ __device__ __forceinline__ bool grid_sync_reduce(Ctrl* c, RSums* rs_all, long lo
   if (s_last) {
     // the sums of the next reduction go to the other set: clear it (every
     // CTA read it before arriving here)
-    for (int q = threadIdx.x; q < SC_STRIDE * RSUM_GROUPS; q += blockDim.x)
-      rs_all->v[(where + 1) & 1][q / RSUM_GROUPS][q % RSUM_GROUPS][0] = 0.0;
-    on_last(&rs_all->v[where & 1][0][0][0]);
+    if (threadIdx.x < SC_STRIDE) c->acc_d[(where + 1) & 1][threadIdx.x] = 0.0;
+    on_last(c->acc_d[where & 1]);
     __syncthreads();
     if (threadIdx.x == 0) {
       st_relaxed_u32(&c->bar_count, 0u);
@@ -421,18 +419,11 @@ __device__ __forceinline__ bool grid_sync_reduce(Ctrl* c, RSums* rs_all, long lo
 template <int K>
 __device__ __forceinline__ void take_sums(Ctrl* c, const double* sums) {
   if (threadIdx.x < K) {
-    double d = 0.0;
-#pragma unroll
-    for (int g = 0; g < RSUM_GROUPS; ++g) d += __ldcg(sums + ((size_t)threadIdx.x * RSUM_GROUPS + g) * RSUM_LINE);
+    const double d = __ldcg(sums + threadIdx.x);
     const float hi = (float)d;
     c->red[threadIdx.x] = make_float2(hi, (float)(d - (double)hi));
   }
   __syncthreads();
-}
-
-// The slot of grid-wide sum k that this CTA adds to.
-__device__ __forceinline__ double* rsum_slot(double* sums, int k) {
-  return sums + ((size_t)k * RSUM_GROUPS + blockIdx.x % RSUM_GROUPS) * RSUM_LINE;
 }
 
 // After the barrier: the K reduced values, in every thread.
@@ -963,7 +954,7 @@ __device__ FD_PASS_ATTR bool pair_pass_impl(PairState* ps_io, float* acc) {
     cta_sum_multi<NS>(v, red64);
     if (tid == 0) {
 #pragma unroll
-      for (int c = 0; c < NS; ++c) atomicAdd(rsum_slot(p.rsum, c), df_to_double(v[c]));
+      for (int c = 0; c < NS; ++c) atomicAdd(p.rsum + c, df_to_double(v[c]));
     }
   }
   ps.pass += 1;
@@ -1013,7 +1004,7 @@ __device__ __forceinline__ void vertex_phase(const KParams& p, float2* red64, do
     cta_sum_multi<K>(v, red64);
     if (threadIdx.x == 0) {
 #pragma unroll
-      for (int k = 0; k < K; ++k) atomicAdd(rsum_slot(rsum, k), df_to_double(v[k]));
+      for (int k = 0; k < K; ++k) atomicAdd(rsum + k, df_to_double(v[k]));
     }
   }
 }
@@ -1214,12 +1205,12 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
   // grid barrier; the last CTA to arrive runs `red` on the grid-wide sums first
 #define FD_SYNC_RED(tag, red)                                                   \
   do {                                                                          \
-    if (!grid_sync_reduce(ctrl, p.rsums, p.bar_timeout_ns, ++nbar, red)) return;\
+    if (!grid_sync_reduce(ctrl, p.bar_timeout_ns, ++nbar, red)) return;         \
     mark(tag);                                                                  \
   } while (0)
 #define FD_SYNC(tag) FD_SYNC_RED(tag, no_reduction)
   // the grid-wide sums the next reduction barrier (index nbar + 1) collects
-#define RSUM (&p.rsums->v[(nbar + 1) & 1][0][0][0])
+#define RSUM (ctrl->acc_d[(nbar + 1) & 1])
   auto red_stress = [&](int nc) {
     return [&, nc](const double* sums) {
       if (nc == 2) take_sums<2>(ctrl, sums);
