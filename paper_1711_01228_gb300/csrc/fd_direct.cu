@@ -165,17 +165,6 @@ __device__ __forceinline__ void block_mma2(const float* At, const float* Bs, f2x
   }
 }
 
-__device__ __forceinline__ void store_acc(float* g, size_t ld, const float (&acc)[8][8], int ty, int tx, float scale) {
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    float* row = g + (size_t)own(ty, q) * ld;
-    *reinterpret_cast<float4*>(row + 4 * tx) =
-        make_float4(scale * acc[q][0], scale * acc[q][1], scale * acc[q][2], scale * acc[q][3]);
-    *reinterpret_cast<float4*>(row + 64 + 4 * tx) =
-        make_float4(scale * acc[q][4], scale * acc[q][5], scale * acc[q][6], scale * acc[q][7]);
-  }
-}
-
 __device__ __forceinline__ void cp_async16(float* smem_dst, const float* gsrc) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gsrc) : "memory");

@@ -46,3 +46,17 @@ def test_status_strings_and_defaults(libpath):
     o = api.options()
     assert (o.omega, o.strategy, o.stop, o.tol, o.max_iter, o.cg_max, o.cg_tol) == (
         0.5, 0, 0, 1e-4, 1000, 200, 1e-6)
+
+
+def test_option_defaults_match_the_header(libpath):
+    # fd_options_default is host code: the documented defaults, no GPU needed
+    from paper_1711_01228_gb300 import api
+
+    o = api.options()
+    assert (o.omega, o.strategy, o.stop, o.seed) == (0.5, api.OMEGA_FIXED, api.STOP_REL_DISP, 0)
+    assert (o.tol, o.max_iter, o.cg_max, o.cg_tol) == (1e-4, 1000, 200, 1e-6)
+    assert (o.solver, o.first_iter) == (api.SOLVER_CG, 0)
+    o2 = api.options(solver=api.SOLVER_DIRECT, first_iter=7)
+    assert (o2.solver, o2.first_iter) == (1, 7)
+    with pytest.raises(TypeError):
+        api.options(no_such_option=1)
