@@ -207,7 +207,7 @@ def run_ours(args, rank, world, local_rank):
                 acc["flops"] += st["pairs"] * (st["matvec_passes"] * FLOP_MV[args.dim] + st["stress_passes"] * FLOP_K2[args.dim])
                 acc["cg"] += st["cg_steps"]
                 acc["runs"].append((nm, om, st["iterations"], st["cg_steps"], st["final_stress"]))
-            acc["n_launch_total"] += 4 + len(oms)  # BFS, fill, row sums, + one layout kernel per run
+            acc["n_launch_total"] += 3 + len(oms)  # BFS, fill, row sums (the launch list: one each), + one layout kernel per run
             L.close()
 
     def zero():
