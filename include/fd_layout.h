@@ -12,6 +12,8 @@
  *   step H   solve L^W X^{k+1} = L^{X^k} X^k, first vertex pinned      Prop. 2.3, Eq. (2-5)
  *   SOR      X~ = (1 + omega) X^{k+1} - omega X^k, kept iff
  *            f(X~) <= f(X^{k+1})                                       Algorithm 2, Eq. (10)
+ *   per-vertex omega_i = omega m_i                                      Sec. 6
+ *   solvers  CG, or the inverse of the shifted L^W made once          Sec. 2
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -53,7 +55,7 @@ typedef enum {
   FD_ERR_CSR = 2,           /* malformed or non-symmetric CSR, bad edge length */
   FD_ERR_DISCONNECTED = 3,  /* graph not connected and disconnected_policy == 0 */
   FD_ERR_NONFINITE = 4,     /* NaN/Inf in the positions or in a computed stress */
-  FD_ERR_CG_BREAKDOWN = 5,  /* p^T L^W p <= 0 inside the linear solve */
+  FD_ERR_CG_BREAKDOWN = 5,  /* the linear solve broke down: p^T L^W p <= 0 in CG, or a pivot of fd_factor <= 0 */
   FD_ERR_CG_MAXITER = 6,    /* reserved (a solve that hits cg_max is counted, not fatal) */
   FD_ERR_TIMEOUT = 7,       /* a device-side grid barrier wait exceeded its time limit */
   FD_ERR_OOM = 8,           /* device or host allocation failed */
