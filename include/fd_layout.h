@@ -180,9 +180,11 @@ fd_status fd_energy(fd_layout* h, const float* X, double* f_out);
  * afford one.  This call allocates nothing and needs no handle: its only
  * scratch is a fixed 32 KB array in the library's device image, which every
  * GPU that loads the library keeps until the process exits.
- *   X       float32 [n][dim], device memory
- *   D       float32 [n][n], device memory, row-major; only the strictly lower
- *           triangle is read: d_ij (i < j) at D[j * n + i], each > 0
+ *   X       float32 [n][dim], memory of the current device (or managed)
+ *   D       float32 [n][n], memory of the current device (or managed),
+ *           row-major; only the strictly lower triangle is read: d_ij (i < j)
+ *           at D[j * n + i]; a pair with d_ij <= 0 counts as no pair (adds 0),
+ *           like an unstored pair of fd_energy
  *   n       1 .. FD_NOALLOC_MAX_N; larger n returns FD_ERR_ARG
  *   dim     1..3
  *   f_out   host or device double; written with f(X)
@@ -190,11 +192,13 @@ fd_status fd_energy(fd_layout* h, const float* X, double* f_out);
  *           synchronises it before returning
  * All calls on a device share the scratch array: calls whose work overlaps on
  * the GPU (two streams, or two host threads at once) race and give wrong
- * results.  The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Errors: FD_ERR_ARG (null or host X/D, sizes out
- * of range), FD_ERR_NONFINITE (non-finite result written to a host f_out),
- * FD_ERR_CUDA. */
+ * results.  Every call looks up the array's address in the current device's
+ * context (cudaGetSymbolAddress, which allocates nothing), so a device that
+ * was reset gets the new address; the first call on a device also loads the
+ * library's device code there, so make it before any stream capture.
+ * Errors: FD_ERR_ARG (null pointer, X or D in host memory or on another
+ * device, sizes out of range), FD_ERR_NONFINITE (the stress is not finite;
+ * the value is still written), FD_ERR_CUDA. */
 fd_status fd_energy_noalloc(const float* X, const float* D, int32_t n, int32_t dim, double* f_out,
                             void* cuda_stream);
 

@@ -37,12 +37,22 @@ shifted_inverse        solver of Eq. (2-5) with L^W fixed        closed forms on
 extrapolate            line 5 of Algorithm 2, Eq. (10); the   m = 1 and m = c reduce to Eq. (10) with omega
                        per-vertex omega_i of Sec. 6           and omega c; m = 0 gives Algorithm 1; candidate
                                                               derived by hand on K2; relabelling equivariance
+criterion              termination of Algorithms 1 and 2      values worked by hand (two vertices, a path of
+                       (the library's reading, below)         three, 4 -> 3); invariance under separate
+                                                              translations and common rotation / scaling; the
+                                                              REL_DISP sequence decays at the rate 1 -
+                                                              lambda_min of Thm 3.2; sor_run's bookkeeping
+force_abs /            sum_j |term| of the rows of -1/2 grad  = |F| with one term (K2) and for a row of one
+force_row_abs          of Eq. (1) (a tolerance scale)         sign; >= |F| (triangle inequality), strictly for
+                                                              mixed signs
+stress_stream          Eq. (1), rows streamed by BFS          equals `stress` on a stored D; a split over
+                                                              processes equals the serial sum to rounding
 =====================  ====================================  ===============================================
 
 The termination rule is not defined by the paper ("until some termination
-conditions were satisfied", Algorithms 1 and 2); the two rules here are the
-library's documented readings (relative displacement of centred layouts, or
-relative stress decrease).  They are pinned only by their definitions.
+conditions were satisfied", Algorithms 1 and 2; Table 1 quotes a relative
+error per data set); the two rules here are the library's readings (relative
+displacement of centred layouts, or relative stress decrease).
 """
 from __future__ import annotations
 
@@ -96,6 +106,11 @@ def _lib():
         lib.orc_rhs_row.argtypes = [i32, i32, P, i32, P, P]
         lib.orc_stress_stream.argtypes = [i32, i32, P, P, P, ctypes.c_double, ctypes.POINTER(i32)]
         lib.orc_stress_stream.restype = ctypes.c_double
+        lib.orc_stress_stream_rows.argtypes = [i32, i32, P, P, P, ctypes.c_double, i32, i32, ctypes.POINTER(i32)]
+        lib.orc_stress_stream_rows.restype = ctypes.c_double
+        lib.orc_force_row_abs.argtypes = [i32, i32, P, i32, P, P]
+        lib.orc_stress_stream_rows_multi.argtypes = [i32, i32, P, P, P, P, ctypes.c_double, i32, i32, P,
+                                                     ctypes.POINTER(i32)]
         _lib_handle = lib
     return _lib_handle
 
@@ -182,6 +197,24 @@ def force_row(X, i: int, drow) -> np.ndarray:
     return out
 
 
+def force_row_abs(X, i: int, drow) -> np.ndarray:
+    """Per coordinate c, A_ic = sum_j |w_ij (d_ij / r_ij - 1)(x_ic - x_jc)|: the
+    magnitude of the terms that make up F_ic (|F_ic| <= A_ic).  Rounding in
+    any summation of the row is bounded relative to A_ic, so per-element force
+    tolerances are stated against it."""
+    X, dr = _f64(X), _f64(drow)
+    n, dim = X.shape
+    out = np.zeros(dim)
+    _lib().orc_force_row_abs(n, dim, _p(X), int(i), _p(dr), _p(out))
+    return out
+
+
+def force_abs(X, D) -> np.ndarray:
+    """force_row_abs for every row of a dense D: [n, dim]."""
+    X, D = _f64(X), _f64(D)
+    return np.stack([force_row_abs(X, i, D[i]) for i in range(X.shape[0])])
+
+
 def rhs_row(X, i: int, drow) -> np.ndarray:
     X, dr = _f64(X), _f64(drow)
     n, dim = X.shape
@@ -190,16 +223,86 @@ def rhs_row(X, i: int, drow) -> np.ndarray:
     return out
 
 
-def stress_stream(X, row_ptr, col_idx, dfill: float = -1.0) -> float:
-    """Eq. (1) for unit-edge graphs, one BFS per row instead of a stored D."""
-    X = _f64(X)
-    rp, ci = _i32(row_ptr), _i32(col_idx)
+def _stress_rows(X, rp, ci, dfill, i0, i1) -> float:
     n, dim = X.shape
     st = ctypes.c_int(0)
-    f = _lib().orc_stress_stream(n, dim, _p(X), _p(rp), _p(ci), float(dfill), ctypes.byref(st))
+    f = _lib().orc_stress_stream_rows(n, dim, _p(X), _p(rp), _p(ci), float(dfill), int(i0), int(i1),
+                                      ctypes.byref(st))
     if st.value != 0:
         raise ValueError(f"stress_stream status {st.value}")
     return float(f)
+
+
+_POOL_ARGS = None
+
+
+def _pool_init(*args):
+    global _POOL_ARGS
+    _POOL_ARGS = args
+
+
+def _stress_rows_task(rng):
+    X, rp, ci, dfill = _POOL_ARGS
+    return _stress_rows(X, rp, ci, dfill, rng[0], rng[1])
+
+
+def _row_ranges(n, workers):
+    cuts = np.linspace(0, n, 8 * workers + 1).astype(int)
+    return [(int(a), int(b)) for a, b in zip(cuts[:-1], cuts[1:]) if b > a]
+
+
+def _stress_rows_multi(Xs, rp, ci, dfill, i0, i1) -> np.ndarray:
+    Xs = [_f64(X) for X in Xs]
+    n = Xs[0].shape[0]
+    dims = np.array([X.shape[1] for X in Xs], dtype=np.int32)
+    ptrs = (ctypes.c_void_p * len(Xs))(*[X.ctypes.data for X in Xs])
+    out = np.zeros(len(Xs))
+    st = ctypes.c_int(0)
+    _lib().orc_stress_stream_rows_multi(n, len(Xs), _p(dims), ptrs, _p(rp), _p(ci), float(dfill), int(i0), int(i1),
+                                        _p(out), ctypes.byref(st))
+    if st.value != 0:
+        raise ValueError(f"stress_stream status {st.value}")
+    return out
+
+
+def _stress_rows_multi_task(rng):
+    Xs, rp, ci, dfill = _POOL_ARGS
+    return _stress_rows_multi(Xs, rp, ci, dfill, rng[0], rng[1])
+
+
+def stress_stream_multi(Xs, row_ptr, col_idx, dfill: float = -1.0, workers: int = 1) -> np.ndarray:
+    """stress_stream of several layouts of one graph (any dimensions), one BFS
+    per row for all of them; rows split over `workers` spawned processes as
+    in stress_stream."""
+    Xs = [_f64(X) for X in Xs]
+    rp, ci = _i32(row_ptr), _i32(col_idx)
+    n = Xs[0].shape[0]
+    if workers <= 1 or n < 4096:
+        return _stress_rows_multi(Xs, rp, ci, dfill, 0, n)
+    import multiprocessing as mp
+
+    with mp.get_context("spawn").Pool(workers, initializer=_pool_init, initargs=(Xs, rp, ci, float(dfill))) as pool:
+        parts = pool.map(_stress_rows_multi_task, _row_ranges(n, workers), chunksize=1)
+    return np.sum(parts, axis=0)
+
+
+def stress_stream(X, row_ptr, col_idx, dfill: float = -1.0, workers: int = 1) -> float:
+    """Eq. (1) for unit-edge graphs, one BFS per row instead of a stored D.
+
+    Eq. (1) sums over the rows i of sum_{j > i}; with workers > 1 the rows are
+    split into ranges evaluated by that many processes (started with the
+    'spawn' method, so that a process holding a GPU context can call this)
+    and the parts are added (only the order of the FP64 additions differs)."""
+    X = _f64(X)
+    rp, ci = _i32(row_ptr), _i32(col_idx)
+    n = X.shape[0]
+    if workers <= 1 or n < 4096:
+        return _stress_rows(X, rp, ci, dfill, 0, n)
+    import multiprocessing as mp
+
+    with mp.get_context("spawn").Pool(workers, initializer=_pool_init, initargs=(X, rp, ci, float(dfill))) as pool:
+        parts = pool.map(_stress_rows_task, _row_ranges(n, workers), chunksize=1)
+    return float(sum(parts))
 
 
 # --------------------------------------------------------------------------

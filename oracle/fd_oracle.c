@@ -220,6 +220,24 @@ void orc_force_row(int n, int dim, const double *X, int i, const double *drow, d
   }
 }
 
+/* Magnitude of the terms of row i of F, per coordinate:
+ * A_ic = sum_{j != i} |w_ij (d_ij/||x_i - x_j|| - 1)(x_ic - x_jc)| (coincident
+ * pairs: |w_ij (x_ic - x_jc)| = 0).  |F_ic| <= A_ic, with equality when every
+ * term of the row has one sign; it is the scale of the rounding error of any
+ * summation of the row's terms, so tolerances on F_ic are stated against it. */
+void orc_force_row_abs(int n, int dim, const double *X, int i, const double *drow, double *Ai) {
+  for (int c = 0; c < dim; ++c) Ai[c] = 0.0;
+  for (int j = 0; j < n; ++j) {
+    if (j == i) continue;
+    double r = orc_dist(dim, X, i, j);
+    double d = drow[j];
+    double w = 1.0 / (d * d);
+    double coef = (r == 0.0) ? -w : w * (d / r - 1.0);
+    for (int c = 0; c < dim; ++c)
+      Ai[c] += fabs(coef * (X[(size_t)i * dim + c] - X[(size_t)j * dim + c]));
+  }
+}
+
 /* Row i of b = L^X X given row i of D. */
 void orc_rhs_row(int n, int dim, const double *X, int i, const double *drow, double *bi) {
   for (int c = 0; c < dim; ++c) bi[c] = 0.0;
@@ -235,10 +253,12 @@ void orc_rhs_row(int n, int dim, const double *X, int i, const double *drow, dou
 }
 
 /* Stress of Eq. (1) without storing D: one BFS per source row (unit edges),
- * then the row's pairs j > i.  Disconnected pairs take dfill (the caller
- * passes max finite d + 1, or a negative value to report an error). */
-double orc_stress_stream(int n, int dim, const double *X, const int *row_ptr,
-                         const int *col_idx, double dfill, int *status) {
+ * then the row's pairs j > i, for the rows i0 <= i < i1 (the whole stress is
+ * the sum over all rows; a caller may split the rows between processes and
+ * add the parts).  Disconnected pairs take dfill (the caller passes max
+ * finite d + 1, or a negative value to report an error). */
+double orc_stress_stream_rows(int n, int dim, const double *X, const int *row_ptr,
+                              const int *col_idx, double dfill, int i0, int i1, int *status) {
   int *q = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
   int *di = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
   *status = ORC_OK;
@@ -248,7 +268,7 @@ double orc_stress_stream(int n, int dim, const double *X, const int *row_ptr,
     return NAN;
   }
   double f = 0.0;
-  for (int i = 0; i < n; ++i) {
+  for (int i = i0; i < i1; ++i) {
     orc_bfs(n, row_ptr, col_idx, i, di, q);
     for (int j = i + 1; j < n; ++j) {
       double d;
@@ -269,4 +289,50 @@ double orc_stress_stream(int n, int dim, const double *X, const int *row_ptr,
   }
   free(q); free(di);
   return f;
+}
+
+/* Stress of Eq. (1) of nl layouts of the same graph (layout l: dims[l]
+ * coordinates, Xs[l] row-major), rows i0 <= i < i1, one BFS per row shared by
+ * all layouts (the distances do not depend on the layout): f_out[l] receives
+ * layout l's part. */
+void orc_stress_stream_rows_multi(int n, int nl, const int *dims, const double *const *Xs,
+                                  const int *row_ptr, const int *col_idx, double dfill, int i0,
+                                  int i1, double *f_out, int *status) {
+  int *q = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+  int *di = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+  *status = ORC_OK;
+  for (int l = 0; l < nl; ++l) f_out[l] = 0.0;
+  if (!q || !di) {
+    free(q); free(di);
+    *status = ORC_ERR_OOM;
+    return;
+  }
+  for (int i = i0; i < i1; ++i) {
+    orc_bfs(n, row_ptr, col_idx, i, di, q);
+    for (int j = i + 1; j < n; ++j) {
+      double d;
+      if (di[j] < 0) {
+        if (dfill < 0) {
+          *status = ORC_ERR_DISCONNECTED;
+          free(q); free(di);
+          return;
+        }
+        d = dfill;
+      } else {
+        d = (double)di[j];
+      }
+      double w = 1.0 / (d * d);
+      for (int l = 0; l < nl; ++l) {
+        double e = orc_dist(dims[l], Xs[l], i, j) - d;
+        f_out[l] += w * e * e;
+      }
+    }
+  }
+  free(q); free(di);
+}
+
+/* The whole stress of Eq. (1), streamed row by row (all rows). */
+double orc_stress_stream(int n, int dim, const double *X, const int *row_ptr,
+                         const int *col_idx, double dfill, int *status) {
+  return orc_stress_stream_rows(n, dim, X, row_ptr, col_idx, dfill, 0, n, status);
 }

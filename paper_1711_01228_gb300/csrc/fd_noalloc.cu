@@ -18,8 +18,6 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include <mutex>
-
 #include "fd_layout.h"
 
 namespace {
@@ -29,11 +27,6 @@ constexpr int NA_MAX_BLOCKS = FD_NOALLOC_MAX_N / NA_THREADS;
 
 // Per-block partial stresses, then the final sum in the last slot.
 static __device__ __align__(256) double g_noalloc_scratch[NA_MAX_BLOCKS + 1];
-
-// Device address of g_noalloc_scratch, looked up once per device.
-constexpr int NA_MAX_DEVICES = 64;
-double* g_scratch_addr[NA_MAX_DEVICES] = {nullptr};
-std::mutex g_scratch_mu;
 
 __device__ __forceinline__ float na_kahan(float& s, float& c, float v) {
   float y = v - c;
@@ -45,7 +38,9 @@ __device__ __forceinline__ float na_kahan(float& s, float& c, float v) {
 
 // Thread i sums w_ij (||x_i - x_j|| - d_ij)^2 over j > i (Eq. (1)), reading
 // d_ij from the strictly lower triangle D[j * n + i] so that a warp's loads
-// are contiguous.  Block partials are FP64, summed in a fixed order.
+// are contiguous.  A pair with d_ij <= 0 is no pair (weight 0), as a zero
+// code is in fd_energy's distance tiles.  Block partials are FP64, summed in
+// a fixed order.
 __global__ void __launch_bounds__(NA_THREADS) na_stress_partials(const float* __restrict__ X,
                                                                  const float* __restrict__ D, int n, int dim,
                                                                  double* partials) {
@@ -62,6 +57,7 @@ __global__ void __launch_bounds__(NA_THREADS) na_stress_partials(const float* __
         r2 = fmaf(t, t, r2);
       }
       const float dij = D[(size_t)j * n + i];
+      if (!(dij > 0.f)) continue;
       const float e = sqrtf(r2) - dij;
       na_kahan(s, c, e * e / (dij * dij));
     }
@@ -88,35 +84,31 @@ __global__ void __launch_bounds__(NA_THREADS) na_stress_final(const double* part
   if (threadIdx.x == 0) *out = red[0];
 }
 
-bool na_on_device(const void* p) {
+// 1: device memory of device `dev` (or managed memory, reachable from every
+// device); 0: host memory, another device's memory, or not a CUDA pointer.
+int na_on_device(const void* p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return 0;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return 1;
+  return (a.type == cudaMemoryTypeDevice && a.device == dev) ? 1 : 0;
 }
 
-// Device address of the scratch array for the current device (set-up on the
-// first call per device).
+// Device address of the scratch array in the current device's context.  The
+// address is looked up on every call (a host-side lookup that allocates
+// nothing): after cudaDeviceReset, or anything else that recreates the
+// context, the library's device image is loaded again and the array may sit
+// elsewhere, so a cached address could point at freed memory.
 fd_status na_scratch(double** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) {
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || p == nullptr) {
     cudaGetLastError();
     return FD_ERR_CUDA;
   }
-  if (dev < 0 || dev >= NA_MAX_DEVICES) return FD_ERR_CUDA;
-  std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (g_scratch_addr[dev] == nullptr) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || p == nullptr) {
-      cudaGetLastError();
-      return FD_ERR_CUDA;
-    }
-    g_scratch_addr[dev] = static_cast<double*>(p);
-  }
-  *out = g_scratch_addr[dev];
+  *out = static_cast<double*>(p);
   return FD_OK;
 }
 
@@ -126,23 +118,34 @@ extern "C" fd_status fd_energy_noalloc(const float* X, const float* D, int32_t n
                                        void* cuda_stream) {
   if (!X || !D || !f_out || n < 1 || dim < 1 || dim > 3) return FD_ERR_ARG;
   if (n > FD_NOALLOC_MAX_N) return FD_ERR_ARG;  // more blocks than the scratch array holds
-  if (!na_on_device(X) || !na_on_device(D)) return FD_ERR_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return FD_ERR_CUDA;
+  }
+  // X and D must be reachable by the kernels on the current device
+  if (!na_on_device(X, dev) || !na_on_device(D, dev)) return FD_ERR_ARG;
   double* scratch = nullptr;
   fd_status s = na_scratch(&scratch);
   if (s != FD_OK) return s;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   const int nblocks = (n + NA_THREADS - 1) / NA_THREADS;
-  const bool dev_out = na_on_device(f_out);
+  // a device f_out is written by the kernel; anything else (host memory, or
+  // another device's memory) gets the value copied from the scratch array
+  const bool dev_out = na_on_device(f_out, dev) != 0;
   double* result = dev_out ? f_out : scratch + NA_MAX_BLOCKS;
   na_stress_partials<<<nblocks, NA_THREADS, 0, st>>>(X, D, n, dim, scratch);
   na_stress_final<<<1, NA_THREADS, 0, st>>>(scratch, nblocks, result);
+  // the value is also read back to the stack to check it is finite
+  double f = 0.0;
   cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess && !dev_out) e = cudaMemcpyAsync(f_out, result, sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&f, result, sizeof(double), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return FD_ERR_CUDA;
   }
-  if (!dev_out && !(*f_out == *f_out && *f_out - *f_out == 0.0)) return FD_ERR_NONFINITE;
+  if (!dev_out) *f_out = f;
+  if (!(f == f && f - f == 0.0)) return FD_ERR_NONFINITE;
   return FD_OK;
 }

@@ -104,3 +104,25 @@ def test_bfs_row_and_stream():
         assert np.array_equal(oracle.bfs_row(rp, ci, s), D[s].astype(np.int32))
     X = synth.initial_layout(150, 2, seed=1)
     assert oracle.stress_stream(X, rp, ci) == pytest.approx(oracle.stress(X, D), rel=1e-12)
+
+
+def test_stream_split_over_processes():
+    # the rows of Eq. (1) split between spawned processes sum to the serial stress
+    rp, ci = synth.erdos_renyi(4500, 6.0, seed=3)
+    X = synth.initial_layout(4500, 2, seed=2)
+    st, D = oracle.apsp(rp, ci, policy=1)
+    fill = float(D.max())
+    f1 = oracle.stress_stream(X, rp, ci, fill)
+    f2 = oracle.stress_stream(X, rp, ci, fill, workers=2)
+    assert f2 == pytest.approx(f1, rel=1e-12)
+    assert f1 == pytest.approx(oracle.stress(X, D), rel=1e-12)
+
+
+def test_stream_several_layouts_share_rows():
+    # one BFS per row for a 2-D and a 3-D layout: each equals its own stress
+    rp, ci = synth.delaunay(300, seed=4)
+    st, D = oracle.apsp(rp, ci)
+    X2, X3 = synth.initial_layout(300, 2, seed=1), synth.initial_layout(300, 3, seed=2)
+    f = oracle.stress_stream_multi([X2, X3], rp, ci)
+    assert f[0] == pytest.approx(oracle.stress(X2, D), rel=1e-12)
+    assert f[1] == pytest.approx(oracle.stress(X3, D), rel=1e-12)

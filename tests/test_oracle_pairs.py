@@ -158,3 +158,27 @@ def test_coincident_vertices():
     # vertex 0 only feels vertex 2 (d = 2): w d (x0 - x2)/r = (1/2)(-1, 0)
     assert np.allclose(b[0], [-0.5, 0.0])
     assert oracle.stress(X, D) == pytest.approx(1.0 + 0.0 + (1.0 - 2.0) ** 2 / 4.0)
+
+
+def test_force_magnitude_bounds_and_equalities():
+    # A_ic = sum_j |w_ij (d_ij/r_ij - 1)(x_ic - x_jc)|, the scale of the
+    # per-element force tolerances.  Pins: with one term (K2) A = |F|; |F| <= A
+    # always (triangle inequality), strictly for a row whose terms mix signs;
+    # A = |F| for a row whose terms share one sign.
+    D2 = _dense_D(*synth.path(2))
+    X2 = np.array([[0.1, 0.3], [1.7, -0.2]])
+    assert np.allclose(oracle.force_abs(X2, D2), np.abs(oracle.forces(X2, D2)), rtol=1e-15, atol=0)
+    D = _dense_D(*synth.delaunay(40, seed=6))
+    X = np.random.default_rng(6).random((40, 2)) * 3.0
+    A, F = oracle.force_abs(X, D), oracle.forces(X, D)
+    assert np.all(np.abs(F) <= A * (1 + 1e-12))
+    assert np.any(np.abs(F) < 0.5 * A)
+    # vertex 0 at the origin, the others on the positive x axis beyond their
+    # ideal distances: every term of row 0 is w (d/r - 1)(0 - x_j) > 0
+    n = 6
+    Dp = _dense_D(*synth.path(n))
+    Xl = np.zeros((n, 2))
+    Xl[1:, 0] = 2.0 * np.arange(1, n) + 0.5
+    A0 = oracle.force_row_abs(Xl, 0, Dp[0])
+    F0 = oracle.force_row(Xl, 0, Dp[0])
+    assert F0[0] > 0 and A0[0] == pytest.approx(F0[0], rel=1e-15) and A0[1] == 0.0

@@ -208,3 +208,99 @@ def test_enumerate_strategy_is_argmin():
     assert fn == pytest.approx(min(fs), rel=1e-15)
     assert om == 0.5 * int(np.argmin(fs))
     assert fn <= fZ
+
+
+# ---------------------------------------------------------------------------
+# The termination criterion.  The paper leaves the rule open ("until some
+# termination conditions were satisfied", Algorithms 1 and 2; Table 1 quotes a
+# relative error per data set); the library's two readings are the relative
+# displacement of centred layouts and the relative decrease of the stress.
+# Pins: values worked by hand, the invariances a displacement measure of
+# layouts defined up to a similarity must have, the linear rate of
+# Theorem 3.2 that the displacement inherits, and the run's bookkeeping
+# (which layouts and stresses enter).  A criterion without centring, divided
+# by the old layout's norm or fed the un-accepted stress fails one of them.
+# ---------------------------------------------------------------------------
+
+def test_criterion_rel_disp_by_hand():
+    # two vertices: (0,0),(2,0) -> (1,0),(2,0).  Centred: (-1,0),(1,0) and
+    # (-0.5,0),(0.5,0); displacement sqrt(0.5) over sqrt(0.5) = 1.
+    # (without centring: 1/sqrt(5); divided by the old norm: 0.5)
+    Xo = np.array([[0.0, 0.0], [2.0, 0.0]])
+    Xn = np.array([[1.0, 0.0], [2.0, 0.0]])
+    assert oracle.criterion(oracle.STOP_REL_DISP, Xo, Xn, 0.0, 0.0) == pytest.approx(1.0, rel=1e-15)
+    # a path of three: (0,0),(1,0),(2,0) -> (0,0),(1,1),(2,0).  Means (1,0) and
+    # (1,1/3); the centred difference is (0,-1/3),(0,2/3),(0,-1/3), squared norm
+    # 2/3; the centred new layout has squared norm 8/3; sqrt(1/4) = 1/2.
+    Xo = np.array([[0.0, 0.0], [1.0, 0.0], [2.0, 0.0]])
+    Xn = np.array([[0.0, 0.0], [1.0, 1.0], [2.0, 0.0]])
+    assert oracle.criterion(oracle.STOP_REL_DISP, Xo, Xn, 0.0, 0.0) == pytest.approx(0.5, rel=1e-15)
+    # a layout collapsed to one point has nothing left to move: 0
+    assert oracle.criterion(oracle.STOP_REL_DISP, Xo, np.ones((3, 2)), 0.0, 0.0) == 0.0
+
+
+def test_criterion_rel_stress_by_hand():
+    # (f_k - f_{k+1}) / f_k: 4 -> 3 gives 1/4 (divided by the new stress: 1/3)
+    assert oracle.criterion(oracle.STOP_REL_STRESS, None, None, 4.0, 3.0) == 0.25
+    assert oracle.criterion(oracle.STOP_REL_STRESS, None, None, 0.0, 0.0) == 0.0
+    with pytest.raises(ValueError):
+        oracle.criterion(7, None, None, 1.0, 1.0)
+
+
+def test_criterion_rel_disp_invariances():
+    # the layouts are defined up to translation (the pinning of Sec. 2 moves
+    # them every H step), so the measure ignores a separate translation of
+    # each; a common rotation or scaling of both leaves it unchanged too
+    rng = np.random.default_rng(5)
+    Xo = rng.random((17, 2))
+    Xn = Xo + 0.05 * rng.standard_normal((17, 2))
+    c0 = oracle.criterion(oracle.STOP_REL_DISP, Xo, Xn, 0.0, 0.0)
+    c1 = oracle.criterion(oracle.STOP_REL_DISP, Xo + np.array([3.0, -1.0]), Xn + np.array([-7.0, 2.5]), 0.0, 0.0)
+    th = 0.7
+    Q = np.array([[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]])
+    c2 = oracle.criterion(oracle.STOP_REL_DISP, Xo @ Q.T, Xn @ Q.T, 0.0, 0.0)
+    c3 = oracle.criterion(oracle.STOP_REL_DISP, 4.0 * Xo, 4.0 * Xn, 0.0, 0.0)
+    assert c1 == pytest.approx(c0, rel=1e-12)
+    assert c2 == pytest.approx(c0, rel=1e-12)
+    assert c3 == pytest.approx(c0, rel=1e-12)
+    # but not under a change of one layout's scale alone
+    assert abs(oracle.criterion(oracle.STOP_REL_DISP, Xo, 2.0 * Xn, 0.0, 0.0) - c0) > 0.1
+
+
+def test_criterion_run_bookkeeping():
+    # sor_run measures each iteration between consecutive accepted layouts
+    # (REL_DISP) and between consecutive accepted stresses (REL_STRESS), and
+    # stops at the first iteration whose criterion is below tol
+    D = _D(*synth.delaunay(40, seed=8))
+    X0 = synth.initial_layout(40, 2, seed=8).astype(np.float64)
+    solver = oracle.PinnedSolver(D)
+    r = oracle.sor_run(D, X0, omega=1.0, tol=0.0, max_iter=12, solver=solver)
+    rs = oracle.sor_run(D, X0, omega=1.0, tol=0.0, max_iter=12, solver=solver, stop=oracle.STOP_REL_STRESS)
+    X, f = X0.copy(), oracle.stress(X0, D)
+    saw_accept_below_h = False
+    for k in range(12):
+        Xn, fn, acc, _, fZ = oracle.sor_step(X, D, 1.0, oracle.OMEGA_FIXED, solver)
+        assert r.trace_crit[k] == oracle.criterion(oracle.STOP_REL_DISP, X, Xn, f, fn)
+        assert rs.trace_crit[k] == (f - fn) / f
+        saw_accept_below_h |= acc and fn < fZ
+        X, f = Xn, fn
+    assert saw_accept_below_h  # the accepted stress, not f(H(X^k)), enters REL_STRESS
+    tol = 0.5 * (r.trace_crit[5] + r.trace_crit[6])
+    first = next(k for k, c in enumerate(r.trace_crit) if c < tol)
+    r2 = oracle.sor_run(D, X0, omega=1.0, tol=tol, max_iter=12, solver=solver)
+    assert r2.iterations == first + 1 and r2.converged
+
+
+def test_criterion_decays_at_theorem_3_2_rate():
+    # Algorithm 1 near x*: X^{k+1} - X^k shrinks by 1 - lambda_min per step
+    # (Theorem 3.2), and the centred norm of X^{k+1} tends to that of x*, so
+    # the REL_DISP criterion decays at the same rate
+    D = _D(*synth.delaunay(9, seed=4))
+    X0 = synth.initial_layout(9, 2, seed=4).astype(np.float64)
+    pert = np.random.default_rng(0).standard_normal((9, 2))
+    lam, steps, J = _theorem_3_2(D, X0, pert, nsteps=2, amp=1e-3)
+    rate = 1.0 - lam[1]
+    xs = oracle.sor_run(D, X0, omega=0.0, tol=1e-15, max_iter=4000).X
+    r = oracle.sor_run(D, xs + 1e-3 * pert, omega=0.0, tol=0.0, max_iter=110)
+    c = np.array(r.trace_crit)
+    assert (c[91:110] / c[90:109]).mean() == pytest.approx(rate, abs=1e-3)
