@@ -1,17 +1,29 @@
 #!/usr/bin/env python3
 """Benchmark of the SOR stress-majorization layout path on GB300.
 
-Workload (graph-drawing benchmark stand-ins, 2-D, X^0 uniform in [0,1]^2):
-Erdos-Renyi n=10,000 mean degree 6, Delaunay mesh of 20,000 uniform points,
-random binary tree n=16,383.  One step lays out every graph of the workload:
-ideal distances from the CSR (multi-source BFS), then Algorithm 2 to
-convergence (relative displacement 1e-4, at most 1000 iterations) at each
-omega of the step's sweep.  The default sweep is the classical factor 1.5
-(the paper's omega = 0.5); ``--sweep`` runs the classical factors 1.0 .. 1.9.
+Headline workload (the largest single-GPU configuration): a Barabasi-Albert
+graph, n = 200,000, m = 3 (about 6e5 edges), laid out in 2-D and in 3-D,
+X^0 uniform in the unit square / cube (seed 0), 200 iterations of
+Algorithm 2 at omega = 0.5 (classical 1.5).  Its distance codes take 20 GB
+per layout, far more than the 129 MB L2, so every all-pairs pass streams them
+from HBM (no L2 flush is needed between steps).
 
-Metric: unordered pair interactions per second over the whole step (every
-all-pairs pass counts n(n-1)/2 pairs: each CG matvec, and each stress/RHS
-evaluation of a candidate layout); SOR iterations per second beside it.
+One step is ITERS_PER_STEP (10) iterations of each layout, continuing the
+trajectory of the step before (fd_run resumed with first_iter), so that the
+default 20 timed steps are exactly the configuration's 200 iterations.  The
+ideal distances (multi-source BFS over the CSR) are computed once per layout
+before the steps and reported beside them (``apsp``); the end-to-end figure
+(``e2e``) includes them.
+
+Metric: unordered pair interactions per second (every all-pairs pass counts
+n(n-1)/2 pairs: each L^W matvec, and each stress/RHS evaluation of a
+candidate layout); SOR iterations per second beside it.
+
+Sections run once after the timed steps: the benchmark-set stand-ins (ER
+n=10,000, Delaunay n=20,000, random binary tree n=16,383) at classical omega
+1.0 ... 1.9, the batched form (4096 graphs), the differentiable form, the
+direct solver and per-vertex omega; every result carries its error against
+the FP64 oracle where the oracle can compute it.
 """
 from __future__ import annotations
 
@@ -31,7 +43,11 @@ sys.path.insert(0, ROOT)
 
 from paper_1711_01228_gb300 import synth  # noqa: E402
 
-WORKLOAD = ("er10k", "delaunay20k", "tree16k")
+WORKLOAD = ("er10k", "delaunay20k", "tree16k")   # benchmark-set stand-ins (sweep section)
+HEADLINE = "ba200k"                               # Barabasi-Albert n=200,000, m=3
+HEADLINE_DIMS = (2, 3)
+HEADLINE_ITERS = 200
+ITERS_PER_STEP = 10
 FLOP_K2 = {1: 13, 2: 19, 3: 25}   # stress + L^X X per unordered pair per candidate
 FLOP_MV = {1: 4, 2: 8, 3: 12}     # L^W p per unordered pair
 
@@ -160,6 +176,86 @@ def omegas(sweep: bool):
     return [round(0.1 * k, 1) for k in range(10)] if sweep else [0.5]
 
 
+def fp32_peak_tflops(dev):
+    """FP32 CUDA-core peak: SMs x 128 lanes x 2 flop x the measured maximum SM clock."""
+    import torch
+
+    peaks, src = _peaks()
+    clk = peaks.get("sm_max_mhz", 2070.0)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    return sms * 128 * 2 * clk * 1e6 / 1e12, sms, clk, src
+
+
+TAG_NAMES = {4: "rhs0", 5: "lw_x0", 6: "lw_u0", 7: "lw_cg", 8: "candidates", 9: "vertex_phase", 10: "dense_apply"}
+
+
+def pass_profile(L, X, dim, iters, opts, code_bytes_total, pairs, fp32_peak, hbm_peak):
+    """Per-pass roofline of the layout kernel from its %globaltimer marks:
+    one extra run of `iters` iterations from X (a copy) with the timeline on.
+    A pass's duration runs from the mark before it to its own mark (grid
+    barrier included).  Candidate passes (stress + L^X X of the two candidate
+    layouts) are rated against the FP32 peak; L^W passes against the HBM copy
+    bandwidth (their 1-byte codes) and the FP32 peak."""
+    import ctypes
+
+    from paper_1711_01228_gb300 import api
+
+    cap = 200000
+    api.lib().fd_timeline_enable(L._h, cap)
+    Xc = X.clone()
+    L.run(Xc, max_iter=iters, **opts)
+    buf = np.zeros(2 * cap)
+    cnt = ctypes.c_int32()
+    api.lib().fd_timeline_read(L._h, buf.ctypes.data, cap, ctypes.byref(cnt))
+    api.lib().fd_timeline_enable(L._h, 0)
+    tl = buf[:2 * cnt.value].reshape(-1, 2)
+    dur = {}
+    for (t0, a), (tag, b) in zip(tl[:-1], tl[1:]):
+        dur.setdefault(int(tag), []).append((b - a) * 1e-9)
+    out = {}
+    for tag, ds in sorted(dur.items()):
+        name = TAG_NAMES.get(tag, str(tag))
+        mean_s = float(np.mean(ds))
+        e = {"count": len(ds), "mean_us": mean_s * 1e6, "total_ms": float(np.sum(ds)) * 1e3}
+        if tag in (5, 6, 7):
+            e["flop_per_pair"] = FLOP_MV[dim]
+            e["achieved_tflops"] = pairs * FLOP_MV[dim] / mean_s / 1e12
+            e["frac_fp32"] = e["achieved_tflops"] / fp32_peak
+            e["code_gbs"] = code_bytes_total / mean_s / 1e9
+            e["frac_hbm"] = e["code_gbs"] / hbm_peak
+        elif tag == 8:
+            e["flop_per_pair"] = 2 * FLOP_K2[dim]
+            e["achieved_tflops"] = pairs * 2 * FLOP_K2[dim] / mean_s / 1e12
+            e["frac_fp32"] = e["achieved_tflops"] / fp32_peak
+            e["code_gbs"] = code_bytes_total / mean_s / 1e9
+            e["frac_hbm"] = e["code_gbs"] / hbm_peak
+        out[name] = e
+    return out
+
+
+def sampled_force_error(L_forces, X, rp, ci, rows, fill=-1.0):
+    """Largest |F_ic - F_ic^oracle| / A_ic over sampled rows (A_ic: the
+    magnitude of the row's terms, oracle.force_row_abs) and the Frobenius
+    relative error over the sample."""
+    import oracle
+
+    F = np.asarray(L_forces, dtype=np.float64)
+    Xd = np.asarray(X, dtype=np.float64)
+    worst, num, den = 0.0, 0.0, 0.0
+    for k, i in enumerate(rows):
+        d = oracle.bfs_row(rp, ci, int(i)).astype(np.float64)
+        if fill > 0:
+            d[d < 0] = fill
+        ref = oracle.force_row(Xd, int(i), d)
+        A = oracle.force_row_abs(Xd, int(i), d)
+        err = np.abs(F[k] - ref)
+        worst = max(worst, float(np.max(err / np.maximum(A, 1e-300))))
+        num += float(np.sum(err ** 2))
+        den += float(np.sum(ref ** 2))
+    return {"max_elem_err_over_row_magnitude": worst, "frobenius_rel": (num / den) ** 0.5 if den > 0 else 0.0,
+            "rows": int(len(rows))}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -170,90 +266,124 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
-    inputs = make_inputs(args.workload.split(","), args.dim)
-    oms = omegas(args.sweep)
-    dev_inputs = [(nm, torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev), torch.from_numpy(x0).to(dev))
-                  for nm, rp, ci, x0 in inputs]
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
-    opts = dict(tol=1e-4, max_iter=args.max_iter, stop=api.STOP_REL_DISP)
-
-    def one_step(acc, host=False):
-        for (nm, rp, ci, x0), (_, rpd, cid, x0d) in zip(inputs, dev_inputs):
-            if host:
-                L = api.Layout(rp, ci, dim=args.dim, disconnected_policy=1)
-            else:
-                L = api.Layout(rpd, cid, dim=args.dim, disconnected_policy=1, stream=stream.cuda_stream)
-            info = L.info()
-            acc["apsp_ms"] += info["apsp_ms"]
-            n_g, m2 = len(rp) - 1, int(rp[-1])
-            # edge pass: per pass over the edge list 20 B per vertex (row_ptr, reached word, next word)
-            # and 12 B per edge end (col_idx, the neighbour's frontier word); 1 B per pair written once
-            acc["apsp_bytes"] += info["bfs_sweeps"] * (20.0 * n_g + 12.0 * m2) + 0.5 * n_g * (n_g - 1)
-            acc["h2d"] += rp.nbytes + ci.nbytes
-            for om in oms:
-                if host:
-                    X = x0.copy()
-                    acc["h2d"] += X.nbytes
-                else:
-                    X = x0d.clone()
-                r = L.run(X, omega=om, **opts)
-                if host:
-                    acc["d2h"] += X.nbytes + 8
-                st = r.stats
-                acc["pairs"] += st["pair_passes"] * st["pairs"]
-                acc["iters"] += st["iterations"]
-                acc["kernel_ms"] += st["kernel_ms"]
-                acc["launches"] += 1
-                acc["flops"] += st["pairs"] * (st["matvec_passes"] * FLOP_MV[args.dim] + st["stress_passes"] * FLOP_K2[args.dim])
-                acc["cg"] += st["cg_steps"]
-                acc["runs"].append((nm, om, st["iterations"], st["cg_steps"], st["final_stress"]))
-            acc["n_launch_total"] += 3 + len(oms)  # BFS, fill, row sums (the launch list: one each), + one layout kernel per run
-            L.close()
+    dims = tuple(int(d) for d in args.dims.split(","))
+    rp, ci = synth.workload(args.headline)
+    n = len(rp) - 1
+    x0 = {d: synth.initial_layout(n, d, 0) for d in dims}
+    rpd, cid = torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev)
+    x0d = {d: torch.from_numpy(x0[d]).to(dev) for d in dims}
+    opts = dict(omega=0.5, tol=0.0, stop=api.STOP_REL_DISP)
+    ips = args.iters_per_step
+    # row a0: ideal distances, once per layout (CUDA events inside fd_layout_create)
+    layouts = {d: api.Layout(rpd, cid, dim=d, disconnected_policy=1, stream=stream.cuda_stream) for d in dims}
+    info = {d: layouts[d].info() for d in dims}
 
     def zero():
-        return dict(pairs=0.0, iters=0, kernel_ms=0.0, apsp_ms=0.0, apsp_bytes=0.0, flops=0.0, cg=0, launches=0,
-                    h2d=0, d2h=0, runs=[], n_launch_total=0)
+        return dict(pairs=0.0, iters=0, kernel_ms=0.0, flops=0.0, cg=0, mv=0.0, st=0.0, launches=0, h2d=0, d2h=0)
 
-    for _ in range(args.warmup):
-        one_step(zero())
+    def step(acc, X, s, host=False, Ls=None):
+        Ls = Ls or layouts
+        for d in dims:
+            r = Ls[d].run(X[d], max_iter=ips, first_iter=s * ips, **opts)
+            st = r.stats
+            acc["pairs"] += st["pair_passes"] * st["pairs"]
+            acc["iters"] += st["iterations"]
+            acc["kernel_ms"] += st["kernel_ms"]
+            acc["flops"] += st["pairs"] * (st["matvec_passes"] * FLOP_MV[d] + st["stress_passes"] * FLOP_K2[d])
+            acc["cg"] += st["cg_steps"]
+            acc["mv"] += st["matvec_passes"]
+            acc["st"] += st["stress_passes"]
+            acc["launches"] += 1
+            acc["last_stress_" + str(d)] = r.stress
+            if host:
+                acc["h2d"] += X[d].numel() * 4
+                acc["d2h"] += X[d].numel() * 4 + 8
+
+    Xw = {d: x0d[d].clone() for d in dims}
+    for s_ in range(args.warmup):
+        step(zero(), Xw, s_)
+    del Xw
     torch.cuda.synchronize()
-    # ----- device-resident timed region
+    # ----- device-resident timed region: the inputs (CSR, X0) and the 20 GB of
+    # distance codes per layout are in HBM; the codes exceed L2, so no flush
     sampler = ClockSampler(local_rank)
     acc = zero()
+    X = {d: x0d[d].clone() for d in dims}
     times = []
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     sampler.start()
-    for _ in range(args.steps):
-        flush.fill_(1.0)  # evict L2 between steps (outside the timed interval)
+    for s_ in range(args.steps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
         e0.record(stream)
-        one_step(acc)
+        step(acc, X, s_)
         e1.record(stream)
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
     torch.cuda.synchronize()
     clocks = sampler.stop()
     total_ms = sum(times)
-    # ----- end to end through the public API with host buffers
+    fp32_peak, sms, clk, src = fp32_peak_tflops(dev)
+    peaks, _ = _peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    # ----- per-pass roofline (timeline of one extra chunk, outside the timed steps)
+    passes = {}
+    for d in dims:
+        passes[str(d)] = pass_profile(layouts[d], X[d], d, ips, opts, info[d]["distance_bytes"], 0.5 * n * (n - 1),
+                                      fp32_peak, hbm)
+    # ----- error against the FP64 oracle: sampled force rows at X0 and at the final layout
+    rng = np.random.default_rng(7)
+    rows = np.unique(np.concatenate([[0, n - 1], rng.choice(n, 14, replace=False)]))
+    runs = []
+    Xf = {d: X[d].cpu().numpy() for d in dims}
+    for d in dims:
+        F0 = layouts[d].forces(x0[d])[rows]
+        Ff = layouts[d].forces(Xf[d])[rows]
+        runs.append({"graph": args.headline, "n": n, "m": int(rp[-1]) // 2, "dim": d, "omega_c": 1.5,
+                     "iterations": args.steps * ips, "final_stress": acc["last_stress_" + str(d)],
+                     "error_vs_oracle": {"forces_at_x0": sampled_force_error(F0, x0[d], rp, ci, rows),
+                                         "forces_at_final": sampled_force_error(Ff, Xf[d], rp, ci, rows)}})
+    apsp = {d: info[d]["apsp_ms"] for d in dims}
+    apsp_bytes = {d: info[d]["bfs_sweeps"] * (20.0 * n + 12.0 * int(rp[-1])) + 0.5 * n * (n - 1) for d in dims}
+    for L in layouts.values():
+        L.close()
+    del layouts
+    torch.cuda.synchronize()
+    # ----- end to end through the public API with host buffers: the handles are
+    # made from the host CSR (distances included), and every step copies the
+    # layouts in from pinned host memory and out again
     acc_e = zero()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps if not args.no_e2e else 0):
-        one_step(acc_e, host=True)
-    torch.cuda.synchronize()
-    e2e_ms = max((time.perf_counter() - t0) * 1e3, 1e-9)
+    e2e_ms = 0.0
+    if not args.no_e2e:
+        Xh = {d: torch.from_numpy(x0[d]).pin_memory() for d in dims}
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Ls = {d: api.Layout(rp, ci, dim=d, disconnected_policy=1) for d in dims}
+        acc_e["h2d"] += rp.nbytes + ci.nbytes
+        for s_ in range(args.steps):
+            step(acc_e, Xh, s_, host=True, Ls=Ls)
+        torch.cuda.synchronize()
+        e2e_ms = max((time.perf_counter() - t0) * 1e3, 1e-9)
+        for L in Ls.values():
+            L.close()
+        del Ls
     total_ms, e2e_ms = max_over_ranks([total_ms, e2e_ms], dev, world)
     value = job_rate(acc["pairs"], world, total_ms)
-    e2e_value = job_rate(acc_e["pairs"], world, e2e_ms)
-    peaks, src = _peaks()
-    clk = peaks.get("sm_max_mhz", 2070.0)
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    fp32_peak = sms * 128 * 2 * clk * 1e6 / 1e12  # TFLOP/s at the maximum SM clock
+    e2e_value = job_rate(acc_e["pairs"], world, e2e_ms) if e2e_ms > 1e-6 else None
     fp32_measured = {"fma_f32": api.fp32_peak(False), "fma_f32x2": api.fp32_peak(True)}
     achieved = acc["flops"] / (acc["kernel_ms"] / 1e3) / 1e12
+    # the final stress of every layout against the oracle's Eq. (1) over all pairs
+    if rank == 0 and not args.no_oracle_check:
+        import oracle
+
+        t0 = time.perf_counter()
+        f_ref = oracle.stress_stream_multi([Xf[d] for d in dims], rp, ci, workers=max(1, (os.cpu_count() or 2) - 1))
+        for r_, fr in zip(runs, f_ref):
+            r_["error_vs_oracle"]["final_stress_rel"] = abs(r_["final_stress"] - fr) / abs(fr)
+            r_["error_vs_oracle"]["oracle_final_stress"] = float(fr)
+            r_["error_vs_oracle"]["oracle_s"] = time.perf_counter() - t0
+    sweep = run_sweep(args, local_rank, fp32_peak) if (args.sweep_sec and rank == 0) else None
     batched = run_batched(args, local_rank, fp32_peak) if (args.batch and rank == 0) else None
     differentiable = run_differentiable(args, local_rank) if (args.grad and rank == 0) else None
     direct = run_direct(args, local_rank, peaks, fp32_peak) if (args.direct_sec and rank == 0) else None
@@ -271,41 +401,130 @@ def run_ours(args, rank, world, local_rank):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": workload_config(args, inputs, world),
+        "config": headline_config(args, n, int(rp[-1]) // 2, world),
         "sor_iterations_per_s": acc["iters"] * world / (total_ms / 1e3),
         "cg_steps_per_sor_iteration": acc["cg"] / max(acc["iters"], 1),
-        "gpu_launches": acc["n_launch_total"],
+        "gpu_launches": acc["launches"],
         "roofline": {"bound": "alu", "kernel": "fd_main_kernel", "achieved": achieved, "peak": fp32_peak,
                      "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                     "traffic": measured_traffic(",".join(args.workload.split(","))),
+                     "traffic": measured_traffic(args.headline),
                      "traffic_unit": "DRAM bytes per launch (ncu, read + write)",
                      "peak_note": f"FP32 CUDA cores {sms} SMs x 128 x 2 flop at {clk:.0f} MHz ({src} max clock)",
                      "peak_measured_tflops": fp32_measured,
                      "peak_measured_note": "fd_fp32_peak: 16 independent FMA chains per thread, scalar and "
-                                           "two-wide packed, best of 5 launches"},
-        "apsp": {"kernel": "bfs_batch_kernel", "ms_per_step": acc["apsp_ms"] / args.steps,
-                 "algorithmic_bytes_per_step": acc["apsp_bytes"] / args.steps,
-                 "achieved_gbs": acc["apsp_bytes"] / (acc["apsp_ms"] / 1e3) / 1e9,
-                 "peak_gbs": peaks.get("hbm_gbs", 6800.0),
-                 "frac": acc["apsp_bytes"] / (acc["apsp_ms"] / 1e3) / 1e9 / peaks.get("hbm_gbs", 6800.0),
-                 "note": "bytes a pass over the edge list must move per 64-source search (row_ptr, reached and "
-                         "next words, col_idx, neighbour frontier words) times the passes run, plus 1 B per "
-                         "pair written; the per-search words are L2-resident, so this is not DRAM traffic"},
+                                           "two-wide packed, best of 5 launches",
+                     "algorithmic_flops_note": "per unordered pair: L^W p 8 (2-D) / 12 (3-D); stress + L^X X "
+                                               "per candidate 19 (2-D) / 25 (3-D); rsqrt not counted",
+                     "passes": passes},
+        "apsp": {"kernel": "bfs_batch_kernel", "ms": apsp,
+                 "algorithmic_bytes": apsp_bytes,
+                 "achieved_gbs": {d: apsp_bytes[d] / (apsp[d] / 1e3) / 1e9 for d in dims},
+                 "peak_gbs": hbm,
+                 "frac": {d: apsp_bytes[d] / (apsp[d] / 1e3) / 1e9 / hbm for d in dims},
+                 "note": "once per layout before the timed steps; bytes a pass over the edge list must move per "
+                         "64-source search (row_ptr, reached and next words, col_idx, neighbour frontier words) "
+                         "times the passes run, plus 1 B per pair written"},
         "layout_kernel_ms_per_step": acc["kernel_ms"] / args.steps,
         "clocks": clocks,
-        "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": acc_e["h2d"] // args.steps,
-                "d2h_bytes_per_step": acc_e["d2h"] // args.steps},
-        "runs": acc["runs"][: len(inputs) * len(oms)],
+        "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": acc_e["h2d"] // max(args.steps, 1),
+                "d2h_bytes_per_step": acc_e["d2h"] // max(args.steps, 1),
+                "note": "fd_layout_create from the host CSR (distances included) + every step's fd_run on pinned "
+                        "host layouts, wall clock"},
+        "runs": runs,
     }
-    if batched is not None:
-        line["batched"] = batched
-    if differentiable is not None:
-        line["differentiable"] = differentiable
-    if direct is not None:
-        line["direct_solver"] = direct
-    if vertex_omega is not None:
-        line["vertex_omega"] = vertex_omega
+    for k, v in (("sweep", sweep), ("batched", batched), ("differentiable", differentiable),
+                 ("direct_solver", direct), ("vertex_omega", vertex_omega)):
+        if v is not None:
+            line[k] = v
     return line
+
+
+def run_sweep(args, local_rank, fp32_peak):
+    """The benchmark-set stand-ins (ER n=10,000 mean degree 6, Delaunay
+    n=20,000, random binary tree n=16,383; 2-D, X0 seed 0) run to convergence
+    (relative displacement 1e-4, at most 1000 iterations) at classical omega
+    1.0 ... 1.9, L2 flushed before each run.  Error against the oracle at
+    omega_c 1.5: final stress (Eq. (1) streamed over all pairs) and sampled
+    force rows at X0 and at the final layout.  Iteration counts against the
+    oracle's: the stand-ins at n ~ 2000 (tests/golden/converged_runs.json,
+    written by the oracle alone) laid out by the GPU with the same options."""
+    import json as _json
+
+    import torch
+
+    import oracle
+    from paper_1711_01228_gb300 import api
+
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    oms = omegas(True) if not args.sweep_quick else [0.0, 0.5, 0.9]
+    out = {"workload": "er10k + delaunay20k + tree16k, 2-D, X0 U[0,1]^2 seed 0, rel-disp tol 1e-4, max "
+                       f"{args.max_iter} iterations, unreachable pairs at (largest d) + 1; L2 flushed before each run",
+           "graphs": {}}
+    tot_pairs, tot_ms, tot_flops = 0.0, 0.0, 0.0
+    for nm in WORKLOAD:
+        rp, ci = synth.workload(nm)
+        n = len(rp) - 1
+        x0 = synth.initial_layout(n, 2, 0)
+        X0 = torch.from_numpy(x0).to(dev)
+        g = {"n": n, "m": int(rp[-1]) // 2, "runs": []}
+        with api.Layout(torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev), dim=2, disconnected_policy=1,
+                        stream=stream.cuda_stream) as L:
+            g["diameter"] = L.info()["diameter"]
+            g["disconnected"] = bool(L.info()["disconnected"])
+            fill = float(g["diameter"] + 1) if g["disconnected"] else -1.0
+            for om in oms:
+                flush.fill_(1.0)
+                torch.cuda.synchronize()
+                X = X0.clone()
+                r = L.run(X, omega=om, tol=1e-4, max_iter=args.max_iter, stop=api.STOP_REL_DISP)
+                st = r.stats
+                tot_pairs += st["pair_passes"] * st["pairs"]
+                tot_ms += st["kernel_ms"]
+                tot_flops += st["pairs"] * (st["matvec_passes"] * FLOP_MV[2] + st["stress_passes"] * FLOP_K2[2])
+                e = {"omega_c": round(1.0 + om, 1), "iterations": r.iterations, "cg_steps": st["cg_steps"],
+                     "final_stress": r.stress, "final_crit": st["final_crit"], "kernel_ms": st["kernel_ms"],
+                     "pairs_per_s": st["pair_passes"] * st["pairs"] / (st["kernel_ms"] / 1e3)}
+                if abs(om - 0.5) < 1e-9 and not args.no_oracle_check:
+                    rng = np.random.default_rng(11)
+                    rows = np.unique(np.concatenate([[0, n - 1], rng.choice(n, 14, replace=False)]))
+                    xf = X.cpu().numpy()
+                    fr = oracle.stress_stream(xf, rp, ci, fill, workers=max(1, (os.cpu_count() or 2) - 1))
+                    e["error_vs_oracle"] = {
+                        "final_stress_rel": abs(r.stress - fr) / abs(fr), "oracle_final_stress": fr,
+                        "forces_at_x0": sampled_force_error(L.forces(x0)[rows], x0, rp, ci, rows, fill),
+                        "forces_at_final": sampled_force_error(L.forces(xf)[rows], xf, rp, ci, rows, fill)}
+                g["runs"].append(e)
+        out["graphs"][nm] = g
+    out["pairs_per_s"] = tot_pairs / (tot_ms / 1e3)
+    out["fp32_frac"] = tot_flops / (tot_ms / 1e3) / 1e12 / fp32_peak
+    # iteration counts against the oracle's on the n ~ 2000 stand-ins of each family
+    gpath = os.path.join(ROOT, "tests", "golden", "converged_runs.json")
+    if os.path.exists(gpath):
+        import importlib.util
+
+        spec = importlib.util.spec_from_file_location("make_converged",
+                                                      os.path.join(ROOT, "tests", "golden", "make_converged.py"))
+        mk = importlib.util.module_from_spec(spec)
+        spec.loader.exec_module(mk)
+        with open(gpath) as f:
+            gold = _json.load(f)
+        cmp_ = []
+        for c in gold["cases"]:
+            if c["kind"] != "family":
+                continue
+            rp, ci = mk.family_graph(c["key"])
+            with api.Layout(rp, ci, dim=2, disconnected_policy=1) as L:
+                X = synth.initial_layout(c["n"], 2, 0)
+                r = L.run(X, omega=c["omega"], tol=gold["tol"], max_iter=gold["max_iter"], stop=api.STOP_REL_DISP)
+            cmp_.append({"graph": c["key"], "n": c["n"], "omega_c": round(1.0 + c["omega"], 1),
+                         "gpu_iterations": r.iterations, "oracle_iterations": c["iterations"],
+                         "gpu_stress": r.stress, "oracle_stress": c["stress"],
+                         "stress_rel": abs(r.stress - c["stress"]) / c["stress"],
+                         "both_capped_or_both_converged": (r.iterations < gold["max_iter"]) == c["converged"]})
+        out["oracle_iterations_n2000"] = cmp_
+    return out
 
 
 def run_batched(args, local_rank, peak_tflops):
@@ -640,57 +859,6 @@ def _largest_component(rp, ci):
     return sub.indptr.astype(np.int32), sub.indices.astype(np.int32), keep
 
 
-def run_scale(args, local_rank):
-    """The method at scale: Barabasi-Albert n = 200,000 (m = 3), 2-D and 3-D,
-    200 iterations of Algorithm 2 at omega = 0.5 (classical 1.5).  Reports
-    throughput, the L^W passes' streaming rate against HBM (the 20 GB of
-    distance codes do not fit in L2), and the error against the FP64 oracle
-    on sampled vertices (distance rows, force rows at X^0)."""
-    import torch
-
-    import oracle
-    from paper_1711_01228_gb300 import api
-
-    rp, ci = synth.workload("ba200k")
-    n = len(rp) - 1
-    peaks, _ = _peaks()
-    rng = np.random.default_rng(7)
-    rows = np.unique(np.concatenate([[0, n - 1], rng.choice(n, 14, replace=False)]))
-    out = {"workload": f"Barabasi-Albert n={n}, m=3 ({int(rp[-1]) // 2} edges), X0 U[0,1]^d seed 0, "
-                       "200 iterations at omega_c 1.5 (tolerance 0)", "dims": {}}
-    for dim in (2, 3):
-        X0 = synth.initial_layout(n, dim, 0)
-        with api.Layout(rp, ci, dim=dim) as L:
-            info = L.info()
-            F = L.forces(X0).astype(np.float64)[rows]
-            Xd = torch.from_numpy(X0).cuda()
-            r = L.run(Xd, omega=0.5, tol=0.0, max_iter=200)
-            st = r.stats
-        Fr = []
-        for i in rows:
-            d = oracle.bfs_row(rp, ci, int(i)).astype(np.float64)
-            Fr.append(oracle.force_row(X0, int(i), d))
-        Fr = np.stack(Fr)
-        pairs = st["pairs"]
-        code_bytes = info["distance_bytes"]
-        out["dims"][str(dim)] = {
-            "distance_bytes": code_bytes, "apsp_ms": info["apsp_ms"], "iterations": st["iterations"],
-            "cg_steps": st["cg_steps"], "kernel_ms": st["kernel_ms"],
-            "pair_interactions_per_s": st["pair_passes"] * pairs / (st["kernel_ms"] / 1e3),
-            "fp32_tflops": pairs * (st["matvec_passes"] * FLOP_MV[dim] + st["stress_passes"] * FLOP_K2[dim])
-            / (st["kernel_ms"] / 1e3) / 1e12,
-            "code_stream_gbs": (st["matvec_passes"] + st["stress_passes"] / 2.0) * code_bytes / (st["kernel_ms"] / 1e3) / 1e9,
-            "hbm_peak_gbs": peaks.get("hbm_gbs", 6800.0),
-            "final_stress": r.stress,
-            "force_rel_err_sampled": float(np.linalg.norm(F - Fr) / np.linalg.norm(Fr)),
-            "sampled_vertices": int(len(rows)),
-        }
-    out["note"] = ("code_stream_gbs counts one read of the distance codes per pass (two-candidate passes read "
-                   "them once for both candidates); force error is Frobenius over the sampled rows, FP32 vs "
-                   "the FP64 oracle")
-    return out
-
-
 TABLE1_AVG = {"iters": {"0": 100.0, "0.5": 67.5, "1.0": 50.4, "1.5": 44.9, "auto": 47.2, "enum": 41.8},
               "time": {"0": 100.0, "0.5": 100.1, "1.0": 74.8, "1.5": 66.7, "auto": 70.2, "enum": 140.9}}
 
@@ -772,56 +940,72 @@ def run_table1(args, local_rank):
                     f"{args.table1_seeds} seeded X0 per case; synthetic graphs stand in for the paper's data sets"}
 
 
-def cpu_sample(budget_s: float):
-    """The oracle, as it is, on a bounded sample of the workload: one pass each
-    of stress, L^X X and L^W p over all pairs of the Erdos-Renyi graph
-    (distances from the oracle's BFS, not timed), repeated to ~budget_s."""
+_CPU_SAMPLE = {}
+
+
+def cpu_sample(budget_s: float, headline: str = HEADLINE):
+    """The oracle, as it is, on a bounded sample of the headline workload:
+    its row functions L^X X and the force (L^X - L^W) X (single-thread FP64,
+    explicit loops) on 32 sampled rows of the 2-D layout, the rows' BFS
+    distances computed beforehand (not timed), repeated to ~budget_s.  A row
+    call evaluates n - 1 ordered pairs, half of an all-pairs pass's n (n - 1)
+    ordered pair evaluations per row share, so it counts (n - 1) / 2
+    unordered pair interactions."""
     import oracle
 
-    rp, ci = synth.workload("er10k")
-    n = len(rp) - 1
-    X = synth.initial_layout(n, 2, 0).astype(np.float64)
-    st, D = oracle.apsp(rp, ci, policy=1)
-    pairs = n * (n - 1) / 2
-    done, t0 = 0, time.perf_counter()
+    if _CPU_SAMPLE.get("headline") != headline:
+        rp, ci = synth.workload(headline)
+        n = len(rp) - 1
+        rows = np.random.default_rng(3).choice(n, 32, replace=False)
+        _CPU_SAMPLE.update(headline=headline, n=n, X=synth.initial_layout(n, 2, 0).astype(np.float64), rows=rows,
+                           drows=[oracle.bfs_row(rp, ci, int(i)).astype(np.float64) for i in rows])
+    n, X, rows, drows = (_CPU_SAMPLE[k] for k in ("n", "X", "rows", "drows"))
+    calls, t0 = 0, time.perf_counter()
     while True:
-        oracle.stress(X, D)
-        oracle.rhs(X, D)
-        oracle.lw_matvec(X, D)
-        done += 3
+        for i, d in zip(rows, drows):
+            oracle.rhs_row(X, int(i), d)
+            oracle.force_row(X, int(i), d)
+            calls += 2
+            if time.perf_counter() - t0 >= budget_s:
+                break
         el = time.perf_counter() - t0
         if el >= budget_s:
             break
-    return {"value": done * pairs / el, "unit": "pairs/s", "cores": 1, "kind": "oracle",
-            "sample": f"oracle stress + L^X X + L^W p, {done} single-thread FP64 passes over the {int(pairs)} "
-                      f"pairs of ER n=10,000 ({el:.1f} s)"}
+    return {"value": calls * 0.5 * (n - 1) / el, "unit": "pairs/s", "cores": 1, "kind": "oracle",
+            "sample": f"oracle rhs_row + force_row, {calls} single-thread FP64 row calls on 32 sampled rows of "
+                      f"{headline} 2-D (n={n}; BFS rows precomputed, not timed) in {el:.1f} s; a row call counts "
+                      "(n-1)/2 unordered pair interactions"}
 
 
-def workload_config(args, inputs, world):
+def headline_config(args, n, m, world):
     """The bench line's config: the workload both arms are quoted on."""
-    return {"workload": "+".join(args.workload.split(",")) + f" {args.dim}-D, X0 U[0,1]^{args.dim} seed 0, omega_c "
-            + ("1.0-1.9 sweep" if args.sweep else "1.5") + ", rel-disp tol 1e-4, max 1000 iters",
-            "graphs": {nm: {"n": len(rp) - 1, "m": int(rp[-1]) // 2} for nm, rp, _, _ in inputs},
-            "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"}
+    return {"workload": f"{args.headline}: Barabasi-Albert n={n} m=3 ({m} edges), "
+                        + "+".join(f"{d}-D" for d in args.dims.split(","))
+                        + f" layouts, X0 U[0,1]^d seed 0, omega_c 1.5, {args.iters_per_step} iterations of "
+                          f"each layout per step ({args.steps} steps = {args.steps * args.iters_per_step} "
+                          "iterations; the configuration is 200)",
+            "l2": "inputs larger than L2 (20 GB of distance codes per layout, streamed every pass); no flush",
+            "parallelism": f"replicas x{world}"}
 
 
 def run_reference(args, rank, world):
     """The oracle, as it is, on the host cores: each step a bounded sample of
-    the workload (see cpu_sample), on the GPU arm's config and metric."""
+    the headline workload (see cpu_sample), on the GPU arm's config and metric."""
     if rank != 0:
         return None
     for _ in range(args.warmup):
-        cpu_sample(1.0)
+        cpu_sample(0.5, args.headline)
     vals = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        vals.append(cpu_sample(3.0))
+        vals.append(cpu_sample(3.0, args.headline))
     el = time.perf_counter() - t0
     v = statistics.mean(x["value"] for x in vals)
+    rp, _ = synth.workload(args.headline)
     return {"impl": "reference", "metric": "pair-interactions/s", "value": v, "unit": "pairs/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(args, make_inputs(args.workload.split(","), args.dim), world),
+            "config": headline_config(args, len(rp) - 1, int(rp[-1]) // 2, world),
             "cpu_baseline": {**vals[-1], "value": v},
             "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
@@ -829,22 +1013,26 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default=",".join(WORKLOAD))
-    ap.add_argument("--sweep", action="store_true")
+    ap.add_argument("--headline", default=HEADLINE, help="graph of the timed steps (synth.workload name)")
+    ap.add_argument("--dims", default=",".join(str(d) for d in HEADLINE_DIMS), help="layout dimensions, e.g. 2,3")
+    ap.add_argument("--iters-per-step", type=int, default=ITERS_PER_STEP)
+    ap.add_argument("--no-sweep", dest="sweep_sec", action="store_false",
+                    help="skip the benchmark-set stand-ins' omega sweep")
+    ap.add_argument("--sweep-quick", action="store_true", help="sweep only classical omega 1.0, 1.5, 1.9")
+    ap.add_argument("--no-oracle-check", action="store_true",
+                    help="skip the oracle's full-size stress evaluations (minutes of host time)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass")
-    ap.add_argument("--max-iter", type=int, default=1000, help="iteration cap per run (1000 = the workload)")
-    ap.add_argument("--dim", type=int, default=2, choices=[1, 2, 3], help="layout dimension (2 = the workload)")
+    ap.add_argument("--max-iter", type=int, default=1000, help="iteration cap per run of the sweep (1000)")
     ap.add_argument("--no-batch", dest="batch", action="store_false", help="skip the batched-form section")
     ap.add_argument("--batch-graphs", type=int, default=4096)
     ap.add_argument("--batch-steps", type=int, default=2)
     ap.add_argument("--batch-sample", type=int, default=64, help="graphs timed through the single-graph path")
     ap.add_argument("--no-grad", dest="grad", action="store_false", help="skip the differentiable-form section")
     ap.add_argument("--table1", action="store_true", help="omega strategies on stand-ins at Table 1's sizes, then exit")
-    ap.add_argument("--scale", action="store_true", help="Barabasi-Albert n=200,000, 2-D and 3-D, 200 iterations, then exit")
     ap.add_argument("--table1-seeds", type=int, default=5)
     ap.add_argument("--grad-n", type=int, default=4096, help="vertices of the differentiable workload (<= 4096)")
     ap.add_argument("--no-direct", dest="direct_sec", action="store_false",
@@ -853,16 +1041,6 @@ def main():
     ap.add_argument("--direct-n", type=int, default=0, help="Delaunay graph size of --direct (0 = delaunay20k)")
     args = ap.parse_args()
     rank, world, local_rank = _env_rank()
-    if args.scale:
-        import torch
-
-        from paper_1711_01228_gb300 import build
-
-        build.build()
-        torch.cuda.set_device(local_rank)
-        if rank == 0:
-            print(json.dumps(run_scale(args, local_rank)), flush=True)
-        return
     if args.direct:
         import torch
 
@@ -898,7 +1076,7 @@ def main():
     else:
         line = run_ours(args, rank, world, local_rank)
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_sample(10.0)
+            line["cpu_baseline"] = cpu_sample(10.0, args.headline)
     if rank == 0 and line is not None:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -245,4 +245,6 @@ def workload(name: str, seed: int = 0):
         return random_binary_tree(16_383, seed)
     if name == "ba200k":
         return barabasi_albert(200_000, 3, seed)
+    if name == "ba50k":
+        return barabasi_albert(50_000, 3, seed)
     raise KeyError(name)
