@@ -50,6 +50,20 @@ HEADLINE_ITERS = 200
 ITERS_PER_STEP = 10
 FLOP_K2 = {1: 13, 2: 19, 3: 25}   # stress + L^X X per unordered pair per candidate
 FLOP_MV = {1: 4, 2: 8, 3: 12}     # L^W p per unordered pair
+# enumerating strategy (stress only): per candidate Delta = Delta_z + omega (Delta_z - Delta_x) 2d, r^2 2d,
+# r/d - 1 3, square-accumulate 2; per pair once Delta_z, Delta_x and their difference 3d
+FLOP_ENUM_CAND = {1: 9, 2: 13, 3: 17}
+FLOP_ENUM_SHARED = {1: 3, 2: 6, 3: 9}
+NENUM = 19
+
+
+def algorithmic_flops(st: dict, dim: int) -> float:
+    """Algorithmic FP32 FLOPs of a layout-kernel call from its fd_stats: L^W
+    passes, stress/RHS passes per candidate, and the enumeration passes'
+    candidate stresses at their own (stress-only) cost; rsqrt not counted."""
+    en = st.get("enum_candidate_passes", 0.0)
+    return st["pairs"] * (st["matvec_passes"] * FLOP_MV[dim] + st["stress_passes"] * FLOP_K2[dim]
+                          + en * FLOP_ENUM_CAND[dim] + en / NENUM * FLOP_ENUM_SHARED[dim])
 
 
 def _env_rank():
@@ -289,7 +303,7 @@ def run_ours(args, rank, world, local_rank):
             acc["pairs"] += st["pair_passes"] * st["pairs"]
             acc["iters"] += st["iterations"]
             acc["kernel_ms"] += st["kernel_ms"]
-            acc["flops"] += st["pairs"] * (st["matvec_passes"] * FLOP_MV[d] + st["stress_passes"] * FLOP_K2[d])
+            acc["flops"] += algorithmic_flops(st, d)
             acc["cg"] += st["cg_steps"]
             acc["mv"] += st["matvec_passes"]
             acc["st"] += st["stress_passes"]
@@ -482,7 +496,7 @@ def run_sweep(args, local_rank, fp32_peak):
                 st = r.stats
                 tot_pairs += st["pair_passes"] * st["pairs"]
                 tot_ms += st["kernel_ms"]
-                tot_flops += st["pairs"] * (st["matvec_passes"] * FLOP_MV[2] + st["stress_passes"] * FLOP_K2[2])
+                tot_flops += algorithmic_flops(st, 2)
                 e = {"omega_c": round(1.0 + om, 1), "iterations": r.iterations, "cg_steps": st["cg_steps"],
                      "final_stress": r.stress, "final_crit": st["final_crit"], "kernel_ms": st["kernel_ms"],
                      "pairs_per_s": st["pair_passes"] * st["pairs"] / (st["kernel_ms"] / 1e3)}

@@ -107,7 +107,8 @@ typedef struct {
   int32_t cg_steps;        /* total CG steps over all H solves */
   int32_t cg_maxed;        /* H solves that stopped at cg_max before reaching cg_tol */
   int32_t accepted;        /* iterations whose extrapolation was kept (line 6 true) */
-  double pair_passes;      /* all-pairs passes evaluated (matvec = 1, stress/RHS per candidate = 1) */
+  double pair_passes;      /* all-pairs passes evaluated (matvec = 1, stress/RHS per candidate = 1,
+                              enumeration: 1 per candidate stress) */
   double pairs;            /* unordered vertex pairs per pass: n (n - 1) / 2 */
   double final_stress;     /* f at the returned layout */
   double final_crit;       /* last termination criterion value */
@@ -116,6 +117,8 @@ typedef struct {
   double kernel_ms;        /* device time of the call's layout kernel (CUDA events on the handle's stream) */
   int32_t cg_stalled;      /* CG columns stopped before cg_tol because rounding left no descent */
   int32_t reserved;
+  double enum_candidate_passes; /* FD_OMEGA_ENUM: candidate stresses evaluated by the enumeration passes
+                              (19 per pass, stress only; not in stress_passes) */
 } fd_stats;
 
 /* Library facts about a handle. */

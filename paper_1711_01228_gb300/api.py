@@ -47,7 +47,8 @@ class Stats(ctypes.Structure):
                 ("accepted", ctypes.c_int32), ("pair_passes", ctypes.c_double), ("pairs", ctypes.c_double),
                 ("final_stress", ctypes.c_double), ("final_crit", ctypes.c_double),
                 ("matvec_passes", ctypes.c_double), ("stress_passes", ctypes.c_double),
-                ("kernel_ms", ctypes.c_double), ("cg_stalled", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("kernel_ms", ctypes.c_double), ("cg_stalled", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("enum_candidate_passes", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):

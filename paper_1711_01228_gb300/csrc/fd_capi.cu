@@ -575,6 +575,7 @@ void fill_stats(fd_layout* h, const Ctrl& c, double kms) {
   h->stats.stress_passes = c.stress_passes;
   h->stats.kernel_ms = kms;
   h->stats.cg_stalled = c.cg_stalled;
+  h->stats.enum_candidate_passes = c.enum_passes;
 }
 
 // Positions in: device pointers are used in place, host arrays are staged.

@@ -70,6 +70,7 @@ struct Ctrl {
   double pair_passes;          // all-pairs passes evaluated
   double matvec_passes;        // y = L^W p passes
   double stress_passes;        // stress (+ RHS or force) passes, per candidate
+  double enum_passes;          // candidate stresses of the enumerating strategy (NENUM per enumeration pass)
   int timeout_where;           // barrier index that timed out (diagnostic)
   int timeline_n;              // timeline entries written
   unsigned long long t_start;  // %globaltimer at kernel start (CTA 0)

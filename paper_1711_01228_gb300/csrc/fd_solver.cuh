@@ -776,7 +776,7 @@ static_assert(sizeof(PassCtl) <= SmemLayout<1, CODE_U8>::OFF_RUN - SmemLayout<1,
 
 // Scalars of the Algorithm 2 loop (shared memory, written by thread 0).
 struct RunState {
-  double f_cur, f_new, crit, passes_mv, passes_st, f_enum0;
+  double f_cur, f_new, crit, passes_mv, passes_st, f_enum0, passes_en;
   int cg_total, cg_maxed, cg_stalled, n_acc, it_outer, it;
   int accept, bsel, stop, all_conv, cg_done;
   int conv[3];
@@ -1296,6 +1296,7 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
     rs->crit = 0.0;
     rs->passes_mv = 0.0;
     rs->passes_st = (p.mode != KM_SOLVE) ? 1.0 : 0.0;
+    rs->passes_en = 0.0;
     rs->cg_total = rs->cg_maxed = rs->cg_stalled = rs->n_acc = rs->it_outer = 0;
     rs->accept = 0;
     rs->bsel = 0;
@@ -1648,7 +1649,8 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
       if (tid == 0) {
         rs->cg_total += rs->it;
         for (int d = 0; d < DIM; ++d) rs->z0[d] = src.z0[d];
-        rs->passes_st += (double)NENUM + 1.0;
+        rs->passes_en += (double)NENUM;  // the enumeration pass: NENUM stresses, no right-hand side
+        rs->passes_st += 1.0;            // the pass on the selected candidate
       }
       if constexpr (WITH_ENUM) {
         if (!pair_pass<DIM, PM_ENUM, 2, CODE>(p, smem, ps, src, acc0, RSUM)) return;
@@ -1781,9 +1783,10 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
     ctrl->accepted = rs->n_acc;
     ctrl->f_final = rs->f_cur;
     ctrl->crit_final = rs->crit;
-    ctrl->pair_passes = rs->passes_mv + rs->passes_st;
+    ctrl->pair_passes = rs->passes_mv + rs->passes_st + rs->passes_en;
     ctrl->matvec_passes = rs->passes_mv;
     ctrl->stress_passes = rs->passes_st;
+    ctrl->enum_passes = rs->passes_en;
   }
 #undef FD_SYNC
 #undef FD_SYNC_RED
