@@ -623,30 +623,27 @@ def run_batched(args, local_rank, peak_tflops):
 
 
 def run_differentiable(args, local_rank):
-    """The differentiable form: stress of a weighted random geometric graph in
-    3-D with its two gradients (positions: the force kernel; edge lengths:
-    shortest-path back-propagation), timed beside the plain stress pass."""
+    """The differentiable form on a random geometric graph of args.grad_n
+    points in the unit cube (mean degree 6, seed 0; its largest component,
+    since derivatives in the edge lengths need every pair connected) in 3-D,
+    every edge length a float32 parameter initialised at 1.0.  Timed: the
+    weighted shortest paths at creation, the stress pass, the position
+    gradient (force pass), the length gradient (shortest-path back-
+    propagation), one autograd.stress_lengths forward + backward, and
+    unrolled_layout with K = 32 iterations of Algorithm 2 (checkpoint every
+    8) forward and forward + backward.  Then a few gradient steps fit the
+    edge lengths so that X^K's distances on 4096 sampled pairs match seeded
+    target distances (a random layout's), loss before and after."""
     import torch
 
     from paper_1711_01228_gb300 import api, autograd
 
     dev = torch.device("cuda", local_rank)
-    # the largest connected component of a random geometric graph (derivatives in the
-    # edge lengths need every pair connected)
     rp0, ci0, pts0 = synth.random_geometric(args.grad_n, 3, 6.0, seed=0)
     rp, ci, keep = _largest_component(rp0, ci0)
-    pts = pts0[keep]
     n = len(rp) - 1
-    s = 0
-    rng = np.random.default_rng(s)
-    w = np.empty(len(ci), dtype=np.float32)
-    seen = {}
-    for u in range(n):
-        for e in range(rp[u], rp[u + 1]):
-            key = (min(u, int(ci[e])), max(u, int(ci[e])))
-            seen.setdefault(key, np.float32(rng.uniform(0.5, 2.0)))
-            w[e] = seen[key]
-    X = torch.from_numpy((pts * 10.0).astype(np.float32)).to(dev)
+    w = np.ones(len(ci), dtype=np.float32)
+    X = torch.from_numpy(synth.initial_layout(n, 3, 0) * 10.0).to(dev)
     wt = torch.from_numpy(w).to(dev).requires_grad_(True)
     rpt, cit = torch.from_numpy(rp), torch.from_numpy(ci)
 
@@ -663,13 +660,15 @@ def run_differentiable(args, local_rank):
             ts.append(e0.elapsed_time(e1))
         return statistics.median(ts)
 
+    t0 = time.perf_counter()
     L = api.Layout(rp, ci, dim=3, edge_len=w, disconnected_policy=0)
+    create_s = time.perf_counter() - t0
+    info = L.info()
     F = torch.empty_like(X)
     G = torch.empty(len(ci), dtype=torch.float32, device=dev)
     ms_energy = timed(lambda: L.energy(X))
     ms_forces = timed(lambda: L.forces(X, out=F))
-    ms_lgrad = timed(lambda: L.length_grad(X, out=G))
-    create_ms = L.info()["apsp_ms"]
+    ms_lgrad = timed(lambda: L.length_grad(X, out=G), reps=1)
     L.close()
 
     def step():
@@ -677,7 +676,7 @@ def run_differentiable(args, local_rank):
         f = autograd.stress_lengths(X, wt, rpt, cit)
         f.backward()
 
-    ms_step = timed(step)
+    ms_step = timed(step, reps=1)
 
     # adjoint through K = 32 unrolled iterations (checkpoint every 8): fit lengths to target distances
     K, every = 32, 8
@@ -685,43 +684,58 @@ def run_differentiable(args, local_rank):
     Yt = torch.from_numpy((rng2.random((n, 3)) * 10.0).astype(np.float32)).to(dev)
     pi = torch.from_numpy(rng2.integers(0, n, 4096)).to(dev)
     pj = torch.from_numpy(rng2.integers(0, n, 4096)).to(dev)
-    keep = pi != pj
-    pi, pj = pi[keep], pj[keep]
+    ok = pi != pj
+    pi, pj = pi[ok], pj[ok]
     tgt = (Yt[pi] - Yt[pj]).norm(dim=1)
     X0 = X.clone()
 
+    def loss_of(lens):
+        XK = autograd.unrolled_layout(X0, lens, rpt, cit, K=K, omega=0.5, every=every)
+        return ((XK[pi] - XK[pj]).norm(dim=1) - tgt).pow(2).sum()
+
     def unrolled_step():
         wt.grad = None
-        XK = autograd.unrolled_layout(X0, wt, rpt, cit, K=K, omega=0.5, every=every)
-        loss = ((XK[pi] - XK[pj]).norm(dim=1) - tgt).pow(2).sum()
-        loss.backward()
-
-    ms_unrolled = timed(unrolled_step, reps=2)
-
-    def unrolled_step_direct():
-        wt.grad = None
-        XK = autograd.unrolled_layout(X0, wt, rpt, cit, K=K, omega=0.5, every=every, solver=api.SOLVER_DIRECT)
-        loss = ((XK[pi] - XK[pj]).norm(dim=1) - tgt).pow(2).sum()
-        loss.backward()
-
-    ms_unrolled_direct = timed(unrolled_step_direct, reps=2)
+        loss_of(wt).backward()
 
     def unrolled_forward():
         with torch.no_grad():
             autograd.unrolled_layout(X0, wt.detach(), rpt, cit, K=K, omega=0.5, every=every)
 
-    ms_unrolled_fwd = timed(unrolled_forward, reps=2)
+    ms_unrolled_fwd = timed(unrolled_forward, reps=1)
+    ms_unrolled = timed(unrolled_step, reps=1)
+    # the fit: Adam on the lengths (kept >= 0.05)
+    lens = torch.ones(len(ci), dtype=torch.float32, device=dev, requires_grad=True)
+    opt = torch.optim.Adam([lens], lr=0.05)
+    losses = []
+    t0 = time.perf_counter()
+    for _ in range(args.grad_fit_steps + 1):
+        opt.zero_grad()
+        loss = loss_of(lens)
+        losses.append(float(loss))
+        if len(losses) > args.grad_fit_steps:
+            break
+        loss.backward()
+        opt.step()
+        with torch.no_grad():
+            lens.clamp_(min=0.05)
+    fit_s = time.perf_counter() - t0
     pairs = 0.5 * n * (n - 1)
     return {"workload": f"largest component (n={n}) of a random geometric graph of {args.grad_n} points in the "
-                        "unit cube x 10, mean degree 6 (seed 0); edge lengths seeded in [0.5, 2]; 3-D",
+                        "unit cube, mean degree 6 (seed 0); edge lengths float32 parameters at 1.0; 3-D, X0 "
+                        "U[0,1]^3 x 10 seed 0",
+            "n": n, "edges": int(len(ci)) // 2, "distance_bytes": info["distance_bytes"],
+            "weighted_apsp_ms": info["apsp_ms"], "create_s": create_s,
             "stress_pass_ms": ms_energy, "position_grad_ms": ms_forces, "length_grad_ms": ms_lgrad,
-            "weighted_apsp_ms": create_ms, "autograd_step_ms": ms_step,
+            "autograd_step_ms": ms_step,
             "unrolled": {"iterations": K, "checkpoint_every": every, "omega_c": 1.5,
                          "forward_ms": ms_unrolled_fwd, "forward_backward_ms": ms_unrolled,
-                         "forward_backward_ms_direct_solver": ms_unrolled_direct,
                          "loss": "squared error of 4096 sampled pair distances of X^K against a seeded "
                                  "random layout's"},
+            "fit": {"optimizer": "Adam lr 0.05 on the edge lengths (>= 0.05)", "steps": args.grad_fit_steps,
+                    "loss_before": losses[0], "loss_after": losses[-1], "losses": losses, "seconds": fit_s},
             "stress_pairs_per_s": pairs / (ms_energy / 1e3), "position_grad_pairs_per_s": pairs / (ms_forces / 1e3),
+            "gradient_check": "FP64 finite differences and the oracle on 64-vertex subgraphs "
+                              "(tests/test_gpu_grad.py), and the homogeneity identity at n ~ 5000",
             "note": "autograd step = fd_layout_create (weighted shortest paths) + stress + forces + length "
                     "gradient, through torch.autograd; every value from the CUDA library"}
 
@@ -1048,7 +1062,8 @@ def main():
     ap.add_argument("--no-grad", dest="grad", action="store_false", help="skip the differentiable-form section")
     ap.add_argument("--table1", action="store_true", help="omega strategies on stand-ins at Table 1's sizes, then exit")
     ap.add_argument("--table1-seeds", type=int, default=5)
-    ap.add_argument("--grad-n", type=int, default=4096, help="vertices of the differentiable workload (<= 4096)")
+    ap.add_argument("--grad-n", type=int, default=50000, help="points of the differentiable workload's graph")
+    ap.add_argument("--grad-fit-steps", type=int, default=3, help="gradient steps of the edge-length fit")
     ap.add_argument("--no-direct", dest="direct_sec", action="store_false",
                     help="skip the direct-solver and per-vertex omega sections")
     ap.add_argument("--direct", action="store_true", help="only the direct-solver section, then exit")

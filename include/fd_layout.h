@@ -211,8 +211,13 @@ fd_status fd_energy_noalloc(const float* X, const float* D, int32_t n, int32_t d
  * F_out is written.  Errors: FD_ERR_ARG, FD_ERR_NONFINITE, FD_ERR_CUDA. */
 fd_status fd_forces(fd_layout* h, const float* X, float* F_out);
 
-/* Largest graph accepted by fd_energy_length_grad. */
-#define FD_GRAD_MAX_N 4096
+/* Largest graph accepted by fd_energy_length_grad and the adjoint's edge-
+ * length derivative (fd_adjoint_reset / fd_adjoint_length_grad).  Up to 4096
+ * vertices every source's search state sits in shared memory; above, in
+ * 28 n bytes of device scratch per CTA (about 1.1 GB at the limit), beside
+ * the float32 distance tiles and the tile array of pair sensitivities
+ * (2 n^2 bytes each). */
+#define FD_GRAD_MAX_N 131072
 
 /* Derivative of the stress f(X) of Eq. (1) with respect to the edge lengths
  * of a weighted graph (d_ij = weighted shortest-path length, Sec. 2 and

@@ -76,7 +76,7 @@ EXPORTED = ["fd_options_default", "fd_layout_create", "fd_layout_destroy", "fd_e
             "fd_batch_last_stats", "fd_energy_length_grad", "fd_sor_step_adjoint", "fd_adjoint_reset",
             "fd_adjoint_length_grad", "fd_set_vertex_omega", "fd_factor", "fd_factor_rows", "fd_factor_release",
             "fd_fp32_peak", "fd_run_trace_ext"]
-GRAD_MAX_N = 4096
+GRAD_MAX_N = 131072
 BATCH_MAX_N = 2048
 TIMELINE_TAGS = {1: "pack", 2: "stress", 3: "forces", 4: "rhs0", 5: "h_init", 6: "cg_au0", 7: "cg_step",
                  8: "candidates", 9: "vertex_phase"}

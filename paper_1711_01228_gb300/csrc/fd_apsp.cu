@@ -18,6 +18,7 @@
 #include <stdint.h>
 
 #include "fd_internal.cuh"
+#include "fd_sssp.cuh"
 
 namespace fdl {
 
@@ -129,38 +130,28 @@ __global__ void __launch_bounds__(1024) bfs_batch_kernel(int n, int nb, const in
   }
 }
 
-// Weighted shortest paths: one source per CTA iteration.
+// Weighted shortest paths: one source per CTA iteration (frontier search of
+// fd_sssp.cuh in the CTA's scratch: 4 n ints), each pair written once into
+// the tile that owns it.  *err is set if a search ran out of rounds.
 __global__ void __launch_bounds__(1024) sssp_relax_kernel(int n, int nb, const int* __restrict__ row_ptr,
                                                           const int* __restrict__ col_idx,
                                                           const float* __restrict__ len,
                                                           const int* __restrict__ tile_base,
                                                           const int* __restrict__ strip_len, float* D,
-                                                          float* scratch, int* maxbits) {
-  float* dist = scratch + (size_t)blockIdx.x * n;
+                                                          int* scratch, int* maxbits, int* err) {
+  __shared__ int s_cnt[2];
+  int* dist = scratch + (size_t)blockIdx.x * 4 * n;
+  int* mark = dist + n;
+  int* fa = mark + n;
+  int* fb = fa + n;
   for (int src = blockIdx.x; src < n; src += gridDim.x) {
-    for (int v = threadIdx.x; v < n; v += blockDim.x) dist[v] = (v == src) ? 0.f : INFINITY;
-    __syncthreads();
-    for (int sweep = 0; sweep < n; ++sweep) {
-      int changed = 0;
-      for (int v = threadIdx.x; v < n; v += blockDim.x) {
-        float best = dist[v];
-        const int e1 = row_ptr[v + 1];
-        for (int e = row_ptr[v]; e < e1; ++e) {
-          const float c = ((volatile float*)dist)[col_idx[e]] + len[e];
-          best = fminf(best, c);
-        }
-        if (best < dist[v]) {
-          dist[v] = best;
-          changed = 1;
-        }
-      }
-      if (!__syncthreads_or(changed)) break;
-    }
+    if (!sssp_frontier(n, src, row_ptr, col_idx, len, dist, mark, fa, fb, s_cnt) && threadIdx.x == 0)
+      atomicExch(err, 1);
     const int I = src / TILE, il = src % TILE;
     const int LI = strip_len[I], tb = tile_base[I];
     int localmax = 0;
     for (int v = threadIdx.x; v < n; v += blockDim.x) {
-      const float dv = dist[v];
+      const float dv = __int_as_float(__ldcg(dist + v));
       if (v == src || !(dv < INFINITY)) continue;
       const int J = v / TILE;
       int k = J - I;
@@ -449,8 +440,9 @@ cudaError_t launch_bfs(int code, int n, int nb, const int* rp, const int* ci, co
 }
 
 cudaError_t launch_sssp(int n, int nb, const int* rp, const int* ci, const float* len, const int* tile_base,
-                        const int* strip_len, float* D, float* scratch, int grid, int* maxbits, cudaStream_t st) {
-  sssp_relax_kernel<<<grid, 1024, 0, st>>>(n, nb, rp, ci, len, tile_base, strip_len, D, scratch, maxbits);
+                        const int* strip_len, float* D, int* scratch, int grid, int* maxbits, int* err,
+                        cudaStream_t st) {
+  sssp_relax_kernel<<<grid, 1024, 0, st>>>(n, nb, rp, ci, len, tile_base, strip_len, D, scratch, maxbits, err);
   return cudaGetLastError();
 }
 

@@ -20,7 +20,8 @@ cudaError_t launch_bfs(int code, int n, int nb, const int* rp, const int* ci, co
                        const int* strip_len, void* D, unsigned long long* scratch, size_t stride, int grid,
                        int* maxlevel, int* overflow, int* sweeps, cudaStream_t st);
 cudaError_t launch_sssp(int n, int nb, const int* rp, const int* ci, const float* len, const int* tile_base,
-                        const int* strip_len, float* D, float* scratch, int grid, int* maxbits, cudaStream_t st);
+                        const int* strip_len, float* D, int* scratch, int grid, int* maxbits, int* err,
+                        cudaStream_t st);
 cudaError_t launch_fill(int code, int n, int nb, int ntiles, const int2* tile_ik, void* D, float fill, int write,
                         unsigned long long* count, int grid, cudaStream_t st);
 cudaError_t launch_rowsum(int code, int n, int nb, const int* tile_base, const int* strip_len, const void* D,
@@ -51,10 +52,14 @@ cudaError_t launch_pair_adjoint(int code, int n, int nb, int dim, const int2* ti
                                 const float* X, const float* lam, const float* Y, float* Xb, float* Db, int sm_count,
                                 cudaStream_t st);
 cudaError_t launch_sp_backprop(int n, int nb, const float* Gt, const int* rp, const int* ci, const float* len,
-                               const int* rev, int nnz, float* gacc, float* out, int sm_count, cudaStream_t st);
+                               const int* rev, int nnz, float* gacc, float* out, int sm_count, int global_path,
+                               int* scratch, int* err, cudaStream_t st);
 cudaError_t launch_length_grad(int n, int nb, int dim, const int2* tile_ik, int ntiles, const float* D,
                                const float* X, float* Gt, const int* rp, const int* ci, const float* len,
-                               const int* rev, int nnz, float* gacc, float* out, int sm_count, cudaStream_t st);
+                               const int* rev, int nnz, float* gacc, float* out, int sm_count, int global_path,
+                               int* scratch, int* err, cudaStream_t st);
+size_t sp_backprop_scratch_ints(int n, int sm_count);
+constexpr int SP_SMEM_MAX_N = 4096;  // shared-memory back-propagation up to this size (fd_grad.cu)
 cudaError_t batch_config_d1(int W, int lut_bytes, int n_pad_max, int nbuf, int* blocks_per_sm, size_t* smem);
 cudaError_t batch_config_d2(int W, int lut_bytes, int n_pad_max, int nbuf, int* blocks_per_sm, size_t* smem);
 cudaError_t batch_config_d3(int W, int lut_bytes, int n_pad_max, int nbuf, int* blocks_per_sm, size_t* smem);
@@ -390,7 +395,7 @@ fd_status build_distances(fd_layout* h, const std::vector<int>& rp, const std::v
 
   FD_TRY(dev_alloc(&d_rp, n + 1));
   FD_TRY(dev_alloc(&d_ci, nnz));
-  FD_TRY(dev_alloc(&d_flags, 4));
+  FD_TRY(dev_alloc(&d_flags, 5));
   FD_TRY(dev_alloc(&d_count, 1));
   FD_TRYC(cudaMemcpyAsync(d_rp, rp.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
   if (nnz) FD_TRYC(cudaMemcpyAsync(d_ci, ci.data(), nnz * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -410,7 +415,7 @@ fd_status build_distances(fd_layout* h, const std::vector<int>& rp, const std::v
     dev_free(h->D);
     FD_TRY(dev_alloc((unsigned char**)&h->D, h->D_bytes));
     FD_TRYC(cudaMemsetAsync(h->D, 0, h->D_bytes, st));
-    FD_TRYC(cudaMemsetAsync(d_flags, 0, 4 * sizeof(int), st));
+    FD_TRYC(cudaMemsetAsync(d_flags, 0, 5 * sizeof(int), st));
     int diameter = 0;
     if (!len) {
       const int nbatches = (n + 63) / 64;
@@ -442,14 +447,19 @@ fd_status build_distances(fd_layout* h, const std::vector<int>& rp, const std::v
       const int grid = std::max(1, std::min(n, 2 * h->sm_count));
       if (scratch) cudaFree(scratch);
       scratch = nullptr;
-      FD_TRYC(cudaMalloc(&scratch, (size_t)grid * n * sizeof(float)));
+      FD_TRYC(cudaMalloc(&scratch, (size_t)grid * 4 * n * sizeof(int)));  // per CTA: distances, stamps, 2 frontiers
       FD_TRYC(cudaEventRecord(h->ev0, st));
-      FD_TRYC(launch_sssp(n, nb, d_rp, d_ci, d_len, h->d_tile_base, h->d_strip_len, (float*)h->D, (float*)scratch,
-                          grid, d_flags + 2, st));
+      FD_TRYC(launch_sssp(n, nb, d_rp, d_ci, d_len, h->d_tile_base, h->d_strip_len, (float*)h->D, (int*)scratch,
+                          grid, d_flags + 2, d_flags + 4, st));
       FD_TRYC(cudaEventRecord(h->ev1, st));
-      int bits;
+      int bits, serr = 0;
       FD_TRYC(cudaMemcpyAsync(&bits, d_flags + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
+      FD_TRYC(cudaMemcpyAsync(&serr, d_flags + 4, sizeof(int), cudaMemcpyDeviceToHost, st));
       FD_TRYC(cudaStreamSynchronize(st));
+      if (serr) {  // a search ran out of rounds
+        cleanup();
+        return FD_ERR_TIMEOUT;
+      }
       float ms = 0.f;
       FD_TRYC(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
       h->apsp_ms = ms;
@@ -842,6 +852,37 @@ fd_status fd_forces(fd_layout* h, const float* X, float* F_out) {
   return FD_OK;
 }
 
+// Scratch of the shortest-path back-propagation: none for the shared-memory
+// kernel; 7 n ints per CTA plus an error flag for the global one (larger
+// graphs, or FDLAYOUT_SP_GLOBAL=1 to test it on small ones).
+struct SpScratch {
+  int global_path = 0;
+  int* ints = nullptr;  // [sp_backprop_scratch_ints]; the last int is the error flag
+  int* err = nullptr;
+  ~SpScratch() { dev_free(ints); }
+  fd_status init(const fd_layout* h, cudaStream_t st) {
+    const char* g = std::getenv("FDLAYOUT_SP_GLOBAL");
+    global_path = (h->n > SP_SMEM_MAX_N || (g && std::atoi(g) != 0)) ? 1 : 0;
+    if (!global_path) return FD_OK;
+    const size_t cnt = sp_backprop_scratch_ints(h->n, h->sm_count) + 1;
+    fd_status s = dev_alloc(&ints, cnt);
+    if (s != FD_OK) return s;
+    err = ints + cnt - 1;
+    FD_CK(cudaMemsetAsync(err, 0, sizeof(int), st));
+    return FD_OK;
+  }
+  // after the stream is synchronised: FD_ERR_TIMEOUT if a search ran out of rounds
+  fd_status check() const {
+    if (!err) return FD_OK;
+    int v = 0;
+    if (cudaMemcpy(&v, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      cudaGetLastError();
+      return FD_ERR_CUDA;
+    }
+    return v ? FD_ERR_TIMEOUT : FD_OK;
+  }
+};
+
 fd_status fd_energy_length_grad(fd_layout* h, const float* X, float* grad_len, double* f_out) {
   if (!h) return FD_ERR_ARG;
   if (!X || !grad_len) return fail(h, FD_ERR_ARG);
@@ -877,10 +918,16 @@ fd_status fd_energy_length_grad(fd_layout* h, const float* X, float* grad_len, d
     return fail(h, s);
   }
   cudaStream_t st = h->stream;
+  SpScratch sp;
+  if ((s = sp.init(h, st)) != FD_OK) {
+    cleanup();
+    return fail(h, s);
+  }
   cudaError_t e = cudaMemcpyAsync(d_tik, tile_ik.data(), h->ntiles * sizeof(int2), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
     e = launch_length_grad(h->n, h->nb, h->dim, d_tik, h->ntiles, (const float*)h->D, dx, d_G, h->d_wrp, h->d_wci,
-                           h->d_wlen, h->d_wrev, h->wnnz, d_acc, dev_out ? grad_len : d_out, h->sm_count, st);
+                           h->d_wlen, h->d_wrev, h->wnnz, d_acc, dev_out ? grad_len : d_out, h->sm_count,
+                           sp.global_path, sp.ints, sp.err, st);
   if (e == cudaSuccess && !dev_out)
     e = cudaMemcpyAsync(grad_len, d_out, (size_t)h->wnnz * sizeof(float), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -889,6 +936,7 @@ fd_status fd_energy_length_grad(fd_layout* h, const float* X, float* grad_len, d
     cudaGetLastError();
     return fail(h, cuda_status(e));
   }
+  if ((s = sp.check()) != FD_OK) return fail(h, s);
   if (f_out) *f_out = c.f_final;
   return FD_OK;
 }
@@ -1014,8 +1062,14 @@ fd_status fd_adjoint_length_grad(fd_layout* h, float* grad_len) {
     return fail(h, s);
   }
   cudaStream_t st = h->stream;
+  SpScratch sp;
+  if ((s = sp.init(h, st)) != FD_OK) {
+    dev_free(d_acc);
+    dev_free(d_out);
+    return fail(h, s);
+  }
   cudaError_t e = launch_sp_backprop(h->n, h->nb, h->d_dbar, h->d_wrp, h->d_wci, h->d_wlen, h->d_wrev, h->wnnz, d_acc,
-                                     dev_out ? grad_len : d_out, h->sm_count, st);
+                                     dev_out ? grad_len : d_out, h->sm_count, sp.global_path, sp.ints, sp.err, st);
   if (e == cudaSuccess && !dev_out)
     e = cudaMemcpyAsync(grad_len, d_out, (size_t)h->wnnz * sizeof(float), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -1025,6 +1079,7 @@ fd_status fd_adjoint_length_grad(fd_layout* h, float* grad_len) {
     cudaGetLastError();
     return fail(h, cuda_status(e));
   }
+  if ((s = sp.check()) != FD_OK) return fail(h, s);
   return FD_OK;
 }
 

@@ -21,6 +21,7 @@
 #include <stdint.h>
 
 #include "fd_internal.cuh"
+#include "fd_sssp.cuh"
 
 namespace fdl {
 
@@ -147,6 +148,86 @@ __global__ void __launch_bounds__(256) sp_backprop_kernel(int n, int nb, int npo
       }
     }
     __syncthreads();
+  }
+}
+
+// The same back-propagation for graphs whose per-source state does not fit
+// shared memory: one source per CTA iteration, 7 n ints of CTA-private
+// global scratch.  Distances come from the frontier search (fd_sssp.cuh: the
+// same FP32 fixed point as the search that stored them), the parent of v is
+// the lowest-index u with dist[u] + l(u, v) == dist[v], and the subtree sums
+// move from the leaves to the source in rounds: a vertex joins the next round
+// once all of its children have added their sums to it (a count of pending
+// children per vertex), so no sort by distance is needed.  Work per source:
+// O(n + m), in about as many rounds as the tree is deep.  Scratch accesses
+// are L2 (.cg) loads and stores or atomics (atomics never refresh L1).
+__global__ void __launch_bounds__(1024) sp_backprop_global_kernel(int n, int nb, const int* __restrict__ rp,
+                                                                  const int* __restrict__ ci,
+                                                                  const float* __restrict__ len,
+                                                                  const float* __restrict__ Gt, float* gacc,
+                                                                  int* scratch, int* err) {
+  __shared__ int s_cnt[2];
+  int* base = scratch + (size_t)blockIdx.x * 7 * n;
+  int* dist = base;
+  int* mark = base + n;
+  int* fa = base + 2 * (size_t)n;
+  int* fb = base + 3 * (size_t)n;
+  int* par_e = base + 4 * (size_t)n;
+  int* pend = base + 5 * (size_t)n;
+  float* acc = reinterpret_cast<float*>(base + 6 * (size_t)n);
+  const int tid = threadIdx.x, bd = blockDim.x;
+  for (int s = blockIdx.x; s < n; s += gridDim.x) {
+    if (!sssp_frontier(n, s, rp, ci, len, dist, mark, fa, fb, s_cnt) && tid == 0) atomicExch(err, 1);
+    // shortest-path tree: the lowest-index tight neighbour is the parent
+    for (int v = tid; v < n; v += bd) {
+      const float dv = __int_as_float(__ldcg(dist + v));
+      int be = -1, bu = 0x7fffffff;
+      if (v != s && dv < INFINITY) {
+        for (int e = rp[v]; e < rp[v + 1]; ++e) {
+          const int u = ci[e];
+          if (u != v && __int_as_float(__ldcg(dist + u)) + len[e] == dv && u < bu) {
+            bu = u;
+            be = e;
+          }
+        }
+      }
+      __stcg(par_e + v, be);
+      __stcg(pend + v, 0);
+      __stcg(acc + v, (v != s) ? pair_value(Gt, nb, s, v) : 0.f);
+    }
+    __syncthreads();
+    for (int v = tid; v < n; v += bd) {
+      const int e = __ldcg(par_e + v);
+      if (e >= 0) atomicAdd(pend + ci[e], 1);
+    }
+    if (tid == 0) s_cnt[0] = 0;
+    __syncthreads();
+    // the leaves start
+    for (int v = tid; v < n; v += bd)
+      if (__ldcg(par_e + v) >= 0 && atomicAdd(pend + v, 0) == 0) __stcg(fa + atomicAdd(s_cnt, 1), v);
+    __syncthreads();
+    int na = s_cnt[0];
+    int* qa = fa;
+    int* qb = fb;
+    while (na > 0) {  // every vertex joins one round at most: at most n rounds
+      if (tid == 0) s_cnt[1] = 0;
+      __syncthreads();
+      for (int k = tid; k < na; k += bd) {
+        const int v = __ldcg(qa + k);
+        const int e = __ldcg(par_e + v);
+        const int u = ci[e];
+        const float a = __ldcg(acc + v);  // final: every child of v added its sum in an earlier round
+        atomicAdd(gacc + e, a);
+        atomicAdd(acc + u, a);
+        if (u != s && atomicSub(pend + u, 1) == 1) __stcg(qb + atomicAdd(s_cnt + 1, 1), u);
+      }
+      __syncthreads();
+      na = s_cnt[1];
+      int* t = qa;
+      qa = qb;
+      qb = t;
+      __syncthreads();  // every thread has read the count before it is reset
+    }
   }
 }
 
@@ -290,18 +371,34 @@ cudaError_t launch_pair_adjoint(int code, int n, int nb, int dim, const int2* ti
   return cudaGetLastError();
 }
 
-// Shortest-path back-propagation of an array of pair sensitivities (tile layout) to the edges.
-cudaError_t launch_sp_backprop(int n, int nb, const float* Gt, const int* rp, const int* ci, const float* len,
-                               const int* rev, int nnz, float* gacc, float* out, int sm_count, cudaStream_t st) {
-  int npow2 = 1;
-  while (npow2 < n) npow2 <<= 1;
-  const size_t smem = (size_t)npow2 * 8 + (size_t)n * 12;
-  cudaError_t e = cudaFuncSetAttribute(sp_backprop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(gacc, 0, (size_t)nnz * sizeof(float), st);
+// Shortest-path back-propagation of an array of pair sensitivities (tile
+// layout) to the edges: in shared memory per source up to SP_SMEM_MAX_N
+// vertices (unless global_path), else with global scratch (scratch:
+// [min(n, 2 SMs)][7 n] ints; err: one int, set if a search ran out of rounds).
+constexpr int SP_SMEM_MAX_N = 4096;
+
+size_t sp_backprop_scratch_ints(int n, int sm_count) {
+  const int grid = n < 2 * sm_count ? n : 2 * sm_count;
+  return (size_t)grid * 7 * (size_t)n;
+}
+
+static cudaError_t sp_backprop_run(int n, int nb, const float* Gt, const int* rp, const int* ci, const float* len,
+                                   const int* rev, int nnz, float* gacc, float* out, int sm_count, int global_path,
+                                   int* scratch, int* err, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(gacc, 0, (size_t)nnz * sizeof(float), st);
   if (e != cudaSuccess) return e;
   const int sgrid = n < 2 * sm_count ? n : 2 * sm_count;
-  sp_backprop_kernel<<<sgrid, 256, smem, st>>>(n, nb, npow2, rp, ci, len, Gt, gacc);
+  if (!global_path && n <= SP_SMEM_MAX_N) {
+    int npow2 = 1;
+    while (npow2 < n) npow2 <<= 1;
+    const size_t smem = (size_t)npow2 * 8 + (size_t)n * 12;
+    e = cudaFuncSetAttribute(sp_backprop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    sp_backprop_kernel<<<sgrid, 256, smem, st>>>(n, nb, npow2, rp, ci, len, Gt, gacc);
+  } else {
+    if (!scratch || !err) return cudaErrorInvalidValue;
+    sp_backprop_global_kernel<<<sgrid, 1024, 0, st>>>(n, nb, rp, ci, len, Gt, gacc, scratch, err);
+  }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int cgrid = (nnz + 255) / 256;
@@ -309,27 +406,21 @@ cudaError_t launch_sp_backprop(int n, int nb, const float* Gt, const int* rp, co
   return cudaGetLastError();
 }
 
+cudaError_t launch_sp_backprop(int n, int nb, const float* Gt, const int* rp, const int* ci, const float* len,
+                               const int* rev, int nnz, float* gacc, float* out, int sm_count, int global_path,
+                               int* scratch, int* err, cudaStream_t st) {
+  return sp_backprop_run(n, nb, Gt, rp, ci, len, rev, nnz, gacc, out, sm_count, global_path, scratch, err, st);
+}
+
 cudaError_t launch_length_grad(int n, int nb, int dim, const int2* tile_ik, int ntiles, const float* D,
                                const float* X, float* Gt, const int* rp, const int* ci, const float* len,
-                               const int* rev, int nnz, float* gacc, float* out, int sm_count, cudaStream_t st) {
+                               const int* rev, int nnz, float* gacc, float* out, int sm_count, int global_path,
+                               int* scratch, int* err, cudaStream_t st) {
   const int tgrid = ntiles < 8 * sm_count ? ntiles : 8 * sm_count;
   pair_dgrad_kernel<<<tgrid > 0 ? tgrid : 1, TILE, 0, st>>>(n, nb, dim, tile_ik, ntiles, D, X, Gt);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  int npow2 = 1;
-  while (npow2 < n) npow2 <<= 1;
-  const size_t smem = (size_t)npow2 * 8 + (size_t)n * 12;
-  e = cudaFuncSetAttribute(sp_backprop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(gacc, 0, (size_t)nnz * sizeof(float), st);
-  if (e != cudaSuccess) return e;
-  const int sgrid = n < 2 * sm_count ? n : 2 * sm_count;
-  sp_backprop_kernel<<<sgrid, 256, smem, st>>>(n, nb, npow2, rp, ci, len, Gt, gacc);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  const int cgrid = (nnz + 255) / 256;
-  if (nnz > 0) combine_directions_kernel<<<cgrid < 4096 ? cgrid : 4096, 256, 0, st>>>(nnz, rev, gacc, out);
-  return cudaGetLastError();
+  return sp_backprop_run(n, nb, Gt, rp, ci, len, rev, nnz, gacc, out, sm_count, global_path, scratch, err, st);
 }
 
 }  // namespace fdl

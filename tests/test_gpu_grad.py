@@ -64,8 +64,13 @@ def test_position_gradient_is_minus_two_forces(seed):
     assert np.linalg.norm(g - fd) <= 1e-5 * np.linalg.norm(fd)
 
 
+@pytest.mark.parametrize("path", ["shared", "global"])
 @pytest.mark.parametrize("seed", [0, 3])
-def test_length_gradient_matches_oracle_and_finite_differences(seed):
+def test_length_gradient_matches_oracle_and_finite_differences(seed, path, monkeypatch):
+    # both back-propagation kernels: per-source state in shared memory (n <= 4096)
+    # and in global scratch (larger graphs; forced here on the small one)
+    if path == "global":
+        monkeypatch.setenv("FDLAYOUT_SP_GLOBAL", "1")
     rp, ci, w, _ = _weighted_rgg(64, 3, seed)
     X0 = (np.random.default_rng(seed + 1).random((64, 3)) * 3.0).astype(np.float32)
     with api.Layout(rp, ci, dim=3, edge_len=w) as L:
@@ -131,16 +136,21 @@ def test_length_gradient_errors():
         with pytest.raises(api.FdError) as e:
             L.length_grad(X)
         assert e.value.status == 1
-    rp, ci = synth.grid(65, 65)  # 4225 vertices > FD_GRAD_MAX_N
+    # a disconnected weighted graph has pairs without a shortest path
+    rp, ci = synth.csr_from_edges(6, [(0, 1), (1, 2), (3, 4), (4, 5)])
     w = np.ones(len(ci), dtype=np.float32)
-    with api.Layout(rp, ci, dim=2, edge_len=w) as L:
+    with api.Layout(rp, ci, dim=2, edge_len=w, disconnected_policy=1) as L:
         with pytest.raises(api.FdError) as e:
-            L.length_grad(synth.initial_layout(4225, 2, 0))
+            L.length_grad(synth.initial_layout(6, 2, 0))
         assert e.value.status == 10
 
 
-@pytest.mark.parametrize("omega,vertex,solver", [(0.0, False, 0), (0.5, False, 0), (0.5, True, 0), (0.5, False, 1)])
-def test_unrolled_adjoint_matches_oracle(omega, vertex, solver):
+@pytest.mark.parametrize("omega,vertex,solver,path", [(0.0, False, 0, "shared"), (0.5, False, 0, "shared"),
+                                                      (0.5, True, 0, "shared"), (0.5, False, 1, "shared"),
+                                                      (0.5, False, 0, "global")])
+def test_unrolled_adjoint_matches_oracle(omega, vertex, solver, path, monkeypatch):
+    if path == "global":
+        monkeypatch.setenv("FDLAYOUT_SP_GLOBAL", "1")
     """Gradient of a loss on X^K (K = 4 iterations of Algorithm 2, checkpoints
     every 2) in X^0 and in the edge lengths, against the FP64 oracle's adjoint
     (itself pinned by finite differences), with the same acceptance decisions."""
@@ -189,3 +199,65 @@ def test_unrolled_adjoint_matches_oracle(omega, vertex, solver):
     g_l = lt.grad.cpu().numpy().astype(np.float64)
     assert np.linalg.norm(g_x - gX0) <= 2e-3 * np.linalg.norm(gX0)
     assert np.linalg.norm(g_l - gw) <= 2e-3 * np.linalg.norm(gw)
+
+
+def test_length_gradient_above_shared_memory_size():
+    """A weighted random geometric graph of 5000 vertices in 3-D (above the
+    shared-memory kernel's 4096): the global back-propagation, checked by what
+    holds at any size.  (1) Distance rows against scipy's Dijkstra.  (2) d_ij
+    is homogeneous of degree 1 in the edge lengths (scaling every length by c
+    scales every shortest path by c), so sum_e l_e df/dl_e = sum_{i<j} d_ij
+    df/dd_ij with df/dd_ij = -2 r (r - d) / d^3 (Eq. (1), w = d^-2), the right
+    side from scipy's distances in FP64.  (3) Central differences of the FP64
+    stress (oracle) over scipy's distances for perturbed lengths, two edges."""
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import shortest_path
+
+    n = 5000
+    rp, ci, pts = synth.random_geometric(n, 3, 6.0, seed=21)
+    A = sp.csr_matrix((np.ones(len(ci)), ci, rp), shape=(n, n))
+    ncomp, lab = sp.csgraph.connected_components(A, directed=False)
+    keep = np.flatnonzero(lab == np.argmax(np.bincount(lab)))
+    sub = A[keep][:, keep].tocsr()
+    sub.sort_indices()
+    rp, ci = sub.indptr.astype(np.int32), sub.indices.astype(np.int32)
+    n = len(rp) - 1
+    assert n > 4096
+    rng = np.random.default_rng(2)
+    lens = {}
+    w = np.empty(len(ci), dtype=np.float32)
+    for u in range(n):
+        for e in range(rp[u], rp[u + 1]):
+            key = (min(u, int(ci[e])), max(u, int(ci[e])))
+            lens.setdefault(key, np.float32(rng.uniform(0.5, 2.0)))
+            w[e] = lens[key]
+    X = (np.random.default_rng(3).random((n, 3)) * 8.0).astype(np.float32)
+
+    def scipy_D(wv):
+        return shortest_path(sp.csr_matrix((wv.astype(np.float64), ci, rp), shape=(n, n)), method="D",
+                             directed=False)
+
+    D = scipy_D(w)
+    with api.Layout(rp, ci, dim=3, edge_len=w) as L:
+        for r in (0, 17, n - 1):
+            assert np.allclose(L.distance_rows(r, 1)[0], D[r], rtol=1e-5, atol=0)
+        f, g = L.length_grad(X)
+    Xd = X.astype(np.float64)
+    assert f == pytest.approx(oracle.stress(Xd, D), rel=1e-5)
+    iu = np.triu_indices(n, 1)
+    r = np.sqrt(((Xd[iu[0]] - Xd[iu[1]]) ** 2).sum(axis=1))
+    d = D[iu]
+    rhs = float(np.sum(d * (-2.0 * r * (r - d) / d ** 3)))
+    lhs = 0.5 * float(np.sum(w.astype(np.float64) * g))  # each edge's two entries carry its derivative
+    assert lhs == pytest.approx(rhs, rel=1e-3)
+    h = 1e-4
+    wd = w.astype(np.float64)
+    for e in np.random.default_rng(4).choice(len(ci), 2, replace=False):
+        u = int(np.searchsorted(rp, e, side="right") - 1)
+        v = int(ci[e])
+        idx = [e] + [k for k in range(rp[v], rp[v + 1]) if ci[k] == u]
+        wp, wm = wd.copy(), wd.copy()
+        wp[idx] += h
+        wm[idx] -= h
+        fdv = (oracle.stress(Xd, scipy_D(wp)) - oracle.stress(Xd, scipy_D(wm))) / (2 * h)
+        assert g[e] == pytest.approx(fdv, rel=2e-3, abs=1e-4 * np.abs(g).max())
