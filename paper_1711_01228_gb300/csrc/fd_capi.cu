@@ -88,7 +88,7 @@ struct fd_layout {
   float* d_s = nullptr;
   float* d_inv_s = nullptr;
   float* d_vec = nullptr;  // pool of the per-vertex vectors
-  float* d_acc = nullptr;      // [3][n_pad][dimp] per-vertex accumulators
+  double* d_acc = nullptr;     // [3][n_pad][dimp] per-vertex accumulators (FP64)
   int nbuf = 2;                 // stages of the kernel's tile pipeline
   Ctrl* d_ctrl = nullptr;
   float* d_stage_in = nullptr;
@@ -780,7 +780,7 @@ fd_status fd_layout_create(fd_layout** out, int32_t n, int32_t dim, const int32_
   if ((s = dev_alloc(&h->d_cta_task_ptr, h->grid + 1)) != FD_OK) return bail(s);
   cudaStream_t st = h->stream;
   if (cudaMemcpyAsync(h->d_lut, lut.data(), lut.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemsetAsync(h->d_acc, 0, 3 * vs * sizeof(float), st) != cudaSuccess ||
+      cudaMemsetAsync(h->d_acc, 0, 3 * vs * sizeof(double), st) != cudaSuccess ||
       cudaMemcpyAsync(h->d_tasks, h->tasks.data(), h->ntasks * sizeof(TaskDesc), cudaMemcpyHostToDevice, st) !=
           cudaSuccess ||
       cudaMemcpyAsync(h->d_cta_task_ptr, h->cta_task_ptr.data(), (h->grid + 1) * sizeof(int),

@@ -109,10 +109,10 @@ struct KParams {
   // layout X^k, its RHS B; candidates Z = X^{k+1}, Xt = X~ and their RHS;
   // CG state Zw (iterate), R (residual), U = M^-1 R, W = L^W U, P, S = L^W P
   float *X, *Z, *Xt, *B, *Bz, *Bt, *Zw, *R, *U, *W, *P, *S;
-  // per-vertex sums of a pass, [3][n_pad][DIMP]: the pair kernels add their
-  // row and column partial sums with vector atomics; the vertex phase after
-  // the pass reads them and clears them for the next pass
-  float* acc;
+  // per-vertex sums of a pass, [3][n_pad][DIMP] FP64: the pair kernels add
+  // their FP32 row and column partial sums with FP64 atomics; the vertex phase
+  // after the pass reads them and clears them for the next pass
+  double* acc;
   Ctrl* ctrl;
   const double* omega_seq;     // [max_iter] omega of each iteration
   double* trace_f;             // [max_iter + 1]

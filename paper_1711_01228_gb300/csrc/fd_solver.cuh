@@ -165,6 +165,28 @@ __device__ __forceinline__ void atomic_addv(float* a, int i, const Vec<DIM>& v) 
   }
 }
 
+// Per-vertex pass sums are FP64: every tile's FP32 column partial and every
+// task's FP32 row partial are added to them with FP64 atomics, so the sum over
+// the CTAs loses nothing to rounding and hardly depends on the order of the
+// atomics (well below FP32 resolution, so runs repeat).  (No vector form of
+// the FP64 reduction exists: one instruction per coordinate.)
+template <int DIM>
+__device__ __forceinline__ void atomic_addv(double* a, int i, const Vec<DIM>& v) {
+  constexpr int DP = DimP<DIM>::v;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d)
+    asm volatile("red.relaxed.gpu.global.add.f64 [%0], %1;" ::"l"(a + (size_t)DP * i + d), "d"((double)v.c[d])
+                 : "memory");
+}
+
+// Stores v (FP32) into accumulator entry i (a given right-hand side, or 0).
+template <int DIM>
+__device__ __forceinline__ void st_acc(double* a, int i, const Vec<DIM>& v) {
+  constexpr int DP = DimP<DIM>::v;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) __stcg(a + (size_t)DP * i + d, (double)v.c[d]);
+}
+
 // PM_ENUM: stress of the NENUM extrapolations (1 + omega) z - omega x,
 // omega = 0, 0.5, ..., 9, of one CG solution z (Sec. 5.2.2).
 enum PairMode { PM_STRESS = 0, PM_FORCES = 1, PM_RHS = 2, PM_MATVEC = 3, PM_ENUM = 4 };
@@ -799,7 +821,7 @@ static_assert(sizeof(KParams) <= SmemLayout<1, CODE_U8>::OFF_TASKS - SmemLayout<
 #define FD_PASS_ATTR __noinline__
 #endif
 template <int DIM, int MODE, int NC, int CODE>
-__device__ FD_PASS_ATTR bool pair_pass_impl(PairState* ps_io, float* acc) {
+__device__ FD_PASS_ATTR bool pair_pass_impl(PairState* ps_io, double* acc) {
   // the dynamic shared memory itself (not a pointer argument), so that every
   // access compiles to a shared-memory instruction with a constant base
   extern __shared__ __align__(256) unsigned char smem[];
@@ -964,7 +986,7 @@ __device__ FD_PASS_ATTR bool pair_pass_impl(PairState* ps_io, float* acc) {
 
 template <int DIM, int MODE, int NC, int CODE>
 __device__ __forceinline__ bool pair_pass(const KParams& p, unsigned char* smem, PairState& ps, const PassSrc& src,
-                                          float* acc, double* rsum = nullptr) {
+                                          double* acc, double* rsum = nullptr) {
   using L = SmemLayout<DIM, CODE>;
   PassCtl* ctl = reinterpret_cast<PassCtl*>(smem + L::OFF_CTL);
   if (threadIdx.x == 0) {
@@ -1119,6 +1141,26 @@ __device__ __forceinline__ Vec<DIM> take_acc(float* a, int i) {
   stv<DIM>(a, i, vzero<DIM>());
   return v;
 }
+template <int DIM>
+__device__ __forceinline__ Vec<DIM> take_acc(double* a, int i) {
+  constexpr int DP = DimP<DIM>::v;
+  Vec<DIM> v;
+  if constexpr (DIM == 1) {
+    v.c[0] = (float)__ldcg(a + i);
+    __stcg(a + i, 0.0);
+  } else {
+    // DP = 2 or 4 doubles per vertex: 16-byte aligned pairs
+    const double2* q = reinterpret_cast<const double2*>(a + (size_t)DP * i);
+    const double2 t0 = __ldcg(q);
+    v.c[0] = (float)t0.x;
+    v.c[1] = (float)t0.y;
+    if constexpr (DIM == 3) v.c[2] = (float)__ldcg(q + 1).x;
+    double2* w = reinterpret_cast<double2*>(a + (size_t)DP * i);
+    __stcg(w, make_double2(0.0, 0.0));
+    if constexpr (DIM == 3) __stcg(w + 1, make_double2(0.0, 0.0));
+  }
+  return v;
+}
 
 __device__ __forceinline__ PassSrc direct_src(const float* a, int kind = SK_DIRECT) {
   PassSrc s;
@@ -1231,11 +1273,11 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
     }
     if (bad) set_error(ctrl, E_NONFINITE);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) stv<DIM>(p.acc + c * vs, i, vzero<DIM>());
+    for (int c = 0; c < 3; ++c) st_acc<DIM>(p.acc + c * vs, i, vzero<DIM>());
     if (p.mode == KM_SOLVE) {
       // the given right-hand side takes the place of L^X X; the CG starts from 0
       stv<DIM>(p.X, i, vzero<DIM>());
-      stv<DIM>(acc0, i, v);
+      st_acc<DIM>(acc0, i, v);
     } else {
       stv<DIM>(p.X, i, v);
     }
