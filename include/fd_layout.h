@@ -138,6 +138,8 @@ typedef struct {
   int32_t bfs_sweeps;      /* unit edges: passes over the edge list summed over the 64-source searches */
   int32_t factored;        /* 1 after fd_factor (FD_SOLVER_DIRECT available) */
   double factor_ms;        /* device time of the last fd_factor (CUDA events) */
+  int32_t tiles_per_stage; /* consecutive tiles of a task per pipeline stage (1 or 2) */
+  int32_t reserved;
 } fd_info;
 
 /* Fills *opt with the defaults: omega 0.5, FIXED, REL_DISP, seed 0,

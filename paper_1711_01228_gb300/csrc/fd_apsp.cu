@@ -34,16 +34,18 @@ __device__ __forceinline__ void put_code(void* D, int tile, int off, float value
     }
   } else {
     float* p = reinterpret_cast<float*>(D) + (size_t)tile * TILE * TILE + off;
-    *p = value;
+    *p = (value > 0.f) ? __frcp_rn(value) : 0.f;  // float tiles hold 1/d
   }
 }
 
+// d of a stored pair (0: no pair or not reached), decoded in FP64.
 template <int CODE>
-__device__ __forceinline__ float get_code(const void* D, int tile, int off) {
+__device__ __forceinline__ double get_code(const void* D, int tile, int off) {
   if constexpr (CODE == CODE_U8) {
-    return (float)(reinterpret_cast<const unsigned char*>(D)[(size_t)tile * TILE * TILE + off]);
+    return (double)(reinterpret_cast<const unsigned char*>(D)[(size_t)tile * TILE * TILE + off]);
   } else {
-    return reinterpret_cast<const float*>(D)[(size_t)tile * TILE * TILE + off];
+    const float c = reinterpret_cast<const float*>(D)[(size_t)tile * TILE * TILE + off];
+    return (c > 0.f) ? 1.0 / (double)c : 0.0;
   }
 }
 
@@ -157,7 +159,7 @@ __global__ void __launch_bounds__(1024) sssp_relax_kernel(int n, int nb, const i
       int k = J - I;
       if (k < 0) k += nb;
       const bool own = (k == 0) ? (v > src) : (k < LI);
-      if (own) D[(size_t)(tb + k) * TILE * TILE + (v % TILE) * TILE + il] = dv;
+      if (own) D[(size_t)(tb + k) * TILE * TILE + (v % TILE) * TILE + il] = __frcp_rn(dv);  // 1/d
       localmax = max(localmax, __float_as_int(dv));
     }
     atomicMax(maxbits, localmax);
@@ -181,7 +183,7 @@ __global__ void fill_unreached_kernel(int n, int nb, int ntiles, const int2* __r
     const int J = (ik.x + ik.y) % nb;
     const int i = ik.x * TILE + il, j = J * TILE + jl;
     const bool real = (i < n) && (j < n) && (ik.y > 0 || il < jl);
-    if (real && get_code<CODE>(D, tile, off) == 0.f) {
+    if (real && get_code<CODE>(D, tile, off) == 0.0) {
       ++local;
       if (write) put_code<CODE>(D, tile, off, fill, nullptr);
     }
@@ -205,8 +207,8 @@ __global__ void __launch_bounds__(TILE) rowsum_kernel(int n, int nb, const int* 
     if constexpr (CODE == CODE_U8) {
       return wl[reinterpret_cast<const unsigned char*>(D)[(size_t)tile * TILE * TILE + off]];
     } else {
-      const double d = reinterpret_cast<const float*>(D)[(size_t)tile * TILE * TILE + off];
-      return d > 0.0 ? 1.0 / (d * d) : 0.0;
+      const double c = reinterpret_cast<const float*>(D)[(size_t)tile * TILE * TILE + off];  // 1/d
+      return c * c;  // the weight the pair loop forms, (1/d)^2
     }
   };
   double acc = 0.0;
@@ -231,7 +233,7 @@ __global__ void __launch_bounds__(TILE) rowsum_kernel(int n, int nb, const int* 
 template <int CODE>
 __global__ void distance_rows_kernel(int n, int nb, const int* __restrict__ tile_base,
                                      const int* __restrict__ strip_len, const void* D, int row0, int nrows,
-                                     double* out) {
+                                     int hop_counts, double* out) {
   const size_t total = (size_t)nrows * n;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (size_t)gridDim.x * blockDim.x) {
@@ -254,7 +256,9 @@ __global__ void distance_rows_kernel(int n, int nb, const int* __restrict__ tile
         }
       }
     }
-    out[idx] = v;
+    // float tiles of a unit-edge graph hold 1/k for a hop count k < 2^24:
+    // rounding the decoded value gives k back exactly
+    out[idx] = hop_counts ? rint(v) : v;
   }
 }
 
@@ -465,15 +469,16 @@ cudaError_t launch_rowsum(int code, int n, int nb, const int* tile_base, const i
 }
 
 cudaError_t launch_distance_rows(int code, int n, int nb, const int* tile_base, const int* strip_len,
-                                 const void* D, int row0, int nrows, double* out, cudaStream_t st) {
+                                 const void* D, int row0, int nrows, int hop_counts, double* out, cudaStream_t st) {
   const size_t total = (size_t)nrows * n;
   int grid = (int)((total + 255) / 256);
   if (grid > 4096) grid = 4096;
   if (grid < 1) grid = 1;
   if (code == CODE_U8)
-    distance_rows_kernel<CODE_U8><<<grid, 256, 0, st>>>(n, nb, tile_base, strip_len, D, row0, nrows, out);
+    distance_rows_kernel<CODE_U8><<<grid, 256, 0, st>>>(n, nb, tile_base, strip_len, D, row0, nrows, 0, out);
   else
-    distance_rows_kernel<CODE_F32><<<grid, 256, 0, st>>>(n, nb, tile_base, strip_len, D, row0, nrows, out);
+    distance_rows_kernel<CODE_F32><<<grid, 256, 0, st>>>(n, nb, tile_base, strip_len, D, row0, nrows, hop_counts,
+                                                         out);
   return cudaGetLastError();
 }
 

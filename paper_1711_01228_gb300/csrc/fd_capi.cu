@@ -27,10 +27,10 @@ cudaError_t launch_fill(int code, int n, int nb, int ntiles, const int2* tile_ik
 cudaError_t launch_rowsum(int code, int n, int nb, const int* tile_base, const int* strip_len, const void* D,
                           float* s, float* inv_s, cudaStream_t st);
 cudaError_t launch_distance_rows(int code, int n, int nb, const int* tile_base, const int* strip_len,
-                                 const void* D, int row0, int nrows, double* out, cudaStream_t st);
-cudaError_t main_config_d1(int code, size_t lut_bytes, int nbuf, int* blocks_per_sm, size_t* smem);
-cudaError_t main_config_d2(int code, size_t lut_bytes, int nbuf, int* blocks_per_sm, size_t* smem);
-cudaError_t main_config_d3(int code, size_t lut_bytes, int nbuf, int* blocks_per_sm, size_t* smem);
+                                 const void* D, int row0, int nrows, int hop_counts, double* out, cudaStream_t st);
+cudaError_t main_config_d1(int code, size_t lut_bytes, int nbuf, int tps, int* blocks_per_sm, size_t* smem);
+cudaError_t main_config_d2(int code, size_t lut_bytes, int nbuf, int tps, int* blocks_per_sm, size_t* smem);
+cudaError_t main_config_d3(int code, size_t lut_bytes, int nbuf, int tps, int* blocks_per_sm, size_t* smem);
 cudaError_t launch_main_d1(int code, const KParams& p, int grid, size_t smem, cudaStream_t st);
 cudaError_t launch_main_d2(int code, const KParams& p, int grid, size_t smem, cudaStream_t st);
 cudaError_t launch_main_d3(int code, const KParams& p, int grid, size_t smem, cudaStream_t st);
@@ -89,7 +89,9 @@ struct fd_layout {
   float* d_inv_s = nullptr;
   float* d_vec = nullptr;  // pool of the per-vertex vectors
   double* d_acc = nullptr;     // [3][n_pad][dimp] per-vertex accumulators (FP64)
+  int weighted = 0;             // 1 if the graph was given edge lengths
   int nbuf = 2;                 // stages of the kernel's tile pipeline
+  int tps = 1;                  // tiles per stage
   Ctrl* d_ctrl = nullptr;
   float* d_stage_in = nullptr;
   float* d_stage_out = nullptr;
@@ -306,10 +308,10 @@ void build_tasks(fd_layout* h) {
   h->ntasks = (int)h->tasks.size();
 }
 
-cudaError_t main_config(int dim, int code, size_t lut_bytes, int nbuf, int* bps, size_t* smem) {
-  if (dim == 1) return main_config_d1(code, lut_bytes, nbuf, bps, smem);
-  if (dim == 2) return main_config_d2(code, lut_bytes, nbuf, bps, smem);
-  return main_config_d3(code, lut_bytes, nbuf, bps, smem);
+cudaError_t main_config(int dim, int code, size_t lut_bytes, int nbuf, int tps, int* bps, size_t* smem) {
+  if (dim == 1) return main_config_d1(code, lut_bytes, nbuf, tps, bps, smem);
+  if (dim == 2) return main_config_d2(code, lut_bytes, nbuf, tps, bps, smem);
+  return main_config_d3(code, lut_bytes, nbuf, tps, bps, smem);
 }
 
 cudaError_t launch_main(int dim, int code, const KParams& p, int grid, size_t smem, cudaStream_t st) {
@@ -538,6 +540,7 @@ KParams base_params(fd_layout* h, int mode) {
   p.lut = h->d_lut;
   p.lut_rows = h->lut_rows;
   p.nbuf = h->nbuf;
+  p.tps = h->tps;
   p.s = h->d_s;
   p.inv_s = h->d_inv_s;
   const size_t vs = (size_t)h->n_pad * h->dimp;
@@ -686,6 +689,7 @@ fd_status fd_layout_create(fd_layout** out, int32_t n, int32_t dim, const int32_
     cudaGetLastError();
     return bail(FD_ERR_CUDA);
   }
+  h->weighted = edge_len ? 1 : 0;
   if ((s = build_distances(h, rp, ci, edge_len ? &len : nullptr, disconnected_policy)) != FD_OK) return bail(s);
   if (edge_len) {
     // keep the CSR on the device for fd_energy_length_grad, with the reverse of every entry
@@ -734,29 +738,44 @@ fd_status fd_layout_create(fd_layout** out, int32_t n, int32_t dim, const int32_
       row[32 + k] = w;
     }
   }
-  // launch configuration of the cooperative kernel: the tile pipeline gets
-  // three stages unless that costs resident CTAs (large tables, 3-D)
+  // launch configuration of the cooperative kernel: the most resident CTAs,
+  // then two tiles per stage (uint8 codes: half the per-tile copy issue,
+  // barrier and vector formation) when two such stages keep that residency,
+  // then the most stages
   const size_t lut_bytes = (size_t)h->lut_rows * LUT_ROW;
-  int bps = 0, best_bps = 0, best_nbuf = 0;
-  int nbuf_only = 0;
+  int bps = 0, best_bps = 0, best_nbuf = 0, best_tps = 1;
+  int nbuf_only = 0, tps_only = 0;
   if (const char* e = std::getenv("FDLAYOUT_NBUF")) nbuf_only = std::atoi(e);  // testing: force the stage count
-  for (int nbuf = MAX_NBUF; nbuf >= 2; --nbuf) {
-    if (nbuf_only && nbuf != nbuf_only) continue;
-    size_t smem = 0;
-    if (main_config(dim, h->code, lut_bytes, nbuf, &bps, &smem) != cudaSuccess) {
-      cudaGetLastError();
-      bps = 0;
-    }
-    if (bps > best_bps) {
-      best_bps = bps;
-      best_nbuf = nbuf;
+  if (const char* e = std::getenv("FDLAYOUT_TPS")) tps_only = std::atoi(e);    // testing: force tiles per stage
+  for (int tps = 2; tps >= 1; --tps) {
+    // Two-tile stages measured faster only for uint8 codes in 1-D/2-D with a
+    // small lookup table (there two of them fit beside it at two CTAs per SM;
+    // 8 KB = hop diameters up to 30); 64 KB float tiles take one per stage, and
+    // in 3-D, or beside a large table, one-tile stages (more of them) win.
+    const bool tps2_ok = h->code == CODE_U8 && dim <= 2 && lut_bytes <= 8192;
+    if (tps == 2 && !tps2_ok && tps_only != 2) continue;
+    if (tps == 2 && (h->code != CODE_U8 || dim == 3)) continue;  // not instantiated
+    if (tps_only && tps != tps_only) continue;
+    for (int nbuf = MAX_NBUF; nbuf >= 2; --nbuf) {
+      if (nbuf_only && nbuf != nbuf_only) continue;
+      size_t smem = 0;
+      if (main_config(dim, h->code, lut_bytes, nbuf, tps, &bps, &smem) != cudaSuccess) {
+        cudaGetLastError();
+        bps = 0;
+      }
+      if (bps > best_bps) {
+        best_bps = bps;
+        best_nbuf = nbuf;
+        best_tps = tps;
+      }
     }
   }
-  if (best_bps < 1 || main_config(dim, h->code, lut_bytes, best_nbuf, &bps, &h->smem) != cudaSuccess) {
+  if (best_bps < 1 || main_config(dim, h->code, lut_bytes, best_nbuf, best_tps, &bps, &h->smem) != cudaSuccess) {
     cudaGetLastError();
     return bail(FD_ERR_CUDA);
   }
   h->nbuf = best_nbuf;
+  h->tps = best_tps;
   h->grid = bps * h->sm_count;
   if (const char* t = std::getenv("FDLAYOUT_BARRIER_TIMEOUT_NS")) {  // testing: make grid-barrier waits run out
     const long long v = std::atoll(t);
@@ -1342,8 +1361,8 @@ fd_status fd_distance_rows(fd_layout* h, int32_t row0, int32_t nrows, double* ou
   double* d = nullptr;
   fd_status s = dev_alloc(&d, (size_t)nrows * h->n);
   if (s != FD_OK) return fail(h, s);
-  cudaError_t e = launch_distance_rows(h->code, h->n, h->nb, h->d_tile_base, h->d_strip_len, h->D, row0, nrows, d,
-                                       h->stream);
+  cudaError_t e = launch_distance_rows(h->code, h->n, h->nb, h->d_tile_base, h->d_strip_len, h->D, row0, nrows,
+                                       h->weighted ? 0 : 1, d, h->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(out, d, (size_t)nrows * h->n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -1370,6 +1389,7 @@ fd_status fd_layout_info(const fd_layout* h, fd_info* info) {
   info->tasks = h->ntasks;
   info->apsp_ms = h->apsp_ms;
   info->stages = h->nbuf;
+  info->tiles_per_stage = h->tps;
   info->bfs_sweeps = h->bfs_sweeps;
   info->factored = h->d_ainv ? 1 : 0;
   info->factor_ms = h->factor_ms;

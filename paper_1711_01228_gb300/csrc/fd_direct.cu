@@ -50,18 +50,23 @@ __global__ void __launch_bounds__(256) dense_build_kernel(int n, int n_pad, int 
       // off-diagonal tiles hold pair (il, jl) at jl * TILE + il; the diagonal
       // tile holds it at max * TILE + min
       const int off = diag ? (max(il, jl) * TILE + min(il, jl)) : e;
-      float d;
-      if (code == CODE_U8) d = (float)reinterpret_cast<const unsigned char*>(D)[(size_t)t * TILE * TILE + off];
-      else d = reinterpret_cast<const float*>(D)[(size_t)t * TILE * TILE + off];
-      sd[jl * SL + il] = d;
+      // the weight d^-2: from the hop count, or the square of a float tile's 1/d
+      float w;
+      if (code == CODE_U8) {
+        const float d = (float)reinterpret_cast<const unsigned char*>(D)[(size_t)t * TILE * TILE + off];
+        w = (d > 0.f) ? 1.f / (d * d) : 0.f;
+      } else {
+        const float c = reinterpret_cast<const float*>(D)[(size_t)t * TILE * TILE + off];
+        w = c * c;
+      }
+      sd[jl * SL + il] = w;
     }
     __syncthreads();
     // entry (i, j) of A': s_i + shift on the diagonal, -d_ij^-2 + shift off it;
     // the identity on the padding
-    auto value = [&](int i, int j, float d) -> float {
+    auto value = [&](int i, int j, float w) -> float {
       if (i >= n || j >= n) return (i == j) ? 1.f : 0.f;
       if (i == j) return s[i] + shift;
-      const float w = (d > 0.f) ? 1.f / (d * d) : 0.f;
       return shift - w;
     };
     // block (I, J): row i = I*T + il, columns J*T + jl (coalesced over jl)

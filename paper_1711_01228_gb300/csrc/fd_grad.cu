@@ -41,16 +41,16 @@ __global__ void __launch_bounds__(TILE) pair_dgrad_kernel(int n, int nb, int dim
     const int il = threadIdx.x;
     for (int jl = 0; jl < TILE; ++jl) {
       const size_t off = (size_t)t * TILE * TILE + (size_t)jl * TILE + il;
-      const float dd = D[off];
+      const float c = D[off];  // 1/d (float tiles)
       float g = 0.f;
-      if (dd > 0.f) {
+      if (c > 0.f) {
         float r2 = 0.f;
         for (int d = 0; d < dim; ++d) {
           const float a = xi[il][d] - xj[jl][d];
           r2 = fmaf(a, a, r2);
         }
         const float r = sqrtf(r2);
-        g = -2.f * r * (r - dd) / (dd * dd * dd);
+        g = -2.f * r * c * c * fmaf(r, c, -1.f);  // -2 r (r - d) / d^3
       }
       Gt[off] = g;
     }
@@ -319,10 +319,14 @@ __global__ void __launch_bounds__(TILE) pair_adjoint_kernel(int n, int nb, int d
     for (int jj = 0; jj < TILE; ++jj) {
       const int jl = (il + jj) & (TILE - 1);  // rotate the columns so that the shared-memory atomics spread
       const size_t off = (size_t)t * TILE * TILE + (size_t)jl * TILE + il;
-      float dd;
-      if constexpr (CODE == CODE_U8) dd = (float)reinterpret_cast<const unsigned char*>(D)[off];
-      else dd = reinterpret_cast<const float*>(D)[off];
-      if (!(dd > 0.f)) continue;
+      float inv_d;  // 1/d: from the hop count, or stored in float tiles
+      if constexpr (CODE == CODE_U8) {
+        const float dd = (float)reinterpret_cast<const unsigned char*>(D)[off];
+        inv_d = (dd > 0.f) ? 1.f / dd : 0.f;
+      } else {
+        inv_d = reinterpret_cast<const float*>(D)[off];
+      }
+      if (!(inv_d > 0.f)) continue;
       float dx[3], dl[3], r2 = 0.f, ul = 0.f, ly = 0.f;
       for (int d = 0; d < dim; ++d) {
         dx[d] = xi[il][d] - xj[jl][d];
@@ -330,7 +334,6 @@ __global__ void __launch_bounds__(TILE) pair_adjoint_kernel(int n, int nb, int d
         r2 = fmaf(dx[d], dx[d], r2);
         ly = fmaf(dl[d], yi[il][d] - yj[jl][d], ly);
       }
-      const float inv_d = 1.f / dd;
       float g = 2.f * ly * inv_d * inv_d * inv_d;  // through w = d^-2 in L^W
       if (r2 > 0.f) {
         const float r = sqrtf(r2), inv_r = 1.f / r;

@@ -12,8 +12,10 @@
 //
 // A tile stores one code per (i, j) pair, column-major over i: byte
 // [jl * TILE + il] for i = I*TILE + il, j = J*TILE + jl.  Code 0 means "no
-// pair" (padding, i >= j inside a diagonal tile); a real pair stores its
-// ideal distance d_ij (hop count as uint8, or float32).
+// pair" (padding, i >= j inside a diagonal tile).  A real pair stores its
+// ideal distance d_ij as a uint8 hop count, or as float32 1/d_ij (the
+// correctly rounded reciprocal): the pair loop needs 1/d and 1/d^2, and the
+// reciprocal spares it a division per pair; an unreached pair (0) stays 0.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -100,7 +102,8 @@ struct KParams {
   const void* D;               // distance tiles
   const unsigned char* lut;    // [lut_rows][LUT_ROW] replicated table: 32 x 1/d, then 32 x 1/d^2
   int lut_rows;                // codes 0 .. lut_rows-1 present in the tiles
-  int nbuf;                    // stages of the tile pipeline (2 or 3)
+  int nbuf;                    // stages of the tile pipeline (2 to 4)
+  int tps;                     // tiles per stage (1, or 2 consecutive tiles of a task)
   const float* s;              // [n_pad] row sums of W (diagonal of L^W)
   const float* inv_s;          // [n_pad] 1/s (0 for padding)
   const float* x_in;           // [n][dim] input layout (device staging)

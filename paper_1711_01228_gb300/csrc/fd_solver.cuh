@@ -269,13 +269,19 @@ struct SmemLayout {
   static constexpr int OFF_PARAMS = 1536; // copy of the kernel parameters
   static constexpr int OFF_TASKS = 2048;  // this CTA's task descriptors
   static constexpr int OFF_LUT = OFF_TASKS + MAX_CTA_TASKS * 16;
-  static constexpr int STAGE = align_up(DBUF + 2 * RAWB, 128);
-  // stage s: codes, raw J, raw I, after the table
+  // A stage holds tps (1 or 2) consecutive tiles of a task: their codes, the
+  // raw arrays of their column blocks (array-major: [array][tps][TILE][DP],
+  // scalars [tps][TILE] after the vector arrays) and those of block I.
+  __host__ __device__ static constexpr int stage(int tps) { return align_up(tps * DBUF + (tps + 1) * RAWB, 128); }
   __host__ __device__ static constexpr int stage_base(int lut_bytes) { return align_up(OFF_LUT + lut_bytes, 128); }
-  __host__ __device__ static constexpr int off_d(int sb, int s) { return sb + s * STAGE; }
-  __host__ __device__ static constexpr int off_rawj(int sb, int s) { return sb + s * STAGE + DBUF; }
-  __host__ __device__ static constexpr int off_rawi(int sb, int s) { return sb + s * STAGE + DBUF + RAWB; }
-  __host__ __device__ static constexpr int bytes(int nbuf, int lut_bytes) { return stage_base(lut_bytes) + nbuf * STAGE; }
+  __host__ __device__ static constexpr int off_d(int sb, int s, int tps) { return sb + s * stage(tps); }
+  __host__ __device__ static constexpr int off_rawj(int sb, int s, int tps) { return sb + s * stage(tps) + tps * DBUF; }
+  __host__ __device__ static constexpr int off_rawi(int sb, int s, int tps) {
+    return sb + s * stage(tps) + tps * DBUF + tps * RAWB;
+  }
+  __host__ __device__ static constexpr int bytes(int nbuf, int lut_bytes, int tps) {
+    return stage_base(lut_bytes) + nbuf * stage(tps);
+  }
 };
 
 struct PairState {
@@ -294,6 +300,7 @@ struct PassArgs {
   long long timeout_ns;
   int n, n_pad, nb, ntasks, nbuf;  // ntasks: this CTA's
   int stage_base;                   // shared-memory offset of stage 0
+  int tps;                          // tiles per stage (1 or 2)
 };
 
 // --------------------------------------------------------------------------
@@ -503,11 +510,11 @@ template <int DIM, int MODE, int NC, int CODE, bool EDGE>
 __device__ __forceinline__ void tile_compute(const unsigned char* __restrict__ dt, const float* __restrict__ colv,
                                              const unsigned char* __restrict__ lut,
                                              Rows<DIM, NC, TileShape<DIM, MODE>::R>& rows, Vec<DIM> (&jout)[NC],
-                                             float (&st)[NStress<MODE, NC>::v], int tid) {
+                                             float (&st)[NStress<MODE, NC>::v], int tid,
+                                             int CA = TILE * DimP<DIM>::v /* floats between the candidate arrays */) {
   using TS = TileShape<DIM, MODE>;
   constexpr int R = TS::R, G = TS::G, CH = TS::CH;
   constexpr int DP = DimP<DIM>::v;
-  constexpr int CA = TILE * DP;  // floats between the formed candidate arrays
   constexpr bool NEED_K = (MODE != PM_MATVEC);
   constexpr bool NEED_W = (MODE == PM_MATVEC || MODE == PM_FORCES);
   const int q = tid & (G - 1), grp = tid / G;
@@ -582,10 +589,9 @@ __device__ __forceinline__ void tile_compute(const unsigned char* __restrict__ d
             W = pk2(lut_at(lut, lut_off(c, off_w, b0)), lut_at(lut, lut_off(c, off_w, b0 + 1)));
           }
         } else {
-          const float d0 = dv[2 * a2], d1 = dv[2 * a2 + 1];
-          const float i0 = d0 > 0.f ? __frcp_rn(d0) : 0.f, i1 = d1 > 0.f ? __frcp_rn(d1) : 0.f;
-          V = pk2(i0, i1);
-          W = pk2(i0 * i0, i1 * i1);
+          // float tiles hold 1/d (0 for no pair)
+          V = pk2(dv[2 * a2], dv[2 * a2 + 1]);
+          W = mul2(V, V);
         }
         if constexpr ((EDGE || CODE != CODE_U8) && (MODE == PM_STRESS || MODE == PM_RHS || MODE == PM_ENUM))
           NEGM = pk2(lo2(V) > 0.f ? -1.f : 0.f, hi2(V) > 0.f ? -1.f : 0.f);
@@ -672,17 +678,17 @@ __device__ __forceinline__ void tile_compute(const unsigned char* __restrict__ d
 }
 
 // Forms element t of block blk of the pass's vectors, in place in the raw
-// arrays (candidate c goes to array c's slot).
+// arrays (candidate c goes to array c's slot): raw is the block's part of
+// array 0, A the floats between arrays, sc the block's scalars (SK_CGU).
 template <int DIM, int NC>
-__device__ __forceinline__ void form_inplace(const PassSrc& s, float* raw, int blk, int t) {
+__device__ __forceinline__ void form_inplace(const PassSrc& s, float* raw, int blk, int t, int A, const float* sc) {
   constexpr int DP = DimP<DIM>::v;
-  constexpr int A = TILE * DP;  // floats per raw array
   const int kind = s.kind;
   if (kind == SK_CGU) {
     const Vec<DIM> r = lds_v<DIM>(raw, t);
     const Vec<DIM> w = lds_v<DIM>(raw + A, t);
     const Vec<DIM> sp = lds_v<DIM>(raw + 2 * A, t);
-    const float is = raw[3 * A + t];
+    const float is = sc[t];
     Vec<DIM> u;
 #pragma unroll
     for (int d = 0; d < DIM; ++d) u.c[d] = cg_u(r.c[d], w.c[d], sp.c[d], is, s.alpha[d], s.beta[d]);
@@ -720,46 +726,70 @@ __device__ __forceinline__ void form_inplace(const PassSrc& s, float* raw, int b
   }
 }
 
-// Thread 0 of a CTA: bulk copies (TMA) of a tile's distance codes and of
-// block J (and, at a task's first tile, block I) of every raw source array,
-// completing on the stage's mbarrier.
-template <int DIM, int CODE>
+// Thread 0 of a CTA: bulk copies (TMA) of a step's c tiles (consecutive in
+// the strip, so their codes are one copy) and of the raw source arrays of
+// their column blocks (one copy per array when the blocks are consecutive),
+// and, at a task's first step, of block I; all complete on the stage's
+// mbarrier.
+template <int DIM, int CODE, int TPS>
 __device__ __forceinline__ void issue_tile(const PassArgs& p, const PassSrc& src, unsigned char* smem, int tile, int I,
-                                        int J, bool first, int s) {
+                                        int J, int c, bool first, int s) {
   using L = SmemLayout<DIM, CODE>;
   constexpr int DP = DimP<DIM>::v;
   constexpr unsigned TBYTES = L::DBUF;
+  constexpr int tps = TPS;
   const int kind = src.kind;
   const int NA = src_arrays(kind);
   const unsigned RB = raw_bytes<DIM>(kind);
+  const int sb = p.stage_base;
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L::OFF_MISC) + s;
   fence_proxy_async();  // this CTA's generic accesses to the stage come before the copy overwrites it
-  mbar_expect_tx(mbar, TBYTES + (first ? 2 * RB : RB));
-  bulk_g2s(smem + L::off_d(p.stage_base, s), reinterpret_cast<const unsigned char*>(p.D) + (size_t)tile * TBYTES, TBYTES, mbar);
-#pragma unroll
-  for (int side = 0; side < 2; ++side) {
-    if (side == 1 && !first) break;
-    float* raw = reinterpret_cast<float*>(smem + (side ? L::off_rawi(p.stage_base, s) : L::off_rawj(p.stage_base, s)));
-    const int blk = side ? I : J;
+  mbar_expect_tx(mbar, c * (TBYTES + RB) + (first ? RB : 0));
+  bulk_g2s(smem + L::off_d(sb, s, tps), reinterpret_cast<const unsigned char*>(p.D) + (size_t)tile * TBYTES, c * TBYTES,
+           mbar);
+  // column blocks J, J + 1 (mod nb): one run of c blocks, or two runs at the wrap
+  float* rawj = reinterpret_cast<float*>(smem + L::off_rawj(sb, s, tps));
+  const int run0 = (J + c <= p.nb) ? c : 1;
+  for (int a = 0; a < NA; ++a) {
+    const bool scalar = (kind == SK_CGU && a == 3);
+    const unsigned ab = scalar ? TILE * 4 : TILE * DP * 4;  // bytes of one block
+    const int stride = scalar ? TILE : TILE * DP;           // floats of one block
+    float* dst = scalar ? rawj + 3 * tps * TILE * DP : rawj + a * tps * TILE * DP;
+    bulk_g2s(dst, src.a[a] + (size_t)J * stride, run0 * ab, mbar);
+    if (run0 < c) bulk_g2s(dst + stride, src.a[a], ab, mbar);  // block 0 after block nb - 1
+  }
+  if (first) {
+    float* rawi = reinterpret_cast<float*>(smem + L::off_rawi(sb, s, tps));
     for (int a = 0; a < NA; ++a) {
       const bool scalar = (kind == SK_CGU && a == 3);
       const unsigned ab = scalar ? TILE * 4 : TILE * DP * 4;
       const int stride = scalar ? TILE : TILE * DP;
-      bulk_g2s(raw + a * TILE * DP, src.a[a] + (size_t)blk * stride, ab, mbar);
+      bulk_g2s(rawi + a * TILE * DP, src.a[a] + (size_t)I * stride, ab, mbar);
     }
   }
 }
 
-// The tiles of one CTA in visiting order: its tasks m = 0..M-1 and the
-// tiles of each task in strip order; both reversed when `rev`.
+// The steps of one CTA in visiting order: its tasks m = 0..M-1 and, inside a
+// task, runs of c = tps consecutive tiles (fewer at the task's end) in strip
+// order; both reversed when `rev` (a step's tiles are k .. k + c - 1 either way).
+template <int TPS>
 struct TileIt {
-  int m, k, M;
+  int m, k, c, M;
   bool rev, valid;
   TaskDesc td;
+  __device__ __forceinline__ void set_from_hi(int hi) {  // reversed: the step ending at tile hi
+    k = max(td.k0, hi - TPS + 1);
+    c = hi - k + 1;
+  }
   __device__ __forceinline__ void load(const PassArgs& g) {
     const int mm = rev ? (M - 1 - m) : m;
     td = (mm < MAX_CTA_TASKS) ? g.tasks_s[mm] : g.tasks_g[mm];
-    k = rev ? td.k1 - 1 : td.k0;
+    if (rev) {
+      set_from_hi(td.k1 - 1);
+    } else {
+      k = td.k0;
+      c = min(TPS, td.k1 - td.k0);
+    }
   }
   __device__ __forceinline__ void begin(const PassArgs& g, bool r) {
     rev = r;
@@ -768,11 +798,16 @@ struct TileIt {
     valid = M > 0;
     if (valid) load(g);
   }
-  __device__ __forceinline__ bool first() const { return k == (rev ? td.k1 - 1 : td.k0); }
-  __device__ __forceinline__ bool last() const { return k == (rev ? td.k0 : td.k1 - 1); }
+  __device__ __forceinline__ bool first() const { return rev ? (k + c == td.k1) : (k == td.k0); }
+  __device__ __forceinline__ bool last() const { return rev ? (k == td.k0) : (k + c == td.k1); }
   __device__ __forceinline__ void next(const PassArgs& g) {
     if (!last()) {
-      k += rev ? -1 : 1;
+      if (rev) {
+        set_from_hi(k - 1);
+      } else {
+        k += c;
+        c = min(TPS, td.k1 - k);
+      }
       return;
     }
     if (++m >= M) {
@@ -781,7 +816,11 @@ struct TileIt {
     }
     load(g);
   }
-  __device__ __forceinline__ int J(int nb) const { return (td.I + k) % nb; }
+  // column block of the step's first tile (k < nb, so one subtraction wraps it)
+  __device__ __forceinline__ int J(int nb) const {
+    const int j = td.I + k;
+    return (j >= nb) ? j - nb : j;
+  }
   __device__ __forceinline__ int tile() const { return td.tile0 + (k - td.k0); }
 };
 
@@ -790,9 +829,10 @@ struct TileIt {
 struct PassCtl {
   PassSrc src;
   PassArgs a;
-  TileIt is;  // next tile to copy (thread 0 only)
-  int s_is;   // its stage
+  TileIt<1> is;  // next step to copy (thread 0 only; TileIt<2> has the same layout)
+  int s_is;      // its stage
 };
+static_assert(sizeof(TileIt<1>) == sizeof(TileIt<2>), "step iterators share the PassCtl slot");
 static_assert(sizeof(PassCtl) <= SmemLayout<1, CODE_U8>::OFF_RUN - SmemLayout<1, CODE_U8>::OFF_CTL,
               "PassCtl must fit its shared-memory slot");
 
@@ -820,7 +860,7 @@ static_assert(sizeof(KParams) <= SmemLayout<1, CODE_U8>::OFF_TASKS - SmemLayout<
 #ifndef FD_PASS_ATTR
 #define FD_PASS_ATTR __noinline__
 #endif
-template <int DIM, int MODE, int NC, int CODE>
+template <int DIM, int MODE, int NC, int CODE, int TPS>
 __device__ FD_PASS_ATTR bool pair_pass_impl(PairState* ps_io, double* acc) {
   // the dynamic shared memory itself (not a pointer argument), so that every
   // access compiles to a shared-memory instruction with a constant base
@@ -847,23 +887,26 @@ __device__ FD_PASS_ATTR bool pair_pass_impl(PairState* ps_io, double* acc) {
   // vectors written before the last grid barrier are read below by bulk copies
   if (tid == 0) fence_proxy_async_global();
   const bool rev = (ps.pass & 1) != 0;
-  TileIt it;  // computed tile
+  TileIt<TPS> it;  // computed step
   it.begin(g, rev);
   int s_it = 0;  // its stage
+  TileIt<TPS>& ctl_is = *reinterpret_cast<TileIt<TPS>*>(&ctl->is);
   if (tid == 0) {
-    TileIt is = it;
+    TileIt<TPS> is = it;
     int s_is = 0;
     for (int k = 0; k < nbuf - 1 && is.valid; ++k) {
-      issue_tile<DIM, CODE>(p, src, smem, is.tile(), is.td.I, is.J(g.nb), is.first(), s_is);
+      issue_tile<DIM, CODE, TPS>(p, src, smem, is.tile(), is.td.I, is.J(g.nb), is.c, is.first(), s_is);
       is.next(g);
       s_is = (s_is + 1 == nbuf) ? 0 : s_is + 1;
     }
-    ctl->is = is;
+    ctl_is = is;
     ctl->s_is = s_is;
   }
   Rows<DIM, NC, R> rows;
+  constexpr int tps = TPS;
+  constexpr int astr = TPS * TILE * DP;  // floats between the raw arrays of the column blocks
   while (it.valid) {
-    const int I = it.td.I, J = it.J(g.nb);
+    const int I = it.td.I, J0 = it.J(g.nb), nc = it.c;
     const bool first = it.first(), last = it.last();
     const unsigned ph = (ps.parity >> s_it) & 1u;
     if (!mbar_wait(mbar + s_it, ph, p.timeout_ns)) {
@@ -874,16 +917,21 @@ __device__ FD_PASS_ATTR bool pair_pass_impl(PairState* ps_io, double* acc) {
       return false;
     }
     ps.parity ^= (1u << s_it);
-    float* rawj = reinterpret_cast<float*>(smem + L::off_rawj(sb, s_it));
-    float* rawi = reinterpret_cast<float*>(smem + L::off_rawi(sb, s_it));
-    form_inplace<DIM, NC>(src, rawj, J, tid);
-    if (first) form_inplace<DIM, NC>(src, rawi, I, tid);
-    __syncthreads();  // formed vectors visible; every thread is done with the stage of the previous tile
-    if (tid == 0 && ctl->is.valid) {
-      TileIt is = ctl->is;
-      issue_tile<DIM, CODE>(p, src, smem, is.tile(), is.td.I, is.J(g.nb), is.first(), ctl->s_is);
+    float* rawj = reinterpret_cast<float*>(smem + L::off_rawj(sb, s_it, tps));
+    float* rawi = reinterpret_cast<float*>(smem + L::off_rawi(sb, s_it, tps));
+    form_inplace<DIM, NC>(src, rawj, J0, tid, astr, rawj + 3 * astr);
+    if constexpr (TPS == 2) {
+      if (nc == 2)
+        form_inplace<DIM, NC>(src, rawj + TILE * DP, (J0 + 1 == g.nb) ? 0 : J0 + 1, tid, astr,
+                              rawj + 3 * astr + TILE);
+    }
+    if (first) form_inplace<DIM, NC>(src, rawi, I, tid, TILE * DP, rawi + 3 * TILE * DP);
+    __syncthreads();  // formed vectors visible; every thread is done with the stage of the previous step
+    if (tid == 0 && ctl_is.valid) {
+      TileIt<TPS> is = ctl_is;
+      issue_tile<DIM, CODE, TPS>(p, src, smem, is.tile(), is.td.I, is.J(g.nb), is.c, is.first(), ctl->s_is);
       is.next(g);
-      ctl->is = is;
+      ctl_is = is;
       ctl->s_is = (ctl->s_is + 1 == nbuf) ? 0 : ctl->s_is + 1;
     }
     const int q = tid & (G - 1);
@@ -901,37 +949,48 @@ __device__ FD_PASS_ATTR bool pair_pass_impl(PairState* ps_io, double* acc) {
           }
         }
     }
-    Vec<DIM> jout[NC];
-    float st[NS];
-    const unsigned char* dt = smem + L::off_d(sb, s_it);
-    const bool edge = (it.k == 0) || (g.n < g.n_pad && (I == g.nb - 1 || J == g.nb - 1));
-    if constexpr (MODE == PM_STRESS || MODE == PM_RHS || MODE == PM_ENUM || (MODE == PM_MATVEC && kMatvecRcp)) {
-      if (edge) tile_compute<DIM, MODE, NC, CODE, true>(dt, rawj, lut, rows, jout, st, tid);
-      else tile_compute<DIM, MODE, NC, CODE, false>(dt, rawj, lut, rows, jout, st, tid);
-    } else {
-      tile_compute<DIM, MODE, NC, CODE, false>(dt, rawj, lut, rows, jout, st, tid);
-    }
-    if constexpr (MODE == PM_STRESS || MODE == PM_RHS || MODE == PM_ENUM) {
+    // the step's tiles: u = 0, and u = 1 when the step holds two
+    auto do_tile = [&](int u) {
+      const int Ju = (J0 + u >= g.nb) ? J0 + u - g.nb : J0 + u;
+      Vec<DIM> jout[NC];
+      float st[NS];
+      const unsigned char* dt = smem + L::off_d(sb, s_it, tps) + u * L::DBUF;
+      const float* colv = rawj + u * TILE * DP;
+      const bool edge = (it.k + u == 0) || (g.n < g.n_pad && (I == g.nb - 1 || Ju == g.nb - 1));
+      if constexpr (MODE == PM_STRESS || MODE == PM_RHS || MODE == PM_ENUM || (MODE == PM_MATVEC && kMatvecRcp)) {
+        if (edge) tile_compute<DIM, MODE, NC, CODE, true>(dt, colv, lut, rows, jout, st, tid, astr);
+        else tile_compute<DIM, MODE, NC, CODE, false>(dt, colv, lut, rows, jout, st, tid, astr);
+      } else {
+        tile_compute<DIM, MODE, NC, CODE, false>(dt, colv, lut, rows, jout, st, tid, astr);
+      }
+      if constexpr (MODE == PM_STRESS || MODE == PM_RHS || MODE == PM_ENUM) {
 #pragma unroll
-      for (int c = 0; c < NS; ++c) kahan_add(ssum[c], scomp[c], st[c]);
-    }
-    if constexpr (MODE != PM_STRESS && MODE != PM_ENUM) {
-      // column sums: thread t holds column t of block J
-      const int j = J * TILE + tid;
-      if (j < g.n) {
+        for (int c = 0; c < NS; ++c) kahan_add(ssum[c], scomp[c], st[c]);
+      }
+      if constexpr (MODE != PM_STRESS && MODE != PM_ENUM) {
+        // column sums: thread t holds column t of block Ju
+        const int j = Ju * TILE + tid;
+        if (j < g.n) {
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          Vec<DIM> v = jout[c];
-          if constexpr (MODE != PM_MATVEC) {
+          for (int c = 0; c < NC; ++c) {
+            Vec<DIM> v = jout[c];
+            if constexpr (MODE != PM_MATVEC) {
 #pragma unroll
-            for (int d = 0; d < DIM; ++d) v.c[d] = -v.c[d];
+              for (int d = 0; d < DIM; ++d) v.c[d] = -v.c[d];
+            }
+            atomic_addv<DIM>(acc + c * vs, j, v);
           }
-          atomic_addv<DIM>(acc + c * vs, j, v);
         }
       }
+    };
+    do_tile(0);
+    if constexpr (TPS == 2) {
+      if (nc == 2) do_tile(1);
+    }
+    if constexpr (MODE != PM_STRESS && MODE != PM_ENUM) {
       if (last) {
         // row sums of the task: the R groups' partials meet in the stage's code buffer
-        float* red = reinterpret_cast<float*>(smem + L::off_d(sb, s_it));  // [NC][R groups][TILE][DP]
+        float* red = reinterpret_cast<float*>(smem + L::off_d(sb, s_it, tps));  // [NC][R groups][TILE][DP]
         const int grp = tid / G;
         __syncthreads();  // every warp is done with the codes
 #pragma unroll
@@ -984,7 +1043,7 @@ __device__ FD_PASS_ATTR bool pair_pass_impl(PairState* ps_io, double* acc) {
   return true;
 }
 
-template <int DIM, int MODE, int NC, int CODE>
+template <int DIM, int MODE, int NC, int CODE, int TPS>
 __device__ __forceinline__ bool pair_pass(const KParams& p, unsigned char* smem, PairState& ps, const PassSrc& src,
                                           double* acc, double* rsum = nullptr) {
   using L = SmemLayout<DIM, CODE>;
@@ -1005,9 +1064,10 @@ __device__ __forceinline__ bool pair_pass(const KParams& p, unsigned char* smem,
     a.ntasks = p.g.cta_task_ptr[blockIdx.x + 1] - t0;
     a.nbuf = p.nbuf;
     a.stage_base = L::stage_base(CODE == CODE_U8 ? p.lut_rows * LUT_ROW : 0);
+    a.tps = p.tps;
   }
   __syncthreads();
-  return pair_pass_impl<DIM, MODE, NC, CODE>(&ps, acc);
+  return pair_pass_impl<DIM, MODE, NC, CODE, TPS>(&ps, acc);
 }
 
 // --------------------------------------------------------------------------
@@ -1181,7 +1241,9 @@ __device__ __forceinline__ PassSrc direct_src(const float* a, int kind = SK_DIRE
 
 // WITH_ENUM: the variant that also runs the enumerating strategy (its pass is
 // kept out of the other variant, whose passes then keep their registers).
-template <int DIM, int CODE, bool WITH_ENUM>
+// TPS: tiles per pipeline stage (a kernel of its own, so that every kernel
+// calls one variant of each pass).
+template <int DIM, int CODE, bool WITH_ENUM, int TPS = 1>
 __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
   using L = SmemLayout<DIM, CODE>;
   constexpr int DP = DimP<DIM>::v;
@@ -1285,7 +1347,7 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
   FD_SYNC(1);
 
   if (p.mode == KM_ENERGY) {
-    if (!pair_pass<DIM, PM_STRESS, 1, CODE>(p, smem, ps, direct_src(p.X), acc0, RSUM)) return;
+    if (!pair_pass<DIM, PM_STRESS, 1, CODE, TPS>(p, smem, ps, direct_src(p.X), acc0, RSUM)) return;
     FD_SYNC_RED(2, red_stress(1));
     if (blockIdx.x == 0 && tid == 0) {
       df f[1];
@@ -1300,7 +1362,7 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
   }
 
   if (p.mode == KM_FORCES) {
-    if (!pair_pass<DIM, PM_FORCES, 1, CODE>(p, smem, ps, direct_src(p.X), acc0)) return;
+    if (!pair_pass<DIM, PM_FORCES, 1, CODE, TPS>(p, smem, ps, direct_src(p.X), acc0)) return;
     FD_SYNC(3);
     vertex_phase<0>(p, red64, nullptr, [&](int i, df(&)[1]) {
       const Vec<DIM> f = take_acc<DIM>(acc0, i);
@@ -1326,7 +1388,7 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
   // b = L^{X^0} X^0 (right-hand side of Eq. (2-5)) and f(X^0) (Eq. (1));
   // KM_SOLVE has its right-hand side already
   if (p.mode != KM_SOLVE) {
-    if (!pair_pass<DIM, PM_RHS, 1, CODE>(p, smem, ps, direct_src(p.X), acc0, RSUM)) return;
+    if (!pair_pass<DIM, PM_RHS, 1, CODE, TPS>(p, smem, ps, direct_src(p.X), acc0, RSUM)) return;
     FD_SYNC_RED(4, red_stress(1));
   }
   if (tid == 0) {
@@ -1364,7 +1426,7 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
         src.sel = rs->accept;
         src.oms = p.om_scale;
       }
-      if (!pair_pass<DIM, PM_MATVEC, 1, CODE>(p, smem, ps, src, acc2)) return;
+      if (!pair_pass<DIM, PM_MATVEC, 1, CODE, TPS>(p, smem, ps, src, acc2)) return;
       if (tid == 0) rs->passes_mv += 1.0;
       FD_SYNC(5);
       // r0 = b - L^W x0, u0 = M^-1 r0, p = s = 0; displacement sums of x0 against X^k.
@@ -1479,7 +1541,7 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
         // step and by every refinement's vertex phase)
         dense_apply<DIM>(p, dbuf, p.R, p.P);
         FD_SYNC(10);
-        if (!pair_pass<DIM, PM_MATVEC, 1, CODE>(p, smem, ps, direct_src(p.P), acc2)) return;
+        if (!pair_pass<DIM, PM_MATVEC, 1, CODE, TPS>(p, smem, ps, direct_src(p.P), acc2)) return;
         if (tid == 0) {
           rs->passes_mv += 1.0;
           ++rs->it;
@@ -1520,7 +1582,7 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
     }
     // ---- CG on L^W Z = b, one reduction per step
     if (p.solver != SOLVER_DIRECT && !rs->all_conv) {
-      if (!pair_pass<DIM, PM_MATVEC, 1, CODE>(p, smem, ps, direct_src(p.U), acc2)) return;
+      if (!pair_pass<DIM, PM_MATVEC, 1, CODE, TPS>(p, smem, ps, direct_src(p.U), acc2)) return;
       if (tid == 0) rs->passes_mv += 1.0;
       FD_SYNC(6);
       // w0 = L^W u0 and delta0 = (w0, u0).  Slots [0,D).
@@ -1571,7 +1633,7 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
           src.alpha[d] = rs->alpha[d];
           src.beta[d] = rs->beta[d];
         }
-        if (!pair_pass<DIM, PM_MATVEC, 1, CODE>(p, smem, ps, src, acc2)) return;
+        if (!pair_pass<DIM, PM_MATVEC, 1, CODE, TPS>(p, smem, ps, src, acc2)) return;
         if (tid == 0) {
           rs->passes_mv += 1.0;
           ++rs->it;
@@ -1695,7 +1757,7 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
         rs->passes_st += 1.0;            // the pass on the selected candidate
       }
       if constexpr (WITH_ENUM) {
-        if (!pair_pass<DIM, PM_ENUM, 2, CODE>(p, smem, ps, src, acc0, RSUM)) return;
+        if (!pair_pass<DIM, PM_ENUM, 2, CODE, TPS>(p, smem, ps, src, acc0, RSUM)) return;
       }
       auto red_enum = [&](const double* sums) { take_sums<NENUM>(ctrl, sums); };
       FD_SYNC_RED(8, red_enum);
@@ -1724,7 +1786,7 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
       sel.om = rs->om_prev;
       sel.sel = rs->accept;
       sel.oms = p.om_scale;
-      if (!pair_pass<DIM, PM_RHS, 1, CODE>(p, smem, ps, sel, acc0, RSUM)) return;
+      if (!pair_pass<DIM, PM_RHS, 1, CODE, TPS>(p, smem, ps, sel, acc0, RSUM)) return;
       FD_SYNC_RED(8, red_stress(1));
       if (tid == 0) {
         df fz[1];
@@ -1771,10 +1833,10 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
       rs->passes_st += two ? 2.0 : 1.0;
     }
     if (two) {
-      if (!pair_pass<DIM, PM_RHS, 2, CODE>(p, smem, ps, src, acc0, RSUM)) return;
+      if (!pair_pass<DIM, PM_RHS, 2, CODE, TPS>(p, smem, ps, src, acc0, RSUM)) return;
       FD_SYNC_RED(8, red_stress(2));
     } else {
-      if (!pair_pass<DIM, PM_RHS, 1, CODE>(p, smem, ps, src, acc0, RSUM)) return;
+      if (!pair_pass<DIM, PM_RHS, 1, CODE, TPS>(p, smem, ps, src, acc0, RSUM)) return;
       FD_SYNC_RED(8, red_stress(1));
     }
     if (tid == 0) {

@@ -5,9 +5,10 @@
 namespace fdl {
 
 template <int CODE>
-static cudaError_t config_one(size_t lut_bytes, int nbuf, int* blocks_per_sm, size_t* smem) {
+static cudaError_t config_one(size_t lut_bytes, int nbuf, int tps, int* blocks_per_sm, size_t* smem) {
+  if (tps != 1) return cudaErrorInvalidValue;  // one tile per stage in 3-D
   using L = SmemLayout<3, CODE>;
-  *smem = (size_t)L::bytes(nbuf, CODE == CODE_U8 ? (int)lut_bytes : 0);
+  *smem = (size_t)L::bytes(nbuf, CODE == CODE_U8 ? (int)lut_bytes : 0, tps);
   cudaError_t e = cudaFuncSetAttribute(fd_main_kernel<3, CODE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)*smem);
   if (e != cudaSuccess) return e;
@@ -21,9 +22,9 @@ static cudaError_t config_one(size_t lut_bytes, int nbuf, int* blocks_per_sm, si
   return e;
 }
 
-cudaError_t main_config_d3(int code, size_t lut_bytes, int nbuf, int* blocks_per_sm, size_t* smem) {
-  return code == CODE_U8 ? config_one<CODE_U8>(lut_bytes, nbuf, blocks_per_sm, smem)
-                         : config_one<CODE_F32>(lut_bytes, nbuf, blocks_per_sm, smem);
+cudaError_t main_config_d3(int code, size_t lut_bytes, int nbuf, int tps, int* blocks_per_sm, size_t* smem) {
+  return code == CODE_U8 ? config_one<CODE_U8>(lut_bytes, nbuf, tps, blocks_per_sm, smem)
+                         : config_one<CODE_F32>(lut_bytes, nbuf, tps, blocks_per_sm, smem);
 }
 
 cudaError_t launch_main_d3(int code, const KParams& p, int grid, size_t smem, cudaStream_t st) {

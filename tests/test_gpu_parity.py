@@ -300,3 +300,28 @@ def test_invariance_under_rigid_motion(dim):
         FY = L.forces(Y.astype(np.float32)).astype(np.float64)
     assert fY == pytest.approx(fX, rel=1e-5)
     assert np.linalg.norm(FY - FX @ Q.T) <= 1e-4 * np.linalg.norm(FX)
+
+
+@pytest.mark.parametrize("tps", ["1", "2"])
+def test_stage_shapes_agree_with_oracle(tps, monkeypatch):
+    # one or two consecutive tiles per pipeline stage (the two-tile kernel serves
+    # uint8 codes in 1-D/2-D): a graph of 6 blocks with a ragged last block, so
+    # that tasks end on odd and even tile counts, steps wrap past the last block,
+    # and few CTAs walk many steps
+    monkeypatch.setenv("FDLAYOUT_TPS", tps)
+    monkeypatch.setenv("FDLAYOUT_MAX_CTAS", "5")
+    rp, ci = synth.barabasi_albert(700, 3, seed=9)
+    n = len(rp) - 1
+    D = _dense(rp, ci)
+    X0 = synth.initial_layout(n, 2, seed=2)
+    with api.Layout(rp, ci, dim=2) as L:
+        assert L.info()["tiles_per_stage"] == int(tps)
+        assert L.energy(X0) == pytest.approx(oracle.stress(X0, D), rel=1e-5)
+        F = L.forces(X0).astype(np.float64)
+        A = oracle.force_abs(X0, D)
+        assert np.all(np.abs(F - oracle.forces(X0, D)) <= 1e-5 * A + 1e-30)
+        X = X0.copy()
+        r = L.run(X, trace=True, omega=0.5, tol=1e-4, max_iter=1000)
+    ref = oracle.sor_run(D, X0.astype(np.float64), omega=0.5, tol=1e-4, max_iter=1000)
+    assert r.stress == pytest.approx(ref.stress, rel=1e-4)
+    assert abs(r.iterations - ref.iterations) <= max(1, math.ceil(0.02 * ref.iterations))
