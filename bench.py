@@ -572,6 +572,7 @@ def run_batched(args, local_rank, peak_tflops):
         times.append(res.stats["kernel_ms"])
     ms = statistics.median(times)
     info = B.info()
+    tiles = B.tiles()
     st = res.stats
     it = res.iterations
     pairs_s = st["pairs"] / (ms / 1e3)
@@ -608,8 +609,15 @@ def run_batched(args, local_rank, peak_tflops):
         "graphs": G, "total_vertices": int(sizes.sum()), "ms": ms, "steps": len(times),
         "pairs_per_s": pairs_s, "sor_iterations_per_s": float(it.sum()) / (ms / 1e3), "graphs_per_s": G / (ms / 1e3),
         "converged": int((it < args.max_iter).sum()), "hit_max_iter": int((it >= args.max_iter).sum()),
-        "launch": {"kernel": "fd_batch_kernel", "grid": info["grid"], "groups_per_cta": groups, "stages": stages,
-                   "tuned": True, "cuda_graph": bool(info["graph_captured"]), "launches_per_run": 1},
+        "launch": {"kernel": "fd_batch_kernel", "grid": info["grid"], "units_per_cta": groups, "stages": stages,
+                   "tuned": True, "cuda_graph": bool(info["graph_captured"]),
+                   "launches_per_run": "one CUDA graph: one persistent launch per tile edge (128, 64, 32)",
+                   "tile_edge_by_bucket": dict(zip(["n<=32", "n<=64", "n<=128", "n<=256", "n<=512", "n<=1024",
+                                                    "n<=2048"], tiles)),
+                   "graphs_by_tile_edge": {"128": info["graphs_t128"], "64": info["graphs_t64"],
+                                           "32": info["graphs_t32"]},
+                   "tuner": "fd_batch_tune: launch shape (units x stages), then per size bucket the tile edge "
+                            "in {128, 64, 32} (each bucket's graphs alone, 5 iterations, best of 2)"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops},
         "l2": "flushed before each timed run (256 MB write)",

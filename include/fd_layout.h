@@ -399,6 +399,10 @@ typedef struct fd_batch fd_batch; /* opaque; owns every graph's distances and st
 /* Largest graph of a batch (vertices). */
 #define FD_BATCH_MAX_N 2048
 
+/* Size buckets of the tile-edge choice: bucket k holds the graphs with
+ * 32 * 2^(k-1) < n <= 32 * 2^k (bucket 0: n <= 32; bucket 6: n <= 2048). */
+#define FD_BATCH_BUCKETS 7
+
 /* Facts about a batch handle. */
 typedef struct {
   int32_t num_graphs, dim;
@@ -414,6 +418,8 @@ typedef struct {
   int32_t stages;          /* tiles in flight per group (2 or 3) */
   int32_t graph_captured;  /* 1 once the launch runs from a captured CUDA graph */
   double apsp_ms;          /* device time of the batched shortest-path kernels at creation */
+  int64_t small_tile_bytes;  /* device bytes of the 32 x 32 and 64 x 64 tiles (graphs below tile edge 128) */
+  int32_t graphs_t128, graphs_t64, graphs_t32;  /* graphs laid out at tile edge 128, 64, 32 */
 } fd_batch_info;
 
 /* Builds a batch of num_graphs undirected graphs in one concatenated CSR:
@@ -437,8 +443,9 @@ fd_status fd_batch_create(fd_batch** out, int32_t num_graphs, int32_t dim, const
 /* Releases every resource of the batch (NULL is a no-op). */
 void fd_batch_destroy(fd_batch* b);
 
-/* Algorithm 2 on every graph of the batch, in one persistent launch (replayed
- * from a captured CUDA graph after the first call with the same launch
+/* Algorithm 2 on every graph of the batch, in one persistent launch per tile
+ * edge in use (the graphs at edge 128, 64 and 32 in turn, all three replayed
+ * from one captured CUDA graph after the first call with the same launch
  * configuration).  X (float32 [N][dim], host or device; graph g's rows are
  * graph_ptr[g] ..) holds every X^0 on entry and the final layouts on return.
  *   opt        strategy FD_OMEGA_FIXED or FD_OMEGA_PROB (the same omega
@@ -464,18 +471,39 @@ fd_status fd_batch_run(fd_batch* b, float* X, const fd_options* opt, const doubl
 fd_status fd_batch_results(const fd_batch* b, int32_t* status, int32_t* cg_steps, int32_t* accepted, double* crit,
                            double* matvec_passes, double* stress_passes, double* graph_ms);
 
-/* Chooses the launch shape of the persistent kernel (128-thread tile groups
- * per CTA in {1, 2} x tiles in flight per group in {2, 3}) by timing each
- * feasible shape on this batch: `probe_iter` iterations of fd_batch_run from
- * X (host or device, left unchanged), best of `repeats` runs each.  The
- * winner is kept for later runs; *groups and *stages receive it (may be
- * NULL).  Errors: as fd_batch_run. */
+/* The autotuner.  Times `probe_iter` iterations of Algorithm 2 from X (host
+ * or device, left unchanged), best of `repeats` runs each:
+ *   1. the launch shape: 128-thread units per CTA in {1, 2} x tiles in
+ *      flight per tile group in {2, 3}, on every graph;
+ *   2. then, size bucket by bucket (FD_BATCH_BUCKETS), the tile edge
+ *      T in {128, 64, 32} of that bucket's graphs, each bucket's graphs run
+ *      alone.  A graph at edge T is cut into ceil(n / T) blocks and T x T
+ *      tiles, computed by groups of T threads.
+ * The winners are kept for later runs (*groups and *stages receive the
+ * shape, fd_batch_get_tiles the edges) and the edges are stored in a
+ * process-wide cache per (bucket, dim) from which fd_batch_create starts
+ * later batches of the same dimension.  Errors: as fd_batch_run. */
 fd_status fd_batch_tune(fd_batch* b, const float* X, const fd_options* opt, int32_t probe_iter, int32_t repeats,
                         int32_t* groups, int32_t* stages);
 
 /* Sets the launch shape directly (groups 1 or 2, stages 2 or 3).
  * Errors: FD_ERR_ARG (infeasible shape). */
 fd_status fd_batch_set_shape(fd_batch* b, int32_t groups, int32_t stages);
+
+/* Sets the tile edge of each size bucket directly: tiles is a host
+ * int32[FD_BATCH_BUCKETS] of 32, 64 or 128 (the graphs of bucket k are laid
+ * out at edge tiles[k]); re-tiles the affected graphs' distance codes on the
+ * device.  Errors: FD_ERR_ARG (another value), FD_ERR_OOM, FD_ERR_CUDA. */
+fd_status fd_batch_set_tiles(fd_batch* b, const int32_t* tiles);
+
+/* The tile edge of each size bucket, to a host int32[FD_BATCH_BUCKETS]. */
+fd_status fd_batch_get_tiles(const fd_batch* b, int32_t* tiles);
+
+/* The process-wide cache of tuned tile edges for layout dimension dim (1-3),
+ * to a host int32[FD_BATCH_BUCKETS] (0 = bucket not tuned yet), and its reset.
+ * fd_batch_create gives an untuned bucket edge 128. */
+fd_status fd_batch_cached_tiles(int32_t dim, int32_t* tiles);
+void fd_batch_clear_tile_cache(void);
 
 /* The hop distances of graph g as stored, float64 [n_g][n_g] host array
  * (d_ii = 0).  Errors: FD_ERR_ARG, FD_ERR_OOM, FD_ERR_CUDA. */

@@ -66,7 +66,9 @@ class BatchInfo(ctypes.Structure):
                 ("num_tiles", ctypes.c_int64), ("distance_bytes", ctypes.c_int64), ("max_n", ctypes.c_int32),
                 ("max_diameter", ctypes.c_int32), ("disconnected", ctypes.c_int32), ("sm_count", ctypes.c_int32),
                 ("grid", ctypes.c_int32), ("groups", ctypes.c_int32), ("stages", ctypes.c_int32),
-                ("graph_captured", ctypes.c_int32), ("apsp_ms", ctypes.c_double)]
+                ("graph_captured", ctypes.c_int32), ("apsp_ms", ctypes.c_double),
+                ("small_tile_bytes", ctypes.c_int64), ("graphs_t128", ctypes.c_int32), ("graphs_t64", ctypes.c_int32),
+                ("graphs_t32", ctypes.c_int32)]
 
 
 EXPORTED = ["fd_options_default", "fd_layout_create", "fd_layout_destroy", "fd_energy", "fd_forces",
@@ -76,9 +78,12 @@ EXPORTED = ["fd_options_default", "fd_layout_create", "fd_layout_destroy", "fd_e
             "fd_batch_tune", "fd_batch_set_shape", "fd_batch_distances", "fd_batch_get_info",
             "fd_batch_last_stats", "fd_energy_length_grad", "fd_sor_step_adjoint", "fd_adjoint_reset",
             "fd_adjoint_length_grad", "fd_set_vertex_omega", "fd_factor", "fd_factor_rows", "fd_factor_release",
-            "fd_fp32_peak", "fd_run_trace_ext"]
+            "fd_fp32_peak", "fd_run_trace_ext", "fd_batch_set_tiles", "fd_batch_get_tiles", "fd_batch_cached_tiles",
+            "fd_batch_clear_tile_cache"]
 GRAD_MAX_N = 131072
 BATCH_MAX_N = 2048
+BATCH_BUCKETS = 7          # size buckets of the tile-edge choice: n <= 32, 64, ..., 2048
+BATCH_TILES = (32, 64, 128)
 TIMELINE_TAGS = {1: "pack", 2: "stress", 3: "forces", 4: "rhs0", 5: "h_init", 6: "cg_au0", 7: "cg_step",
                  8: "candidates", 9: "vertex_phase"}
 NOALLOC_MAX_N = 524288
@@ -158,6 +163,14 @@ def lib():
     L.fd_batch_tune.restype = i32
     L.fd_batch_set_shape.argtypes = [P, i32, i32]
     L.fd_batch_set_shape.restype = i32
+    L.fd_batch_set_tiles.argtypes = [P, P]
+    L.fd_batch_set_tiles.restype = i32
+    L.fd_batch_get_tiles.argtypes = [P, P]
+    L.fd_batch_get_tiles.restype = i32
+    L.fd_batch_cached_tiles.argtypes = [i32, P]
+    L.fd_batch_cached_tiles.restype = i32
+    L.fd_batch_clear_tile_cache.argtypes = []
+    L.fd_batch_clear_tile_cache.restype = None
     L.fd_batch_distances.argtypes = [P, i32, P]
     L.fd_batch_distances.restype = i32
     L.fd_batch_get_info.argtypes = [P, ctypes.POINTER(BatchInfo)]
@@ -563,8 +576,20 @@ class Batch:
     def set_shape(self, groups: int, stages: int):
         _check(lib().fd_batch_set_shape(self._h, int(groups), int(stages)), "fd_batch_set_shape")
 
+    def set_tiles(self, tiles):
+        """Tile edge (32, 64 or 128) of each of the BATCH_BUCKETS size buckets."""
+        t = np.ascontiguousarray(np.asarray(tiles, dtype=np.int32).reshape(BATCH_BUCKETS))
+        _check(lib().fd_batch_set_tiles(self._h, t.ctypes.data), "fd_batch_set_tiles")
+
+    def tiles(self) -> list:
+        t = np.zeros(BATCH_BUCKETS, dtype=np.int32)
+        _check(lib().fd_batch_get_tiles(self._h, t.ctypes.data), "fd_batch_get_tiles")
+        return t.tolist()
+
     def tune(self, X, probe_iter: int = 5, repeats: int = 2, **opts):
-        """Times every feasible launch shape on X and keeps the fastest."""
+        """The autotuner: times every feasible launch shape on X and keeps the
+        fastest, then the tile edge of each size bucket (read back with
+        tiles()); returns (groups, stages)."""
         o = options(**opts)
         g, s = ctypes.c_int32(), ctypes.c_int32()
         _check(lib().fd_batch_tune(self._h, _ptr(X, np.float32), ctypes.byref(o), int(probe_iter), int(repeats),
@@ -620,3 +645,14 @@ def concat_graphs(graphs):
     rp_all = np.concatenate(rps).astype(np.int32)
     ci_all = np.concatenate(cis).astype(np.int32) if cis else np.zeros(0, dtype=np.int32)
     return gp, rp_all, ci_all
+
+
+def batch_cached_tiles(dim: int) -> list:
+    """Tile edges tuned in this process for layout dimension dim (0: not tuned)."""
+    t = np.zeros(BATCH_BUCKETS, dtype=np.int32)
+    _check(lib().fd_batch_cached_tiles(int(dim), t.ctypes.data), "fd_batch_cached_tiles")
+    return t.tolist()
+
+
+def batch_clear_tile_cache():
+    lib().fd_batch_clear_tile_cache()

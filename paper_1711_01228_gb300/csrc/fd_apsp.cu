@@ -401,30 +401,56 @@ __global__ void __launch_bounds__(TILE) rowsum_multi_kernel(const BGraph* __rest
 }
 
 // The full distance matrix of one graph of a batch (float64 [n][n], d_ii = 0).
+// The stored code of pair (i, j), i != j, of one graph's TILE x TILE half ring.
+__device__ __forceinline__ unsigned char code_at(const unsigned char* Dg, int nb, int i, int j) {
+  const int I = i / TILE, J = j / TILE, il = i % TILE, jl = j % TILE;
+  if (I == J) {
+    const int a = min(il, jl), b = max(il, jl);
+    return Dg[(size_t)hr_base(nb, I) * TILE * TILE + b * TILE + a];
+  }
+  int k = J - I;
+  if (k < 0) k += nb;
+  if (k < hr_len(nb, I)) return Dg[((size_t)hr_base(nb, I) + k) * TILE * TILE + jl * TILE + il];
+  int k2 = I - J;
+  if (k2 < 0) k2 += nb;
+  return Dg[((size_t)hr_base(nb, J) + k2) * TILE * TILE + il * TILE + jl];
+}
+
 __global__ void distance_graph_kernel(const unsigned char* Dg, int n, int nb, double* out) {
   const size_t total = (size_t)n * n;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(idx / n), j = (int)(idx % n);
-    double v = 0.0;
-    if (i != j) {
-      const int I = i / TILE, J = j / TILE, il = i % TILE, jl = j % TILE;
-      if (I == J) {
-        const int a = min(il, jl), b = max(il, jl);
-        v = Dg[(size_t)hr_base(nb, I) * TILE * TILE + b * TILE + a];
-      } else {
-        int k = J - I;
-        if (k < 0) k += nb;
-        if (k < hr_len(nb, I)) {
-          v = Dg[((size_t)hr_base(nb, I) + k) * TILE * TILE + jl * TILE + il];
-        } else {
-          int k2 = I - J;
-          if (k2 < 0) k2 += nb;
-          v = Dg[((size_t)hr_base(nb, J) + k2) * TILE * TILE + il * TILE + jl];
-        }
+    out[idx] = (i != j) ? (double)code_at(Dg, nb, i, j) : 0.0;
+  }
+}
+
+// The T x T half ring (T = gr.T < TILE, nbt blocks, same layout rules as the
+// TILE x TILE one: column-major codes, a diagonal tile holds i < j only, 0 for
+// no pair) of each listed graph, from its TILE x TILE tiles.  One CTA per
+// graph at a time.
+__global__ void __launch_bounds__(256) retile_multi_kernel(const BGraph* __restrict__ graphs,
+                                                           const int* __restrict__ list, int count,
+                                                           const unsigned char* __restrict__ D,
+                                                           unsigned char* __restrict__ DT) {
+  for (int li = blockIdx.x; li < count; li += gridDim.x) {
+    const BGraph gr = graphs[list[li]];
+    const int T = gr.T, nbt = gr.nbt, n = gr.n, TB = T * T;
+    const unsigned char* Dg = D + (size_t)gr.t0 * TILE * TILE;
+    unsigned char* out = DT + gr.dt;
+    int I = 0;
+    for (int t = 0; t < hr_tiles(nbt); ++t) {
+      while (hr_base(nbt, I + 1) <= t) ++I;
+      const int k = t - hr_base(nbt, I);
+      const int J = (I + k) % nbt;
+      for (int e = threadIdx.x; e < TB; e += blockDim.x) {
+        const int jl = e / T, il = e % T;
+        const int i = I * T + il, j = J * T + jl;
+        unsigned char c = 0;
+        if (i < n && j < n && i != j && (k != 0 || i < j)) c = code_at(Dg, gr.nb, i, j);
+        out[(size_t)t * TB + e] = c;
       }
     }
-    out[idx] = v;
   }
 }
 
@@ -511,6 +537,12 @@ cudaError_t launch_distance_graph(const unsigned char* Dg, int n, int nb, double
   if (grid > 4096) grid = 4096;
   if (grid < 1) grid = 1;
   distance_graph_kernel<<<grid, 256, 0, st>>>(Dg, n, nb, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_retile_multi(const BGraph* graphs, const int* list, int count, const unsigned char* D,
+                                unsigned char* DT, int grid, cudaStream_t st) {
+  retile_multi_kernel<<<grid, 256, 0, st>>>(graphs, list, count, D, DT);
   return cudaGetLastError();
 }
 

@@ -8,13 +8,17 @@
 // synchronisation: graphs never share a CTA, so a CTA barrier is the only
 // barrier, and a CTA's reductions stay in shared memory.
 //
-// Inside a CTA, W groups of 128 threads split the tiles of a pass (contiguous
-// ranges of the graph's half-ring tile order, fd_internal.cuh).  A group runs
-// the same 128 x 128 symmetric tile arithmetic as the single-graph kernel
-// (tile_compute in fd_solver.cuh), with the tile's distance codes arriving by
-// 1-D bulk copies (TMA) into the group's own stages.  Every per-vertex vector
-// of the graph lives in shared memory or in L2-resident pools: the pass input
-// V[nb][NC][TILE][DP] and the pass sums A[NC][n_pad][DP] in shared memory
+// Tile edge per graph.  A graph's pairs are cut into T x T tiles with
+// T = 32, 64 or 128 (its blocks of T vertices in the half-ring order of
+// fd_internal.cuh), chosen per size bucket by the host's autotuner: small
+// graphs waste most of a 128 x 128 tile on padding.  The CTA's W * 128
+// threads form W * 128 / T tile groups of T threads, which split the tiles of
+// a pass (contiguous ranges of the half ring).  A group runs the same
+// symmetric tile arithmetic as the single-graph kernel (tile_compute in
+// fd_solver.cuh at edge T), with the tile's distance codes arriving by 1-D
+// bulk copies (TMA) into the group's own stages.  Every per-vertex vector of
+// the graph lives in shared memory or in L2-resident pools: the pass input
+// V[nb][NC][T][DP] and the pass sums A[NC][n_pad][DP] in shared memory
 // (column and row sums are added with shared-memory atomics, because two
 // groups may touch one block), the CG state in global pools.
 //
@@ -25,9 +29,12 @@
 
 namespace fdl {
 
-constexpr int BGT = 128;          // threads per tile group
-constexpr int BMAX_W = 2;         // tile groups per CTA
+constexpr int BGT = 128;          // threads of one 128-thread unit (a CTA has W = 1 or 2 units)
+constexpr int BMAX_W = 2;         // 128-thread units per CTA
+constexpr int BMAX_G = BMAX_W * BGT / 32;  // tile groups per CTA at the smallest tile (T = 32)
 constexpr int BMAX_NBUF = 3;      // stages per group
+// Stage bytes per 128 threads and stage: at tile edge T the 128 / T groups of
+// T threads hold T * T bytes each, T * 128 <= TILE * TILE in all.
 constexpr int BTILE_BYTES = TILE * TILE;
 
 // Shared-memory layout of the batched kernel.
@@ -36,7 +43,7 @@ struct BSmem {
   static constexpr int DP = DimP<DIM>::v;
   static constexpr int OFF_RED = 0;       // double [warps][BRED_K] reduction scratch
   static constexpr int BRED_K = 8;
-  static constexpr int OFF_MBAR = 1024;   // [BMAX_W][BMAX_NBUF] mbarriers
+  static constexpr int OFF_MBAR = 1024;   // [BMAX_G][BMAX_NBUF] mbarriers
   static constexpr int OFF_ST = 1280;     // BState
   static constexpr int OFF_P = 2048;      // copy of BParams
   static constexpr int OFF_LUT = 3072;
@@ -58,17 +65,21 @@ struct BState {
   float rz[3], bb[3], alpha[3], beta[3];
   int conv[3];
   int graph, it, cg_total, n_acc, stop, abort, status, k;
-  unsigned parity;       // mbarrier phase bits of every group (bit w * BMAX_NBUF + s)
+  unsigned parity;       // mbarrier phase bits of every group (bit w * BMAX_NBUF + s, w < BMAX_G)
   int pass;
 };
 static_assert(sizeof(BState) <= 2048 - 1280, "BState must fit its slot");
+static_assert(BMAX_G * BMAX_NBUF * 8 <= 1280 - 1024 && BMAX_G * BMAX_NBUF <= 32, "mbarrier slots and parity bits");
 static_assert(sizeof(BParams) <= 3072 - 2048, "BParams must fit its slot");
 
+// Barrier of tile group w (T threads; named barrier 1 + w, barrier 0 is the CTA's).
+template <int T>
 __device__ __forceinline__ void group_sync(int w) {
-  asm volatile("bar.sync %0, %1;" ::"r"(1 + w), "r"(BGT) : "memory");
+  asm volatile("bar.sync %0, %1;" ::"r"(1 + w), "r"(T) : "memory");
 }
 
 // Group barrier that also ANDs a predicate over the group's threads.
+template <int T>
 __device__ __forceinline__ bool group_and(int w, bool pred) {
   unsigned r;
   asm volatile(
@@ -77,7 +88,7 @@ __device__ __forceinline__ bool group_and(int w, bool pred) {
       "bar.red.and.pred q, %2, %3, p;\n\t"
       "selp.u32 %0, 1, 0, q;\n\t}"
       : "=r"(r)
-      : "r"((unsigned)pred), "r"(1 + w), "r"(BGT)
+      : "r"((unsigned)pred), "r"(1 + w), "r"(T)
       : "memory");
   return r != 0;
 }
@@ -106,10 +117,11 @@ __device__ __forceinline__ void bcta_sum(double (&v)[K], double* scratch, BState
   __syncthreads();
 }
 
-// Index of candidate c of padded vertex i in the pass input V[nb][NC][TILE][DP].
-template <int DIM>
+// Index of candidate c of padded vertex i in the pass input V[nb][NC][T][DP]
+// (blocks of the graph's tile edge T).
+template <int DIM, int T>
 __device__ __forceinline__ int vidx(int i, int c, int nc) {
-  return (((i / TILE) * nc + c) * TILE + (i % TILE)) * DimP<DIM>::v;
+  return (((i / T) * nc + c) * T + (i % T)) * DimP<DIM>::v;
 }
 
 __device__ __forceinline__ void s_red_add(float* a, float v) {
@@ -117,17 +129,23 @@ __device__ __forceinline__ void s_red_add(float* a, float v) {
 }
 
 // --------------------------------------------------------------------------
-// One all-pairs pass over the tiles of one graph.  Group w takes tiles
-// [T w / W, T (w+1) / W) of the strip-major order; sums go to A (candidate c
-// at A + c * n_pad_max * DP), stress per candidate to st->red[c].
-// Returns false (and sets st->abort) if a copy wait timed out.
+// One all-pairs pass over the T x T tiles of one graph (T = 32, 64 or 128,
+// chosen per graph).  The CTA's W * 128 threads form GW = W * 128 / T tile
+// groups of T threads; group w takes tiles [T_g w / GW, T_g (w + 1) / GW) of
+// the strip-major order (T_g tiles in all) from the codes at Dg.  Sums go to
+// A (candidate c at A + c * n_pad_max * DP), stress per candidate to
+// st->red[c].  Returns false (and sets st->abort) if a copy wait timed out.
 // --------------------------------------------------------------------------
-template <int DIM, int MODE, int NC, int W>
-__device__ __noinline__ bool bpass(int n, int nb, long long t0) {
+template <int DIM, int MODE, int NC, int W, int T>
+__device__ __noinline__ bool bpass(int n, int nb, const unsigned char* Dg) {
   extern __shared__ __align__(256) unsigned char smem[];
   using SL = BSmem<DIM>;
-  using TS = TileShape<DIM, MODE>;
+  using TS = TileShape<DIM, MODE, T>;
   constexpr int R = TS::R, G = TS::G, DP = DimP<DIM>::v;
+  constexpr int GW = W * BGT / T;      // tile groups of the CTA
+  constexpr int TB = T * T;            // code bytes of one tile
+  constexpr int NWG = (T + 31) / 32;   // warps of a group
+  static_assert(GW <= BMAX_G, "mbarrier slots");
   const BParams& p = *reinterpret_cast<const BParams*>(smem + SL::OFF_P);
   BState* st = reinterpret_cast<BState*>(smem + SL::OFF_ST);
   const int lut_bytes = p.lut_rows * LUT_ROW;
@@ -136,14 +154,13 @@ __device__ __noinline__ bool bpass(int n, int nb, long long t0) {
   float* A = reinterpret_cast<float*>(smem + SL::off_a(lut_bytes, p.n_pad_max));
   unsigned char* stg0 = smem + SL::off_stage(lut_bytes, p.n_pad_max);
   uint64_t* mbar0 = reinterpret_cast<uint64_t*>(smem + SL::OFF_MBAR);
-  const int w = threadIdx.x / BGT, tid = threadIdx.x % BGT, nbuf = p.nbuf;
+  const int w = threadIdx.x / T, tid = threadIdx.x % T, nbuf = p.nbuf;
   const int astride = p.n_pad_max * DP;
-  const int T = hr_tiles(nb);
-  const int ta = (int)((long long)T * w / W), tb = (int)((long long)T * (w + 1) / W);
-  unsigned char* stg = stg0 + (size_t)w * nbuf * BTILE_BYTES;
+  const int NT = hr_tiles(nb);
+  const int ta = (int)((long long)NT * w / GW), tb = (int)((long long)NT * (w + 1) / GW);
+  unsigned char* stg = stg0 + (size_t)w * nbuf * TB;
   uint64_t* mbar = mbar0 + w * BMAX_NBUF;
   unsigned parity = (st->parity >> (w * BMAX_NBUF)) & ((1u << BMAX_NBUF) - 1u);
-  const unsigned char* Dg = p.D + (size_t)t0 * BTILE_BYTES;
   constexpr int NS = NStress<MODE, NC>::v;
   float ssum[NS], scomp[NS];
 #pragma unroll
@@ -155,8 +172,8 @@ __device__ __noinline__ bool bpass(int n, int nb, long long t0) {
     if (tid == 0) {
       for (int k = 0; k < nbuf - 1 && ta + k < tb; ++k) {
         fence_proxy_async();
-        mbar_expect_tx(mbar + k, BTILE_BYTES);
-        bulk_g2s(stg + k * BTILE_BYTES, Dg + (size_t)(ta + k) * BTILE_BYTES, BTILE_BYTES, mbar + k);
+        mbar_expect_tx(mbar + k, TB);
+        bulk_g2s(stg + k * TB, Dg + (size_t)(ta + k) * TB, TB, mbar + k);
         inflight |= 1u << k;
       }
     }
@@ -173,7 +190,7 @@ __device__ __noinline__ bool bpass(int n, int nb, long long t0) {
       // the group decides together (a thread whose own wait timed out makes
       // every thread of the group leave); also the barrier after which the
       // stage of the previous tile may be refilled
-      if (!group_and(w, mbar_wait(mbar + s, ph, p.timeout_ns))) {
+      if (!group_and<T>(w, mbar_wait(mbar + s, ph, p.timeout_ns))) {
         ok = false;
         st->abort = 1;
         break;
@@ -183,8 +200,8 @@ __device__ __noinline__ bool bpass(int n, int nb, long long t0) {
       if (tid == 0 && t + nbuf - 1 < tb) {
         const int sn = (s + nbuf - 1) % nbuf;
         fence_proxy_async();
-        mbar_expect_tx(mbar + sn, BTILE_BYTES);
-        bulk_g2s(stg + sn * BTILE_BYTES, Dg + (size_t)(t + nbuf - 1) * BTILE_BYTES, BTILE_BYTES, mbar + sn);
+        mbar_expect_tx(mbar + sn, TB);
+        bulk_g2s(stg + sn * TB, Dg + (size_t)(t + nbuf - 1) * TB, TB, mbar + sn);
         inflight |= 1u << sn;
       }
       const int q = tid & (G - 1);
@@ -193,9 +210,9 @@ __device__ __noinline__ bool bpass(int n, int nb, long long t0) {
         for (int c = 0; c < NC; ++c)
 #pragma unroll
           for (int a2 = 0; a2 < R / 2; ++a2) {
-            const int i0 = I * TILE + R * q + 2 * a2;
-            const Vec<DIM> x0 = lds_v<DIM>(V, vidx<DIM>(i0, c, NC) / DP);
-            const Vec<DIM> x1 = lds_v<DIM>(V, vidx<DIM>(i0 + 1, c, NC) / DP);
+            const int i0 = I * T + R * q + 2 * a2;
+            const Vec<DIM> x0 = lds_v<DIM>(V, vidx<DIM, T>(i0, c, NC) / DP);
+            const Vec<DIM> x1 = lds_v<DIM>(V, vidx<DIM, T>(i0 + 1, c, NC) / DP);
 #pragma unroll
             for (int d = 0; d < DIM; ++d) {
               rows.x[c][d][a2] = pk2(x0.c[d], x1.c[d]);
@@ -206,17 +223,17 @@ __device__ __noinline__ bool bpass(int n, int nb, long long t0) {
       }
       Vec<DIM> jout[NC];
       float stv_[NS];
-      const unsigned char* dt = stg + s * BTILE_BYTES;
-      const float* colv = V + (size_t)J * NC * TILE * DP;
-      const bool edge = (k == 0) || (n < nb * TILE && (I == nb - 1 || J == nb - 1));
-      if (edge) tile_compute<DIM, MODE, NC, CODE_U8, true>(dt, colv, lut, rows, jout, stv_, tid);
-      else tile_compute<DIM, MODE, NC, CODE_U8, false>(dt, colv, lut, rows, jout, stv_, tid);
+      const unsigned char* dt = stg + s * TB;
+      const float* colv = V + (size_t)J * NC * T * DP;
+      const bool edge = (k == 0) || (n < nb * T && (I == nb - 1 || J == nb - 1));
+      if (edge) tile_compute<DIM, MODE, NC, CODE_U8, true, T>(dt, colv, lut, rows, jout, stv_, tid);
+      else tile_compute<DIM, MODE, NC, CODE_U8, false, T>(dt, colv, lut, rows, jout, stv_, tid);
       if constexpr (MODE == PM_STRESS || MODE == PM_RHS) {
 #pragma unroll
         for (int c = 0; c < NS; ++c) kahan_add(ssum[c], scomp[c], stv_[c]);
       }
       if constexpr (MODE != PM_STRESS) {
-        const int j = J * TILE + tid;
+        const int j = J * T + tid;
         if (j < n) {
 #pragma unroll
           for (int c = 0; c < NC; ++c)
@@ -224,35 +241,53 @@ __device__ __noinline__ bool bpass(int n, int nb, long long t0) {
             for (int d = 0; d < DIM; ++d)
               s_red_add(A + c * astride + j * DP + d, (MODE == PM_MATVEC) ? jout[c].c[d] : -jout[c].c[d]);
         }
-        // row sums when the range leaves block row I
+        // row sums when the range leaves block row I: the column groups of a
+        // warp are added by shuffles, the group's warps meet in the stage's
+        // code buffer ([NC][warps][T][DP] floats: NC * DP * T * T / 8 bytes)
         const bool last = (t + 1 == tb) || (k + 1 == LI);
         if (last) {
-          float* red = reinterpret_cast<float*>(stg + s * BTILE_BYTES);  // [NC][R groups][TILE][DP]
-          const int grp = tid / G;
-          group_sync(w);  // every thread is done with the codes
+          float* red = reinterpret_cast<float*>(stg + s * TB);
+          const int lane = tid & 31, wl = tid >> 5;
 #pragma unroll
           for (int c = 0; c < NC; ++c)
 #pragma unroll
-            for (int a2 = 0; a2 < R / 2; ++a2) {
-              Vec<DIM> v0, v1;
+            for (int d = 0; d < DIM; ++d)
 #pragma unroll
-              for (int d = 0; d < DIM; ++d) {
-                v0.c[d] = lo2(rows.acc[c][d][a2]);
-                v1.c[d] = hi2(rows.acc[c][d][a2]);
+              for (int a2 = 0; a2 < R / 2; ++a2) {
+                float lo = lo2(rows.acc[c][d][a2]), hi = hi2(rows.acc[c][d][a2]);
+#pragma unroll
+                for (int m = G; m < 32 && m < T; m <<= 1) {
+                  lo += __shfl_xor_sync(0xffffffffu, lo, m);
+                  hi += __shfl_xor_sync(0xffffffffu, hi, m);
+                }
+                rows.acc[c][d][a2] = pk2(lo, hi);
               }
-              float* base = red + ((size_t)(c * R + grp) * TILE) * DP;
-              sts_v<DIM>(base, R * q + 2 * a2, v0);
-              sts_v<DIM>(base, R * q + 2 * a2 + 1, v1);
-            }
-          group_sync(w);
-          const int i = I * TILE + tid;
+          group_sync<T>(w);  // every thread is done with the codes
+          if (lane < G) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+#pragma unroll
+              for (int a2 = 0; a2 < R / 2; ++a2) {
+                Vec<DIM> v0, v1;
+#pragma unroll
+                for (int d = 0; d < DIM; ++d) {
+                  v0.c[d] = lo2(rows.acc[c][d][a2]);
+                  v1.c[d] = hi2(rows.acc[c][d][a2]);
+                }
+                float* base = red + ((size_t)(c * NWG + wl) * T) * DP;
+                sts_v<DIM>(base, R * q + 2 * a2, v0);
+                sts_v<DIM>(base, R * q + 2 * a2 + 1, v1);
+              }
+          }
+          group_sync<T>(w);
+          const int i = I * T + tid;
           if (i < n) {
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
-              Vec<DIM> sm = lds_v<DIM>(red + ((size_t)(c * R) * TILE) * DP, tid);
+              Vec<DIM> sm = lds_v<DIM>(red + ((size_t)(c * NWG) * T) * DP, tid);
 #pragma unroll
-              for (int gg = 1; gg < R; ++gg) {
-                const Vec<DIM> v = lds_v<DIM>(red + ((size_t)(c * R + gg) * TILE) * DP, tid);
+              for (int gg = 1; gg < NWG; ++gg) {
+                const Vec<DIM> v = lds_v<DIM>(red + ((size_t)(c * NWG + gg) * T) * DP, tid);
 #pragma unroll
                 for (int d = 0; d < DIM; ++d) sm.c[d] += v.c[d];
               }
@@ -298,7 +333,7 @@ __device__ __noinline__ bool bpass(int n, int nb, long long t0) {
 // --------------------------------------------------------------------------
 // Algorithm 2 for one graph, by the whole CTA.
 // --------------------------------------------------------------------------
-template <int DIM, int W>
+template <int DIM, int W, int T>
 __device__ __forceinline__ void run_graph(int g) {
   extern __shared__ __align__(256) unsigned char smem[];
   using SL = BSmem<DIM>;
@@ -311,8 +346,10 @@ __device__ __forceinline__ void run_graph(int g) {
   float* A0 = reinterpret_cast<float*>(smem + SL::off_a(lut_bytes, p.n_pad_max));
   float* A1 = A0 + p.n_pad_max * DP;
   const BGraph gr = p.graphs[g];
-  const int n = gr.n, nb = gr.nb, n_pad = nb * TILE;
-  const long long t0 = gr.t0;
+  // blocks of the graph's tile edge T (32, 64 or 128) and its codes
+  constexpr int lgT = (T == 32) ? 5 : (T == 64) ? 6 : 7;
+  const int n = gr.n, nb = gr.nbt, n_pad = nb * T;
+  const unsigned char* Dg = (T == TILE) ? p.D + (size_t)gr.t0 * TILE * TILE : p.DT + gr.dt;
   const size_t vo = (size_t)gr.p0 * DP;
   float* X = p.X + vo;
   float* Z = p.Z + vo;
@@ -338,7 +375,7 @@ __device__ __forceinline__ void run_graph(int g) {
       x.c[d] = v;
     }
     stv<DIM>(X, i, x);
-    sts_v<DIM>(V, vidx<DIM>(i, 0, 1) / DP, x);
+    sts_v<DIM>(V, vidx<DIM, T>(i, 0, 1) / DP, x);
   }
   for (int e = tid; e < 2 * p.n_pad_max * DP; e += nt) A0[e] = 0.f;
   if (tid == 0) {
@@ -378,7 +415,7 @@ __device__ __forceinline__ void run_graph(int g) {
     return;
   }
   // b = L^{X^0} X^0 and f(X^0)
-  if (!bpass<DIM, PM_RHS, 1, W>(n, nb, t0)) return;
+  if (!bpass<DIM, PM_RHS, 1, W, T>(n, nb, Dg)) return;
   if (tid == 0) {
     st->f_cur = st->red[0];
     st->pst += 1.0;
@@ -402,9 +439,9 @@ __device__ __forceinline__ void run_graph(int g) {
   int k = 0;
   for (;; ++k) {
     // ---- H step: L^W Z = B by Jacobi-preconditioned CG from Z = X^k
-    for (int i = tid; i < n_pad; i += nt) sts_v<DIM>(V, vidx<DIM>(i, 0, 1) / DP, ldv<DIM>(X, i));
+    for (int i = tid; i < n_pad; i += nt) sts_v<DIM>(V, vidx<DIM, T>(i, 0, 1) / DP, ldv<DIM>(X, i));
     __syncthreads();
-    if (!bpass<DIM, PM_MATVEC, 1, W>(n, nb, t0)) return;
+    if (!bpass<DIM, PM_MATVEC, 1, W, T>(n, nb, Dg)) return;
     {
       double v[3 * DIM];
 #pragma unroll
@@ -426,7 +463,7 @@ __device__ __forceinline__ void run_graph(int g) {
         stv<DIM>(Z, i, x);
         stv<DIM>(Rr, i, r);
         stv<DIM>(Pp, i, u);
-        sts_v<DIM>(V, vidx<DIM>(i, 0, 1) / DP, u);
+        sts_v<DIM>(V, vidx<DIM, T>(i, 0, 1) / DP, u);
       }
       if (tid == 0) st->pmv += 1.0;
       bcta_sum<3 * DIM>(v, scratch, st);
@@ -446,7 +483,7 @@ __device__ __forceinline__ void run_graph(int g) {
       for (int d = 0; d < DIM; ++d) all = all && st->conv[d];
       if (all) break;
       if (st->it >= p.cg_max) break;
-      if (!bpass<DIM, PM_MATVEC, 1, W>(n, nb, t0)) return;
+      if (!bpass<DIM, PM_MATVEC, 1, W, T>(n, nb, Dg)) return;
       // q = L^W p (kept in A0), (p, q)
       {
         double v[DIM];
@@ -534,7 +571,7 @@ __device__ __forceinline__ void run_graph(int g) {
 #pragma unroll
           for (int d = 0; d < DIM; ++d) pp.c[d] = fmaf(be[d], pp.c[d], is * r.c[d]);
           stv<DIM>(Pp, i, pp);
-          sts_v<DIM>(V, vidx<DIM>(i, 0, 1) / DP, pp);
+          sts_v<DIM>(V, vidx<DIM, T>(i, 0, 1) / DP, pp);
         }
         __syncthreads();
       }
@@ -555,18 +592,18 @@ __device__ __forceinline__ void run_graph(int g) {
       }
       stv<DIM>(Z, i, z);
       if (two) {
-        sts_v<DIM>(V, vidx<DIM>(i, 0, 2) / DP, z);
-        sts_v<DIM>(V, vidx<DIM>(i, 1, 2) / DP, xt);
+        sts_v<DIM>(V, vidx<DIM, T>(i, 0, 2) / DP, z);
+        sts_v<DIM>(V, vidx<DIM, T>(i, 1, 2) / DP, xt);
       } else {
-        sts_v<DIM>(V, vidx<DIM>(i, 0, 1) / DP, z);
+        sts_v<DIM>(V, vidx<DIM, T>(i, 0, 1) / DP, z);
       }
     }
     if (tid == 0) st->cg_total += st->it;
     __syncthreads();
     if (two) {
-      if (!bpass<DIM, PM_RHS, 2, W>(n, nb, t0)) return;
+      if (!bpass<DIM, PM_RHS, 2, W, T>(n, nb, Dg)) return;
     } else {
-      if (!bpass<DIM, PM_RHS, 1, W>(n, nb, t0)) return;
+      if (!bpass<DIM, PM_RHS, 1, W, T>(n, nb, Dg)) return;
     }
     const double fZ = st->red[0], fT = two ? st->red[1] : st->red[0];
     const bool accept = two && (fT <= fZ);  // line 6, ties accept
@@ -624,10 +661,20 @@ __device__ __forceinline__ void run_graph(int g) {
   finish(k + 1);
 }
 
-template <int DIM, int W>
+// Tile-edge class of the graphs a launch runs: 0 (T = 128), 1 (64), 2 (32).
+template <int T>
+struct TileClass {
+  static constexpr int v = (T == TILE) ? 0 : (T == 64) ? 1 : 2;
+};
+
+// One persistent launch per tile edge present in the batch (all of them in
+// one captured CUDA graph): the CTAs take the graphs of class TileClass<T>
+// from p.order[cls_off[c] .. cls_off[c + 1]) through queue p.queue[c].
+template <int DIM, int W, int T>
 __global__ void __launch_bounds__(BGT * W, 1) fd_batch_kernel(const BParams* pp) {
   extern __shared__ __align__(256) unsigned char smem[];
   using SL = BSmem<DIM>;
+  constexpr int CLS = TileClass<T>::v;
   {
     static_assert(sizeof(BParams) % 8 == 0, "BParams copy granularity");
     const unsigned long long* src = reinterpret_cast<const unsigned long long*>(pp);
@@ -640,7 +687,7 @@ __global__ void __launch_bounds__(BGT * W, 1) fd_batch_kernel(const BParams* pp)
   {
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + SL::OFF_MBAR);
     if (threadIdx.x == 0) {
-      for (int k = 0; k < BMAX_W * BMAX_NBUF; ++k) mbar_init(&mbar[k], 1);
+      for (int k = 0; k < BMAX_G * BMAX_NBUF; ++k) mbar_init(&mbar[k], 1);
       fence_mbar_init();
       st->parity = 0u;
     }
@@ -650,13 +697,14 @@ __global__ void __launch_bounds__(BGT * W, 1) fd_batch_kernel(const BParams* pp)
   }
   __syncthreads();
   __shared__ int s_next;
+  const int q0 = p.cls_off[CLS], q1 = p.cls_off[CLS + 1];
   while (true) {
-    if (threadIdx.x == 0) s_next = atomicAdd(p.queue, 1);
+    if (threadIdx.x == 0) s_next = q0 + atomicAdd(p.queue + CLS, 1);
     __syncthreads();
     const int qi = s_next;
     __syncthreads();
-    if (qi >= p.G) break;
-    run_graph<DIM, W>(p.order[qi]);
+    if (qi >= q1) break;
+    run_graph<DIM, W, T>(p.order[qi]);
     __syncthreads();
     if (st->abort) {
       if (threadIdx.x == 0) {

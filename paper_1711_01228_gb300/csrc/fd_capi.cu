@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <numeric>
 #include <vector>
@@ -63,9 +64,11 @@ constexpr int SP_SMEM_MAX_N = 4096;  // shared-memory back-propagation up to thi
 cudaError_t batch_config_d1(int W, int lut_bytes, int n_pad_max, int nbuf, int* blocks_per_sm, size_t* smem);
 cudaError_t batch_config_d2(int W, int lut_bytes, int n_pad_max, int nbuf, int* blocks_per_sm, size_t* smem);
 cudaError_t batch_config_d3(int W, int lut_bytes, int n_pad_max, int nbuf, int* blocks_per_sm, size_t* smem);
-cudaError_t launch_batch_d1(int W, const BParams* p, int grid, size_t smem, cudaStream_t st);
-cudaError_t launch_batch_d2(int W, const BParams* p, int grid, size_t smem, cudaStream_t st);
-cudaError_t launch_batch_d3(int W, const BParams* p, int grid, size_t smem, cudaStream_t st);
+cudaError_t launch_batch_d1(int W, int cls, const BParams* p, int grid, size_t smem, cudaStream_t st);
+cudaError_t launch_batch_d2(int W, int cls, const BParams* p, int grid, size_t smem, cudaStream_t st);
+cudaError_t launch_batch_d3(int W, int cls, const BParams* p, int grid, size_t smem, cudaStream_t st);
+cudaError_t launch_retile_multi(const BGraph* graphs, const int* list, int count, const unsigned char* D,
+                                unsigned char* DT, int grid, cudaStream_t st);
 }  // namespace fdl
 
 using namespace fdl;
@@ -1439,11 +1442,17 @@ struct fd_batch {
   int device = 0, sm_count = 0;
   cudaStream_t stream = nullptr;
   std::vector<BGraph> graphs;
-  std::vector<int> order;
+  std::vector<int> order;    // by size, largest first
+  std::vector<int> run_order;  // the graphs of tile class 0, 1, 2, each largest first
+  int cls_off[4] = {0, 0, 0, 0};
+  int tiles[FD_BATCH_BUCKETS];  // tile edge per size bucket
   BGraph* d_graphs = nullptr;
   int* d_order = nullptr;
+  int* d_order_sub = nullptr;  // [G] order of a run over a subset (the tuner's probes)
   unsigned char* D = nullptr;
   size_t D_bytes = 0;
+  unsigned char* DT = nullptr;  // T x T tiles of the graphs with T < TILE
+  size_t DT_bytes = 0, DT_cap = 0;
   unsigned char* d_lut = nullptr;
   int lut_rows = 0, max_diam = 0, disconnected = 0;
   float* d_s = nullptr;
@@ -1453,7 +1462,7 @@ struct fd_batch {
   double* d_omega = nullptr; // [G]
   double* d_omega_seq = nullptr;
   int omega_seq_cap = 0;
-  int* d_queue = nullptr;    // [0] queue position, [1] launch error
+  int* d_queue = nullptr;    // [0..2] queue position per tile class, [3] launch error
   int* d_iout = nullptr;     // [4][G] iterations, CG steps, accepted, status
   double* d_dout = nullptr;  // [5][G] final stress, criterion, L^W passes, stress passes, device ms
   BParams* d_params = nullptr;
@@ -1464,6 +1473,10 @@ struct fd_batch {
   size_t g_smem = 0;
   int captured = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // the three tile classes run concurrently (fork / join on events), so that
+  // the SMs a class leaves at its end take up the next class's graphs
+  cudaStream_t aux[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr, ev_join[3] = {nullptr, nullptr, nullptr};
   double apsp_ms = 0.0;
   long long timeout_ns = 30000000000LL;
   std::vector<int> h_iout;
@@ -1478,7 +1491,9 @@ void batch_release(fd_batch* b) {
   b->gexec = nullptr;
   dev_free(b->d_graphs);
   dev_free(b->d_order);
+  dev_free(b->d_order_sub);
   dev_free(b->D);
+  dev_free(b->DT);
   dev_free(b->d_lut);
   dev_free(b->d_s);
   dev_free(b->d_inv_s);
@@ -1493,6 +1508,14 @@ void batch_release(fd_batch* b) {
   if (b->ev0) cudaEventDestroy(b->ev0);
   if (b->ev1) cudaEventDestroy(b->ev1);
   b->ev0 = b->ev1 = nullptr;
+  for (int c = 0; c < 3; ++c) {
+    if (b->aux[c]) cudaStreamDestroy(b->aux[c]);
+    if (b->ev_join[c]) cudaEventDestroy(b->ev_join[c]);
+    b->aux[c] = nullptr;
+    b->ev_join[c] = nullptr;
+  }
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  b->ev_fork = nullptr;
 }
 
 cudaError_t batch_config(int dim, int W, int lut_bytes, int n_pad_max, int nbuf, int* bps, size_t* smem) {
@@ -1501,10 +1524,110 @@ cudaError_t batch_config(int dim, int W, int lut_bytes, int n_pad_max, int nbuf,
   return batch_config_d3(W, lut_bytes, n_pad_max, nbuf, bps, smem);
 }
 
-cudaError_t launch_batch(int dim, int W, const BParams* p, int grid, size_t smem, cudaStream_t st) {
-  if (dim == 1) return launch_batch_d1(W, p, grid, smem, st);
-  if (dim == 2) return launch_batch_d2(W, p, grid, smem, st);
-  return launch_batch_d3(W, p, grid, smem, st);
+cudaError_t launch_batch(int dim, int W, int cls, const BParams* p, int grid, size_t smem, cudaStream_t st) {
+  if (dim == 1) return launch_batch_d1(W, cls, p, grid, smem, st);
+  if (dim == 2) return launch_batch_d2(W, cls, p, grid, smem, st);
+  return launch_batch_d3(W, cls, p, grid, smem, st);
+}
+
+// The three persistent launches of a run (tile classes T = 128, 64, 32; a
+// class without graphs ends at its first queue read), after the queues and
+// the error flag are cleared.  They run concurrently on the batch's own
+// streams (class 0, the largest graphs, first and at the highest priority),
+// forked from and joined back into st: a CTA of the next class starts on an
+// SM as soon as a CTA of an earlier class has run out of graphs.
+cudaError_t launch_batch_all(fd_batch* b, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(b->d_queue, 0, 4 * sizeof(int), st);
+  if (e == cudaSuccess) e = cudaEventRecord(b->ev_fork, st);
+  for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
+    e = cudaStreamWaitEvent(b->aux[c], b->ev_fork, 0);
+    if (e == cudaSuccess) e = launch_batch(b->dim, b->W, c, b->d_params, b->grid, b->smem, b->aux[c]);
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev_join[c], b->aux[c]);
+  }
+  for (int c = 0; c < 3 && e == cudaSuccess; ++c) e = cudaStreamWaitEvent(st, b->ev_join[c], 0);
+  return e;
+}
+
+// Size bucket of an n-vertex graph: n <= 32, 64, 128, 256, 512, 1024, 2048.
+int batch_bucket(int n) {
+  int k = 0;
+  while (k < FD_BATCH_BUCKETS - 1 && n > (32 << k)) ++k;
+  return k;
+}
+
+int tile_class(int T) { return (T == TILE) ? 0 : (T == 64) ? 1 : 2; }
+
+// Tile edges chosen by fd_batch_tune, per (size bucket, dimension), for this
+// process: a later batch of the same dimension starts from them.
+std::mutex g_tile_mu;
+int g_tile_cache[4][FD_BATCH_BUCKETS] = {};  // 0 = not tuned
+
+// The order of a run over the graphs `ids` (ascending positions in the
+// size order): grouped by tile class, largest first inside each class.
+void class_order(const std::vector<BGraph>& gs, const std::vector<int>& ids, std::vector<int>& out, int* off) {
+  out.clear();
+  for (int c = 0; c < 3; ++c) {
+    off[c] = (int)out.size();
+    for (int g : ids)
+      if (tile_class(gs[g].T) == c) out.push_back(g);
+  }
+  off[3] = (int)out.size();
+}
+
+// Gives every graph the tile edge of its size bucket and builds the small-
+// tile pool (the graphs with T < TILE, re-tiled from the TILE x TILE pool).
+fd_status batch_set_tiles(fd_batch* b, const int* tiles) {
+  for (int k = 0; k < FD_BATCH_BUCKETS; ++k)
+    if (tiles[k] != 32 && tiles[k] != 64 && tiles[k] != TILE) return FD_ERR_ARG;
+  std::vector<BGraph> gs = b->graphs;
+  std::vector<int> small;
+  long long dt = 0;
+  for (int g = 0; g < b->G; ++g) {
+    BGraph& gr = gs[g];
+    gr.T = tiles[batch_bucket(gr.n)];
+    gr.nbt = (gr.n + gr.T - 1) / gr.T;
+    gr.dt = 0;
+    if (gr.T < TILE) {
+      gr.dt = dt;
+      dt += (long long)hr_tiles(gr.nbt) * gr.T * gr.T;
+      small.push_back(g);
+    }
+  }
+  cudaStream_t st = b->stream;
+  if ((size_t)dt > b->DT_cap) {
+    dev_free(b->DT);
+    b->DT_cap = 0;
+    fd_status s = dev_alloc(&b->DT, (size_t)dt);
+    if (s != FD_OK) return s;
+    b->DT_cap = (size_t)dt;
+  }
+  std::vector<int> ord;
+  int off[4];
+  class_order(gs, b->order, ord, off);
+  int* d_list = nullptr;
+  fd_status s = FD_OK;
+  if (!small.empty() && (s = dev_alloc(&d_list, small.size())) != FD_OK) return s;
+  cudaError_t e = cudaMemcpyAsync(b->d_graphs, gs.data(), gs.size() * sizeof(BGraph), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_order, ord.data(), ord.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && !small.empty()) {
+    e = cudaMemcpyAsync(d_list, small.data(), small.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = launch_retile_multi(b->d_graphs, d_list, (int)small.size(), b->D, b->DT,
+                              std::max(1, std::min((int)small.size(), 8 * b->sm_count)), st);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  dev_free(d_list);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_status(e);
+  }
+  b->graphs = gs;
+  b->run_order = ord;
+  std::memcpy(b->cls_off, off, sizeof(off));
+  std::memcpy(b->tiles, tiles, sizeof(b->tiles));
+  b->DT_bytes = (size_t)dt;
+  return FD_OK;
 }
 
 // Sets the launch shape if it is feasible (at least one resident CTA per SM).
@@ -1536,10 +1659,9 @@ fd_status batch_launch(fd_batch* b, double* kernel_ms) {
   if (!b->gexec && st != nullptr) {
     cudaGraph_t graph = nullptr;
     if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-      cudaError_t e1 = cudaMemsetAsync(b->d_queue, 0, 2 * sizeof(int), st);
-      cudaError_t e2 = launch_batch(b->dim, b->W, b->d_params, b->grid, b->smem, st);
+      cudaError_t e2 = launch_batch_all(b, st);
       cudaError_t e3 = cudaStreamEndCapture(st, &graph);
-      if (e1 == cudaSuccess && e2 == cudaSuccess && e3 == cudaSuccess && graph) {
+      if (e2 == cudaSuccess && e3 == cudaSuccess && graph) {
         if (cudaGraphInstantiate(&b->gexec, graph, 0) != cudaSuccess) b->gexec = nullptr;
       }
       if (graph) cudaGraphDestroy(graph);
@@ -1557,28 +1679,28 @@ fd_status batch_launch(fd_batch* b, double* kernel_ms) {
     FD_CK(cudaGraphLaunch(b->gexec, st));
     b->captured = 1;
   } else {
-    FD_CK(cudaMemsetAsync(b->d_queue, 0, 2 * sizeof(int), st));
-    FD_CK(launch_batch(b->dim, b->W, b->d_params, b->grid, b->smem, st));
+    FD_CK(launch_batch_all(b, st));
     b->captured = 0;
   }
   FD_CK(cudaEventRecord(b->ev1, st));
-  int q[2] = {0, 0};
+  int q[4] = {0, 0, 0, 0};
   b->h_iout.resize((size_t)4 * b->G);
   b->h_dout.resize((size_t)5 * b->G);
-  FD_CK(cudaMemcpyAsync(q, b->d_queue, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  FD_CK(cudaMemcpyAsync(q, b->d_queue, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
   FD_CK(cudaMemcpyAsync(b->h_iout.data(), b->d_iout, (size_t)4 * b->G * sizeof(int), cudaMemcpyDeviceToHost, st));
   FD_CK(cudaMemcpyAsync(b->h_dout.data(), b->d_dout, (size_t)5 * b->G * sizeof(double), cudaMemcpyDeviceToHost, st));
   FD_CK(cudaStreamSynchronize(st));
   float ms = 0.f;
   FD_CK(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
   *kernel_ms = ms;
-  if (q[1] != 0) return (fd_status)q[1];
+  if (q[3] != 0) return (fd_status)q[3];
   return FD_OK;
 }
 
-// Runs Algorithm 2 on every graph from the layouts at x_in, writing x_out.
+// Runs Algorithm 2 on every graph (or on the graphs `subset`, positions in
+// the size order) from the layouts at x_in, writing x_out.
 fd_status batch_run_dev(fd_batch* b, const float* x_in, float* x_out, const fd_options* opt, const double* omega,
-                        int max_iter, double* kernel_ms) {
+                        int max_iter, double* kernel_ms, const std::vector<int>* subset = nullptr) {
   if (!opt || !(opt->omega >= 0.0) || !std::isfinite(opt->omega) || max_iter < 1 || opt->cg_max < 0 ||
       !(opt->tol >= 0.0) || !(opt->cg_tol >= 0.0) || (opt->stop != FD_STOP_REL_DISP && opt->stop != FD_STOP_REL_STRESS))
     return FD_ERR_ARG;
@@ -1614,9 +1736,18 @@ fd_status batch_run_dev(fd_batch* b, const float* x_in, float* x_out, const fd_o
   std::memset(&p, 0, sizeof(p));
   p.graphs = b->d_graphs;
   p.order = b->d_order;
+  std::memcpy(p.cls_off, b->cls_off, sizeof(p.cls_off));
+  if (subset) {
+    std::vector<int> ord;
+    class_order(b->graphs, *subset, ord, p.cls_off);
+    if (!ord.empty())
+      FD_CK(cudaMemcpyAsync(b->d_order_sub, ord.data(), ord.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    p.order = b->d_order_sub;
+  }
   p.G = b->G;
   p.dim = b->dim;
   p.D = b->D;
+  p.DT = b->DT;
   p.lut = b->d_lut;
   p.lut_rows = b->lut_rows;
   p.s = b->d_s;
@@ -1637,7 +1768,7 @@ fd_status batch_run_dev(fd_batch* b, const float* x_in, float* x_out, const fd_o
   p.tol = opt->tol;
   p.cg_tol = opt->cg_tol;
   p.queue = b->d_queue;
-  p.err = b->d_queue + 1;
+  p.err = b->d_queue + 3;
   const size_t G = (size_t)b->G;
   p.iters = b->d_iout;
   p.cg_steps = b->d_iout + G;
@@ -1725,9 +1856,24 @@ fd_status fd_batch_create(fd_batch** out, int32_t num_graphs, int32_t dim, const
   b->stream = (cudaStream_t)cuda_stream;
   if (cudaGetDevice(&b->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess ||
-      cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess) {
+      cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     return bail(FD_ERR_CUDA);
+  }
+  {
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+      cudaGetLastError();
+      return bail(FD_ERR_CUDA);
+    }
+    for (int c = 0; c < 3; ++c) {
+      if (cudaStreamCreateWithPriority(&b->aux[c], cudaStreamNonBlocking, c == 0 ? greatest : least) != cudaSuccess ||
+          cudaEventCreateWithFlags(&b->ev_join[c], cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(FD_ERR_CUDA);
+      }
+    }
   }
   // geometry: padded vertex pools and tile pool, graph order (largest first)
   b->graphs.resize(G);
@@ -1739,6 +1885,9 @@ fd_status fd_batch_create(fd_batch** out, int32_t num_graphs, int32_t dim, const
     gr.v0 = gp[g];
     gr.p0 = (int)p0;
     gr.t0 = t0;
+    gr.T = TILE;
+    gr.nbt = gr.nb;
+    gr.dt = 0;
     p0 += (long long)gr.nb * TILE;
     t0 += hr_tiles(gr.nb);
     b->max_n = std::max(b->max_n, gr.n);
@@ -1755,6 +1904,7 @@ fd_status fd_batch_create(fd_batch** out, int32_t num_graphs, int32_t dim, const
   b->D_bytes = (size_t)b->ntiles * TILE * TILE;
   if ((s = dev_alloc(&b->d_graphs, G)) != FD_OK) return bail(s);
   if ((s = dev_alloc(&b->d_order, G)) != FD_OK) return bail(s);
+  if ((s = dev_alloc(&b->d_order_sub, G)) != FD_OK) return bail(s);
   if ((s = dev_alloc(&b->D, b->D_bytes)) != FD_OK) return bail(s);
   if (cudaMemcpyAsync(b->d_graphs, b->graphs.data(), G * sizeof(BGraph), cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemcpyAsync(b->d_order, b->order.data(), G * sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess ||
@@ -1885,7 +2035,7 @@ fd_status fd_batch_create(fd_batch** out, int32_t num_graphs, int32_t dim, const
   if ((s = dev_alloc(&b->d_pool, 5 * ps)) != FD_OK) return bail(s);
   if ((s = dev_alloc(&b->d_xin, (size_t)N * dim)) != FD_OK) return bail(s);
   if ((s = dev_alloc(&b->d_omega, (size_t)G)) != FD_OK) return bail(s);
-  if ((s = dev_alloc(&b->d_queue, 2)) != FD_OK) return bail(s);
+  if ((s = dev_alloc(&b->d_queue, 4)) != FD_OK) return bail(s);
   if ((s = dev_alloc(&b->d_iout, (size_t)4 * G)) != FD_OK) return bail(s);
   if ((s = dev_alloc(&b->d_dout, (size_t)5 * G)) != FD_OK) return bail(s);
   if ((s = dev_alloc(&b->d_params, 1)) != FD_OK) return bail(s);
@@ -1901,6 +2051,13 @@ fd_status fd_batch_create(fd_batch** out, int32_t num_graphs, int32_t dim, const
   for (auto& sh : shapes)
     if ((s = batch_shape(b, sh[0], sh[1])) == FD_OK) break;
   if (s != FD_OK) return bail(FD_ERR_CUDA);
+  // tile edges: the ones tuned earlier in this process for this dimension, else TILE
+  int tiles[FD_BATCH_BUCKETS];
+  {
+    std::lock_guard<std::mutex> lk(g_tile_mu);
+    for (int k = 0; k < FD_BATCH_BUCKETS; ++k) tiles[k] = g_tile_cache[dim][k] ? g_tile_cache[dim][k] : TILE;
+  }
+  if ((s = batch_set_tiles(b, tiles)) != FD_OK) return bail(s);
   *out = b;
   return FD_OK;
 }
@@ -1968,40 +2125,99 @@ fd_status fd_batch_tune(fd_batch* b, const float* X, const fd_options* opt, int3
   fd_status s = dev_alloc(&d_out, nx);
   if (s != FD_OK) return s;
   const cudaMemcpyKind kind = is_device_ptr(X) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  // best of `repeats` probe runs (over `subset`, or every graph)
+  auto probe = [&](const std::vector<int>* subset, double* t_best) -> fd_status {
+    *t_best = 1e300;
+    for (int r = 0; r < repeats; ++r) {
+      if (cudaMemcpyAsync(b->d_xin, X, nx * sizeof(float), kind, b->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return FD_ERR_CUDA;
+      }
+      double kms = 0.0;
+      fd_status e = batch_run_dev(b, b->d_xin, d_out, opt, nullptr, probe_iter, &kms, subset);
+      if (e != FD_OK && e != FD_ERR_NONFINITE) return e;
+      *t_best = std::min(*t_best, kms);
+    }
+    return FD_OK;
+  };
+  // 1. launch shape (tile groups x stages) at the current tile edges
   const int W0 = b->W, nbuf0 = b->nbuf;
   int bestW = W0, bestN = nbuf0;
   double best = 1e300;
   const int shapes[4][2] = {{1, 2}, {1, 3}, {2, 2}, {2, 3}};
   for (auto& sh : shapes) {
     if (batch_shape(b, sh[0], sh[1]) != FD_OK) continue;
-    double t_best = 1e300;
-    for (int r = 0; r < repeats && s == FD_OK; ++r) {
-      if (cudaMemcpyAsync(b->d_xin, X, nx * sizeof(float), kind, b->stream) != cudaSuccess) {
-        cudaGetLastError();
-        s = FD_ERR_CUDA;
-        break;
-      }
-      double kms = 0.0;
-      fd_status e = batch_run_dev(b, b->d_xin, d_out, opt, nullptr, probe_iter, &kms);
-      if (e != FD_OK && e != FD_ERR_NONFINITE) s = e;
-      t_best = std::min(t_best, kms);
-    }
-    if (s != FD_OK) break;
-    if (t_best < best) {
-      best = t_best;
+    double t = 0.0;
+    if ((s = probe(nullptr, &t)) != FD_OK) break;
+    if (t < best) {
+      best = t;
       bestW = sh[0];
       bestN = sh[1];
     }
+  }
+  if (s == FD_OK) s = batch_shape(b, bestW, bestN);
+  // 2. tile edge per size bucket: each bucket's graphs alone at T = 32, 64, 128
+  int tiles[FD_BATCH_BUCKETS];
+  std::memcpy(tiles, b->tiles, sizeof(tiles));
+  for (int k = 0; k < FD_BATCH_BUCKETS && s == FD_OK; ++k) {
+    std::vector<int> ids;
+    for (int g : b->order)
+      if (batch_bucket(b->graphs[g].n) == k) ids.push_back(g);
+    if (ids.empty()) continue;
+    int bestT = tiles[k];
+    double tb = 1e300;
+    for (int T : {TILE, 64, 32}) {
+      int trial[FD_BATCH_BUCKETS];
+      std::memcpy(trial, tiles, sizeof(trial));
+      trial[k] = T;
+      if ((s = batch_set_tiles(b, trial)) != FD_OK) break;
+      double t = 0.0;
+      if ((s = probe(&ids, &t)) != FD_OK) break;
+      if (t < tb) {
+        tb = t;
+        bestT = T;
+      }
+    }
+    tiles[k] = bestT;
   }
   dev_free(d_out);
   if (s != FD_OK) {
     batch_shape(b, W0, nbuf0);
     return s;
   }
-  batch_shape(b, bestW, bestN);
+  if ((s = batch_set_tiles(b, tiles)) != FD_OK) return s;
+  {
+    std::lock_guard<std::mutex> lk(g_tile_mu);
+    for (int k = 0; k < FD_BATCH_BUCKETS; ++k) g_tile_cache[b->dim][k] = tiles[k];
+  }
   if (groups) *groups = b->W;
   if (stages) *stages = b->nbuf;
   return FD_OK;
+}
+
+fd_status fd_batch_set_tiles(fd_batch* b, const int32_t* tiles) {
+  if (!b || !tiles) return FD_ERR_ARG;
+  int t[FD_BATCH_BUCKETS];
+  for (int k = 0; k < FD_BATCH_BUCKETS; ++k) t[k] = tiles[k];
+  return batch_set_tiles(b, t);
+}
+
+fd_status fd_batch_get_tiles(const fd_batch* b, int32_t* tiles) {
+  if (!b || !tiles) return FD_ERR_ARG;
+  for (int k = 0; k < FD_BATCH_BUCKETS; ++k) tiles[k] = b->tiles[k];
+  return FD_OK;
+}
+
+fd_status fd_batch_cached_tiles(int32_t dim, int32_t* tiles) {
+  if (dim < 1 || dim > 3 || !tiles) return FD_ERR_ARG;
+  std::lock_guard<std::mutex> lk(g_tile_mu);
+  for (int k = 0; k < FD_BATCH_BUCKETS; ++k) tiles[k] = g_tile_cache[dim][k];
+  return FD_OK;
+}
+
+void fd_batch_clear_tile_cache(void) {
+  std::lock_guard<std::mutex> lk(g_tile_mu);
+  std::memset(g_tile_cache, 0, sizeof(g_tile_cache));
 }
 
 fd_status fd_batch_distances(fd_batch* b, int32_t g, double* out) {
@@ -2038,6 +2254,12 @@ fd_status fd_batch_get_info(const fd_batch* b, fd_batch_info* info) {
   info->stages = b->nbuf;
   info->graph_captured = b->captured;
   info->apsp_ms = b->apsp_ms;
+  info->small_tile_bytes = (int64_t)b->DT_bytes;
+  int counts[3] = {0, 0, 0};
+  for (const BGraph& gr : b->graphs) ++counts[tile_class(gr.T)];
+  info->graphs_t128 = counts[0];
+  info->graphs_t64 = counts[1];
+  info->graphs_t32 = counts[2];
   return FD_OK;
 }
 

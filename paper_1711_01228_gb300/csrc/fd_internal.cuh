@@ -163,16 +163,23 @@ struct BGraph {
   int n, nb;     // vertices, blocks of TILE vertices
   int v0;        // first vertex of the graph in the caller's concatenated arrays
   int p0;        // first padded vertex in the internal pools (a multiple of TILE)
-  long long t0;  // first tile of the graph in the distance pool
+  long long t0;  // first tile of the graph in the distance pool (TILE x TILE tiles)
+  // tile edge of the layout kernel: T = TILE reads the tiles at t0; T = 32 or
+  // 64 reads nbt = ceil(n / T) blocks' half ring of T x T tiles (the same
+  // layout at the smaller edge) from byte dt of the small-tile pool
+  int T, nbt;
+  long long dt;
 };
 
 // Parameters of one batched launch (device memory, so that a captured CUDA
 // graph keeps one pointer while the host rewrites the block between runs).
 struct BParams {
   const BGraph* graphs;   // [G]
-  const int* order;       // [G] processing order (largest first)
+  const int* order;       // [G] processing order: the graphs of tile class 0, 1, 2 (T = 128, 64, 32), each largest first
+  int cls_off[4];         // class c owns order[cls_off[c] .. cls_off[c + 1])
   int G, dim;
-  const unsigned char* D; // uint8 distance tiles of every graph
+  const unsigned char* D; // uint8 distance tiles of every graph (TILE x TILE)
+  const unsigned char* DT;// the graphs with T < TILE: their T x T tiles
   const unsigned char* lut;
   int lut_rows;
   const float* s;         // [P] row sums of W (diagonal of L^W)
@@ -184,7 +191,7 @@ struct BParams {
   const double* omega_seq;// [max_iter] omega of iteration k (FD_OMEGA_PROB), or NULL
   int max_iter, cg_max, stop;
   double tol, cg_tol;
-  int* queue;             // next position in `order`
+  int* queue;             // [3] next position of each tile class in its part of `order`
   int* err;               // first launch-level error
   // per-graph results
   int* iters;

@@ -240,14 +240,18 @@ __host__ __device__ constexpr int raw_bytes(int kind) {
   return (kind == SK_CGU) ? 3 * TILE * DimP<DIM>::v * 4 + TILE * 4 : src_arrays(kind) * TILE * DimP<DIM>::v * 4;
 }
 
-// Rows per lane and column-accumulator chains of a pass kind.  Chain h
-// serves the steps t = h (mod CH) and travels CH lanes per use (no travel
-// when CH = G).
-template <int DIM, int MODE>
+// Rows per lane and column-accumulator chains of a pass kind, for a tile of
+// T x T pairs computed by T threads (T = TILE in the single-graph kernel; the
+// batched kernel also runs T = 32 and 64).  G = T / R lanes cover the rows,
+// and the T / G groups of G lanes take disjoint columns.  Chain h serves the
+// steps t = h (mod CH) and travels CH lanes per use (no travel when CH = G).
+template <int DIM, int MODE, int T = TILE>
 struct TileShape {
   static constexpr int R = (MODE == PM_MATVEC) ? (DIM == 3 ? 8 : 16) : 4;
-  static constexpr int G = TILE / R;
-  static constexpr int CH = (MODE == PM_MATVEC) ? (DIM == 3 ? 4 : 8) : 2;
+  static constexpr int G = T / R;
+  static constexpr int CH0 = (MODE == PM_MATVEC) ? (DIM == 3 ? 4 : 8) : 2;
+  static constexpr int CH = (CH0 < G) ? CH0 : G;
+  static_assert(G >= 2 && G <= 32 && (G & (G - 1)) == 0, "a column group is 2..32 lanes of one warp");
   static_assert(G % CH == 0, "chains must divide the group");
 };
 
@@ -506,13 +510,13 @@ __device__ __forceinline__ unsigned lut_off(unsigned codes, unsigned lane_off, u
 // Pairs this lane's rows with the G columns its group visits.  EDGE tiles
 // (diagonal blocks, padding) may hold code 0 ("no pair"), whose stress term
 // must vanish; elsewhere every code is a real distance.
-template <int DIM, int MODE, int NC, int CODE, bool EDGE>
+template <int DIM, int MODE, int NC, int CODE, bool EDGE, int T = TILE>
 __device__ __forceinline__ void tile_compute(const unsigned char* __restrict__ dt, const float* __restrict__ colv,
                                              const unsigned char* __restrict__ lut,
-                                             Rows<DIM, NC, TileShape<DIM, MODE>::R>& rows, Vec<DIM> (&jout)[NC],
+                                             Rows<DIM, NC, TileShape<DIM, MODE, T>::R>& rows, Vec<DIM> (&jout)[NC],
                                              float (&st)[NStress<MODE, NC>::v], int tid,
-                                             int CA = TILE * DimP<DIM>::v /* floats between the candidate arrays */) {
-  using TS = TileShape<DIM, MODE>;
+                                             int CA = T * DimP<DIM>::v /* floats between the candidate arrays */) {
+  using TS = TileShape<DIM, MODE, T>;
   constexpr int R = TS::R, G = TS::G, CH = TS::CH;
   constexpr int DP = DimP<DIM>::v;
   constexpr bool NEED_K = (MODE != PM_MATVEC);
@@ -541,7 +545,7 @@ __device__ __forceinline__ void tile_compute(const unsigned char* __restrict__ d
       unsigned cw[(R + 3) / 4];
       float dv[(CODE == CODE_U8) ? 1 : R];
       if constexpr (CODE == CODE_U8) {
-        const unsigned char* cp = dt + jl * TILE + R * q;
+        const unsigned char* cp = dt + jl * T + R * q;
         if constexpr (R == 16) {
           const uint4 c = *reinterpret_cast<const uint4*>(cp);
           cw[0] = c.x;
@@ -556,7 +560,7 @@ __device__ __forceinline__ void tile_compute(const unsigned char* __restrict__ d
           cw[0] = *reinterpret_cast<const unsigned*>(cp);
         }
       } else {
-        const float4* cp = reinterpret_cast<const float4*>(dt) + (jl * TILE + R * q) / 4;
+        const float4* cp = reinterpret_cast<const float4*>(dt) + (jl * T + R * q) / 4;
 #pragma unroll
         for (int k = 0; k < R / 4; ++k) {
           const float4 v = cp[k];

@@ -1,10 +1,13 @@
 """Host-side pieces of the batched form (no GPU): the concatenation of
 graphs into one CSR and the batched workload's generators."""
 import math
+import os
+import shutil
 
 import numpy as np
+import pytest
 
-from paper_1711_01228_gb300 import api, synth
+from paper_1711_01228_gb300 import api, build, synth
 
 
 def test_concat_graphs_is_the_disjoint_union():
@@ -41,6 +44,18 @@ def test_batch_graph_mix():
             assert v not in nb and len(set(nb.tolist())) == len(nb)
     X = synth.batch_initial_layout([len(rp) - 1 for rp, _ in gs], 2, seed=0)
     assert X.dtype == np.float32 and X.shape[1] == 2 and np.all((X >= 0) & (X < 1))
+
+
+def test_tile_cache_is_host_state():
+    # the tuned tile edges live in a process-wide table on the host
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    build.build()
+    api.batch_clear_tile_cache()
+    for dim in (1, 2, 3):
+        assert api.batch_cached_tiles(dim) == [0] * api.BATCH_BUCKETS
+    with pytest.raises(api.FdError):
+        api.batch_cached_tiles(4)
 
 
 def test_trace_jsonl(tmp_path):

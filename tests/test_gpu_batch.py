@@ -154,8 +154,13 @@ def test_tuner_and_graph_capture():
         g, s = B.tune(torch.from_numpy(X0).cuda(), probe_iter=3, repeats=1)
         assert (g, s) in ((1, 2), (1, 3), (2, 2), (2, 3))
         assert (B.info()["groups"], B.info()["stages"]) == (g, s)
-        # one tile group adds every sum in a fixed order: replays are bit-identical
+        tiles = B.tiles()
+        assert all(t in api.BATCH_TILES for t in tiles)
+        assert api.batch_cached_tiles(2) == tiles  # kept for later batches of this dimension
+        # one tile group (one 128-thread unit at edge 128) adds every sum in a
+        # fixed order: replays are bit-identical
         B.set_shape(1, 2)
+        B.set_tiles([128] * api.BATCH_BUCKETS)
         Xa = torch.from_numpy(X0).cuda()
         ra = B.run(Xa, omega=0.5, tol=1e-4, max_iter=1000)
         Xb = torch.from_numpy(X0).cuda()
@@ -164,6 +169,81 @@ def test_tuner_and_graph_capture():
     assert np.array_equal(ra.iterations, rb.iterations)
     assert np.array_equal(ra.stress, rb.stress)
     assert torch.equal(Xa, Xb)
+
+
+def _edge_graphs():
+    """Sizes across the 32- and 64-vertex block boundaries and into buckets 0-4."""
+    return [synth.path(1), synth.path(2), synth.complete(3), synth.erdos_renyi(31, 4.0, seed=21),
+            synth.grid(4, 8), synth.random_geometric(33, 2, 6.0, seed=22)[:2], synth.erdos_renyi(63, 4.0, seed=23),
+            synth.grid(8, 8), synth.random_binary_tree(65, seed=24), synth.erdos_renyi(100, 4.0, seed=25),
+            synth.random_geometric(129, 2, 6.0, seed=26)[:2], synth.erdos_renyi(300, 4.0, seed=27)]
+
+
+def _connected(rp, ci):
+    return oracle.apsp(rp, ci, policy=0)[0] == 0
+
+
+# Every tile edge against the oracle: the stress after one iteration (every
+# code of every tile enters it) within 1e-5, converged stress within 1e-4, and
+# the iteration count within 2 % on the connected graphs.  On the
+# disconnected ones (unreachable pairs at (largest d) + 1) the criterion
+# decays by under 2 % per iteration near the tolerance, the FP32 runs of every
+# path (both kernels, every tile edge) stop 1-10 % before the FP64 oracle
+# (e.g. ER n = 31: 248-254 vs 265 in 2-D), and only the stress is compared.
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("tile", [32, 64, 128])
+def test_every_tile_edge_agrees(tile, dim):
+    gs = _edge_graphs()
+    sizes = [len(rp) - 1 for rp, _ in gs]
+    X0 = _layouts(sizes, dim, seed=7)
+    with api.Batch.from_graphs(gs, dim=dim, disconnected_policy=1) as B:
+        B.set_tiles([tile] * api.BATCH_BUCKETS)
+        info = B.info()
+        assert info[f"graphs_t{tile}"] == len(gs)
+        X1 = X0.copy()
+        r1 = B.run(X1, omega=0.5, tol=0.0, max_iter=1)
+        X = X0.copy()
+        r = B.run(X, omega=0.5, tol=1e-4, max_iter=1000)
+        gp = B.graph_ptr
+    for g, (rp, ci) in enumerate(gs):
+        _, D = oracle.apsp(rp, ci, policy=1)
+        x0 = X0[gp[g]:gp[g + 1]].astype(np.float64)
+        one = oracle.sor_run(D, x0, omega=0.5, tol=0.0, max_iter=1)
+        assert r1.stress[g] == pytest.approx(one.stress, rel=1e-5, abs=1e-9), (g, tile)
+        ref = oracle.sor_run(D, x0, omega=0.5, tol=1e-4, max_iter=1000)
+        assert r.stress[g] == pytest.approx(ref.stress, rel=1e-4, abs=1e-9), (g, tile)
+        if _connected(rp, ci):
+            assert _close_iters(int(r.iterations[g]), ref.iterations), (g, tile, r.iterations[g], ref.iterations)
+
+
+def test_mixed_tile_edges_and_cache():
+    gs = _edge_graphs() + [synth.delaunay(700, seed=28)]
+    sizes = [len(rp) - 1 for rp, _ in gs]
+    X0 = _layouts(sizes, 2, seed=8)
+    tiles = [32, 64, 32, 64, 128, 64, 128]
+    api.batch_clear_tile_cache()
+    with api.Batch.from_graphs(gs, dim=2, disconnected_policy=1) as B:
+        assert B.tiles() == [128] * api.BATCH_BUCKETS  # nothing cached: edge 128
+        B.set_tiles(tiles)
+        assert B.tiles() == tiles
+        info = B.info()
+        edge = [tiles[min(6, max(0, int(np.ceil(np.log2(max(n, 1) / 32)))))] for n in sizes]
+        assert (info["graphs_t32"], info["graphs_t64"], info["graphs_t128"]) == (
+            edge.count(32), edge.count(64), edge.count(128))
+        assert info["small_tile_bytes"] > 0
+        X = X0.copy()
+        r = B.run(X, omega=0.5, tol=1e-4, max_iter=1000)
+        gp = B.graph_ptr
+        with pytest.raises(api.FdError) as e:
+            B.set_tiles([16] * api.BATCH_BUCKETS)
+        assert e.value.status == 1
+    for g, (rp, ci) in enumerate(gs):
+        _, D = oracle.apsp(rp, ci, policy=1)
+        ref = oracle.sor_run(D, X0[gp[g]:gp[g + 1]].astype(np.float64), omega=0.5, tol=1e-4, max_iter=1000)
+        assert r.stress[g] == pytest.approx(ref.stress, rel=1e-4, abs=1e-9), g
+        if _connected(rp, ci):
+            assert _close_iters(int(r.iterations[g]), ref.iterations), g
+    assert api.batch_cached_tiles(2) == [0] * api.BATCH_BUCKETS  # set_tiles does not touch the cache
 
 
 def test_batch_errors():
