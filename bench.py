@@ -630,6 +630,65 @@ def run_batched(args, local_rank, peak_tflops):
     }
 
 
+def run_batch_tiles(args, local_rank, peak_tflops):
+    """The batched workload at every fixed tile edge (128, 64, 32 for all size
+    buckets, launch shape 2 units x 2 stages) and with the autotuner's choice:
+    per case the kernel's CUDA-event time (one warm-up run, L2 flushed before
+    the timed run), pair interactions/s, the FP32 fraction, and per size bucket
+    the device time per all-pairs pass and the share of all CTA time."""
+    import torch
+
+    from paper_1711_01228_gb300 import api
+
+    dev = torch.device("cuda", local_rank)
+    G = args.batch_graphs
+    graphs = synth.batch_graphs(G, seed=0)
+    sizes = np.array([len(rp) - 1 for rp, _ in graphs])
+    X0 = synth.batch_initial_layout(sizes, 2, seed=0)
+    stream = torch.cuda.Stream(dev)
+    opts = dict(omega=0.5, tol=1e-4, max_iter=args.max_iter, stop=api.STOP_REL_DISP)
+    Xd = torch.from_numpy(X0).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    buckets = [(0, 32), (32, 64), (64, 128), (128, 256), (256, 512), (512, 1024), (1024, 2048)]
+    api.batch_clear_tile_cache()
+    B = api.Batch.from_graphs(graphs, dim=2, disconnected_policy=1, stream=stream.cuda_stream)
+    cases = []
+
+    def measure(label):
+        X = Xd.clone()
+        B.run(X, **opts)
+        X = Xd.clone()
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        res = B.run(X, **opts)
+        ms = res.stats["kernel_ms"]
+        flops = float(np.sum(0.5 * sizes * (sizes - 1) * (res.matvec_passes * FLOP_MV[2]
+                                                          + res.stress_passes * FLOP_K2[2])))
+        info = B.info()
+        tot = float(res.graph_ms.sum())
+        per = {}
+        for lo, hi in buckets:
+            m = (sizes > lo) & (sizes <= hi)
+            npass = float((res.matvec_passes[m] + res.stress_passes[m]).sum())
+            per[f"n<={hi}"] = {"graphs": int(m.sum()), "us_per_pass": 1e3 * float(res.graph_ms[m].sum()) / max(npass, 1.0),
+                              "cta_time_share": float(res.graph_ms[m].sum()) / tot}
+        cases.append({"tiles": label, "tile_edge_by_bucket": B.tiles(), "units_per_cta": info["groups"],
+                      "stages": info["stages"], "kernel_ms": ms, "pairs_per_s": res.stats["pairs"] / (ms / 1e3),
+                      "fp32_frac": flops / (ms / 1e3) / 1e12 / peak_tflops, "buckets": per})
+
+    with B:
+        for T in (128, 64, 32):
+            B.set_shape(2, 2)
+            B.set_tiles([T] * api.BATCH_BUCKETS)
+            measure(f"{T} everywhere")
+        B.set_tiles([128] * api.BATCH_BUCKETS)
+        B.tune(Xd, probe_iter=5, repeats=2, **opts)
+        measure("tuned")
+    return {"batch_tiles": {"workload": f"{G} graphs of the batched workload (synth.batch_graphs, seed 0), 2-D, "
+                                        f"omega_c 1.5, rel-disp tol 1e-4, max {args.max_iter} iterations",
+                            "cases": cases}}
+
+
 def run_differentiable(args, local_rank):
     """The differentiable form on a random geometric graph of args.grad_n
     points in the unit cube (mean degree 6, seed 0; its largest component,
@@ -1067,6 +1126,8 @@ def main():
     ap.add_argument("--batch-graphs", type=int, default=4096)
     ap.add_argument("--batch-steps", type=int, default=2)
     ap.add_argument("--batch-sample", type=int, default=64, help="graphs timed through the single-graph path")
+    ap.add_argument("--batch-tiles", action="store_true",
+                    help="the batched workload at every fixed tile edge and tuned, then exit")
     ap.add_argument("--no-grad", dest="grad", action="store_false", help="skip the differentiable-form section")
     ap.add_argument("--table1", action="store_true", help="omega strategies on stand-ins at Table 1's sizes, then exit")
     ap.add_argument("--table1-seeds", type=int, default=5)
@@ -1093,6 +1154,19 @@ def main():
             print(json.dumps(run_direct(args, local_rank, peaks, fp32_peak)), flush=True)
             if not args.direct_n:
                 print(json.dumps(run_vertex_omega(args, local_rank)), flush=True)
+        return
+    if args.batch_tiles:
+        import torch
+
+        from paper_1711_01228_gb300 import build
+
+        build.build()
+        torch.cuda.set_device(local_rank)
+        if rank == 0:
+            peaks, src = _peaks()
+            sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
+            fp32_peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            print(json.dumps(run_batch_tiles(args, local_rank, fp32_peak)), flush=True)
         return
     if args.table1:
         import torch
