@@ -773,6 +773,65 @@ __device__ __forceinline__ void issue_tile(const PassArgs& p, const PassSrc& src
   }
 }
 
+// Whether a step's copies are issued by four warps (issue_step_part) or all
+// by thread 0 (issue_tile).  Measured at n = 200,000: with two tiles per
+// stage (2-D) the split takes 7-10 % off an L^W pass; with one tile per
+// stage (3-D) it made the pass 2 % slower.
+template <int TPS>
+constexpr bool kSplitIssue = (TPS == 2);
+
+// One step's copies, as the thread that prepares them describes them to the
+// warps that issue them (two alternating slots in shared memory).
+struct IssueDesc {
+  int tile, I, J;
+  int flags;  // c | first << 8 | stage << 16 | valid << 24
+  __device__ __forceinline__ int c() const { return flags & 0xff; }
+  __device__ __forceinline__ bool first() const { return ((flags >> 8) & 1) != 0; }
+  __device__ __forceinline__ int stage() const { return (flags >> 16) & 0xff; }
+  __device__ __forceinline__ bool valid() const { return (flags >> 24) != 0; }
+};
+
+// The copy issue of one step spread over the CTA's four warps: lane 0 of
+// warp 0 arms the stage's mbarrier with the step's bytes and copies the
+// codes; lane 0 of warp (a + 1) mod 4 copies raw array a (its column blocks
+// and, at a task's first step, block I).  A copy may complete before the
+// mbarrier is armed: the transaction count goes negative until the armed
+// arrival, and the phase cannot complete without that arrival.
+template <int DIM, int CODE, int TPS>
+__device__ __forceinline__ void issue_step_part(const PassArgs& p, const PassSrc& src, unsigned char* smem,
+                                                const IssueDesc& d, int warp) {
+  using L = SmemLayout<DIM, CODE>;
+  constexpr int DP = DimP<DIM>::v;
+  constexpr unsigned TBYTES = L::DBUF;
+  constexpr int tps = TPS;
+  const int kind = src.kind;
+  const int NA = src_arrays(kind);
+  const int c = d.c(), s = d.stage(), J = d.J;
+  const bool first = d.first();
+  const int sb = p.stage_base;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L::OFF_MISC) + s;
+  fence_proxy_async();  // this CTA's generic accesses to the stage come before the copy overwrites it
+  if (warp == 0) {
+    const unsigned RB = raw_bytes<DIM>(kind);
+    mbar_expect_tx(mbar, c * (TBYTES + RB) + (first ? RB : 0));
+    bulk_g2s(smem + L::off_d(sb, s, tps), reinterpret_cast<const unsigned char*>(p.D) + (size_t)d.tile * TBYTES,
+             c * TBYTES, mbar);
+  }
+  float* rawj = reinterpret_cast<float*>(smem + L::off_rawj(sb, s, tps));
+  float* rawi = reinterpret_cast<float*>(smem + L::off_rawi(sb, s, tps));
+  const int run0 = (J + c <= p.nb) ? c : 1;
+  for (int a = 0; a < NA; ++a) {
+    if (((a + 1) & 3) != warp) continue;
+    const bool scalar = (kind == SK_CGU && a == 3);
+    const unsigned ab = scalar ? TILE * 4 : TILE * DP * 4;  // bytes of one block
+    const int stride = scalar ? TILE : TILE * DP;           // floats of one block
+    float* dst = scalar ? rawj + 3 * tps * TILE * DP : rawj + a * tps * TILE * DP;
+    bulk_g2s(dst, src.a[a] + (size_t)J * stride, run0 * ab, mbar);
+    if (run0 < c) bulk_g2s(dst + stride, src.a[a], ab, mbar);  // block 0 after block nb - 1
+    if (first) bulk_g2s(rawi + a * TILE * DP, src.a[a] + (size_t)d.I * stride, ab, mbar);
+  }
+}
+
 // The steps of one CTA in visiting order: its tasks m = 0..M-1 and, inside a
 // task, runs of c = tps consecutive tiles (fewer at the task's end) in strip
 // order; both reversed when `rev` (a step's tiles are k .. k + c - 1 either way).
@@ -833,8 +892,9 @@ struct TileIt {
 struct PassCtl {
   PassSrc src;
   PassArgs a;
-  TileIt<1> is;  // next step to copy (thread 0 only; TileIt<2> has the same layout)
+  TileIt<1> is;  // the step after the one in desc (thread 0 only; TileIt<2> has the same layout)
   int s_is;      // its stage
+  IssueDesc desc[2];  // the step whose copies the loop's step t issues: desc[t & 1]
 };
 static_assert(sizeof(TileIt<1>) == sizeof(TileIt<2>), "step iterators share the PassCtl slot");
 static_assert(sizeof(PassCtl) <= SmemLayout<1, CODE_U8>::OFF_RUN - SmemLayout<1, CODE_U8>::OFF_CTL,
@@ -895,6 +955,21 @@ __device__ FD_PASS_ATTR bool pair_pass_impl(PairState* ps_io, double* acc) {
   it.begin(g, rev);
   int s_it = 0;  // its stage
   TileIt<TPS>& ctl_is = *reinterpret_cast<TileIt<TPS>*>(&ctl->is);
+  // describes the step at ctl_is (its stage ctl->s_is) into desc[slot] and moves past it
+  auto prepare = [&](int slot) {
+    TileIt<TPS> is = ctl_is;
+    IssueDesc d;
+    d.tile = is.valid ? is.tile() : 0;
+    d.I = is.valid ? is.td.I : 0;
+    d.J = is.valid ? is.J(g.nb) : 0;
+    d.flags = is.valid ? (is.c | (is.first() ? 1 << 8 : 0) | (ctl->s_is << 16) | (1 << 24)) : 0;
+    ctl->desc[slot] = d;
+    if (is.valid) {
+      is.next(g);
+      ctl_is = is;
+      ctl->s_is = (ctl->s_is + 1 == nbuf) ? 0 : ctl->s_is + 1;
+    }
+  };
   if (tid == 0) {
     TileIt<TPS> is = it;
     int s_is = 0;
@@ -905,7 +980,9 @@ __device__ FD_PASS_ATTR bool pair_pass_impl(PairState* ps_io, double* acc) {
     }
     ctl_is = is;
     ctl->s_is = s_is;
+    if constexpr (kSplitIssue<TPS>) prepare(0);
   }
+  int t_step = 0;
   Rows<DIM, NC, R> rows;
   constexpr int tps = TPS;
   constexpr int astr = TPS * TILE * DP;  // floats between the raw arrays of the column blocks
@@ -931,7 +1008,13 @@ __device__ FD_PASS_ATTR bool pair_pass_impl(PairState* ps_io, double* acc) {
     }
     if (first) form_inplace<DIM, NC>(src, rawi, I, tid, TILE * DP, rawi + 3 * TILE * DP);
     __syncthreads();  // formed vectors visible; every thread is done with the stage of the previous step
-    if (tid == 0 && ctl_is.valid) {
+    if constexpr (kSplitIssue<TPS>) {
+      // the copies of the step nbuf - 1 ahead, lane 0 of each warp a part
+      const IssueDesc& d = ctl->desc[t_step & 1];
+      if ((tid & 31) == 0 && d.valid()) issue_step_part<DIM, CODE, TPS>(p, src, smem, d, tid >> 5);
+      if (tid == 0) prepare((t_step + 1) & 1);
+      ++t_step;
+    } else if (tid == 0 && ctl_is.valid) {
       TileIt<TPS> is = ctl_is;
       issue_tile<DIM, CODE, TPS>(p, src, smem, is.tile(), is.td.I, is.J(g.nb), is.c, is.first(), ctl->s_is);
       is.next(g);
