@@ -197,8 +197,14 @@ def test_unrolled_adjoint_matches_oracle(omega, vertex, solver, path, monkeypatc
     gw = 0.5 * oracle.pair_to_edge_grad(rp, ci, w.astype(np.float64), Gd)
     g_x = Xt.grad.cpu().numpy().astype(np.float64)
     g_l = lt.grad.cpu().numpy().astype(np.float64)
-    assert np.linalg.norm(g_x - gX0) <= 2e-3 * np.linalg.norm(gX0)
-    assert np.linalg.norm(g_l - gw) <= 2e-3 * np.linalg.norm(gw)
+    # Bound: each of the 2K solves (K forward H steps, K adjoint solves) stops
+    # at relative residual cg_tol = 1e-7, an error of at most kappa_eff * 1e-7
+    # in its solution with kappa_eff (Jacobi-preconditioned L^W on the range)
+    # under 100 on these graphs; the iteration map is a contraction, so the
+    # errors add: 2K * 100 * 1e-7 = 8e-5 < 1e-4 (FP32 rounding, ~1e-6, below
+    # it).  Measured: 1e-6 to 3e-6 with either solver.
+    assert np.linalg.norm(g_x - gX0) <= 1e-4 * np.linalg.norm(gX0)
+    assert np.linalg.norm(g_l - gw) <= 1e-4 * np.linalg.norm(gw)
 
 
 def test_length_gradient_above_shared_memory_size():
