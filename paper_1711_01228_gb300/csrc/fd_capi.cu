@@ -548,7 +548,7 @@ KParams base_params(fd_layout* h, int mode) {
   p.inv_s = h->d_inv_s;
   const size_t vs = (size_t)h->n_pad * h->dimp;
   float* v = h->d_vec;
-  float** slots[] = {&p.X, &p.Z, &p.Xt, &p.B, &p.Bz, &p.Bt, &p.Zw, &p.R, &p.U, &p.W, &p.P, &p.S};
+  float** slots[] = {&p.X, &p.R0, &p.Xt, &p.B, &p.Bz, &p.Bt, &p.Zw, &p.R, &p.U, &p.W, &p.P, &p.S};
   for (int k = 0; k < 12; ++k) *slots[k] = v + k * vs;
   p.acc = h->d_acc;
   p.ctrl = h->d_ctrl;
@@ -751,13 +751,14 @@ fd_status fd_layout_create(fd_layout** out, int32_t n, int32_t dim, const int32_
   if (const char* e = std::getenv("FDLAYOUT_NBUF")) nbuf_only = std::atoi(e);  // testing: force the stage count
   if (const char* e = std::getenv("FDLAYOUT_TPS")) tps_only = std::atoi(e);    // testing: force tiles per stage
   for (int tps = 2; tps >= 1; --tps) {
-    // Two-tile stages measured faster only for uint8 codes in 1-D/2-D with a
-    // small lookup table (there two of them fit beside it at two CTAs per SM;
-    // 8 KB = hop diameters up to 30); 64 KB float tiles take one per stage, and
-    // in 3-D, or beside a large table, one-tile stages (more of them) win.
-    const bool tps2_ok = h->code == CODE_U8 && dim <= 2 && lut_bytes <= 8192;
+    // Two-tile stages measured faster only for uint8 codes with a small lookup
+    // table (there two of them fit beside it at two CTAs per SM; 8 KB = hop
+    // diameters up to 30): L^W passes 10 % faster in 2-D, 5-7 % in 3-D (two
+    // stages there); 64 KB float tiles take one per stage, and beside a large
+    // table one-tile stages (more of them) win.
+    const bool tps2_ok = h->code == CODE_U8 && lut_bytes <= 8192;
     if (tps == 2 && !tps2_ok && tps_only != 2) continue;
-    if (tps == 2 && (h->code != CODE_U8 || dim == 3)) continue;  // not instantiated
+    if (tps == 2 && h->code != CODE_U8) continue;  // not instantiated
     if (tps_only && tps != tps_only) continue;
     for (int nbuf = MAX_NBUF; nbuf >= 2; --nbuf) {
       if (nbuf_only && nbuf != nbuf_only) continue;

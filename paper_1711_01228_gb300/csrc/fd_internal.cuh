@@ -109,9 +109,10 @@ struct KParams {
   const float* x_in;           // [n][dim] input layout (device staging)
   float* x_out;                // [n][dim] output (layout or forces)
   // internal vectors, [n_pad][DIMP] with DIMP = 1, 2, 4 for dim = 1, 2, 3:
-  // layout X^k, its RHS B; candidates Z = X^{k+1}, Xt = X~ and their RHS;
-  // CG state Zw (iterate), R (residual), U = M^-1 R, W = L^W U, P, S = L^W P
-  float *X, *Z, *Xt, *B, *Bz, *Bt, *Zw, *R, *U, *W, *P, *S;
+  // layout X^k and the H step's right-hand side B = L^{X^k} X^k and initial
+  // residual R0 = B - L^W X^k; Xt, Bz, Bt spare; CG state Zw (iterate),
+  // R (residual), U = M^-1 R, W = L^W U, P, S = L^W P
+  float *X, *R0, *Xt, *B, *Bz, *Bt, *Zw, *R, *U, *W, *P, *S;
   // per-vertex sums of a pass, [3][n_pad][DIMP] FP64: the pair kernels add
   // their FP32 row and column partial sums with FP64 atomics; the vertex phase
   // after the pass reads them and clears them for the next pass

@@ -773,10 +773,14 @@ __device__ __forceinline__ void issue_tile(const PassArgs& p, const PassSrc& src
   }
 }
 
+// Iterations between the all-pairs passes that recompute L^W x0 at the start
+// of an H step (in between it comes from the previous step's vectors).
+constexpr int LWX_REFRESH = 16;
+
 // Whether a step's copies are issued by four warps (issue_step_part) or all
 // by thread 0 (issue_tile).  Measured at n = 200,000: with two tiles per
-// stage (2-D) the split takes 7-10 % off an L^W pass; with one tile per
-// stage (3-D) it made the pass 2 % slower.
+// stage the split takes 7-10 % off an L^W pass in 2-D; with one tile per
+// stage (3-D, before it took two-tile stages) it made the pass 2 % slower.
 template <int TPS>
 constexpr bool kSplitIssue = (TPS == 2);
 
@@ -1503,19 +1507,34 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
   for (int k = 0;; ++k) {
     // ---- start of the H step.  x0 = X^0, or the candidate line 6 kept (formed
     // on the fly from the CG solution and the previous layout); L^W x0.
+    // L^W x0 comes from an all-pairs pass at the launch's first iteration and
+    // every LWX_REFRESH-th; in between from the previous H step's own
+    // vectors, with no pass: its solve ended at z with residual R = B - L^W z
+    // (kept by the CG recurrences), and started from X^k with R0 = B - L^W X^k,
+    // so L^W z = B - R, L^W X^k = B - R0, and the kept candidate's product is
+    // L^W z, or (1 + w_i) L^W z - w_i L^W X^k for the extrapolation of Eq. (10)
+    // (L^W 1 = 0: the pin's translation changes nothing).  The recurrence
+    // residual drifts from the true one by about FP32 rounding of the CG
+    // updates (1e-7 of R per H step), far below the solve tolerance; the
+    // periodic pass resets it.  Per-vertex factors (Sec. 6) scale the
+    // extrapolation vertex by vertex, and L^W does not commute with that
+    // scaling: with factors every H step runs the pass.
+    const bool lwx_pass = (k % LWX_REFRESH) == 0 || p.om_scale != nullptr;
     {
-      PassSrc src = direct_src(k == 0 ? p.X : p.Zw, k == 0 ? SK_DIRECT : SK_SEL);
-      if (k > 0) {
-        src.a[1] = p.X;
+      if (lwx_pass) {
+        PassSrc src = direct_src(k == 0 ? p.X : p.Zw, k == 0 ? SK_DIRECT : SK_SEL);
+        if (k > 0) {
+          src.a[1] = p.X;
 #pragma unroll
-        for (int d = 0; d < DIM; ++d) src.z0[d] = rs->z0[d];
-        src.om = rs->om_prev;
-        src.sel = rs->accept;
-        src.oms = p.om_scale;
+          for (int d = 0; d < DIM; ++d) src.z0[d] = rs->z0[d];
+          src.om = rs->om_prev;
+          src.sel = rs->accept;
+          src.oms = p.om_scale;
+        }
+        if (!pair_pass<DIM, PM_MATVEC, 1, CODE, TPS>(p, smem, ps, src, acc2)) return;
+        if (tid == 0) rs->passes_mv += 1.0;
+        FD_SYNC(5);
       }
-      if (!pair_pass<DIM, PM_MATVEC, 1, CODE, TPS>(p, smem, ps, src, acc2)) return;
-      if (tid == 0) rs->passes_mv += 1.0;
-      FD_SYNC(5);
       // r0 = b - L^W x0, u0 = M^-1 r0, p = s = 0; displacement sums of x0 against X^k.
       // Scalars: [0,D) r.u  [D,2D) r.r  [2D,3D) b.b  [3D,4D) sum dx  [4D,5D) sum dx^2
       //          [5D,6D) sum x  [6D,7D) sum x^2
@@ -1528,12 +1547,12 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
       vertex_phase<7 * DIM>(p, red64, RSUM, [&](int i, df(&v)[7 * DIM]) {
         const bool real = i < n;
         const Vec<DIM> xo = ldv<DIM>(p.X, i);
+        const float om_i = (!first && oms) ? om_p * __ldg(oms + i) : om_p;  // Sec. 6: omega_i = omega m_i
         Vec<DIM> x0;
         if (first) {
           x0 = xo;
         } else {
           const Vec<DIM> zw = ldv<DIM>(p.Zw, i);
-          const float om_i = oms ? om_p * __ldg(oms + i) : om_p;  // Sec. 6: omega_i = omega m_i
 #pragma unroll
           for (int d = 0; d < DIM; ++d) {
             const float z = zw.c[d] - z0[d];
@@ -1542,13 +1561,26 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
         }
         const Vec<DIM> bz = take_acc<DIM>(acc0, i);
         const Vec<DIM> bt = take_acc<DIM>(acc1, i);
-        const Vec<DIM> a = take_acc<DIM>(acc2, i);
         const Vec<DIM> b = bsel ? bt : bz;
         const float s = __ldcg(p.s + i), is = __ldcg(p.inv_s + i);
+        // L^W x0: from the pass, or from the previous H step's vectors
+        Vec<DIM> lwx;
+        if (lwx_pass) {
+          const Vec<DIM> a = take_acc<DIM>(acc2, i);
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) lwx.c[d] = fmaf(s, x0.c[d], -a.c[d]);
+        } else {
+          const Vec<DIM> bk = ldv<DIM>(p.B, i), rf = ldv<DIM>(p.R, i), r0 = ldv<DIM>(p.R0, i);
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) {
+            const float lz = bk.c[d] - rf.c[d];
+            lwx.c[d] = acc_t ? fmaf(1.f + om_i, lz, -om_i * (bk.c[d] - r0.c[d])) : lz;
+          }
+        }
         Vec<DIM> r, u;
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
-          r.c[d] = b.c[d] - fmaf(s, x0.c[d], -a.c[d]);
+          r.c[d] = b.c[d] - lwx.c[d];
           u.c[d] = is * r.c[d];
           const df dx = real ? df_diff(x0.c[d], xo.c[d]) : df_of(0.f);
           const float xv = real ? x0.c[d] : 0.f;
@@ -1563,6 +1595,8 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
         stv<DIM>(p.Zw, i, x0);
         stv<DIM>(p.X, i, x0);
         stv<DIM>(p.R, i, r);
+        stv<DIM>(p.R0, i, r);
+        stv<DIM>(p.B, i, b);
         stv<DIM>(p.U, i, u);
         stv<DIM>(p.P, i, vzero<DIM>());
         stv<DIM>(p.S, i, vzero<DIM>());

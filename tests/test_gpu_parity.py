@@ -325,3 +325,38 @@ def test_stage_shapes_agree_with_oracle(tps, monkeypatch):
     ref = oracle.sor_run(D, X0.astype(np.float64), omega=0.5, tol=1e-4, max_iter=1000)
     assert r.stress == pytest.approx(ref.stress, rel=1e-4)
     assert abs(r.iterations - ref.iterations) <= max(1, math.ceil(0.02 * ref.iterations))
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("solver", [api.SOLVER_CG, api.SOLVER_DIRECT])
+def test_h_step_start_from_previous_step(dim, solver):
+    """Inside one launch, L^W X^{k+1} at the start of an H step comes from the
+    previous H step's right-hand side and residuals (L^W z = B - R, L^W X^k =
+    B - R0) instead of an all-pairs pass, except at every 16th iteration.  One
+    launch of 20 iterations against 20 launches of one iteration each (every one
+    of which runs the pass): the same acceptance decisions, layouts within 1e-4
+    relative, final stresses within 1e-5 of each other, and both within the
+    converged-run bound 1e-4 of the FP64 oracle's run (20 iterations of H steps
+    solved to CG's 1e-6 drift from the exact solves by a few 1e-5)."""
+    rp, ci = synth.delaunay(1200, seed=31)
+    n = len(rp) - 1
+    st, D = oracle.apsp(rp, ci)
+    X0 = synth.initial_layout(n, dim, seed=4)
+    K = 20
+    with api.Layout(rp, ci, dim=dim) as L:
+        if solver == api.SOLVER_DIRECT:
+            L.factor()
+        Xa = X0.copy()
+        ra = L.run(Xa, trace=True, omega=0.5, tol=0.0, max_iter=K, solver=solver)
+        assert ra.iterations == K
+        Xb = X0.copy()
+        acc_b = []
+        for k in range(K):
+            f, acc, _ = L.sor_step(Xb, k=k, omega=0.5, solver=solver)
+            acc_b.append(bool(acc))
+    assert list(map(bool, ra.accepted[:K])) == acc_b
+    assert np.linalg.norm(Xa - Xb) <= 1e-4 * np.linalg.norm(Xb)
+    assert ra.stress == pytest.approx(f, rel=1e-5)
+    ref = oracle.sor_run(D, X0.astype(np.float64), omega=0.5, tol=0.0, max_iter=K)
+    assert ra.stress == pytest.approx(ref.stress, rel=1e-4)
+    assert f == pytest.approx(ref.stress, rel=1e-4)
