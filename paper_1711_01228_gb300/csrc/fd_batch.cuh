@@ -356,6 +356,7 @@ __device__ __forceinline__ void run_graph(int g) {
   float* Rr = p.R + vo;
   float* Pp = p.Pd + vo;
   float* B = p.B + vo;
+  float* R0 = p.R0 + vo;
   const float* S = p.s + gr.p0;
   const float* IS = p.inv_s + gr.p0;
   const float* xin = p.x_in + (size_t)gr.v0 * DIM;
@@ -438,10 +439,17 @@ __device__ __forceinline__ void run_graph(int g) {
 
   int k = 0;
   for (;; ++k) {
-    // ---- H step: L^W Z = B by Jacobi-preconditioned CG from Z = X^k
-    for (int i = tid; i < n_pad; i += nt) sts_v<DIM>(V, vidx<DIM, T>(i, 0, 1) / DP, ldv<DIM>(X, i));
-    __syncthreads();
-    if (!bpass<DIM, PM_MATVEC, 1, W, T>(n, nb, Dg)) return;
+    // ---- H step: L^W Z = B by Jacobi-preconditioned CG from Z = X^k.  The
+    // starting residual B - L^W X^k takes an all-pairs pass at the first
+    // iteration and every LWX_REFRESH-th; in between the previous iteration
+    // left it in R0 (L^W X^k from that H step's B, R and R0, as in the
+    // single-graph kernel).
+    const bool lwx_pass = (k % LWX_REFRESH) == 0;
+    if (lwx_pass) {
+      for (int i = tid; i < n_pad; i += nt) sts_v<DIM>(V, vidx<DIM, T>(i, 0, 1) / DP, ldv<DIM>(X, i));
+      __syncthreads();
+      if (!bpass<DIM, PM_MATVEC, 1, W, T>(n, nb, Dg)) return;
+    }
     {
       double v[3 * DIM];
 #pragma unroll
@@ -449,12 +457,17 @@ __device__ __forceinline__ void run_graph(int g) {
       for (int i = tid; i < n_pad; i += nt) {
         const Vec<DIM> x = ldv<DIM>(X, i), b = ldv<DIM>(B, i);
         const float s = __ldcg(S + i), is = __ldcg(IS + i);
+        const Vec<DIM> r0 = lwx_pass ? vzero<DIM>() : ldv<DIM>(R0, i);
         Vec<DIM> r, u;
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
-          const float a = A0[i * DP + d];
-          A0[i * DP + d] = 0.f;
-          r.c[d] = b.c[d] - fmaf(s, x.c[d], -a);
+          if (lwx_pass) {
+            const float a = A0[i * DP + d];
+            A0[i * DP + d] = 0.f;
+            r.c[d] = b.c[d] - fmaf(s, x.c[d], -a);
+          } else {
+            r.c[d] = r0.c[d];
+          }
           u.c[d] = is * r.c[d];
           v[d] += (double)(r.c[d] * u.c[d]);
           v[DIM + d] += (double)(r.c[d] * r.c[d]);
@@ -462,10 +475,11 @@ __device__ __forceinline__ void run_graph(int g) {
         }
         stv<DIM>(Z, i, x);
         stv<DIM>(Rr, i, r);
+        stv<DIM>(R0, i, r);
         stv<DIM>(Pp, i, u);
         sts_v<DIM>(V, vidx<DIM, T>(i, 0, 1) / DP, u);
       }
-      if (tid == 0) st->pmv += 1.0;
+      if (tid == 0 && lwx_pass) st->pmv += 1.0;
       bcta_sum<3 * DIM>(v, scratch, st);
       if (tid == 0) {
         for (int d = 0; d < DIM; ++d) {
@@ -615,7 +629,11 @@ __device__ __forceinline__ void run_graph(int g) {
       for (int e = 0; e < 4 * DIM; ++e) v[e] = 0.0;
       for (int i = tid; i < n_pad; i += nt) {
         const Vec<DIM> z = ldv<DIM>(Z, i), x = ldv<DIM>(X, i);
-        Vec<DIM> xn, b;
+        // this H step's B, final residual R = B - L^W z and starting residual
+        // R0 = B - L^W X^k give L^W X^{k+1} (z or the extrapolation) and the
+        // next step's starting residual without a pass
+        const Vec<DIM> bo = ldv<DIM>(B, i), rf = ldv<DIM>(Rr, i), r0 = ldv<DIM>(R0, i);
+        Vec<DIM> xn, b, r0n;
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
           xn.c[d] = accept ? ((i < n) ? sor_xt(z.c[d], x.c[d], om) : 0.f) : z.c[d];
@@ -623,6 +641,9 @@ __device__ __forceinline__ void run_graph(int g) {
           A0[i * DP + d] = 0.f;
           if (two) A1[i * DP + d] = 0.f;
           b.c[d] = accept ? b1 : b0;
+          const float lz = bo.c[d] - rf.c[d];
+          const float lwx = accept ? fmaf(1.f + om, lz, -om * (bo.c[d] - r0.c[d])) : lz;
+          r0n.c[d] = b.c[d] - lwx;
           if (i < n) {
             const double dx = (double)xn.c[d] - (double)x.c[d];
             v[d] += (double)xn.c[d];
@@ -633,6 +654,7 @@ __device__ __forceinline__ void run_graph(int g) {
         }
         stv<DIM>(X, i, xn);
         stv<DIM>(B, i, b);
+        stv<DIM>(R0, i, r0n);
       }
       bcta_sum<4 * DIM>(v, scratch, st);
       if (tid == 0) {

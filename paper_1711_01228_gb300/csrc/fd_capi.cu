@@ -1458,7 +1458,7 @@ struct fd_batch {
   int lut_rows = 0, max_diam = 0, disconnected = 0;
   float* d_s = nullptr;
   float* d_inv_s = nullptr;
-  float* d_pool = nullptr;   // X, Z, R, P, B: [5][P][dimp]
+  float* d_pool = nullptr;   // X, Z, R, P, B, R0: [6][P][dimp]
   float* d_xin = nullptr;    // [N][dim] staging of host layouts
   double* d_omega = nullptr; // [G]
   double* d_omega_seq = nullptr;
@@ -1761,6 +1761,7 @@ fd_status batch_run_dev(fd_batch* b, const float* x_in, float* x_out, const fd_o
   p.R = b->d_pool + 2 * ps;
   p.Pd = b->d_pool + 3 * ps;
   p.B = b->d_pool + 4 * ps;
+  p.R0 = b->d_pool + 5 * ps;
   p.omega = b->d_omega;
   p.omega_seq = seq;
   p.max_iter = max_iter;
@@ -2033,7 +2034,7 @@ fd_status fd_batch_create(fd_batch** out, int32_t num_graphs, int32_t dim, const
   }
   const size_t ps = (size_t)b->P * b->dimp;
   if ((s = dev_alloc(&b->d_lut, lut.size())) != FD_OK) return bail(s);
-  if ((s = dev_alloc(&b->d_pool, 5 * ps)) != FD_OK) return bail(s);
+  if ((s = dev_alloc(&b->d_pool, 6 * ps)) != FD_OK) return bail(s);
   if ((s = dev_alloc(&b->d_xin, (size_t)N * dim)) != FD_OK) return bail(s);
   if ((s = dev_alloc(&b->d_omega, (size_t)G)) != FD_OK) return bail(s);
   if ((s = dev_alloc(&b->d_queue, 4)) != FD_OK) return bail(s);
@@ -2041,7 +2042,7 @@ fd_status fd_batch_create(fd_batch** out, int32_t num_graphs, int32_t dim, const
   if ((s = dev_alloc(&b->d_dout, (size_t)5 * G)) != FD_OK) return bail(s);
   if ((s = dev_alloc(&b->d_params, 1)) != FD_OK) return bail(s);
   if (cudaMemcpyAsync(b->d_lut, lut.data(), lut.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemsetAsync(b->d_pool, 0, 5 * ps * sizeof(float), st) != cudaSuccess ||
+      cudaMemsetAsync(b->d_pool, 0, 6 * ps * sizeof(float), st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess) {
     cudaGetLastError();
     return bail(FD_ERR_CUDA);

@@ -188,6 +188,7 @@ struct BParams {
   const float* x_in;      // [N][dim] input layouts, concatenated
   float* x_out;           // [N][dim] output layouts
   float *X, *Z, *R, *Pd, *B;  // [P][DP] layout, CG iterate, residual, direction, right-hand side
+  float* R0;              // [P][DP] the next H step's starting residual (between refresh passes)
   const double* omega;    // [G] omega of each graph (FD_OMEGA_FIXED)
   const double* omega_seq;// [max_iter] omega of iteration k (FD_OMEGA_PROB), or NULL
   int max_iter, cg_max, stop;
