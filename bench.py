@@ -200,7 +200,8 @@ def fp32_peak_tflops(dev):
     return sms * 128 * 2 * clk * 1e6 / 1e12, sms, clk, src
 
 
-TAG_NAMES = {4: "rhs0", 5: "lw_x0", 6: "lw_u0", 7: "lw_cg", 8: "candidates", 9: "vertex_phase", 10: "dense_apply"}
+TAG_NAMES = {4: "rhs0", 5: "lw_x0", 6: "lw_u0", 7: "lw_cg", 8: "candidates", 9: "vertex_phase", 10: "dense_apply",
+             12: "cg_last"}
 
 
 def pass_profile(L, X, dim, iters, opts, code_bytes_total, pairs, fp32_peak, hbm_peak):

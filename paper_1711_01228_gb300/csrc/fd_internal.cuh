@@ -27,7 +27,7 @@ constexpr int TILE = 128;          // vertices per tile side
 constexpr int CTA = 128;           // threads per CTA of the pair kernels (4 warps)
 constexpr int LUT_N = 256;         // uint8 codes
 constexpr int LUT_ROW = 256;       // bytes per code in the replicated table: 32 x 1/d, then 32 x 1/d^2
-constexpr int SC_STRIDE = 24;      // scalars of one grid-wide reduction, at most
+constexpr int SC_STRIDE = 36;      // scalars of one grid-wide reduction, at most
 constexpr int MAX_NBUF = 4;        // stages of the tile pipeline
 constexpr int MAX_CTA_TASKS = 128; // task descriptors a CTA keeps in shared memory
 
@@ -76,7 +76,7 @@ struct Ctrl {
   int timeout_where;           // barrier index that timed out (diagnostic)
   int timeline_n;              // timeline entries written
   unsigned long long t_start;  // %globaltimer at kernel start (CTA 0)
-  float2 red[32];              // grid-wide sums of a reduction barrier (double-float), written by its last CTA
+  float2 red[SC_STRIDE];       // grid-wide sums of a reduction barrier (double-float), written by its last CTA
   double red_d[4];             // FP64 scalars computed by that CTA (termination criterion)
   // every CTA adds its partial sums (FP64 atomics) to set (b & 1) before it
   // arrives at reduction barrier b; the last CTA at barrier b clears set

@@ -908,7 +908,7 @@ static_assert(sizeof(PassCtl) <= SmemLayout<1, CODE_U8>::OFF_RUN - SmemLayout<1,
 struct RunState {
   double f_cur, f_new, crit, passes_mv, passes_st, f_enum0, passes_en;
   int cg_total, cg_maxed, cg_stalled, n_acc, it_outer, it;
-  int accept, bsel, stop, all_conv, cg_done;
+  int accept, bsel, stop, all_conv, cg_done, cg_last;
   int conv[3];
   float z0[3], om_prev;
   float alpha[3], beta[3], gam[3], rz[3], bb[3];
@@ -1736,6 +1736,8 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
         }
       }
       __syncthreads();
+      if (tid == 0) rs->cg_last = 0;
+      __syncthreads();
       while (true) {
         // One step of preconditioned CG in the single-reduction form of
         // Chronopoulos and Gear: p = u + beta p, s = w + beta s, x += alpha p,
@@ -1743,8 +1745,36 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
         // the next direction p' = u + beta' p is needed before beta' is known;
         // it is expanded as (u,w) + beta' ((u,s) + (p,w)) + beta'^2 (p,s) from
         // dot products taken here, instead of the usual recurrence, which
-        // loses positivity in FP32.
+        // loses positivity in FP32.  The pass of a step computes w for the
+        // step after it; when the residual that step leaves, expanded as
+        // |r - alpha (w + beta s)|^2 from dot products taken here too, already
+        // meets cg_tol, the step runs without its pass (cg_last) and ends the
+        // solve: that pass's w would never be used.
         // Slots: [0,D) r.u  [D,2D) w.u  [2D,3D) r.r  [3D,4D) u.s  [4D,5D) p.w  [5D,6D) p.s
+        //        [6D,7D) r.w  [7D,8D) r.s  [8D,9D) w.w  [9D,10D) w.s  [10D,11D) s.s
+        if (rs->cg_last) {
+          float al[DIM], be[DIM];
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) {
+            al[d] = rs->alpha[d];
+            be[d] = rs->beta[d];
+          }
+          vertex_phase<0>(p, red64, nullptr, [&](int i, df(&)[1]) {
+            const Vec<DIM> u = ldv<DIM>(p.U, i), w = ldv<DIM>(p.W, i), pp = ldv<DIM>(p.P, i),
+                           sp = ldv<DIM>(p.S, i);
+            Vec<DIM> x = ldv<DIM>(p.Zw, i), r = ldv<DIM>(p.R, i);
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) {
+              x.c[d] = fmaf(al[d], fmaf(be[d], pp.c[d], u.c[d]), x.c[d]);
+              r.c[d] = fmaf(-al[d], fmaf(be[d], sp.c[d], w.c[d]), r.c[d]);
+            }
+            stv<DIM>(p.Zw, i, x);
+            stv<DIM>(p.R, i, r);
+          });
+          if (tid == 0) ++rs->it;
+          FD_SYNC(12);
+          break;
+        }
         PassSrc src = direct_src(p.R, SK_CGU);
         src.a[1] = p.W;
         src.a[2] = p.S;
@@ -1766,7 +1796,10 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
           al[d] = src.alpha[d];
           be[d] = src.beta[d];
         }
-        vertex_phase<6 * DIM>(p, red64, RSUM, [&](int i, df(&v)[6 * DIM]) {
+        // 11 D sums: more than the reduction scratch at OFF_RED64 holds in 3-D;
+        // the stage area is idle between passes and takes them
+        float2* red_cg_buf = reinterpret_cast<float2*>(smem + L::stage_base(CODE == CODE_U8 ? p.lut_rows * LUT_ROW : 0));
+        vertex_phase<11 * DIM>(p, red_cg_buf, RSUM, [&](int i, df(&v)[11 * DIM]) {
           const float s = __ldcg(p.s + i), is = __ldcg(p.inv_s + i);
           Vec<DIM> u = ldv<DIM>(p.U, i), w = ldv<DIM>(p.W, i), pp = ldv<DIM>(p.P, i), sp = ldv<DIM>(p.S, i);
           Vec<DIM> x = ldv<DIM>(p.Zw, i), r = ldv<DIM>(p.R, i);
@@ -1788,6 +1821,11 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
             v[3 * DIM + d] = df_add(v[3 * DIM + d], df_prod(un, sn));
             v[4 * DIM + d] = df_add(v[4 * DIM + d], df_prod(pn, w.c[d]));
             v[5 * DIM + d] = df_add(v[5 * DIM + d], df_prod(pn, sn));
+            v[6 * DIM + d] = df_add(v[6 * DIM + d], df_prod(r.c[d], w.c[d]));
+            v[7 * DIM + d] = df_add(v[7 * DIM + d], df_prod(r.c[d], sn));
+            v[8 * DIM + d] = df_add(v[8 * DIM + d], df_prod(w.c[d], w.c[d]));
+            v[9 * DIM + d] = df_add(v[9 * DIM + d], df_prod(w.c[d], sn));
+            v[10 * DIM + d] = df_add(v[10 * DIM + d], df_prod(sn, sn));
           }
           stv<DIM>(p.P, i, pp);
           stv<DIM>(p.S, i, sp);
@@ -1796,11 +1834,11 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
           stv<DIM>(p.U, i, u);
           stv<DIM>(p.W, i, w);
         });
-        auto red_cg = [&](const double* sums) { take_sums<6 * DIM>(ctrl, sums); };
+        auto red_cg = [&](const double* sums) { take_sums<11 * DIM>(ctrl, sums); };
         FD_SYNC_RED(9, red_cg);
         if (tid == 0) {
-          df v[6 * DIM];
-          load_red<6 * DIM>(ctrl, v);
+          df v[11 * DIM];
+          load_red<11 * DIM>(ctrl, v);
           int done = 1;
           for (int d = 0; d < DIM; ++d) {
             const float gn = df_f(v[d]), dn = df_f(v[DIM + d]), rrn = df_f(v[2 * DIM + d]);
@@ -1831,6 +1869,23 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
             done = 1;
           }
           rs->cg_done = done;
+          if (!done) {
+            // the residual after the next update, r' = r - alpha (w + beta s), per
+            // column: if every column meets cg_tol with it, the next step is the
+            // last and needs no pass
+            int last = 1;
+            for (int d = 0; d < DIM; ++d) {
+              if (rs->conv[d]) continue;
+              const double al = rs->alpha[d], be = rs->beta[d];
+              const double rr = df_to_double(v[2 * DIM + d]);
+              const double rs_ = df_to_double(v[6 * DIM + d]) + be * df_to_double(v[7 * DIM + d]);
+              const double ss = df_to_double(v[8 * DIM + d]) + 2.0 * be * df_to_double(v[9 * DIM + d]) +
+                                be * be * df_to_double(v[10 * DIM + d]);
+              const double rr_next = rr - 2.0 * al * rs_ + al * al * ss;
+              if (!(rr_next <= (double)cgt2 * (double)rs->bb[d])) last = 0;
+            }
+            rs->cg_last = last;
+          }
         }
         __syncthreads();
         if (rs->cg_done) break;

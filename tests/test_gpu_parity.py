@@ -305,12 +305,16 @@ def test_invariance_under_rigid_motion(dim):
 @pytest.mark.parametrize("tps", ["1", "2"])
 def test_stage_shapes_agree_with_oracle(tps, monkeypatch):
     # one or two consecutive tiles per pipeline stage (the two-tile kernel serves
-    # uint8 codes in 1-D/2-D): a graph of 6 blocks with a ragged last block, so
-    # that tasks end on odd and even tile counts, steps wrap past the last block,
-    # and few CTAs walk many steps
+    # uint8 codes with a small table): a graph of 6 blocks with a ragged last
+    # block, so that tasks end on odd and even tile counts, steps wrap past the
+    # last block, and few CTAs walk many steps.  A Delaunay mesh, whose run
+    # converges (111 iterations in FP64), so that the converged-run bounds
+    # apply; a capped run (the 700-vertex BA graph stops at 1000 iterations
+    # with its stress still falling 5e-6 per iteration) compares trajectories,
+    # not layouts.
     monkeypatch.setenv("FDLAYOUT_TPS", tps)
     monkeypatch.setenv("FDLAYOUT_MAX_CTAS", "5")
-    rp, ci = synth.barabasi_albert(700, 3, seed=9)
+    rp, ci = synth.delaunay(700, seed=9)
     n = len(rp) - 1
     D = _dense(rp, ci)
     X0 = synth.initial_layout(n, 2, seed=2)
