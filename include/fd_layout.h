@@ -119,6 +119,9 @@ typedef struct {
   int32_t reserved;
   double enum_candidate_passes; /* FD_OMEGA_ENUM: candidate stresses evaluated by the enumeration passes
                               (19 per pass, stress only; not in stress_passes) */
+  double rhs_skipped;      /* candidate evaluations counted in stress_passes whose right-hand side was
+                              not computed: the two-candidate pass computes only the extrapolated
+                              layout's (one per such pass) */
 } fd_stats;
 
 /* Library facts about a handle. */

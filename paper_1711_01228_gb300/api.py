@@ -48,7 +48,7 @@ class Stats(ctypes.Structure):
                 ("final_stress", ctypes.c_double), ("final_crit", ctypes.c_double),
                 ("matvec_passes", ctypes.c_double), ("stress_passes", ctypes.c_double),
                 ("kernel_ms", ctypes.c_double), ("cg_stalled", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("enum_candidate_passes", ctypes.c_double)]
+                ("enum_candidate_passes", ctypes.c_double), ("rhs_skipped", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):

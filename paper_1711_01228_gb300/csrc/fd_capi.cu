@@ -592,6 +592,7 @@ void fill_stats(fd_layout* h, const Ctrl& c, double kms) {
   h->stats.kernel_ms = kms;
   h->stats.cg_stalled = c.cg_stalled;
   h->stats.enum_candidate_passes = c.enum_passes;
+  h->stats.rhs_skipped = c.rhs_skipped;
 }
 
 // Positions in: device pointers are used in place, host arrays are staged.

@@ -73,6 +73,7 @@ struct Ctrl {
   double matvec_passes;        // y = L^W p passes
   double stress_passes;        // stress (+ RHS or force) passes, per candidate
   double enum_passes;          // candidate stresses of the enumerating strategy (NENUM per enumeration pass)
+  double rhs_skipped;          // candidate evaluations (in stress_passes) without their right-hand side
   int timeout_where;           // barrier index that timed out (diagnostic)
   int timeline_n;              // timeline entries written
   unsigned long long t_start;  // %globaltimer at kernel start (CTA 0)

@@ -189,7 +189,10 @@ __device__ __forceinline__ void st_acc(double* a, int i, const Vec<DIM>& v) {
 
 // PM_ENUM: stress of the NENUM extrapolations (1 + omega) z - omega x,
 // omega = 0, 0.5, ..., 9, of one CG solution z (Sec. 5.2.2).
-enum PairMode { PM_STRESS = 0, PM_FORCES = 1, PM_RHS = 2, PM_MATVEC = 3, PM_ENUM = 4 };
+// PM_K2L: the two candidates' stresses and the right-hand side of the second
+// only (the extrapolated layout, which line 6 of Algorithm 2 keeps in most
+// iterations); when the first is kept, a PM_RHS pass of its own follows.
+enum PairMode { PM_STRESS = 0, PM_FORCES = 1, PM_RHS = 2, PM_MATVEC = 3, PM_ENUM = 4, PM_K2L = 5 };
 constexpr int NENUM = 19;
 constexpr float ENUM_STEP = 0.5f;
 
@@ -597,7 +600,8 @@ __device__ __forceinline__ void tile_compute(const unsigned char* __restrict__ d
           V = pk2(dv[2 * a2], dv[2 * a2 + 1]);
           W = mul2(V, V);
         }
-        if constexpr ((EDGE || CODE != CODE_U8) && (MODE == PM_STRESS || MODE == PM_RHS || MODE == PM_ENUM))
+        if constexpr ((EDGE || CODE != CODE_U8) &&
+                      (MODE == PM_STRESS || MODE == PM_RHS || MODE == PM_K2L || MODE == PM_ENUM))
           NEGM = pk2(lo2(V) > 0.f ? -1.f : 0.f, hi2(V) > 0.f ? -1.f : 0.f);
         if constexpr (MODE == PM_MATVEC) {
 #pragma unroll
@@ -637,16 +641,18 @@ __device__ __forceinline__ void tile_compute(const unsigned char* __restrict__ d
             for (int d = 1; d < DIM; ++d) R2 = fma2(DX[d], DX[d], R2);
             const f2x RS = pk2(rsqrt_approx(lo2(R2)), rsqrt_approx(hi2(R2)));
             f2x CO = mul2(RS, V);  // 1 / (d r)
-            if constexpr (MODE == PM_STRESS || MODE == PM_RHS) {
+            if constexpr (MODE == PM_STRESS || MODE == PM_RHS || MODE == PM_K2L) {
               const f2x TT = fma2(R2, CO, NEGM);  // r / d - 1
               stp[c] = fma2(TT, TT, stp[c]);
             }
             if constexpr (MODE == PM_FORCES) CO = sub2(CO, W);  // 1 / (d r) - 1 / d^2
             if constexpr (MODE != PM_STRESS) {
+              if (MODE != PM_K2L || c == NC - 1) {
 #pragma unroll
-              for (int d = 0; d < DIM; ++d) {
-                rows.acc[c][d][a2] = fma2(CO, DX[d], rows.acc[c][d][a2]);
-                J[c][d] = (a2 == 0) ? mul2(CO, DX[d]) : fma2(CO, DX[d], J[c][d]);
+                for (int d = 0; d < DIM; ++d) {
+                  rows.acc[c][d][a2] = fma2(CO, DX[d], rows.acc[c][d][a2]);
+                  J[c][d] = (a2 == 0) ? mul2(CO, DX[d]) : fma2(CO, DX[d], J[c][d]);
+                }
               }
             }
           }
@@ -657,6 +663,7 @@ __device__ __forceinline__ void tile_compute(const unsigned char* __restrict__ d
         for (int c = 0; c < NC; ++c)
 #pragma unroll
           for (int d = 0; d < DIM; ++d) {
+            if (MODE == PM_K2L && c != NC - 1) continue;
             jacc[h][c][d] += lo2(J[c][d]);
             jacc[h][c][d] += hi2(J[c][d]);
             if constexpr (CH < G) jacc[h][c][d] = __shfl_sync(0xffffffffu, jacc[h][c][d], (q + CH) & (G - 1), G);
@@ -669,6 +676,12 @@ __device__ __forceinline__ void tile_compute(const unsigned char* __restrict__ d
   for (int e = 0; e < NS; ++e) st[e] = lo2(stp[e]) + hi2(stp[e]);
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
+    if constexpr (MODE == PM_K2L) {
+      if (c != NC - 1) {
+        jout[c] = vzero<DIM>();
+        continue;
+      }
+    }
     if constexpr (MODE != PM_STRESS && MODE != PM_ENUM) {
 #pragma unroll
       for (int d = 0; d < DIM; ++d) {
@@ -1048,13 +1061,14 @@ __device__ FD_PASS_ATTR bool pair_pass_impl(PairState* ps_io, double* acc) {
       const unsigned char* dt = smem + L::off_d(sb, s_it, tps) + u * L::DBUF;
       const float* colv = rawj + u * TILE * DP;
       const bool edge = (it.k + u == 0) || (g.n < g.n_pad && (I == g.nb - 1 || Ju == g.nb - 1));
-      if constexpr (MODE == PM_STRESS || MODE == PM_RHS || MODE == PM_ENUM || (MODE == PM_MATVEC && kMatvecRcp)) {
+      if constexpr (MODE == PM_STRESS || MODE == PM_RHS || MODE == PM_K2L || MODE == PM_ENUM ||
+                    (MODE == PM_MATVEC && kMatvecRcp)) {
         if (edge) tile_compute<DIM, MODE, NC, CODE, true>(dt, colv, lut, rows, jout, st, tid, astr);
         else tile_compute<DIM, MODE, NC, CODE, false>(dt, colv, lut, rows, jout, st, tid, astr);
       } else {
         tile_compute<DIM, MODE, NC, CODE, false>(dt, colv, lut, rows, jout, st, tid, astr);
       }
-      if constexpr (MODE == PM_STRESS || MODE == PM_RHS || MODE == PM_ENUM) {
+      if constexpr (MODE == PM_STRESS || MODE == PM_RHS || MODE == PM_K2L || MODE == PM_ENUM) {
 #pragma unroll
         for (int c = 0; c < NS; ++c) kahan_add(ssum[c], scomp[c], st[c]);
       }
@@ -1064,6 +1078,7 @@ __device__ FD_PASS_ATTR bool pair_pass_impl(PairState* ps_io, double* acc) {
         if (j < g.n) {
 #pragma unroll
           for (int c = 0; c < NC; ++c) {
+            if (MODE == PM_K2L && c != NC - 1) continue;
             Vec<DIM> v = jout[c];
             if constexpr (MODE != PM_MATVEC) {
 #pragma unroll
@@ -1088,6 +1103,7 @@ __device__ FD_PASS_ATTR bool pair_pass_impl(PairState* ps_io, double* acc) {
         for (int c = 0; c < NC; ++c)
 #pragma unroll
           for (int a2 = 0; a2 < R / 2; ++a2) {
+            if (MODE == PM_K2L && c != NC - 1) continue;
             Vec<DIM> v0, v1;
 #pragma unroll
             for (int d = 0; d < DIM; ++d) {
@@ -1103,6 +1119,7 @@ __device__ FD_PASS_ATTR bool pair_pass_impl(PairState* ps_io, double* acc) {
         if (i < g.n) {
 #pragma unroll
           for (int c = 0; c < NC; ++c) {
+            if (MODE == PM_K2L && c != NC - 1) continue;
             Vec<DIM> s = lds_v<DIM>(red + ((size_t)(c * R) * TILE) * DP, tid);
 #pragma unroll
             for (int gg = 1; gg < R; ++gg) {
@@ -1119,7 +1136,7 @@ __device__ FD_PASS_ATTR bool pair_pass_impl(PairState* ps_io, double* acc) {
     s_it = (s_it + 1 == nbuf) ? 0 : s_it + 1;
   }
   // stress of this CTA's pairs (per candidate), double-float slots per CTA
-  if constexpr (MODE == PM_STRESS || MODE == PM_RHS || MODE == PM_ENUM) {
+  if constexpr (MODE == PM_STRESS || MODE == PM_RHS || MODE == PM_K2L || MODE == PM_ENUM) {
     df v[NS];
 #pragma unroll
     for (int c = 0; c < NS; ++c) v[c] = df_add(df_of(ssum[c]), df_of(-scomp[c]));
@@ -2008,8 +2025,11 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
       rs->om_prev = src.om;
       rs->passes_st += two ? 2.0 : 1.0;
     }
+    // Both candidates' stresses, and the right-hand side of the extrapolated
+    // one only: line 6 keeps it in most iterations; when it keeps z instead, a
+    // pass for z's right-hand side follows (below).
     if (two) {
-      if (!pair_pass<DIM, PM_RHS, 2, CODE, TPS>(p, smem, ps, src, acc0, RSUM)) return;
+      if (!pair_pass<DIM, PM_K2L, 2, CODE, TPS>(p, smem, ps, src, acc0, RSUM)) return;
       FD_SYNC_RED(8, red_stress(2));
     } else {
       if (!pair_pass<DIM, PM_RHS, 1, CODE, TPS>(p, smem, ps, src, acc0, RSUM)) return;
@@ -2020,6 +2040,7 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
       load_red<2>(ctrl, fz);
       const double fZ = df_to_double(fz[0]);
       const double fT = two ? df_to_double(fz[1]) : fZ;
+      if (two && blockIdx.x == 0) ctrl->rhs_skipped += 1.0;
       if (!isfinite(fZ) || !isfinite(fT)) {
         set_error(ctrl, E_NONFINITE);
         rs->stop = 1;
@@ -2044,6 +2065,20 @@ __global__ void __launch_bounds__(CTA, 2) fd_main_kernel(KParams p_in) {
     }
     __syncthreads();
     if (rs->stop) return;
+    if (two && !rs->accept) {
+      // z is kept: its right-hand side, which the two-candidate pass left out
+      // (this pass recomputes z's stress; that value is not used)
+      PassSrc zs = direct_src(p.Zw, SK_SEL);
+      zs.a[1] = p.X;
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) zs.z0[d] = src.z0[d];
+      zs.om = src.om;
+      zs.sel = 0;
+      zs.oms = p.om_scale;
+      if (!pair_pass<DIM, PM_RHS, 1, CODE, TPS>(p, smem, ps, zs, acc0, RSUM)) return;
+      if (tid == 0) rs->passes_st += 1.0;
+      FD_SYNC_RED(11, red_stress(1));
+    }
   }
 
   // --- output: X holds the layout accepted by the last iteration
