@@ -588,7 +588,9 @@ def run_batched(args, local_rank, peak_tflops):
     flops = 0.0
     for g in range(G):
         pg = 0.5 * sizes[g] * (sizes[g] - 1)
-        flops += pg * (res.matvec_passes[g] * FLOP_MV[2] + res.stress_passes[g] * FLOP_K2[2])
+        # one two-candidate pass per iteration (omega != 0), without the first candidate's RHS
+        flops += pg * (res.matvec_passes[g] * FLOP_MV[2] + res.stress_passes[g] * FLOP_K2[2]
+                       - it[g] * FLOP_RHS[2])
     achieved = flops / (ms / 1e3) / 1e12
     Xb = X.cpu().numpy()
     B.close()
@@ -672,7 +674,8 @@ def run_batch_tiles(args, local_rank, peak_tflops):
         res = B.run(X, **opts)
         ms = res.stats["kernel_ms"]
         flops = float(np.sum(0.5 * sizes * (sizes - 1) * (res.matvec_passes * FLOP_MV[2]
-                                                          + res.stress_passes * FLOP_K2[2])))
+                                                          + res.stress_passes * FLOP_K2[2]
+                                                          - res.iterations * FLOP_RHS[2])))
         info = B.info()
         tot = float(res.graph_ms.sum())
         per = {}

@@ -228,7 +228,7 @@ __device__ __noinline__ bool bpass(int n, int nb, const unsigned char* Dg) {
       const bool edge = (k == 0) || (n < nb * T && (I == nb - 1 || J == nb - 1));
       if (edge) tile_compute<DIM, MODE, NC, CODE_U8, true, T>(dt, colv, lut, rows, jout, stv_, tid);
       else tile_compute<DIM, MODE, NC, CODE_U8, false, T>(dt, colv, lut, rows, jout, stv_, tid);
-      if constexpr (MODE == PM_STRESS || MODE == PM_RHS) {
+      if constexpr (MODE == PM_STRESS || MODE == PM_RHS || MODE == PM_K2L) {
 #pragma unroll
         for (int c = 0; c < NS; ++c) kahan_add(ssum[c], scomp[c], stv_[c]);
       }
@@ -236,10 +236,12 @@ __device__ __noinline__ bool bpass(int n, int nb, const unsigned char* Dg) {
         const int j = J * T + tid;
         if (j < n) {
 #pragma unroll
-          for (int c = 0; c < NC; ++c)
+          for (int c = 0; c < NC; ++c) {
+            if (MODE == PM_K2L && c != NC - 1) continue;  // no right-hand side of the first candidate
 #pragma unroll
             for (int d = 0; d < DIM; ++d)
               s_red_add(A + c * astride + j * DP + d, (MODE == PM_MATVEC) ? jout[c].c[d] : -jout[c].c[d]);
+          }
         }
         // row sums when the range leaves block row I: the column groups of a
         // warp are added by shuffles, the group's warps meet in the stage's
@@ -254,6 +256,7 @@ __device__ __noinline__ bool bpass(int n, int nb, const unsigned char* Dg) {
             for (int d = 0; d < DIM; ++d)
 #pragma unroll
               for (int a2 = 0; a2 < R / 2; ++a2) {
+                if (MODE == PM_K2L && c != NC - 1) continue;
                 float lo = lo2(rows.acc[c][d][a2]), hi = hi2(rows.acc[c][d][a2]);
 #pragma unroll
                 for (int m = G; m < 32 && m < T; m <<= 1) {
@@ -268,6 +271,7 @@ __device__ __noinline__ bool bpass(int n, int nb, const unsigned char* Dg) {
             for (int c = 0; c < NC; ++c)
 #pragma unroll
               for (int a2 = 0; a2 < R / 2; ++a2) {
+                if (MODE == PM_K2L && c != NC - 1) continue;
                 Vec<DIM> v0, v1;
 #pragma unroll
                 for (int d = 0; d < DIM; ++d) {
@@ -284,6 +288,7 @@ __device__ __noinline__ bool bpass(int n, int nb, const unsigned char* Dg) {
           if (i < n) {
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
+              if (MODE == PM_K2L && c != NC - 1) continue;
               Vec<DIM> sm = lds_v<DIM>(red + ((size_t)(c * NWG) * T) * DP, tid);
 #pragma unroll
               for (int gg = 1; gg < NWG; ++gg) {
@@ -319,7 +324,7 @@ __device__ __noinline__ bool bpass(int n, int nb, const unsigned char* Dg) {
     atomicAnd(&st->parity, ~(((1u << BMAX_NBUF) - 1u) << (w * BMAX_NBUF)));
     atomicOr(&st->parity, parity << (w * BMAX_NBUF));
   }
-  if constexpr (MODE == PM_STRESS || MODE == PM_RHS) {
+  if constexpr (MODE == PM_STRESS || MODE == PM_RHS || MODE == PM_K2L) {
     double v[NS];
 #pragma unroll
     for (int c = 0; c < NS; ++c) v[c] = (double)ssum[c] - (double)scomp[c];
@@ -614,14 +619,22 @@ __device__ __forceinline__ void run_graph(int g) {
     }
     if (tid == 0) st->cg_total += st->it;
     __syncthreads();
+    // both candidates' stresses, the right-hand side of the extrapolated one
+    // only (line 6 mostly keeps it); a pass for z's follows when z is kept
     if (two) {
-      if (!bpass<DIM, PM_RHS, 2, W, T>(n, nb, Dg)) return;
+      if (!bpass<DIM, PM_K2L, 2, W, T>(n, nb, Dg)) return;
     } else {
       if (!bpass<DIM, PM_RHS, 1, W, T>(n, nb, Dg)) return;
     }
     const double fZ = st->red[0], fT = two ? st->red[1] : st->red[0];
     const bool accept = two && (fT <= fZ);  // line 6, ties accept
     const double f_prev = st->f_cur, f_next = accept ? fT : fZ;
+    if (two && !accept) {
+      for (int i = tid; i < n_pad; i += nt) sts_v<DIM>(V, vidx<DIM, T>(i, 0, 1) / DP, ldv<DIM>(Z, i));
+      __syncthreads();
+      if (!bpass<DIM, PM_RHS, 1, W, T>(n, nb, Dg)) return;  // z's right-hand side into A0
+      if (tid == 0) st->pst += 1.0;
+    }
     // X^{k+1}, its right-hand side, and the displacement sums of the termination rule
     {
       double v[4 * DIM];
