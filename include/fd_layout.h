@@ -138,11 +138,13 @@ typedef struct {
   int32_t tasks;           /* work items (runs of tiles) per all-pairs pass */
   double apsp_ms;          /* device time of the shortest-path kernel at creation (CUDA events) */
   int32_t stages;          /* tiles in flight per CTA in the layout kernel's copy pipeline (2 to 4) */
-  int32_t bfs_sweeps;      /* unit edges: passes over the edge list summed over the 64-source searches */
+  int32_t bfs_sweeps;      /* unit edges: passes over the edge list summed over the multi-source searches */
   int32_t factored;        /* 1 after fd_factor (FD_SOLVER_DIRECT available) */
   double factor_ms;        /* device time of the last fd_factor (CUDA events) */
   int32_t tiles_per_stage; /* consecutive tiles of a task per pipeline stage (1 or 2) */
-  int32_t reserved;
+  int32_t bfs_sources;     /* unit edges: sources per multi-source search: 64 (one search per CTA) or
+                              256 (one search over all CTAs, a grid barrier per level; n >= 65536 and
+                              vertex 0's eccentricity <= 32) */
 } fd_info;
 
 /* Fills *opt with the defaults: omega 0.5, FIXED, REL_DISP, seed 0,

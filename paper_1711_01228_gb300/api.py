@@ -58,7 +58,7 @@ class Info(ctypes.Structure):
                 ("sm_count", ctypes.c_int32), ("grid", ctypes.c_int32), ("tasks", ctypes.c_int32),
                 ("apsp_ms", ctypes.c_double), ("stages", ctypes.c_int32), ("bfs_sweeps", ctypes.c_int32),
                 ("factored", ctypes.c_int32), ("factor_ms", ctypes.c_double), ("tiles_per_stage", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("bfs_sources", ctypes.c_int32)]
 
 
 class BatchInfo(ctypes.Structure):

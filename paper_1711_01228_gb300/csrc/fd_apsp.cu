@@ -132,6 +132,370 @@ __global__ void __launch_bounds__(1024) bfs_batch_kernel(int n, int nb, const in
   }
 }
 
+// Breadth-first searches for large graphs of small diameter.  bfs_batch_kernel
+// gives each CTA a 64-source batch of its own, and at n = 200,000 the CTAs'
+// per-vertex words (3 x 8 B x n each, 1.5 GB over 304 CTAs) overflow L2, so
+// every 8-byte neighbour-word gather costs a 32-byte DRAM sector.  Here all
+// CTAs take one batch of 256 sources at a time (a 32-byte word per vertex and
+// level) level by level, with a grid barrier (bounded waits) after each
+// level, so the words stay in L2.  A level costs a grid barrier, so this pays
+// for graphs with few levels per search (chosen on the host).
+//
+// Words: vis (sources that reached v) and the frontier F_l (sources that
+// reached v at level l) of every level l <= lcap, kept to the end of the
+// batch; deeper levels alternate between two further slots.  The 1-byte
+// codes of levels <= lcap are written at the end of the batch, 16 sources per
+// 16-byte store (the byte d_sv of source s is l for the l whose F_l holds s),
+// instead of one byte store per pair as each is reached; codes of deeper
+// levels (and float codes) are written as reached.
+//
+// A level ends with its slowest vertex, so vertices of degree above
+// WIDE_BIG_DEG (listed in big[] by the host, largest degree first) are pulled
+// by a warp each, the lanes striding over the edges; the others by a thread
+// each.  A batch ends after the level that reached nothing or the level after
+// which every vertex holds every source.
+constexpr int WIDE_BIG_DEG = 16;
+
+struct __align__(32) Words4 {
+  unsigned long long w[4];
+};
+
+__device__ __forceinline__ void or_word(Words4& acc, const Words4* f) {
+  const ulonglong2* q = reinterpret_cast<const ulonglong2*>(f);
+  const ulonglong2 lo = __ldcg(q), hi = __ldcg(q + 1);
+  acc.w[0] |= lo.x;
+  acc.w[1] |= lo.y;
+  acc.w[2] |= hi.x;
+  acc.w[3] |= hi.y;
+}
+
+// acc |= fr[col_idx[e]] over e = e0, e0 + st, .. < e1, four gathers in flight
+// (a level lasts as long as its slowest vertex's chain of L2 round trips).
+__device__ __forceinline__ void gather_or(Words4& acc, const Words4* fr, const int* __restrict__ col_idx, int e0,
+                                          int e1, int st) {
+  int e = e0;
+  for (; e + 3 * st < e1; e += 4 * st) {
+    const int u0 = col_idx[e], u1 = col_idx[e + st], u2 = col_idx[e + 2 * st], u3 = col_idx[e + 3 * st];
+    or_word(acc, fr + u0);
+    or_word(acc, fr + u1);
+    or_word(acc, fr + u2);
+    or_word(acc, fr + u3);
+  }
+  for (; e < e1; e += st) or_word(acc, fr + col_idx[e]);
+}
+
+// Codes of the sources of word w (sources s0 + 64 w ..) in the bits of nw
+// (reached v at this level) whose pair with v the batch's strips store.
+template <int CODE>
+__device__ __forceinline__ void wide_codes(void* D, int v, int s0, int w, unsigned long long nw, int nb,
+                                           const int* __restrict__ tile_base, const int* __restrict__ strip_len,
+                                           unsigned long long full, int level, int* overflow) {
+  const int sw = s0 + 64 * w, I = sw / TILE, il0 = sw % TILE;
+  int k;
+  unsigned long long m = nw & owned_bits(v, sw, I, nb, strip_len[I], full, &k);
+  if (!m) return;
+  const int tb = tile_base[I], jl = v % TILE;
+  while (m) {
+    const int b = __ffsll((long long)m) - 1;
+    m &= m - 1ull;
+    put_code<CODE>(D, tb + k, jl * TILE + il0 + b, (float)level, overflow);
+  }
+}
+
+// Frontier slot of level l: l itself up to lcap, then two alternating slots.
+__device__ __forceinline__ int wide_slot(int l, int lcap) { return (l <= lcap) ? l : lcap + 1 + (l & 1); }
+
+// acc |= (the bits of the batch's sources s0 .. s0 + nsrc - 1 among col_idx[e],
+// e = e0, e0 + st, .. < e1): the frontier of level 0 without reading it.
+__device__ __forceinline__ void source_or(Words4& acc, const int* __restrict__ col_idx, int e0, int e1, int st,
+                                          int s0, int nsrc) {
+  for (int e = e0; e < e1; e += st) {
+    const int d = col_idx[e] - s0;
+    if (d >= 0 && d < nsrc) {
+      const unsigned long long bit = 1ull << (d & 63);
+      const int w = d >> 6;  // register selects, not a local-memory index
+      acc.w[0] |= (w == 0) ? bit : 0ull;
+      acc.w[1] |= (w == 1) ? bit : 0ull;
+      acc.w[2] |= (w == 2) ? bit : 0ull;
+      acc.w[3] |= (w == 3) ? bit : 0ull;
+    }
+  }
+}
+
+// Grid barrier b of the level loop, fused with the OR of two per-CTA flags
+// (bit 0: a vertex was reached at this level; bit 1: a vertex is still
+// unreached by some source).  Slot b mod 3 of bar3 counts arrivals in bits
+// 0-20, flag-0 CTAs in bits 21-41, flag-1 CTAs in bits 42-62; CTA 0 clears
+// slot b + 1 before it arrives at b (its last readers arrived at b - 1).
+// Returns the two ORed flags, or -1 after a wait of timeout_ns (E_TIMEOUT
+// recorded) or another CTA's error.
+__device__ __forceinline__ int wide_barrier(unsigned long long* bar3, int b, int flags, Ctrl* ctrl,
+                                            long long timeout_ns) {
+  __shared__ int s_res;
+  const int f0 = __syncthreads_or(flags & 1), f1 = __syncthreads_or(flags & 2);
+  if (threadIdx.x == 0) {
+    if (blockIdx.x == 0) atomicExch(bar3 + (b + 1) % 3, 0ull);
+    __threadfence();
+    atomicAdd(bar3 + b % 3, 1ull + (f0 ? (1ull << 21) : 0ull) + (f1 ? (1ull << 42) : 0ull));
+    volatile unsigned long long* slot = bar3 + b % 3;
+    volatile int* err = &ctrl->err;
+    unsigned long long v = *slot;
+    int res = 0;
+    if ((v & 0x1fffffull) != gridDim.x) {
+      const unsigned long long t0 = globaltimer_ns();
+      while (true) {
+        v = *slot;
+        if ((v & 0x1fffffull) == gridDim.x) break;
+        if (*err != 0) {
+          res = -1;
+          break;
+        }
+        if ((long long)(globaltimer_ns() - t0) > timeout_ns) {
+          atomicCAS(&ctrl->err, 0, (int)E_TIMEOUT);
+          atomicExch(&ctrl->timeout_where, b);
+          res = -1;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    if (res == 0) res = (((v >> 21) & 0x1fffffull) ? 1 : 0) | (((v >> 42) & 0x1fffffull) ? 2 : 0);
+    s_res = res;
+  }
+  __syncthreads();
+  return s_res;
+}
+
+// 1-byte codes of vertex v's pairs with the sources of word w (s0 + 64 w ..)
+// from the frontiers F_1 .. F_lmax (disjoint bit sets): byte b of a 16-source
+// group is l where bit b is in F_l, 0 where no F_l holds it (unreached, filled
+// later; or reached below level lmax, written as reached: merge ORs the stored
+// bytes in, each byte being nonzero on one side at most).
+// spread[x]: byte i is 1 where bit i of x is set.
+__device__ __forceinline__ void wide_decode_word(unsigned char* D, int v, int s0, int w, unsigned long long fw,
+                                              const Words4* __restrict__ F, int n, int lmax, bool merge, int nb,
+                                              const int* __restrict__ tile_base,
+                                              const int* __restrict__ strip_len,
+                                              const unsigned long long* spread) {
+  if (!fw) return;
+  const int sw = s0 + 64 * w, I = sw / TILE, il0 = sw % TILE;
+  int k;
+  const unsigned long long om = owned_bits(v, sw, I, nb, strip_len[I], fw, &k);
+  if (!om) return;
+  unsigned long long c[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) c[q] = 0ull;
+  for (int l = 1; l <= lmax; ++l) {
+    const unsigned long long x = __ldcg(&F[(size_t)l * n + v].w[w]);
+    if (!x) continue;
+    const unsigned long long lv = (unsigned long long)l;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) c[q] |= spread[(x >> (8 * q)) & 0xff] * lv;
+  }
+  unsigned char* row = D + (size_t)(tile_base[I] + k) * TILE * TILE + (v % TILE) * TILE + il0;
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    const unsigned gm = (unsigned)(om >> (16 * g)) & 0xffffu;
+    if (gm == 0xffffu) {
+      ulonglong2* p = reinterpret_cast<ulonglong2*>(row + 16 * g);
+      if (merge) {
+        const ulonglong2 o = *p;
+        *p = make_ulonglong2(c[2 * g] | o.x, c[2 * g + 1] | o.y);
+      } else {
+        *p = make_ulonglong2(c[2 * g], c[2 * g + 1]);
+      }
+    } else if (gm) {  // the diagonal block or the ragged last batch: owned bytes only
+      for (int b = 0; b < 16; ++b) {
+        const unsigned char cb = (unsigned char)(c[2 * g + (b >> 3)] >> (8 * (b & 7)));
+        if (((gm >> b) & 1u) && (cb || !merge)) row[16 * g + b] = cb;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ unsigned long long pick4(const unsigned long long* a, int w) {
+  return (w == 0) ? a[0] : (w == 1) ? a[1] : (w == 2) ? a[2] : a[3];  // register selects
+}
+
+// Sources s0 + 64 w .. of a batch of nsrc sources, as bits of word w.
+__device__ __forceinline__ unsigned long long wide_full(int nsrc, int w) {
+  const int c = min(64, max(0, nsrc - 64 * w));
+  return (c == 64) ? ~0ull : ((1ull << c) - 1ull);
+}
+
+// The batch's own bits of vertex v (its level-0 frontier).
+__device__ __forceinline__ Words4 self_bits(int v, int s0, int nsrc) {
+  Words4 b;
+  const int d = v - s0;
+#pragma unroll
+  for (int w = 0; w < 4; ++w) b.w[w] = (d >= 64 * w && d < 64 * w + 64 && d < nsrc) ? (1ull << (d & 63)) : 0ull;
+  return b;
+}
+
+template <int CODE>
+__global__ void __launch_bounds__(512, 2) bfs_wide_kernel(int n, int nb, const int* __restrict__ row_ptr,
+                                                           const int* __restrict__ col_idx,
+                                                           const int* __restrict__ tile_base,
+                                                           const int* __restrict__ strip_len, void* D,
+                                                           Words4* words, int lcap, const int* __restrict__ big,
+                                                           int nbig, unsigned long long* bar3, Ctrl* ctrl,
+                                                           long long timeout_ns, int* maxlevel, int* overflow,
+                                                           int* sweeps) {
+  __shared__ unsigned long long spread[256];
+  for (int x = threadIdx.x; x < 256; x += blockDim.x) {
+    unsigned long long e = 0ull;
+    for (int i = 0; i < 8; ++i)
+      if ((x >> i) & 1) e |= 1ull << (8 * i);
+    spread[x] = e;
+  }
+  __syncthreads();
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gstride = gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31, gwarp = gtid >> 5, nwarps = gstride >> 5;
+  const int nbatches = (n + 255) / 256;
+  Words4* vis = words;
+  Words4* F = words + n;  // [lcap + 3][n]; slot 0 unused (level 1 reads col_idx alone)
+  int b = 0;
+  for (int batch = 0; batch < nbatches; ++batch) {
+    const int s0 = batch * 256;
+    const int nsrc = min(256, n - s0);
+    // full_at(w): the batch's sources in word w, recomputed where used (registers)
+#define full_at(w) wide_full(nsrc, (w))
+    // Every vertex's words (vis, F_l) are written only by its own agent (the
+    // thread or warp below, the same in every batch and level), so a batch
+    // starts without a barrier: its level 1 reads no frontier.
+    int level = 0, deepest = 0;
+    while (true) {
+      ++level;
+      const Words4* fr = F + (size_t)wide_slot(level - 1, lcap) * n;
+      Words4* nx = F + (size_t)wide_slot(level, lcap) * n;
+      const bool now = (CODE != CODE_U8) || level > lcap;  // codes written as reached
+      int any = 0, open_after = 0;
+      // vertices of degree <= WIDE_BIG_DEG: a thread each
+      for (int v = gtid; v < n; v += gstride) {
+        const int e0 = row_ptr[v], e1 = row_ptr[v + 1];
+        if (e1 - e0 > WIDE_BIG_DEG) continue;
+        const Words4 vs = (level == 1) ? self_bits(v, s0, nsrc) : vis[v];
+        Words4 nw;
+        bool open = false;
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+          nw.w[w] = 0ull;
+          open = open || (vs.w[w] != full_at(w));
+        }
+        Words4 nv = vs;
+        if (open) {
+          Words4 acc;
+#pragma unroll
+          for (int w = 0; w < 4; ++w) acc.w[w] = 0ull;
+          if (level == 1)
+            source_or(acc, col_idx, e0, e1, 1, s0, nsrc);
+          else
+            gather_or(acc, fr, col_idx, e0, e1, 1);
+          bool got = false, still = false;
+#pragma unroll
+          for (int w = 0; w < 4; ++w) {
+            nw.w[w] = acc.w[w] & ~vs.w[w] & full_at(w);
+            nv.w[w] = vs.w[w] | nw.w[w];
+            got = got || (nw.w[w] != 0ull);
+            still = still || (nv.w[w] != full_at(w));
+          }
+          if (still) open_after = 2;
+          if (got) {
+            any = 1;
+            if (now) {
+#pragma unroll
+              for (int w = 0; w < 4; ++w)
+                if (nw.w[w])
+                  wide_codes<CODE>(D, v, s0, w, nw.w[w], nb, tile_base, strip_len, full_at(w), level, overflow);
+            }
+          }
+          if (got || level == 1) vis[v] = nv;
+        } else if (level == 1) {
+          vis[v] = vs;
+        }
+        nx[v] = nw;
+      }
+      // vertices of larger degree: a warp each; lane l then writes the codes
+      // of bits [8 (l % 8), 8 (l % 8) + 8) of word l / 8
+      for (int i = gwarp; i < nbig; i += nwarps) {
+        const int v = big[i];
+        const Words4 vs = (level == 1) ? self_bits(v, s0, nsrc) : vis[v];
+        bool open = false;
+#pragma unroll
+        for (int w = 0; w < 4; ++w) open = open || (vs.w[w] != full_at(w));
+        Words4 nw;
+#pragma unroll
+        for (int w = 0; w < 4; ++w) nw.w[w] = 0ull;
+        Words4 nv = vs;
+        if (open) {  // warp-uniform
+          Words4 acc;
+#pragma unroll
+          for (int w = 0; w < 4; ++w) acc.w[w] = 0ull;
+          const int e0 = row_ptr[v] + lane, e1 = row_ptr[v + 1];
+          if (level == 1)
+            source_or(acc, col_idx, e0, e1, 32, s0, nsrc);
+          else
+            gather_or(acc, fr, col_idx, e0, e1, 32);
+          bool got = false, still = false;
+#pragma unroll
+          for (int w = 0; w < 4; ++w) {
+            const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)acc.w[w]);
+            const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(acc.w[w] >> 32));
+            nw.w[w] = (((unsigned long long)hi << 32) | lo) & ~vs.w[w] & full_at(w);
+            nv.w[w] = vs.w[w] | nw.w[w];
+            got = got || (nw.w[w] != 0ull);
+            still = still || (nv.w[w] != full_at(w));
+          }
+          if (still) open_after = 2;
+          if (got) {
+            any = 1;
+            if (now) {
+              const int w = lane >> 3;
+              const unsigned long long mine = pick4(nw.w, w) & (0xffull << (8 * (lane & 7)));
+              if (mine)
+                wide_codes<CODE>(D, v, s0, w, mine, nb, tile_base, strip_len, full_at(w), level, overflow);
+            }
+          }
+        }
+        if (lane == 0) {
+          if (open || level == 1) vis[v] = nv;
+          nx[v] = nw;
+        }
+      }
+      const int res = wide_barrier(bar3, b++, any | open_after, ctrl, timeout_ns);
+      if (res < 0) return;
+      if (!(res & 1)) {  // nothing reached at this level: the previous one was the last
+        deepest = level - 1;
+        break;
+      }
+      if (!(res & 2)) {  // every vertex reached by every source
+        deepest = level;
+        break;
+      }
+    }
+    if constexpr (CODE == CODE_U8) {
+      // codes of levels 1 .. min(deepest, lcap), each vertex by its own agent
+      const int lmax = min(deepest, lcap);
+      const bool merge = deepest > lcap;
+      unsigned char* Du = reinterpret_cast<unsigned char*>(D);
+      for (int v = gtid; v < n; v += gstride) {
+        if (row_ptr[v + 1] - row_ptr[v] > WIDE_BIG_DEG) continue;
+        for (int w = 0; w < 4; ++w)
+          wide_decode_word(Du, v, s0, w, full_at(w), F, n, lmax, merge, nb, tile_base, strip_len, spread);
+      }
+      for (int i = gwarp; i < nbig; i += nwarps)
+        if (lane < 4)
+          wide_decode_word(Du, big[i], s0, lane, full_at(lane), F, n, lmax, merge, nb, tile_base, strip_len,
+                           spread);
+    }
+#undef full_at
+    if (gtid == 0) {
+      atomicMax(maxlevel, deepest);
+      atomicAdd(sweeps, level);  // passes over the edge list
+    }
+  }
+}
+
 // Weighted shortest paths: one source per CTA iteration (frontier search of
 // fd_sssp.cuh in the CTA's scratch: 4 n ints), each pair written once into
 // the tile that owns it.  *err is set if a search ran out of rounds.
@@ -467,6 +831,27 @@ cudaError_t launch_bfs(int code, int n, int nb, const int* rp, const int* ci, co
     bfs_batch_kernel<CODE_F32><<<grid, 1024, 0, st>>>(n, nb, rp, ci, tile_base, strip_len, D, scratch, stride,
                                                       nbatches, maxlevel, overflow, sweeps);
   return cudaGetLastError();
+}
+
+// Cooperative launch of bfs_wide_kernel (every CTA resident): words
+// [lcap + 4][n] Words4 (vis, then the frontier slots); lcap: frontiers kept
+// for the end-of-batch codes (1-byte codes only, <= 255); big [nbig] the
+// vertices of degree > WIDE_BIG_DEG; bar3 [3] and ctrl zeroed by the caller.
+cudaError_t launch_bfs_wide(int code, int n, int nb, const int* rp, const int* ci, const int* tile_base,
+                            const int* strip_len, void* D, void* words, int lcap, const int* big, int nbig,
+                            unsigned long long* bar3, Ctrl* ctrl, long long timeout_ns, int sm_count, int* maxlevel,
+                            int* overflow, int* sweeps, cudaStream_t st) {
+  if (lcap < 0 || lcap > 255) return cudaErrorInvalidValue;
+  const void* fn = (code == CODE_U8) ? (const void*)bfs_wide_kernel<CODE_U8> : (const void*)bfs_wide_kernel<CODE_F32>;
+  int bps = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, 512, 0);
+  if (e != cudaSuccess) return e;
+  if (bps < 1) return cudaErrorInvalidConfiguration;
+  Words4* w4 = reinterpret_cast<Words4*>(words);
+  void* args[] = {&n,    &nb,   (void*)&rp, (void*)&ci,  (void*)&tile_base, (void*)&strip_len,
+                  &D,    &w4,   &lcap,      (void*)&big, &nbig,             &bar3,
+                  &ctrl, &timeout_ns, &maxlevel, &overflow,  &sweeps};
+  return cudaLaunchCooperativeKernel(fn, dim3(bps * sm_count), dim3(512), args, 0, st);
 }
 
 cudaError_t launch_sssp(int n, int nb, const int* rp, const int* ci, const float* len, const int* tile_base,

@@ -20,6 +20,10 @@ namespace fdl {
 cudaError_t launch_bfs(int code, int n, int nb, const int* rp, const int* ci, const int* tile_base,
                        const int* strip_len, void* D, unsigned long long* scratch, size_t stride, int grid,
                        int* maxlevel, int* overflow, int* sweeps, cudaStream_t st);
+cudaError_t launch_bfs_wide(int code, int n, int nb, const int* rp, const int* ci, const int* tile_base,
+                            const int* strip_len, void* D, void* words, int lcap, const int* big, int nbig,
+                            unsigned long long* bar3, Ctrl* ctrl, long long timeout_ns, int sm_count, int* maxlevel,
+                            int* overflow, int* sweeps, cudaStream_t st);
 cudaError_t launch_sssp(int n, int nb, const int* rp, const int* ci, const float* len, const int* tile_base,
                         const int* strip_len, float* D, int* scratch, int grid, int* maxbits, int* err,
                         cudaStream_t st);
@@ -128,7 +132,8 @@ struct fd_layout {
   int* d_wrev = nullptr;  // index of the reverse entry of every CSR entry
   int wnnz = 0;
   int wsimple = 0;        // no self loops, no repeated entries
-  int bfs_sweeps = 0;     // passes over the edge list of all 64-source searches
+  int bfs_sweeps = 0;     // passes over the edge list of all multi-source searches
+  int bfs_sources = 0;    // sources per search: 64 (one CTA each) or 256 (all CTAs, level-synchronous)
   // unrolled differentiation: pair sensitivities summed over the adjoint steps (tile layout)
   float* d_dbar = nullptr;
   float* d_adj = nullptr;  // [4][n][dim]: Y, Yb, lam, Xb staging
@@ -411,7 +416,8 @@ fd_status build_distances(fd_layout* h, const std::vector<int>& rp, const std::v
   FD_TRYC(cudaMemcpyAsync(d_tile_ik, tile_ik.data(), h->ntiles * sizeof(int2), cudaMemcpyHostToDevice, st));
 
   int code = len ? CODE_F32 : CODE_U8;
-  if (code == CODE_U8 && host_ecc0(n, rp, ci) >= 254) code = CODE_F32;
+  const int ecc0 = n ? host_ecc0(n, rp, ci) : 0;
+  if (code == CODE_U8 && ecc0 >= 254) code = CODE_F32;
   float fill = 0.f;
   for (int attempt = 0; attempt < 2; ++attempt) {
     h->code = code;
@@ -423,19 +429,61 @@ fd_status build_distances(fd_layout* h, const std::vector<int>& rp, const std::v
     FD_TRYC(cudaMemsetAsync(d_flags, 0, 5 * sizeof(int), st));
     int diameter = 0;
     if (!len) {
-      const int nbatches = (n + 63) / 64;
-      const int grid = std::max(1, std::min(nbatches, 2 * h->sm_count));
-      const size_t stride = (size_t)3 * n;
       if (scratch) cudaFree(scratch);
       scratch = nullptr;
-      FD_TRYC(cudaMalloc(&scratch, (size_t)grid * stride * sizeof(unsigned long long)));
+      // Level-synchronous 256-source searches over all CTAs for large graphs
+      // of few levels (a grid barrier per level); one 64-source search per
+      // CTA otherwise.  FDLAYOUT_BFS_WIDE=0/1 forces either (testing).
+      bool wide = n >= 65536 && ecc0 <= 32;
+      if (const char* e = std::getenv("FDLAYOUT_BFS_WIDE")) wide = (e[0] == '1');
+      Ctrl* d_bctrl = nullptr;
+      int* d_big = nullptr;
+      std::vector<int> big;
+      // frontiers kept for the end-of-batch 1-byte codes: the levels of
+      // vertex 0's component are <= 2 ecc0, other components' may be more
+      // (deeper levels write their codes as reached)
+      const int lcap = (code == CODE_U8) ? std::min(255, std::max(16, 2 * ecc0 + 1)) : 0;
+      const size_t wbytes = (size_t)(lcap + 4) * n * 32, cbytes = (sizeof(Ctrl) + 255) / 256 * 256;
+      if (wide) {
+        for (int v = 0; v < n; ++v)
+          if (rp[v + 1] - rp[v] > 16) big.push_back(v);  // WIDE_BIG_DEG: a warp per vertex
+        std::stable_sort(big.begin(), big.end(),
+                         [&](int a, int b) { return rp[a + 1] - rp[a] > rp[b + 1] - rp[b]; });
+        // [lcap + 4][n] 32-byte words, the 3 barrier slots, the error state, big[]
+        FD_TRYC(cudaMalloc(&scratch, wbytes + 256 + cbytes + big.size() * sizeof(int) + 4));
+        FD_TRYC(cudaMemsetAsync((char*)scratch + wbytes, 0, 256 + cbytes, st));
+        d_bctrl = reinterpret_cast<Ctrl*>((char*)scratch + wbytes + 256);
+        d_big = reinterpret_cast<int*>((char*)scratch + wbytes + 256 + cbytes);
+        if (!big.empty())
+          FD_TRYC(cudaMemcpyAsync(d_big, big.data(), big.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+      } else {
+        const int nbatches = (n + 63) / 64;
+        const int grid = std::max(1, std::min(nbatches, 2 * h->sm_count));
+        const size_t stride = (size_t)3 * n;
+        FD_TRYC(cudaMalloc(&scratch, (size_t)grid * stride * sizeof(unsigned long long)));
+      }
       FD_TRYC(cudaEventRecord(h->ev0, st));
-      FD_TRYC(launch_bfs(code, n, nb, d_rp, d_ci, h->d_tile_base, h->d_strip_len, h->D,
-                         (unsigned long long*)scratch, stride, grid, d_flags, d_flags + 1, d_flags + 3, st));
+      if (wide) {
+        FD_TRYC(launch_bfs_wide(code, n, nb, d_rp, d_ci, h->d_tile_base, h->d_strip_len, h->D, scratch, lcap, d_big,
+                                (int)big.size(), (unsigned long long*)((char*)scratch + wbytes), d_bctrl, h->bar_timeout_ns,
+                                h->sm_count, d_flags, d_flags + 1, d_flags + 3, st));
+      } else {
+        const int nbatches = (n + 63) / 64;
+        const int grid = std::max(1, std::min(nbatches, 2 * h->sm_count));
+        FD_TRYC(launch_bfs(code, n, nb, d_rp, d_ci, h->d_tile_base, h->d_strip_len, h->D,
+                           (unsigned long long*)scratch, (size_t)3 * n, grid, d_flags, d_flags + 1, d_flags + 3, st));
+      }
       FD_TRYC(cudaEventRecord(h->ev1, st));
       int flags[4];
       FD_TRYC(cudaMemcpyAsync(flags, d_flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+      int berr = 0;
+      if (wide) FD_TRYC(cudaMemcpyAsync(&berr, &d_bctrl->err, sizeof(int), cudaMemcpyDeviceToHost, st));
       FD_TRYC(cudaStreamSynchronize(st));
+      if (berr) {  // a grid-barrier wait ran out
+        cleanup();
+        return FD_ERR_TIMEOUT;
+      }
+      h->bfs_sources = wide ? 256 : 64;
       float ms = 0.f;
       FD_TRYC(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
       h->apsp_ms = ms;
@@ -1396,6 +1444,7 @@ fd_status fd_layout_info(const fd_layout* h, fd_info* info) {
   info->stages = h->nbuf;
   info->tiles_per_stage = h->tps;
   info->bfs_sweeps = h->bfs_sweeps;
+  info->bfs_sources = h->bfs_sources;
   info->factored = h->d_ainv ? 1 : 0;
   info->factor_ms = h->factor_ms;
   return FD_OK;

@@ -56,6 +56,44 @@ def test_distances_bit_exact(name):
     assert info["diameter"] == int(D.max()) or info["disconnected"] == 1
 
 
+def _short_and_long_path():
+    # vertex 0 on a 3-vertex path (eccentricity 2), beside a 300-vertex path
+    # (diameter 299 would need float codes; 200 vertices: 199 fits a byte):
+    # searches from the long path run far deeper than vertex 0's component
+    edges = [(0, 1), (1, 2)] + [(i, i + 1) for i in range(3, 202)]
+    return synth.csr_from_edges(203, edges)
+
+
+WIDE_GRAPHS = dict(GRAPHS, star700=lambda: synth.star(700), path300=lambda: synth.path(300),
+                   paths203=_short_and_long_path)
+
+
+@pytest.mark.parametrize("name", ["path2", "k3", "grid20", "er300", "tree383", "ba1500", "rgg2049", "star700",
+                                  "path300", "paths203"])
+def test_distances_bit_exact_level_synchronous(name, monkeypatch):
+    # the 256-source search over all CTAs (a grid barrier per level), forced at
+    # sizes the dense oracle holds: one ragged batch (n < 256), several batches
+    # with a ragged last one, a disconnected graph, a deep tree (many levels),
+    # vertices of degree above 16 (pulled by a warp each: the hubs of ba1500,
+    # the centre of star700), float codes (path300: diameter 299 > 254), and
+    # levels past the frontiers kept for the end-of-batch codes (paths203:
+    # those codes are written as reached and merged with the decoded ones)
+    rp, ci = WIDE_GRAPHS[name]()
+    D = _dense(rp, ci)
+    n = len(rp) - 1
+    monkeypatch.setenv("FDLAYOUT_BFS_WIDE", "1")
+    with api.Layout(rp, ci, dim=2, disconnected_policy=1) as L:
+        got = L.distance_rows(0, n)
+        info = L.info()
+    assert info["bfs_sources"] == 256
+    assert np.array_equal(got, D)
+    assert info["diameter"] == int(D.max()) or info["disconnected"] == 1
+    monkeypatch.setenv("FDLAYOUT_BFS_WIDE", "0")
+    with api.Layout(rp, ci, dim=2, disconnected_policy=1) as L:
+        assert L.info()["bfs_sources"] == 64
+        assert np.array_equal(L.distance_rows(0, n), got)
+
+
 def test_distances_weighted():
     rp, ci = synth.delaunay(300, seed=7)
     rng = np.random.default_rng(0)

@@ -76,6 +76,7 @@ def test_ba200k(graph):
         with api.Layout(rp, ci, dim=dim) as L:
             info = L.info()
             assert info["code_bytes"] == 1 and info["disconnected"] == 0
+            assert info["bfs_sources"] == 256  # n >= 65536, few levels: the level-synchronous search
             for i in rows[:6]:
                 assert np.array_equal(L.distance_rows(int(i), 1)[0],
                                       oracle.bfs_row(rp, ci, int(i)).astype(np.float64))
