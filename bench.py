@@ -452,7 +452,9 @@ def run_ours(args, rank, world, local_rank):
                  "frac": {d: apsp_bytes[d] / (apsp[d] / 1e3) / 1e9 / hbm for d in dims},
                  "note": "once per layout before the timed steps; bytes a pass over the edge list must move per "
                          "multi-source search (row_ptr, reached and next words, col_idx, neighbour frontier words) "
-                         "times the passes run, plus 1 B per pair written"},
+                         "times the passes run, plus 1 B per pair written; for bfs_wide_kernel (256 sources "
+                         "per search, all CTAs, a grid barrier per level) the words are L2-resident and the "
+                         "kernel is bound by the per-level latency, not by these bytes"},
         "layout_kernel_ms_per_step": acc["kernel_ms"] / args.steps,
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": acc_e["h2d"] // max(args.steps, 1),

@@ -285,13 +285,23 @@ __device__ __forceinline__ void wide_decode_word(unsigned char* D, int v, int s0
   unsigned long long c[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) c[q] = 0ull;
-  for (int l = 1; l <= lmax; ++l) {
-    const unsigned long long x = __ldcg(&F[(size_t)l * n + v].w[w]);
-    if (!x) continue;
+  auto level_bytes = [&](unsigned long long x, int l) {
+    if (!x) return;
     const unsigned long long lv = (unsigned long long)l;
 #pragma unroll
     for (int q = 0; q < 8; ++q) c[q] |= spread[(x >> (8 * q)) & 0xff] * lv;
+  };
+  const unsigned long long* Fw = &F[v].w[w];  // F_l's word w of v: Fw[4 n l]
+  int l = 1;
+  for (; l + 3 <= lmax; l += 4) {  // four loads in flight
+    const unsigned long long x0 = __ldcg(Fw + (size_t)4 * n * l), x1 = __ldcg(Fw + (size_t)4 * n * (l + 1)),
+                             x2 = __ldcg(Fw + (size_t)4 * n * (l + 2)), x3 = __ldcg(Fw + (size_t)4 * n * (l + 3));
+    level_bytes(x0, l);
+    level_bytes(x1, l + 1);
+    level_bytes(x2, l + 2);
+    level_bytes(x3, l + 3);
   }
+  for (; l <= lmax; ++l) level_bytes(__ldcg(Fw + (size_t)4 * n * l), l);
   unsigned char* row = D + (size_t)(tile_base[I] + k) * TILE * TILE + (v % TILE) * TILE + il0;
 #pragma unroll
   for (int g = 0; g < 4; ++g) {
