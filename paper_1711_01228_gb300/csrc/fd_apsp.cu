@@ -150,11 +150,14 @@ __global__ void __launch_bounds__(1024) bfs_batch_kernel(int n, int nb, const in
 // levels (and float codes) are written as reached.
 //
 // A level ends with its slowest vertex, so vertices of degree above
-// WIDE_BIG_DEG (listed in big[] by the host, largest degree first) are pulled
-// by a warp each, the lanes striding over the edges; the others by a thread
-// each.  A batch ends after the level that reached nothing or the level after
+// WIDE_BIG_DEG are pulled by a warp each, the lanes striding over the edges
+// (tasks[] from the host, largest degree first), the others by a thread
+// each; a vertex of degree above WIDE_HUB_CHUNK (a hub) is split into tasks
+// of WIDE_HUB_CHUNK edges, whose warps OR their partial words into the
+// hub's word and the last of which finishes the vertex.  A batch ends after the level that reached nothing or the level after
 // which every vertex holds every source.
 constexpr int WIDE_BIG_DEG = 16;
+constexpr int WIDE_HUB_CHUNK = 256;
 
 struct __align__(32) Words4 {
   unsigned long long w[4];
@@ -347,8 +350,10 @@ __global__ void __launch_bounds__(512, 2) bfs_wide_kernel(int n, int nb, const i
                                                            const int* __restrict__ col_idx,
                                                            const int* __restrict__ tile_base,
                                                            const int* __restrict__ strip_len, void* D,
-                                                           Words4* words, int lcap, const int* __restrict__ big,
-                                                           int nbig, unsigned long long* bar3, Ctrl* ctrl,
+                                                           Words4* words, int lcap, const int4* __restrict__ tasks,
+                                                           int ntasks, Words4* hubacc, int* hubcnt,
+                                                           const int* __restrict__ hubparts, int nhub,
+                                                           unsigned long long* bar3, Ctrl* ctrl,
                                                            long long timeout_ns, int* maxlevel, int* overflow,
                                                            int* sweeps) {
   __shared__ unsigned long long spread[256];
@@ -425,11 +430,26 @@ __global__ void __launch_bounds__(512, 2) bfs_wide_kernel(int n, int nb, const i
         }
         nx[v] = nw;
       }
-      // vertices of larger degree: a warp each; lane l then writes the codes
-      // of bits [8 (l % 8), 8 (l % 8) + 8) of word l / 8
-      for (int i = gwarp; i < nbig; i += nwarps) {
-        const int v = big[i];
-        const Words4 vs = (level == 1) ? self_bits(v, s0, nsrc) : vis[v];
+      // vertices of larger degree: a task per warp, (v, first edge, end,
+      // hub): hub -1 for a whole vertex, else 2 h + (1 for the hub's first
+      // task).  The warp that finishes a vertex (the whole-vertex one, or a
+      // hub's last) writes its words; lane l then writes the codes of bits
+      // [8 (l % 8), 8 (l % 8) + 8) of word l / 8.  vis[v] of a hub is
+      // written by whichever warp finishes it: read past L1.
+      for (int i = gwarp; i < ntasks; i += nwarps) {
+        const int4 tk = tasks[i];
+        const int v = tk.x, hub = tk.w;
+        Words4 vs;
+        if (level == 1) {
+          vs = self_bits(v, s0, nsrc);
+        } else {
+          const ulonglong2* q = reinterpret_cast<const ulonglong2*>(vis + v);
+          const ulonglong2 lo = __ldcg(q), hi = __ldcg(q + 1);
+          vs.w[0] = lo.x;
+          vs.w[1] = lo.y;
+          vs.w[2] = hi.x;
+          vs.w[3] = hi.y;
+        }
         bool open = false;
 #pragma unroll
         for (int w = 0; w < 4; ++w) open = open || (vs.w[w] != full_at(w));
@@ -437,37 +457,69 @@ __global__ void __launch_bounds__(512, 2) bfs_wide_kernel(int n, int nb, const i
 #pragma unroll
         for (int w = 0; w < 4; ++w) nw.w[w] = 0ull;
         Words4 nv = vs;
-        if (open) {  // warp-uniform
+        bool finish = (hub < 0) || (!open && (hub & 1));  // warp-uniform
+        if (open) {  // warp-uniform (every task of a hub reads the same vis)
           Words4 acc;
 #pragma unroll
           for (int w = 0; w < 4; ++w) acc.w[w] = 0ull;
-          const int e0 = row_ptr[v] + lane, e1 = row_ptr[v + 1];
           if (level == 1)
-            source_or(acc, col_idx, e0, e1, 32, s0, nsrc);
+            source_or(acc, col_idx, tk.y + lane, tk.z, 32, s0, nsrc);
           else
-            gather_or(acc, fr, col_idx, e0, e1, 32);
-          bool got = false, still = false;
+            gather_or(acc, fr, col_idx, tk.y + lane, tk.z, 32);
 #pragma unroll
           for (int w = 0; w < 4; ++w) {
             const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)acc.w[w]);
             const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(acc.w[w] >> 32));
-            nw.w[w] = (((unsigned long long)hi << 32) | lo) & ~vs.w[w] & full_at(w);
-            nv.w[w] = vs.w[w] | nw.w[w];
-            got = got || (nw.w[w] != 0ull);
-            still = still || (nv.w[w] != full_at(w));
+            acc.w[w] = ((unsigned long long)hi << 32) | lo;
           }
-          if (still) open_after = 2;
-          if (got) {
-            any = 1;
-            if (now) {
-              const int w = lane >> 3;
-              const unsigned long long mine = pick4(nw.w, w) & (0xffull << (8 * (lane & 7)));
-              if (mine)
-                wide_codes<CODE>(D, v, s0, w, mine, nb, tile_base, strip_len, full_at(w), level, overflow);
+          if (hub >= 0) {
+            const int h = hub >> 1;
+            int last = 0;
+            if (lane == 0) {
+#pragma unroll
+              for (int w = 0; w < 4; ++w)
+                if (acc.w[w]) atomicOr(&hubacc[h].w[w], acc.w[w]);
+              __threadfence();
+              last = (atomicAdd(hubcnt + h, 1) == hubparts[h] - 1);
+            }
+            finish = __shfl_sync(0xffffffffu, last, 0) != 0;
+            if (finish) {  // every other task of the hub has added its words
+              __threadfence();
+              const ulonglong2* q = reinterpret_cast<const ulonglong2*>(hubacc + h);
+              const ulonglong2 lo = __ldcg(q), hi = __ldcg(q + 1);
+              acc.w[0] = lo.x;
+              acc.w[1] = lo.y;
+              acc.w[2] = hi.x;
+              acc.w[3] = hi.y;
+              __syncwarp();
+              if (lane == 0) {  // ready for the next level (after the grid barrier)
+                hubacc[h] = Words4{{0ull, 0ull, 0ull, 0ull}};
+                hubcnt[h] = 0;
+              }
+            }
+          }
+          if (finish) {
+            bool got = false, still = false;
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+              nw.w[w] = acc.w[w] & ~vs.w[w] & full_at(w);
+              nv.w[w] = vs.w[w] | nw.w[w];
+              got = got || (nw.w[w] != 0ull);
+              still = still || (nv.w[w] != full_at(w));
+            }
+            if (still) open_after = 2;
+            if (got) {
+              any = 1;
+              if (now) {
+                const int w = lane >> 3;
+                const unsigned long long mine = pick4(nw.w, w) & (0xffull << (8 * (lane & 7)));
+                if (mine)
+                  wide_codes<CODE>(D, v, s0, w, mine, nb, tile_base, strip_len, full_at(w), level, overflow);
+              }
             }
           }
         }
-        if (lane == 0) {
+        if (finish && lane == 0) {
           if (open || level == 1) vis[v] = nv;
           nx[v] = nw;
         }
@@ -493,10 +545,15 @@ __global__ void __launch_bounds__(512, 2) bfs_wide_kernel(int n, int nb, const i
         for (int w = 0; w < 4; ++w)
           wide_decode_word(Du, v, s0, w, full_at(w), F, n, lmax, merge, nb, tile_base, strip_len, spread);
       }
-      for (int i = gwarp; i < nbig; i += nwarps)
-        if (lane < 4)
-          wide_decode_word(Du, big[i], s0, lane, full_at(lane), F, n, lmax, merge, nb, tile_base, strip_len,
+      for (int i = gwarp; i < ntasks; i += nwarps) {
+        const int4 tk = tasks[i];
+        if (lane < 4 && (tk.w < 0 || (tk.w & 1)))  // a hub by the warp of its first task
+          wide_decode_word(Du, tk.x, s0, lane, full_at(lane), F, n, lmax, merge, nb, tile_base, strip_len,
                            spread);
+      }
+      // a hub's words of the next batch's level 1 are written by whichever
+      // warp finishes it, possibly another than the one that just read them
+      if (nhub > 0 && wide_barrier(bar3, b++, 0, ctrl, timeout_ns) < 0) return;
     }
 #undef full_at
     if (gtid == 0) {
@@ -845,12 +902,16 @@ cudaError_t launch_bfs(int code, int n, int nb, const int* rp, const int* ci, co
 
 // Cooperative launch of bfs_wide_kernel (every CTA resident): words
 // [lcap + 4][n] Words4 (vis, then the frontier slots); lcap: frontiers kept
-// for the end-of-batch codes (1-byte codes only, <= 255); big [nbig] the
-// vertices of degree > WIDE_BIG_DEG; bar3 [3] and ctrl zeroed by the caller.
+// for the end-of-batch codes (1-byte codes only, <= 255); tasks [ntasks] the
+// warp tasks of the vertices of degree > WIDE_BIG_DEG (hubs of degree >
+// WIDE_HUB_CHUNK split in tasks of WIDE_HUB_CHUNK edges; hubparts [nhub]
+// their task counts); hubacc [nhub] (32-byte aligned), hubcnt [nhub], bar3
+// [3] and ctrl zeroed by the caller.
 cudaError_t launch_bfs_wide(int code, int n, int nb, const int* rp, const int* ci, const int* tile_base,
-                            const int* strip_len, void* D, void* words, int lcap, const int* big, int nbig,
-                            unsigned long long* bar3, Ctrl* ctrl, long long timeout_ns, int sm_count, int* maxlevel,
-                            int* overflow, int* sweeps, cudaStream_t st) {
+                            const int* strip_len, void* D, void* words, int lcap, const int4* tasks, int ntasks,
+                            void* hubacc, int* hubcnt, const int* hubparts, int nhub, unsigned long long* bar3,
+                            Ctrl* ctrl, long long timeout_ns, int sm_count, int* maxlevel, int* overflow, int* sweeps,
+                            cudaStream_t st) {
   if (lcap < 0 || lcap > 255) return cudaErrorInvalidValue;
   const void* fn = (code == CODE_U8) ? (const void*)bfs_wide_kernel<CODE_U8> : (const void*)bfs_wide_kernel<CODE_F32>;
   int bps = 0;
@@ -858,8 +919,10 @@ cudaError_t launch_bfs_wide(int code, int n, int nb, const int* rp, const int* c
   if (e != cudaSuccess) return e;
   if (bps < 1) return cudaErrorInvalidConfiguration;
   Words4* w4 = reinterpret_cast<Words4*>(words);
+  Words4* hacc = reinterpret_cast<Words4*>(hubacc);
   void* args[] = {&n,    &nb,   (void*)&rp, (void*)&ci,  (void*)&tile_base, (void*)&strip_len,
-                  &D,    &w4,   &lcap,      (void*)&big, &nbig,             &bar3,
+                  &D,    &w4,   &lcap,      (void*)&tasks, &ntasks,         &hacc, &hubcnt, (void*)&hubparts, &nhub,
+                  &bar3,
                   &ctrl, &timeout_ns, &maxlevel, &overflow,  &sweeps};
   return cudaLaunchCooperativeKernel(fn, dim3(bps * sm_count), dim3(512), args, 0, st);
 }

@@ -21,9 +21,10 @@ cudaError_t launch_bfs(int code, int n, int nb, const int* rp, const int* ci, co
                        const int* strip_len, void* D, unsigned long long* scratch, size_t stride, int grid,
                        int* maxlevel, int* overflow, int* sweeps, cudaStream_t st);
 cudaError_t launch_bfs_wide(int code, int n, int nb, const int* rp, const int* ci, const int* tile_base,
-                            const int* strip_len, void* D, void* words, int lcap, const int* big, int nbig,
-                            unsigned long long* bar3, Ctrl* ctrl, long long timeout_ns, int sm_count, int* maxlevel,
-                            int* overflow, int* sweeps, cudaStream_t st);
+                            const int* strip_len, void* D, void* words, int lcap, const int4* tasks, int ntasks,
+                            void* hubacc, int* hubcnt, const int* hubparts, int nhub, unsigned long long* bar3,
+                            Ctrl* ctrl, long long timeout_ns, int sm_count, int* maxlevel, int* overflow, int* sweeps,
+                            cudaStream_t st);
 cudaError_t launch_sssp(int n, int nb, const int* rp, const int* ci, const float* len, const int* tile_base,
                         const int* strip_len, float* D, int* scratch, int grid, int* maxbits, int* err,
                         cudaStream_t st);
@@ -437,25 +438,56 @@ fd_status build_distances(fd_layout* h, const std::vector<int>& rp, const std::v
       bool wide = n >= 65536 && ecc0 <= 32;
       if (const char* e = std::getenv("FDLAYOUT_BFS_WIDE")) wide = (e[0] == '1');
       Ctrl* d_bctrl = nullptr;
-      int* d_big = nullptr;
-      std::vector<int> big;
+      int4* d_tasks = nullptr;
+      int *d_hubcnt = nullptr, *d_hubparts = nullptr;
+      void* d_hubacc = nullptr;
+      std::vector<int4> tasks;
+      std::vector<int> hubparts;
       // frontiers kept for the end-of-batch 1-byte codes: the levels of
       // vertex 0's component are <= 2 ecc0, other components' may be more
       // (deeper levels write their codes as reached)
       const int lcap = (code == CODE_U8) ? std::min(255, std::max(16, 2 * ecc0 + 1)) : 0;
       const size_t wbytes = (size_t)(lcap + 4) * n * 32, cbytes = (sizeof(Ctrl) + 255) / 256 * 256;
       if (wide) {
+        // warp tasks: vertices of degree > 16 (WIDE_BIG_DEG), largest first;
+        // a hub of degree > 256 (WIDE_HUB_CHUNK) as tasks of 256 edges
+        std::vector<int> big;
         for (int v = 0; v < n; ++v)
-          if (rp[v + 1] - rp[v] > 16) big.push_back(v);  // WIDE_BIG_DEG: a warp per vertex
+          if (rp[v + 1] - rp[v] > 16) big.push_back(v);
         std::stable_sort(big.begin(), big.end(),
                          [&](int a, int b) { return rp[a + 1] - rp[a] > rp[b + 1] - rp[b]; });
-        // [lcap + 4][n] 32-byte words, the 3 barrier slots, the error state, big[]
-        FD_TRYC(cudaMalloc(&scratch, wbytes + 256 + cbytes + big.size() * sizeof(int) + 4));
-        FD_TRYC(cudaMemsetAsync((char*)scratch + wbytes, 0, 256 + cbytes, st));
-        d_bctrl = reinterpret_cast<Ctrl*>((char*)scratch + wbytes + 256);
-        d_big = reinterpret_cast<int*>((char*)scratch + wbytes + 256 + cbytes);
-        if (!big.empty())
-          FD_TRYC(cudaMemcpyAsync(d_big, big.data(), big.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+        for (int v : big) {
+          const int deg = rp[v + 1] - rp[v];
+          if (deg > 256) {
+            const int hid = (int)hubparts.size(), parts = (deg + 255) / 256;
+            hubparts.push_back(parts);
+            for (int q = 0; q < parts; ++q)
+              tasks.push_back(make_int4(v, rp[v] + 256 * q, std::min(rp[v] + 256 * (q + 1), rp[v + 1]),
+                                        2 * hid + (q == 0 ? 1 : 0)));
+          } else {
+            tasks.push_back(make_int4(v, rp[v], rp[v + 1], -1));
+          }
+        }
+        const size_t nh = hubparts.size();
+        const size_t tbytes = (tasks.size() * sizeof(int4) + 255) / 256 * 256;
+        const size_t hbytes = nh * 32 + nh * sizeof(int);  // hub words, hub counters (zeroed)
+        // [lcap + 4][n] 32-byte words, the 3 barrier slots, the error state,
+        // tasks, hub words and counters, hub task counts
+        char* base = nullptr;
+        FD_TRYC(cudaMalloc(&scratch, wbytes + 256 + cbytes + tbytes + hbytes + nh * sizeof(int) + 16));
+        base = (char*)scratch + wbytes;
+        FD_TRYC(cudaMemsetAsync(base, 0, 256 + cbytes, st));
+        d_bctrl = reinterpret_cast<Ctrl*>(base + 256);
+        d_tasks = reinterpret_cast<int4*>(base + 256 + cbytes);
+        d_hubacc = base + 256 + cbytes + tbytes;
+        d_hubcnt = reinterpret_cast<int*>(base + 256 + cbytes + tbytes + nh * 32);
+        d_hubparts = d_hubcnt + nh;
+        if (!tasks.empty())
+          FD_TRYC(cudaMemcpyAsync(d_tasks, tasks.data(), tasks.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+        if (nh) {
+          FD_TRYC(cudaMemsetAsync(d_hubacc, 0, hbytes, st));
+          FD_TRYC(cudaMemcpyAsync(d_hubparts, hubparts.data(), nh * sizeof(int), cudaMemcpyHostToDevice, st));
+        }
       } else {
         const int nbatches = (n + 63) / 64;
         const int grid = std::max(1, std::min(nbatches, 2 * h->sm_count));
@@ -464,8 +496,9 @@ fd_status build_distances(fd_layout* h, const std::vector<int>& rp, const std::v
       }
       FD_TRYC(cudaEventRecord(h->ev0, st));
       if (wide) {
-        FD_TRYC(launch_bfs_wide(code, n, nb, d_rp, d_ci, h->d_tile_base, h->d_strip_len, h->D, scratch, lcap, d_big,
-                                (int)big.size(), (unsigned long long*)((char*)scratch + wbytes), d_bctrl, h->bar_timeout_ns,
+        FD_TRYC(launch_bfs_wide(code, n, nb, d_rp, d_ci, h->d_tile_base, h->d_strip_len, h->D, scratch, lcap, d_tasks,
+                                (int)tasks.size(), d_hubacc, d_hubcnt, d_hubparts, (int)hubparts.size(),
+                                (unsigned long long*)((char*)scratch + wbytes), d_bctrl, h->bar_timeout_ns,
                                 h->sm_count, d_flags, d_flags + 1, d_flags + 3, st));
       } else {
         const int nbatches = (n + 63) / 64;

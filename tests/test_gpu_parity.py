@@ -64,18 +64,32 @@ def _short_and_long_path():
     return synth.csr_from_edges(203, edges)
 
 
+def _er_with_hubs():
+    # an Erdos-Renyi graph (n = 2000, mean degree 4) with two hubs joined to
+    # 700 and 300 random vertices: degrees above 256, split over several warps
+    rp, ci = synth.erdos_renyi(2000, 4.0, seed=3)
+    rng = np.random.default_rng(5)
+    edges = {(min(u, int(v)), max(u, int(v))) for u in range(2000) for v in ci[rp[u]:rp[u + 1]] if u != v}
+    for hub, k in ((17, 700), (1500, 300)):
+        for v in rng.choice(2000, k, replace=False):
+            if int(v) != hub:
+                edges.add((min(hub, int(v)), max(hub, int(v))))
+    return synth.csr_from_edges(2000, sorted(edges))
+
+
 WIDE_GRAPHS = dict(GRAPHS, star700=lambda: synth.star(700), path300=lambda: synth.path(300),
-                   paths203=_short_and_long_path)
+                   paths203=_short_and_long_path, erhubs2000=_er_with_hubs)
 
 
 @pytest.mark.parametrize("name", ["path2", "k3", "grid20", "er300", "tree383", "ba1500", "rgg2049", "star700",
-                                  "path300", "paths203"])
+                                  "path300", "paths203", "erhubs2000"])
 def test_distances_bit_exact_level_synchronous(name, monkeypatch):
     # the 256-source search over all CTAs (a grid barrier per level), forced at
     # sizes the dense oracle holds: one ragged batch (n < 256), several batches
     # with a ragged last one, a disconnected graph, a deep tree (many levels),
-    # vertices of degree above 16 (pulled by a warp each: the hubs of ba1500,
-    # the centre of star700), float codes (path300: diameter 299 > 254), and
+    # vertices of degree above 16 (pulled by a warp each: the hubs of ba1500;
+    # above 256, split over several warps: the centre of star700, the two
+    # hubs of erhubs2000), float codes (path300: diameter 299 > 254), and
     # levels past the frontiers kept for the end-of-batch codes (paths203:
     # those codes are written as reached and merged with the decoded ones)
     rp, ci = WIDE_GRAPHS[name]()
