@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(512, 2) bfs_wide_kernel(int n, int nb, const i
   }
   __syncthreads();
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gstride = gridDim.x * blockDim.x;
-  const int lane = threadIdx.x & 31, gwarp = gtid >> 5, nwarps = gstride >> 5;
+  const int lane = threadIdx.x & 31, nwarps = gstride >> 5, twarp = (gstride - 1 - gtid) >> 5;
   const int nbatches = (n + 255) / 256;
   Words4* vis = words;
   Words4* F = words + n;  // [lcap + 3][n]; slot 0 unused (level 1 reads col_idx alone)
@@ -435,8 +435,10 @@ __global__ void __launch_bounds__(512, 2) bfs_wide_kernel(int n, int nb, const i
       // task).  The warp that finishes a vertex (the whole-vertex one, or a
       // hub's last) writes its words; lane l then writes the codes of bits
       // [8 (l % 8), 8 (l % 8) + 8) of word l / 8.  vis[v] of a hub is
-      // written by whichever warp finishes it: read past L1.
-      for (int i = gwarp; i < ntasks; i += nwarps) {
+      // written by whichever warp finishes it: read past L1.  Tasks go to
+      // the warps from the last one down (twarp), so the largest ones land
+      // on warps whose threads hold one small vertex, not two.
+      for (int i = twarp; i < ntasks; i += nwarps) {
         const int4 tk = tasks[i];
         const int v = tk.x, hub = tk.w;
         Words4 vs;
@@ -545,7 +547,7 @@ __global__ void __launch_bounds__(512, 2) bfs_wide_kernel(int n, int nb, const i
         for (int w = 0; w < 4; ++w)
           wide_decode_word(Du, v, s0, w, full_at(w), F, n, lmax, merge, nb, tile_base, strip_len, spread);
       }
-      for (int i = gwarp; i < ntasks; i += nwarps) {
+      for (int i = twarp; i < ntasks; i += nwarps) {
         const int4 tk = tasks[i];
         if (lane < 4 && (tk.w < 0 || (tk.w & 1)))  // a hub by the warp of its first task
           wide_decode_word(Du, tk.x, s0, lane, full_at(lane), F, n, lmax, merge, nb, tile_base, strip_len,
