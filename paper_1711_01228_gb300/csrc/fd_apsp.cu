@@ -154,8 +154,9 @@ __global__ void __launch_bounds__(1024) bfs_batch_kernel(int n, int nb, const in
 // (tasks[] from the host, largest degree first), the others by a thread
 // each; a vertex of degree above WIDE_HUB_CHUNK (a hub) is split into tasks
 // of WIDE_HUB_CHUNK edges, whose warps OR their partial words into the
-// hub's word and the last of which finishes the vertex.  A batch ends after the level that reached nothing or the level after
-// which every vertex holds every source.
+// hub's word and the last of which finishes the vertex.  A batch ends after
+// the level that reached nothing or the level after which every vertex
+// holds every source.
 constexpr int WIDE_BIG_DEG = 16;
 constexpr int WIDE_HUB_CHUNK = 256;
 
